@@ -1,0 +1,216 @@
+"""ctypes wrapper of the FP64 CPU oracle (``qbx_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers. It shares no code with the CUDA path
+and never imports it.
+
+Every function computes the plain definition of a quantity of the paper
+(Rachh, Kloeckner, O'Neil, Fast algorithms for QBX I), FP64:
+
+* ``centres``                Sec. 2.2, c = s + side (h_k/2) n.
+* ``qbx_coefficients``       Sec. 7 Eq. (localexpcoeffs): alpha at centres over all sources.
+* ``direct_potential``       Sec. 3.2 Eq. (gauss-layerpot): smooth Gauss quadrature.
+* ``qbx_evaluate``           Sec. 2.1 Eq. (phiapprox): truncated J-expansion.
+* ``associate``              Sec. 6.1 target association, brute force over all centres.
+* ``layer_potential``        Sec. 2.3 steps 2-3 without acceleration: associate,
+                             then QBX where associated and direct quadrature elsewhere.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qbx_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I8 = ctypes.POINTER(ctypes.c_int8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (FP64, OpenMP, no fast-math, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp",
+           "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+            lib.oracle_bessel.argtypes = [ctypes.c_int, ctypes.c_int64, _D, _D, _D]
+            lib.oracle_centres.argtypes = [ctypes.c_int64, _D, _D, _I64, _D, ctypes.c_int, _D, _D]
+            lib.oracle_qbx_coefficients.argtypes = [
+                ctypes.c_int64, _D, _D, _D, _D, _D,
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int64, _D, ctypes.c_int, _D]
+            lib.oracle_direct_potential.argtypes = [
+                ctypes.c_int64, _D, _D, _D, _D, _D,
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int64, _D, _D]
+            lib.oracle_qbx_evaluate.argtypes = [ctypes.c_int64, _D, _I32, _D, _D, ctypes.c_int,
+                                                ctypes.c_double, _D]
+            lib.oracle_associate.restype = ctypes.c_int64
+            lib.oracle_associate.argtypes = [
+                ctypes.c_int64, _D, _I64, _I8, ctypes.c_int64, _D, _I64, _D,
+                ctypes.c_int64, _D, _D, ctypes.c_double, _I32]
+            _lib = lib
+    return _lib
+
+
+def _p(a, ptype):
+    if a is None:
+        return ctypes.cast(None, ptype)
+    return a.ctypes.data_as(ptype)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().oracle_set_num_threads(int(n))
+
+
+def bessel_j(order: int, x) -> np.ndarray:
+    x = _f64(np.atleast_1d(x))
+    out = np.empty_like(x)
+    _load().oracle_bessel(int(order), x.size, _p(x, _D), _p(out, _D), _p(None, _D))
+    return out
+
+
+def hankel1(order: int, x) -> np.ndarray:
+    x = _f64(np.atleast_1d(x))
+    out = np.empty(2 * x.size)
+    _load().oracle_bessel(int(order), x.size, _p(x, _D), _p(None, _D), _p(out, _D))
+    return out.view(np.complex128)
+
+
+def centres(node_xy, normal_xy, panel_of_node, panel_h, sides: int):
+    node_xy = _f64(node_xy)
+    normal_xy = _f64(normal_xy)
+    panel_of_node = np.ascontiguousarray(panel_of_node, dtype=np.int64)
+    panel_h = _f64(panel_h)
+    n = node_xy.shape[0]
+    cxy = np.empty((n * sides, 2))
+    crad = np.empty(n * sides)
+    _load().oracle_centres(n, _p(node_xy, _D), _p(normal_xy, _D), _p(panel_of_node, _I64),
+                           _p(panel_h, _D), int(sides), _p(cxy, _D), _p(crad, _D))
+    return cxy, crad
+
+
+def qbx_coefficients(src_xy, src_normal, weight, k, ctr_xy, p, sigma_S=None, sigma_D=None,
+                     cS=1.0, cD=1.0) -> np.ndarray:
+    src_xy, src_normal, weight, ctr_xy = map(_f64, (src_xy, src_normal, weight, ctr_xy))
+    sS, sD = _c128(sigma_S), _c128(sigma_D)
+    n_ctr = ctr_xy.shape[0]
+    P = 2 * p + 1
+    out = np.empty(2 * n_ctr * P)
+    cS, cD = complex(cS), complex(cD)
+    _load().oracle_qbx_coefficients(src_xy.shape[0], _p(src_xy, _D), _p(src_normal, _D),
+                                    _p(weight, _D), _p(sS, _D), _p(sD, _D),
+                                    cS.real, cS.imag, cD.real, cD.imag, float(k),
+                                    n_ctr, _p(ctr_xy, _D), int(p), _p(out, _D))
+    return out.view(np.complex128).reshape(n_ctr, P)
+
+
+def direct_potential(src_xy, src_normal, weight, k, tgt_xy, sigma_S=None, sigma_D=None,
+                     cS=1.0, cD=1.0) -> np.ndarray:
+    src_xy, src_normal, weight, tgt_xy = map(_f64, (src_xy, src_normal, weight, tgt_xy))
+    sS, sD = _c128(sigma_S), _c128(sigma_D)
+    n_tgt = tgt_xy.shape[0]
+    out = np.empty(2 * n_tgt)
+    cS, cD = complex(cS), complex(cD)
+    _load().oracle_direct_potential(src_xy.shape[0], _p(src_xy, _D), _p(src_normal, _D),
+                                    _p(weight, _D), _p(sS, _D), _p(sD, _D),
+                                    cS.real, cS.imag, cD.real, cD.imag, float(k),
+                                    n_tgt, _p(tgt_xy, _D), _p(out, _D))
+    return out.view(np.complex128)
+
+
+def qbx_evaluate(tgt_xy, centre_of_target, ctr_xy, alpha, p, k) -> np.ndarray:
+    tgt_xy, ctr_xy = _f64(tgt_xy), _f64(ctr_xy)
+    cot = np.ascontiguousarray(centre_of_target, dtype=np.int32)
+    al = _c128(alpha)
+    out = np.zeros(2 * tgt_xy.shape[0])
+    _load().oracle_qbx_evaluate(tgt_xy.shape[0], _p(tgt_xy, _D), _p(cot, _I32), _p(ctr_xy, _D),
+                                _p(al, _D), int(p), float(k), _p(out, _D))
+    return out.view(np.complex128)
+
+
+def associate(tgt_xy, node_xy, panel_of_node, panel_h, ctr_xy, ctr_radius, eps_assoc,
+              on_surface_node=None, on_surface_side=None):
+    """Returns (centre_of_target int32 [-1 direct, -2 failure], n_failures)."""
+    tgt_xy, node_xy, panel_h, ctr_xy, ctr_radius = map(
+        _f64, (tgt_xy, node_xy, panel_h, ctr_xy, ctr_radius))
+    pon = np.ascontiguousarray(panel_of_node, dtype=np.int64)
+    osn = None if on_surface_node is None else np.ascontiguousarray(on_surface_node, np.int64)
+    oss = None if on_surface_side is None else np.ascontiguousarray(on_surface_side, np.int8)
+    out = np.empty(tgt_xy.shape[0], dtype=np.int32)
+    fails = _load().oracle_associate(tgt_xy.shape[0], _p(tgt_xy, _D), _p(osn, _I64),
+                                     _p(oss, _I8), node_xy.shape[0], _p(node_xy, _D),
+                                     _p(pon, _I64), _p(panel_h, _D), ctr_xy.shape[0],
+                                     _p(ctr_xy, _D), _p(ctr_radius, _D), float(eps_assoc),
+                                     _p(out, _I32))
+    return out, int(fails)
+
+
+def layer_potential(geom, tgt_xy, p, sigma_S=None, sigma_D=None, cS=1.0, cD=1.0, sides=2,
+                    eps_assoc=0.1, on_surface_node=None, on_surface_side=None,
+                    centre_of_target=None):
+    """Global QBX evaluation without acceleration (Sec. 2.3, steps 2-3 done directly).
+
+    ``geom`` is a dict with node_xy, normal_xy, weight, panel_of_node, panel_h, k.
+    If ``centre_of_target`` is given it replaces the oracle's own association
+    (used to evaluate on a shared association where several answers are correct).
+    Returns (u, centre_of_target, alpha_at_used_centres dict)."""
+    cxy, crad = centres(geom["node_xy"], geom["normal_xy"], geom["panel_of_node"],
+                        geom["panel_h"], sides)
+    if centre_of_target is None:
+        centre_of_target, fails = associate(tgt_xy, geom["node_xy"], geom["panel_of_node"],
+                                            geom["panel_h"], cxy, crad, eps_assoc,
+                                            on_surface_node, on_surface_side)
+        if fails:
+            raise RuntimeError("oracle: target association failed for %d targets" % fails)
+    centre_of_target = np.asarray(centre_of_target, dtype=np.int32)
+    tgt_xy = _f64(tgt_xy)
+    u = np.zeros(tgt_xy.shape[0], dtype=np.complex128)
+    direct = np.nonzero(centre_of_target < 0)[0]
+    if direct.size:
+        u[direct] = direct_potential(geom["node_xy"], geom["normal_xy"], geom["weight"],
+                                     geom["k"], tgt_xy[direct], sigma_S, sigma_D, cS, cD)
+    qbx = np.nonzero(centre_of_target >= 0)[0]
+    if qbx.size:
+        used, inv = np.unique(centre_of_target[qbx], return_inverse=True)
+        alpha = qbx_coefficients(geom["node_xy"], geom["normal_xy"], geom["weight"], geom["k"],
+                                 cxy[used], p, sigma_S, sigma_D, cS, cD)
+        u[qbx] = qbx_evaluate(tgt_xy[qbx], inv.astype(np.int32), cxy[used], alpha, p, geom["k"])
+    return u, centre_of_target
