@@ -1,0 +1,365 @@
+"""Benchmark: QBX layer-potential targets/s on one GB300 (and N replicas under torchrun).
+
+Default workload: the starfish r(t) = 1 + 0.3 cos 5t, k = 10, 512 panels x 16
+Gauss-Legendre nodes (8192 sources, 16 384 centres), combined field
+D[s] + i k S[s] with a random complex density of Fourier modes |n| <= 20,
+p = 12, p_fmm = 20, 316 x 316 grid targets on [-2, 2]^2. One step is one
+qbx_layer_potential_eval over all targets with the plan prebuilt and the
+density resident on the device. L2 is flushed (a 256 MiB write) before every
+timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                  [--mode fmm|direct] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain, slow definition) on the
+host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QBX-FMM layer-potential targets/sec at stated rel err, mixed vs FP64 on 1 GB300"
+UNIT = "targets/s"
+CONFIG_NUM = 2
+# FP64 FMA peak of a GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP32 FMA peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.070 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM traffic per launch of the dominant kernel from the committed ncu summaries
+# (profiles/); None until measured for the current kernel version.
+KNOWN_TRAFFIC = {}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flop_model(stats, p, p_box, has_S, has_D):
+    """Algorithmic FP64 flops per kernel class (complex FMA = 8, base Hankel values
+    charged 0). P = 2p+1 QBX terms, Q = 2 p_box + 1 box terms."""
+    P, Q = 2 * p + 1, 2 * p_box + 1
+    lay = (1 if has_S else 0) + (1 if has_D else 0)
+    f = {}
+    f["p2qbxl"] = stats["p2qbxl_pairs"] * ((18 * P if has_S else 0) + (10 * P if has_D else 0))
+    f["p2p"] = stats["p2p_pairs"] * 8 * lay
+    f["qbxl2p"] = stats["n_qbx_targets"] * 16 * P
+    f["m2l"] = stats["v_pairs"] * 8 * Q * Q
+    f["m2qbxl"] = stats["m2qbxl_pairs"] * 8 * Q * P
+    f["m2p"] = stats["m2p_pairs"] * 16 * Q
+    f["l2qbxl"] = stats["n_centres"] * 8 * Q * P
+    f["l2p"] = stats["n_targets"] * 16 * Q
+    f["p2m"] = stats["n_sources"] * 16 * Q * lay
+    f["p2l"] = stats["p2l_pairs"] * 16 * Q * lay
+    f["m2m"] = f["l2l"] = stats["m2m_l2l"] * 8 * Q * Q // 2
+    return f
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, w, ws, rank, local):
+    import torch
+    from paper_1602_05301_gb300 import qbx
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = w["geom"]
+    mode = qbx.QBX_FMM if args.mode == "fmm" else qbx.QBX_DIRECT
+    prec = qbx.QBX_MIXED if args.precision == "mixed" else qbx.QBX_FP64
+    lp = qbx.LayerPotential(g.as_dict(), w["p"], sides=w["sides"])
+    t0 = time.perf_counter()
+    lp.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"], mode=mode,
+             p_fmm=w["p_fmm"], p_add=-1, n_max=args.n_max, eps_assoc=w["eps_assoc"])
+    tree_s = time.perf_counter() - t0
+    n_t = lp.n_targets
+    sS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).to(dev) if w["sigma_S"] is not None else None
+    sD = torch.from_numpy(np.ascontiguousarray(w["sigma_D"])).to(dev) if w["sigma_D"] is not None else None
+    out = torch.empty(n_t, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        lp.eval(sigma_S=sS, sigma_D=sD, cS=w["cS"], cD=w["cD"], out=out, precision=prec,
+                stream=sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    launches = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+            launches += lp.stats()["launches"]
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = ws * n_t * args.steps / (total_ms / 1e3)
+    stats = lp.stats()
+
+    # per-kernel device times (events around each kernel class on the eval stream)
+    lp.set_timing(True)
+    per = {}
+    for _ in range(3):
+        flush.zero_()
+        step()
+        for kname, ms in lp.stage_times().items():
+            per.setdefault(kname, []).append(ms)
+    lp.set_timing(False)
+    per = {k: statistics.median(v) for k, v in per.items() if max(v) > 0}
+    flops = flop_model(stats, w["p"], stats["p_box"], sS is not None, sD is not None)
+    dom = max(per, key=per.get) if per else None
+    roof = None
+    if dom:
+        achieved = flops.get(dom, 0) / (per[dom] / 1e3) / 1e12
+        peak = FP32_PEAK_TFLOPS if (prec == qbx.QBX_MIXED and dom in ("m2l", "l2l", "m2m")) \
+            else FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": KNOWN_TRAFFIC.get((w["name"], dom, args.mode, args.precision)),
+                "flops_per_launch": flops.get(dom, 0), "ms_per_launch": per[dom],
+                "peak_basis": "derived: 152 SMs x FMA/clk x 2 x 2.070 GHz (see DESIGN.md)"}
+
+    # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
+    hS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).pin_memory() if sS is not None else None
+    hD = torch.from_numpy(np.ascontiguousarray(w["sigma_D"])).pin_memory() if sD is not None else None
+    hout = torch.empty(n_t, dtype=torch.complex128).pin_memory()
+    for _ in range(2):
+        lp.eval(sigma_S=hS, sigma_D=hD, cS=w["cS"], cD=w["cD"], out=hout, precision=prec,
+                stream=sp)
+    torch.cuda.synchronize()
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        lp.eval(sigma_S=hS, sigma_D=hD, cS=w["cS"], cD=w["cD"], out=hout, precision=prec,
+                stream=sp)
+        e2e_s.append(time.perf_counter() - a)
+    e2e_t = torch.tensor([sum(e2e_s)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    h2d = 16 * g.n * ((1 if hS is not None else 0) + (1 if hD is not None else 0))
+    e2e = {"value": ws * n_t * args.steps / float(e2e_t.item()), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * n_t}
+    res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+               warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
+               scaling="weak", vs_baseline=None,
+               dtype="f64" if prec == qbx.QBX_FP64 else "f32+f64",
+               data="synthetic",
+               config={"workload": "%s: starfish r=1+0.3cos5t, k=10, 512 panels x 16 GL "
+                                   "(8192 sources, 16384 centres), D+ikS, p=12, p_fmm=20, "
+                                   "316x316 grid targets" % w["name"],
+                       "mode": args.mode, "precision": args.precision, "n_targets": n_t,
+                       "n_qbx_targets": stats["n_qbx_targets"], "p_box": stats["p_box"],
+                       "n_boxes": stats["n_boxes"], "tree_build_s": tree_s,
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+               roofline=roof, per_kernel_ms=per, gpu_launches=launches,
+               clocks=clk.summary(), e2e=e2e)
+    lp.close()
+    return res
+
+
+# ---------------------------------------------------------------- oracle (CPU) timing
+def oracle_sample(w, assoc, budget_s=12.0, seed=0):
+    """Times the FP64 oracle on a stratified sample of targets (the workload's
+    direct/QBX mix, each target summed over all sources, QBX targets including
+    their centre's coefficients). Returns (targets/s, threads, description)."""
+    from oracle import oracle
+    g = w["geom"]
+    rng = np.random.default_rng(seed)
+    qbx_t = np.nonzero(assoc >= 0)[0]
+    dir_t = np.nonzero(assoc < 0)[0]
+    frac_q = qbx_t.size / max(1, assoc.size)
+    n_q, n_d = 4, 32
+    done_t, elapsed = 0, 0.0
+    t_q = t_d = 0.0
+    nq_done = nd_done = 0
+    while elapsed < budget_s:
+        tq = rng.choice(qbx_t, min(n_q, qbx_t.size), replace=False) if qbx_t.size else []
+        td = rng.choice(dir_t, min(n_d, dir_t.size), replace=False) if dir_t.size else []
+        for ts, is_q in ((tq, True), (td, False)):
+            if len(ts) == 0:
+                continue
+            a = time.perf_counter()
+            oracle.layer_potential(g.as_dict(), w["tgt_xy"][ts], w["p"], w["sigma_S"],
+                                   w["sigma_D"], w["cS"], w["cD"], sides=w["sides"],
+                                   centre_of_target=assoc[ts])
+            dt = time.perf_counter() - a
+            if is_q:
+                t_q += dt
+                nq_done += len(ts)
+            else:
+                t_d += dt
+                nd_done += len(ts)
+            elapsed += dt
+    per_q = t_q / max(1, nq_done)
+    per_d = t_d / max(1, nd_done)
+    per_t = frac_q * per_q + (1 - frac_q) * per_d
+    desc = ("%d QBX + %d direct targets (of %d; QBX fraction %.4f), each over all %d sources, "
+            "%.1f s of oracle time, extrapolated to the full target mix"
+            % (nq_done, nd_done, assoc.size, frac_q, g.n, elapsed))
+    return 1.0 / per_t, oracle.num_threads(), desc
+
+
+def gpu_assoc_free(w):
+    """Association for the CPU-only reference arm: the oracle's own brute force."""
+    from oracle import oracle
+    g = w["geom"]
+    cxy, crad = oracle.centres(g.node_xy, g.normal_xy, g.panel_of_node, g.panel_h, w["sides"])
+    cot, fails = oracle.associate(w["tgt_xy"], g.node_xy, g.panel_of_node, g.panel_h, cxy, crad,
+                                  w["eps_assoc"], w["on_surface_node"], w["on_surface_side"])
+    return cot
+
+
+def run_reference(args, w):
+    from oracle import oracle
+    oracle.build()
+    assoc = gpu_assoc_free(w)
+    vals = []
+    desc = ""
+    per_step_budget = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        v, cores, desc = oracle_sample(w, assoc, budget_s=per_step_budget, seed=i)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    return dict(metric=METRIC, value=value, unit=UNIT, n_gpus=1, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * w["tgt_xy"].shape[0] / value,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config={"workload": "%s (oracle: direct Global QBX, FP64 CPU)" % w["name"],
+                        "mode": "direct", "precision": "fp64"},
+                cpu_baseline={"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                              "sample": desc},
+                e2e={"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                     "d2h_bytes_per_step": 0})
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mode", default="direct", choices=["fmm", "direct"])
+    ap.add_argument("--n-max", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    from qbx_workloads import make_config
+    w = make_config(CONFIG_NUM)
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, w)), flush=True)
+        return
+    import torch
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1602_05301_gb300 import build as b
+    if rank == 0:
+        b.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    res = run_ours(args, w, ws, rank, local)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from paper_1602_05301_gb300 import qbx
+        lp = qbx.LayerPotential(w["geom"].as_dict(), w["p"], sides=w["sides"])
+        assoc = lp.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"])
+        lp.close()
+        v, cores, desc = oracle_sample(w, assoc)
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": desc}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

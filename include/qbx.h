@@ -1,0 +1,181 @@
+/*
+ * qbx.h -- C ABI of the GB300 (sm_103a) implementation of FMM-accelerated
+ * Global QBX for 2D Helmholtz layer potentials (Rachh, Kloeckner, O'Neil,
+ * "Fast algorithms for Quadrature by Expansion I: Globally valid expansions").
+ *
+ * The problem (Sec. 1, Eq. (dlp), Eq. (helmholtz-ker); Sec. 2.2; Sec. 7):
+ * given closed curves cut into Gauss-Legendre panels, a wavenumber k, complex
+ * densities and targets anywhere in the plane, return
+ *     u(t) = cS * S[sigma_S](t) + cD * D[sigma_D](t),
+ *     S[s](t) = int (i/4) H_0(k|t-y|) s(y) ds(y),
+ *     D[s](t) = int n_y . grad_y (i/4) H_0(k|t-y|) s(y) ds(y),   n outward,
+ * at every target: by QBX (Sec. 2.1, Eq. (jexp)-(phiapprox)) with the globally
+ * valid expansion of its associated centre (Sec. 6.1) where the target is
+ * associated, by smooth Gauss quadrature (Sec. 3.2, Eq. (gauss-layerpot))
+ * elsewhere. Targets on the curve receive the one-sided limit of the side they
+ * request (Sec. 2, Eq. (oneside)).
+ *
+ * Conventions
+ *  - Complex numbers are interleaved (re, im) doubles.
+ *  - Points and normals are [n][2] doubles (x, y).
+ *  - Every pointer argument may be host or device memory; the library asks
+ *    the CUDA runtime which it is. Device pointers must live on the current
+ *    device. Host outputs are written before the call returns.
+ *  - The caller owns every buffer it passes; the library copies what it keeps
+ *    and never frees caller memory. The handle owns all memory it allocates.
+ *  - No C++ exception crosses this boundary. Every call returns a status; on a
+ *    non-OK status qbx_last_error() holds a message (thread-local).
+ *  - One handle must not be used from two threads at once; distinct handles
+ *    are independent.
+ */
+#ifndef QBX_GB300_H
+#define QBX_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qbx_handle qbx_handle;
+
+typedef enum {
+  QBX_OK = 0,
+  QBX_ERR_ARG = 1,          /* invalid argument (NULL, size, order out of range)      */
+  QBX_ERR_OOM = 2,          /* device or pinned host allocation failed                */
+  QBX_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed            */
+  QBX_ERR_CONDITION = 4,    /* Condition 4 (k * max h <= 5, Sec. 3.2) is violated     */
+  QBX_ERR_ASSOCIATION = 5,  /* a target in Gamma_near found no centre (Sec. 6.1)      */
+  QBX_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                     */
+  QBX_ERR_STATE = 7         /* call out of order (e.g. eval before tree build)        */
+} qbx_status;
+
+enum { QBX_FP64 = 0, QBX_MIXED = 1 };          /* arithmetic of the evaluation   */
+enum { QBX_DIRECT = 0, QBX_FMM = 1 };          /* how the sums are computed      */
+
+/* Maximum QBX order p accepted (expansions l = -p..p). */
+#define QBX_MAX_P 16
+
+/*
+ * Geometry (Sec. 2.2). The density grid carries the expansion centres
+ *     c = s + side * (h_k / 2) * n    (side +1: exterior, -1: interior),
+ * one per density node and requested side. Centre numbering: the exterior
+ * centre of node j is j; with center_sides == 2 the interior centre of node j
+ * is n_nodes + j. The source grid carries the quadrature (Sec. 3.2 and
+ * Sec. 7, Eq. (QBXFMMpot)); when src_xy is NULL the density grid is the source
+ * grid and `weight` gives its weights. Densities passed to eval live on the
+ * source grid.
+ *
+ * All curves of one geometry share the wavenumber k (they form one problem).
+ */
+typedef struct {
+  int64_t n_panels;
+  int32_t q;                     /* density nodes per panel (n_nodes = n_panels * q)      */
+  const double *node_xy;         /* [n_nodes][2]                                          */
+  const double *normal_xy;       /* [n_nodes][2] outward unit normals                      */
+  const double *weight;          /* [n_nodes] arclength weights (used if src_xy == NULL)   */
+  const double *panel_h;         /* [n_panels] panel arclengths h_k                        */
+  int32_t q_src;                 /* source nodes per panel (0 => the density grid)         */
+  const double *src_xy;          /* [n_panels * q_src][2] or NULL                          */
+  const double *src_normal_xy;   /* [n_panels * q_src][2] or NULL                          */
+  const double *src_weight;      /* [n_panels * q_src] or NULL                             */
+  double k;                      /* wavenumber, real, > 0                                  */
+  int32_t p_qbx;                 /* QBX order p, 0 <= p <= QBX_MAX_P                        */
+  int32_t center_sides;          /* 1: exterior centres only, 2: both sides                */
+} qbx_geometry_desc;
+
+/*
+ * Copies the geometry to the device and places the centres.
+ * Errors: QBX_ERR_ARG on NULL/invalid sizes, QBX_ERR_CONDITION if
+ * k * max_k h_k > 5 (Condition 4), QBX_ERR_OOM / QBX_ERR_CUDA.
+ * On success *out owns the new handle (free with qbx_destroy).
+ */
+qbx_status qbx_geometry_create(const qbx_geometry_desc *desc, qbx_handle **out);
+
+/*
+ * Targets and evaluation plan (Sec. 6.1 association, Sec. 7 tree and lists).
+ * on_surface_node[t] = j >= 0 marks target t as lying on density node j; it
+ * then uses the centre of node j on side on_surface_side[t] (+1 exterior,
+ * -1 interior; the interior side needs center_sides == 2). Other targets take
+ * the nearest centre c with |t - c| <= (1 + eps_assoc) h/2 (ties: smaller
+ * centre index); a target with no such centre whose distance to some density
+ * node of panel k is <= h_k/4 is an association failure; the rest use direct
+ * quadrature.
+ * mode: QBX_DIRECT (all pairs) or QBX_FMM (quadtree, Sec. 7).
+ * p_fmm, p_add: box expansion order p_box = p_fmm + p_add; p_add < 0 selects
+ * Table 2 of the paper (p <= 8) extended by p_add = 2.5 p beyond it.
+ * n_max: particles per leaf (sources + centres + targets), 0 => 64.
+ * assoc_out (optional, [n_targets] int32) receives the centre of every target
+ * (-1: direct quadrature).
+ * Errors: QBX_ERR_ASSOCIATION (count and first target in qbx_last_error()),
+ * QBX_ERR_ARG, QBX_ERR_OOM, QBX_ERR_CUDA. Synchronous.
+ */
+typedef struct {
+  int64_t n_targets;
+  const double *target_xy;         /* [n_targets][2]                                     */
+  const int64_t *on_surface_node;  /* [n_targets] or NULL (no on-surface targets)        */
+  const int8_t *on_surface_side;   /* [n_targets] or NULL (all +1)                       */
+  int32_t mode;                    /* QBX_DIRECT | QBX_FMM                               */
+  int32_t p_fmm;
+  int32_t p_add;
+  int32_t n_max;
+  double eps_assoc;                /* <= 0 => 0.1                                        */
+  int32_t *assoc_out;              /* optional                                           */
+} qbx_tree_desc;
+
+qbx_status qbx_tree_build(qbx_handle *h, const qbx_tree_desc *desc);
+
+/*
+ * Evaluates u = cS S[sigma_S] + cD D[sigma_D] at every target (Sec. 7,
+ * Stages 2-8 in FMM mode, then QBX evaluation at associated targets, Sec. 2.3
+ * step 3). sigma_S / sigma_D: complex [n_src] on the source grid; either may be
+ * NULL (that layer is absent). out: complex [n_targets]. alpha_out (optional):
+ * complex [n_centres][2p+1], l = -p..p, the QBX coefficients of every centre.
+ * precision: QBX_FP64 or QBX_MIXED. cuda_stream: a cudaStream_t (NULL: the
+ * legacy default stream). With device buffers the call is asynchronous on the
+ * stream; with any host buffer it copies through the stream and returns after
+ * the result is in host memory.
+ */
+qbx_status qbx_layer_potential_eval(qbx_handle *h, double cS_re, double cS_im,
+                                    const double *sigma_S, double cD_re, double cD_im,
+                                    const double *sigma_D, double *out, double *alpha_out,
+                                    int32_t precision, void *cuda_stream);
+
+/* Frees every resource of the handle. NULL-safe. Synchronises the device work
+ * of the handle first. */
+void qbx_destroy(qbx_handle *h);
+
+/* Message of the last non-OK status on this thread ("" if none). */
+const char *qbx_last_error(void);
+
+/*
+ * Plan statistics after qbx_tree_build (for logging and benchmarks):
+ * stats[0] n_sources, [1] n_centres, [2] n_targets, [3] n_qbx_targets,
+ * [4] n_boxes, [5] n_leaves, [6] tree depth, [7] p_box, [8] U-list pairs
+ * (leaf, leaf), [9] V-list pairs, [10] W-list pairs, [11] X-list pairs,
+ * [12] source-centre pairs evaluated directly (P2QBXL), [13] source-target
+ * pairs evaluated directly (P2P), [14] (box, centre) pairs of M2QBXL,
+ * [15] (box, target) pairs of M2P, [16] kernel launches of the last eval,
+ * [17] sources in X-list boxes summed over boxes (P2L pairs), [18] M2M plus
+ * L2L translations, [19] reserved. Unused entries are 0. n_stats >= 20.
+ */
+qbx_status qbx_get_stats(const qbx_handle *h, int64_t *stats, int32_t n_stats);
+
+/*
+ * Device time of each kernel class of the last eval, in milliseconds, when
+ * timing was enabled with qbx_set_timing(h, 1) before that eval (events are
+ * recorded on the eval stream; reading them synchronises it).
+ * times[i] for i < n_times follows enum qbx_stage; returns the number filled.
+ */
+enum qbx_stage {
+  QBX_STAGE_STRENGTHS = 0, QBX_STAGE_P2M, QBX_STAGE_M2M, QBX_STAGE_P2P, QBX_STAGE_P2QBXL,
+  QBX_STAGE_M2L, QBX_STAGE_M2P, QBX_STAGE_M2QBXL, QBX_STAGE_P2L, QBX_STAGE_L2L,
+  QBX_STAGE_L2P, QBX_STAGE_L2QBXL, QBX_STAGE_QBXL2P, QBX_STAGE_COUNT
+};
+qbx_status qbx_set_timing(qbx_handle *h, int32_t enable);
+int32_t qbx_get_stage_times(qbx_handle *h, double *times_ms, int32_t n_times);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QBX_GB300_H */

@@ -1,0 +1,65 @@
+// Quadtree, interaction lists and FMM plan (Sec. 4 and Sec. 7 of the paper).
+#pragma once
+#include "qbx_internal.h"
+
+// particle classes held by the tree
+enum { PT_SRC = 0, PT_CTR = 1, PT_TGT = 2, PT_NODE = 3, PT_COUNT = 4 };
+
+constexpr int kMortonBits = 24;   // levels 0..24
+constexpr int kMaxLevels = 24;
+
+struct BoxArrays {
+  DevBuf<int> level, parent, child;     // child: [n][4], -1 = none
+  DevBuf<int2> ij;                      // integer position at own level
+  DevBuf<unsigned long long> key;       // Morton key of (ij) at own level
+  DevBuf<double2> centre;
+  DevBuf<int2> rng[PT_COUNT];           // [start, end) in each sorted particle array
+};
+
+struct Csr {
+  DevBuf<int> off, idx;
+  int64_t nnz = 0;
+};
+
+struct FmmPlan {
+  // tree
+  double x0 = 0, y0 = 0, side = 0;      // root square [x0, x0+side] x [y0, y0+side]
+  int n_levels = 0, n_boxes = 0;
+  std::vector<int> level_off;           // [n_levels + 1]
+  BoxArrays box;
+  std::vector<int> h_level_off;
+  // sorted particles: perm[type][i] = original index of the i-th particle in tree order
+  DevBuf<unsigned long long> keys[PT_COUNT];
+  DevBuf<int> perm[PT_COUNT];
+  int64_t count[PT_COUNT] = {0, 0, 0, 0};
+  // lists
+  Csr U, V, W, X;
+  DevBuf<int> V_cls;                    // offset class of every V entry (0..48)
+  DevBuf<int> leaves;                   // leaf box ids
+  int n_leaves = 0;
+  std::vector<std::vector<int>> h_nonleaf_by_level;  // parents per level (host copy of ids)
+  DevBuf<int> nonleaf;                  // all non-leaf boxes ordered by level
+  std::vector<int> nonleaf_off;         // [n_levels + 1] offsets into nonleaf
+  DevBuf<int> xbox;                     // boxes with non-empty X list
+  int n_xbox = 0;
+  DevBuf<int> vbox;                     // boxes with non-empty V list
+  int n_vbox = 0;
+  // orders and scales
+  int pb = 0, Q = 0;
+  DevBuf<double> scale;                 // per level s_l = min(1, k * side_l)
+  DevBuf<cd> t_m2l;                     // [n_levels][49][4pb+1] scaled Hankel vectors
+  DevBuf<cd> t_m2m;                     // [n_levels][4][4pb+1] conj(V_m(d)) child->parent
+  DevBuf<cd> t_l2l;                     // [n_levels][4][4pb+1] (-1)^m V_m(d) parent->child
+  // sorted particle data used by the eval kernels
+  DevBuf<double2> s_xy, s_nrm, c_xy, t_xy;
+  DevBuf<int> t_assoc;                  // association of sorted targets (centre id or -1)
+  // expansions
+  DevBuf<cd> mpole, local;              // [n_boxes][Q]
+  DevBuf<cd> qs, ds;                    // sorted strengths
+  DevBuf<int> err;                      // device error flags
+};
+
+qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max);
+qbx_status tree_lists(qbx_handle* h, FmmPlan* f);
+qbx_status tree_associate(qbx_handle* h, FmmPlan* f, const int64_t* on_node, const int8_t* on_side,
+                          double eps);

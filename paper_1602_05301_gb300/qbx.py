@@ -1,0 +1,244 @@
+"""Thin Python binding of the C ABI in include/qbx.h (argument marshalling only).
+
+The functions keep the ABI's names (qbx_geometry_create, qbx_tree_build,
+qbx_layer_potential_eval, qbx_destroy, ...). Arrays may be numpy arrays (host)
+or torch tensors (host, pinned host or CUDA); the library decides by pointer.
+Nothing here computes any part of the layer potential: without the compiled
+CUDA library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqbx_gb300.so")
+
+QBX_OK, QBX_ERR_ARG, QBX_ERR_OOM, QBX_ERR_CUDA, QBX_ERR_CONDITION = 0, 1, 2, 3, 4
+QBX_ERR_ASSOCIATION, QBX_ERR_TIMEOUT, QBX_ERR_STATE = 5, 6, 7
+QBX_FP64, QBX_MIXED = 0, 1
+QBX_DIRECT, QBX_FMM = 0, 1
+QBX_MAX_P = 16
+STAGES = ["strengths", "p2m", "m2m", "p2p", "p2qbxl", "m2l", "m2p", "m2qbxl", "p2l", "l2l",
+          "l2p", "l2qbxl", "qbxl2p"]
+STATUS_NAMES = {0: "QBX_OK", 1: "QBX_ERR_ARG", 2: "QBX_ERR_OOM", 3: "QBX_ERR_CUDA",
+                4: "QBX_ERR_CONDITION", 5: "QBX_ERR_ASSOCIATION", 6: "QBX_ERR_TIMEOUT",
+                7: "QBX_ERR_STATE"}
+
+_vp = ctypes.c_void_p
+
+
+class qbx_geometry_desc(ctypes.Structure):
+    _fields_ = [("n_panels", ctypes.c_int64), ("q", ctypes.c_int32),
+                ("node_xy", _vp), ("normal_xy", _vp), ("weight", _vp), ("panel_h", _vp),
+                ("q_src", ctypes.c_int32), ("src_xy", _vp), ("src_normal_xy", _vp),
+                ("src_weight", _vp), ("k", ctypes.c_double), ("p_qbx", ctypes.c_int32),
+                ("center_sides", ctypes.c_int32)]
+
+
+class qbx_tree_desc(ctypes.Structure):
+    _fields_ = [("n_targets", ctypes.c_int64), ("target_xy", _vp), ("on_surface_node", _vp),
+                ("on_surface_side", _vp), ("mode", ctypes.c_int32), ("p_fmm", ctypes.c_int32),
+                ("p_add", ctypes.c_int32), ("n_max", ctypes.c_int32),
+                ("eps_assoc", ctypes.c_double), ("assoc_out", _vp)]
+
+
+class QBXError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library() -> ctypes.CDLL:
+    """Loads libqbx_gb300.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build() "
+                                   "(or paper_1602_05301_gb300/build.py) first" % LIB_PATH)
+            lib = ctypes.CDLL(LIB_PATH)
+            lib.qbx_geometry_create.restype = ctypes.c_int
+            lib.qbx_geometry_create.argtypes = [ctypes.POINTER(qbx_geometry_desc),
+                                                ctypes.POINTER(_vp)]
+            lib.qbx_tree_build.restype = ctypes.c_int
+            lib.qbx_tree_build.argtypes = [_vp, ctypes.POINTER(qbx_tree_desc)]
+            lib.qbx_layer_potential_eval.restype = ctypes.c_int
+            lib.qbx_layer_potential_eval.argtypes = [
+                _vp, ctypes.c_double, ctypes.c_double, _vp, ctypes.c_double, ctypes.c_double,
+                _vp, _vp, _vp, ctypes.c_int32, _vp]
+            lib.qbx_destroy.restype = None
+            lib.qbx_destroy.argtypes = [_vp]
+            lib.qbx_last_error.restype = ctypes.c_char_p
+            lib.qbx_last_error.argtypes = []
+            lib.qbx_get_stats.restype = ctypes.c_int
+            lib.qbx_get_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
+            lib.qbx_set_timing.restype = ctypes.c_int
+            lib.qbx_set_timing.argtypes = [_vp, ctypes.c_int32]
+            lib.qbx_get_stage_times.restype = ctypes.c_int32
+            lib.qbx_get_stage_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.c_int32]
+            _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != QBX_OK:
+        raise QBXError(status, library().qbx_last_error().decode())
+
+
+def ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"], "contiguous array expected"
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------- ABI-named wrappers
+def qbx_geometry_create(desc: qbx_geometry_desc):
+    h = _vp()
+    _check(library().qbx_geometry_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def qbx_tree_build(handle, desc: qbx_tree_desc):
+    _check(library().qbx_tree_build(handle, ctypes.byref(desc)))
+
+
+def qbx_layer_potential_eval(handle, cS, sigma_S, cD, sigma_D, out, alpha_out=None,
+                             precision=QBX_FP64, cuda_stream=None):
+    cS, cD = complex(cS), complex(cD)
+    _check(library().qbx_layer_potential_eval(handle, cS.real, cS.imag, ptr(sigma_S), cD.real,
+                                              cD.imag, ptr(sigma_D), ptr(out), ptr(alpha_out),
+                                              int(precision), cuda_stream))
+
+
+def qbx_destroy(handle):
+    if handle:
+        library().qbx_destroy(handle)
+
+
+def qbx_get_stats(handle):
+    st = (ctypes.c_int64 * 20)()
+    _check(library().qbx_get_stats(handle, st, 20))
+    return list(st)
+
+
+def qbx_set_timing(handle, enable: bool):
+    _check(library().qbx_set_timing(handle, 1 if enable else 0))
+
+
+def qbx_get_stage_times(handle):
+    t = (ctypes.c_double * len(STAGES))()
+    n = library().qbx_get_stage_times(handle, t, len(STAGES))
+    return {STAGES[i]: t[i] for i in range(n)}
+
+
+def qbx_last_error() -> str:
+    return library().qbx_last_error().decode()
+
+
+# ---------------------------------------------------------------- convenience object
+def _host_f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class LayerPotential:
+    """Owns one handle: geometry -> plan -> evaluations.
+
+    geom: object with node_xy, normal_xy, weight, panel_h (numpy), q, k (scalar or [1]).
+    src:  optional oversampled source grid (same panels): dict with q, node_xy,
+          normal_xy, weight.
+    """
+
+    def __init__(self, geom, p, sides=2, src=None):
+        self._keep = []
+        k = float(np.atleast_1d(geom.k)[0]) if hasattr(geom, "k") else float(geom["k"])
+        g = geom if isinstance(geom, dict) else geom.__dict__
+        node_xy, normal_xy = _host_f64(g["node_xy"]), _host_f64(g["normal_xy"])
+        weight, panel_h = _host_f64(g["weight"]), _host_f64(g["panel_h"])
+        self._keep += [node_xy, normal_xy, weight, panel_h]
+        d = qbx_geometry_desc()
+        d.n_panels = panel_h.shape[0]
+        d.q = int(g["q"])
+        d.node_xy, d.normal_xy, d.weight, d.panel_h = map(ptr, (node_xy, normal_xy, weight,
+                                                               panel_h))
+        if src is not None:
+            sxy, snr, sw = (_host_f64(src["node_xy"]), _host_f64(src["normal_xy"]),
+                            _host_f64(src["weight"]))
+            self._keep += [sxy, snr, sw]
+            d.q_src = int(src["q"])
+            d.src_xy, d.src_normal_xy, d.src_weight = ptr(sxy), ptr(snr), ptr(sw)
+        d.k = k
+        d.p_qbx = int(p)
+        d.center_sides = int(sides)
+        self.k, self.p, self.sides = k, int(p), int(sides)
+        self.n_nodes = node_xy.shape[0]
+        self.n_src = (d.n_panels * d.q_src) if src is not None else self.n_nodes
+        self.n_centres = self.n_nodes * self.sides
+        self.handle = qbx_geometry_create(d)
+        self._keep = []
+        self.n_targets = 0
+
+    def build(self, target_xy, on_surface_node=None, on_surface_side=None, mode=QBX_DIRECT,
+              p_fmm=0, p_add=-1, n_max=0, eps_assoc=0.1):
+        txy = _host_f64(target_xy)
+        n = txy.shape[0]
+        osn = None if on_surface_node is None else np.ascontiguousarray(on_surface_node,
+                                                                        np.int64)
+        oss = None if on_surface_side is None else np.ascontiguousarray(on_surface_side,
+                                                                        np.int8)
+        assoc = np.empty(n, dtype=np.int32)
+        d = qbx_tree_desc(n, ptr(txy), ptr(osn), ptr(oss), int(mode), int(p_fmm), int(p_add),
+                          int(n_max), float(eps_assoc), ptr(assoc))
+        qbx_tree_build(self.handle, d)
+        self.n_targets = n
+        return assoc
+
+    def eval(self, sigma_S=None, sigma_D=None, cS=1.0, cD=1.0, out=None, alpha_out=None,
+             precision=QBX_FP64, stream=None):
+        """Densities / outputs: complex128 numpy arrays or torch tensors (host or CUDA)."""
+        def prep(a):
+            if a is None or hasattr(a, "data_ptr"):
+                return a
+            return np.ascontiguousarray(a, dtype=np.complex128)
+        sigma_S, sigma_D = prep(sigma_S), prep(sigma_D)
+        if out is None:
+            out = np.empty(self.n_targets, dtype=np.complex128)
+        qbx_layer_potential_eval(self.handle, cS, sigma_S, cD, sigma_D, out, alpha_out,
+                                 precision, stream)
+        return out
+
+    def stats(self):
+        names = ["n_sources", "n_centres", "n_targets", "n_qbx_targets", "n_boxes", "n_leaves",
+                 "depth", "p_box", "u_pairs", "v_pairs", "w_pairs", "x_pairs",
+                 "p2qbxl_pairs", "p2p_pairs", "m2qbxl_pairs", "m2p_pairs", "launches",
+                 "p2l_pairs", "m2m_l2l", "reserved"]
+        return dict(zip(names, qbx_get_stats(self.handle)))
+
+    def set_timing(self, on=True):
+        qbx_set_timing(self.handle, on)
+
+    def stage_times(self):
+        return qbx_get_stage_times(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            qbx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
