@@ -114,6 +114,7 @@ extern "C" qbx_status qbx_geometry_create(const qbx_geometry_desc* d, qbx_handle
   h->q = d->q;
   h->n_nodes = n_nodes;
   h->k = d->k;
+  h->h_max = hmax;
   h->p = d->p_qbx;
   h->sides = d->center_sides;
   h->q_src = own_src ? d->q_src : d->q;
@@ -197,7 +198,7 @@ extern "C" qbx_status qbx_tree_build(qbx_handle* h, const qbx_tree_desc* d) {
   QBX_CUDA_TRY(cudaMemcpy(h->counters.ptr, init, sizeof(init), cudaMemcpyHostToDevice));
   h->mode = d->mode;
   if (d->mode == QBX_FMM) {
-    QBX_TRY(fmm_plan_build(h, d));  // association through the tree, lists, orders
+    QBX_TRY(fmm_plan_build(h, d, dn.ptr, ds.ptr, eps));  // tree, lists, association, orders
   } else {
     QBX_TRY(launch_associate_direct(h, dn.ptr, ds.ptr, eps, 0));
   }

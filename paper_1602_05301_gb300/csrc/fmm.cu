@@ -1,22 +1,1117 @@
-// FMM-accelerated Global QBX (Sec. 7): placeholder until the tree kernels land.
-#include "qbx_internal.h"
+// FMM-accelerated Global QBX (Sec. 7.2, Stages 2-8), FP64.
+//
+// Expansions about box centres, with per-level scale s = min(1, k * side):
+//   multipole  phi(x) = sum_n  mh_n s^|n| W_n(x - m)            (H-expansion)
+//   local      psi(x) = sum_n  lh_n s^-|n| conj(V_n(x - m))      (J-expansion)
+// where W_n(z) = H_n(k|z|) e^{i n arg z} and V_n(z) = J_n(k|z|) e^{i n arg z}.
+// Storing mh = a / s^|n| and lh = gamma s^|n| keeps the stored numbers of
+// order one although H_n grows and J_n decays factorially with n for small
+// k*side. The operators come from Graf's addition theorem (DLMF 10.23.7):
+//   W_n(A - B) = sum_l W_{n+l}(A) conj(V_l(B))   (|B| < |A|),
+//   V_n(A - B) = sum_l V_{n+l}(A) conj(V_l(B))   (all A, B),
+// giving, in unscaled form (d the translation vector),
+//   P2M   a_n     = sum_j q_j conj(V_n(y_j - m))                   (Stage 2)
+//   M2M   a_s     = sum_n a'_n conj(V_{s-n}(m' - m))               (Stage 2)
+//   M2L   gamma_l = (-1)^l sum_n a_n W_{n+l}(m_b - m_c)            (Stage 4)
+//   P2L   gamma_l = sum_j q_j W_l(y_j - m)                         (Stage 6)
+//   L2L   gamma'_s = sum_n gamma_n (-1)^{s-n} V_{s-n}(m' - m)      (Stage 7)
+// and the QBX steps marked "New" in the paper: P2QBXL (Stage 3), M2QBXL
+// (Stage 5) and L2QBXL (Stage 8) are P2L, M2L and L2L with a QBX centre as the
+// target and order p. A double-layer source contributes
+// (k/2)(nu Z_{n-1} - conj(nu) Z_{n+1}) for Z = W, and the conjugate form for
+// conj(V), with nu = n_x + i n_y its normal (normal derivative of the Graf
+// kernel in the source).
+#include <algorithm>
+#include <cstdio>
+#include <vector>
 
-struct FmmPlan {
-  int dummy;
+#include "special.cuh"
+#include "tree.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kChunk = 16;  // sources per shared-memory chunk in P2M / P2L
+constexpr double kRescale = 1e100;
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
+
+struct Fmm {
+  // boxes
+  const int* level;
+  const int* child;
+  const double2* centre;
+  const int2* rsrc;
+  const int2* rctr;
+  const int2* rtgt;
+  // lists
+  const int *uoff, *uidx, *voff, *vidx, *vcls, *woff, *widx, *xoff, *xidx;
+  // sorted particles
+  const double2* sxy;
+  const double2* snrm;
+  const cd* qs;
+  const cd* ds;
+  const double2* cxy;
+  const int* cid;
+  const double2* txy;
+  const int* tid;
+  const int* tassoc;
+  // tables
+  const double* scale;   // [n_levels]
+  const double* pw;      // [n_levels][2pb+3] s^j
+  const double* ipw;     // [n_levels][pb+2]  s^-j
+  const cd* t_m2l;       // [n_levels][49][4pb+1]
+  const cd* t_m2m;       // [n_levels][4][4pb+1]
+  const cd* t_l2l;       // [n_levels][4][4pb+1]
+  cd* mpole;
+  cd* local;
+  double k;
+  int pb, Q, p, n_levels, has_S, has_D;
 };
 
-qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d) {
-  (void)h;
-  (void)d;
-  set_error("QBX_FMM mode is not available in this build");
-  return QBX_ERR_ARG;
+__device__ __forceinline__ const double* pw_row(const Fmm& F, int l) { return F.pw + (size_t)l * (2 * F.pb + 3); }
+__device__ __forceinline__ const double* ipw_row(const Fmm& F, int l) { return F.ipw + (size_t)l * (F.pb + 2); }
+
+// Unnormalised Miller recurrence for J_0..J_M of x into row[0..M]; returns the
+// normalisation (divide by it). Rescales the stored part when values grow.
+__device__ double miller_row(double x, int M, double* row, int stride) {
+  if (x < 1e-8) {
+    double t = 1.0;
+    for (int i = 0; i <= M; ++i) {
+      row[i * stride] = t;
+      t *= 0.5 * x / (double)(i + 1);
+    }
+    return 1.0;
+  }
+  const double inv = 2.0 / x;
+  const int N = miller_start(M, x);
+  double fn1 = 0.0, fn = 1e-200, sum = 0.0;
+  for (int i = 0; i <= M; ++i) row[i * stride] = 0.0;
+  for (int n = N; n >= 1; --n) {
+    const double fm = (double)n * inv * fn - fn1;
+    if ((n & 1) == 0) sum += fn;
+    if (n - 1 <= M) row[(n - 1) * stride] = fm;
+    fn1 = fn;
+    fn = fm;
+    if (fabs(fn) > kRescale) {
+      const double sc = 1.0 / kRescale;
+      fn *= sc;
+      fn1 *= sc;
+      sum *= sc;
+      for (int i = n - 1; i <= M; ++i) row[i * stride] *= sc;
+    }
+  }
+  return fn + 2.0 * sum;
 }
 
-qbx_status fmm_eval(qbx_handle* h, bool has_S, bool has_D, cd* out, int precision,
-                    cudaStream_t s) {
-  (void)h; (void)has_S; (void)has_D; (void)out; (void)precision; (void)s;
-  set_error("QBX_FMM mode is not available in this build");
-  return QBX_ERR_STATE;
+// ---------------------------------------------------------------- translation tables
+// One thread per (level, item): items 0..48 M2L offset classes, 49..52 M2M
+// quadrants, 53..56 L2L quadrants.
+__global__ void tables_kernel(int n_levels, double side, double k, int pb,
+                              const double* __restrict__ scale, cd* __restrict__ t_m2l,
+                              cd* __restrict__ t_m2m, cd* __restrict__ t_l2l,
+                              double* __restrict__ jwork) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_levels * 57) return;
+  const int l = g / 57, item = g % 57;
+  const int T = 4 * pb + 1, M = 2 * pb;
+  const double sl = side / (double)(1 << l);
+  if (item < 49) {
+    cd* out = t_m2l + ((size_t)l * 49 + item) * T;
+    const int dx = item / 7 - 3, dy = item % 7 - 3;  // (ix_b - ix_c, iy_b - iy_c)
+    if (l < 2 || max(abs(dx), abs(dy)) < 2) {
+      for (int m = 0; m < T; ++m) out[m] = mk(0.0, 0.0);
+      return;
+    }
+    const double s = scale[l];
+    const double Dx = dx * sl, Dy = dy * sl, r = sqrt(Dx * Dx + Dy * Dy), x = k * r;
+    const cd e1 = mk(Dx / r, Dy / r);
+    cd h0, h1;
+    hankel01(x, h0, h1);
+    cd hm1 = h0, hm = cscale(h1, s);  // scaled H_m s^m
+    cd e = mk(1.0, 0.0);
+    out[M] = h0;
+    for (int m = 1; m <= M; ++m) {
+      e = cmul(e, e1);
+      const cd hh = m == 1 ? hm : hm;
+      out[M + m] = cmul(hh, e);
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      out[M - m] = cscale(cmul(hh, cconj(e)), sg);
+      // next: H_{m+1} s^{m+1} = (2m/x) s H_m s^m - s^2 H_{m-1} s^{m-1}
+      const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
+      hm1 = hm;
+      hm = hn;
+    }
+    return;
+  }
+  const bool m2m = item < 53;
+  const int c = m2m ? item - 49 : item - 53;
+  cd* out = (m2m ? t_m2m : t_l2l) + ((size_t)l * 4 + c) * T;
+  if (l + 1 >= n_levels) {
+    for (int m = 0; m < T; ++m) out[m] = mk(0.0, 0.0);
+    return;
+  }
+  // child centre minus parent centre, child side = sl/2
+  const double cs = 0.5 * sl;
+  const double dx = ((c & 1) - 0.5) * cs, dy = ((c >> 1) - 0.5) * cs;
+  const double r = sqrt(dx * dx + dy * dy), x = k * r;
+  double* J = jwork + (size_t)g * (M + 1);
+  const double norm = miller_row(x, M, J, 1);
+  const cd e1 = mk(dx / r, dy / r);
+  cd e = mk(1.0, 0.0);
+  for (int m = 0; m <= M; ++m) {
+    const double j = J[m] / norm;
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    if (m2m) {  // conj(V_m) = J_m e^{-im th}; conj(V_{-m}) = (-1)^m J_m e^{im th}
+      out[M + m] = cscale(cconj(e), j);
+      out[M - m] = cscale(e, sg * j);
+    } else {    // (-1)^m V_m = (-1)^m J_m e^{im th}; (-1)^m V_{-m} = J_m e^{-im th}
+      out[M + m] = cscale(e, sg * j);
+      out[M - m] = cscale(cconj(e), j);
+    }
+    e = cmul(e, e1);
+  }
+}
+
+__global__ void powers_kernel(int n_levels, int pb, const double* __restrict__ scale,
+                              double* __restrict__ pw, double* __restrict__ ipw) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_levels) return;
+  const double s = scale[l];
+  double a = 1.0;
+  for (int j = 0; j < 2 * pb + 3; ++j) {
+    pw[(size_t)l * (2 * pb + 3) + j] = a;
+    a *= s;
+  }
+  a = 1.0;
+  for (int j = 0; j < pb + 2; ++j) {
+    ipw[(size_t)l * (pb + 2) + j] = a;
+    a /= s;
+  }
+}
+
+// ---------------------------------------------------------------- strengths
+__global__ void gather_strengths_kernel(int64_t n, const int* __restrict__ perm,
+                                        const cd* __restrict__ q, const cd* __restrict__ d,
+                                        cd* __restrict__ qs, cd* __restrict__ ds) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  qs[i] = q[perm[i]];
+  ds[i] = d[perm[i]];
+}
+
+// ---------------------------------------------------------------- P2M (Stage 2)
+// CTA per leaf. Threads 0..kChunk-1 fill one row each with
+// conj(V_m(y - m_b)) / s^m, m = 0..pb+1; then all threads reduce over the rows.
+__global__ void __launch_bounds__(kThreads) p2m_kernel(Fmm F, const int* __restrict__ leaves) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, R = pb + 2;
+  cd* rows = smem;                      // [kChunk][R]
+  cd* sq = rows + kChunk * R;           // [kChunk]
+  cd* sd = sq + kChunk;                 // [kChunk]
+  cd* snu = sd + kChunk;                // [kChunk]
+  __shared__ int cnt;
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rsrc[b];
+  const int l = F.level[b];
+  const double s = F.scale[l];
+  const double2 m = F.centre[b];
+  const double hk = 0.5 * F.k;
+  cd acc[2];
+  acc[0] = acc[1] = mk(0.0, 0.0);
+  for (int base = r.x; base < r.y; base += kChunk) {
+    if (threadIdx.x == 0) cnt = min(kChunk, r.y - base);
+    if (threadIdx.x < kChunk && base + (int)threadIdx.x < r.y) {
+      const int i = base + threadIdx.x;
+      const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
+      const double rr = sqrt(dx * dx + dy * dy);
+      double* row = (double*)(rows + threadIdx.x * R);  // J values in the real slots
+      const double norm = miller_row(F.k * rr, R - 1, row, 2);
+      const cd em = rr > 0.0 ? mk(dx / rr, -dy / rr) : mk(1.0, 0.0);  // e^{-i th}
+      cd e = mk(1.0, 0.0);
+      double is = 1.0 / norm;
+      for (int j = 0; j < R; ++j) {
+        const double v = row[2 * j] * is;
+        rows[threadIdx.x * R + j] = cscale(e, v);
+        e = cmul(e, em);
+        is /= s;
+      }
+      sq[threadIdx.x] = F.qs[i];
+      sd[threadIdx.x] = F.ds[i];
+      snu[threadIdx.x] = mk(F.snrm[i].x, F.snrm[i].y);
+    }
+    __syncthreads();
+    for (int o = 0; o < 2; ++o) {
+      const int n = (int)threadIdx.x + o * kThreads - pb;
+      if (n > pb) continue;
+      const int an = abs(n);
+      for (int j = 0; j < cnt; ++j) {
+        const cd* row = rows + j * R;
+        // cv(t) = conj(V_t)/s^|t|; for t < 0: (-1)^t conj(row[|t|])
+        auto cv = [&](int t) -> cd {
+          const int at = abs(t);
+          cd v = row[at];
+          if (t < 0) {
+            v = cconj(v);
+            if (at & 1) v = mk(-v.x, -v.y);
+          }
+          return v;
+        };
+        if (F.has_S) cfma(acc[o], sq[j], cv(n));
+        if (F.has_D) {
+          const double fm = (abs(n - 1) > an) ? s : 1.0 / s;
+          const double fp = (abs(n + 1) > an) ? s : 1.0 / s;
+          const cd t = csub(cscale(cmul(cconj(snu[j]), cv(n - 1)), fm),
+                            cscale(cmul(snu[j], cv(n + 1)), fp));
+          cfma(acc[o], cscale(sd[j], hk), t);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int o = 0; o < 2; ++o) {
+    const int n = (int)threadIdx.x + o * kThreads - pb;
+    if (n <= pb) F.mpole[(size_t)b * F.Q + (n + pb)] = acc[o];
+  }
+}
+
+// ---------------------------------------------------------------- M2M (Stage 2)
+__global__ void __launch_bounds__(kThreads) m2m_kernel(Fmm F, const int* __restrict__ boxes) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, Q = F.Q, T = 4 * pb + 1;
+  cd* a = smem;        // [Q]
+  cd* t = a + Q;       // [T]
+  const int b = boxes[blockIdx.x];
+  const int l = F.level[b];
+  const double* pwc = pw_row(F, l + 1);
+  const double* ipp = ipw_row(F, l);
+  cd acc[2];
+  acc[0] = acc[1] = mk(0.0, 0.0);
+  for (int c = 0; c < 4; ++c) {
+    const int d = F.child[4 * b + c];
+    if (d < 0) continue;
+    for (int i = threadIdx.x; i < Q; i += kThreads)
+      a[i] = cscale(F.mpole[(size_t)d * Q + i], pwc[abs(i - pb)]);
+    const cd* tab = F.t_m2m + ((size_t)l * 4 + c) * T;
+    for (int i = threadIdx.x; i < T; i += kThreads) t[i] = tab[i];
+    __syncthreads();
+    for (int o = 0; o < 2; ++o) {
+      const int s = (int)threadIdx.x + o * kThreads - pb;
+      if (s > pb) continue;
+      cd sum = mk(0.0, 0.0);
+      for (int n = -pb; n <= pb; ++n) cfma(sum, t[s - n + 2 * pb], a[n + pb]);
+      acc[o] = cadd(acc[o], sum);
+    }
+    __syncthreads();
+  }
+  for (int o = 0; o < 2; ++o) {
+    const int s = (int)threadIdx.x + o * kThreads - pb;
+    if (s <= pb) F.mpole[(size_t)b * Q + s + pb] = cscale(acc[o], ipp[abs(s)]);
+  }
+}
+
+// ---------------------------------------------------------------- M2L (Stage 4)
+// lh_l += (-1)^l sum_n What_{n+l} mh_n c(l,n), What_m = s^|m| W_m(m_b - m_c),
+// c(l,n) = s^{2 min(|l|,|n|)} when l and n have opposite signs, else 1.
+__global__ void __launch_bounds__(kThreads) m2l_kernel(Fmm F, const int* __restrict__ boxes) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, Q = F.Q, T = 4 * pb + 1;
+  cd* a = smem;                       // [Q]
+  cd* w = a + Q;                      // [T]
+  double* p2 = (double*)(w + T);      // [pb+1] s^{2j}
+  const int b = boxes[blockIdx.x];
+  const int l = F.level[b];
+  const double* pwl = pw_row(F, l);
+  for (int j = threadIdx.x; j <= pb; j += kThreads) p2[j] = pwl[2 * j];
+  cd acc[2];
+  acc[0] = acc[1] = mk(0.0, 0.0);
+  for (int e = F.voff[b]; e < F.voff[b + 1]; ++e) {
+    const int c = F.vidx[e];
+    const cd* tab = F.t_m2l + ((size_t)l * 49 + F.vcls[e]) * T;
+    for (int i = threadIdx.x; i < Q; i += kThreads) a[i] = F.mpole[(size_t)c * Q + i];
+    for (int i = threadIdx.x; i < T; i += kThreads) w[i] = tab[i];
+    __syncthreads();
+    for (int o = 0; o < 2; ++o) {
+      const int lo = (int)threadIdx.x + o * kThreads - pb;
+      if (lo > pb) continue;
+      cd same = mk(0.0, 0.0), opp = mk(0.0, 0.0);
+      for (int n = -pb; n <= pb; ++n) {
+        const cd term = cmul(w[n + lo + 2 * pb], a[n + pb]);
+        if ((lo < 0 && n > 0) || (lo > 0 && n < 0)) {
+          const int mn = min(abs(lo), abs(n));
+          opp = cadd(opp, cscale(term, p2[mn]));
+        } else {
+          same = cadd(same, term);
+        }
+      }
+      const cd sum = cadd(same, opp);
+      acc[o] = (lo & 1) ? csub(acc[o], sum) : cadd(acc[o], sum);
+    }
+    __syncthreads();
+  }
+  for (int o = 0; o < 2; ++o) {
+    const int lo = (int)threadIdx.x + o * kThreads - pb;
+    if (lo <= pb) {
+      cd* dst = F.local + (size_t)b * Q + lo + pb;
+      *dst = cadd(*dst, acc[o]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- P2L (Stage 6)
+// CTA per box with an X list: lh_l += s^|l| sum_j [q W_l + d (k/2)(nu W_{l-1} - conj(nu) W_{l+1})]
+__global__ void __launch_bounds__(kThreads) p2l_kernel(Fmm F, const int* __restrict__ boxes) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, R = pb + 2;
+  cd* hrow = smem;                  // [kChunk][R] H_m s^m
+  cd* erow = hrow + kChunk * R;     // [kChunk][R] e^{i m th}
+  cd* sq = erow + kChunk * R;
+  cd* sd = sq + kChunk;
+  cd* snu = sd + kChunk;
+  __shared__ int cnt;
+  const int b = boxes[blockIdx.x];
+  const int l = F.level[b];
+  const double s = F.scale[l];
+  const double2 m = F.centre[b];
+  const double hk = 0.5 * F.k;
+  cd acc[2];
+  acc[0] = acc[1] = mk(0.0, 0.0);
+  for (int e = F.xoff[b]; e < F.xoff[b + 1]; ++e) {
+    const int2 r = F.rsrc[F.xidx[e]];
+    for (int base = r.x; base < r.y; base += kChunk) {
+      if (threadIdx.x == 0) cnt = min(kChunk, r.y - base);
+      if (threadIdx.x < kChunk && base + (int)threadIdx.x < r.y) {
+        const int i = base + threadIdx.x;
+        const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
+        const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+        const cd e1 = mk(dx / rr, dy / rr);
+        cd h0, h1;
+        hankel01(x, h0, h1);
+        cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
+        cd* hr = hrow + threadIdx.x * R;
+        cd* er = erow + threadIdx.x * R;
+        hr[0] = h0;
+        er[0] = ee;
+        for (int j = 1; j < R; ++j) {
+          ee = cmul(ee, e1);
+          hr[j] = hm;
+          er[j] = ee;
+          const cd hn = csub(cscale(hm, 2.0 * j * s / x), cscale(hm1, s * s));
+          hm1 = hm;
+          hm = hn;
+        }
+        sq[threadIdx.x] = F.qs[i];
+        sd[threadIdx.x] = F.ds[i];
+        snu[threadIdx.x] = mk(F.snrm[i].x, F.snrm[i].y);
+      }
+      __syncthreads();
+      for (int o = 0; o < 2; ++o) {
+        const int n = (int)threadIdx.x + o * kThreads - pb;
+        if (n > pb) continue;
+        const int an = abs(n);
+        for (int j = 0; j < cnt; ++j) {
+          const cd* hr = hrow + j * R;
+          const cd* er = erow + j * R;
+          // Wh(t) = s^|t| W_t; for t < 0: (-1)^t H_|t| s^|t| conj(e^{i|t|th})
+          auto wh = [&](int t) -> cd {
+            const int at = abs(t);
+            cd v = t >= 0 ? cmul(hr[at], er[at]) : cmul(hr[at], cconj(er[at]));
+            if (t < 0 && (at & 1)) v = mk(-v.x, -v.y);
+            return v;
+          };
+          if (F.has_S) cfma(acc[o], sq[j], wh(n));
+          if (F.has_D) {
+            const double fm = (abs(n - 1) > an) ? 1.0 / s : s;  // s^{|n| - |n-1|}
+            const double fp = (abs(n + 1) > an) ? 1.0 / s : s;
+            const cd t = csub(cscale(cmul(snu[j], wh(n - 1)), fm),
+                              cscale(cmul(cconj(snu[j]), wh(n + 1)), fp));
+            cfma(acc[o], cscale(sd[j], hk), t);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int o = 0; o < 2; ++o) {
+    const int n = (int)threadIdx.x + o * kThreads - pb;
+    if (n <= pb) {
+      cd* dst = F.local + (size_t)b * F.Q + n + pb;
+      *dst = cadd(*dst, acc[o]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- L2L (Stage 7)
+__global__ void __launch_bounds__(kThreads) l2l_kernel(Fmm F, const int* __restrict__ boxes) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, Q = F.Q, T = 4 * pb + 1;
+  cd* g = smem;   // true local coefficients gamma_n
+  cd* t = g + Q;
+  const int b = boxes[blockIdx.x];
+  const int l = F.level[b];
+  const double* ipp = ipw_row(F, l);
+  const double* pwc = pw_row(F, l + 1);
+  for (int i = threadIdx.x; i < Q; i += kThreads)
+    g[i] = cscale(F.local[(size_t)b * Q + i], ipp[abs(i - pb)]);
+  for (int c = 0; c < 4; ++c) {
+    const int d = F.child[4 * b + c];
+    if (d < 0) continue;
+    const cd* tab = F.t_l2l + ((size_t)l * 4 + c) * T;
+    for (int i = threadIdx.x; i < T; i += kThreads) t[i] = tab[i];
+    __syncthreads();
+    for (int o = 0; o < 2; ++o) {
+      const int s = (int)threadIdx.x + o * kThreads - pb;
+      if (s > pb) continue;
+      cd sum = mk(0.0, 0.0);
+      for (int n = -pb; n <= pb; ++n) cfma(sum, t[s - n + 2 * pb], g[n + pb]);
+      cd* dst = F.local + (size_t)d * Q + s + pb;
+      *dst = cadd(*dst, cscale(sum, pwc[abs(s)]));
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- targets (Stages 3, 5, 8)
+// CTA per leaf; one thread per target of the leaf (strided). Only targets that
+// are not associated with a QBX centre are evaluated.
+// L2P writes out[t], M2P and P2P add to it.
+__global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restrict__ leaves,
+                                                       cd* __restrict__ out) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, Q = F.Q;
+  cd* g = smem;
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rtgt[b];
+  if (r.y <= r.x) return;
+  const int l = F.level[b];
+  const double* ipp = ipw_row(F, l);
+  for (int i = threadIdx.x; i < Q; i += kThreads)
+    g[i] = cscale(F.local[(size_t)b * Q + i], ipp[abs(i - pb)]);
+  __syncthreads();
+  const double2 m = F.centre[b];
+  for (int i = r.x + threadIdx.x; i < r.y; i += kThreads) {
+    if (F.tassoc[i] >= 0) continue;
+    const double dx = F.txy[i].x - m.x, dy = F.txy[i].y - m.y;
+    const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+    const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
+    // psi = sum_m f_m [g_m e^{-im th} + (m>0) (-1)^m g_{-m} e^{im th}] / norm
+    cd epb = mk(1.0, 0.0);
+    for (int j = 0; j < pb; ++j) epb = cmul(epb, e1);  // e^{i pb th}
+    cd acc = mk(0.0, 0.0);
+    double norm;
+    if (x < 1e-8) {
+      acc = g[pb];  // only J_0 survives
+      norm = 1.0;
+    } else {
+      const double inv = 2.0 / x;
+      const int N = miller_start(pb, x);
+      double fn1 = 0.0, fn = 1e-200, sum = 0.0;
+      cd e = epb;  // e^{i m th} for the current m (set when m <= pb)
+      for (int n = N; n >= 1; --n) {
+        const double fm = (double)n * inv * fn - fn1;  // f_{n-1}
+        if ((n & 1) == 0) sum += fn;
+        const int mm = n - 1;
+        if (mm <= pb) {
+          if (mm < pb) e = cmul(e, cconj(e1));
+          cfma(acc, cscale(g[pb + mm], fm), cconj(e));
+          if (mm > 0) cfma(acc, cscale(g[pb - mm], (mm & 1) ? -fm : fm), e);
+        }
+        fn1 = fn;
+        fn = fm;
+        if (fabs(fn) > kRescale) {
+          const double sc = 1.0 / kRescale;
+          fn *= sc; fn1 *= sc; sum *= sc;
+          acc = cscale(acc, sc);
+        }
+      }
+      norm = fn + 2.0 * sum;
+    }
+    out[F.tid[i]] = cscale(acc, 1.0 / norm);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restrict__ leaves,
+                                                       cd* __restrict__ out) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, Q = F.Q;
+  cd* a = smem;
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rtgt[b];
+  const int e0 = F.woff[b], e1_ = F.woff[b + 1];
+  if (r.y <= r.x || e1_ <= e0) return;
+  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
+    const int i = i0 + threadIdx.x;
+    const bool act = i < r.y && F.tassoc[i] < 0;
+    cd acc = mk(0.0, 0.0);
+    for (int e = e0; e < e1_; ++e) {
+      const int c = F.widx[e];
+      __syncthreads();
+      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = F.mpole[(size_t)c * Q + j];
+      __syncthreads();
+      if (!act) continue;
+      const double s = F.scale[F.level[c]];
+      const double2 mc = F.centre[c];
+      const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
+      const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+      const cd e1 = mk(dx / rr, dy / rr);
+      cd h0, h1;
+      hankel01(x, h0, h1);
+      cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
+      cd sum = cmul(a[pb], h0);
+      for (int m = 1; m <= pb; ++m) {
+        ee = cmul(ee, e1);
+        cfma(sum, a[pb + m], cmul(hm, ee));
+        const cd v = cmul(hm, cconj(ee));
+        cfma(sum, a[pb - m], (m & 1) ? mk(-v.x, -v.y) : v);
+        const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
+        hm1 = hm;
+        hm = hn;
+      }
+      acc = cadd(acc, sum);
+    }
+    if (act) {
+      cd* dst = out + F.tid[i];
+      *dst = cadd(*dst, acc);
+    }
+  }
+}
+
+template <bool HS, bool HD>
+__global__ void __launch_bounds__(kThreads) p2p_ulist_kernel(Fmm F, const int* __restrict__ leaves,
+                                                             cd* __restrict__ out) {
+  __shared__ double2 s_xy[kThreads];
+  __shared__ double2 s_n[kThreads];
+  __shared__ cd s_q[kThreads];
+  __shared__ cd s_d[kThreads];
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rtgt[b];
+  if (r.y <= r.x) return;
+  const double k = F.k;
+  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
+    const int i = i0 + threadIdx.x;
+    const bool act = i < r.y && F.tassoc[i] < 0;
+    const double tx = act ? F.txy[i].x : 0.0, ty = act ? F.txy[i].y : 0.0;
+    cd acc = mk(0.0, 0.0);
+    for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
+      const int2 sr = F.rsrc[F.uidx[e]];
+      for (int base = sr.x; base < sr.y; base += kThreads) {
+        __syncthreads();
+        const int j = base + threadIdx.x;
+        if (j < sr.y) {
+          s_xy[threadIdx.x] = F.sxy[j];
+          if (HS) s_q[threadIdx.x] = F.qs[j];
+          if (HD) {
+            s_n[threadIdx.x] = F.snrm[j];
+            s_d[threadIdx.x] = F.ds[j];
+          }
+        }
+        __syncthreads();
+        const int cnt = min(kThreads, sr.y - base);
+        if (!act) continue;
+        for (int jj = 0; jj < cnt; ++jj) {
+          const double dx = tx - s_xy[jj].x, dy = ty - s_xy[jj].y;
+          const double rr = sqrt(dx * dx + dy * dy);
+          if (rr == 0.0) continue;
+          const double x = k * rr;
+          if (HS) cfma(acc, s_q[jj], mk(j0(x), y0(x)));
+          if (HD) {
+            const double f = k * (s_n[jj].x * dx + s_n[jj].y * dy) / rr;
+            cfma(acc, s_d[jj], mk(f * j1(x), f * y1(x)));
+          }
+        }
+      }
+    }
+    if (act) {
+      cd* dst = out + F.tid[i];
+      *dst = cadd(*dst, acc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- centres (Stages 3, 5, 8 "New")
+// L2QBXL: alpha_s = sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p.
+template <int PM>
+__global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
+                                                          cd* __restrict__ alpha) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, Q = F.Q, p = F.p, P = 2 * p + 1;
+  cd* g = smem;
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rctr[b];
+  if (r.y <= r.x) return;
+  const int l = F.level[b];
+  const double* ipp = ipw_row(F, l);
+  for (int i = threadIdx.x; i < Q; i += kThreads)
+    g[i] = cscale(F.local[(size_t)b * Q + i], ipp[abs(i - pb)]);
+  __syncthreads();
+  const double2 mb = F.centre[b];
+  const int M = pb + p;
+  for (int i = r.x + threadIdx.x; i < r.y; i += kThreads) {
+    const double dx = F.cxy[i].x - mb.x, dy = F.cxy[i].y - mb.y;
+    const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+    const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
+    cd acc[2 * PM + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
+    // one order m of V: V_m = f_m e^{im th}, V_{-m} = (-1)^m f_m e^{-im th}
+    auto add_m = [&](int mm, double fm, cd e) {
+      const double sg = (mm & 1) ? -1.0 : 1.0;
+      const cd vp = cscale(e, fm * sg);           // (-1)^m V_m
+      const cd vn = cscale(cconj(e), fm);         // (-1)^m V_{-m} = J_m e^{-im th}
+#pragma unroll
+      for (int so = -PM; so <= PM; ++so) {
+        if (so < -p || so > p) continue;
+        const int n1 = so - mm;                   // uses V_m
+        if (n1 >= -pb && n1 <= pb) cfma(acc[so + PM], g[n1 + pb], vp);
+        if (mm > 0) {
+          const int n2 = so + mm;                 // uses V_{-m}
+          if (n2 >= -pb && n2 <= pb) cfma(acc[so + PM], g[n2 + pb], vn);
+        }
+      }
+    };
+    double norm;
+    if (x < 1e-8) {
+      add_m(0, 1.0, mk(1.0, 0.0));
+      norm = 1.0;
+    } else {
+      cd e = mk(1.0, 0.0);
+      for (int j = 0; j < M; ++j) e = cmul(e, e1);  // e^{i M th}
+      const double inv = 2.0 / x;
+      const int N = miller_start(M, x);
+      double fn1 = 0.0, fn = 1e-200, sum = 0.0;
+      for (int n = N; n >= 1; --n) {
+        const double fm = (double)n * inv * fn - fn1;
+        if ((n & 1) == 0) sum += fn;
+        const int mm = n - 1;
+        if (mm <= M) {
+          if (mm < M) e = cmul(e, cconj(e1));
+          add_m(mm, fm, e);
+        }
+        fn1 = fn;
+        fn = fm;
+        if (fabs(fn) > kRescale) {
+          const double sc = 1.0 / kRescale;
+          fn *= sc; fn1 *= sc; sum *= sc;
+#pragma unroll
+          for (int j = 0; j <= 2 * PM; ++j) acc[j] = cscale(acc[j], sc);
+        }
+      }
+      norm = fn + 2.0 * sum;
+    }
+    const double in = 1.0 / norm;
+    cd* dst = alpha + (size_t)F.cid[i] * P;
+    for (int so = -p; so <= p; ++so) dst[so + p] = cscale(acc[so + PM], in);
+  }
+}
+
+// M2QBXL: alpha_l += (-1)^l sum_n mh_n Wh_{n+l} s^{|n| - |n+l|},  Wh_m = s^|m| W_m(z - m_c)
+template <int PM>
+__global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
+                                                          cd* __restrict__ alpha) {
+  extern __shared__ cd smem[];
+  const int pb = F.pb, Q = F.Q, p = F.p, P = 2 * p + 1;
+  cd* a = smem;
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rctr[b];
+  const int e0 = F.woff[b], e1_ = F.woff[b + 1];
+  if (r.y <= r.x || e1_ <= e0) return;
+  const int M = pb + p;
+  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
+    const int i = i0 + threadIdx.x;
+    const bool act = i < r.y;
+    cd acc[2 * PM + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
+    for (int e = e0; e < e1_; ++e) {
+      const int c = F.widx[e];
+      __syncthreads();
+      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = F.mpole[(size_t)c * Q + j];
+      __syncthreads();
+      if (!act) continue;
+      const double s = F.scale[F.level[c]];
+      const double is = 1.0 / s;
+      const double2 mc = F.centre[c];
+      const double dx = F.cxy[i].x - mc.x, dy = F.cxy[i].y - mc.y;
+      const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+      const cd e1 = mk(dx / rr, dy / rr);
+      cd h0, h1;
+      hankel01(x, h0, h1);
+      cd hm1 = h0, hm = h0, ee = mk(1.0, 0.0);
+      for (int mm = 0; mm <= M; ++mm) {
+        if (mm == 1) { hm1 = h0; hm = cscale(h1, s); }
+        if (mm >= 1) ee = cmul(ee, e1);
+        const cd wp = cmul(hm, ee);                                   // Wh_m
+        const cd wq = cscale(cmul(hm, cconj(ee)), (mm & 1) ? -1.0 : 1.0);  // Wh_{-m}
+#pragma unroll
+        for (int lo = -PM; lo <= PM; ++lo) {
+          if (lo < -p || lo > p) continue;
+          const double sg = (lo & 1) ? -1.0 : 1.0;
+          const int n1 = mm - lo;  // n + l = m
+          if (n1 >= -pb && n1 <= pb) {
+            // s^{|n| - |m|}
+            int ex = abs(n1) - mm;
+            double f = 1.0;
+            for (int q = 0; q < abs(ex); ++q) f *= (ex > 0 ? s : is);
+            cfma(acc[lo + PM], cscale(a[n1 + pb], sg * f), wp);
+          }
+          if (mm > 0) {
+            const int n2 = -mm - lo;  // n + l = -m
+            if (n2 >= -pb && n2 <= pb) {
+              int ex = abs(n2) - mm;
+              double f = 1.0;
+              for (int q = 0; q < abs(ex); ++q) f *= (ex > 0 ? s : is);
+              cfma(acc[lo + PM], cscale(a[n2 + pb], sg * f), wq);
+            }
+          }
+        }
+        if (mm >= 1) {
+          const cd hn = csub(cscale(hm, 2.0 * mm * s / x), cscale(hm1, s * s));
+          hm1 = hm;
+          hm = hn;
+        }
+      }
+    }
+    if (act) {
+      cd* dst = alpha + (size_t)F.cid[i] * P;
+      for (int lo = -p; lo <= p; ++lo) dst[lo + p] = cadd(dst[lo + p], acc[lo + PM]);
+    }
+  }
+}
+
+// P2QBXL over the U list (Stage 3 "New"): direct coefficients from nearby sources.
+template <int PM, bool HS, bool HD>
+__global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
+                                                                const int* __restrict__ leaves,
+                                                                cd* __restrict__ alpha) {
+  __shared__ double2 s_xy[kThreads];
+  __shared__ double2 s_nu[kThreads];
+  __shared__ cd s_q[kThreads];
+  __shared__ cd s_d[kThreads];
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rctr[b];
+  if (r.y <= r.x) return;
+  const double k = F.k, hk = 0.5 * k;
+  const int p = F.p, P = 2 * p + 1;
+  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
+    const int i = i0 + threadIdx.x;
+    const bool act = i < r.y;
+    const double cx = act ? F.cxy[i].x : 0.0, cy = act ? F.cxy[i].y : 0.0;
+    cd acc[2 * PM + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
+    for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
+      const int2 sr = F.rsrc[F.uidx[e]];
+      for (int base = sr.x; base < sr.y; base += kThreads) {
+        __syncthreads();
+        const int j = base + threadIdx.x;
+        if (j < sr.y) {
+          s_xy[threadIdx.x] = F.sxy[j];
+          if (HS) s_q[threadIdx.x] = F.qs[j];
+          if (HD) {
+            s_nu[threadIdx.x] = F.snrm[j];
+            s_d[threadIdx.x] = F.ds[j];
+          }
+        }
+        __syncthreads();
+        const int cnt = min(kThreads, sr.y - base);
+        if (!act) continue;
+        for (int jj = 0; jj < cnt; ++jj) {
+          const double dx = s_xy[jj].x - cx, dy = s_xy[jj].y - cy;
+          const double rr = sqrt(dx * dx + dy * dy);
+          if (rr == 0.0) continue;
+          const double ir = 1.0 / rr, x = k * rr, ix2 = 2.0 / x;
+          const cd e1 = mk(dx * ir, dy * ir);
+          cd h0, h1;
+          hankel01(x, h0, h1);
+          const cd q = HS ? s_q[jj] : mk(0.0, 0.0);
+          const cd dk = HD ? cscale(s_d[jj], hk) : mk(0.0, 0.0);
+          const cd nu = HD ? mk(s_nu[jj].x, s_nu[jj].y) : mk(0.0, 0.0);
+          const cd nub = cconj(nu);
+          const cd w1 = cmul(h1, e1);
+          const cd wm1 = cscale(cmul(h1, cconj(e1)), -1.0);
+          if (HS) cfma(acc[PM], q, h0);
+          if (HD) cfma(acc[PM], dk, csub(cmul(nu, wm1), cmul(nub, w1)));
+          cd hprev = h0, hcur = h1, eprev = mk(1.0, 0.0), ecur = e1;
+          double sgn = -1.0;
+#pragma unroll
+          for (int m = 1; m <= PM; ++m) {
+            if (m > p) break;
+            const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
+            const cd enext = cmul(ecur, e1);
+            const cd w_m = cmul(hcur, ecur);
+            const cd w_p = cmul(hnext, enext);
+            const cd w_pm = cmul(hprev, eprev);
+            const cd v_m = cscale(cmul(hcur, cconj(ecur)), sgn);
+            const cd v_p = cscale(cmul(hnext, cconj(enext)), -sgn);
+            const cd v_pm = cscale(cmul(hprev, cconj(eprev)), -sgn);
+            if (HS) {
+              cfma(acc[PM + m], q, w_m);
+              cfma(acc[PM - m], q, v_m);
+            }
+            if (HD) {
+              cfma(acc[PM + m], dk, csub(cmul(nu, w_pm), cmul(nub, w_p)));
+              cfma(acc[PM - m], dk, csub(cmul(nu, v_p), cmul(nub, v_pm)));
+            }
+            hprev = hcur;
+            hcur = hnext;
+            eprev = ecur;
+            ecur = enext;
+            sgn = -sgn;
+          }
+        }
+      }
+    }
+    if (act) {
+      cd* dst = alpha + (size_t)F.cid[i] * P;
+      for (int lo = -p; lo <= p; ++lo) dst[lo + p] = cadd(dst[lo + p], acc[lo + PM]);
+    }
+  }
+}
+
+int p_add_default(int p) {
+  // Table 2 of the paper for p <= 8 (2: 5, 4: 5, 6: 15, 8: 20); 2.5 p beyond
+  if (p <= 4) return 5;
+  if (p <= 6) return 15;
+  if (p <= 8) return 20;
+  return (5 * p + 1) / 2;
+}
+
+}  // namespace
+
+#define TRY(x)                          \
+  do {                                  \
+    qbx_status s_ = (x);                \
+    if (s_ != QBX_OK) return s_;        \
+  } while (0)
+
+qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* on_node_dev,
+                          const int8_t* on_side_dev, double eps) {
+  if (h->fmm) fmm_plan_free(h->fmm);
+  FmmPlan* f = new FmmPlan();
+  h->fmm = f;
+  const int n_max = d->n_max > 0 ? d->n_max : 64;
+  TRY(tree_build(h, f, n_max));
+  TRY(tree_lists(h, f));
+  TRY(tree_associate(h, f, on_node_dev, on_side_dev, eps));
+  TRY(gather_sorted(h, f));
+  const int p_add = d->p_add >= 0 ? d->p_add : p_add_default(h->p);
+  f->pb = std::max(1, d->p_fmm + p_add);
+  if (f->pb > 80) {
+    set_error("box expansion order p_fmm + p_add = %d exceeds 80", f->pb);
+    return QBX_ERR_ARG;
+  }
+  f->Q = 2 * f->pb + 1;
+  // scales, powers, translation tables
+  std::vector<double> sc(f->n_levels);
+  for (int l = 0; l < f->n_levels; ++l) {
+    sc[l] = std::min(1.0, h->k * f->side / (double)(1 << l));
+    if (std::pow(sc[l], f->pb + 1) < 1e-250) {
+      set_error("tree level %d too fine for the box order %d (k*side = %.3g)", l, f->pb, sc[l]);
+      return QBX_ERR_ARG;
+    }
+  }
+  QBX_CUDA_TRY(f->scale.alloc(f->n_levels));
+  QBX_CUDA_TRY(cudaMemcpy(f->scale.ptr, sc.data(), sc.size() * sizeof(double),
+                          cudaMemcpyHostToDevice));
+  const int T = 4 * f->pb + 1;
+  QBX_CUDA_TRY(f->t_m2l.alloc((size_t)f->n_levels * 49 * T));
+  QBX_CUDA_TRY(f->t_m2m.alloc((size_t)f->n_levels * 4 * T));
+  QBX_CUDA_TRY(f->t_l2l.alloc((size_t)f->n_levels * 4 * T));
+  QBX_CUDA_TRY(f->pw.alloc((size_t)f->n_levels * (2 * f->pb + 3)));
+  QBX_CUDA_TRY(f->ipw.alloc((size_t)f->n_levels * (f->pb + 2)));
+  DevBuf<double> jwork;
+  QBX_CUDA_TRY(jwork.alloc((size_t)f->n_levels * 57 * (2 * f->pb + 1)));
+  tables_kernel<<<nblk(f->n_levels * 57, 64), 64>>>(f->n_levels, f->side, h->k, f->pb,
+                                                    f->scale.ptr, f->t_m2l.ptr, f->t_m2m.ptr,
+                                                    f->t_l2l.ptr, jwork.ptr);
+  powers_kernel<<<1, 64>>>(f->n_levels, f->pb, f->scale.ptr, f->pw.ptr, f->ipw.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  QBX_CUDA_TRY(f->mpole.alloc((size_t)f->n_boxes * f->Q));
+  QBX_CUDA_TRY(f->local.alloc((size_t)f->n_boxes * f->Q));
+  QBX_CUDA_TRY(f->qs.alloc(std::max<int64_t>(1, h->n_src)));
+  QBX_CUDA_TRY(f->ds.alloc(std::max<int64_t>(1, h->n_src)));
+  // leaves holding sources (P2M)
+  QBX_CUDA_TRY(cudaDeviceSynchronize());
+  // stats
+  std::vector<int> uoff(f->n_boxes + 1), woff(f->n_boxes + 1), xoff(f->n_boxes + 1);
+  std::vector<int2> rs(f->n_boxes), rc(f->n_boxes), rt(f->n_boxes);
+  std::vector<int> uidx(std::max<int64_t>(1, f->U.nnz)), widx(std::max<int64_t>(1, f->W.nnz)),
+      xidx(std::max<int64_t>(1, f->X.nnz));
+  QBX_CUDA_TRY(cudaMemcpy(uoff.data(), f->U.off.ptr, uoff.size() * 4, cudaMemcpyDeviceToHost));
+  QBX_CUDA_TRY(cudaMemcpy(woff.data(), f->W.off.ptr, woff.size() * 4, cudaMemcpyDeviceToHost));
+  QBX_CUDA_TRY(cudaMemcpy(xoff.data(), f->X.off.ptr, xoff.size() * 4, cudaMemcpyDeviceToHost));
+  QBX_CUDA_TRY(cudaMemcpy(rs.data(), f->box.rng[PT_SRC].ptr, rs.size() * 8, cudaMemcpyDeviceToHost));
+  QBX_CUDA_TRY(cudaMemcpy(rc.data(), f->box.rng[PT_CTR].ptr, rc.size() * 8, cudaMemcpyDeviceToHost));
+  QBX_CUDA_TRY(cudaMemcpy(rt.data(), f->box.rng[PT_TGT].ptr, rt.size() * 8, cudaMemcpyDeviceToHost));
+  if (f->U.nnz) QBX_CUDA_TRY(cudaMemcpy(uidx.data(), f->U.idx.ptr, f->U.nnz * 4, cudaMemcpyDeviceToHost));
+  if (f->W.nnz) QBX_CUDA_TRY(cudaMemcpy(widx.data(), f->W.idx.ptr, f->W.nnz * 4, cudaMemcpyDeviceToHost));
+  if (f->X.nnz) QBX_CUDA_TRY(cudaMemcpy(xidx.data(), f->X.idx.ptr, f->X.nnz * 4, cudaMemcpyDeviceToHost));
+  std::vector<int> assoc_s(std::max<int64_t>(1, h->n_tgt));
+  if (h->n_tgt)
+    QBX_CUDA_TRY(cudaMemcpy(assoc_s.data(), f->t_assoc.ptr, h->n_tgt * 4, cudaMemcpyDeviceToHost));
+  std::vector<int> leaves(f->n_leaves);
+  QBX_CUDA_TRY(cudaMemcpy(leaves.data(), f->leaves.ptr, leaves.size() * 4, cudaMemcpyDeviceToHost));
+  int64_t p2qbxl = 0, p2p = 0, m2qbxl = 0, m2p = 0, p2l = 0;
+  std::vector<int> src_leaves;
+  for (int b : leaves) {
+    int64_t us = 0;
+    for (int e = uoff[b]; e < uoff[b + 1]; ++e) us += rs[uidx[e]].y - rs[uidx[e]].x;
+    int64_t nd = 0;
+    for (int i = rt[b].x; i < rt[b].y; ++i) nd += assoc_s[i] < 0 ? 1 : 0;
+    p2qbxl += us * (rc[b].y - rc[b].x);
+    p2p += us * nd;
+    m2qbxl += (int64_t)(woff[b + 1] - woff[b]) * (rc[b].y - rc[b].x);
+    m2p += (int64_t)(woff[b + 1] - woff[b]) * nd;
+    if (rs[b].y > rs[b].x) src_leaves.push_back(b);
+  }
+  for (int b = 0; b < f->n_boxes; ++b)
+    for (int e = xoff[b]; e < xoff[b + 1]; ++e) p2l += rs[xidx[e]].y - rs[xidx[e]].x;
+  QBX_CUDA_TRY(f->src_leaves.alloc(std::max<size_t>(1, src_leaves.size())));
+  if (!src_leaves.empty())
+    QBX_CUDA_TRY(cudaMemcpy(f->src_leaves.ptr, src_leaves.data(), src_leaves.size() * 4,
+                            cudaMemcpyHostToDevice));
+  f->n_src_leaves = (int)src_leaves.size();
+  h->stats[4] = f->n_boxes;
+  h->stats[5] = f->n_leaves;
+  h->stats[6] = f->n_levels - 1;
+  h->stats[7] = f->pb;
+  h->stats[8] = f->U.nnz;
+  h->stats[9] = f->V.nnz;
+  h->stats[10] = f->W.nnz;
+  h->stats[11] = f->X.nnz;
+  h->stats[12] = p2qbxl;
+  h->stats[13] = p2p;
+  h->stats[14] = m2qbxl;
+  h->stats[15] = m2p;
+  h->stats[17] = p2l;
+  h->stats[18] = 2 * (f->n_boxes - 1);
+  return QBX_OK;
+}
+
+namespace {
+
+Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
+  Fmm F;
+  F.level = f->box.level.ptr;
+  F.child = f->box.child.ptr;
+  F.centre = f->box.centre.ptr;
+  F.rsrc = f->box.rng[PT_SRC].ptr;
+  F.rctr = f->box.rng[PT_CTR].ptr;
+  F.rtgt = f->box.rng[PT_TGT].ptr;
+  F.uoff = f->U.off.ptr; F.uidx = f->U.idx.ptr;
+  F.voff = f->V.off.ptr; F.vidx = f->V.idx.ptr; F.vcls = f->V_cls.ptr;
+  F.woff = f->W.off.ptr; F.widx = f->W.idx.ptr;
+  F.xoff = f->X.off.ptr; F.xidx = f->X.idx.ptr;
+  F.sxy = f->s_xy.ptr; F.snrm = f->s_nrm.ptr; F.qs = f->qs.ptr; F.ds = f->ds.ptr;
+  F.cxy = f->c_xy.ptr; F.cid = f->perm[PT_CTR].ptr;
+  F.txy = f->t_xy.ptr; F.tid = f->perm[PT_TGT].ptr; F.tassoc = f->t_assoc.ptr;
+  F.scale = f->scale.ptr; F.pw = f->pw.ptr; F.ipw = f->ipw.ptr;
+  F.t_m2l = f->t_m2l.ptr; F.t_m2m = f->t_m2m.ptr; F.t_l2l = f->t_l2l.ptr;
+  F.mpole = f->mpole.ptr; F.local = f->local.ptr;
+  F.k = h->k; F.pb = f->pb; F.Q = f->Q; F.p = h->p; F.n_levels = f->n_levels;
+  F.has_S = S ? 1 : 0; F.has_D = D ? 1 : 0;
+  return F;
+}
+
+template <int PM>
+void launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D, cd* alpha,
+                           cudaStream_t s) {
+  const size_t smQ = (size_t)F.Q * sizeof(cd);
+  stage_begin(h, QBX_STAGE_L2QBXL, s);
+  l2qbxl_kernel<PM><<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, alpha);
+  stage_end(h, QBX_STAGE_L2QBXL, s);
+  stage_begin(h, QBX_STAGE_M2QBXL, s);
+  m2qbxl_kernel<PM><<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, alpha);
+  stage_end(h, QBX_STAGE_M2QBXL, s);
+  stage_begin(h, QBX_STAGE_P2QBXL, s);
+  if (S && D) p2qbxl_ulist_kernel<PM, true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+  else if (S) p2qbxl_ulist_kernel<PM, true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+  else if (D) p2qbxl_ulist_kernel<PM, false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+  stage_end(h, QBX_STAGE_P2QBXL, s);
+  h->launches += (S || D) ? 3 : 2;
+}
+
+}  // namespace
+
+qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaStream_t s) {
+  (void)precision;
+  FmmPlan* f = h->fmm;
+  if (!f) { set_error("FMM plan missing"); return QBX_ERR_STATE; }
+  const int pb = f->pb, Q = f->Q, T = 4 * pb + 1;
+  if (h->n_src > 0) {
+    gather_strengths_kernel<<<nblk(h->n_src, 256), 256, 0, s>>>(
+        h->n_src, f->perm[PT_SRC].ptr, h->q_str.ptr, h->d_str.ptr, f->qs.ptr, f->ds.ptr);
+    h->launches += 1;
+  }
+  Fmm F = make_view(h, f, S, D);
+  QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_boxes * Q * sizeof(cd), s));
+  QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_boxes * Q * sizeof(cd), s));
+  // Stage 2: P2M, M2M
+  const size_t sm_p2m = (size_t)(kChunk * (pb + 2) + 3 * kChunk) * sizeof(cd);
+  stage_begin(h, QBX_STAGE_P2M, s);
+  if (f->n_src_leaves > 0 && (S || D)) {
+    p2m_kernel<<<f->n_src_leaves, kThreads, sm_p2m, s>>>(F, f->src_leaves.ptr);
+    h->launches += 1;
+  }
+  stage_end(h, QBX_STAGE_P2M, s);
+  const size_t sm_tr = (size_t)(Q + T) * sizeof(cd);
+  stage_begin(h, QBX_STAGE_M2M, s);
+  for (int l = f->n_levels - 2; l >= 0; --l) {
+    const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
+    if (nb == 0) continue;
+    m2m_kernel<<<nb, kThreads, sm_tr, s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+    h->launches += 1;
+  }
+  stage_end(h, QBX_STAGE_M2M, s);
+  // Stage 4: M2L
+  stage_begin(h, QBX_STAGE_M2L, s);
+  if (f->n_vbox > 0) {
+    m2l_kernel<<<f->n_vbox, kThreads, sm_tr + (pb + 1) * sizeof(double), s>>>(F, f->vbox.ptr);
+    h->launches += 1;
+  }
+  stage_end(h, QBX_STAGE_M2L, s);
+  // Stage 6: P2L
+  stage_begin(h, QBX_STAGE_P2L, s);
+  if (f->n_xbox > 0 && (S || D)) {
+    const size_t sm = (size_t)(2 * kChunk * (pb + 2) + 3 * kChunk) * sizeof(cd);
+    p2l_kernel<<<f->n_xbox, kThreads, sm, s>>>(F, f->xbox.ptr);
+    h->launches += 1;
+  }
+  stage_end(h, QBX_STAGE_P2L, s);
+  // Stage 7: L2L
+  stage_begin(h, QBX_STAGE_L2L, s);
+  for (int l = 1; l + 1 < f->n_levels; ++l) {
+    const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
+    if (nb == 0) continue;
+    l2l_kernel<<<nb, kThreads, sm_tr, s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+    h->launches += 1;
+  }
+  stage_end(h, QBX_STAGE_L2L, s);
+  // Stages 3, 5, 8 at targets
+  const size_t smQ = (size_t)Q * sizeof(cd);
+  if (f->n_leaves > 0 && h->n_direct_tgt > 0) {
+    stage_begin(h, QBX_STAGE_L2P, s);
+    l2p_kernel<<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, out);
+    stage_end(h, QBX_STAGE_L2P, s);
+    stage_begin(h, QBX_STAGE_M2P, s);
+    m2p_kernel<<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, out);
+    stage_end(h, QBX_STAGE_M2P, s);
+    stage_begin(h, QBX_STAGE_P2P, s);
+    if (S && D) p2p_ulist_kernel<true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, out);
+    else if (S) p2p_ulist_kernel<true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, out);
+    else if (D) p2p_ulist_kernel<false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, out);
+    stage_end(h, QBX_STAGE_P2P, s);
+    h->launches += (S || D) ? 3 : 2;
+  }
+  // Stages 3, 5, 8 at centres: the QBX coefficients
+  if (f->n_leaves > 0 && h->n_ctr > 0) {
+    if (h->p <= 4) launch_centre_kernels<4>(F, f, h, S, D, h->alpha.ptr, s);
+    else if (h->p <= 8) launch_centre_kernels<8>(F, f, h, S, D, h->alpha.ptr, s);
+    else if (h->p <= 12) launch_centre_kernels<12>(F, f, h, S, D, h->alpha.ptr, s);
+    else launch_centre_kernels<16>(F, f, h, S, D, h->alpha.ptr, s);
+  }
+  QBX_CUDA_TRY(cudaGetLastError());
+  return QBX_OK;
 }
 
 void fmm_plan_free(FmmPlan* f) { delete f; }

@@ -68,6 +68,7 @@ struct qbx_handle {
   int64_t n_panels = 0, n_nodes = 0, n_src = 0, n_ctr = 0;
   int q = 0, q_src = 0, p = 0, sides = 1;
   double k = 0;
+  double h_max = 0;                         // longest panel
   DevBuf<double> node_xy, node_nrm, panel_h;
   DevBuf<double> src_xy, src_nrm, src_w;
   DevBuf<double> ctr_xy, ctr_r;
@@ -105,7 +106,8 @@ qbx_status launch_associate_direct(qbx_handle* h, const int64_t* on_node, const 
                                    double eps, cudaStream_t s);
 qbx_status launch_place_centres(qbx_handle* h, cudaStream_t s);
 // fmm.cu
-qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d);
+qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* on_node_dev,
+                          const int8_t* on_side_dev, double eps);
 qbx_status fmm_eval(qbx_handle* h, bool has_S, bool has_D, cd* out, int precision,
                     cudaStream_t s);
 void fmm_plan_free(FmmPlan* f);

@@ -47,6 +47,9 @@ struct FmmPlan {
   // orders and scales
   int pb = 0, Q = 0;
   DevBuf<double> scale;                 // per level s_l = min(1, k * side_l)
+  DevBuf<double> pw, ipw;               // per level powers s^j, s^-j
+  DevBuf<int> src_leaves;               // leaves holding sources
+  int n_src_leaves = 0;
   DevBuf<cd> t_m2l;                     // [n_levels][49][4pb+1] scaled Hankel vectors
   DevBuf<cd> t_m2m;                     // [n_levels][4][4pb+1] conj(V_m(d)) child->parent
   DevBuf<cd> t_l2l;                     // [n_levels][4][4pb+1] (-1)^m V_m(d) parent->child
@@ -61,5 +64,6 @@ struct FmmPlan {
 
 qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max);
 qbx_status tree_lists(qbx_handle* h, FmmPlan* f);
+qbx_status gather_sorted(qbx_handle* h, FmmPlan* f);
 qbx_status tree_associate(qbx_handle* h, FmmPlan* f, const int64_t* on_node, const int8_t* on_side,
                           double eps);
