@@ -175,6 +175,47 @@ enum qbx_stage {
 qbx_status qbx_set_timing(qbx_handle *h, int32_t enable);
 int32_t qbx_get_stage_times(qbx_handle *h, double *times_ms, int32_t n_times);
 
+/*
+ * Allocation-free direct QBX evaluation. The paper has no counterpart: this is
+ * an interface addition for callers that must not allocate device memory, for
+ * example an application whose HBM is entirely handed out up front by its own
+ * pool allocator, or a time-critical loop that cannot afford the device-wide
+ * synchronisation that cudaMalloc/cudaFree may cause. It performs no
+ * allocation of any kind: the caller passes every input and output, and the
+ * intermediate strengths and QBX coefficients live in one fixed array of
+ * 2^19 complex doubles (8 MiB) that the library reserves on every GPU where it
+ * is loaded, held until the process exits.
+ *
+ * Computes, for every target t, the QBX evaluation of Eq. (phiapprox) with the
+ * coefficients of centre tgt_centre[t] taken over ALL sources (the direct
+ * all-pairs sum of Eq. (localexpcoeffs)) for u = cS S[sigma_S] + cD D[sigma_D]:
+ * the same arithmetic as qbx_layer_potential_eval in QBX_DIRECT mode at
+ * associated targets. No association is done here; an out-of-range centre
+ * index gives NaN at that target.
+ *  - All pointers are DEVICE memory on the current device (checked): src_xy
+ *    [n_src][2], src_normal_xy [n_src][2], src_weight [n_src], sigma_S /
+ *    sigma_D complex [n_src] (either may be NULL, not both), ctr_xy
+ *    [n_ctr][2], tgt_xy [n_tgt][2], tgt_centre int32 [n_tgt], out complex
+ *    [n_tgt].
+ *  - Limit: 2 * n_src + n_ctr * (2p + 1) <= 2^19; larger problems return
+ *    QBX_ERR_ARG with the required size in qbx_last_error(). 0 <= p <= 16.
+ *  - Asynchronous on cuda_stream (NULL: legacy default stream).
+ *  - The first call on a device looks up the device address of the scratch
+ *    array (cudaGetSymbolAddress) and caches it; make that first call before
+ *    any stream capture begins.
+ *  - Every call on a device shares the one scratch array and leaves its last
+ *    contents there; calls whose GPU work overlaps (different streams, no
+ *    ordering between them) race on it and must be serialised by the caller.
+ */
+qbx_status qbx_direct_qbx_eval_noalloc(int64_t n_src, const double *src_xy,
+                                       const double *src_normal_xy, const double *src_weight,
+                                       double k, double cS_re, double cS_im,
+                                       const double *sigma_S, double cD_re, double cD_im,
+                                       const double *sigma_D, int64_t n_ctr,
+                                       const double *ctr_xy, int32_t p, int64_t n_tgt,
+                                       const double *tgt_xy, const int32_t *tgt_centre,
+                                       double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

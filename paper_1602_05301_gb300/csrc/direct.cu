@@ -384,3 +384,175 @@ qbx_status launch_place_centres(qbx_handle* h, cudaStream_t s) {
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;
 }
+
+// ---------------------------------------------------------------- allocation-free entry point
+// qbx_direct_qbx_eval_noalloc: the direct QBX evaluation (strengths -> coefficients
+// at every centre from every source -> J-expansion at each target) for callers
+// that may not allocate device memory. Its scratch (strengths and coefficients)
+// is the file-scope array below, reserved once per device when the library's
+// module loads and shared by every call on that device.
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kNoAllocScratch = int64_t(1) << 19;  // complex doubles = 8 MiB per device
+static __device__ __align__(256) cd g_noalloc_scratch[kNoAllocScratch];
+
+constexpr int kNoAllocMaxDevices = 128;
+std::mutex g_noalloc_mu;
+cd* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// J-expansion of centre centre[t] at target t (Eq. (phiapprox)); an out-of-range
+// centre index yields NaN for that target.
+template <int PM>
+__global__ void __launch_bounds__(128) qbxl2p_each_kernel(int64_t n_tgt,
+                                                          const double* __restrict__ tgt_xy,
+                                                          const int32_t* __restrict__ centre,
+                                                          int64_t n_ctr,
+                                                          const double* __restrict__ ctr_xy,
+                                                          const cd* __restrict__ alpha, double k,
+                                                          int p, cd* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_tgt) return;
+  const int64_t c = centre[t];
+  if (c < 0 || c >= n_ctr) {
+    out[t] = mk(__longlong_as_double(0x7ff8000000000000LL), __longlong_as_double(0x7ff8000000000000LL));
+    return;
+  }
+  const double dx = tgt_xy[2 * t] - ctr_xy[2 * c];
+  const double dy = tgt_xy[2 * t + 1] - ctr_xy[2 * c + 1];
+  const double rho = sqrt(dx * dx + dy * dy);
+  const cd e1 = rho > 0.0 ? mk(dx / rho, dy / rho) : mk(1.0, 0.0);
+  double J[PM + 1];
+  bessel_j_array<PM>(k * rho, J);
+  const int P = 2 * p + 1;
+  const cd* a = alpha + c * P + p;
+  cd u = cscale(a[0], J[0]);
+  cd e = mk(1.0, 0.0);
+  double sgn = 1.0;
+#pragma unroll
+  for (int m = 1; m <= PM; ++m) {
+    if (m > p) break;
+    e = cmul(e, e1);
+    sgn = -sgn;
+    cfma(u, cscale(a[m], J[m]), cconj(e));
+    cfma(u, cscale(a[-m], sgn * J[m]), e);
+  }
+  out[t] = u;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <int PM>
+void noalloc_launch(int64_t n_src, const double* sxy, const double* snrm, const cd* q,
+                    const cd* d, bool S, bool D, double k, int64_t n_ctr, const double* cxy,
+                    int p, cd* alpha, int64_t n_tgt, const double* txy, const int32_t* tc,
+                    cd* out, cudaStream_t s) {
+  if (n_ctr > 0) {
+    dim3 g(nblk(n_ctr, kTile));
+    if (S && D)
+      p2qbxl_direct_kernel<PM, true, true><<<g, kTile, 0, s>>>(n_ctr, cxy, n_src, sxy, snrm, q,
+                                                               d, k, p, alpha);
+    else if (S)
+      p2qbxl_direct_kernel<PM, true, false><<<g, kTile, 0, s>>>(n_ctr, cxy, n_src, sxy, snrm, q,
+                                                                d, k, p, alpha);
+    else
+      p2qbxl_direct_kernel<PM, false, true><<<g, kTile, 0, s>>>(n_ctr, cxy, n_src, sxy, snrm, q,
+                                                                d, k, p, alpha);
+  }
+  if (n_tgt > 0)
+    qbxl2p_each_kernel<PM><<<nblk(n_tgt, 128), 128, 0, s>>>(n_tgt, txy, tc, n_ctr, cxy, alpha, k,
+                                                            p, out);
+}
+
+}  // namespace
+
+extern "C" qbx_status qbx_direct_qbx_eval_noalloc(
+    int64_t n_src, const double* src_xy, const double* src_normal_xy, const double* src_weight,
+    double k, double cS_re, double cS_im, const double* sigma_S, double cD_re, double cD_im,
+    const double* sigma_D, int64_t n_ctr, const double* ctr_xy, int32_t p, int64_t n_tgt,
+    const double* tgt_xy, const int32_t* tgt_centre, double* out, void* cuda_stream) {
+  set_error("%s", "");
+  if (n_src < 0 || n_ctr < 0 || n_tgt < 0 || p < 0 || p > QBX_MAX_P || !(k > 0.0)) {
+    set_error("qbx_direct_qbx_eval_noalloc: invalid size, order or wavenumber");
+    return QBX_ERR_ARG;
+  }
+  if (!sigma_S && !sigma_D) {
+    set_error("qbx_direct_qbx_eval_noalloc: at least one of sigma_S, sigma_D is required");
+    return QBX_ERR_ARG;
+  }
+  const int64_t P = 2 * (int64_t)p + 1;
+  const int64_t need = 2 * n_src + n_ctr * P;
+  if (need > kNoAllocScratch) {
+    set_error("qbx_direct_qbx_eval_noalloc: needs %lld complex scratch values "
+              "(2*n_src + n_ctr*(2p+1)) but the static scratch holds %lld",
+              (long long)need, (long long)kNoAllocScratch);
+    return QBX_ERR_ARG;
+  }
+  const void* dev_ptrs[] = {src_xy, src_normal_xy, src_weight, ctr_xy, tgt_xy, tgt_centre, out};
+  const int64_t sizes[] = {n_src, n_src, n_src, n_ctr, n_tgt, n_tgt, n_tgt};
+  for (int i = 0; i < 7; ++i)
+    if (sizes[i] > 0 && (!dev_ptrs[i] || !on_device(dev_ptrs[i]))) {
+      set_error("qbx_direct_qbx_eval_noalloc: argument %d must be device memory", i);
+      return QBX_ERR_ARG;
+    }
+  if ((sigma_S && !on_device(sigma_S)) || (sigma_D && !on_device(sigma_D))) {
+    set_error("qbx_direct_qbx_eval_noalloc: densities must be device memory");
+    return QBX_ERR_ARG;
+  }
+  int dev = 0;
+  QBX_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("qbx_direct_qbx_eval_noalloc: device ordinal %d not supported", dev);
+    return QBX_ERR_ARG;
+  }
+  cd* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) {
+        set_error("qbx_direct_qbx_eval_noalloc: cudaGetSymbolAddress failed: %s",
+                  cudaGetErrorString(e));
+        return QBX_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = (cd*)ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (n_src == 0 && n_tgt == 0) return QBX_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cd* q = scratch;
+  cd* d = scratch + n_src;
+  cd* alpha = scratch + 2 * n_src;
+  if (n_src > 0)
+    strengths_kernel<<<nblk(n_src, 256), 256, 0, s>>>(
+        n_src, src_weight, mk(cS_re, cS_im), (const cd*)sigma_S, mk(cD_re, cD_im),
+        (const cd*)sigma_D, q, d);
+  const bool S = sigma_S != nullptr, D = sigma_D != nullptr;
+  const cd* cq = q;
+  const cd* cdd = d;
+  cd* o = (cd*)out;
+  if (p <= 4)
+    noalloc_launch<4>(n_src, src_xy, src_normal_xy, cq, cdd, S, D, k, n_ctr, ctr_xy, p, alpha,
+                      n_tgt, tgt_xy, tgt_centre, o, s);
+  else if (p <= 8)
+    noalloc_launch<8>(n_src, src_xy, src_normal_xy, cq, cdd, S, D, k, n_ctr, ctr_xy, p, alpha,
+                      n_tgt, tgt_xy, tgt_centre, o, s);
+  else if (p <= 12)
+    noalloc_launch<12>(n_src, src_xy, src_normal_xy, cq, cdd, S, D, k, n_ctr, ctr_xy, p, alpha,
+                       n_tgt, tgt_xy, tgt_centre, o, s);
+  else
+    noalloc_launch<16>(n_src, src_xy, src_normal_xy, cq, cdd, S, D, k, n_ctr, ctr_xy, p, alpha,
+                       n_tgt, tgt_xy, tgt_centre, o, s);
+  QBX_CUDA_TRY(cudaGetLastError());
+  return QBX_OK;
+}
