@@ -326,7 +326,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--mode", default="direct", choices=["fmm", "direct"])
+    ap.add_argument("--mode", default="fmm", choices=["fmm", "direct"])
     ap.add_argument("--n-max", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -176,6 +176,28 @@ qbx_status qbx_set_timing(qbx_handle *h, int32_t enable);
 int32_t qbx_get_stage_times(qbx_handle *h, double *times_ms, int32_t n_times);
 
 /*
+ * Tree inspection after qbx_tree_build in QBX_FMM mode (the quadtree of Sec. 4
+ * and Sec. 7.2, Stage 1, and its U, V, W, X lists). All outputs are HOST
+ * memory; any pointer may be NULL (skipped).
+ *   info[8]: [0] n_boxes, [1] n_levels, [2..5] entries of the U, V, W, X
+ *            lists, [6] p_box, [7] n_leaves.
+ *   root[3]: x0, y0, side of the root square [x0, x0+side] x [y0, y0+side].
+ *   box_level [n_boxes]; box_ij [n_boxes][2] integer position at the box's
+ *   level; box_child [n_boxes][4] (-1: none; quadrant q = ix&1 + 2(iy&1));
+ *   box_range [n_boxes][4][2]: [start, end) of the box's sources, centres,
+ *   targets and density nodes in the sorted orders perm_src [n_src],
+ *   perm_ctr [n_centres], perm_tgt [n_targets] (original indices).
+ *   lists_off [4][n_boxes + 1] and lists_idx [info[2]+...+info[5]]: CSR of
+ *   the U, V, W, X lists, concatenated in that order (offsets are local to
+ *   each list).
+ * Errors: QBX_ERR_STATE if no FMM plan exists.
+ */
+qbx_status qbx_export_tree(const qbx_handle *h, int64_t *info, double *root, int32_t *box_level,
+                           int32_t *box_ij, int32_t *box_child, int32_t *box_range,
+                           int32_t *lists_off, int32_t *lists_idx, int32_t *perm_src,
+                           int32_t *perm_ctr, int32_t *perm_tgt);
+
+/*
  * Allocation-free direct QBX evaluation. The paper has no counterpart: this is
  * an interface addition for callers that must not allocate device memory, for
  * example an application whose HBM is entirely handed out up front by its own

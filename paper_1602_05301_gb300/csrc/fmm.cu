@@ -33,6 +33,12 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kChunk = 16;  // sources per shared-memory chunk in P2M / P2L
 constexpr double kRescale = 1e100;
+// Leaves holding a centre are at least this many expansion radii wide.
+constexpr double kLeafOverRadius = 4.0;
+// A W-list box c is translated to a centre z (M2QBXL) only if
+// (R_c + r_z) <= kW * |z - m_c| (R_c: half-diagonal of c, r_z: disk radius);
+// otherwise its sources are summed directly into the coefficients.
+constexpr double kW = 0.6;
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
 
@@ -52,6 +58,7 @@ struct Fmm {
   const cd* qs;
   const cd* ds;
   const double2* cxy;
+  const double* crad;    // sorted centre radii
   const int* cid;
   const double2* txy;
   const int* tid;
@@ -65,7 +72,7 @@ struct Fmm {
   const cd* t_l2l;       // [n_levels][4][4pb+1]
   cd* mpole;
   cd* local;
-  double k;
+  double k, side;
   int pb, Q, p, n_levels, has_S, has_D;
 };
 
@@ -704,18 +711,70 @@ __global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __re
   }
 }
 
-// M2QBXL: alpha_l += (-1)^l sum_n mh_n Wh_{n+l} s^{|n| - |n+l|},  Wh_m = s^|m| W_m(z - m_c)
-template <int PM>
+// M2QBXL: alpha_l += (-1)^l sum_n mh_n Wh_{n+l} s^{|n| - |n+l|},  Wh_m = s^|m| W_m(z - m_c).
+// A W box too close to the centre's disk for its multipole series to converge
+// on the whole disk ((R_c + r_z) > kW |z - m_c|) is summed source by source.
+template <int PM, bool HS, bool HD>
+__global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
+                                                          cd* __restrict__ alpha);
+
+// One source's contribution to the QBX coefficients of a centre (P2QBXL):
+// alpha_l += q W_l + d (k/2) (nu W_{l-1} - conj(nu) W_{l+1}),  W_l = H_l(k r) e^{i l th},
+// (r, th) the polar coordinates of source - centre; upward Hankel recurrence.
+template <int PM, bool HS, bool HD>
+__device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, double dy, cd q,
+                                            cd dsrc, cd nu, double k, int p) {
+  const double rr = sqrt(dx * dx + dy * dy);
+  if (rr == 0.0) return;
+  const double ir = 1.0 / rr, x = k * rr, ix2 = 2.0 / x;
+  const cd e1 = mk(dx * ir, dy * ir);
+  cd h0, h1;
+  hankel01(x, h0, h1);
+  const cd dk = cscale(dsrc, 0.5 * k);
+  const cd nub = cconj(nu);
+  const cd w1 = cmul(h1, e1);
+  const cd wm1 = cscale(cmul(h1, cconj(e1)), -1.0);
+  if (HS) cfma(acc[PM], q, h0);
+  if (HD) cfma(acc[PM], dk, csub(cmul(nu, wm1), cmul(nub, w1)));
+  cd hprev = h0, hcur = h1, eprev = mk(1.0, 0.0), ecur = e1;
+  double sgn = -1.0;
+#pragma unroll
+  for (int m = 1; m <= PM; ++m) {
+    if (m > p) break;
+    const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
+    const cd enext = cmul(ecur, e1);
+    if (HS) {
+      cfma(acc[PM + m], q, cmul(hcur, ecur));
+      cfma(acc[PM - m], q, cscale(cmul(hcur, cconj(ecur)), sgn));
+    }
+    if (HD) {
+      const cd w_p = cmul(hnext, enext), w_pm = cmul(hprev, eprev);
+      const cd v_p = cscale(cmul(hnext, cconj(enext)), -sgn);
+      const cd v_pm = cscale(cmul(hprev, cconj(eprev)), -sgn);
+      cfma(acc[PM + m], dk, csub(cmul(nu, w_pm), cmul(nub, w_p)));
+      cfma(acc[PM - m], dk, csub(cmul(nu, v_p), cmul(nub, v_pm)));
+    }
+    hprev = hcur;
+    hcur = hnext;
+    eprev = ecur;
+    ecur = enext;
+    sgn = -sgn;
+  }
+}
+
+template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
                                                           cd* __restrict__ alpha) {
   extern __shared__ cd smem[];
   const int pb = F.pb, Q = F.Q, p = F.p, P = 2 * p + 1;
-  cd* a = smem;
+  cd* a = smem;                          // [Q]
+  double* fpw = (double*)(a + Q);        // [2p+1]: s^j, j = -p..p
   const int b = leaves[blockIdx.x];
   const int2 r = F.rctr[b];
   const int e0 = F.woff[b], e1_ = F.woff[b + 1];
   if (r.y <= r.x || e1_ <= e0) return;
   const int M = pb + p;
+  const double k = F.k;
   for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
     const int i = i0 + threadIdx.x;
     const bool act = i < r.y;
@@ -724,15 +783,32 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __re
     for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
     for (int e = e0; e < e1_; ++e) {
       const int c = F.widx[e];
+      const int lc = F.level[c];
+      const double s = F.scale[lc];
       __syncthreads();
       for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = F.mpole[(size_t)c * Q + j];
+      for (int j = threadIdx.x; j <= 2 * p; j += kThreads) {
+        double f = 1.0;
+        const int ex = j - p;
+        for (int t = 0; t < abs(ex); ++t) f *= (ex > 0 ? s : 1.0 / s);
+        fpw[j] = f;
+      }
       __syncthreads();
       if (!act) continue;
-      const double s = F.scale[F.level[c]];
-      const double is = 1.0 / s;
+      const double2 z = F.cxy[i];
       const double2 mc = F.centre[c];
-      const double dx = F.cxy[i].x - mc.x, dy = F.cxy[i].y - mc.y;
-      const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+      const double dx = z.x - mc.x, dy = z.y - mc.y;
+      const double rr = sqrt(dx * dx + dy * dy);
+      const double Rc = 0.70710678118654752 * F.side / (double)(1 << lc);
+      if (Rc + F.crad[i] > kW * rr) {
+        const int2 sr = F.rsrc[c];
+        for (int j = sr.x; j < sr.y; ++j)
+          p2qbxl_pair<PM, HS, HD>(acc, F.sxy[j].x - z.x, F.sxy[j].y - z.y,
+                                  HS ? F.qs[j] : mk(0.0, 0.0), HD ? F.ds[j] : mk(0.0, 0.0),
+                                  HD ? mk(F.snrm[j].x, F.snrm[j].y) : mk(0.0, 0.0), k, p);
+        continue;
+      }
+      const double x = k * rr;
       const cd e1 = mk(dx / rr, dy / rr);
       cd h0, h1;
       hankel01(x, h0, h1);
@@ -740,28 +816,19 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __re
       for (int mm = 0; mm <= M; ++mm) {
         if (mm == 1) { hm1 = h0; hm = cscale(h1, s); }
         if (mm >= 1) ee = cmul(ee, e1);
-        const cd wp = cmul(hm, ee);                                   // Wh_m
+        const cd wp = cmul(hm, ee);                                        // Wh_m
         const cd wq = cscale(cmul(hm, cconj(ee)), (mm & 1) ? -1.0 : 1.0);  // Wh_{-m}
 #pragma unroll
         for (int lo = -PM; lo <= PM; ++lo) {
           if (lo < -p || lo > p) continue;
           const double sg = (lo & 1) ? -1.0 : 1.0;
           const int n1 = mm - lo;  // n + l = m
-          if (n1 >= -pb && n1 <= pb) {
-            // s^{|n| - |m|}
-            int ex = abs(n1) - mm;
-            double f = 1.0;
-            for (int q = 0; q < abs(ex); ++q) f *= (ex > 0 ? s : is);
-            cfma(acc[lo + PM], cscale(a[n1 + pb], sg * f), wp);
-          }
+          if (n1 >= -pb && n1 <= pb)
+            cfma(acc[lo + PM], cscale(a[n1 + pb], sg * fpw[abs(n1) - mm + p]), wp);
           if (mm > 0) {
             const int n2 = -mm - lo;  // n + l = -m
-            if (n2 >= -pb && n2 <= pb) {
-              int ex = abs(n2) - mm;
-              double f = 1.0;
-              for (int q = 0; q < abs(ex); ++q) f *= (ex > 0 ? s : is);
-              cfma(acc[lo + PM], cscale(a[n2 + pb], sg * f), wq);
-            }
+            if (n2 >= -pb && n2 <= pb)
+              cfma(acc[lo + PM], cscale(a[n2 + pb], sg * fpw[abs(n2) - mm + p]), wq);
           }
         }
         if (mm >= 1) {
@@ -790,7 +857,7 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
   const int b = leaves[blockIdx.x];
   const int2 r = F.rctr[b];
   if (r.y <= r.x) return;
-  const double k = F.k, hk = 0.5 * k;
+  const double k = F.k;
   const int p = F.p, P = 2 * p + 1;
   for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
     const int i = i0 + threadIdx.x;
@@ -815,50 +882,10 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
         __syncthreads();
         const int cnt = min(kThreads, sr.y - base);
         if (!act) continue;
-        for (int jj = 0; jj < cnt; ++jj) {
-          const double dx = s_xy[jj].x - cx, dy = s_xy[jj].y - cy;
-          const double rr = sqrt(dx * dx + dy * dy);
-          if (rr == 0.0) continue;
-          const double ir = 1.0 / rr, x = k * rr, ix2 = 2.0 / x;
-          const cd e1 = mk(dx * ir, dy * ir);
-          cd h0, h1;
-          hankel01(x, h0, h1);
-          const cd q = HS ? s_q[jj] : mk(0.0, 0.0);
-          const cd dk = HD ? cscale(s_d[jj], hk) : mk(0.0, 0.0);
-          const cd nu = HD ? mk(s_nu[jj].x, s_nu[jj].y) : mk(0.0, 0.0);
-          const cd nub = cconj(nu);
-          const cd w1 = cmul(h1, e1);
-          const cd wm1 = cscale(cmul(h1, cconj(e1)), -1.0);
-          if (HS) cfma(acc[PM], q, h0);
-          if (HD) cfma(acc[PM], dk, csub(cmul(nu, wm1), cmul(nub, w1)));
-          cd hprev = h0, hcur = h1, eprev = mk(1.0, 0.0), ecur = e1;
-          double sgn = -1.0;
-#pragma unroll
-          for (int m = 1; m <= PM; ++m) {
-            if (m > p) break;
-            const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
-            const cd enext = cmul(ecur, e1);
-            const cd w_m = cmul(hcur, ecur);
-            const cd w_p = cmul(hnext, enext);
-            const cd w_pm = cmul(hprev, eprev);
-            const cd v_m = cscale(cmul(hcur, cconj(ecur)), sgn);
-            const cd v_p = cscale(cmul(hnext, cconj(enext)), -sgn);
-            const cd v_pm = cscale(cmul(hprev, cconj(eprev)), -sgn);
-            if (HS) {
-              cfma(acc[PM + m], q, w_m);
-              cfma(acc[PM - m], q, v_m);
-            }
-            if (HD) {
-              cfma(acc[PM + m], dk, csub(cmul(nu, w_pm), cmul(nub, w_p)));
-              cfma(acc[PM - m], dk, csub(cmul(nu, v_p), cmul(nub, v_pm)));
-            }
-            hprev = hcur;
-            hcur = hnext;
-            eprev = ecur;
-            ecur = enext;
-            sgn = -sgn;
-          }
-        }
+        for (int jj = 0; jj < cnt; ++jj)
+          p2qbxl_pair<PM, HS, HD>(acc, s_xy[jj].x - cx, s_xy[jj].y - cy,
+                                  HS ? s_q[jj] : mk(0.0, 0.0), HD ? s_d[jj] : mk(0.0, 0.0),
+                                  HD ? mk(s_nu[jj].x, s_nu[jj].y) : mk(0.0, 0.0), k, p);
       }
     }
     if (act) {
@@ -890,7 +917,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   FmmPlan* f = new FmmPlan();
   h->fmm = f;
   const int n_max = d->n_max > 0 ? d->n_max : 64;
-  TRY(tree_build(h, f, n_max));
+  TRY(tree_build(h, f, n_max, kLeafOverRadius));
   TRY(tree_lists(h, f));
   TRY(tree_associate(h, f, on_node_dev, on_side_dev, eps));
   TRY(gather_sorted(h, f));
@@ -1003,12 +1030,12 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   F.woff = f->W.off.ptr; F.widx = f->W.idx.ptr;
   F.xoff = f->X.off.ptr; F.xidx = f->X.idx.ptr;
   F.sxy = f->s_xy.ptr; F.snrm = f->s_nrm.ptr; F.qs = f->qs.ptr; F.ds = f->ds.ptr;
-  F.cxy = f->c_xy.ptr; F.cid = f->perm[PT_CTR].ptr;
+  F.cxy = f->c_xy.ptr; F.crad = f->c_r.ptr; F.cid = f->perm[PT_CTR].ptr;
   F.txy = f->t_xy.ptr; F.tid = f->perm[PT_TGT].ptr; F.tassoc = f->t_assoc.ptr;
   F.scale = f->scale.ptr; F.pw = f->pw.ptr; F.ipw = f->ipw.ptr;
   F.t_m2l = f->t_m2l.ptr; F.t_m2m = f->t_m2m.ptr; F.t_l2l = f->t_l2l.ptr;
   F.mpole = f->mpole.ptr; F.local = f->local.ptr;
-  F.k = h->k; F.pb = f->pb; F.Q = f->Q; F.p = h->p; F.n_levels = f->n_levels;
+  F.k = h->k; F.side = f->side; F.pb = f->pb; F.Q = f->Q; F.p = h->p; F.n_levels = f->n_levels;
   F.has_S = S ? 1 : 0; F.has_D = D ? 1 : 0;
   return F;
 }
@@ -1021,7 +1048,10 @@ void launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool
   l2qbxl_kernel<PM><<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, alpha);
   stage_end(h, QBX_STAGE_L2QBXL, s);
   stage_begin(h, QBX_STAGE_M2QBXL, s);
-  m2qbxl_kernel<PM><<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, alpha);
+  const size_t smW = smQ + (size_t)(PM + 1) * sizeof(cd);
+  if (S && D) m2qbxl_kernel<PM, true, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
+  else if (S) m2qbxl_kernel<PM, true, false><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
+  else if (D) m2qbxl_kernel<PM, false, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
   stage_end(h, QBX_STAGE_M2QBXL, s);
   stage_begin(h, QBX_STAGE_P2QBXL, s);
   if (S && D) p2qbxl_ulist_kernel<PM, true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
@@ -1115,3 +1145,49 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
 }
 
 void fmm_plan_free(FmmPlan* f) { delete f; }
+
+extern "C" qbx_status qbx_export_tree(const qbx_handle* h, int64_t* info, double* root,
+                                      int32_t* box_level, int32_t* box_ij, int32_t* box_child,
+                                      int32_t* box_range, int32_t* lists_off,
+                                      int32_t* lists_idx, int32_t* perm_src, int32_t* perm_ctr,
+                                      int32_t* perm_tgt) {
+  if (!h) { set_error("qbx_export_tree: NULL handle"); return QBX_ERR_ARG; }
+  const FmmPlan* f = h->fmm;
+  if (!f || !h->planned || h->mode != QBX_FMM) {
+    set_error("qbx_export_tree: no FMM plan (call qbx_tree_build with QBX_FMM)");
+    return QBX_ERR_STATE;
+  }
+  const int nb = f->n_boxes;
+  if (info) {
+    info[0] = nb; info[1] = f->n_levels; info[2] = f->U.nnz; info[3] = f->V.nnz;
+    info[4] = f->W.nnz; info[5] = f->X.nnz; info[6] = f->pb; info[7] = f->n_leaves;
+  }
+  if (root) { root[0] = f->x0; root[1] = f->y0; root[2] = f->side; }
+  if (box_level) QBX_CUDA_TRY(cudaMemcpy(box_level, f->box.level.ptr, nb * 4, cudaMemcpyDeviceToHost));
+  if (box_ij) QBX_CUDA_TRY(cudaMemcpy(box_ij, f->box.ij.ptr, nb * 8, cudaMemcpyDeviceToHost));
+  if (box_child) QBX_CUDA_TRY(cudaMemcpy(box_child, f->box.child.ptr, (size_t)nb * 16, cudaMemcpyDeviceToHost));
+  if (box_range) {
+    std::vector<int2> r(nb);
+    for (int t = 0; t < PT_COUNT; ++t) {
+      QBX_CUDA_TRY(cudaMemcpy(r.data(), f->box.rng[t].ptr, (size_t)nb * 8, cudaMemcpyDeviceToHost));
+      for (int b = 0; b < nb; ++b) {
+        box_range[(size_t)b * 8 + 2 * t] = r[b].x;
+        box_range[(size_t)b * 8 + 2 * t + 1] = r[b].y;
+      }
+    }
+  }
+  const Csr* L[4] = {&f->U, &f->V, &f->W, &f->X};
+  size_t pos = 0;
+  for (int i = 0; i < 4; ++i) {
+    if (lists_off)
+      QBX_CUDA_TRY(cudaMemcpy(lists_off + (size_t)i * (nb + 1), L[i]->off.ptr, (nb + 1) * 4,
+                              cudaMemcpyDeviceToHost));
+    if (lists_idx && L[i]->nnz)
+      QBX_CUDA_TRY(cudaMemcpy(lists_idx + pos, L[i]->idx.ptr, L[i]->nnz * 4, cudaMemcpyDeviceToHost));
+    pos += L[i]->nnz;
+  }
+  if (perm_src && h->n_src) QBX_CUDA_TRY(cudaMemcpy(perm_src, f->perm[PT_SRC].ptr, h->n_src * 4, cudaMemcpyDeviceToHost));
+  if (perm_ctr && h->n_ctr) QBX_CUDA_TRY(cudaMemcpy(perm_ctr, f->perm[PT_CTR].ptr, h->n_ctr * 4, cudaMemcpyDeviceToHost));
+  if (perm_tgt && h->n_tgt) QBX_CUDA_TRY(cudaMemcpy(perm_tgt, f->perm[PT_TGT].ptr, h->n_tgt * 4, cudaMemcpyDeviceToHost));
+  return QBX_OK;
+}

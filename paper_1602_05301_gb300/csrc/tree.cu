@@ -110,17 +110,25 @@ __device__ __forceinline__ int2 child_range(const KeySet& ks, int t, int2 r, u64
   return make_int2(a, b);
 }
 
+// A box is split when it holds more than n_max sources + centres + targets,
+// unless its children would be narrower than kappa times the expansion radius
+// of a centre it holds: every QBX disk then stays well inside the region where
+// the local expansion of its leaf converges.
 __global__ void split_count_kernel(int nb, int off, int level, int n_max, KeySet ks,
                                    const u64* __restrict__ bkey, const int2* __restrict__ r0,
                                    const int2* __restrict__ r1, const int2* __restrict__ r2,
-                                   const int2* __restrict__ r3, int* __restrict__ nchild) {
+                                   const int2* __restrict__ r3, const double* __restrict__ crad,
+                                   double child_side, double kappa,
+                                   int* __restrict__ nchild) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   int b = off + i;
   const int2 r[PT_COUNT] = {r0[b], r1[b], r2[b], r3[b]};
   int total = (r[0].y - r[0].x) + (r[1].y - r[1].x) + (r[2].y - r[2].x);
+  bool wide = true;
+  for (int j = r[PT_CTR].x; j < r[PT_CTR].y && wide; ++j) wide = kappa * crad[j] <= child_side;
   int cnt = 0;
-  if (total > n_max && level < kMaxLevels) {
+  if (total > n_max && level < kMaxLevels && wide) {
     for (int c = 0; c < 4; ++c) {
       bool ne = false;
       for (int t = 0; t < PT_COUNT && !ne; ++t) {
@@ -502,7 +510,7 @@ qbx_status counts_to_offsets(const int* cnt, DevBuf<int>& off, int n, int64_t* t
     if (s_ != QBX_OK) return s_;        \
   } while (0)
 
-qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max) {
+qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max, double kappa) {
   const double* xy[PT_COUNT] = {h->src_xy.ptr, h->ctr_xy.ptr, h->tgt_xy.ptr, h->node_xy.ptr};
   const int64_t n[PT_COUNT] = {h->n_src, h->n_ctr, h->n_tgt, h->n_nodes};
   for (int t = 0; t < PT_COUNT; ++t) f->count[t] = n[t];
@@ -545,6 +553,14 @@ qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max) {
     QBX_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp.ptr, bytes, k0.ptr, f->keys[t].ptr, v0.ptr,
                                                  f->perm[t].ptr, (int)m, 0, 2 * kMortonBits));
   }
+  // centre radii in Morton order (for the split rule)
+  DevBuf<double> crad_sorted;
+  QBX_CUDA_TRY(crad_sorted.alloc(std::max<int64_t>(1, n[PT_CTR])));
+  if (n[PT_CTR] > 0) {
+    gather_kernel<double><<<nblk(n[PT_CTR], 256), 256>>>(n[PT_CTR], f->perm[PT_CTR].ptr,
+                                                         h->ctr_r.ptr, crad_sorted.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+  }
   // levels
   size_t cap = 1024;
   BoxArrays& B = f->box;
@@ -582,7 +598,8 @@ qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max) {
     QBX_CUDA_TRY(choff.alloc(nb));
     split_count_kernel<<<nblk(nb, 128), 128>>>(nb, off, level, n_max, ks, B.key.ptr,
                                                B.rng[0].ptr, B.rng[1].ptr, B.rng[2].ptr,
-                                               B.rng[3].ptr, nch.ptr);
+                                               B.rng[3].ptr, crad_sorted.ptr,
+                                               side / (double)(1 << (level + 1)), kappa, nch.ptr);
     QBX_CUDA_TRY(cudaGetLastError());
     TRY(scan(nch.ptr, choff.ptr, nb));
     int last_off = 0, last_cnt = 0;
@@ -746,6 +763,12 @@ qbx_status gather_sorted(qbx_handle* h, FmmPlan* f) {
   TRY(g2(f->s_nrm, h->src_nrm.ptr, f->perm[PT_SRC], h->n_src));
   TRY(g2(f->c_xy, h->ctr_xy.ptr, f->perm[PT_CTR], h->n_ctr));
   TRY(g2(f->t_xy, h->tgt_xy.ptr, f->perm[PT_TGT], h->n_tgt));
+  QBX_CUDA_TRY(f->c_r.alloc(std::max<int64_t>(1, h->n_ctr)));
+  if (h->n_ctr) {
+    gather_kernel<double><<<nblk(h->n_ctr, 256), 256>>>(h->n_ctr, f->perm[PT_CTR].ptr,
+                                                        h->ctr_r.ptr, f->c_r.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+  }
   QBX_CUDA_TRY(f->t_assoc.alloc(std::max<int64_t>(1, h->n_tgt)));
   if (h->n_tgt) {
     gather_kernel<int><<<nblk(h->n_tgt, 256), 256>>>(h->n_tgt, f->perm[PT_TGT].ptr,

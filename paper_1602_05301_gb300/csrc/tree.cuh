@@ -55,6 +55,7 @@ struct FmmPlan {
   DevBuf<cd> t_l2l;                     // [n_levels][4][4pb+1] (-1)^m V_m(d) parent->child
   // sorted particle data used by the eval kernels
   DevBuf<double2> s_xy, s_nrm, c_xy, t_xy;
+  DevBuf<double> c_r;                   // sorted centre radii
   DevBuf<int> t_assoc;                  // association of sorted targets (centre id or -1)
   // expansions
   DevBuf<cd> mpole, local;              // [n_boxes][Q]
@@ -62,7 +63,7 @@ struct FmmPlan {
   DevBuf<int> err;                      // device error flags
 };
 
-qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max);
+qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max, double kappa);
 qbx_status tree_lists(qbx_handle* h, FmmPlan* f);
 qbx_status gather_sorted(qbx_handle* h, FmmPlan* f);
 qbx_status tree_associate(qbx_handle* h, FmmPlan* f, const int64_t* on_node, const int8_t* on_side,

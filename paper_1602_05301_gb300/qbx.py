@@ -85,6 +85,8 @@ def library() -> ctypes.CDLL:
             lib.qbx_get_stage_times.restype = ctypes.c_int32
             lib.qbx_get_stage_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.c_int32]
+            lib.qbx_export_tree.restype = ctypes.c_int
+            lib.qbx_export_tree.argtypes = [_vp] + [_vp] * 11
             _lib = lib
     return _lib
 
@@ -142,6 +144,36 @@ def qbx_get_stage_times(handle):
     t = (ctypes.c_double * len(STAGES))()
     n = library().qbx_get_stage_times(handle, t, len(STAGES))
     return {STAGES[i]: t[i] for i in range(n)}
+
+
+def qbx_export_tree(handle, n_src, n_ctr, n_tgt):
+    """Copies the FMM tree and lists to numpy arrays (see include/qbx.h)."""
+    lib = library()
+    info = np.zeros(8, np.int64)
+    root = np.zeros(3)
+    _check(lib.qbx_export_tree(handle, ptr(info), ptr(root), None, None, None, None, None, None,
+                               None, None, None))
+    nb = int(info[0])
+    out = dict(info=info, root=root, level=np.zeros(nb, np.int32),
+               ij=np.zeros((nb, 2), np.int32), child=np.zeros((nb, 4), np.int32),
+               range=np.zeros((nb, 4, 2), np.int32), off=np.zeros((4, nb + 1), np.int32),
+               idx=np.zeros(max(1, int(info[2:6].sum())), np.int32),
+               perm_src=np.zeros(max(1, n_src), np.int32),
+               perm_ctr=np.zeros(max(1, n_ctr), np.int32),
+               perm_tgt=np.zeros(max(1, n_tgt), np.int32))
+    _check(lib.qbx_export_tree(handle, ptr(info), ptr(root), ptr(out["level"]), ptr(out["ij"]),
+                               ptr(out["child"]), ptr(out["range"]), ptr(out["off"]),
+                               ptr(out["idx"]), ptr(out["perm_src"]), ptr(out["perm_ctr"]),
+                               ptr(out["perm_tgt"])))
+    lists = {}
+    pos = 0
+    for i, name in enumerate("UVWX"):
+        n = int(info[2 + i])
+        seg = out["idx"][pos:pos + n]
+        lists[name] = [seg[out["off"][i][b]:out["off"][i][b + 1]] for b in range(nb)]
+        pos += n
+    out["lists"] = lists
+    return out
 
 
 def qbx_last_error() -> str:
@@ -225,6 +257,9 @@ class LayerPotential:
                  "p2qbxl_pairs", "p2p_pairs", "m2qbxl_pairs", "m2p_pairs", "launches",
                  "p2l_pairs", "m2m_l2l", "reserved"]
         return dict(zip(names, qbx_get_stats(self.handle)))
+
+    def export_tree(self):
+        return qbx_export_tree(self.handle, self.n_src, self.n_centres, self.n_targets)
 
     def set_timing(self, on=True):
         qbx_set_timing(self.handle, on)
