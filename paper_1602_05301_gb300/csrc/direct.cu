@@ -158,11 +158,15 @@ __global__ void __launch_bounds__(kTile) p2p_direct_kernel(
         const double r = sqrt(dx * dx + dy * dy);
         if (r == 0.0) continue;
         const double x = k * r;
-        if (HS) cfma(acc, s_q[jj], mk(j0(x), y0(x)));
-        if (HD) {
-          const double f = k * (s_n[jj].x * dx + s_n[jj].y * dy) / r;
-          cfma(acc, s_d[jj], mk(f * j1(x), f * y1(x)));
+        cd h0, h1;
+        if (x < 2.0) {
+          hankel01_series(x, h0, h1);
+        } else {
+          if (HS) h0 = mk(j0(x), y0(x));
+          if (HD) h1 = mk(j1(x), y1(x));
         }
+        if (HS) cfma(acc, s_q[jj], h0);
+        if (HD) cfma(acc, s_d[jj], cscale(h1, k * (s_n[jj].x * dx + s_n[jj].y * dy) / r));
       }
     }
     __syncthreads();

@@ -320,48 +320,77 @@ __global__ void __launch_bounds__(kThreads) m2m_kernel(Fmm F, const int* __restr
 // ---------------------------------------------------------------- M2L (Stage 4)
 // lh_l += (-1)^l sum_n What_{n+l} mh_n c(l,n), What_m = s^|m| W_m(m_b - m_c),
 // c(l,n) = s^{2 min(|l|,|n|)} when l and n have opposite signs, else 1.
+// sum_{n=n0}^{n1-1} w[n] a[n] with four independent accumulators, so that the
+// dependent FP64 multiply-add chains of one thread overlap.
+__device__ __forceinline__ cd cdot(const cd* w, const cd* a, int n0, int n1) {
+  cd s0 = mk(0.0, 0.0), s1 = s0, s2 = s0, s3 = s0;
+  int n = n0;
+  for (; n + 3 < n1; n += 4) {
+    cfma(s0, w[n], a[n]);
+    cfma(s1, w[n + 1], a[n + 1]);
+    cfma(s2, w[n + 2], a[n + 2]);
+    cfma(s3, w[n + 3], a[n + 3]);
+  }
+  for (; n < n1; ++n) cfma(s0, w[n], a[n]);
+  return cadd(cadd(s0, s1), cadd(s2, s3));
+}
+
 __global__ void __launch_bounds__(kThreads) m2l_kernel(Fmm F, const int* __restrict__ boxes) {
   extern __shared__ cd smem[];
   const int pb = F.pb, Q = F.Q, T = 4 * pb + 1;
-  cd* a = smem;                       // [Q]
-  cd* w = a + Q;                      // [T]
+  cd* a = smem;                       // [Q]   mh_n
+  cd* a2 = a + Q;                     // [Q]   mh_n s^{2|n|}
+  cd* w = a2 + Q;                     // [T]   What_m
   double* p2 = (double*)(w + T);      // [pb+1] s^{2j}
   const int b = boxes[blockIdx.x];
   const int l = F.level[b];
   const double* pwl = pw_row(F, l);
   for (int j = threadIdx.x; j <= pb; j += kThreads) p2[j] = pwl[2 * j];
-  cd acc[2];
-  acc[0] = acc[1] = mk(0.0, 0.0);
+  const int lo = (int)threadIdx.x - pb;  // output order of this thread (Q <= kThreads + ...)
+  cd acc = mk(0.0, 0.0), acc2 = mk(0.0, 0.0);
+  const int lo2 = lo + kThreads;         // second output when Q > kThreads
+  __syncthreads();
   for (int e = F.voff[b]; e < F.voff[b + 1]; ++e) {
     const int c = F.vidx[e];
     const cd* tab = F.t_m2l + ((size_t)l * 49 + F.vcls[e]) * T;
-    for (int i = threadIdx.x; i < Q; i += kThreads) a[i] = F.mpole[(size_t)c * Q + i];
+    for (int i = threadIdx.x; i < Q; i += kThreads) {
+      const cd v = F.mpole[(size_t)c * Q + i];
+      a[i] = v;
+      a2[i] = cscale(v, p2[abs(i - pb)]);
+    }
     for (int i = threadIdx.x; i < T; i += kThreads) w[i] = tab[i];
     __syncthreads();
+    // Split of the n range by the sign of n relative to lo: same sign -> factor 1;
+    // opposite sign with |n| <= |lo| -> s^{2|n|} (folded into a2); |n| > |lo| -> s^{2|lo|}.
     for (int o = 0; o < 2; ++o) {
-      const int lo = (int)threadIdx.x + o * kThreads - pb;
-      if (lo > pb) continue;
-      cd same = mk(0.0, 0.0), opp = mk(0.0, 0.0);
-      for (int n = -pb; n <= pb; ++n) {
-        const cd term = cmul(w[n + lo + 2 * pb], a[n + pb]);
-        if ((lo < 0 && n > 0) || (lo > 0 && n < 0)) {
-          const int mn = min(abs(lo), abs(n));
-          opp = cadd(opp, cscale(term, p2[mn]));
-        } else {
-          same = cadd(same, term);
-        }
+      const int L = o == 0 ? lo : lo2;
+      if (L > pb) continue;
+      const cd* wl = w + L + 2 * pb;   // wl[n] = What_{n+L}
+      const cd* ac = a + pb;   // ac[n] = mh_n
+      const cd* ac2 = a2 + pb;
+      cd same, near, far;
+      if (L >= 0) {
+        same = cdot(wl, ac, 0, pb + 1);
+        near = cdot(wl, ac2, -L, 0);
+        far = cdot(wl, ac, -pb, -L);
+      } else {
+        same = cdot(wl, ac, -pb, 1);
+        near = cdot(wl, ac2, 1, -L + 1);
+        far = cdot(wl, ac, -L + 1, pb + 1);
       }
-      const cd sum = cadd(same, opp);
-      acc[o] = (lo & 1) ? csub(acc[o], sum) : cadd(acc[o], sum);
+      cd sum = cadd(cadd(same, near), cscale(far, p2[abs(L)]));
+      if (L & 1) sum = mk(-sum.x, -sum.y);
+      if (o == 0) acc = cadd(acc, sum); else acc2 = cadd(acc2, sum);
     }
     __syncthreads();
   }
-  for (int o = 0; o < 2; ++o) {
-    const int lo = (int)threadIdx.x + o * kThreads - pb;
-    if (lo <= pb) {
-      cd* dst = F.local + (size_t)b * Q + lo + pb;
-      *dst = cadd(*dst, acc[o]);
-    }
+  if (lo <= pb) {
+    cd* dst = F.local + (size_t)b * Q + lo + pb;
+    *dst = cadd(*dst, acc);
+  }
+  if (lo2 <= pb) {
+    cd* dst = F.local + (size_t)b * Q + lo2 + pb;
+    *dst = cadd(*dst, acc2);
   }
 }
 
@@ -620,11 +649,15 @@ __global__ void __launch_bounds__(kThreads) p2p_ulist_kernel(Fmm F, const int* _
           const double rr = sqrt(dx * dx + dy * dy);
           if (rr == 0.0) continue;
           const double x = k * rr;
-          if (HS) cfma(acc, s_q[jj], mk(j0(x), y0(x)));
-          if (HD) {
-            const double f = k * (s_n[jj].x * dx + s_n[jj].y * dy) / rr;
-            cfma(acc, s_d[jj], mk(f * j1(x), f * y1(x)));
+          cd h0, h1;
+          if (x < 2.0) {
+            hankel01_series(x, h0, h1);
+          } else {
+            if (HS) h0 = mk(j0(x), y0(x));
+            if (HD) h1 = mk(j1(x), y1(x));
           }
+          if (HS) cfma(acc, s_q[jj], h0);
+          if (HD) cfma(acc, s_d[jj], cscale(h1, k * (s_n[jj].x * dx + s_n[jj].y * dy) / rr));
         }
       }
     }
@@ -895,6 +928,158 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
   }
 }
 
+// ---------------------------------------------------------------- mixed precision P2QBXL
+// H_0, H_1, the Hankel recurrence and the angular factors stay FP64; the terms
+// rho^|l| W_l (rho = k r_c, which keeps them of moderate size) are rounded to
+// FP32, multiplied by the FP32 strengths and added with Kahan compensation into
+// ah_l = alpha_l rho^|l|; alpha_l = ah_l rho^-|l| is formed in FP64 at the end.
+__device__ __forceinline__ void kahan2(float2& s, float2& c, float2 v) {
+  float y = v.x - c.x, t = s.x + y;
+  c.x = (t - s.x) - y;
+  s.x = t;
+  y = v.y - c.y;
+  t = s.y + y;
+  c.y = (t - s.y) - y;
+  s.y = t;
+}
+__device__ __forceinline__ float2 fmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 fsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2(cd a) { return make_float2((float)a.x, (float)a.y); }
+
+template <int PM, bool HS, bool HD>
+__device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float2 (&C)[2 * PM + 1],
+                                                  double dx, double dy, float2 q, float2 A,
+                                                  float2 B, double k, double rho, int p) {
+  const double rr = sqrt(dx * dx + dy * dy);
+  if (rr == 0.0) return;
+  const double x = k * rr;
+  const cd e1 = mk(dx / rr, dy / rr);
+  cd h0, h1;
+  hankel01(x, h0, h1);
+  // scaled Hankel values hs_m = H_m rho^m: hs_{m+1} = (2m rho / x) hs_m - rho^2 hs_{m-1}
+  const double r2 = rho * rho, c1 = 2.0 * rho / x, ir = 1.0 / rho;
+  cd hprev = h0, hcur = cscale(h1, rho);
+  cd eprev = mk(1.0, 0.0), ecur = e1;
+  // W^s_m = rho^|m| W_m for m = -1, 0, 1
+  float2 wm1 = f2(cscale(cmul(hcur, cconj(ecur)), -1.0));  // W^s_{-1}
+  float2 w0 = f2(h0);
+  float2 w1 = f2(cmul(hcur, ecur));
+  // l = 0: q W_0 + A W_{-1} - B W_1, with rho^0 W_{-1} = W^s_{-1} / rho, W_1 = W^s_1 / rho
+  {
+    float2 v = make_float2(0.f, 0.f);
+    if (HS) v = fmul(q, w0);
+    if (HD) {
+      const float fi = (float)ir;
+      const float2 t = fsub(fmul(A, wm1), fmul(B, w1));
+      v = make_float2(v.x + fi * t.x, v.y + fi * t.y);
+    }
+    kahan2(S[PM], C[PM], v);
+  }
+  float2 wp_prev = w0, wp_cur = w1;   // W^s_{m-1}, W^s_m (positive side)
+  float2 wn_prev = w0, wn_cur = wm1;  // W^s_{-(m-1)}, W^s_{-m}
+  double sgn = -1.0;                  // (-1)^m for m = 1
+  const float fr = (float)rho, fi = (float)ir;
+#pragma unroll
+  for (int m = 1; m <= PM; ++m) {
+    if (m > p) break;
+    const cd hnext = csub(cscale(hcur, c1 * m), cscale(hprev, r2));
+    const cd enext = cmul(ecur, e1);
+    const float2 wp_next = f2(cmul(hnext, enext));                          // W^s_{m+1}
+    const float2 wn_next = f2(cscale(cmul(hnext, cconj(enext)), -sgn));     // W^s_{-(m+1)}
+    // rho^m W_{m-1} = rho W^s_{m-1},  rho^m W_{m+1} = W^s_{m+1} / rho (same for -m)
+    float2 vp = make_float2(0.f, 0.f), vn = make_float2(0.f, 0.f);
+    if (HS) {
+      vp = fmul(q, wp_cur);
+      vn = fmul(q, wn_cur);
+    }
+    if (HD) {
+      const float2 ap = fmul(A, wp_prev), bp = fmul(B, wp_next);
+      vp.x += fr * ap.x - fi * bp.x;
+      vp.y += fr * ap.y - fi * bp.y;
+      const float2 an = fmul(A, wn_next), bn = fmul(B, wn_prev);
+      vn.x += fi * an.x - fr * bn.x;
+      vn.y += fi * an.y - fr * bn.y;
+    }
+    kahan2(S[PM + m], C[PM + m], vp);
+    kahan2(S[PM - m], C[PM - m], vn);
+    hprev = hcur;
+    hcur = hnext;
+    eprev = ecur;
+    ecur = enext;
+    wp_prev = wp_cur;
+    wp_cur = wp_next;
+    wn_prev = wn_cur;
+    wn_cur = wn_next;
+    sgn = -sgn;
+  }
+}
+
+template <int PM, bool HS, bool HD>
+__global__ void __launch_bounds__(kThreads) p2qbxl_ulist_mixed_kernel(
+    Fmm F, const int* __restrict__ leaves, cd* __restrict__ alpha) {
+  __shared__ double2 s_xy[kThreads];
+  __shared__ float2 s_q[kThreads];
+  __shared__ float2 s_A[kThreads];
+  __shared__ float2 s_B[kThreads];
+  const int b = leaves[blockIdx.x];
+  const int2 r = F.rctr[b];
+  if (r.y <= r.x) return;
+  const double k = F.k;
+  const int p = F.p, P = 2 * p + 1;
+  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
+    const int i = i0 + threadIdx.x;
+    const bool act = i < r.y;
+    const double cx = act ? F.cxy[i].x : 0.0, cy = act ? F.cxy[i].y : 0.0;
+    const double rho = act ? k * F.crad[i] : 1.0;
+    float2 S[2 * PM + 1], C[2 * PM + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * PM; ++j) S[j] = C[j] = make_float2(0.f, 0.f);
+    for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
+      const int2 sr = F.rsrc[F.uidx[e]];
+      for (int base = sr.x; base < sr.y; base += kThreads) {
+        __syncthreads();
+        const int j = base + threadIdx.x;
+        if (j < sr.y) {
+          s_xy[threadIdx.x] = F.sxy[j];
+          if (HS) s_q[threadIdx.x] = f2(F.qs[j]);
+          if (HD) {  // A = d (k/2) nu, B = d (k/2) conj(nu)
+            const cd dk = cscale(F.ds[j], 0.5 * k);
+            const cd nu = mk(F.snrm[j].x, F.snrm[j].y);
+            s_A[threadIdx.x] = f2(cmul(dk, nu));
+            s_B[threadIdx.x] = f2(cmul(dk, cconj(nu)));
+          }
+        }
+        __syncthreads();
+        const int cnt = min(kThreads, sr.y - base);
+        if (!act) continue;
+        for (int jj = 0; jj < cnt; ++jj)
+          p2qbxl_pair_mixed<PM, HS, HD>(S, C, s_xy[jj].x - cx, s_xy[jj].y - cy,
+                                        HS ? s_q[jj] : make_float2(0.f, 0.f),
+                                        HD ? s_A[jj] : make_float2(0.f, 0.f),
+                                        HD ? s_B[jj] : make_float2(0.f, 0.f), k, rho, p);
+      }
+    }
+    if (act) {
+      cd* dst = alpha + (size_t)F.cid[i] * P;
+      double ip = 1.0;
+      const double irho = 1.0 / rho;
+#pragma unroll
+      for (int m = 0; m <= PM; ++m) {
+        if (m > p) break;
+        const float2 sp = S[PM + m], cp = C[PM + m];
+        dst[p + m] = cadd(dst[p + m], mk(((double)sp.x - cp.x) * ip, ((double)sp.y - cp.y) * ip));
+        if (m > 0) {
+          const float2 sn = S[PM - m], cn = C[PM - m];
+          dst[p - m] = cadd(dst[p - m], mk(((double)sn.x - cn.x) * ip, ((double)sn.y - cn.y) * ip));
+        }
+        ip *= irho;
+      }
+    }
+  }
+}
+
 int p_add_default(int p) {
   // Table 2 of the paper for p <= 8 (2: 5, 4: 5, 6: 15, 8: 20); 2.5 p beyond
   if (p <= 4) return 5;
@@ -955,6 +1140,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   QBX_CUDA_TRY(cudaGetLastError());
   QBX_CUDA_TRY(f->mpole.alloc((size_t)f->n_boxes * f->Q));
   QBX_CUDA_TRY(f->local.alloc((size_t)f->n_boxes * f->Q));
+  TRY(mixed_plan_build(h, f));
   QBX_CUDA_TRY(f->qs.alloc(std::max<int64_t>(1, h->n_src)));
   QBX_CUDA_TRY(f->ds.alloc(std::max<int64_t>(1, h->n_src)));
   // leaves holding sources (P2M)
@@ -1042,7 +1228,7 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
 
 template <int PM>
 void launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D, cd* alpha,
-                           cudaStream_t s) {
+                           bool mixed, cudaStream_t s) {
   const size_t smQ = (size_t)F.Q * sizeof(cd);
   stage_begin(h, QBX_STAGE_L2QBXL, s);
   l2qbxl_kernel<PM><<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, alpha);
@@ -1054,9 +1240,15 @@ void launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool
   else if (D) m2qbxl_kernel<PM, false, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
   stage_end(h, QBX_STAGE_M2QBXL, s);
   stage_begin(h, QBX_STAGE_P2QBXL, s);
-  if (S && D) p2qbxl_ulist_kernel<PM, true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
-  else if (S) p2qbxl_ulist_kernel<PM, true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
-  else if (D) p2qbxl_ulist_kernel<PM, false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+  if (mixed) {
+    if (S && D) p2qbxl_ulist_mixed_kernel<PM, true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+    else if (S) p2qbxl_ulist_mixed_kernel<PM, true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+    else if (D) p2qbxl_ulist_mixed_kernel<PM, false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+  } else {
+    if (S && D) p2qbxl_ulist_kernel<PM, true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+    else if (S) p2qbxl_ulist_kernel<PM, true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+    else if (D) p2qbxl_ulist_kernel<PM, false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+  }
   stage_end(h, QBX_STAGE_P2QBXL, s);
   h->launches += (S || D) ? 3 : 2;
 }
@@ -1064,7 +1256,6 @@ void launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool
 }  // namespace
 
 qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaStream_t s) {
-  (void)precision;
   FmmPlan* f = h->fmm;
   if (!f) { set_error("FMM plan missing"); return QBX_ERR_STATE; }
   const int pb = f->pb, Q = f->Q, T = 4 * pb + 1;
@@ -1095,8 +1286,10 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   stage_end(h, QBX_STAGE_M2M, s);
   // Stage 4: M2L
   stage_begin(h, QBX_STAGE_M2L, s);
-  if (f->n_vbox > 0) {
-    m2l_kernel<<<f->n_vbox, kThreads, sm_tr + (pb + 1) * sizeof(double), s>>>(F, f->vbox.ptr);
+  if (precision == QBX_MIXED) {
+    TRY(launch_m2l_f32(h, f, s));
+  } else if (f->n_vbox > 0) {
+    m2l_kernel<<<f->n_vbox, kThreads, sm_tr + Q * sizeof(cd) + (pb + 1) * sizeof(double), s>>>(F, f->vbox.ptr);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_M2L, s);
@@ -1135,10 +1328,10 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   }
   // Stages 3, 5, 8 at centres: the QBX coefficients
   if (f->n_leaves > 0 && h->n_ctr > 0) {
-    if (h->p <= 4) launch_centre_kernels<4>(F, f, h, S, D, h->alpha.ptr, s);
-    else if (h->p <= 8) launch_centre_kernels<8>(F, f, h, S, D, h->alpha.ptr, s);
-    else if (h->p <= 12) launch_centre_kernels<12>(F, f, h, S, D, h->alpha.ptr, s);
-    else launch_centre_kernels<16>(F, f, h, S, D, h->alpha.ptr, s);
+    if (h->p <= 4) launch_centre_kernels<4>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
+    else if (h->p <= 8) launch_centre_kernels<8>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
+    else if (h->p <= 12) launch_centre_kernels<12>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
+    else launch_centre_kernels<16>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
   }
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;

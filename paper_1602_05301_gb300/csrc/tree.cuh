@@ -61,7 +61,13 @@ struct FmmPlan {
   DevBuf<cd> mpole, local;              // [n_boxes][Q]
   DevBuf<cd> qs, ds;                    // sorted strengths
   DevBuf<int> err;                      // device error flags
+  // mixed precision (sigma-normalised FP32 M2L)
+  DevBuf<double> lsig, conv;            // [n_levels][pb+1] log sig_j, s^j / sig_j
+  DevBuf<float2> tm_f32;                // [n_levels][49][Q][Q] M2L matrices
 };
+
+qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f);
+qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 
 qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max, double kappa);
 qbx_status tree_lists(qbx_handle* h, FmmPlan* f);

@@ -153,3 +153,36 @@ def test_fmm_starfish_config_sampled_parity(qbxmod, oracle):
     wgt = np.abs(jv(np.arange(-w["p"], w["p"] + 1)[None, :], g.k[0] * crad[cs][:, None]))
     assert rel_l2(alpha[cs] * wgt, a_ref * wgt) < TOL64
     lp.close()
+
+
+def test_mixed_precision_starfish_config(qbxmod, oracle):
+    """QBX_MIXED (FP32 translations with compensated sums, FP64 special functions and
+    final sums) on the full starfish workload: relative l2 error <= 1e-6 against the
+    FP64 path on every target and against the oracle on a sample; the error of each
+    result (near targets, far targets, QBX coefficients) is reported."""
+    w = make_config(2)
+    g = w["geom"]
+    lp = qbxmod.LayerPotential(g.as_dict(), w["p"], sides=2)
+    assoc = lp.build(w["tgt_xy"], mode=qbxmod.QBX_FMM, p_fmm=w["p_fmm"])
+    P = 2 * w["p"] + 1
+    a64 = np.empty((lp.n_centres, P), np.complex128)
+    a32 = np.empty((lp.n_centres, P), np.complex128)
+    args = dict(sigma_S=w["sigma_S"], sigma_D=w["sigma_D"], cS=w["cS"], cD=w["cD"])
+    u64 = lp.eval(alpha_out=a64, precision=qbxmod.QBX_FP64, **args)
+    u32 = lp.eval(alpha_out=a32, precision=qbxmod.QBX_MIXED, **args)
+    near = assoc >= 0
+    from scipy.special import jv
+    crad = np.concatenate([0.5 * g.panel_h[g.panel_of_node]] * 2)
+    wgt = np.abs(jv(np.arange(-w["p"], w["p"] + 1)[None, :], g.k[0] * crad[:, None]))
+    errs = dict(all=rel_l2(u32, u64), near=rel_l2(u32[near], u64[near]),
+                far=rel_l2(u32[~near], u64[~near]), alpha=rel_l2(a32 * wgt, a64 * wgt))
+    print("mixed vs fp64:", errs)
+    assert max(errs.values()) < 1e-6, errs
+    rng = np.random.default_rng(9)
+    sample = np.concatenate([rng.choice(np.nonzero(near)[0], 32, replace=False),
+                             rng.choice(np.nonzero(~near)[0], 64, replace=False)])
+    u_ref, _ = oracle.layer_potential(g.as_dict(), w["tgt_xy"][sample], w["p"], w["sigma_S"],
+                                      w["sigma_D"], w["cS"], w["cD"], sides=2,
+                                      centre_of_target=assoc[sample])
+    assert rel_l2(u32[sample], u_ref) < 1e-6
+    lp.close()
