@@ -43,6 +43,21 @@ KNOWN_TRAFFIC = {}
 
 
 # ---------------------------------------------------------------- helpers
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """Largest value of x over all ranks (the slowest rank sets the job time)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, ws: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return ws * units_per_rank * steps / (max_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -171,12 +186,8 @@ def run_ours(args, w, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = ws * n_t * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
+    value = job_throughput(n_t, ws, args.steps, total_ms)
     stats = lp.stats()
 
     # per-kernel device times (events around each kernel class on the eval stream)
@@ -218,11 +229,9 @@ def run_ours(args, w, ws, rank, local):
         lp.eval(sigma_S=hS, sigma_D=hD, cS=w["cS"], cD=w["cD"], out=hout, precision=prec,
                 stream=sp)
         e2e_s.append(time.perf_counter() - a)
-    e2e_t = torch.tensor([sum(e2e_s)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = max_over_ranks(1e3 * sum(e2e_s), ws, dev)
     h2d = 16 * g.n * ((1 if hS is not None else 0) + (1 if hD is not None else 0))
-    e2e = {"value": ws * n_t * args.steps / float(e2e_t.item()), "unit": UNIT,
+    e2e = {"value": job_throughput(n_t, ws, args.steps, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * n_t}
     res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
                warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,

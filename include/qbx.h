@@ -198,6 +198,45 @@ qbx_status qbx_export_tree(const qbx_handle *h, int64_t *info, double *root, int
                            int32_t *perm_ctr, int32_t *perm_tgt);
 
 /*
+ * Measured plan selection. Builds the plan of `desc` (targets, association)
+ * for each candidate -- QBX_DIRECT, and QBX_FMM with n_max in {32, 64, 128}
+ * -- times `reps` evaluations of each with CUDA events (random unit
+ * densities, the given precision and layers: has_S / has_D 0 or 1) and
+ * leaves the fastest plan built in the handle. times_ms (optional, [4])
+ * receives the median time of each candidate in that order (0 for a
+ * candidate that is skipped: FMM plans are skipped for fewer than 512
+ * sources); *chosen receives the index of the winner. Decisions are cached
+ * per (sources rounded to a power of two, k * mean panel length rounded to
+ * 1/8, p, precision) so that similar problems of a batch are timed once.
+ * desc->mode, desc->n_max are ignored. Synchronous.
+ */
+qbx_status qbx_autotune(qbx_handle *h, const qbx_tree_desc *desc, int32_t precision,
+                        int32_t has_S, int32_t has_D, int32_t reps, double *times_ms,
+                        int32_t *chosen);
+
+/*
+ * Batched evaluation of many independent problems (for example curves with
+ * their own wavenumbers and densities), each a handle after qbx_tree_build.
+ * The evaluations of all handles are captured once into one CUDA graph whose
+ * branches run concurrently (handles are dealt round-robin onto n_streams
+ * streams), so that many small problems fill the GPU; later calls replay the
+ * graph. Densities and results are concatenated in handle order:
+ * sigma_S / sigma_D complex [sum n_src_i] (either may be NULL for all
+ * handles), out complex [sum n_targets_i]; cS, cD complex [n] per handle.
+ * Pointers may be host or device memory; the batch owns device staging
+ * buffers whose addresses the graph uses. A change of precision, layers or
+ * coefficients re-captures the graph. Synchronous when any pointer is host
+ * memory, else asynchronous on cuda_stream.
+ */
+typedef struct qbx_batch qbx_batch;
+qbx_status qbx_batch_create(int32_t n, qbx_handle *const *handles, int32_t n_streams,
+                            qbx_batch **out);
+qbx_status qbx_batch_eval(qbx_batch *b, const double *cS, const double *sigma_S,
+                          const double *cD, const double *sigma_D, double *out,
+                          int32_t precision, void *cuda_stream);
+void qbx_batch_destroy(qbx_batch *b);
+
+/*
  * Allocation-free direct QBX evaluation. The paper has no counterpart: this is
  * an interface addition for callers that must not allocate device memory, for
  * example an application whose HBM is entirely handed out up front by its own

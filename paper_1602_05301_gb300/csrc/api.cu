@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -54,13 +55,35 @@ std::vector<T> to_host(const T* src, size_t n) {
 
 }  // namespace
 
+// QBX_DEBUG_SYNC=1 in the environment: synchronise around every stage and
+// report the first stage whose kernels failed (a debugging aid; off by default).
+int debug_sync() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("QBX_DEBUG_SYNC");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v;
+}
+
+static void debug_check(qbx_handle* h, int stage, cudaStream_t s, bool end) {
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && h->dbg_err == cudaSuccess) {
+    h->dbg_err = e;
+    h->dbg_stage = stage;
+    h->dbg_end = end;
+  }
+}
+
 void stage_begin(qbx_handle* h, int stage, cudaStream_t s) {
+  if (debug_sync()) debug_check(h, stage, s, false);
   if (!h->timing) return;
   cudaEventRecord(h->ev[2 * stage], s);
   h->ev_used[stage] = true;
 }
 
 void stage_end(qbx_handle* h, int stage, cudaStream_t s) {
+  if (debug_sync()) debug_check(h, stage, s, true);
   if (!h->timing) return;
   cudaEventRecord(h->ev[2 * stage + 1], s);
 }
@@ -283,6 +306,7 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
   if (alpha_out && !alpha_dev) host_io = true;
 
   h->launches = 0;
+  h->dbg_err = cudaSuccess;
   stage_begin(h, QBX_STAGE_STRENGTHS, s);
   QBX_TRY(launch_strengths(h, mk(cS_re, cS_im), sS, mk(cD_re, cD_im), sD, s));
   stage_end(h, QBX_STAGE_STRENGTHS, s);
@@ -300,6 +324,11 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
   QBX_TRY(launch_qbxl2p(h, o, s));
   stage_end(h, QBX_STAGE_QBXL2P, s);
   h->stats[16] = h->launches;
+  if (h->dbg_err != cudaSuccess) {
+    set_error("debug sync: stage %d (%s) failed: %s", h->dbg_stage, h->dbg_end ? "end" : "begin",
+              cudaGetErrorString(h->dbg_err));
+    return QBX_ERR_CUDA;
+  }
   if (!out_dev)
     QBX_CUDA_TRY(cudaMemcpyAsync(out, o, h->n_tgt * sizeof(cd), cudaMemcpyDefault, s));
   if (alpha_out)

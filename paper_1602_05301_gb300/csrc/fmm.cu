@@ -212,65 +212,59 @@ __global__ void gather_strengths_kernel(int64_t n, const int* __restrict__ perm,
 // conj(V_m(y - m_b)) / s^m, m = 0..pb+1; then all threads reduce over the rows.
 __global__ void __launch_bounds__(kThreads) p2m_kernel(Fmm F, const int* __restrict__ leaves) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, R = pb + 2;
-  cd* rows = smem;                      // [kChunk][R]
-  cd* sq = rows + kChunk * R;           // [kChunk]
-  cd* sd = sq + kChunk;                 // [kChunk]
-  cd* snu = sd + kChunk;                // [kChunk]
-  __shared__ int cnt;
+  const int pb = F.pb, RW = 2 * pb + 3;   // row: conj(V_t)/s^|t|, t = -(pb+1)..pb+1
+  cd* rows = smem;                        // [kChunk][RW]
+  cd* sq = rows + kChunk * RW;            // [kChunk]
+  cd* sa = sq + kChunk;                   // [kChunk]  d (k/2) conj(nu)
+  cd* sb = sa + kChunk;                   // [kChunk]  d (k/2) nu
   const int b = leaves[blockIdx.x];
   const int2 r = F.rsrc[b];
   const int l = F.level[b];
-  const double s = F.scale[l];
+  const double s = F.scale[l], is = 1.0 / s;
   const double2 m = F.centre[b];
   const double hk = 0.5 * F.k;
   cd acc[2];
   acc[0] = acc[1] = mk(0.0, 0.0);
   for (int base = r.x; base < r.y; base += kChunk) {
-    if (threadIdx.x == 0) cnt = min(kChunk, r.y - base);
-    if (threadIdx.x < kChunk && base + (int)threadIdx.x < r.y) {
+    const int cnt = min(kChunk, r.y - base);
+    if ((int)threadIdx.x < cnt) {
       const int i = base + threadIdx.x;
       const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
       const double rr = sqrt(dx * dx + dy * dy);
-      double* row = (double*)(rows + threadIdx.x * R);  // J values in the real slots
-      const double norm = miller_row(F.k * rr, R - 1, row, 2);
+      cd* row = rows + threadIdx.x * RW + (pb + 1);
+      // J_0..J_{pb+1} (unnormalised) into the real parts of row[0..pb+1]
+      const double norm = miller_row(F.k * rr, pb + 1, (double*)row, 2);
       const cd em = rr > 0.0 ? mk(dx / rr, -dy / rr) : mk(1.0, 0.0);  // e^{-i th}
       cd e = mk(1.0, 0.0);
-      double is = 1.0 / norm;
-      for (int j = 0; j < R; ++j) {
-        const double v = row[2 * j] * is;
-        rows[threadIdx.x * R + j] = cscale(e, v);
+      double f = 1.0 / norm;
+      for (int j = 0; j <= pb + 1; ++j) {
+        const double v = row[j].x * f;                // J_j / s^j
+        const cd c = cscale(e, v);                    // conj(V_j) / s^j
+        row[j] = c;
+        if (j > 0) row[-j] = (j & 1) ? mk(-c.x, c.y) : mk(c.x, -c.y);  // (-1)^j conj(c)
         e = cmul(e, em);
-        is /= s;
+        f *= is;
       }
+      const cd dk = cscale(F.ds[i], hk);
+      const cd nu = mk(F.snrm[i].x, F.snrm[i].y);
       sq[threadIdx.x] = F.qs[i];
-      sd[threadIdx.x] = F.ds[i];
-      snu[threadIdx.x] = mk(F.snrm[i].x, F.snrm[i].y);
+      sa[threadIdx.x] = cmul(dk, cconj(nu));
+      sb[threadIdx.x] = cmul(dk, nu);
     }
     __syncthreads();
     for (int o = 0; o < 2; ++o) {
       const int n = (int)threadIdx.x + o * kThreads - pb;
       if (n > pb) continue;
       const int an = abs(n);
+      // conj(V_{n-+1})/s^|n| = row[n-+1] s^{|n-+1| - |n|}
+      const double fm = (abs(n - 1) > an) ? s : is;
+      const double fp = (abs(n + 1) > an) ? s : is;
       for (int j = 0; j < cnt; ++j) {
-        const cd* row = rows + j * R;
-        // cv(t) = conj(V_t)/s^|t|; for t < 0: (-1)^t conj(row[|t|])
-        auto cv = [&](int t) -> cd {
-          const int at = abs(t);
-          cd v = row[at];
-          if (t < 0) {
-            v = cconj(v);
-            if (at & 1) v = mk(-v.x, -v.y);
-          }
-          return v;
-        };
-        if (F.has_S) cfma(acc[o], sq[j], cv(n));
+        const cd* row = rows + j * RW + (pb + 1);
+        if (F.has_S) cfma(acc[o], sq[j], row[n]);
         if (F.has_D) {
-          const double fm = (abs(n - 1) > an) ? s : 1.0 / s;
-          const double fp = (abs(n + 1) > an) ? s : 1.0 / s;
-          const cd t = csub(cscale(cmul(cconj(snu[j]), cv(n - 1)), fm),
-                            cscale(cmul(snu[j], cv(n + 1)), fp));
-          cfma(acc[o], cscale(sd[j], hk), t);
+          cfma(acc[o], cscale(sa[j], fm), row[n - 1]);
+          cfma(acc[o], cscale(sb[j], -fp), row[n + 1]);
         }
       }
     }
@@ -320,19 +314,13 @@ __global__ void __launch_bounds__(kThreads) m2m_kernel(Fmm F, const int* __restr
 // ---------------------------------------------------------------- M2L (Stage 4)
 // lh_l += (-1)^l sum_n What_{n+l} mh_n c(l,n), What_m = s^|m| W_m(m_b - m_c),
 // c(l,n) = s^{2 min(|l|,|n|)} when l and n have opposite signs, else 1.
-// sum_{n=n0}^{n1-1} w[n] a[n] with four independent accumulators, so that the
-// dependent FP64 multiply-add chains of one thread overlap.
+// sum_{n=n0}^{n1-1} w[n] a[n]. One accumulator: the FP64 pipe (two FMAs per
+// clock per SM) is the limit, not the latency of the dependent chain, so extra
+// accumulators only add instructions (measured slower).
 __device__ __forceinline__ cd cdot(const cd* w, const cd* a, int n0, int n1) {
-  cd s0 = mk(0.0, 0.0), s1 = s0, s2 = s0, s3 = s0;
-  int n = n0;
-  for (; n + 3 < n1; n += 4) {
-    cfma(s0, w[n], a[n]);
-    cfma(s1, w[n + 1], a[n + 1]);
-    cfma(s2, w[n + 2], a[n + 2]);
-    cfma(s3, w[n + 3], a[n + 3]);
-  }
-  for (; n < n1; ++n) cfma(s0, w[n], a[n]);
-  return cadd(cadd(s0, s1), cadd(s2, s3));
+  cd s = mk(0.0, 0.0);
+  for (int n = n0; n < n1; ++n) cfma(s, w[n], a[n]);
+  return s;
 }
 
 __global__ void __launch_bounds__(kThreads) m2l_kernel(Fmm F, const int* __restrict__ boxes) {
@@ -398,16 +386,14 @@ __global__ void __launch_bounds__(kThreads) m2l_kernel(Fmm F, const int* __restr
 // CTA per box with an X list: lh_l += s^|l| sum_j [q W_l + d (k/2)(nu W_{l-1} - conj(nu) W_{l+1})]
 __global__ void __launch_bounds__(kThreads) p2l_kernel(Fmm F, const int* __restrict__ boxes) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, R = pb + 2;
-  cd* hrow = smem;                  // [kChunk][R] H_m s^m
-  cd* erow = hrow + kChunk * R;     // [kChunk][R] e^{i m th}
-  cd* sq = erow + kChunk * R;
-  cd* sd = sq + kChunk;
-  cd* snu = sd + kChunk;
-  __shared__ int cnt;
+  const int pb = F.pb, RW = 2 * pb + 3;   // row: Wh_t for t = -(pb+1)..pb+1 at index t + pb + 1
+  cd* rows = smem;                        // [kChunk][RW]
+  cd* sq = rows + kChunk * RW;            // [kChunk]
+  cd* sa = sq + kChunk;                   // [kChunk]  A = d (k/2) nu
+  cd* sb = sa + kChunk;                   // [kChunk]  B = d (k/2) conj(nu)
   const int b = boxes[blockIdx.x];
   const int l = F.level[b];
-  const double s = F.scale[l];
+  const double s = F.scale[l], is = 1.0 / s;
   const double2 m = F.centre[b];
   const double hk = 0.5 * F.k;
   cd acc[2];
@@ -415,53 +401,46 @@ __global__ void __launch_bounds__(kThreads) p2l_kernel(Fmm F, const int* __restr
   for (int e = F.xoff[b]; e < F.xoff[b + 1]; ++e) {
     const int2 r = F.rsrc[F.xidx[e]];
     for (int base = r.x; base < r.y; base += kChunk) {
-      if (threadIdx.x == 0) cnt = min(kChunk, r.y - base);
-      if (threadIdx.x < kChunk && base + (int)threadIdx.x < r.y) {
+      const int cnt = min(kChunk, r.y - base);
+      if ((int)threadIdx.x < cnt) {
         const int i = base + threadIdx.x;
         const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
         const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
         const cd e1 = mk(dx / rr, dy / rr);
         cd h0, h1;
         hankel01(x, h0, h1);
+        cd* row = rows + threadIdx.x * RW + (pb + 1);   // row[t], t = -(pb+1)..pb+1
         cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
-        cd* hr = hrow + threadIdx.x * R;
-        cd* er = erow + threadIdx.x * R;
-        hr[0] = h0;
-        er[0] = ee;
-        for (int j = 1; j < R; ++j) {
+        row[0] = h0;
+        for (int j = 1; j <= pb + 1; ++j) {
           ee = cmul(ee, e1);
-          hr[j] = hm;
-          er[j] = ee;
+          row[j] = cmul(hm, ee);                                  // s^j W_j
+          const cd v = cmul(hm, cconj(ee));
+          row[-j] = (j & 1) ? mk(-v.x, -v.y) : v;                 // s^j W_{-j}
           const cd hn = csub(cscale(hm, 2.0 * j * s / x), cscale(hm1, s * s));
           hm1 = hm;
           hm = hn;
         }
+        const cd dk = cscale(F.ds[i], hk);
+        const cd nu = mk(F.snrm[i].x, F.snrm[i].y);
         sq[threadIdx.x] = F.qs[i];
-        sd[threadIdx.x] = F.ds[i];
-        snu[threadIdx.x] = mk(F.snrm[i].x, F.snrm[i].y);
+        sa[threadIdx.x] = cmul(dk, nu);
+        sb[threadIdx.x] = cmul(dk, cconj(nu));
       }
       __syncthreads();
       for (int o = 0; o < 2; ++o) {
         const int n = (int)threadIdx.x + o * kThreads - pb;
         if (n > pb) continue;
         const int an = abs(n);
+        // s^|n| W_{n-1} = Wh_{n-1} s^{|n| - |n-1|}, s^|n| W_{n+1} = Wh_{n+1} s^{|n| - |n+1|}
+        const double fm = (abs(n - 1) > an) ? is : s;
+        const double fp = (abs(n + 1) > an) ? is : s;
         for (int j = 0; j < cnt; ++j) {
-          const cd* hr = hrow + j * R;
-          const cd* er = erow + j * R;
-          // Wh(t) = s^|t| W_t; for t < 0: (-1)^t H_|t| s^|t| conj(e^{i|t|th})
-          auto wh = [&](int t) -> cd {
-            const int at = abs(t);
-            cd v = t >= 0 ? cmul(hr[at], er[at]) : cmul(hr[at], cconj(er[at]));
-            if (t < 0 && (at & 1)) v = mk(-v.x, -v.y);
-            return v;
-          };
-          if (F.has_S) cfma(acc[o], sq[j], wh(n));
+          const cd* row = rows + j * RW + (pb + 1);
+          if (F.has_S) cfma(acc[o], sq[j], row[n]);
           if (F.has_D) {
-            const double fm = (abs(n - 1) > an) ? 1.0 / s : s;  // s^{|n| - |n-1|}
-            const double fp = (abs(n + 1) > an) ? 1.0 / s : s;
-            const cd t = csub(cscale(cmul(snu[j], wh(n - 1)), fm),
-                              cscale(cmul(cconj(snu[j]), wh(n + 1)), fp));
-            cfma(acc[o], cscale(sd[j], hk), t);
+            cfma(acc[o], cscale(sa[j], fm), row[n - 1]);
+            cfma(acc[o], cscale(sb[j], -fp), row[n + 1]);
           }
         }
       }
@@ -756,41 +735,59 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __re
 // (r, th) the polar coordinates of source - centre; upward Hankel recurrence.
 template <int PM, bool HS, bool HD>
 __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, double dy, cd q,
-                                            cd dsrc, cd nu, double k, int p) {
+                                            cd A, cd B, double k, int p) {
+  // A = d (k/2) nu, B = d (k/2) conj(nu): alpha_l += q W_l + A W_{l-1} - B W_{l+1}.
+  // W_m and W_{-m} are kept in sliding windows so each is formed once.
   const double rr = sqrt(dx * dx + dy * dy);
   if (rr == 0.0) return;
   const double ir = 1.0 / rr, x = k * rr, ix2 = 2.0 / x;
   const cd e1 = mk(dx * ir, dy * ir);
   cd h0, h1;
   hankel01(x, h0, h1);
-  const cd dk = cscale(dsrc, 0.5 * k);
-  const cd nub = cconj(nu);
   const cd w1 = cmul(h1, e1);
   const cd wm1 = cscale(cmul(h1, cconj(e1)), -1.0);
   if (HS) cfma(acc[PM], q, h0);
-  if (HD) cfma(acc[PM], dk, csub(cmul(nu, wm1), cmul(nub, w1)));
-  cd hprev = h0, hcur = h1, eprev = mk(1.0, 0.0), ecur = e1;
-  double sgn = -1.0;
+  if (HD) {
+    cfma(acc[PM], A, wm1);
+    cfma(acc[PM], mk(-B.x, -B.y), w1);
+  }
+  cd hprev = h0, hcur = h1, ecur = e1;
+  cd wp_prev = h0, wp_cur = w1;   // W_{m-1}, W_m
+  cd wn_prev = h0, wn_cur = wm1;  // W_{-(m-1)}, W_{-m}
+  const cd mB = mk(-B.x, -B.y);
+  double sgn = -1.0;              // (-1)^m
 #pragma unroll
   for (int m = 1; m <= PM; ++m) {
     if (m > p) break;
-    const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
-    const cd enext = cmul(ecur, e1);
     if (HS) {
-      cfma(acc[PM + m], q, cmul(hcur, ecur));
-      cfma(acc[PM - m], q, cscale(cmul(hcur, cconj(ecur)), sgn));
+      cfma(acc[PM + m], q, wp_cur);
+      cfma(acc[PM - m], q, wn_cur);
     }
     if (HD) {
-      const cd w_p = cmul(hnext, enext), w_pm = cmul(hprev, eprev);
-      const cd v_p = cscale(cmul(hnext, cconj(enext)), -sgn);
-      const cd v_pm = cscale(cmul(hprev, cconj(eprev)), -sgn);
-      cfma(acc[PM + m], dk, csub(cmul(nu, w_pm), cmul(nub, w_p)));
-      cfma(acc[PM - m], dk, csub(cmul(nu, v_p), cmul(nub, v_pm)));
+      const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
+      const cd enext = cmul(ecur, e1);
+      const cd wp_next = cmul(hnext, enext);
+      const cd wn_next = cscale(cmul(hnext, cconj(enext)), -sgn);
+      cfma(acc[PM + m], A, wp_prev);
+      cfma(acc[PM + m], mB, wp_next);
+      cfma(acc[PM - m], A, wn_next);
+      cfma(acc[PM - m], mB, wn_prev);
+      hprev = hcur;
+      hcur = hnext;
+      ecur = enext;
+      wp_prev = wp_cur;
+      wp_cur = wp_next;
+      wn_prev = wn_cur;
+      wn_cur = wn_next;
+    } else if (m < p) {
+      const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
+      const cd enext = cmul(ecur, e1);
+      hprev = hcur;
+      hcur = hnext;
+      ecur = enext;
+      wp_cur = cmul(hnext, enext);
+      wn_cur = cscale(cmul(hnext, cconj(enext)), -sgn);
     }
-    hprev = hcur;
-    hcur = hnext;
-    eprev = ecur;
-    ecur = enext;
     sgn = -sgn;
   }
 }
@@ -836,9 +833,13 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __re
       if (Rc + F.crad[i] > kW * rr) {
         const int2 sr = F.rsrc[c];
         for (int j = sr.x; j < sr.y; ++j)
+        {
+          const cd dk = HD ? cscale(F.ds[j], 0.5 * k) : mk(0.0, 0.0);
+          const cd nu = HD ? mk(F.snrm[j].x, F.snrm[j].y) : mk(0.0, 0.0);
           p2qbxl_pair<PM, HS, HD>(acc, F.sxy[j].x - z.x, F.sxy[j].y - z.y,
-                                  HS ? F.qs[j] : mk(0.0, 0.0), HD ? F.ds[j] : mk(0.0, 0.0),
-                                  HD ? mk(F.snrm[j].x, F.snrm[j].y) : mk(0.0, 0.0), k, p);
+                                  HS ? F.qs[j] : mk(0.0, 0.0), cmul(dk, nu), cmul(dk, cconj(nu)),
+                                  k, p);
+        }
         continue;
       }
       const double x = k * rr;
@@ -884,9 +885,9 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
                                                                 const int* __restrict__ leaves,
                                                                 cd* __restrict__ alpha) {
   __shared__ double2 s_xy[kThreads];
-  __shared__ double2 s_nu[kThreads];
+  __shared__ cd s_nu[kThreads];  // B = d (k/2) conj(nu)
   __shared__ cd s_q[kThreads];
-  __shared__ cd s_d[kThreads];
+  __shared__ cd s_d[kThreads];   // A = d (k/2) nu
   const int b = leaves[blockIdx.x];
   const int2 r = F.rctr[b];
   if (r.y <= r.x) return;
@@ -908,8 +909,10 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
           s_xy[threadIdx.x] = F.sxy[j];
           if (HS) s_q[threadIdx.x] = F.qs[j];
           if (HD) {
-            s_nu[threadIdx.x] = F.snrm[j];
-            s_d[threadIdx.x] = F.ds[j];
+            const cd dk = cscale(F.ds[j], 0.5 * k);
+            const cd nu = mk(F.snrm[j].x, F.snrm[j].y);
+            s_d[threadIdx.x] = cmul(dk, nu);
+            s_nu[threadIdx.x] = cmul(dk, cconj(nu));
           }
         }
         __syncthreads();
@@ -918,7 +921,7 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
         for (int jj = 0; jj < cnt; ++jj)
           p2qbxl_pair<PM, HS, HD>(acc, s_xy[jj].x - cx, s_xy[jj].y - cy,
                                   HS ? s_q[jj] : mk(0.0, 0.0), HD ? s_d[jj] : mk(0.0, 0.0),
-                                  HD ? mk(s_nu[jj].x, s_nu[jj].y) : mk(0.0, 0.0), k, p);
+                                  HD ? s_nu[jj] : mk(0.0, 0.0), k, p);
       }
     }
     if (act) {
@@ -961,11 +964,13 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   // scaled Hankel values hs_m = H_m rho^m: hs_{m+1} = (2m rho / x) hs_m - rho^2 hs_{m-1}
   const double r2 = rho * rho, c1 = 2.0 * rho / x, ir = 1.0 / rho;
   cd hprev = h0, hcur = cscale(h1, rho);
-  cd eprev = mk(1.0, 0.0), ecur = e1;
+  // angular factors e^{i m th} in FP32 (unit modulus; rounding grows like m eps_32)
+  const float2 e1f = f2(e1);
+  float2 ecur = e1f;
   // W^s_m = rho^|m| W_m for m = -1, 0, 1
-  float2 wm1 = f2(cscale(cmul(hcur, cconj(ecur)), -1.0));  // W^s_{-1}
+  float2 wm1 = f2(cscale(cmul(hcur, cconj(e1)), -1.0));  // W^s_{-1}
   float2 w0 = f2(h0);
-  float2 w1 = f2(cmul(hcur, ecur));
+  float2 w1 = f2(cmul(hcur, e1));
   // l = 0: q W_0 + A W_{-1} - B W_1, with rho^0 W_{-1} = W^s_{-1} / rho, W_1 = W^s_1 / rho
   {
     float2 v = make_float2(0.f, 0.f);
@@ -985,9 +990,12 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   for (int m = 1; m <= PM; ++m) {
     if (m > p) break;
     const cd hnext = csub(cscale(hcur, c1 * m), cscale(hprev, r2));
-    const cd enext = cmul(ecur, e1);
-    const float2 wp_next = f2(cmul(hnext, enext));                          // W^s_{m+1}
-    const float2 wn_next = f2(cscale(cmul(hnext, cconj(enext)), -sgn));     // W^s_{-(m+1)}
+    const float2 enext = fmul(ecur, e1f);
+    const float2 hn32 = f2(hnext);
+    const float2 wp_next = fmul(hn32, enext);                                // W^s_{m+1}
+    const float2 wq = fmul(hn32, make_float2(enext.x, -enext.y));
+    const float fs = (float)(-sgn);
+    const float2 wn_next = make_float2(fs * wq.x, fs * wq.y);                // W^s_{-(m+1)}
     // rho^m W_{m-1} = rho W^s_{m-1},  rho^m W_{m+1} = W^s_{m+1} / rho (same for -m)
     float2 vp = make_float2(0.f, 0.f), vn = make_float2(0.f, 0.f);
     if (HS) {
@@ -1006,7 +1014,6 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
     kahan2(S[PM - m], C[PM - m], vn);
     hprev = hcur;
     hcur = hnext;
-    eprev = ecur;
     ecur = enext;
     wp_prev = wp_cur;
     wp_cur = wp_next;
@@ -1227,17 +1234,19 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
 }
 
 template <int PM>
-void launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D, cd* alpha,
-                           bool mixed, cudaStream_t s) {
+qbx_status launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
+                                 cd* alpha, bool mixed, cudaStream_t s) {
   const size_t smQ = (size_t)F.Q * sizeof(cd);
   stage_begin(h, QBX_STAGE_L2QBXL, s);
   l2qbxl_kernel<PM><<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, alpha);
+  QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
   stage_begin(h, QBX_STAGE_M2QBXL, s);
   const size_t smW = smQ + (size_t)(PM + 1) * sizeof(cd);
   if (S && D) m2qbxl_kernel<PM, true, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
   else if (S) m2qbxl_kernel<PM, true, false><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
   else if (D) m2qbxl_kernel<PM, false, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
+  QBX_KCHECK("m2qbxl", s);
   stage_end(h, QBX_STAGE_M2QBXL, s);
   stage_begin(h, QBX_STAGE_P2QBXL, s);
   if (mixed) {
@@ -1249,8 +1258,10 @@ void launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool
     else if (S) p2qbxl_ulist_kernel<PM, true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
     else if (D) p2qbxl_ulist_kernel<PM, false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
   }
+  QBX_KCHECK("p2qbxl_ulist", s);
   stage_end(h, QBX_STAGE_P2QBXL, s);
   h->launches += (S || D) ? 3 : 2;
+  return QBX_OK;
 }
 
 }  // namespace
@@ -1262,16 +1273,18 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   if (h->n_src > 0) {
     gather_strengths_kernel<<<nblk(h->n_src, 256), 256, 0, s>>>(
         h->n_src, f->perm[PT_SRC].ptr, h->q_str.ptr, h->d_str.ptr, f->qs.ptr, f->ds.ptr);
+    QBX_KCHECK("gather_strengths", s);
     h->launches += 1;
   }
   Fmm F = make_view(h, f, S, D);
   QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_boxes * Q * sizeof(cd), s));
   QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_boxes * Q * sizeof(cd), s));
   // Stage 2: P2M, M2M
-  const size_t sm_p2m = (size_t)(kChunk * (pb + 2) + 3 * kChunk) * sizeof(cd);
+  const size_t sm_p2m = (size_t)(kChunk * (2 * pb + 3) + 3 * kChunk) * sizeof(cd);
   stage_begin(h, QBX_STAGE_P2M, s);
   if (f->n_src_leaves > 0 && (S || D)) {
     p2m_kernel<<<f->n_src_leaves, kThreads, sm_p2m, s>>>(F, f->src_leaves.ptr);
+    QBX_KCHECK("p2m", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_P2M, s);
@@ -1281,6 +1294,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
     if (nb == 0) continue;
     m2m_kernel<<<nb, kThreads, sm_tr, s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+    QBX_KCHECK("m2m", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_M2M, s);
@@ -1290,14 +1304,16 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     TRY(launch_m2l_f32(h, f, s));
   } else if (f->n_vbox > 0) {
     m2l_kernel<<<f->n_vbox, kThreads, sm_tr + Q * sizeof(cd) + (pb + 1) * sizeof(double), s>>>(F, f->vbox.ptr);
+    QBX_KCHECK("m2l", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_M2L, s);
   // Stage 6: P2L
   stage_begin(h, QBX_STAGE_P2L, s);
   if (f->n_xbox > 0 && (S || D)) {
-    const size_t sm = (size_t)(2 * kChunk * (pb + 2) + 3 * kChunk) * sizeof(cd);
+    const size_t sm = (size_t)(kChunk * (2 * pb + 3) + 3 * kChunk) * sizeof(cd);
     p2l_kernel<<<f->n_xbox, kThreads, sm, s>>>(F, f->xbox.ptr);
+    QBX_KCHECK("p2l", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_P2L, s);
@@ -1307,6 +1323,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
     if (nb == 0) continue;
     l2l_kernel<<<nb, kThreads, sm_tr, s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+    QBX_KCHECK("l2l", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_L2L, s);
@@ -1315,9 +1332,11 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   if (f->n_leaves > 0 && h->n_direct_tgt > 0) {
     stage_begin(h, QBX_STAGE_L2P, s);
     l2p_kernel<<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, out);
+    QBX_KCHECK("l2p", s);
     stage_end(h, QBX_STAGE_L2P, s);
     stage_begin(h, QBX_STAGE_M2P, s);
     m2p_kernel<<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, out);
+    QBX_KCHECK("m2p", s);
     stage_end(h, QBX_STAGE_M2P, s);
     stage_begin(h, QBX_STAGE_P2P, s);
     if (S && D) p2p_ulist_kernel<true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, out);
@@ -1328,10 +1347,10 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   }
   // Stages 3, 5, 8 at centres: the QBX coefficients
   if (f->n_leaves > 0 && h->n_ctr > 0) {
-    if (h->p <= 4) launch_centre_kernels<4>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
-    else if (h->p <= 8) launch_centre_kernels<8>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
-    else if (h->p <= 12) launch_centre_kernels<12>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
-    else launch_centre_kernels<16>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s);
+    if (h->p <= 4) TRY(launch_centre_kernels<4>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
+    else if (h->p <= 8) TRY(launch_centre_kernels<8>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
+    else if (h->p <= 12) TRY(launch_centre_kernels<12>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
+    else TRY(launch_centre_kernels<16>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
   }
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;

@@ -91,6 +91,9 @@ struct qbx_handle {
   bool timing = false;
   cudaEvent_t ev[2 * QBX_STAGE_COUNT] = {};
   bool ev_used[QBX_STAGE_COUNT] = {};
+  cudaError_t dbg_err = cudaSuccess;        // QBX_DEBUG_SYNC bookkeeping
+  int dbg_stage = -1;
+  bool dbg_end = false;
 };
 
 // ---------------------------------------------------------------- kernels entry points
@@ -115,3 +118,15 @@ void fmm_plan_free(FmmPlan* f);
 // stage timing helpers (api.cu)
 void stage_begin(qbx_handle* h, int stage, cudaStream_t s);
 void stage_end(qbx_handle* h, int stage, cudaStream_t s);
+// QBX_DEBUG_SYNC=1: synchronise after every kernel and name the one that failed
+int debug_sync();
+#define QBX_KCHECK(name, stream)                                                      \
+  do {                                                                                \
+    if (debug_sync()) {                                                               \
+      const cudaError_t e_ = cudaStreamSynchronize(stream);                           \
+      if (e_ != cudaSuccess) {                                                        \
+        set_error("kernel %s failed: %s", name, cudaGetErrorString(e_));              \
+        return QBX_ERR_CUDA;                                                          \
+      }                                                                               \
+    }                                                                                 \
+  } while (0)

@@ -87,6 +87,17 @@ def library() -> ctypes.CDLL:
                                                 ctypes.c_int32]
             lib.qbx_export_tree.restype = ctypes.c_int
             lib.qbx_export_tree.argtypes = [_vp] + [_vp] * 11
+            lib.qbx_autotune.restype = ctypes.c_int
+            lib.qbx_autotune.argtypes = [_vp, ctypes.POINTER(qbx_tree_desc), ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
+                                         _vp]
+            lib.qbx_batch_create.restype = ctypes.c_int
+            lib.qbx_batch_create.argtypes = [ctypes.c_int32, _vp, ctypes.c_int32,
+                                             ctypes.POINTER(_vp)]
+            lib.qbx_batch_eval.restype = ctypes.c_int
+            lib.qbx_batch_eval.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp]
+            lib.qbx_batch_destroy.restype = None
+            lib.qbx_batch_destroy.argtypes = [_vp]
             _lib = lib
     return _lib
 
@@ -261,6 +272,26 @@ class LayerPotential:
     def export_tree(self):
         return qbx_export_tree(self.handle, self.n_src, self.n_centres, self.n_targets)
 
+    def autotune(self, target_xy, on_surface_node=None, on_surface_side=None, p_fmm=0,
+                 p_add=-1, eps_assoc=0.1, precision=QBX_FP64, has_S=True, has_D=True, reps=3):
+        """Times direct and FMM plans (qbx_autotune) and keeps the fastest built."""
+        txy = _host_f64(target_xy)
+        n = txy.shape[0]
+        osn = None if on_surface_node is None else np.ascontiguousarray(on_surface_node,
+                                                                        np.int64)
+        oss = None if on_surface_side is None else np.ascontiguousarray(on_surface_side,
+                                                                        np.int8)
+        assoc = np.empty(n, dtype=np.int32)
+        d = qbx_tree_desc(n, ptr(txy), ptr(osn), ptr(oss), QBX_DIRECT, int(p_fmm), int(p_add),
+                          0, float(eps_assoc), ptr(assoc))
+        times = np.zeros(4)
+        chosen = np.zeros(1, np.int32)
+        _check(library().qbx_autotune(self.handle, ctypes.byref(d), int(precision),
+                                      int(bool(has_S)), int(bool(has_D)), int(reps), ptr(times),
+                                      ptr(chosen)))
+        self.n_targets = n
+        return assoc, times, int(chosen[0])
+
     def set_timing(self, on=True):
         qbx_set_timing(self.handle, on)
 
@@ -270,6 +301,52 @@ class LayerPotential:
     def close(self):
         if getattr(self, "handle", None):
             qbx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many planned LayerPotential objects evaluated together (qbx_batch_*): one
+    CUDA graph with concurrent branches. Densities / outputs are concatenated in
+    the order of `problems`."""
+
+    def __init__(self, problems, n_streams=16):
+        self.problems = list(problems)
+        arr = (_vp * len(self.problems))(*[p.handle for p in self.problems])
+        self._arr = arr
+        b = _vp()
+        _check(library().qbx_batch_create(len(self.problems), ctypes.cast(arr, _vp),
+                                          int(n_streams), ctypes.byref(b)))
+        self.handle = b
+        self.n_src = sum(p.n_src for p in self.problems)
+        self.n_targets = sum(p.n_targets for p in self.problems)
+
+    def eval(self, sigma_S=None, sigma_D=None, cS=None, cD=None, out=None,
+             precision=QBX_FP64, stream=None):
+        def prep(a):
+            if a is None or hasattr(a, "data_ptr"):
+                return a
+            return np.ascontiguousarray(a, dtype=np.complex128)
+        n = len(self.problems)
+        cs = None if cS is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(cS, np.complex128), (n,))).view(np.float64)
+        cd = None if cD is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(cD, np.complex128), (n,))).view(np.float64)
+        sigma_S, sigma_D = prep(sigma_S), prep(sigma_D)
+        if out is None:
+            out = np.empty(self.n_targets, dtype=np.complex128)
+        _check(library().qbx_batch_eval(self.handle, ptr(cs), ptr(sigma_S), ptr(cd),
+                                        ptr(sigma_D), ptr(out), int(precision), stream))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            library().qbx_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
