@@ -22,6 +22,7 @@
 // where (rho, theta) and (rho', theta') are polar coordinates of x-c and y-c.
 // Complex arrays are interleaved (re, im) doubles.
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -50,21 +51,42 @@ static cplx hankel1(int l, double x) {
   return (l < 0 && (m & 1)) ? -h : h;
 }
 
+// H_m(x) for m = 0..M into h[0..M] (M + 1 library call pairs); the value at a
+// negative order follows by reflection, see hankel_from().
+static void hankel_table(int M, double x, cplx* h) {
+  for (int m = 0; m <= M; ++m) h[m] = hankel1(m, x);
+}
+static inline cplx hankel_from(const cplx* h, int l) {
+  int m = l < 0 ? -l : l;
+  return (l < 0 && (m & 1)) ? -h[m] : h[m];
+}
+
 // n . grad_y [ H_l(k|y-c|) e^{i l arg(y-c)} ] at y, written out in polar
 // coordinates about c: e^{i l th} [ k H_l'(k r) (n . rhat) + (i l / r) H_l(k r) (n . thhat) ]
 // with H_l' = (H_{l-1} - H_{l+1}) / 2 (the derivative of Eq. (graf-coefficient)'s
 // kernel along the source normal, as needed for the double layer of Eq. (dlp)).
-static cplx dn_hankel_wave(int l, double k, double dx, double dy, double nx, double ny) {
+// h holds H_m(k r) for m = 0..|l|+1 (hankel_table).
+static cplx dn_hankel_wave(int l, const cplx* h, double k, double dx, double dy, double nx,
+                           double ny) {
   double r = std::sqrt(dx * dx + dy * dy);
   double th = std::atan2(dy, dx);
   double c = std::cos(th), s = std::sin(th);
   double n_rhat = nx * c + ny * s;
   double n_thhat = -nx * s + ny * c;
-  cplx h = hankel1(l, k * r);
-  cplx hp = 0.5 * (hankel1(l - 1, k * r) - hankel1(l + 1, k * r));
+  cplx hl = hankel_from(h, l);
+  cplx hp = 0.5 * (hankel_from(h, l - 1) - hankel_from(h, l + 1));
   cplx e = std::polar(1.0, l * th);
-  return e * (k * hp * n_rhat + (I * (double)l / r) * h * n_thhat);
+  return e * (k * hp * n_rhat + (I * (double)l / r) * hl * n_thhat);
 }
+
+// The sums over sources below are split into fixed blocks of kBlock sources;
+// each block is summed in source order and the block sums are added in block
+// order. The split depends only on the number of sources, so results do not
+// depend on the thread count, and a few centres or targets still keep every
+// core busy.
+static const int64_t kBlock = 2048;
+// Upper bound on the partial sums held at once (complex values).
+static const int64_t kPartialCap = (int64_t)1 << 22;
 
 static inline cplx load_c(const double* a, int64_t i) { return cplx(a[2 * i], a[2 * i + 1]); }
 
@@ -130,27 +152,44 @@ void oracle_qbx_coefficients(int64_t n_src, const double* src_xy, const double* 
                              int64_t n_ctr, const double* ctr_xy, int p, double* alpha_out) {
   const cplx cS(cS_re, cS_im), cD(cD_re, cD_im);
   const int P = 2 * p + 1;
-#pragma omp parallel for schedule(dynamic, 4)
-  for (int64_t c = 0; c < n_ctr; ++c) {
-    std::vector<cplx> acc(P, cplx(0.0, 0.0));
-    for (int64_t j = 0; j < n_src; ++j) {
-      double dx = src_xy[2 * j] - ctr_xy[2 * c];
-      double dy = src_xy[2 * j + 1] - ctr_xy[2 * c + 1];
-      double r = std::sqrt(dx * dx + dy * dy);
-      double th = std::atan2(dy, dx);
-      for (int l = -p; l <= p; ++l) {
-        cplx term(0.0, 0.0);
-        if (sigma_S) term += cS * load_c(sigma_S, j) * hankel1(l, k * r) * std::polar(1.0, l * th);
-        if (sigma_D)
-          term += cD * load_c(sigma_D, j) *
-                  dn_hankel_wave(l, k, dx, dy, src_normal[2 * j], src_normal[2 * j + 1]);
-        acc[l + p] += weight[j] * term;
+  const int64_t nb = n_src > 0 ? (n_src + kBlock - 1) / kBlock : 0;
+  const int64_t group = std::max<int64_t>(1, kPartialCap / std::max<int64_t>(1, nb * P));
+  for (int64_t c0 = 0; c0 < n_ctr; c0 += group) {
+    const int64_t c1 = std::min(n_ctr, c0 + group);
+    std::vector<cplx> part((size_t)((c1 - c0) * nb * P), cplx(0.0, 0.0));
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int64_t c = c0; c < c1; ++c) {
+      for (int64_t blk = 0; blk < nb; ++blk) {
+        cplx* acc = part.data() + ((c - c0) * nb + blk) * P;
+        std::vector<cplx> h(p + 2);
+        const int64_t j1 = std::min(n_src, (blk + 1) * kBlock);
+        for (int64_t j = blk * kBlock; j < j1; ++j) {
+          double dx = src_xy[2 * j] - ctr_xy[2 * c];
+          double dy = src_xy[2 * j + 1] - ctr_xy[2 * c + 1];
+          double r = std::sqrt(dx * dx + dy * dy);
+          double th = std::atan2(dy, dx);
+          hankel_table(sigma_D ? p + 1 : p, k * r, h.data());
+          for (int l = -p; l <= p; ++l) {
+            cplx term(0.0, 0.0);
+            if (sigma_S)
+              term += cS * load_c(sigma_S, j) * hankel_from(h.data(), l) * std::polar(1.0, l * th);
+            if (sigma_D)
+              term += cD * load_c(sigma_D, j) *
+                      dn_hankel_wave(l, h.data(), k, dx, dy, src_normal[2 * j],
+                                     src_normal[2 * j + 1]);
+            acc[l + p] += weight[j] * term;
+          }
+        }
       }
     }
-    for (int l = 0; l < P; ++l) {
-      cplx a = 0.25 * I * acc[l];
-      alpha_out[2 * (c * P + l)] = a.real();
-      alpha_out[2 * (c * P + l) + 1] = a.imag();
+    for (int64_t c = c0; c < c1; ++c) {
+      for (int l = 0; l < P; ++l) {
+        cplx sum(0.0, 0.0);
+        for (int64_t blk = 0; blk < nb; ++blk) sum += part[((c - c0) * nb + blk) * P + l];
+        cplx a = 0.25 * I * sum;
+        alpha_out[2 * (c * P + l)] = a.real();
+        alpha_out[2 * (c * P + l) + 1] = a.imag();
+      }
     }
   }
 }
@@ -164,24 +203,38 @@ void oracle_direct_potential(int64_t n_src, const double* src_xy, const double* 
                              double cS_re, double cS_im, double cD_re, double cD_im, double k,
                              int64_t n_tgt, const double* tgt_xy, double* u_out) {
   const cplx cS(cS_re, cS_im), cD(cD_re, cD_im);
-#pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t t = 0; t < n_tgt; ++t) {
-    cplx acc(0.0, 0.0);
-    for (int64_t j = 0; j < n_src; ++j) {
-      double dx = tgt_xy[2 * t] - src_xy[2 * j];
-      double dy = tgt_xy[2 * t + 1] - src_xy[2 * j + 1];
-      double r = std::sqrt(dx * dx + dy * dy);
-      cplx term(0.0, 0.0);
-      if (sigma_S) term += cS * load_c(sigma_S, j) * hankel1(0, k * r);
-      if (sigma_D) {
-        double ndotd = src_normal[2 * j] * dx + src_normal[2 * j + 1] * dy;
-        term += cD * load_c(sigma_D, j) * k * hankel1(1, k * r) * (ndotd / r);
+  const int64_t nb = n_src > 0 ? (n_src + kBlock - 1) / kBlock : 0;
+  const int64_t group = std::max<int64_t>(1, kPartialCap / std::max<int64_t>(1, nb));
+  for (int64_t t0 = 0; t0 < n_tgt; t0 += group) {
+    const int64_t t1 = std::min(n_tgt, t0 + group);
+    std::vector<cplx> part((size_t)((t1 - t0) * nb), cplx(0.0, 0.0));
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int64_t t = t0; t < t1; ++t) {
+      for (int64_t blk = 0; blk < nb; ++blk) {
+        cplx acc(0.0, 0.0);
+        const int64_t j1 = std::min(n_src, (blk + 1) * kBlock);
+        for (int64_t j = blk * kBlock; j < j1; ++j) {
+          double dx = tgt_xy[2 * t] - src_xy[2 * j];
+          double dy = tgt_xy[2 * t + 1] - src_xy[2 * j + 1];
+          double r = std::sqrt(dx * dx + dy * dy);
+          cplx term(0.0, 0.0);
+          if (sigma_S) term += cS * load_c(sigma_S, j) * hankel1(0, k * r);
+          if (sigma_D) {
+            double ndotd = src_normal[2 * j] * dx + src_normal[2 * j + 1] * dy;
+            term += cD * load_c(sigma_D, j) * k * hankel1(1, k * r) * (ndotd / r);
+          }
+          acc += weight[j] * term;
+        }
+        part[(t - t0) * nb + blk] = acc;
       }
-      acc += weight[j] * term;
     }
-    acc *= 0.25 * I;
-    u_out[2 * t] = acc.real();
-    u_out[2 * t + 1] = acc.imag();
+    for (int64_t t = t0; t < t1; ++t) {
+      cplx acc(0.0, 0.0);
+      for (int64_t blk = 0; blk < nb; ++blk) acc += part[(t - t0) * nb + blk];
+      acc *= 0.25 * I;
+      u_out[2 * t] = acc.real();
+      u_out[2 * t + 1] = acc.imag();
+    }
   }
 }
 
