@@ -119,23 +119,56 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def flop_model(stats, p, p_box, has_S, has_D):
-    """Algorithmic FP64 flops per kernel class (complex FMA = 8, base Hankel values
-    charged 0). P = 2p+1 QBX terms, Q = 2 p_box + 1 box terms."""
-    P, Q = 2 * p + 1, 2 * p_box + 1
+def flop_model(lp, stats, p, has_S, has_D, assoc, fmm):
+    """Algorithmic flops per kernel class (complex multiply-add = 8 flops; the
+    Bessel/Hankel values a kernel generates are not charged). P = 2p+1 QBX
+    terms; a box on tree level l carries Q_l = 2 pb_l + 1 terms (per-level
+    orders), and every translation is charged with the orders of its boxes."""
+    P = 2 * p + 1
     lay = (1 if has_S else 0) + (1 if has_D else 0)
     f = {}
     f["p2qbxl"] = stats["p2qbxl_pairs"] * ((18 * P if has_S else 0) + (10 * P if has_D else 0))
     f["p2p"] = stats["p2p_pairs"] * 8 * lay
     f["qbxl2p"] = stats["n_qbx_targets"] * 16 * P
-    f["m2l"] = stats["v_pairs"] * 8 * Q * Q
-    f["m2qbxl"] = stats["m2qbxl_pairs"] * 8 * Q * P
-    f["m2p"] = stats["m2p_pairs"] * 16 * Q
-    f["l2qbxl"] = stats["n_centres"] * 8 * Q * P
-    f["l2p"] = stats["n_targets"] * 16 * Q
-    f["p2m"] = stats["n_sources"] * 16 * Q * lay
-    f["p2l"] = stats["p2l_pairs"] * 16 * Q * lay
-    f["m2m"] = f["l2l"] = stats["m2m_l2l"] * 8 * Q * Q // 2
+    if not fmm:
+        return f
+    t = lp.export_tree()
+    pbl = lp.box_orders().astype(np.int64)
+    lev = t["level"].astype(np.int64)
+    nb = lev.size
+    Qb = 2 * pbl[lev] + 1
+    child = t["child"]
+    rng = t["range"].astype(np.int64)
+    nsrc = rng[:, 0, 1] - rng[:, 0, 0]
+    nctr = rng[:, 1, 1] - rng[:, 1, 0]
+    # direct (non-QBX) targets per box, from the sorted target order
+    direct = (assoc[t["perm_tgt"][:lp.n_targets]] < 0).astype(np.int64)
+    cdir = np.concatenate([[0], np.cumsum(direct)])
+    ndir = cdir[rng[:, 2, 1]] - cdir[rng[:, 2, 0]]
+    leaf = np.all(child < 0, axis=1)
+    info = t["info"]
+    base = np.concatenate([[0], np.cumsum(info[2:6])]).astype(np.int64)
+    def entries(i):  # (box, entry) pairs of list i in U, V, W, X order
+        cnt = np.diff(t["off"][i]).astype(np.int64)
+        own = np.repeat(np.arange(nb), cnt)
+        return own, t["idx"][base[i]:base[i] + cnt.sum()].astype(np.int64)
+    vb, _ = entries(1)
+    f["m2l"] = 8 * int(np.sum(Qb[vb] ** 2))
+    parent = np.full(nb, -1, np.int64)
+    for q in range(4):
+        has = child[:, q] >= 0
+        parent[child[has, q]] = np.nonzero(has)[0]
+    mm = (lev >= 3) & (parent >= 0)
+    f["m2m"] = f["l2l"] = 8 * int(np.sum(Qb[mm] * Qb[parent[mm]]))
+    f["p2m"] = 16 * lay * int(np.sum((nsrc * Qb)[leaf & (lev >= 2)]))
+    xb, xc = entries(3)
+    f["p2l"] = 16 * lay * int(np.sum(Qb[xb] * nsrc[xc]))
+    wb, wc = entries(2)
+    wq = np.bincount(wb, weights=Qb[wc], minlength=nb)
+    f["m2qbxl"] = 8 * P * int(np.sum((nctr * wq)[leaf]))
+    f["m2p"] = 16 * int(np.sum((ndir * wq)[leaf]))
+    f["l2qbxl"] = 8 * P * int(np.sum((nctr * Qb)[leaf]))
+    f["l2p"] = 16 * int(np.sum((ndir * Qb)[leaf]))
     return f
 
 
@@ -151,8 +184,8 @@ def run_ours(args, w, ws, rank, local):
     prec = qbx.QBX_MIXED if args.precision == "mixed" else qbx.QBX_FP64
     lp = qbx.LayerPotential(g.as_dict(), w["p"], sides=w["sides"])
     t0 = time.perf_counter()
-    lp.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"], mode=mode,
-             p_fmm=w["p_fmm"], p_add=-1, n_max=args.n_max, eps_assoc=w["eps_assoc"])
+    assoc = lp.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"], mode=mode,
+                     p_fmm=w["p_fmm"], p_add=-1, n_max=args.n_max, eps_assoc=w["eps_assoc"])
     tree_s = time.perf_counter() - t0
     n_t = lp.n_targets
     sS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).to(dev) if w["sigma_S"] is not None else None
@@ -200,7 +233,8 @@ def run_ours(args, w, ws, rank, local):
             per.setdefault(kname, []).append(ms)
     lp.set_timing(False)
     per = {k: statistics.median(v) for k, v in per.items() if max(v) > 0}
-    flops = flop_model(stats, w["p"], stats["p_box"], sS is not None, sD is not None)
+    flops = flop_model(lp, stats, w["p"], sS is not None, sD is not None, assoc,
+                       mode == qbx.QBX_FMM)
     dom = max(per, key=per.get) if per else None
     roof = None
     if dom:
@@ -242,7 +276,8 @@ def run_ours(args, w, ws, rank, local):
                                    "(8192 sources, 16384 centres), D+ikS, p=12, p_fmm=20, "
                                    "316x316 grid targets" % w["name"],
                        "mode": args.mode, "precision": args.precision, "n_targets": n_t,
-                       "n_qbx_targets": stats["n_qbx_targets"], "p_box": stats["p_box"],
+                       "n_qbx_targets": stats["n_qbx_targets"],
+                       "box_orders": [int(x) for x in lp.box_orders()] if mode == qbx.QBX_FMM else None,
                        "n_boxes": stats["n_boxes"], "tree_build_s": tree_s,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single"},

@@ -102,8 +102,10 @@ qbx_status qbx_geometry_create(const qbx_geometry_desc *desc, qbx_handle **out);
  * node of panel k is <= h_k/4 is an association failure; the rest use direct
  * quadrature.
  * mode: QBX_DIRECT (all pairs) or QBX_FMM (quadtree, Sec. 7).
- * p_fmm, p_add: box expansion order p_box = p_fmm + p_add; p_add < 0 selects
- * Table 2 of the paper (p <= 8) extended by p_add = 2.5 p beyond it.
+ * p_fmm, p_add: box expansion orders (Sec. 8.3): p_fmm on the finest tree
+ * level, larger orders on coarser levels whose boxes span wavelengths (see
+ * qbx_fmm_level_orders), each plus p_add; p_add < 0 selects Table 2 of the
+ * paper (p <= 8) extended by p_add = 2.5 p beyond it.
  * n_max: particles per leaf (sources + centres + targets), 0 => 64.
  * assoc_out (optional, [n_targets] int32) receives the centre of every target
  * (-1: direct quadrature).
@@ -151,13 +153,15 @@ const char *qbx_last_error(void);
 /*
  * Plan statistics after qbx_tree_build (for logging and benchmarks):
  * stats[0] n_sources, [1] n_centres, [2] n_targets, [3] n_qbx_targets,
- * [4] n_boxes, [5] n_leaves, [6] tree depth, [7] p_box, [8] U-list pairs
+ * [4] n_boxes, [5] n_leaves, [6] tree depth, [7] box order on the finest
+ * level (p_fmm + p_add), [8] U-list pairs
  * (leaf, leaf), [9] V-list pairs, [10] W-list pairs, [11] X-list pairs,
  * [12] source-centre pairs evaluated directly (P2QBXL), [13] source-target
  * pairs evaluated directly (P2P), [14] (box, centre) pairs of M2QBXL,
  * [15] (box, target) pairs of M2P, [16] kernel launches of the last eval,
  * [17] sources in X-list boxes summed over boxes (P2L pairs), [18] M2M plus
- * L2L translations, [19] reserved. Unused entries are 0. n_stats >= 20.
+ * L2L translations, [19] largest box order over the levels. Unused entries
+ * are 0. n_stats >= 20.
  */
 qbx_status qbx_get_stats(const qbx_handle *h, int64_t *stats, int32_t n_stats);
 
@@ -180,7 +184,7 @@ int32_t qbx_get_stage_times(qbx_handle *h, double *times_ms, int32_t n_times);
  * and Sec. 7.2, Stage 1, and its U, V, W, X lists). All outputs are HOST
  * memory; any pointer may be NULL (skipped).
  *   info[8]: [0] n_boxes, [1] n_levels, [2..5] entries of the U, V, W, X
- *            lists, [6] p_box, [7] n_leaves.
+ *            lists, [6] box order on the finest level, [7] n_leaves.
  *   root[3]: x0, y0, side of the root square [x0, x0+side] x [y0, y0+side].
  *   box_level [n_boxes]; box_ij [n_boxes][2] integer position at the box's
  *   level; box_child [n_boxes][4] (-1: none; quadrant q = ix&1 + 2(iy&1));
@@ -196,6 +200,31 @@ qbx_status qbx_export_tree(const qbx_handle *h, int64_t *info, double *root, int
                            int32_t *box_ij, int32_t *box_child, int32_t *box_range,
                            int32_t *lists_off, int32_t *lists_idx, int32_t *perm_src,
                            int32_t *perm_ctr, int32_t *perm_tgt);
+
+/*
+ * The box order of every level of the handle's FMM plan (as computed by
+ * qbx_fmm_level_orders for its tree): pb_out int32 [n], entries past the
+ * tree's depth set to 0. Errors: QBX_ERR_STATE if no FMM plan exists.
+ */
+qbx_status qbx_get_box_orders(const qbx_handle *h, int32_t *pb_out, int32_t n);
+
+/*
+ * Box expansion orders of a quadtree level by level (Sec. 8.3, "Maintaining
+ * Expansion Accuracy"). Level l has boxes of side root_side / 2^l and
+ * half-side R_l; its outgoing order is the smallest p with
+ *   max_{n > p} |H_n(3 k R_l)| max_{y <= sqrt2 k R_l} |J_n(y)| <= eps,
+ * the bound the paper states for sources within sqrt2 R of a box centre and
+ * targets beyond 3R. eps is the value of that bound for n > p_fmm at
+ * k R = min(k R_finest, 1) (R_finest: half-side on level n_levels - 1), so
+ * the finest level gets p_fmm itself unless its boxes exceed k R = 1.
+ * pb_out[l] (int32 [n_levels]) receives that order plus p_add for levels
+ * l >= 2 and 0 for levels 0 and 1 (no well-separated boxes there).
+ * Host computation only. Errors: QBX_ERR_ARG for k <= 0, root_side <= 0,
+ * n_levels outside 1..25, p_fmm < 1, p_add < 0, or a level needing an order
+ * above 1200 (boxes spanning too many wavelengths).
+ */
+qbx_status qbx_fmm_level_orders(double k, double root_side, int32_t n_levels, int32_t p_fmm,
+                                int32_t p_add, int32_t *pb_out);
 
 /*
  * Measured plan selection. Builds the plan of `desc` (targets, association)

@@ -23,6 +23,8 @@
 // kernel in the source).
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <set>
 #include <vector>
 
 #include "special.cuh"
@@ -41,6 +43,13 @@ constexpr double kLeafOverRadius = 4.0;
 constexpr double kW = 0.6;
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
+// opt-in shared memory per block of the current device (set by configure_kernels)
+int g_smem_optin = 48 * 1024;
+#define TRY_MIXED(x)                    \
+  do {                                  \
+    qbx_status s_ = (x);                \
+    if (s_ != QBX_OK) return s_;        \
+  } while (0)
 
 struct Fmm {
   // boxes
@@ -63,21 +72,27 @@ struct Fmm {
   const double2* txy;
   const int* tid;
   const int* tassoc;
-  // tables
+  // orders and tables (box order pb_l per level; Q_l = 2 pb_l + 1 coefficients)
+  const int* lpb;        // [n_levels]
+  const long long* eoff; // [n_boxes] first coefficient of each box in mpole / local
   const double* scale;   // [n_levels]
-  const double* pw;      // [n_levels][2pb+3] s^j
-  const double* ipw;     // [n_levels][pb+2]  s^-j
-  const cd* t_m2l;       // [n_levels][49][4pb+1]
-  const cd* t_m2m;       // [n_levels][4][4pb+1]
-  const cd* t_l2l;       // [n_levels][4][4pb+1]
+  const double* pw;      // [n_levels][2 pbmax + 3] s^j
+  const double* ipw;     // [n_levels][pbmax + 2]  s^-j
+  const cd* t_m2l;       // [n_levels][49][4 pbmax + 1], order m stored at m + 2 pbmax
+  const cd* t_m2m;       // [n_levels][4][4 pbmax + 1]
+  const cd* t_l2l;       // [n_levels][4][4 pbmax + 1]
   cd* mpole;
   cd* local;
   double k, side;
-  int pb, Q, p, n_levels, has_S, has_D;
+  int pbmax, p, n_levels, has_S, has_D;
 };
 
-__device__ __forceinline__ const double* pw_row(const Fmm& F, int l) { return F.pw + (size_t)l * (2 * F.pb + 3); }
-__device__ __forceinline__ const double* ipw_row(const Fmm& F, int l) { return F.ipw + (size_t)l * (F.pb + 2); }
+__device__ __forceinline__ const double* pw_row(const Fmm& F, int l) { return F.pw + (size_t)l * (2 * F.pbmax + 3); }
+__device__ __forceinline__ const double* ipw_row(const Fmm& F, int l) { return F.ipw + (size_t)l * (F.pbmax + 2); }
+// Centred translation table of (level l, item): entry m at [m].
+__device__ __forceinline__ const cd* table(const Fmm& F, const cd* t, int items, int l, int item) {
+  return t + ((size_t)l * items + item) * (4 * F.pbmax + 1) + 2 * F.pbmax;
+}
 
 // Unnormalised Miller recurrence for J_0..J_M of x into row[0..M]; returns the
 // normalisation (divide by it). Rescales the stored part when values grow.
@@ -113,23 +128,26 @@ __device__ double miller_row(double x, int M, double* row, int stride) {
 
 // ---------------------------------------------------------------- translation tables
 // One thread per (level, item): items 0..48 M2L offset classes, 49..52 M2M
-// quadrants, 53..56 L2L quadrants.
-__global__ void tables_kernel(int n_levels, double side, double k, int pb,
-                              const double* __restrict__ scale, cd* __restrict__ t_m2l,
-                              cd* __restrict__ t_m2m, cd* __restrict__ t_l2l,
-                              double* __restrict__ jwork) {
+// quadrants, 53..56 L2L quadrants. Rows have stride 4 pbmax + 1 with order m
+// at m + 2 pbmax; only the orders a level's translations read are written:
+// |m| <= 2 pb_l for M2L, |m| <= pb_l + pb_{l+1} for M2M / L2L. Levels 0 and 1
+// carry no expansions.
+__global__ void tables_kernel(int n_levels, double side, double k, int pbmax,
+                              const int* __restrict__ lpb, const double* __restrict__ scale,
+                              cd* __restrict__ t_m2l, cd* __restrict__ t_m2m,
+                              cd* __restrict__ t_l2l, double* __restrict__ jwork) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_levels * 57) return;
   const int l = g / 57, item = g % 57;
-  const int T = 4 * pb + 1, M = 2 * pb;
+  const int TS = 4 * pbmax + 1, C = 2 * pbmax;
+  const int pb = lpb[l];
+  if (l < 2 || pb == 0) return;
   const double sl = side / (double)(1 << l);
   if (item < 49) {
-    cd* out = t_m2l + ((size_t)l * 49 + item) * T;
+    cd* out = t_m2l + ((size_t)l * 49 + item) * TS + C;
     const int dx = item / 7 - 3, dy = item % 7 - 3;  // (ix_b - ix_c, iy_b - iy_c)
-    if (l < 2 || max(abs(dx), abs(dy)) < 2) {
-      for (int m = 0; m < T; ++m) out[m] = mk(0.0, 0.0);
-      return;
-    }
+    if (max(abs(dx), abs(dy)) < 2) return;          // not a V-list offset
+    const int M = 2 * pb;
     const double s = scale[l];
     const double Dx = dx * sl, Dy = dy * sl, r = sqrt(Dx * Dx + Dy * Dy), x = k * r;
     const cd e1 = mk(Dx / r, Dy / r);
@@ -137,13 +155,12 @@ __global__ void tables_kernel(int n_levels, double side, double k, int pb,
     hankel01(x, h0, h1);
     cd hm1 = h0, hm = cscale(h1, s);  // scaled H_m s^m
     cd e = mk(1.0, 0.0);
-    out[M] = h0;
+    out[0] = h0;
     for (int m = 1; m <= M; ++m) {
       e = cmul(e, e1);
-      const cd hh = m == 1 ? hm : hm;
-      out[M + m] = cmul(hh, e);
+      out[m] = cmul(hm, e);
       const double sg = (m & 1) ? -1.0 : 1.0;
-      out[M - m] = cscale(cmul(hh, cconj(e)), sg);
+      out[-m] = cscale(cmul(hm, cconj(e)), sg);
       // next: H_{m+1} s^{m+1} = (2m/x) s H_m s^m - s^2 H_{m-1} s^{m-1}
       const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
       hm1 = hm;
@@ -151,18 +168,16 @@ __global__ void tables_kernel(int n_levels, double side, double k, int pb,
     }
     return;
   }
+  if (l + 1 >= n_levels) return;
   const bool m2m = item < 53;
   const int c = m2m ? item - 49 : item - 53;
-  cd* out = (m2m ? t_m2m : t_l2l) + ((size_t)l * 4 + c) * T;
-  if (l + 1 >= n_levels) {
-    for (int m = 0; m < T; ++m) out[m] = mk(0.0, 0.0);
-    return;
-  }
+  cd* out = (m2m ? t_m2m : t_l2l) + ((size_t)l * 4 + c) * TS + C;
+  const int M = pb + lpb[l + 1];
   // child centre minus parent centre, child side = sl/2
   const double cs = 0.5 * sl;
   const double dx = ((c & 1) - 0.5) * cs, dy = ((c >> 1) - 0.5) * cs;
   const double r = sqrt(dx * dx + dy * dy), x = k * r;
-  double* J = jwork + (size_t)g * (M + 1);
+  double* J = jwork + (size_t)g * (2 * pbmax + 1);
   const double norm = miller_row(x, M, J, 1);
   const cd e1 = mk(dx / r, dy / r);
   cd e = mk(1.0, 0.0);
@@ -170,30 +185,33 @@ __global__ void tables_kernel(int n_levels, double side, double k, int pb,
     const double j = J[m] / norm;
     const double sg = (m & 1) ? -1.0 : 1.0;
     if (m2m) {  // conj(V_m) = J_m e^{-im th}; conj(V_{-m}) = (-1)^m J_m e^{im th}
-      out[M + m] = cscale(cconj(e), j);
-      out[M - m] = cscale(e, sg * j);
+      out[m] = cscale(cconj(e), j);
+      out[-m] = cscale(e, sg * j);
     } else {    // (-1)^m V_m = (-1)^m J_m e^{im th}; (-1)^m V_{-m} = J_m e^{-im th}
-      out[M + m] = cscale(e, sg * j);
-      out[M - m] = cscale(cconj(e), j);
+      out[m] = cscale(e, sg * j);
+      out[-m] = cscale(cconj(e), j);
     }
     e = cmul(e, e1);
   }
 }
 
-__global__ void powers_kernel(int n_levels, int pb, const double* __restrict__ scale,
-                              double* __restrict__ pw, double* __restrict__ ipw) {
+// Per level: pw[j] = s^j for j <= 2 pb_l + 2, ipw[j] = s^-j for j <= pb_l + 1 (rest 0).
+__global__ void powers_kernel(int n_levels, int pbmax, const int* __restrict__ lpb,
+                              const double* __restrict__ scale, double* __restrict__ pw,
+                              double* __restrict__ ipw) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_levels) return;
   const double s = scale[l];
+  const int pb = lpb[l];
   double a = 1.0;
-  for (int j = 0; j < 2 * pb + 3; ++j) {
-    pw[(size_t)l * (2 * pb + 3) + j] = a;
+  for (int j = 0; j < 2 * pbmax + 3; ++j) {
+    pw[(size_t)l * (2 * pbmax + 3) + j] = j <= 2 * pb + 2 ? a : 0.0;
     a *= s;
   }
   a = 1.0;
-  for (int j = 0; j < pb + 2; ++j) {
-    ipw[(size_t)l * (pb + 2) + j] = a;
-    a /= s;
+  for (int j = 0; j < pbmax + 2; ++j) {
+    ipw[(size_t)l * (pbmax + 2) + j] = j <= pb + 1 ? a : 0.0;
+    if (j <= pb + 1) a /= s;
   }
 }
 
@@ -208,25 +226,38 @@ __global__ void gather_strengths_kernel(int64_t n, const int* __restrict__ perm,
 }
 
 // ---------------------------------------------------------------- P2M (Stage 2)
-// CTA per leaf. Threads 0..kChunk-1 fill one row each with
+// Shared memory of the source-row kernels (P2M, P2L): an accumulator per output
+// order, then up to kChunk rows of 2 pb + 3 table values and three strengths.
+__host__ __device__ inline size_t rows_smem(int pb, int chunk) {
+  return ((size_t)(2 * pb + 1) + (size_t)chunk * (2 * pb + 6)) * sizeof(cd);
+}
+__device__ inline int rows_chunk(int pb, size_t sm_bytes) {
+  const size_t per = (size_t)(2 * pb + 6) * sizeof(cd);
+  const size_t avail = sm_bytes - (size_t)(2 * pb + 1) * sizeof(cd);
+  return (int)min((size_t)kChunk, avail / per);
+}
+
+// CTA per leaf. Threads 0..chunk-1 fill one row each with
 // conj(V_m(y - m_b)) / s^m, m = 0..pb+1; then all threads reduce over the rows.
-__global__ void __launch_bounds__(kThreads) p2m_kernel(Fmm F, const int* __restrict__ leaves) {
+__global__ void __launch_bounds__(kThreads) p2m_kernel(Fmm F, const int* __restrict__ leaves,
+                                                       unsigned sm_bytes) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, RW = 2 * pb + 3;   // row: conj(V_t)/s^|t|, t = -(pb+1)..pb+1
-  cd* rows = smem;                        // [kChunk][RW]
-  cd* sq = rows + kChunk * RW;            // [kChunk]
-  cd* sa = sq + kChunk;                   // [kChunk]  d (k/2) conj(nu)
-  cd* sb = sa + kChunk;                   // [kChunk]  d (k/2) nu
   const int b = leaves[blockIdx.x];
-  const int2 r = F.rsrc[b];
   const int l = F.level[b];
+  const int pb = F.lpb[l], Q = 2 * pb + 1, RW = 2 * pb + 3;  // row: conj(V_t)/s^|t|, |t| <= pb+1
+  const int chunk = rows_chunk(pb, sm_bytes);
+  cd* acc = smem;                         // [Q]
+  cd* rows = acc + Q;                     // [chunk][RW]
+  cd* sq = rows + chunk * RW;             // [chunk]
+  cd* sa = sq + chunk;                    // [chunk]  d (k/2) conj(nu)
+  cd* sb = sa + chunk;                    // [chunk]  d (k/2) nu
+  const int2 r = F.rsrc[b];
   const double s = F.scale[l], is = 1.0 / s;
   const double2 m = F.centre[b];
   const double hk = 0.5 * F.k;
-  cd acc[2];
-  acc[0] = acc[1] = mk(0.0, 0.0);
-  for (int base = r.x; base < r.y; base += kChunk) {
-    const int cnt = min(kChunk, r.y - base);
+  for (int i = threadIdx.x; i < Q; i += kThreads) acc[i] = mk(0.0, 0.0);
+  for (int base = r.x; base < r.y; base += chunk) {
+    const int cnt = min(chunk, r.y - base);
     if ((int)threadIdx.x < cnt) {
       const int i = base + threadIdx.x;
       const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
@@ -252,63 +283,64 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(Fmm F, const int* __restr
       sb[threadIdx.x] = cmul(dk, nu);
     }
     __syncthreads();
-    for (int o = 0; o < 2; ++o) {
-      const int n = (int)threadIdx.x + o * kThreads - pb;
-      if (n > pb) continue;
+    for (int n = (int)threadIdx.x - pb; n <= pb; n += kThreads) {
       const int an = abs(n);
       // conj(V_{n-+1})/s^|n| = row[n-+1] s^{|n-+1| - |n|}
       const double fm = (abs(n - 1) > an) ? s : is;
       const double fp = (abs(n + 1) > an) ? s : is;
+      cd a = acc[n + pb];
       for (int j = 0; j < cnt; ++j) {
         const cd* row = rows + j * RW + (pb + 1);
-        if (F.has_S) cfma(acc[o], sq[j], row[n]);
+        if (F.has_S) cfma(a, sq[j], row[n]);
         if (F.has_D) {
-          cfma(acc[o], cscale(sa[j], fm), row[n - 1]);
-          cfma(acc[o], cscale(sb[j], -fp), row[n + 1]);
+          cfma(a, cscale(sa[j], fm), row[n - 1]);
+          cfma(a, cscale(sb[j], -fp), row[n + 1]);
         }
       }
+      acc[n + pb] = a;
     }
     __syncthreads();
   }
-  for (int o = 0; o < 2; ++o) {
-    const int n = (int)threadIdx.x + o * kThreads - pb;
-    if (n <= pb) F.mpole[(size_t)b * F.Q + (n + pb)] = acc[o];
-  }
+  cd* dst = F.mpole + F.eoff[b];
+  for (int i = threadIdx.x; i < Q; i += kThreads) dst[i] = acc[i];
 }
 
 // ---------------------------------------------------------------- M2M (Stage 2)
+// CTA per parent (level l, order pp) over its children (level l+1, order pc):
+// a_s = sum_{|n| <= pc} a'_n conj(V_{s-n}), |s| <= pp.
+__host__ __device__ inline size_t m2m_smem(int pp, int pc) {
+  return ((size_t)(2 * pc + 1) + (size_t)(2 * (pp + pc) + 1) + (size_t)(2 * pp + 1)) * sizeof(cd);
+}
+
 __global__ void __launch_bounds__(kThreads) m2m_kernel(Fmm F, const int* __restrict__ boxes) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, Q = F.Q, T = 4 * pb + 1;
-  cd* a = smem;        // [Q]
-  cd* t = a + Q;       // [T]
   const int b = boxes[blockIdx.x];
   const int l = F.level[b];
+  const int pp = F.lpb[l], pc = F.lpb[l + 1];
+  const int Qp = 2 * pp + 1, Qc = 2 * pc + 1, M = pp + pc, T = 2 * M + 1;
+  cd* a = smem;        // [Qc]
+  cd* t = a + Qc;      // [T]  t[m + M] = conj(V_m)
+  cd* acc = t + T;     // [Qp]
   const double* pwc = pw_row(F, l + 1);
   const double* ipp = ipw_row(F, l);
-  cd acc[2];
-  acc[0] = acc[1] = mk(0.0, 0.0);
+  for (int i = threadIdx.x; i < Qp; i += kThreads) acc[i] = mk(0.0, 0.0);
   for (int c = 0; c < 4; ++c) {
     const int d = F.child[4 * b + c];
     if (d < 0) continue;
-    for (int i = threadIdx.x; i < Q; i += kThreads)
-      a[i] = cscale(F.mpole[(size_t)d * Q + i], pwc[abs(i - pb)]);
-    const cd* tab = F.t_m2m + ((size_t)l * 4 + c) * T;
-    for (int i = threadIdx.x; i < T; i += kThreads) t[i] = tab[i];
+    const cd* mp = F.mpole + F.eoff[d];
+    for (int i = threadIdx.x; i < Qc; i += kThreads) a[i] = cscale(mp[i], pwc[abs(i - pc)]);
+    const cd* tab = table(F, F.t_m2m, 4, l, c);
+    for (int i = threadIdx.x; i < T; i += kThreads) t[i] = tab[i - M];
     __syncthreads();
-    for (int o = 0; o < 2; ++o) {
-      const int s = (int)threadIdx.x + o * kThreads - pb;
-      if (s > pb) continue;
+    for (int s = (int)threadIdx.x - pp; s <= pp; s += kThreads) {
       cd sum = mk(0.0, 0.0);
-      for (int n = -pb; n <= pb; ++n) cfma(sum, t[s - n + 2 * pb], a[n + pb]);
-      acc[o] = cadd(acc[o], sum);
+      for (int n = -pc; n <= pc; ++n) cfma(sum, t[s - n + M], a[n + pc]);
+      acc[s + pp] = cadd(acc[s + pp], sum);
     }
     __syncthreads();
   }
-  for (int o = 0; o < 2; ++o) {
-    const int s = (int)threadIdx.x + o * kThreads - pb;
-    if (s <= pb) F.mpole[(size_t)b * Q + s + pb] = cscale(acc[o], ipp[abs(s)]);
-  }
+  cd* dst = F.mpole + F.eoff[b];
+  for (int i = threadIdx.x; i < Qp; i += kThreads) dst[i] = cscale(acc[i], ipp[abs(i - pp)]);
 }
 
 // ---------------------------------------------------------------- M2L (Stage 4)
@@ -323,38 +355,40 @@ __device__ __forceinline__ cd cdot(const cd* w, const cd* a, int n0, int n1) {
   return s;
 }
 
+__host__ __device__ inline size_t m2l_smem(int pb) {
+  return (size_t)(3 * (2 * pb + 1) + 4 * pb + 1) * sizeof(cd) + (size_t)(pb + 1) * sizeof(double);
+}
+
 __global__ void __launch_bounds__(kThreads) m2l_kernel(Fmm F, const int* __restrict__ boxes) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, Q = F.Q, T = 4 * pb + 1;
-  cd* a = smem;                       // [Q]   mh_n
-  cd* a2 = a + Q;                     // [Q]   mh_n s^{2|n|}
-  cd* w = a2 + Q;                     // [T]   What_m
-  double* p2 = (double*)(w + T);      // [pb+1] s^{2j}
   const int b = boxes[blockIdx.x];
   const int l = F.level[b];
+  const int pb = F.lpb[l], Q = 2 * pb + 1, T = 4 * pb + 1;
+  cd* a = smem;                       // [Q]   mh_n
+  cd* a2 = a + Q;                     // [Q]   mh_n s^{2|n|}
+  cd* w = a2 + Q;                     // [T]   What_m at m + 2 pb
+  cd* acc = w + T;                    // [Q]
+  double* p2 = (double*)(acc + Q);    // [pb+1] s^{2j}
   const double* pwl = pw_row(F, l);
   for (int j = threadIdx.x; j <= pb; j += kThreads) p2[j] = pwl[2 * j];
-  const int lo = (int)threadIdx.x - pb;  // output order of this thread (Q <= kThreads + ...)
-  cd acc = mk(0.0, 0.0), acc2 = mk(0.0, 0.0);
-  const int lo2 = lo + kThreads;         // second output when Q > kThreads
+  for (int i = threadIdx.x; i < Q; i += kThreads) acc[i] = mk(0.0, 0.0);
   __syncthreads();
   for (int e = F.voff[b]; e < F.voff[b + 1]; ++e) {
     const int c = F.vidx[e];
-    const cd* tab = F.t_m2l + ((size_t)l * 49 + F.vcls[e]) * T;
+    const cd* tab = table(F, F.t_m2l, 49, l, F.vcls[e]);
+    const cd* mp = F.mpole + F.eoff[c];
     for (int i = threadIdx.x; i < Q; i += kThreads) {
-      const cd v = F.mpole[(size_t)c * Q + i];
+      const cd v = mp[i];
       a[i] = v;
       a2[i] = cscale(v, p2[abs(i - pb)]);
     }
-    for (int i = threadIdx.x; i < T; i += kThreads) w[i] = tab[i];
+    for (int i = threadIdx.x; i < T; i += kThreads) w[i] = tab[i - 2 * pb];
     __syncthreads();
-    // Split of the n range by the sign of n relative to lo: same sign -> factor 1;
-    // opposite sign with |n| <= |lo| -> s^{2|n|} (folded into a2); |n| > |lo| -> s^{2|lo|}.
-    for (int o = 0; o < 2; ++o) {
-      const int L = o == 0 ? lo : lo2;
-      if (L > pb) continue;
+    // Split of the n range by the sign of n relative to L: same sign -> factor 1;
+    // opposite sign with |n| <= |L| -> s^{2|n|} (folded into a2); |n| > |L| -> s^{2|L|}.
+    for (int L = (int)threadIdx.x - pb; L <= pb; L += kThreads) {
       const cd* wl = w + L + 2 * pb;   // wl[n] = What_{n+L}
-      const cd* ac = a + pb;   // ac[n] = mh_n
+      const cd* ac = a + pb;           // ac[n] = mh_n
       const cd* ac2 = a2 + pb;
       cd same, near, far;
       if (L >= 0) {
@@ -368,40 +402,36 @@ __global__ void __launch_bounds__(kThreads) m2l_kernel(Fmm F, const int* __restr
       }
       cd sum = cadd(cadd(same, near), cscale(far, p2[abs(L)]));
       if (L & 1) sum = mk(-sum.x, -sum.y);
-      if (o == 0) acc = cadd(acc, sum); else acc2 = cadd(acc2, sum);
+      acc[L + pb] = cadd(acc[L + pb], sum);
     }
     __syncthreads();
   }
-  if (lo <= pb) {
-    cd* dst = F.local + (size_t)b * Q + lo + pb;
-    *dst = cadd(*dst, acc);
-  }
-  if (lo2 <= pb) {
-    cd* dst = F.local + (size_t)b * Q + lo2 + pb;
-    *dst = cadd(*dst, acc2);
-  }
+  cd* dst = F.local + F.eoff[b];
+  for (int i = threadIdx.x; i < Q; i += kThreads) dst[i] = cadd(dst[i], acc[i]);
 }
 
 // ---------------------------------------------------------------- P2L (Stage 6)
 // CTA per box with an X list: lh_l += s^|l| sum_j [q W_l + d (k/2)(nu W_{l-1} - conj(nu) W_{l+1})]
-__global__ void __launch_bounds__(kThreads) p2l_kernel(Fmm F, const int* __restrict__ boxes) {
+__global__ void __launch_bounds__(kThreads) p2l_kernel(Fmm F, const int* __restrict__ boxes,
+                                                       unsigned sm_bytes) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, RW = 2 * pb + 3;   // row: Wh_t for t = -(pb+1)..pb+1 at index t + pb + 1
-  cd* rows = smem;                        // [kChunk][RW]
-  cd* sq = rows + kChunk * RW;            // [kChunk]
-  cd* sa = sq + kChunk;                   // [kChunk]  A = d (k/2) nu
-  cd* sb = sa + kChunk;                   // [kChunk]  B = d (k/2) conj(nu)
   const int b = boxes[blockIdx.x];
   const int l = F.level[b];
+  const int pb = F.lpb[l], Q = 2 * pb + 1, RW = 2 * pb + 3;  // row: Wh_t, |t| <= pb+1
+  const int chunk = rows_chunk(pb, sm_bytes);
+  cd* acc = smem;                         // [Q]
+  cd* rows = acc + Q;                     // [chunk][RW]
+  cd* sq = rows + chunk * RW;             // [chunk]
+  cd* sa = sq + chunk;                    // [chunk]  A = d (k/2) nu
+  cd* sb = sa + chunk;                    // [chunk]  B = d (k/2) conj(nu)
   const double s = F.scale[l], is = 1.0 / s;
   const double2 m = F.centre[b];
   const double hk = 0.5 * F.k;
-  cd acc[2];
-  acc[0] = acc[1] = mk(0.0, 0.0);
+  for (int i = threadIdx.x; i < Q; i += kThreads) acc[i] = mk(0.0, 0.0);
   for (int e = F.xoff[b]; e < F.xoff[b + 1]; ++e) {
     const int2 r = F.rsrc[F.xidx[e]];
-    for (int base = r.x; base < r.y; base += kChunk) {
-      const int cnt = min(kChunk, r.y - base);
+    for (int base = r.x; base < r.y; base += chunk) {
+      const int cnt = min(chunk, r.y - base);
       if ((int)threadIdx.x < cnt) {
         const int i = base + threadIdx.x;
         const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
@@ -428,59 +458,59 @@ __global__ void __launch_bounds__(kThreads) p2l_kernel(Fmm F, const int* __restr
         sb[threadIdx.x] = cmul(dk, cconj(nu));
       }
       __syncthreads();
-      for (int o = 0; o < 2; ++o) {
-        const int n = (int)threadIdx.x + o * kThreads - pb;
-        if (n > pb) continue;
+      for (int n = (int)threadIdx.x - pb; n <= pb; n += kThreads) {
         const int an = abs(n);
         // s^|n| W_{n-1} = Wh_{n-1} s^{|n| - |n-1|}, s^|n| W_{n+1} = Wh_{n+1} s^{|n| - |n+1|}
         const double fm = (abs(n - 1) > an) ? is : s;
         const double fp = (abs(n + 1) > an) ? is : s;
+        cd a = acc[n + pb];
         for (int j = 0; j < cnt; ++j) {
           const cd* row = rows + j * RW + (pb + 1);
-          if (F.has_S) cfma(acc[o], sq[j], row[n]);
+          if (F.has_S) cfma(a, sq[j], row[n]);
           if (F.has_D) {
-            cfma(acc[o], cscale(sa[j], fm), row[n - 1]);
-            cfma(acc[o], cscale(sb[j], -fp), row[n + 1]);
+            cfma(a, cscale(sa[j], fm), row[n - 1]);
+            cfma(a, cscale(sb[j], -fp), row[n + 1]);
           }
         }
+        acc[n + pb] = a;
       }
       __syncthreads();
     }
   }
-  for (int o = 0; o < 2; ++o) {
-    const int n = (int)threadIdx.x + o * kThreads - pb;
-    if (n <= pb) {
-      cd* dst = F.local + (size_t)b * F.Q + n + pb;
-      *dst = cadd(*dst, acc[o]);
-    }
-  }
+  cd* dst = F.local + F.eoff[b];
+  for (int i = threadIdx.x; i < Q; i += kThreads) dst[i] = cadd(dst[i], acc[i]);
 }
 
 // ---------------------------------------------------------------- L2L (Stage 7)
+// CTA per parent (level l, order pp) into its children (order pc):
+// gamma'_s = sum_{|n| <= pp} gamma_n (-1)^{s-n} V_{s-n}, |s| <= pc.
+__host__ __device__ inline size_t l2l_smem(int pp, int pc) {
+  return ((size_t)(2 * pp + 1) + (size_t)(2 * (pp + pc) + 1)) * sizeof(cd);
+}
+
 __global__ void __launch_bounds__(kThreads) l2l_kernel(Fmm F, const int* __restrict__ boxes) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, Q = F.Q, T = 4 * pb + 1;
-  cd* g = smem;   // true local coefficients gamma_n
-  cd* t = g + Q;
   const int b = boxes[blockIdx.x];
   const int l = F.level[b];
+  const int pp = F.lpb[l], pc = F.lpb[l + 1];
+  const int Qp = 2 * pp + 1, M = pp + pc, T = 2 * M + 1;
+  cd* g = smem;   // true local coefficients gamma_n
+  cd* t = g + Qp;
   const double* ipp = ipw_row(F, l);
   const double* pwc = pw_row(F, l + 1);
-  for (int i = threadIdx.x; i < Q; i += kThreads)
-    g[i] = cscale(F.local[(size_t)b * Q + i], ipp[abs(i - pb)]);
+  const cd* lp = F.local + F.eoff[b];
+  for (int i = threadIdx.x; i < Qp; i += kThreads) g[i] = cscale(lp[i], ipp[abs(i - pp)]);
   for (int c = 0; c < 4; ++c) {
     const int d = F.child[4 * b + c];
     if (d < 0) continue;
-    const cd* tab = F.t_l2l + ((size_t)l * 4 + c) * T;
-    for (int i = threadIdx.x; i < T; i += kThreads) t[i] = tab[i];
+    const cd* tab = table(F, F.t_l2l, 4, l, c);
+    for (int i = threadIdx.x; i < T; i += kThreads) t[i] = tab[i - M];
     __syncthreads();
-    for (int o = 0; o < 2; ++o) {
-      const int s = (int)threadIdx.x + o * kThreads - pb;
-      if (s > pb) continue;
+    cd* dl = F.local + F.eoff[d];
+    for (int s = (int)threadIdx.x - pc; s <= pc; s += kThreads) {
       cd sum = mk(0.0, 0.0);
-      for (int n = -pb; n <= pb; ++n) cfma(sum, t[s - n + 2 * pb], g[n + pb]);
-      cd* dst = F.local + (size_t)d * Q + s + pb;
-      *dst = cadd(*dst, cscale(sum, pwc[abs(s)]));
+      for (int n = -pp; n <= pp; ++n) cfma(sum, t[s - n + M], g[n + pp]);
+      dl[s + pc] = cadd(dl[s + pc], cscale(sum, pwc[abs(s)]));
     }
     __syncthreads();
   }
@@ -493,15 +523,15 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Fmm F, const int* __restr
 __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restrict__ leaves,
                                                        cd* __restrict__ out) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, Q = F.Q;
   cd* g = smem;
   const int b = leaves[blockIdx.x];
   const int2 r = F.rtgt[b];
   if (r.y <= r.x) return;
   const int l = F.level[b];
+  const int pb = F.lpb[l], Q = 2 * pb + 1;
   const double* ipp = ipw_row(F, l);
-  for (int i = threadIdx.x; i < Q; i += kThreads)
-    g[i] = cscale(F.local[(size_t)b * Q + i], ipp[abs(i - pb)]);
+  const cd* lp = F.local + F.eoff[b];
+  for (int i = threadIdx.x; i < Q; i += kThreads) g[i] = cscale(lp[i], ipp[abs(i - pb)]);
   __syncthreads();
   const double2 m = F.centre[b];
   for (int i = r.x + threadIdx.x; i < r.y; i += kThreads) {
@@ -548,7 +578,6 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
 __global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restrict__ leaves,
                                                        cd* __restrict__ out) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, Q = F.Q;
   cd* a = smem;
   const int b = leaves[blockIdx.x];
   const int2 r = F.rtgt[b];
@@ -560,11 +589,14 @@ __global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restr
     cd acc = mk(0.0, 0.0);
     for (int e = e0; e < e1_; ++e) {
       const int c = F.widx[e];
+      const int lc = F.level[c];
+      const int pb = F.lpb[lc], Q = 2 * pb + 1;
+      const cd* mp = F.mpole + F.eoff[c];
       __syncthreads();
-      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = F.mpole[(size_t)c * Q + j];
+      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = mp[j];
       __syncthreads();
       if (!act) continue;
-      const double s = F.scale[F.level[c]];
+      const double s = F.scale[lc];
       const double2 mc = F.centre[c];
       const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
       const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
@@ -653,15 +685,16 @@ template <int PM>
 __global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
                                                           cd* __restrict__ alpha) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, Q = F.Q, p = F.p, P = 2 * p + 1;
+  const int p = F.p, P = 2 * p + 1;
   cd* g = smem;
   const int b = leaves[blockIdx.x];
   const int2 r = F.rctr[b];
   if (r.y <= r.x) return;
   const int l = F.level[b];
+  const int pb = F.lpb[l], Q = 2 * pb + 1;
   const double* ipp = ipw_row(F, l);
-  for (int i = threadIdx.x; i < Q; i += kThreads)
-    g[i] = cscale(F.local[(size_t)b * Q + i], ipp[abs(i - pb)]);
+  const cd* lp = F.local + F.eoff[b];
+  for (int i = threadIdx.x; i < Q; i += kThreads) g[i] = cscale(lp[i], ipp[abs(i - pb)]);
   __syncthreads();
   const double2 mb = F.centre[b];
   const int M = pb + p;
@@ -796,14 +829,13 @@ template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
                                                           cd* __restrict__ alpha) {
   extern __shared__ cd smem[];
-  const int pb = F.pb, Q = F.Q, p = F.p, P = 2 * p + 1;
-  cd* a = smem;                          // [Q]
-  double* fpw = (double*)(a + Q);        // [2p+1]: s^j, j = -p..p
+  const int p = F.p, P = 2 * p + 1;
+  double* fpw = (double*)smem;           // [2p+1]: s^j, j = -p..p
+  cd* a = smem + (p + 1);                // [Q_c]
   const int b = leaves[blockIdx.x];
   const int2 r = F.rctr[b];
   const int e0 = F.woff[b], e1_ = F.woff[b + 1];
   if (r.y <= r.x || e1_ <= e0) return;
-  const int M = pb + p;
   const double k = F.k;
   for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
     const int i = i0 + threadIdx.x;
@@ -815,8 +847,10 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __re
       const int c = F.widx[e];
       const int lc = F.level[c];
       const double s = F.scale[lc];
+      const int pb = F.lpb[lc], Q = 2 * pb + 1, M = pb + p;
+      const cd* mp = F.mpole + F.eoff[c];
       __syncthreads();
-      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = F.mpole[(size_t)c * Q + j];
+      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = mp[j];
       for (int j = threadIdx.x; j <= 2 * p; j += kThreads) {
         double f = 1.0;
         const int ex = j - p;
@@ -1087,6 +1121,45 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_ulist_mixed_kernel(
   }
 }
 
+// Lift the 48 KB default of dynamic shared memory to the device's opt-in
+// maximum for every kernel that uses it (once per device); the size given at
+// each launch still decides the occupancy.
+template <int PM>
+cudaError_t allow_smem_centre(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute((const void*)l2qbxl_kernel<PM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void* k[3] = {(const void*)m2qbxl_kernel<PM, true, true>,
+                      (const void*)m2qbxl_kernel<PM, true, false>,
+                      (const void*)m2qbxl_kernel<PM, false, true>};
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+qbx_status configure_kernels() {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  QBX_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(dev)) return QBX_OK;
+  int optin = 0;
+  QBX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const void* k[] = {(const void*)p2m_kernel, (const void*)m2m_kernel, (const void*)m2l_kernel,
+                     (const void*)p2l_kernel, (const void*)l2l_kernel, (const void*)l2p_kernel,
+                     (const void*)m2p_kernel};
+  for (const void* f : k)
+    QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  QBX_CUDA_TRY(allow_smem_centre<4>(optin));
+  QBX_CUDA_TRY(allow_smem_centre<8>(optin));
+  QBX_CUDA_TRY(allow_smem_centre<12>(optin));
+  QBX_CUDA_TRY(allow_smem_centre<16>(optin));
+  TRY_MIXED(configure_mixed_kernels(optin));
+  g_smem_optin = optin;
+  done.insert(dev);
+  return QBX_OK;
+}
+
 int p_add_default(int p) {
   // Table 2 of the paper for p <= 8 (2: 5, 4: 5, 6: 15, 8: 20); 2.5 p beyond
   if (p <= 4) return 5;
@@ -1114,39 +1187,71 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   TRY(tree_associate(h, f, on_node_dev, on_side_dev, eps));
   TRY(gather_sorted(h, f));
   const int p_add = d->p_add >= 0 ? d->p_add : p_add_default(h->p);
-  f->pb = std::max(1, d->p_fmm + p_add);
-  if (f->pb > 80) {
-    set_error("box expansion order p_fmm + p_add = %d exceeds 80", f->pb);
+  if (f->n_levels > kMaxLevels + 1) {
+    set_error("tree has %d levels (at most %d)", f->n_levels, kMaxLevels + 1);
     return QBX_ERR_ARG;
   }
-  f->Q = 2 * f->pb + 1;
+  // box order per level (Sec. 8.3): p_fmm on the finest level, more on coarse
+  // levels whose boxes span wavelengths, plus p_add
+  f->h_pb.assign(f->n_levels, 0);
+  TRY(qbx_fmm_level_orders(h->k, f->side, f->n_levels, std::max(1, d->p_fmm), p_add,
+                           f->h_pb.data()));
+  f->pb_max = 1;
+  for (int l = 0; l < f->n_levels; ++l) f->pb_max = std::max(f->pb_max, f->h_pb[l]);
+  f->pb_fine = f->h_pb[f->n_levels - 1];
   // scales, powers, translation tables
   std::vector<double> sc(f->n_levels);
   for (int l = 0; l < f->n_levels; ++l) {
     sc[l] = std::min(1.0, h->k * f->side / (double)(1 << l));
-    if (std::pow(sc[l], f->pb + 1) < 1e-250) {
-      set_error("tree level %d too fine for the box order %d (k*side = %.3g)", l, f->pb, sc[l]);
+    if (l >= 2 && std::pow(sc[l], f->h_pb[l] + 1) < 1e-250) {
+      set_error("tree level %d too fine for the box order %d (k*side = %.3g)", l, f->h_pb[l],
+                sc[l]);
       return QBX_ERR_ARG;
     }
   }
+  // coefficient offsets: boxes of level l are [level_off[l], level_off[l+1])
+  {
+    std::vector<long long> eo(f->n_boxes);
+    long long off = 0;
+    for (int l = 0; l < f->n_levels; ++l)
+      for (int b = f->level_off[l]; b < f->level_off[l + 1]; ++b) {
+        eo[b] = off;
+        off += 2 * f->h_pb[l] + 1;
+      }
+    f->n_coef = off;
+    QBX_CUDA_TRY(f->eoff.alloc(std::max(1, f->n_boxes)));
+    if (f->n_boxes)
+      QBX_CUDA_TRY(cudaMemcpy(f->eoff.ptr, eo.data(), eo.size() * sizeof(long long),
+                              cudaMemcpyHostToDevice));
+  }
+  QBX_CUDA_TRY(f->lpb.alloc(f->n_levels));
+  QBX_CUDA_TRY(cudaMemcpy(f->lpb.ptr, f->h_pb.data(), f->n_levels * sizeof(int),
+                          cudaMemcpyHostToDevice));
   QBX_CUDA_TRY(f->scale.alloc(f->n_levels));
   QBX_CUDA_TRY(cudaMemcpy(f->scale.ptr, sc.data(), sc.size() * sizeof(double),
                           cudaMemcpyHostToDevice));
-  const int T = 4 * f->pb + 1;
-  QBX_CUDA_TRY(f->t_m2l.alloc((size_t)f->n_levels * 49 * T));
-  QBX_CUDA_TRY(f->t_m2m.alloc((size_t)f->n_levels * 4 * T));
-  QBX_CUDA_TRY(f->t_l2l.alloc((size_t)f->n_levels * 4 * T));
-  QBX_CUDA_TRY(f->pw.alloc((size_t)f->n_levels * (2 * f->pb + 3)));
-  QBX_CUDA_TRY(f->ipw.alloc((size_t)f->n_levels * (f->pb + 2)));
+  const int pbm = f->pb_max, TS = 4 * pbm + 1;
+  QBX_CUDA_TRY(f->t_m2l.alloc((size_t)f->n_levels * 49 * TS));
+  QBX_CUDA_TRY(f->t_m2m.alloc((size_t)f->n_levels * 4 * TS));
+  QBX_CUDA_TRY(f->t_l2l.alloc((size_t)f->n_levels * 4 * TS));
+  QBX_CUDA_TRY(f->pw.alloc((size_t)f->n_levels * (2 * pbm + 3)));
+  QBX_CUDA_TRY(f->ipw.alloc((size_t)f->n_levels * (pbm + 2)));
   DevBuf<double> jwork;
-  QBX_CUDA_TRY(jwork.alloc((size_t)f->n_levels * 57 * (2 * f->pb + 1)));
-  tables_kernel<<<nblk(f->n_levels * 57, 64), 64>>>(f->n_levels, f->side, h->k, f->pb,
+  QBX_CUDA_TRY(jwork.alloc((size_t)f->n_levels * 57 * (2 * pbm + 1)));
+  tables_kernel<<<nblk(f->n_levels * 57, 64), 64>>>(f->n_levels, f->side, h->k, pbm, f->lpb.ptr,
                                                     f->scale.ptr, f->t_m2l.ptr, f->t_m2m.ptr,
                                                     f->t_l2l.ptr, jwork.ptr);
-  powers_kernel<<<1, 64>>>(f->n_levels, f->pb, f->scale.ptr, f->pw.ptr, f->ipw.ptr);
+  powers_kernel<<<1, 64>>>(f->n_levels, pbm, f->lpb.ptr, f->scale.ptr, f->pw.ptr, f->ipw.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
-  QBX_CUDA_TRY(f->mpole.alloc((size_t)f->n_boxes * f->Q));
-  QBX_CUDA_TRY(f->local.alloc((size_t)f->n_boxes * f->Q));
+  QBX_CUDA_TRY(f->mpole.alloc(std::max<int64_t>(1, f->n_coef)));
+  QBX_CUDA_TRY(f->local.alloc(std::max<int64_t>(1, f->n_coef)));
+  TRY(configure_kernels());
+  // the largest per-block footprint (M2L at the largest order) bounds all others
+  if (m2l_smem(f->pb_max) > (size_t)g_smem_optin) {
+    set_error("box order %d needs %zu bytes of shared memory per block (device: %d)", f->pb_max,
+              m2l_smem(f->pb_max), g_smem_optin);
+    return QBX_ERR_ARG;
+  }
   TRY(mixed_plan_build(h, f));
   QBX_CUDA_TRY(f->qs.alloc(std::max<int64_t>(1, h->n_src)));
   QBX_CUDA_TRY(f->ds.alloc(std::max<int64_t>(1, h->n_src)));
@@ -1169,8 +1274,9 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   std::vector<int> assoc_s(std::max<int64_t>(1, h->n_tgt));
   if (h->n_tgt)
     QBX_CUDA_TRY(cudaMemcpy(assoc_s.data(), f->t_assoc.ptr, h->n_tgt * 4, cudaMemcpyDeviceToHost));
-  std::vector<int> leaves(f->n_leaves);
+  std::vector<int> leaves(f->n_leaves), blev(f->n_boxes);
   QBX_CUDA_TRY(cudaMemcpy(leaves.data(), f->leaves.ptr, leaves.size() * 4, cudaMemcpyDeviceToHost));
+  QBX_CUDA_TRY(cudaMemcpy(blev.data(), f->box.level.ptr, blev.size() * 4, cudaMemcpyDeviceToHost));
   int64_t p2qbxl = 0, p2p = 0, m2qbxl = 0, m2p = 0, p2l = 0;
   std::vector<int> src_leaves;
   for (int b : leaves) {
@@ -1182,8 +1288,15 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     p2p += us * nd;
     m2qbxl += (int64_t)(woff[b + 1] - woff[b]) * (rc[b].y - rc[b].x);
     m2p += (int64_t)(woff[b + 1] - woff[b]) * nd;
-    if (rs[b].y > rs[b].x) src_leaves.push_back(b);
+    if (rs[b].y > rs[b].x && blev[b] >= 2) src_leaves.push_back(b);
+    f->q_leaf = std::max(f->q_leaf, 2 * f->h_pb[blev[b]] + 1);
+    for (int e = woff[b]; e < woff[b + 1]; ++e)
+      f->q_w = std::max(f->q_w, 2 * f->h_pb[blev[widx[e]]] + 1);
   }
+  // leaves come in level order, so src_leaves does too
+  f->src_leaf_off.assign(f->n_levels + 1, 0);
+  for (int b : src_leaves) f->src_leaf_off[blev[b] + 1] += 1;
+  for (int l = 0; l < f->n_levels; ++l) f->src_leaf_off[l + 1] += f->src_leaf_off[l];
   for (int b = 0; b < f->n_boxes; ++b)
     for (int e = xoff[b]; e < xoff[b + 1]; ++e) p2l += rs[xidx[e]].y - rs[xidx[e]].x;
   QBX_CUDA_TRY(f->src_leaves.alloc(std::max<size_t>(1, src_leaves.size())));
@@ -1194,7 +1307,8 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   h->stats[4] = f->n_boxes;
   h->stats[5] = f->n_leaves;
   h->stats[6] = f->n_levels - 1;
-  h->stats[7] = f->pb;
+  h->stats[7] = f->pb_fine;
+  h->stats[19] = f->pb_max;
   h->stats[8] = f->U.nnz;
   h->stats[9] = f->V.nnz;
   h->stats[10] = f->W.nnz;
@@ -1204,7 +1318,12 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   h->stats[14] = m2qbxl;
   h->stats[15] = m2p;
   h->stats[17] = p2l;
-  h->stats[18] = 2 * (f->n_boxes - 1);
+  {
+    int64_t mm = 0;  // M2M and L2L translations (parents on levels >= 2)
+    for (int b = 0; b < f->n_boxes; ++b)
+      if (blev[b] >= 3) mm += 2;
+    h->stats[18] = mm;
+  }
   return QBX_OK;
 }
 
@@ -1225,10 +1344,11 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   F.sxy = f->s_xy.ptr; F.snrm = f->s_nrm.ptr; F.qs = f->qs.ptr; F.ds = f->ds.ptr;
   F.cxy = f->c_xy.ptr; F.crad = f->c_r.ptr; F.cid = f->perm[PT_CTR].ptr;
   F.txy = f->t_xy.ptr; F.tid = f->perm[PT_TGT].ptr; F.tassoc = f->t_assoc.ptr;
+  F.lpb = f->lpb.ptr; F.eoff = f->eoff.ptr;
   F.scale = f->scale.ptr; F.pw = f->pw.ptr; F.ipw = f->ipw.ptr;
   F.t_m2l = f->t_m2l.ptr; F.t_m2m = f->t_m2m.ptr; F.t_l2l = f->t_l2l.ptr;
   F.mpole = f->mpole.ptr; F.local = f->local.ptr;
-  F.k = h->k; F.side = f->side; F.pb = f->pb; F.Q = f->Q; F.p = h->p; F.n_levels = f->n_levels;
+  F.k = h->k; F.side = f->side; F.pbmax = f->pb_max; F.p = h->p; F.n_levels = f->n_levels;
   F.has_S = S ? 1 : 0; F.has_D = D ? 1 : 0;
   return F;
 }
@@ -1236,13 +1356,12 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
 template <int PM>
 qbx_status launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
                                  cd* alpha, bool mixed, cudaStream_t s) {
-  const size_t smQ = (size_t)F.Q * sizeof(cd);
   stage_begin(h, QBX_STAGE_L2QBXL, s);
-  l2qbxl_kernel<PM><<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, alpha);
+  l2qbxl_kernel<PM><<<f->n_leaves, kThreads, (size_t)f->q_leaf * sizeof(cd), s>>>(F, f->leaves.ptr, alpha);
   QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
   stage_begin(h, QBX_STAGE_M2QBXL, s);
-  const size_t smW = smQ + (size_t)(PM + 1) * sizeof(cd);
+  const size_t smW = (size_t)(f->q_w + h->p + 1) * sizeof(cd);
   if (S && D) m2qbxl_kernel<PM, true, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
   else if (S) m2qbxl_kernel<PM, true, false><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
   else if (D) m2qbxl_kernel<PM, false, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
@@ -1264,12 +1383,29 @@ qbx_status launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S
   return QBX_OK;
 }
 
+// Shared memory of a source-row kernel (P2M, P2L) at box order pb: a full
+// chunk of rows when it fits the opt-in limit, else as many rows as fit.
+size_t rows_launch_smem(int pb) {
+  return std::min(rows_smem(pb, kChunk), (size_t)g_smem_optin);
+}
+
+// Largest box order among the levels l with off[l+1] > off[l] (boxes of a
+// level-ordered list); the single launch over the list sizes its shared memory
+// for it. The lists are ordered coarse to fine, so the CTAs with the most work
+// (highest orders) start first.
+int max_order(const std::vector<int>& pb, const std::vector<int>& off) {
+  int m = 0;
+  for (size_t l = 0; l + 1 < off.size(); ++l)
+    if (off[l + 1] > off[l]) m = std::max(m, pb[l]);
+  return m;
+}
+
 }  // namespace
 
 qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaStream_t s) {
   FmmPlan* f = h->fmm;
   if (!f) { set_error("FMM plan missing"); return QBX_ERR_STATE; }
-  const int pb = f->pb, Q = f->Q, T = 4 * pb + 1;
+  const std::vector<int>& pb = f->h_pb;
   if (h->n_src > 0) {
     gather_strengths_kernel<<<nblk(h->n_src, 256), 256, 0, s>>>(
         h->n_src, f->perm[PT_SRC].ptr, h->q_str.ptr, h->d_str.ptr, f->qs.ptr, f->ds.ptr);
@@ -1277,23 +1413,22 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     h->launches += 1;
   }
   Fmm F = make_view(h, f, S, D);
-  QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_boxes * Q * sizeof(cd), s));
-  QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_boxes * Q * sizeof(cd), s));
-  // Stage 2: P2M, M2M
-  const size_t sm_p2m = (size_t)(kChunk * (2 * pb + 3) + 3 * kChunk) * sizeof(cd);
+  QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
+  QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
+  // Stage 2: P2M (one launch per leaf level), M2M
   stage_begin(h, QBX_STAGE_P2M, s);
-  if (f->n_src_leaves > 0 && (S || D)) {
-    p2m_kernel<<<f->n_src_leaves, kThreads, sm_p2m, s>>>(F, f->src_leaves.ptr);
+  if ((S || D) && f->n_src_leaves > 0) {
+    const size_t sm = rows_launch_smem(max_order(pb, f->src_leaf_off));
+    p2m_kernel<<<f->n_src_leaves, kThreads, sm, s>>>(F, f->src_leaves.ptr, (unsigned)sm);
     QBX_KCHECK("p2m", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_P2M, s);
-  const size_t sm_tr = (size_t)(Q + T) * sizeof(cd);
   stage_begin(h, QBX_STAGE_M2M, s);
-  for (int l = f->n_levels - 2; l >= 0; --l) {
+  for (int l = f->n_levels - 2; l >= 2; --l) {
     const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
     if (nb == 0) continue;
-    m2m_kernel<<<nb, kThreads, sm_tr, s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+    m2m_kernel<<<nb, kThreads, m2m_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
     QBX_KCHECK("m2m", s);
     h->launches += 1;
   }
@@ -1303,39 +1438,38 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   if (precision == QBX_MIXED) {
     TRY(launch_m2l_f32(h, f, s));
   } else if (f->n_vbox > 0) {
-    m2l_kernel<<<f->n_vbox, kThreads, sm_tr + Q * sizeof(cd) + (pb + 1) * sizeof(double), s>>>(F, f->vbox.ptr);
+    m2l_kernel<<<f->n_vbox, kThreads, m2l_smem(max_order(pb, f->vbox_off)), s>>>(F, f->vbox.ptr);
     QBX_KCHECK("m2l", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_M2L, s);
   // Stage 6: P2L
   stage_begin(h, QBX_STAGE_P2L, s);
-  if (f->n_xbox > 0 && (S || D)) {
-    const size_t sm = (size_t)(kChunk * (2 * pb + 3) + 3 * kChunk) * sizeof(cd);
-    p2l_kernel<<<f->n_xbox, kThreads, sm, s>>>(F, f->xbox.ptr);
+  if ((S || D) && f->n_xbox > 0) {
+    const size_t sm = rows_launch_smem(max_order(pb, f->xbox_off));
+    p2l_kernel<<<f->n_xbox, kThreads, sm, s>>>(F, f->xbox.ptr, (unsigned)sm);
     QBX_KCHECK("p2l", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_P2L, s);
   // Stage 7: L2L
   stage_begin(h, QBX_STAGE_L2L, s);
-  for (int l = 1; l + 1 < f->n_levels; ++l) {
+  for (int l = 2; l + 1 < f->n_levels; ++l) {
     const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
     if (nb == 0) continue;
-    l2l_kernel<<<nb, kThreads, sm_tr, s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+    l2l_kernel<<<nb, kThreads, l2l_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
     QBX_KCHECK("l2l", s);
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_L2L, s);
   // Stages 3, 5, 8 at targets
-  const size_t smQ = (size_t)Q * sizeof(cd);
   if (f->n_leaves > 0 && h->n_direct_tgt > 0) {
     stage_begin(h, QBX_STAGE_L2P, s);
-    l2p_kernel<<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, out);
+    l2p_kernel<<<f->n_leaves, kThreads, (size_t)f->q_leaf * sizeof(cd), s>>>(F, f->leaves.ptr, out);
     QBX_KCHECK("l2p", s);
     stage_end(h, QBX_STAGE_L2P, s);
     stage_begin(h, QBX_STAGE_M2P, s);
-    m2p_kernel<<<f->n_leaves, kThreads, smQ, s>>>(F, f->leaves.ptr, out);
+    m2p_kernel<<<f->n_leaves, kThreads, (size_t)f->q_w * sizeof(cd), s>>>(F, f->leaves.ptr, out);
     QBX_KCHECK("m2p", s);
     stage_end(h, QBX_STAGE_M2P, s);
     stage_begin(h, QBX_STAGE_P2P, s);
@@ -1372,7 +1506,7 @@ extern "C" qbx_status qbx_export_tree(const qbx_handle* h, int64_t* info, double
   const int nb = f->n_boxes;
   if (info) {
     info[0] = nb; info[1] = f->n_levels; info[2] = f->U.nnz; info[3] = f->V.nnz;
-    info[4] = f->W.nnz; info[5] = f->X.nnz; info[6] = f->pb; info[7] = f->n_leaves;
+    info[4] = f->W.nnz; info[5] = f->X.nnz; info[6] = f->pb_fine; info[7] = f->n_leaves;
   }
   if (root) { root[0] = f->x0; root[1] = f->y0; root[2] = f->side; }
   if (box_level) QBX_CUDA_TRY(cudaMemcpy(box_level, f->box.level.ptr, nb * 4, cudaMemcpyDeviceToHost));
@@ -1401,5 +1535,16 @@ extern "C" qbx_status qbx_export_tree(const qbx_handle* h, int64_t* info, double
   if (perm_src && h->n_src) QBX_CUDA_TRY(cudaMemcpy(perm_src, f->perm[PT_SRC].ptr, h->n_src * 4, cudaMemcpyDeviceToHost));
   if (perm_ctr && h->n_ctr) QBX_CUDA_TRY(cudaMemcpy(perm_ctr, f->perm[PT_CTR].ptr, h->n_ctr * 4, cudaMemcpyDeviceToHost));
   if (perm_tgt && h->n_tgt) QBX_CUDA_TRY(cudaMemcpy(perm_tgt, f->perm[PT_TGT].ptr, h->n_tgt * 4, cudaMemcpyDeviceToHost));
+  return QBX_OK;
+}
+
+extern "C" qbx_status qbx_get_box_orders(const qbx_handle* h, int32_t* pb_out, int32_t n) {
+  if (!h || !pb_out || n < 0) { set_error("qbx_get_box_orders: bad arguments"); return QBX_ERR_ARG; }
+  const FmmPlan* f = h->fmm;
+  if (!f || !h->planned || h->mode != QBX_FMM) {
+    set_error("qbx_get_box_orders: no FMM plan (call qbx_tree_build with QBX_FMM)");
+    return QBX_ERR_STATE;
+  }
+  for (int l = 0; l < n; ++l) pb_out[l] = l < f->n_levels ? f->h_pb[l] : 0;
   return QBX_OK;
 }

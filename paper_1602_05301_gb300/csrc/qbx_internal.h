@@ -62,6 +62,9 @@ struct DevBuf {
 
 // ---------------------------------------------------------------- geometry / plan
 struct FmmPlan;  // fmm.cu
+// Largest box expansion order (coarse boxes spanning many wavelengths need
+// orders of about k * side; beyond this the plan is refused).
+constexpr int kMaxBoxOrder = 1200;
 
 struct qbx_handle {
   // geometry (device)

@@ -695,8 +695,12 @@ qbx_status tree_lists(qbx_handle* h, FmmPlan* f) {
                           cudaMemcpyDeviceToHost));
   std::vector<int> leaves, nonleaf, vbox, xbox;
   f->nonleaf_off.assign(f->n_levels + 1, 0);
+  f->vbox_off.assign(f->n_levels + 1, 0);
+  f->xbox_off.assign(f->n_levels + 1, 0);
   for (int l = 0; l < f->n_levels; ++l) {
     f->nonleaf_off[l] = (int)nonleaf.size();
+    f->vbox_off[l] = (int)vbox.size();
+    f->xbox_off[l] = (int)xbox.size();
     for (int b = f->level_off[l]; b < f->level_off[l + 1]; ++b) {
       bool leaf = child[4 * b] < 0 && child[4 * b + 1] < 0 && child[4 * b + 2] < 0 &&
                   child[4 * b + 3] < 0;
@@ -706,6 +710,8 @@ qbx_status tree_lists(qbx_handle* h, FmmPlan* f) {
     }
   }
   f->nonleaf_off[f->n_levels] = (int)nonleaf.size();
+  f->vbox_off[f->n_levels] = (int)vbox.size();
+  f->xbox_off[f->n_levels] = (int)xbox.size();
   f->n_leaves = (int)leaves.size();
   f->n_vbox = (int)vbox.size();
   f->n_xbox = (int)xbox.size();

@@ -44,29 +44,40 @@ struct FmmPlan {
   int n_xbox = 0;
   DevBuf<int> vbox;                     // boxes with non-empty V list
   int n_vbox = 0;
-  // orders and scales
-  int pb = 0, Q = 0;
+  // orders and scales: box order pb_l per level (0 on levels 0 and 1, which
+  // carry no expansions), Q_l = 2 pb_l + 1 coefficients per box
+  std::vector<int> h_pb;                // [n_levels]
+  int pb_max = 0, pb_fine = 0;          // largest order; order at the finest level
+  DevBuf<int> lpb;                      // [n_levels]
+  DevBuf<long long> eoff;               // [n_boxes] first coefficient of each box
+  int64_t n_coef = 0;                   // coefficients per expansion array
   DevBuf<double> scale;                 // per level s_l = min(1, k * side_l)
   DevBuf<double> pw, ipw;               // per level powers s^j, s^-j
-  DevBuf<int> src_leaves;               // leaves holding sources
+  DevBuf<int> src_leaves;               // leaves holding sources (levels >= 2)
   int n_src_leaves = 0;
-  DevBuf<cd> t_m2l;                     // [n_levels][49][4pb+1] scaled Hankel vectors
-  DevBuf<cd> t_m2m;                     // [n_levels][4][4pb+1] conj(V_m(d)) child->parent
-  DevBuf<cd> t_l2l;                     // [n_levels][4][4pb+1] (-1)^m V_m(d) parent->child
+  // src_leaves, xbox and vbox are ordered by level; [n_levels + 1] offsets
+  std::vector<int> src_leaf_off, xbox_off, vbox_off;
+  int q_leaf = 1, q_w = 1;              // largest Q_l among leaves / W-list boxes
+  DevBuf<cd> t_m2l;                     // [n_levels][49][4 pb_max + 1] scaled Hankel vectors
+  DevBuf<cd> t_m2m;                     // [n_levels][4][4 pb_max + 1] conj(V_m(d)) child->parent
+  DevBuf<cd> t_l2l;                     // [n_levels][4][4 pb_max + 1] (-1)^m V_m(d) parent->child
   // sorted particle data used by the eval kernels
   DevBuf<double2> s_xy, s_nrm, c_xy, t_xy;
   DevBuf<double> c_r;                   // sorted centre radii
   DevBuf<int> t_assoc;                  // association of sorted targets (centre id or -1)
   // expansions
-  DevBuf<cd> mpole, local;              // [n_boxes][Q]
+  DevBuf<cd> mpole, local;              // [n_coef], box b at eoff[b]
   DevBuf<cd> qs, ds;                    // sorted strengths
   DevBuf<int> err;                      // device error flags
   // mixed precision (sigma-normalised FP32 M2L)
-  DevBuf<double> lsig, conv;            // [n_levels][pb+1] log sig_j, s^j / sig_j
-  DevBuf<float2> tm_f32;                // [n_levels][49][Q][Q] M2L matrices
+  DevBuf<double> lsig, conv;            // [n_levels][pb_max+1] log sig_j, s^j / sig_j
+  DevBuf<float2> tm_f32;                // per level l >= 2: [49][Q_l][Q_l] M2L matrices
+  DevBuf<long long> tm_off;             // [n_levels] offset of level l's matrices
+  std::vector<long long> h_tm_off;
 };
 
 qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f);
+qbx_status configure_mixed_kernels(int smem_optin);
 qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 
 qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max, double kappa);

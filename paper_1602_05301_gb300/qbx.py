@@ -98,6 +98,11 @@ def library() -> ctypes.CDLL:
             lib.qbx_batch_eval.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, _vp]
             lib.qbx_batch_destroy.restype = None
             lib.qbx_batch_destroy.argtypes = [_vp]
+            lib.qbx_get_box_orders.restype = ctypes.c_int
+            lib.qbx_get_box_orders.argtypes = [_vp, _vp, ctypes.c_int32]
+            lib.qbx_fmm_level_orders.restype = ctypes.c_int
+            lib.qbx_fmm_level_orders.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_int32, _vp]
             _lib = lib
     return _lib
 
@@ -187,6 +192,15 @@ def qbx_export_tree(handle, n_src, n_ctr, n_tgt):
     return out
 
 
+def qbx_fmm_level_orders(k: float, root_side: float, n_levels: int, p_fmm: int,
+                         p_add: int) -> np.ndarray:
+    """Box expansion order of every tree level (0 on levels 0 and 1)."""
+    out = np.zeros(n_levels, dtype=np.int32)
+    _check(library().qbx_fmm_level_orders(float(k), float(root_side), int(n_levels), int(p_fmm),
+                                          int(p_add), out.ctypes.data))
+    return out
+
+
 def qbx_last_error() -> str:
     return library().qbx_last_error().decode()
 
@@ -266,8 +280,15 @@ class LayerPotential:
         names = ["n_sources", "n_centres", "n_targets", "n_qbx_targets", "n_boxes", "n_leaves",
                  "depth", "p_box", "u_pairs", "v_pairs", "w_pairs", "x_pairs",
                  "p2qbxl_pairs", "p2p_pairs", "m2qbxl_pairs", "m2p_pairs", "launches",
-                 "p2l_pairs", "m2m_l2l", "reserved"]
+                 "p2l_pairs", "m2m_l2l", "p_box_max"]
         return dict(zip(names, qbx_get_stats(self.handle)))
+
+    def box_orders(self):
+        """Box expansion order of every tree level of the FMM plan."""
+        out = np.zeros(25, dtype=np.int32)
+        _check(library().qbx_get_box_orders(self.handle, out.ctypes.data, 25))
+        depth = int(self.stats()["depth"])
+        return out[:depth + 1]
 
     def export_tree(self):
         return qbx_export_tree(self.handle, self.n_src, self.n_centres, self.n_targets)

@@ -1,7 +1,10 @@
-"""The large starfish workload at full size (k=50, 131 072 nodes, p=16, box
-order 70), FMM on the GPU, checked against the FP64 oracle on sampled targets
-(each sample summed over all sources): FP64 within 1e-10, mixed precision
-within 1e-6 of FP64 on every target."""
+"""The two large workloads at full size, FMM on the GPU, checked against the
+FP64 oracle on sampled targets (each sample summed over all sources):
+starfish k=50 (131 072 nodes, p=16, box order 70 on the finest level) and 200
+ellipses in [0,100]^2 (2^20 nodes, k=20, 1e6 targets, double layer, p=16),
+whose coarse boxes span hundreds of wavelengths and need the level-dependent
+box orders. FP64 within 1e-10, mixed precision within 1e-6 of FP64 on every
+target."""
 import numpy as np
 import pytest
 
@@ -25,7 +28,7 @@ def qbxmod():
     return qbx
 
 
-@pytest.mark.parametrize("num,n_q,n_d", [(3, 12, 48)])
+@pytest.mark.parametrize("num,n_q,n_d", [(3, 12, 48), (5, 4, 16)])
 def test_large_workload_sampled_parity(qbxmod, oracle, num, n_q, n_d):
     w = make_config(num)
     g = w["geom"]
