@@ -33,6 +33,11 @@
 namespace {
 
 constexpr int kThreads = 128;
+// CTA size of the per-leaf kernels (threads over the centres or targets of one
+// leaf). Leaves that hold centres are kept at least kLeafOverRadius disk radii
+// wide, so they carry many centres (about 65 on the starfish workloads) and few
+// leaves hold any: one warp per leaf left most SMs idle (measured 2x slower).
+constexpr int kLeafThreads = 128;
 constexpr int kChunk = 16;  // sources per shared-memory chunk in P2M / P2L
 constexpr double kRescale = 1e100;
 // Leaves holding a centre are at least this many expansion radii wide.
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Fmm F, const int* __restr
 // CTA per leaf; one thread per target of the leaf (strided). Only targets that
 // are not associated with a QBX centre are evaluated.
 // L2P writes out[t], M2P and P2P add to it.
-__global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restrict__ leaves,
+__global__ void __launch_bounds__(kLeafThreads) l2p_kernel(Fmm F, const int* __restrict__ leaves,
                                                        cd* __restrict__ out) {
   extern __shared__ cd smem[];
   cd* g = smem;
@@ -529,12 +534,11 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
   if (r.y <= r.x) return;
   const int l = F.level[b];
   const int pb = F.lpb[l], Q = 2 * pb + 1;
-  const double* ipp = ipw_row(F, l);
-  const cd* lp = F.local + F.eoff[b];
-  for (int i = threadIdx.x; i < Q; i += kThreads) g[i] = cscale(lp[i], ipp[abs(i - pb)]);
+  const cd* lp = F.local + F.eoff[b];  // true local coefficients (unscaled)
+  for (int i = threadIdx.x; i < Q; i += kLeafThreads) g[i] = lp[i];
   __syncthreads();
   const double2 m = F.centre[b];
-  for (int i = r.x + threadIdx.x; i < r.y; i += kThreads) {
+  for (int i = r.x + threadIdx.x; i < r.y; i += kLeafThreads) {
     if (F.tassoc[i] >= 0) continue;
     const double dx = F.txy[i].x - m.x, dy = F.txy[i].y - m.y;
     const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
@@ -575,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
   }
 }
 
-__global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restrict__ leaves,
+__global__ void __launch_bounds__(kLeafThreads) m2p_kernel(Fmm F, const int* __restrict__ leaves,
                                                        cd* __restrict__ out) {
   extern __shared__ cd smem[];
   cd* a = smem;
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restr
   const int2 r = F.rtgt[b];
   const int e0 = F.woff[b], e1_ = F.woff[b + 1];
   if (r.y <= r.x || e1_ <= e0) return;
-  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
+  for (int i0 = r.x; i0 < r.y; i0 += kLeafThreads) {
     const int i = i0 + threadIdx.x;
     const bool act = i < r.y && F.tassoc[i] < 0;
     cd acc = mk(0.0, 0.0);
@@ -593,7 +597,7 @@ __global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restr
       const int pb = F.lpb[lc], Q = 2 * pb + 1;
       const cd* mp = F.mpole + F.eoff[c];
       __syncthreads();
-      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = mp[j];
+      for (int j = threadIdx.x; j < Q; j += kLeafThreads) a[j] = mp[j];
       __syncthreads();
       if (!act) continue;
       const double s = F.scale[lc];
@@ -624,24 +628,24 @@ __global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restr
 }
 
 template <bool HS, bool HD>
-__global__ void __launch_bounds__(kThreads) p2p_ulist_kernel(Fmm F, const int* __restrict__ leaves,
+__global__ void __launch_bounds__(kLeafThreads) p2p_ulist_kernel(Fmm F, const int* __restrict__ leaves,
                                                              cd* __restrict__ out) {
-  __shared__ double2 s_xy[kThreads];
-  __shared__ double2 s_n[kThreads];
-  __shared__ cd s_q[kThreads];
-  __shared__ cd s_d[kThreads];
+  __shared__ double2 s_xy[kLeafThreads];
+  __shared__ double2 s_n[kLeafThreads];
+  __shared__ cd s_q[kLeafThreads];
+  __shared__ cd s_d[kLeafThreads];
   const int b = leaves[blockIdx.x];
   const int2 r = F.rtgt[b];
   if (r.y <= r.x) return;
   const double k = F.k;
-  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
+  for (int i0 = r.x; i0 < r.y; i0 += kLeafThreads) {
     const int i = i0 + threadIdx.x;
     const bool act = i < r.y && F.tassoc[i] < 0;
     const double tx = act ? F.txy[i].x : 0.0, ty = act ? F.txy[i].y : 0.0;
     cd acc = mk(0.0, 0.0);
     for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
       const int2 sr = F.rsrc[F.uidx[e]];
-      for (int base = sr.x; base < sr.y; base += kThreads) {
+      for (int base = sr.x; base < sr.y; base += kLeafThreads) {
         __syncthreads();
         const int j = base + threadIdx.x;
         if (j < sr.y) {
@@ -653,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) p2p_ulist_kernel(Fmm F, const int* _
           }
         }
         __syncthreads();
-        const int cnt = min(kThreads, sr.y - base);
+        const int cnt = min(kLeafThreads, sr.y - base);
         if (!act) continue;
         for (int jj = 0; jj < cnt; ++jj) {
           const double dx = tx - s_xy[jj].x, dy = ty - s_xy[jj].y;
@@ -680,25 +684,22 @@ __global__ void __launch_bounds__(kThreads) p2p_ulist_kernel(Fmm F, const int* _
 }
 
 // ---------------------------------------------------------------- centres (Stages 3, 5, 8 "New")
-// L2QBXL: alpha_s = sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p.
+// L2QBXL: alpha_s = sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p; one
+// thread per centre, reading its leaf's true local coefficients gamma (leaf
+// locals are unscaled in place once the downward pass is complete).
+// Writes alpha (the first of the three centre stages).
 template <int PM>
-__global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
-                                                          cd* __restrict__ alpha) {
-  extern __shared__ cd smem[];
+__global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                          int n_ctr, cd* __restrict__ alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_ctr) return;
   const int p = F.p, P = 2 * p + 1;
-  cd* g = smem;
-  const int b = leaves[blockIdx.x];
-  const int2 r = F.rctr[b];
-  if (r.y <= r.x) return;
-  const int l = F.level[b];
-  const int pb = F.lpb[l], Q = 2 * pb + 1;
-  const double* ipp = ipw_row(F, l);
-  const cd* lp = F.local + F.eoff[b];
-  for (int i = threadIdx.x; i < Q; i += kThreads) g[i] = cscale(lp[i], ipp[abs(i - pb)]);
-  __syncthreads();
+  const int b = cleaf[i];
+  const int pb = F.lpb[F.level[b]];
+  const cd* g = F.local + F.eoff[b];
   const double2 mb = F.centre[b];
   const int M = pb + p;
-  for (int i = r.x + threadIdx.x; i < r.y; i += kThreads) {
+  {
     const double dx = F.cxy[i].x - mb.x, dy = F.cxy[i].y - mb.y;
     const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
     const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
@@ -756,12 +757,18 @@ __global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __re
   }
 }
 
-// M2QBXL: alpha_l += (-1)^l sum_n mh_n Wh_{n+l} s^{|n| - |n+l|},  Wh_m = s^|m| W_m(z - m_c).
-// A W box too close to the centre's disk for its multipole series to converge
-// on the whole disk ((R_c + r_z) > kW |z - m_c|) is summed source by source.
-template <int PM, bool HS, bool HD>
-__global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
-                                                          cd* __restrict__ alpha);
+// Leaf local coefficients lh_n = gamma_n s^|n| -> gamma_n, in place, once the
+// downward pass (M2L, P2L, L2L) is complete; L2P and L2QBXL read gamma.
+__global__ void __launch_bounds__(kThreads) unscale_leaf_locals_kernel(Fmm F,
+                                                                       const int* __restrict__ leaves) {
+  const int b = leaves[blockIdx.x];
+  const int l = F.level[b];
+  const int pb = F.lpb[l], Q = 2 * pb + 1;
+  const double* ipp = ipw_row(F, l);
+  cd* lp = F.local + F.eoff[b];
+  for (int i = threadIdx.x; i < Q; i += kThreads) lp[i] = cscale(lp[i], ipp[abs(i - pb)]);
+}
+
 
 // One source's contribution to the QBX coefficients of a centre (P2QBXL):
 // alpha_l += q W_l + d (k/2) (nu W_{l-1} - conj(nu) W_{l+1}),  W_l = H_l(k r) e^{i l th},
@@ -825,144 +832,94 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
   }
 }
 
+// M2QBXL: alpha_l += (-1)^l sum_n mh_n Wh_{n+l} s^{|n| - |n+l|},  Wh_m = s^|m| W_m(z - m_c),
+// one thread per (centre, W-list box) pair, the pair's coefficients written to
+// partial[pair][2p+1]; m2qbxl_sum_kernel adds each centre's pairs in order.
+// A W box too close to the centre's disk for its multipole series to converge
+// on the whole disk ((R_c + r_z) > kW |z - m_c|) is summed source by source.
 template <int PM, bool HS, bool HD>
-__global__ void __launch_bounds__(kThreads) m2qbxl_kernel(Fmm F, const int* __restrict__ leaves,
-                                                          cd* __restrict__ alpha) {
-  extern __shared__ cd smem[];
+__global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int* __restrict__ pair_ctr,
+                                                               const int* __restrict__ pair_box,
+                                                               int n_pairs, cd* __restrict__ partial) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_pairs) return;
+  const int i = pair_ctr[t], c = pair_box[t];
   const int p = F.p, P = 2 * p + 1;
-  double* fpw = (double*)smem;           // [2p+1]: s^j, j = -p..p
-  cd* a = smem + (p + 1);                // [Q_c]
-  const int b = leaves[blockIdx.x];
-  const int2 r = F.rctr[b];
-  const int e0 = F.woff[b], e1_ = F.woff[b + 1];
-  if (r.y <= r.x || e1_ <= e0) return;
   const double k = F.k;
-  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
-    const int i = i0 + threadIdx.x;
-    const bool act = i < r.y;
-    cd acc[2 * PM + 1];
+  cd acc[2 * PM + 1];
 #pragma unroll
-    for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
-    for (int e = e0; e < e1_; ++e) {
-      const int c = F.widx[e];
-      const int lc = F.level[c];
-      const double s = F.scale[lc];
-      const int pb = F.lpb[lc], Q = 2 * pb + 1, M = pb + p;
-      const cd* mp = F.mpole + F.eoff[c];
-      __syncthreads();
-      for (int j = threadIdx.x; j < Q; j += kThreads) a[j] = mp[j];
-      for (int j = threadIdx.x; j <= 2 * p; j += kThreads) {
-        double f = 1.0;
-        const int ex = j - p;
-        for (int t = 0; t < abs(ex); ++t) f *= (ex > 0 ? s : 1.0 / s);
-        fpw[j] = f;
-      }
-      __syncthreads();
-      if (!act) continue;
-      const double2 z = F.cxy[i];
-      const double2 mc = F.centre[c];
-      const double dx = z.x - mc.x, dy = z.y - mc.y;
-      const double rr = sqrt(dx * dx + dy * dy);
-      const double Rc = 0.70710678118654752 * F.side / (double)(1 << lc);
-      if (Rc + F.crad[i] > kW * rr) {
-        const int2 sr = F.rsrc[c];
-        for (int j = sr.x; j < sr.y; ++j)
-        {
-          const cd dk = HD ? cscale(F.ds[j], 0.5 * k) : mk(0.0, 0.0);
-          const cd nu = HD ? mk(F.snrm[j].x, F.snrm[j].y) : mk(0.0, 0.0);
-          p2qbxl_pair<PM, HS, HD>(acc, F.sxy[j].x - z.x, F.sxy[j].y - z.y,
-                                  HS ? F.qs[j] : mk(0.0, 0.0), cmul(dk, nu), cmul(dk, cconj(nu)),
-                                  k, p);
+  for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
+  const int lc = F.level[c];
+  const double s = F.scale[lc];
+  const int pb = F.lpb[lc], M = pb + p;
+  const cd* a = F.mpole + F.eoff[c];
+  const double* pwl = pw_row(F, lc);
+  const double* ipl = ipw_row(F, lc);
+  const double2 z = F.cxy[i];
+  const double2 mc = F.centre[c];
+  const double dx = z.x - mc.x, dy = z.y - mc.y;
+  const double rr = sqrt(dx * dx + dy * dy);
+  const double Rc = 0.70710678118654752 * F.side / (double)(1 << lc);
+  if (Rc + F.crad[i] > kW * rr) {
+    const int2 sr = F.rsrc[c];
+    for (int j = sr.x; j < sr.y; ++j) {
+      const cd dk = HD ? cscale(F.ds[j], 0.5 * k) : mk(0.0, 0.0);
+      const cd nu = HD ? mk(F.snrm[j].x, F.snrm[j].y) : mk(0.0, 0.0);
+      p2qbxl_pair<PM, HS, HD>(acc, F.sxy[j].x - z.x, F.sxy[j].y - z.y,
+                              HS ? F.qs[j] : mk(0.0, 0.0), cmul(dk, nu), cmul(dk, cconj(nu)), k, p);
+    }
+  } else {
+    const double x = k * rr;
+    const cd e1 = mk(dx / rr, dy / rr);
+    cd h0, h1;
+    hankel01(x, h0, h1);
+    cd hm1 = h0, hm = h0, ee = mk(1.0, 0.0);
+    for (int mm = 0; mm <= M; ++mm) {
+      if (mm == 1) { hm1 = h0; hm = cscale(h1, s); }
+      if (mm >= 1) ee = cmul(ee, e1);
+      const cd wp = cmul(hm, ee);                                        // Wh_m
+      const cd wq = cscale(cmul(hm, cconj(ee)), (mm & 1) ? -1.0 : 1.0);  // Wh_{-m}
+#pragma unroll
+      for (int lo = -PM; lo <= PM; ++lo) {
+        if (lo < -p || lo > p) continue;
+        const double sg = (lo & 1) ? -1.0 : 1.0;
+        const int n1 = mm - lo;  // n + l = m
+        if (n1 >= -pb && n1 <= pb) {
+          const int ex = abs(n1) - mm;  // s^{|n| - |n+l|}, |ex| <= p
+          cfma(acc[lo + PM], cscale(a[n1 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wp);
         }
-        continue;
-      }
-      const double x = k * rr;
-      const cd e1 = mk(dx / rr, dy / rr);
-      cd h0, h1;
-      hankel01(x, h0, h1);
-      cd hm1 = h0, hm = h0, ee = mk(1.0, 0.0);
-      for (int mm = 0; mm <= M; ++mm) {
-        if (mm == 1) { hm1 = h0; hm = cscale(h1, s); }
-        if (mm >= 1) ee = cmul(ee, e1);
-        const cd wp = cmul(hm, ee);                                        // Wh_m
-        const cd wq = cscale(cmul(hm, cconj(ee)), (mm & 1) ? -1.0 : 1.0);  // Wh_{-m}
-#pragma unroll
-        for (int lo = -PM; lo <= PM; ++lo) {
-          if (lo < -p || lo > p) continue;
-          const double sg = (lo & 1) ? -1.0 : 1.0;
-          const int n1 = mm - lo;  // n + l = m
-          if (n1 >= -pb && n1 <= pb)
-            cfma(acc[lo + PM], cscale(a[n1 + pb], sg * fpw[abs(n1) - mm + p]), wp);
-          if (mm > 0) {
-            const int n2 = -mm - lo;  // n + l = -m
-            if (n2 >= -pb && n2 <= pb)
-              cfma(acc[lo + PM], cscale(a[n2 + pb], sg * fpw[abs(n2) - mm + p]), wq);
+        if (mm > 0) {
+          const int n2 = -mm - lo;  // n + l = -m
+          if (n2 >= -pb && n2 <= pb) {
+            const int ex = abs(n2) - mm;
+            cfma(acc[lo + PM], cscale(a[n2 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wq);
           }
         }
-        if (mm >= 1) {
-          const cd hn = csub(cscale(hm, 2.0 * mm * s / x), cscale(hm1, s * s));
-          hm1 = hm;
-          hm = hn;
-        }
+      }
+      if (mm >= 1) {
+        const cd hn = csub(cscale(hm, 2.0 * mm * s / x), cscale(hm1, s * s));
+        hm1 = hm;
+        hm = hn;
       }
     }
-    if (act) {
-      cd* dst = alpha + (size_t)F.cid[i] * P;
-      for (int lo = -p; lo <= p; ++lo) dst[lo + p] = cadd(dst[lo + p], acc[lo + PM]);
-    }
   }
+  cd* dst = partial + (size_t)t * P;
+  for (int lo = -p; lo <= p; ++lo) dst[lo + p] = acc[lo + PM];
 }
 
-// P2QBXL over the U list (Stage 3 "New"): direct coefficients from nearby sources.
-template <int PM, bool HS, bool HD>
-__global__ void __launch_bounds__(kThreads) p2qbxl_ulist_kernel(Fmm F,
-                                                                const int* __restrict__ leaves,
-                                                                cd* __restrict__ alpha) {
-  __shared__ double2 s_xy[kThreads];
-  __shared__ cd s_nu[kThreads];  // B = d (k/2) conj(nu)
-  __shared__ cd s_q[kThreads];
-  __shared__ cd s_d[kThreads];   // A = d (k/2) nu
-  const int b = leaves[blockIdx.x];
-  const int2 r = F.rctr[b];
-  if (r.y <= r.x) return;
-  const double k = F.k;
-  const int p = F.p, P = 2 * p + 1;
-  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
-    const int i = i0 + threadIdx.x;
-    const bool act = i < r.y;
-    const double cx = act ? F.cxy[i].x : 0.0, cy = act ? F.cxy[i].y : 0.0;
-    cd acc[2 * PM + 1];
-#pragma unroll
-    for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
-    for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
-      const int2 sr = F.rsrc[F.uidx[e]];
-      for (int base = sr.x; base < sr.y; base += kThreads) {
-        __syncthreads();
-        const int j = base + threadIdx.x;
-        if (j < sr.y) {
-          s_xy[threadIdx.x] = F.sxy[j];
-          if (HS) s_q[threadIdx.x] = F.qs[j];
-          if (HD) {
-            const cd dk = cscale(F.ds[j], 0.5 * k);
-            const cd nu = mk(F.snrm[j].x, F.snrm[j].y);
-            s_d[threadIdx.x] = cmul(dk, nu);
-            s_nu[threadIdx.x] = cmul(dk, cconj(nu));
-          }
-        }
-        __syncthreads();
-        const int cnt = min(kThreads, sr.y - base);
-        if (!act) continue;
-        for (int jj = 0; jj < cnt; ++jj)
-          p2qbxl_pair<PM, HS, HD>(acc, s_xy[jj].x - cx, s_xy[jj].y - cy,
-                                  HS ? s_q[jj] : mk(0.0, 0.0), HD ? s_d[jj] : mk(0.0, 0.0),
-                                  HD ? s_nu[jj] : mk(0.0, 0.0), k, p);
-      }
-    }
-    if (act) {
-      cd* dst = alpha + (size_t)F.cid[i] * P;
-      for (int lo = -p; lo <= p; ++lo) dst[lo + p] = cadd(dst[lo + p], acc[lo + PM]);
-    }
-  }
+// alpha[centre] += sum of its pairs' partial coefficients, in pair order.
+__global__ void m2qbxl_sum_kernel(int n_ctr, int P, const int* __restrict__ cpo,
+                                  const cd* __restrict__ partial, const int* __restrict__ cid,
+                                  cd* __restrict__ alpha) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)n_ctr * P) return;
+  const int i = (int)(g / P), l = (int)(g % P);
+  const int t0 = cpo[i], t1 = cpo[i + 1];
+  if (t1 == t0) return;
+  cd sum = mk(0.0, 0.0);
+  for (int t = t0; t < t1; ++t) sum = cadd(sum, partial[(size_t)t * P + l]);
+  cd* dst = alpha + (size_t)cid[i] * P + l;
+  *dst = cadd(*dst, sum);
 }
 
 // ---------------------------------------------------------------- mixed precision P2QBXL
@@ -1057,84 +1014,9 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   }
 }
 
-template <int PM, bool HS, bool HD>
-__global__ void __launch_bounds__(kThreads) p2qbxl_ulist_mixed_kernel(
-    Fmm F, const int* __restrict__ leaves, cd* __restrict__ alpha) {
-  __shared__ double2 s_xy[kThreads];
-  __shared__ float2 s_q[kThreads];
-  __shared__ float2 s_A[kThreads];
-  __shared__ float2 s_B[kThreads];
-  const int b = leaves[blockIdx.x];
-  const int2 r = F.rctr[b];
-  if (r.y <= r.x) return;
-  const double k = F.k;
-  const int p = F.p, P = 2 * p + 1;
-  for (int i0 = r.x; i0 < r.y; i0 += kThreads) {
-    const int i = i0 + threadIdx.x;
-    const bool act = i < r.y;
-    const double cx = act ? F.cxy[i].x : 0.0, cy = act ? F.cxy[i].y : 0.0;
-    const double rho = act ? k * F.crad[i] : 1.0;
-    float2 S[2 * PM + 1], C[2 * PM + 1];
-#pragma unroll
-    for (int j = 0; j <= 2 * PM; ++j) S[j] = C[j] = make_float2(0.f, 0.f);
-    for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
-      const int2 sr = F.rsrc[F.uidx[e]];
-      for (int base = sr.x; base < sr.y; base += kThreads) {
-        __syncthreads();
-        const int j = base + threadIdx.x;
-        if (j < sr.y) {
-          s_xy[threadIdx.x] = F.sxy[j];
-          if (HS) s_q[threadIdx.x] = f2(F.qs[j]);
-          if (HD) {  // A = d (k/2) nu, B = d (k/2) conj(nu)
-            const cd dk = cscale(F.ds[j], 0.5 * k);
-            const cd nu = mk(F.snrm[j].x, F.snrm[j].y);
-            s_A[threadIdx.x] = f2(cmul(dk, nu));
-            s_B[threadIdx.x] = f2(cmul(dk, cconj(nu)));
-          }
-        }
-        __syncthreads();
-        const int cnt = min(kThreads, sr.y - base);
-        if (!act) continue;
-        for (int jj = 0; jj < cnt; ++jj)
-          p2qbxl_pair_mixed<PM, HS, HD>(S, C, s_xy[jj].x - cx, s_xy[jj].y - cy,
-                                        HS ? s_q[jj] : make_float2(0.f, 0.f),
-                                        HD ? s_A[jj] : make_float2(0.f, 0.f),
-                                        HD ? s_B[jj] : make_float2(0.f, 0.f), k, rho, p);
-      }
-    }
-    if (act) {
-      cd* dst = alpha + (size_t)F.cid[i] * P;
-      double ip = 1.0;
-      const double irho = 1.0 / rho;
-#pragma unroll
-      for (int m = 0; m <= PM; ++m) {
-        if (m > p) break;
-        const float2 sp = S[PM + m], cp = C[PM + m];
-        dst[p + m] = cadd(dst[p + m], mk(((double)sp.x - cp.x) * ip, ((double)sp.y - cp.y) * ip));
-        if (m > 0) {
-          const float2 sn = S[PM - m], cn = C[PM - m];
-          dst[p - m] = cadd(dst[p - m], mk(((double)sn.x - cn.x) * ip, ((double)sn.y - cn.y) * ip));
-        }
-        ip *= irho;
-      }
-    }
-  }
-}
-
 // Lift the 48 KB default of dynamic shared memory to the device's opt-in
 // maximum for every kernel that uses it (once per device); the size given at
 // each launch still decides the occupancy.
-template <int PM>
-cudaError_t allow_smem_centre(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute((const void*)l2qbxl_kernel<PM>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  const void* k[3] = {(const void*)m2qbxl_kernel<PM, true, true>,
-                      (const void*)m2qbxl_kernel<PM, true, false>,
-                      (const void*)m2qbxl_kernel<PM, false, true>};
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
-    e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  return e;
-}
 
 qbx_status configure_kernels() {
   static std::mutex mu;
@@ -1150,14 +1032,128 @@ qbx_status configure_kernels() {
                      (const void*)m2p_kernel};
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  QBX_CUDA_TRY(allow_smem_centre<4>(optin));
-  QBX_CUDA_TRY(allow_smem_centre<8>(optin));
-  QBX_CUDA_TRY(allow_smem_centre<12>(optin));
-  QBX_CUDA_TRY(allow_smem_centre<16>(optin));
   TRY_MIXED(configure_mixed_kernels(optin));
   g_smem_optin = optin;
   done.insert(dev);
   return QBX_OK;
+}
+
+// ---------------------------------------------------------------- P2QBXL, one warp per centre
+// Lanes stride over the concatenated sources of the centre's U-list boxes (so
+// the load is balanced to within one source), each lane keeps partial
+// coefficients, and a reduce-scatter of shuffles adds them: after it, lane L
+// holds coefficient indices K L .. K L + K - 1 of the 32 K padded ones
+// (K = 1 for p <= 15, 2 for p = 16). Padding indices hold zeros.
+template <int NC>
+__device__ __forceinline__ void warp_reduce_scatter(cd (&acc)[NC], int lane) {
+  constexpr int NP = 32 * ((NC + 31) / 32);
+#pragma unroll
+  for (int h = NP / 2, off = 16; off >= 1; h >>= 1, off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const cd lo = i < NC ? acc[i] : mk(0.0, 0.0);
+      const cd hi = i + h < NC ? acc[i + h] : mk(0.0, 0.0);
+      const cd send = upper ? lo : hi;
+      cd keep = upper ? hi : lo;
+      keep.x += __shfl_xor_sync(0xffffffffu, send.x, off);
+      keep.y += __shfl_xor_sync(0xffffffffu, send.y, off);
+      if (i < NC) acc[i] = keep;
+    }
+  }
+}
+
+// For each source of the U list of leaf b, in an order that deals the
+// concatenated sources round-robin over the lanes, call fn(j).
+template <typename Fn>
+__device__ __forceinline__ void for_ulist_sources(const Fmm& F, int b, int lane, Fn&& fn) {
+  int t0 = 0;  // index of the box's first source in the concatenation
+  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
+    const int2 sr = F.rsrc[F.uidx[e]];
+    const int cnt = sr.y - sr.x;
+    for (int jl = (lane - t0) & 31; jl < cnt; jl += 32) fn(sr.x + jl);
+    t0 += cnt;
+  }
+}
+
+template <int PM, bool HS, bool HD>
+__global__ void __launch_bounds__(kThreads) p2qbxl_warp_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                               int n_ctr, cd* __restrict__ alpha) {
+  const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // sorted centre
+  const int lane = threadIdx.x & 31;
+  if (i >= n_ctr) return;  // whole warps leave together
+  const int b = cleaf[i];
+  const double k = F.k;
+  const int p = F.p, P = 2 * p + 1;
+  const double2 c = F.cxy[i];
+  cd acc[2 * PM + 1];
+#pragma unroll
+  for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
+  for_ulist_sources(F, b, lane, [&](int j) {
+    const double2 y = F.sxy[j];
+    cd A = mk(0.0, 0.0), B = mk(0.0, 0.0);
+    if (HD) {
+      const cd dk = cscale(F.ds[j], 0.5 * k);
+      const cd nu = mk(F.snrm[j].x, F.snrm[j].y);
+      A = cmul(dk, nu);
+      B = cmul(dk, cconj(nu));
+    }
+    p2qbxl_pair<PM, HS, HD>(acc, y.x - c.x, y.y - c.y, HS ? F.qs[j] : mk(0.0, 0.0), A, B, k, p);
+  });
+  warp_reduce_scatter<2 * PM + 1>(acc, lane);
+  constexpr int K = (2 * PM + 1 + 31) / 32;
+  cd* dst = alpha + (size_t)F.cid[i] * P;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int lo = K * lane + j - PM;
+    if (lo >= -p && lo <= p) dst[lo + p] = cadd(dst[lo + p], acc[j]);
+  }
+}
+
+template <int PM, bool HS, bool HD>
+__global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                                     int n_ctr, cd* __restrict__ alpha) {
+  const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n_ctr) return;
+  const int b = cleaf[i];
+  const double k = F.k;
+  const int p = F.p, P = 2 * p + 1;
+  const double2 c = F.cxy[i];
+  const double rho = k * F.crad[i];
+  float2 S[2 * PM + 1], C[2 * PM + 1];
+#pragma unroll
+  for (int j = 0; j <= 2 * PM; ++j) S[j] = C[j] = make_float2(0.f, 0.f);
+  for_ulist_sources(F, b, lane, [&](int j) {
+    const double2 y = F.sxy[j];
+    float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+    if (HD) {  // A = d (k/2) nu, B = d (k/2) conj(nu)
+      const cd dk = cscale(F.ds[j], 0.5 * k);
+      const cd nu = mk(F.snrm[j].x, F.snrm[j].y);
+      A = f2(cmul(dk, nu));
+      B = f2(cmul(dk, cconj(nu)));
+    }
+    p2qbxl_pair_mixed<PM, HS, HD>(S, C, y.x - c.x, y.y - c.y,
+                                  HS ? f2(F.qs[j]) : make_float2(0.f, 0.f), A, B, k, rho, p);
+  });
+  // lane partial sums (compensation removed) in FP64, then the warp sum
+  cd acc[2 * PM + 1];
+#pragma unroll
+  for (int j = 0; j <= 2 * PM; ++j)
+    acc[j] = mk((double)S[j].x - (double)C[j].x, (double)S[j].y - (double)C[j].y);
+  warp_reduce_scatter<2 * PM + 1>(acc, lane);
+  constexpr int K = (2 * PM + 1 + 31) / 32;
+  cd* dst = alpha + (size_t)F.cid[i] * P;
+  const double irho = 1.0 / rho;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int lo = K * lane + j - PM;
+    if (lo >= -p && lo <= p) {
+      double ip = 1.0;  // rho^-|lo|: ah_l = alpha_l rho^|l|
+      for (int t = 0; t < abs(lo); ++t) ip *= irho;
+      dst[lo + p] = cadd(dst[lo + p], cscale(acc[j], ip));
+    }
+  }
 }
 
 int p_add_default(int p) {
@@ -1293,6 +1289,35 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     for (int e = woff[b]; e < woff[b + 1]; ++e)
       f->q_w = std::max(f->q_w, 2 * f->h_pb[blev[widx[e]]] + 1);
   }
+  // leaf of every centre (sorted order)
+  std::vector<int> cl(std::max<int64_t>(1, h->n_ctr), 0);
+  for (int b : leaves)
+    for (int i = rc[b].x; i < rc[b].y; ++i) cl[i] = b;
+  QBX_CUDA_TRY(f->cleaf.alloc(cl.size()));
+  QBX_CUDA_TRY(cudaMemcpy(f->cleaf.ptr, cl.data(), cl.size() * sizeof(int),
+                          cudaMemcpyHostToDevice));
+  // (centre, W-list box) pairs for M2QBXL in sorted-centre order, CSR by centre
+  {
+    std::vector<int> pc, pbx, off(std::max<int64_t>(1, h->n_ctr) + 1, 0);
+    for (int64_t i = 0; i < h->n_ctr; ++i) {
+      const int b = cl[i];
+      for (int e = woff[b]; e < woff[b + 1]; ++e) {
+        pc.push_back((int)i);
+        pbx.push_back(widx[e]);
+      }
+      off[i + 1] = (int)pc.size();
+    }
+    f->n_wpairs = (int)pc.size();
+    QBX_CUDA_TRY(f->wp_ctr.alloc(std::max<size_t>(1, pc.size())));
+    QBX_CUDA_TRY(f->wp_box.alloc(std::max<size_t>(1, pc.size())));
+    QBX_CUDA_TRY(f->wp_off.alloc(off.size()));
+    QBX_CUDA_TRY(f->wpart.alloc(std::max<size_t>(1, pc.size() * (size_t)(2 * h->p + 1))));
+    if (!pc.empty()) {
+      QBX_CUDA_TRY(cudaMemcpy(f->wp_ctr.ptr, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->wp_box.ptr, pbx.data(), pbx.size() * 4, cudaMemcpyHostToDevice));
+    }
+    QBX_CUDA_TRY(cudaMemcpy(f->wp_off.ptr, off.data(), off.size() * 4, cudaMemcpyHostToDevice));
+  }
   // leaves come in level order, so src_leaves does too
   f->src_leaf_off.assign(f->n_levels + 1, 0);
   for (int b : src_leaves) f->src_leaf_off[blev[b] + 1] += 1;
@@ -1357,29 +1382,39 @@ template <int PM>
 qbx_status launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
                                  cd* alpha, bool mixed, cudaStream_t s) {
   stage_begin(h, QBX_STAGE_L2QBXL, s);
-  l2qbxl_kernel<PM><<<f->n_leaves, kThreads, (size_t)f->q_leaf * sizeof(cd), s>>>(F, f->leaves.ptr, alpha);
+  l2qbxl_kernel<PM><<<nblk(h->n_ctr, kThreads), kThreads, 0, s>>>(F, f->cleaf.ptr, (int)h->n_ctr, alpha);
   QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
   stage_begin(h, QBX_STAGE_M2QBXL, s);
-  const size_t smW = (size_t)(f->q_w + h->p + 1) * sizeof(cd);
-  if (S && D) m2qbxl_kernel<PM, true, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
-  else if (S) m2qbxl_kernel<PM, true, false><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
-  else if (D) m2qbxl_kernel<PM, false, true><<<f->n_leaves, kThreads, smW, s>>>(F, f->leaves.ptr, alpha);
-  QBX_KCHECK("m2qbxl", s);
+  if (f->n_wpairs > 0 && (S || D)) {
+    const int np = f->n_wpairs;
+    cd* part = f->wpart.ptr;
+    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<nblk(np, kThreads), kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
+    else if (S) m2qbxl_pair_kernel<PM, true, false><<<nblk(np, kThreads), kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
+    else m2qbxl_pair_kernel<PM, false, true><<<nblk(np, kThreads), kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
+    QBX_KCHECK("m2qbxl", s);
+    const int P = 2 * h->p + 1;
+    m2qbxl_sum_kernel<<<nblk(h->n_ctr * P, 256), 256, 0, s>>>((int)h->n_ctr, P, f->wp_off.ptr, part,
+                                                              f->perm[PT_CTR].ptr, alpha);
+    QBX_KCHECK("m2qbxl_sum", s);
+    h->launches += 2;
+  }
   stage_end(h, QBX_STAGE_M2QBXL, s);
   stage_begin(h, QBX_STAGE_P2QBXL, s);
+  const int nc = (int)h->n_ctr;
+  const unsigned gw = nblk(nc, kThreads / 32);  // one warp per centre
   if (mixed) {
-    if (S && D) p2qbxl_ulist_mixed_kernel<PM, true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
-    else if (S) p2qbxl_ulist_mixed_kernel<PM, true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
-    else if (D) p2qbxl_ulist_mixed_kernel<PM, false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+    if (S && D) p2qbxl_warp_mixed_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
+    else if (S) p2qbxl_warp_mixed_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
+    else if (D) p2qbxl_warp_mixed_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
   } else {
-    if (S && D) p2qbxl_ulist_kernel<PM, true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
-    else if (S) p2qbxl_ulist_kernel<PM, true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
-    else if (D) p2qbxl_ulist_kernel<PM, false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, alpha);
+    if (S && D) p2qbxl_warp_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
+    else if (S) p2qbxl_warp_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
+    else if (D) p2qbxl_warp_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
   }
-  QBX_KCHECK("p2qbxl_ulist", s);
+  QBX_KCHECK("p2qbxl", s);
   stage_end(h, QBX_STAGE_P2QBXL, s);
-  h->launches += (S || D) ? 3 : 2;
+  h->launches += (S || D) ? 2 : 1;
   return QBX_OK;
 }
 
@@ -1461,21 +1496,26 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     QBX_KCHECK("l2l", s);
     h->launches += 1;
   }
+  if (f->n_leaves > 0) {
+    unscale_leaf_locals_kernel<<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr);
+    QBX_KCHECK("unscale_leaf_locals", s);
+    h->launches += 1;
+  }
   stage_end(h, QBX_STAGE_L2L, s);
   // Stages 3, 5, 8 at targets
   if (f->n_leaves > 0 && h->n_direct_tgt > 0) {
     stage_begin(h, QBX_STAGE_L2P, s);
-    l2p_kernel<<<f->n_leaves, kThreads, (size_t)f->q_leaf * sizeof(cd), s>>>(F, f->leaves.ptr, out);
+    l2p_kernel<<<f->n_leaves, kLeafThreads, (size_t)f->q_leaf * sizeof(cd), s>>>(F, f->leaves.ptr, out);
     QBX_KCHECK("l2p", s);
     stage_end(h, QBX_STAGE_L2P, s);
     stage_begin(h, QBX_STAGE_M2P, s);
-    m2p_kernel<<<f->n_leaves, kThreads, (size_t)f->q_w * sizeof(cd), s>>>(F, f->leaves.ptr, out);
+    m2p_kernel<<<f->n_leaves, kLeafThreads, (size_t)f->q_w * sizeof(cd), s>>>(F, f->leaves.ptr, out);
     QBX_KCHECK("m2p", s);
     stage_end(h, QBX_STAGE_M2P, s);
     stage_begin(h, QBX_STAGE_P2P, s);
-    if (S && D) p2p_ulist_kernel<true, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, out);
-    else if (S) p2p_ulist_kernel<true, false><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, out);
-    else if (D) p2p_ulist_kernel<false, true><<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr, out);
+    if (S && D) p2p_ulist_kernel<true, true><<<f->n_leaves, kLeafThreads, 0, s>>>(F, f->leaves.ptr, out);
+    else if (S) p2p_ulist_kernel<true, false><<<f->n_leaves, kLeafThreads, 0, s>>>(F, f->leaves.ptr, out);
+    else if (D) p2p_ulist_kernel<false, true><<<f->n_leaves, kLeafThreads, 0, s>>>(F, f->leaves.ptr, out);
     stage_end(h, QBX_STAGE_P2P, s);
     h->launches += (S || D) ? 3 : 2;
   }

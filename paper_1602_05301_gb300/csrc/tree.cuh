@@ -58,6 +58,11 @@ struct FmmPlan {
   // src_leaves, xbox and vbox are ordered by level; [n_levels + 1] offsets
   std::vector<int> src_leaf_off, xbox_off, vbox_off;
   int q_leaf = 1, q_w = 1;              // largest Q_l among leaves / W-list boxes
+  DevBuf<int> cleaf;                    // [n_centres] leaf of each sorted centre
+  // M2QBXL work items: (sorted centre, W-list box) pairs grouped by centre
+  int n_wpairs = 0;
+  DevBuf<int> wp_ctr, wp_box, wp_off;   // [n_wpairs], [n_wpairs], [n_centres + 1]
+  DevBuf<cd> wpart;                     // [n_wpairs][2p+1] partial coefficients
   DevBuf<cd> t_m2l;                     // [n_levels][49][4 pb_max + 1] scaled Hankel vectors
   DevBuf<cd> t_m2m;                     // [n_levels][4][4 pb_max + 1] conj(V_m(d)) child->parent
   DevBuf<cd> t_l2l;                     // [n_levels][4][4 pb_max + 1] (-1)^m V_m(d) parent->child
