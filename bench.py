@@ -8,7 +8,12 @@ qbx_layer_potential_eval over all targets with the plan prebuilt and the
 density resident on the device. L2 is flushed (a 256 MiB write) before every
 timed step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+The headline is the mixed-precision path (FP32 M2L and P2QBXL accumulation,
+FP64 special functions and final sums) at its stated error against the FP64
+path, which is timed on the same plan and inputs and reported beside it, with
+the speedup over the cheapest FP64 plan (lowest p_fmm) of equal accuracy.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
                   [--mode fmm|direct] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the plain, slow definition) on the
@@ -33,6 +38,9 @@ sys.path.insert(0, ROOT)
 METRIC = "QBX-FMM layer-potential targets/sec at stated rel err, mixed vs FP64 on 1 GB300"
 UNIT = "targets/s"
 CONFIG_NUM = 2
+WORKLOADS = {2: "%s: starfish r=1+0.3cos5t, k=10, 512 panels x 16 GL (8192 sources, 16384 "
+                "centres), D+ikS with random Fourier density |n|<=20, p=12, p_fmm=20, 316x316 "
+                "grid targets on [-2,2]^2"}
 # FP64 FMA peak of a GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP32 FMA peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.070 GHz.
@@ -165,7 +173,12 @@ def flop_model(lp, stats, p, has_S, has_D, assoc, fmm):
     f["p2l"] = 16 * lay * int(np.sum(Qb[xb] * nsrc[xc]))
     wb, wc = entries(2)
     wq = np.bincount(wb, weights=Qb[wc], minlength=nb)
-    f["m2qbxl"] = 8 * P * int(np.sum((nctr * wq)[leaf]))
+    # M2QBXL runs for the (centre, W box) pairs whose box is far enough from the
+    # centre's disk (stats m2qbxl_pairs; the others are P2QBXL pairs), charged at
+    # the mean box order over the W lists of the centres' leaves
+    w_all = float(np.sum((nctr * (wq > 0) * np.diff(t["off"][2]))[leaf]))
+    w_q = float(np.sum((nctr * wq)[leaf]))
+    f["m2qbxl"] = int(8 * P * stats["m2qbxl_pairs"] * (w_q / w_all if w_all else 0.0))
     f["m2p"] = 16 * int(np.sum((ndir * wq)[leaf]))
     f["l2qbxl"] = 8 * P * int(np.sum((nctr * Qb)[leaf]))
     f["l2p"] = 16 * int(np.sum((ndir * Qb)[leaf]))
@@ -173,6 +186,36 @@ def flop_model(lp, stats, p, has_S, has_D, assoc, fmm):
 
 
 # ---------------------------------------------------------------- our arm
+def timed_steps(step, steps, warmup, stream, flush, ws, dev, lp):
+    """Device time of `steps` calls of step() (after `warmup` untimed ones), L2
+    flushed before each, CUDA events on the launching stream; max over ranks."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    launches = 0
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+        launches += lp.stats()["launches"]
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), ws, dev)
+    return total_ms, launches
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
 def run_ours(args, w, ws, rank, local):
     import torch
     from paper_1602_05301_gb300 import qbx
@@ -180,7 +223,8 @@ def run_ours(args, w, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     g = w["geom"]
-    mode = qbx.QBX_FMM if args.mode == "fmm" else qbx.QBX_DIRECT
+    fmm = args.mode == "fmm"
+    mode = qbx.QBX_FMM if fmm else qbx.QBX_DIRECT
     prec = qbx.QBX_MIXED if args.precision == "mixed" else qbx.QBX_FP64
     lp = qbx.LayerPotential(g.as_dict(), w["p"], sides=w["sides"])
     t0 = time.perf_counter()
@@ -195,57 +239,77 @@ def run_ours(args, w, ws, rank, local):
     sp = stream.cuda_stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
-        lp.eval(sigma_S=sS, sigma_D=sD, cS=w["cS"], cD=w["cD"], out=out, precision=prec,
-                stream=sp)
+    def stepper(handle, pr, o):
+        return lambda: handle.eval(sigma_S=sS, sigma_D=sD, cS=w["cS"], cD=w["cD"], out=o,
+                                   precision=pr, stream=sp)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    launches = 0
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            flush.zero_()
-            evs[i][0].record(stream)
-            step()
-            evs[i][1].record(stream)
-            launches += lp.stats()["launches"]
-        torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = max_over_ranks(sum(step_ms), ws, dev)
+        total_ms, launches = timed_steps(stepper(lp, prec, out), args.steps, args.warmup, stream,
+                                         flush, ws, dev, lp)
     value = job_throughput(n_t, ws, args.steps, total_ms)
     stats = lp.stats()
+    u_main = out.cpu().numpy()
+
+    # the other precision on the same plan and inputs: speed and the stated error
+    other = qbx.QBX_FP64 if prec == qbx.QBX_MIXED else qbx.QBX_MIXED
+    out2 = torch.empty_like(out)
+    ms2, _ = timed_steps(stepper(lp, other, out2), args.steps, args.warmup, stream, flush, ws,
+                         dev, lp)
+    u_other = out2.cpu().numpy()
+    u64, u32 = (u_other, u_main) if prec == qbx.QBX_MIXED else (u_main, u_other)
+    err_mixed = rel_l2(u32, u64)
+    comparison = {"fp64" if other == qbx.QBX_FP64 else "mixed": {
+        "value": job_throughput(n_t, ws, args.steps, ms2), "ms_per_step": ms2 / args.steps}}
+
+    # speedup at equal accuracy: the fastest FP64 plan, over box orders p_fmm + p_add
+    # from 8 up to the workload's own, whose error against the full-order FP64
+    # result is no larger than the mixed path's
+    eq = None
+    if fmm and not args.no_equal_accuracy:
+        eq_rows = []
+        for pf, pa in [(q, 0) for q in range(8, 52, 4)] + [(w["p_fmm"], -1)]:
+            lq = qbx.LayerPotential(g.as_dict(), w["p"], sides=w["sides"])
+            lq.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"], mode=mode,
+                     p_fmm=pf, p_add=pa, n_max=args.n_max, eps_assoc=w["eps_assoc"])
+            oq = torch.empty_like(out)
+            msq, _ = timed_steps(stepper(lq, qbx.QBX_FP64, oq), max(3, args.steps // 4), 2,
+                                 stream, flush, ws, dev, lq)
+            eq_rows.append({"p_fmm": pf, "p_add": pa, "p_box_finest": int(lq.stats()["p_box"]),
+                            "rel_err_vs_fp64": rel_l2(oq.cpu().numpy(), u64),
+                            "value": job_throughput(n_t, ws, max(3, args.steps // 4), msq)})
+            lq.close()
+        ok = [r for r in eq_rows if r["rel_err_vs_fp64"] <= err_mixed]
+        best = max(ok, key=lambda r: r["value"]) if ok else None
+        mixed_value = value if prec == qbx.QBX_MIXED else comparison["mixed"]["value"]
+        eq = {"mixed_rel_err_vs_fp64": err_mixed, "fp64_sweep": eq_rows,
+              "fp64_at_equal_accuracy": best,
+              "speedup_mixed_over_fp64": (mixed_value / best["value"]) if best else None}
 
     # per-kernel device times (events around each kernel class on the eval stream)
     lp.set_timing(True)
     per = {}
     for _ in range(3):
         flush.zero_()
-        step()
+        stepper(lp, prec, out)()
         for kname, ms in lp.stage_times().items():
             per.setdefault(kname, []).append(ms)
     lp.set_timing(False)
     per = {k: statistics.median(v) for k, v in per.items() if max(v) > 0}
-    flops = flop_model(lp, stats, w["p"], sS is not None, sD is not None, assoc,
-                       mode == qbx.QBX_FMM)
+    flops = flop_model(lp, stats, w["p"], sS is not None, sD is not None, assoc, fmm)
     dom = max(per, key=per.get) if per else None
     roof = None
     if dom:
         achieved = flops.get(dom, 0) / (per[dom] / 1e3) / 1e12
-        peak = FP32_PEAK_TFLOPS if (prec == qbx.QBX_MIXED and dom in ("m2l", "l2l", "m2m")) \
-            else FP64_PEAK_TFLOPS
+        fp32 = prec == qbx.QBX_MIXED and dom in ("m2l",)
+        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": KNOWN_TRAFFIC.get((w["name"], dom, args.mode, args.precision)),
                 "flops_per_launch": flops.get(dom, 0), "ms_per_launch": per[dom],
-                "peak_basis": "derived: 152 SMs x FMA/clk x 2 x 2.070 GHz (see DESIGN.md)"}
+                "peak_basis": ("FP32" if fp32 else "FP64") +
+                              " FMA rate derived from unit counts and the 2.070 GHz max clock "
+                              "(152 SMs x %s FMA/clk x 2 flop); measured here: FP64 1.25, "
+                              "FP32 69.6 TFLOP/s" % ("128" if fp32 else "2")}
 
     # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
     hS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).pin_memory() if sS is not None else None
@@ -272,17 +336,16 @@ def run_ours(args, w, ws, rank, local):
                scaling="weak", vs_baseline=None,
                dtype="f64" if prec == qbx.QBX_FP64 else "f32+f64",
                data="synthetic",
-               config={"workload": "%s: starfish r=1+0.3cos5t, k=10, 512 panels x 16 GL "
-                                   "(8192 sources, 16384 centres), D+ikS, p=12, p_fmm=20, "
-                                   "316x316 grid targets" % w["name"],
+               rel_err_mixed_vs_fp64=err_mixed,
+               config={"workload": WORKLOADS[CONFIG_NUM] % w["name"],
                        "mode": args.mode, "precision": args.precision, "n_targets": n_t,
                        "n_qbx_targets": stats["n_qbx_targets"],
-                       "box_orders": [int(x) for x in lp.box_orders()] if mode == qbx.QBX_FMM else None,
+                       "box_orders": [int(x) for x in lp.box_orders()] if fmm else None,
                        "n_boxes": stats["n_boxes"], "tree_build_s": tree_s,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single"},
                roofline=roof, per_kernel_ms=per, gpu_launches=launches,
-               clocks=clk.summary(), e2e=e2e)
+               clocks=clk.summary(), e2e=e2e, equal_accuracy=eq, **comparison)
     lp.close()
     return res
 
@@ -369,10 +432,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--mode", default="fmm", choices=["fmm", "direct"])
     ap.add_argument("--n-max", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-equal-accuracy", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     from qbx_workloads import make_config

@@ -525,161 +525,152 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Fmm F, const int* __restr
 // CTA per leaf; one thread per target of the leaf (strided). Only targets that
 // are not associated with a QBX centre are evaluated.
 // L2P writes out[t], M2P and P2P add to it.
-__global__ void __launch_bounds__(kLeafThreads) l2p_kernel(Fmm F, const int* __restrict__ leaves,
+// Deal the sources of box c round-robin over the lanes, continuing the
+// concatenation at index t0 (updated), calling fn(j) for this lane's sources.
+template <typename Fn>
+__device__ __forceinline__ void deal_box_sources(const Fmm& F, int c, int lane, int& t0, Fn&& fn) {
+  const int2 sr = F.rsrc[c];
+  const int cnt = sr.y - sr.x;
+  for (int jl = (lane - t0) & 31; jl < cnt; jl += 32) fn(sr.x + jl);
+  t0 += cnt;
+}
+
+// For each source of the U list of leaf b, in an order that deals the
+// concatenated sources round-robin over the lanes, call fn(j).
+template <typename Fn>
+__device__ __forceinline__ void for_ulist_sources(const Fmm& F, int b, int lane, Fn&& fn) {
+  int t0 = 0;  // index of the box's first source in the concatenation
+  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) deal_box_sources(F, F.uidx[e], lane, t0, fn);
+}
+
+// L2P: one thread per direct target (sorted index list), from the true local
+// coefficients gamma of its leaf. Writes out (the first of the target stages).
+__global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restrict__ dtgt,
+                                                       const int* __restrict__ tleaf, int n,
                                                        cd* __restrict__ out) {
-  extern __shared__ cd smem[];
-  cd* g = smem;
-  const int b = leaves[blockIdx.x];
-  const int2 r = F.rtgt[b];
-  if (r.y <= r.x) return;
-  const int l = F.level[b];
-  const int pb = F.lpb[l], Q = 2 * pb + 1;
-  const cd* lp = F.local + F.eoff[b];  // true local coefficients (unscaled)
-  for (int i = threadIdx.x; i < Q; i += kLeafThreads) g[i] = lp[i];
-  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = dtgt[t];
+  const int b = tleaf[i];
+  const int pb = F.lpb[F.level[b]];
+  const cd* g = F.local + F.eoff[b];
   const double2 m = F.centre[b];
-  for (int i = r.x + threadIdx.x; i < r.y; i += kLeafThreads) {
-    if (F.tassoc[i] >= 0) continue;
-    const double dx = F.txy[i].x - m.x, dy = F.txy[i].y - m.y;
-    const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-    const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
-    // psi = sum_m f_m [g_m e^{-im th} + (m>0) (-1)^m g_{-m} e^{im th}] / norm
-    cd epb = mk(1.0, 0.0);
-    for (int j = 0; j < pb; ++j) epb = cmul(epb, e1);  // e^{i pb th}
-    cd acc = mk(0.0, 0.0);
-    double norm;
-    if (x < 1e-8) {
-      acc = g[pb];  // only J_0 survives
-      norm = 1.0;
-    } else {
-      const double inv = 2.0 / x;
-      const int N = miller_start(pb, x);
-      double fn1 = 0.0, fn = 1e-200, sum = 0.0;
-      cd e = epb;  // e^{i m th} for the current m (set when m <= pb)
-      for (int n = N; n >= 1; --n) {
-        const double fm = (double)n * inv * fn - fn1;  // f_{n-1}
-        if ((n & 1) == 0) sum += fn;
-        const int mm = n - 1;
-        if (mm <= pb) {
-          if (mm < pb) e = cmul(e, cconj(e1));
-          cfma(acc, cscale(g[pb + mm], fm), cconj(e));
-          if (mm > 0) cfma(acc, cscale(g[pb - mm], (mm & 1) ? -fm : fm), e);
-        }
-        fn1 = fn;
-        fn = fm;
-        if (fabs(fn) > kRescale) {
-          const double sc = 1.0 / kRescale;
-          fn *= sc; fn1 *= sc; sum *= sc;
-          acc = cscale(acc, sc);
-        }
+  const double dx = F.txy[i].x - m.x, dy = F.txy[i].y - m.y;
+  const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+  const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
+  // psi = sum_m f_m [g_m e^{-im th} + (m>0) (-1)^m g_{-m} e^{im th}] / norm
+  cd epb = mk(1.0, 0.0);
+  for (int j = 0; j < pb; ++j) epb = cmul(epb, e1);  // e^{i pb th}
+  cd acc = mk(0.0, 0.0);
+  double norm;
+  if (x < 1e-8) {
+    acc = g[pb];  // only J_0 survives
+    norm = 1.0;
+  } else {
+    const double inv = 2.0 / x;
+    const int N = miller_start(pb, x);
+    double fn1 = 0.0, fn = 1e-200, sum = 0.0;
+    cd e = epb;  // e^{i m th} for the current m (set when m <= pb)
+    for (int nn = N; nn >= 1; --nn) {
+      const double fm = (double)nn * inv * fn - fn1;  // f_{nn-1}
+      if ((nn & 1) == 0) sum += fn;
+      const int mm = nn - 1;
+      if (mm <= pb) {
+        if (mm < pb) e = cmul(e, cconj(e1));
+        cfma(acc, cscale(g[pb + mm], fm), cconj(e));
+        if (mm > 0) cfma(acc, cscale(g[pb - mm], (mm & 1) ? -fm : fm), e);
       }
-      norm = fn + 2.0 * sum;
+      fn1 = fn;
+      fn = fm;
+      if (fabs(fn) > kRescale) {
+        const double sc = 1.0 / kRescale;
+        fn *= sc; fn1 *= sc; sum *= sc;
+        acc = cscale(acc, sc);
+      }
     }
-    out[F.tid[i]] = cscale(acc, 1.0 / norm);
+    norm = fn + 2.0 * sum;
   }
+  out[F.tid[i]] = cscale(acc, 1.0 / norm);
 }
 
-__global__ void __launch_bounds__(kLeafThreads) m2p_kernel(Fmm F, const int* __restrict__ leaves,
+// M2P: one thread per direct target whose leaf has a W list; adds to out.
+__global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restrict__ wtgt,
+                                                       const int* __restrict__ tleaf, int n,
                                                        cd* __restrict__ out) {
-  extern __shared__ cd smem[];
-  cd* a = smem;
-  const int b = leaves[blockIdx.x];
-  const int2 r = F.rtgt[b];
-  const int e0 = F.woff[b], e1_ = F.woff[b + 1];
-  if (r.y <= r.x || e1_ <= e0) return;
-  for (int i0 = r.x; i0 < r.y; i0 += kLeafThreads) {
-    const int i = i0 + threadIdx.x;
-    const bool act = i < r.y && F.tassoc[i] < 0;
-    cd acc = mk(0.0, 0.0);
-    for (int e = e0; e < e1_; ++e) {
-      const int c = F.widx[e];
-      const int lc = F.level[c];
-      const int pb = F.lpb[lc], Q = 2 * pb + 1;
-      const cd* mp = F.mpole + F.eoff[c];
-      __syncthreads();
-      for (int j = threadIdx.x; j < Q; j += kLeafThreads) a[j] = mp[j];
-      __syncthreads();
-      if (!act) continue;
-      const double s = F.scale[lc];
-      const double2 mc = F.centre[c];
-      const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
-      const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-      const cd e1 = mk(dx / rr, dy / rr);
-      cd h0, h1;
-      hankel01(x, h0, h1);
-      cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
-      cd sum = cmul(a[pb], h0);
-      for (int m = 1; m <= pb; ++m) {
-        ee = cmul(ee, e1);
-        cfma(sum, a[pb + m], cmul(hm, ee));
-        const cd v = cmul(hm, cconj(ee));
-        cfma(sum, a[pb - m], (m & 1) ? mk(-v.x, -v.y) : v);
-        const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
-        hm1 = hm;
-        hm = hn;
-      }
-      acc = cadd(acc, sum);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = wtgt[t];
+  const int b = tleaf[i];
+  cd acc = mk(0.0, 0.0);
+  for (int e = F.woff[b]; e < F.woff[b + 1]; ++e) {
+    const int c = F.widx[e];
+    const int lc = F.level[c];
+    const int pb = F.lpb[lc];
+    const cd* a = F.mpole + F.eoff[c];
+    const double s = F.scale[lc];
+    const double2 mc = F.centre[c];
+    const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
+    const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+    const cd e1 = mk(dx / rr, dy / rr);
+    cd h0, h1;
+    hankel01(x, h0, h1);
+    cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
+    cd sum = cmul(a[pb], h0);
+    for (int m = 1; m <= pb; ++m) {
+      ee = cmul(ee, e1);
+      cfma(sum, a[pb + m], cmul(hm, ee));
+      const cd v = cmul(hm, cconj(ee));
+      cfma(sum, a[pb - m], (m & 1) ? mk(-v.x, -v.y) : v);
+      const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
+      hm1 = hm;
+      hm = hn;
     }
-    if (act) {
-      cd* dst = out + F.tid[i];
-      *dst = cadd(*dst, acc);
-    }
+    acc = cadd(acc, sum);
   }
+  cd* dst = out + F.tid[i];
+  *dst = cadd(*dst, acc);
 }
 
+// P2P over the U list: one warp per direct target whose leaf's U list holds
+// sources; lanes deal the sources round-robin, a shuffle tree adds them.
 template <bool HS, bool HD>
-__global__ void __launch_bounds__(kLeafThreads) p2p_ulist_kernel(Fmm F, const int* __restrict__ leaves,
-                                                             cd* __restrict__ out) {
-  __shared__ double2 s_xy[kLeafThreads];
-  __shared__ double2 s_n[kLeafThreads];
-  __shared__ cd s_q[kLeafThreads];
-  __shared__ cd s_d[kLeafThreads];
-  const int b = leaves[blockIdx.x];
-  const int2 r = F.rtgt[b];
-  if (r.y <= r.x) return;
+__global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __restrict__ utgt,
+                                                            const int* __restrict__ tleaf, int n,
+                                                            cd* __restrict__ out) {
+  const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= n) return;
+  const int i = utgt[t];
+  const int b = tleaf[i];
   const double k = F.k;
-  for (int i0 = r.x; i0 < r.y; i0 += kLeafThreads) {
-    const int i = i0 + threadIdx.x;
-    const bool act = i < r.y && F.tassoc[i] < 0;
-    const double tx = act ? F.txy[i].x : 0.0, ty = act ? F.txy[i].y : 0.0;
-    cd acc = mk(0.0, 0.0);
-    for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
-      const int2 sr = F.rsrc[F.uidx[e]];
-      for (int base = sr.x; base < sr.y; base += kLeafThreads) {
-        __syncthreads();
-        const int j = base + threadIdx.x;
-        if (j < sr.y) {
-          s_xy[threadIdx.x] = F.sxy[j];
-          if (HS) s_q[threadIdx.x] = F.qs[j];
-          if (HD) {
-            s_n[threadIdx.x] = F.snrm[j];
-            s_d[threadIdx.x] = F.ds[j];
-          }
-        }
-        __syncthreads();
-        const int cnt = min(kLeafThreads, sr.y - base);
-        if (!act) continue;
-        for (int jj = 0; jj < cnt; ++jj) {
-          const double dx = tx - s_xy[jj].x, dy = ty - s_xy[jj].y;
-          const double rr = sqrt(dx * dx + dy * dy);
-          if (rr == 0.0) continue;
-          const double x = k * rr;
-          cd h0, h1;
-          if (x < 2.0) {
-            hankel01_series(x, h0, h1);
-          } else {
-            if (HS) h0 = mk(j0(x), y0(x));
-            if (HD) h1 = mk(j1(x), y1(x));
-          }
-          if (HS) cfma(acc, s_q[jj], h0);
-          if (HD) cfma(acc, s_d[jj], cscale(h1, k * (s_n[jj].x * dx + s_n[jj].y * dy) / rr));
-        }
-      }
+  const double tx = F.txy[i].x, ty = F.txy[i].y;
+  cd acc = mk(0.0, 0.0);
+  for_ulist_sources(F, b, lane, [&](int j) {
+    const double dx = tx - F.sxy[j].x, dy = ty - F.sxy[j].y;
+    const double rr = sqrt(dx * dx + dy * dy);
+    if (rr == 0.0) return;
+    const double x = k * rr;
+    cd h0, h1;
+    if (x < 2.0) {
+      hankel01_series(x, h0, h1);
+    } else {
+      if (HS) h0 = mk(j0(x), y0(x));
+      if (HD) h1 = mk(j1(x), y1(x));
     }
-    if (act) {
-      cd* dst = out + F.tid[i];
-      *dst = cadd(*dst, acc);
+    if (HS) cfma(acc, F.qs[j], h0);
+    if (HD) {
+      const double2 nv = F.snrm[j];
+      cfma(acc, F.ds[j], cscale(h1, k * (nv.x * dx + nv.y * dy) / rr));
     }
+  });
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if (lane == 0) {
+    cd* dst = out + F.tid[i];
+    *dst = cadd(*dst, acc);
   }
 }
 
@@ -833,22 +824,28 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
 }
 
 // M2QBXL: alpha_l += (-1)^l sum_n mh_n Wh_{n+l} s^{|n| - |n+l|},  Wh_m = s^|m| W_m(z - m_c),
-// one thread per (centre, W-list box) pair, the pair's coefficients written to
-// partial[pair][2p+1]; m2qbxl_sum_kernel adds each centre's pairs in order.
-// A W box too close to the centre's disk for its multipole series to converge
-// on the whole disk ((R_c + r_z) > kW |z - m_c|) is summed source by source.
+// for the (centre, W-list box) pairs whose box is far enough from the centre's
+// disk for the multipole series to converge on it ((R_c + r_z) <= kW |z - m_c|;
+// the others are summed source by source with the U list in P2QBXL). Each pair
+// is split over kM2qbxlSplit threads by output order; each writes its orders of
+// partial[pair][2p+1], and m2qbxl_sum_kernel adds each centre's pairs in order.
+constexpr int kM2qbxlSplit = 4;
 template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int* __restrict__ pair_ctr,
                                                                const int* __restrict__ pair_box,
                                                                int n_pairs, cd* __restrict__ partial) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int LC = (2 * PM + 1 + kM2qbxlSplit - 1) / kM2qbxlSplit;  // orders per thread
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = g / kM2qbxlSplit, part = g % kM2qbxlSplit;
   if (t >= n_pairs) return;
   const int i = pair_ctr[t], c = pair_box[t];
   const int p = F.p, P = 2 * p + 1;
+  const int lo0 = -p + part * LC;  // first output order of this thread
+  if (lo0 > p) return;
   const double k = F.k;
-  cd acc[2 * PM + 1];
+  cd acc[LC];
 #pragma unroll
-  for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
+  for (int j = 0; j < LC; ++j) acc[j] = mk(0.0, 0.0);
   const int lc = F.level[c];
   const double s = F.scale[lc];
   const int pb = F.lpb[lc], M = pb + p;
@@ -859,52 +856,44 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int*
   const double2 mc = F.centre[c];
   const double dx = z.x - mc.x, dy = z.y - mc.y;
   const double rr = sqrt(dx * dx + dy * dy);
-  const double Rc = 0.70710678118654752 * F.side / (double)(1 << lc);
-  if (Rc + F.crad[i] > kW * rr) {
-    const int2 sr = F.rsrc[c];
-    for (int j = sr.x; j < sr.y; ++j) {
-      const cd dk = HD ? cscale(F.ds[j], 0.5 * k) : mk(0.0, 0.0);
-      const cd nu = HD ? mk(F.snrm[j].x, F.snrm[j].y) : mk(0.0, 0.0);
-      p2qbxl_pair<PM, HS, HD>(acc, F.sxy[j].x - z.x, F.sxy[j].y - z.y,
-                              HS ? F.qs[j] : mk(0.0, 0.0), cmul(dk, nu), cmul(dk, cconj(nu)), k, p);
-    }
-  } else {
-    const double x = k * rr;
-    const cd e1 = mk(dx / rr, dy / rr);
-    cd h0, h1;
-    hankel01(x, h0, h1);
-    cd hm1 = h0, hm = h0, ee = mk(1.0, 0.0);
-    for (int mm = 0; mm <= M; ++mm) {
-      if (mm == 1) { hm1 = h0; hm = cscale(h1, s); }
-      if (mm >= 1) ee = cmul(ee, e1);
-      const cd wp = cmul(hm, ee);                                        // Wh_m
-      const cd wq = cscale(cmul(hm, cconj(ee)), (mm & 1) ? -1.0 : 1.0);  // Wh_{-m}
+  const double x = k * rr;
+  const cd e1 = mk(dx / rr, dy / rr);
+  cd h0, h1;
+  hankel01(x, h0, h1);
+  cd hm1 = h0, hm = h0, ee = mk(1.0, 0.0);
+  for (int mm = 0; mm <= M; ++mm) {
+    if (mm == 1) { hm1 = h0; hm = cscale(h1, s); }
+    if (mm >= 1) ee = cmul(ee, e1);
+    const cd wp = cmul(hm, ee);                                        // Wh_m
+    const cd wq = cscale(cmul(hm, cconj(ee)), (mm & 1) ? -1.0 : 1.0);  // Wh_{-m}
 #pragma unroll
-      for (int lo = -PM; lo <= PM; ++lo) {
-        if (lo < -p || lo > p) continue;
-        const double sg = (lo & 1) ? -1.0 : 1.0;
-        const int n1 = mm - lo;  // n + l = m
-        if (n1 >= -pb && n1 <= pb) {
-          const int ex = abs(n1) - mm;  // s^{|n| - |n+l|}, |ex| <= p
-          cfma(acc[lo + PM], cscale(a[n1 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wp);
-        }
-        if (mm > 0) {
-          const int n2 = -mm - lo;  // n + l = -m
-          if (n2 >= -pb && n2 <= pb) {
-            const int ex = abs(n2) - mm;
-            cfma(acc[lo + PM], cscale(a[n2 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wq);
-          }
+    for (int j = 0; j < LC; ++j) {
+      const int lo = lo0 + j;
+      if (lo > p) break;
+      const double sg = (lo & 1) ? -1.0 : 1.0;
+      const int n1 = mm - lo;  // n + l = m
+      if (n1 >= -pb && n1 <= pb) {
+        const int ex = abs(n1) - mm;  // s^{|n| - |n+l|}, |ex| <= p
+        cfma(acc[j], cscale(a[n1 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wp);
+      }
+      if (mm > 0) {
+        const int n2 = -mm - lo;  // n + l = -m
+        if (n2 >= -pb && n2 <= pb) {
+          const int ex = abs(n2) - mm;
+          cfma(acc[j], cscale(a[n2 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wq);
         }
       }
-      if (mm >= 1) {
-        const cd hn = csub(cscale(hm, 2.0 * mm * s / x), cscale(hm1, s * s));
-        hm1 = hm;
-        hm = hn;
-      }
+    }
+    if (mm >= 1) {
+      const cd hn = csub(cscale(hm, 2.0 * mm * s / x), cscale(hm1, s * s));
+      hm1 = hm;
+      hm = hn;
     }
   }
   cd* dst = partial + (size_t)t * P;
-  for (int lo = -p; lo <= p; ++lo) dst[lo + p] = acc[lo + PM];
+#pragma unroll
+  for (int j = 0; j < LC; ++j)
+    if (lo0 + j <= p) dst[lo0 + j + p] = acc[j];
 }
 
 // alpha[centre] += sum of its pairs' partial coefficients, in pair order.
@@ -1063,21 +1052,10 @@ __device__ __forceinline__ void warp_reduce_scatter(cd (&acc)[NC], int lane) {
   }
 }
 
-// For each source of the U list of leaf b, in an order that deals the
-// concatenated sources round-robin over the lanes, call fn(j).
-template <typename Fn>
-__device__ __forceinline__ void for_ulist_sources(const Fmm& F, int b, int lane, Fn&& fn) {
-  int t0 = 0;  // index of the box's first source in the concatenation
-  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) {
-    const int2 sr = F.rsrc[F.uidx[e]];
-    const int cnt = sr.y - sr.x;
-    for (int jl = (lane - t0) & 31; jl < cnt; jl += 32) fn(sr.x + jl);
-    t0 += cnt;
-  }
-}
-
 template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) p2qbxl_warp_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                               const int* __restrict__ wdoff,
+                                                               const int* __restrict__ wdbox,
                                                                int n_ctr, cd* __restrict__ alpha) {
   const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // sorted centre
   const int lane = threadIdx.x & 31;
@@ -1089,7 +1067,7 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_kernel(Fmm F, const int*
   cd acc[2 * PM + 1];
 #pragma unroll
   for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
-  for_ulist_sources(F, b, lane, [&](int j) {
+  auto one = [&](int j) {
     const double2 y = F.sxy[j];
     cd A = mk(0.0, 0.0), B = mk(0.0, 0.0);
     if (HD) {
@@ -1099,7 +1077,11 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_kernel(Fmm F, const int*
       B = cmul(dk, cconj(nu));
     }
     p2qbxl_pair<PM, HS, HD>(acc, y.x - c.x, y.y - c.y, HS ? F.qs[j] : mk(0.0, 0.0), A, B, k, p);
-  });
+  };
+  // U-list boxes of the leaf, then the W-list boxes summed directly for this centre
+  int t0 = 0;
+  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) deal_box_sources(F, F.uidx[e], lane, t0, one);
+  for (int e = wdoff[i]; e < wdoff[i + 1]; ++e) deal_box_sources(F, wdbox[e], lane, t0, one);
   warp_reduce_scatter<2 * PM + 1>(acc, lane);
   constexpr int K = (2 * PM + 1 + 31) / 32;
   cd* dst = alpha + (size_t)F.cid[i] * P;
@@ -1112,6 +1094,8 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_kernel(Fmm F, const int*
 
 template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                                     const int* __restrict__ wdoff,
+                                                                     const int* __restrict__ wdbox,
                                                                      int n_ctr, cd* __restrict__ alpha) {
   const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -1124,7 +1108,7 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
   float2 S[2 * PM + 1], C[2 * PM + 1];
 #pragma unroll
   for (int j = 0; j <= 2 * PM; ++j) S[j] = C[j] = make_float2(0.f, 0.f);
-  for_ulist_sources(F, b, lane, [&](int j) {
+  auto one = [&](int j) {
     const double2 y = F.sxy[j];
     float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
     if (HD) {  // A = d (k/2) nu, B = d (k/2) conj(nu)
@@ -1135,7 +1119,10 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
     }
     p2qbxl_pair_mixed<PM, HS, HD>(S, C, y.x - c.x, y.y - c.y,
                                   HS ? f2(F.qs[j]) : make_float2(0.f, 0.f), A, B, k, rho, p);
-  });
+  };
+  int t0 = 0;
+  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) deal_box_sources(F, F.uidx[e], lane, t0, one);
+  for (int e = wdoff[i]; e < wdoff[i + 1]; ++e) deal_box_sources(F, wdbox[e], lane, t0, one);
   // lane partial sums (compensation removed) in FP64, then the warp sum
   cd acc[2 * PM + 1];
 #pragma unroll
@@ -1289,6 +1276,36 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     for (int e = woff[b]; e < woff[b + 1]; ++e)
       f->q_w = std::max(f->q_w, 2 * f->h_pb[blev[widx[e]]] + 1);
   }
+  // leaf of every sorted target; direct targets, and those among them whose
+  // leaf has U-list sources (P2P) or a W list (M2P)
+  {
+    std::vector<int> tl(std::max<int64_t>(1, h->n_tgt), 0), dt, ut, wt;
+    for (int b : leaves)
+      for (int i = rt[b].x; i < rt[b].y; ++i) tl[i] = b;
+    std::vector<int64_t> usrc(f->n_boxes, 0);
+    for (int b : leaves)
+      for (int e = uoff[b]; e < uoff[b + 1]; ++e) usrc[b] += rs[uidx[e]].y - rs[uidx[e]].x;
+    for (int64_t i = 0; i < h->n_tgt; ++i) {
+      if (assoc_s[i] >= 0) continue;
+      const int b = tl[i];
+      dt.push_back((int)i);
+      if (usrc[b] > 0) ut.push_back((int)i);
+      if (woff[b + 1] > woff[b]) wt.push_back((int)i);
+    }
+    auto up = [](DevBuf<int>& d, const std::vector<int>& v) -> qbx_status {
+      QBX_CUDA_TRY(d.alloc(std::max<size_t>(1, v.size())));
+      if (!v.empty())
+        QBX_CUDA_TRY(cudaMemcpy(d.ptr, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+      return QBX_OK;
+    };
+    TRY(up(f->tleaf, tl));
+    TRY(up(f->dtgt, dt));
+    TRY(up(f->utgt, ut));
+    TRY(up(f->wtgt, wt));
+    f->n_dtgt = (int)dt.size();
+    f->n_utgt = (int)ut.size();
+    f->n_wtgt = (int)wt.size();
+  }
   // leaf of every centre (sorted order)
   std::vector<int> cl(std::max<int64_t>(1, h->n_ctr), 0);
   for (int b : leaves)
@@ -1296,17 +1313,42 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   QBX_CUDA_TRY(f->cleaf.alloc(cl.size()));
   QBX_CUDA_TRY(cudaMemcpy(f->cleaf.ptr, cl.data(), cl.size() * sizeof(int),
                           cudaMemcpyHostToDevice));
-  // (centre, W-list box) pairs for M2QBXL in sorted-centre order, CSR by centre
+  // (centre, W-list box) pairs in sorted-centre order, CSR by centre: those
+  // whose box is far enough from the centre's disk for M2QBXL
+  // ((R_c + r_z) <= kW |z - m_c|), and the rest, summed directly in P2QBXL
+  int64_t w_direct_src = 0;
   {
+    std::vector<double2> cxy(std::max<int64_t>(1, h->n_ctr)), bctr(f->n_boxes);
+    std::vector<double> crad(std::max<int64_t>(1, h->n_ctr));
+    if (h->n_ctr) {
+      QBX_CUDA_TRY(cudaMemcpy(cxy.data(), f->c_xy.ptr, h->n_ctr * sizeof(double2), cudaMemcpyDeviceToHost));
+      QBX_CUDA_TRY(cudaMemcpy(crad.data(), f->c_r.ptr, h->n_ctr * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    QBX_CUDA_TRY(cudaMemcpy(bctr.data(), f->box.centre.ptr, f->n_boxes * sizeof(double2), cudaMemcpyDeviceToHost));
     std::vector<int> pc, pbx, off(std::max<int64_t>(1, h->n_ctr) + 1, 0);
+    std::vector<int> dbx, doff(std::max<int64_t>(1, h->n_ctr) + 1, 0);
     for (int64_t i = 0; i < h->n_ctr; ++i) {
       const int b = cl[i];
       for (int e = woff[b]; e < woff[b + 1]; ++e) {
-        pc.push_back((int)i);
-        pbx.push_back(widx[e]);
+        const int c = widx[e];
+        const double dx = cxy[i].x - bctr[c].x, dy = cxy[i].y - bctr[c].y;
+        const double Rc = 0.70710678118654752 * f->side / (double)(1 << blev[c]);
+        if (Rc + crad[i] > kW * std::sqrt(dx * dx + dy * dy)) {
+          dbx.push_back(c);
+          w_direct_src += rs[c].y - rs[c].x;
+        } else {
+          pc.push_back((int)i);
+          pbx.push_back(c);
+        }
       }
       off[i + 1] = (int)pc.size();
+      doff[i + 1] = (int)dbx.size();
     }
+    QBX_CUDA_TRY(f->wd_box.alloc(std::max<size_t>(1, dbx.size())));
+    QBX_CUDA_TRY(f->wd_off.alloc(doff.size()));
+    if (!dbx.empty())
+      QBX_CUDA_TRY(cudaMemcpy(f->wd_box.ptr, dbx.data(), dbx.size() * 4, cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(cudaMemcpy(f->wd_off.ptr, doff.data(), doff.size() * 4, cudaMemcpyHostToDevice));
     f->n_wpairs = (int)pc.size();
     QBX_CUDA_TRY(f->wp_ctr.alloc(std::max<size_t>(1, pc.size())));
     QBX_CUDA_TRY(f->wp_box.alloc(std::max<size_t>(1, pc.size())));
@@ -1338,9 +1380,9 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   h->stats[9] = f->V.nnz;
   h->stats[10] = f->W.nnz;
   h->stats[11] = f->X.nnz;
-  h->stats[12] = p2qbxl;
+  h->stats[12] = p2qbxl + w_direct_src;
   h->stats[13] = p2p;
-  h->stats[14] = m2qbxl;
+  h->stats[14] = f->n_wpairs;
   h->stats[15] = m2p;
   h->stats[17] = p2l;
   {
@@ -1389,9 +1431,10 @@ qbx_status launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S
   if (f->n_wpairs > 0 && (S || D)) {
     const int np = f->n_wpairs;
     cd* part = f->wpart.ptr;
-    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<nblk(np, kThreads), kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
-    else if (S) m2qbxl_pair_kernel<PM, true, false><<<nblk(np, kThreads), kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
-    else m2qbxl_pair_kernel<PM, false, true><<<nblk(np, kThreads), kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
+    const unsigned gb = nblk((int64_t)np * kM2qbxlSplit, kThreads);
+    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<gb, kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
+    else if (S) m2qbxl_pair_kernel<PM, true, false><<<gb, kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
+    else m2qbxl_pair_kernel<PM, false, true><<<gb, kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
     QBX_KCHECK("m2qbxl", s);
     const int P = 2 * h->p + 1;
     m2qbxl_sum_kernel<<<nblk(h->n_ctr * P, 256), 256, 0, s>>>((int)h->n_ctr, P, f->wp_off.ptr, part,
@@ -1404,13 +1447,13 @@ qbx_status launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S
   const int nc = (int)h->n_ctr;
   const unsigned gw = nblk(nc, kThreads / 32);  // one warp per centre
   if (mixed) {
-    if (S && D) p2qbxl_warp_mixed_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
-    else if (S) p2qbxl_warp_mixed_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
-    else if (D) p2qbxl_warp_mixed_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
+    if (S && D) p2qbxl_warp_mixed_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
+    else if (S) p2qbxl_warp_mixed_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
+    else if (D) p2qbxl_warp_mixed_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
   } else {
-    if (S && D) p2qbxl_warp_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
-    else if (S) p2qbxl_warp_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
-    else if (D) p2qbxl_warp_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, nc, alpha);
+    if (S && D) p2qbxl_warp_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
+    else if (S) p2qbxl_warp_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
+    else if (D) p2qbxl_warp_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
   }
   QBX_KCHECK("p2qbxl", s);
   stage_end(h, QBX_STAGE_P2QBXL, s);
@@ -1502,22 +1545,31 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_L2L, s);
-  // Stages 3, 5, 8 at targets
-  if (f->n_leaves > 0 && h->n_direct_tgt > 0) {
+  // Stages 3, 5, 8 at targets (direct targets only; QBX targets are evaluated
+  // from their centres' coefficients)
+  if (f->n_dtgt > 0) {
     stage_begin(h, QBX_STAGE_L2P, s);
-    l2p_kernel<<<f->n_leaves, kLeafThreads, (size_t)f->q_leaf * sizeof(cd), s>>>(F, f->leaves.ptr, out);
+    l2p_kernel<<<nblk(f->n_dtgt, kThreads), kThreads, 0, s>>>(F, f->dtgt.ptr, f->tleaf.ptr, f->n_dtgt, out);
     QBX_KCHECK("l2p", s);
     stage_end(h, QBX_STAGE_L2P, s);
+    h->launches += 1;
     stage_begin(h, QBX_STAGE_M2P, s);
-    m2p_kernel<<<f->n_leaves, kLeafThreads, (size_t)f->q_w * sizeof(cd), s>>>(F, f->leaves.ptr, out);
-    QBX_KCHECK("m2p", s);
+    if (f->n_wtgt > 0) {
+      m2p_kernel<<<nblk(f->n_wtgt, kThreads), kThreads, 0, s>>>(F, f->wtgt.ptr, f->tleaf.ptr, f->n_wtgt, out);
+      QBX_KCHECK("m2p", s);
+      h->launches += 1;
+    }
     stage_end(h, QBX_STAGE_M2P, s);
     stage_begin(h, QBX_STAGE_P2P, s);
-    if (S && D) p2p_ulist_kernel<true, true><<<f->n_leaves, kLeafThreads, 0, s>>>(F, f->leaves.ptr, out);
-    else if (S) p2p_ulist_kernel<true, false><<<f->n_leaves, kLeafThreads, 0, s>>>(F, f->leaves.ptr, out);
-    else if (D) p2p_ulist_kernel<false, true><<<f->n_leaves, kLeafThreads, 0, s>>>(F, f->leaves.ptr, out);
+    if (f->n_utgt > 0 && (S || D)) {
+      const unsigned gw = nblk(f->n_utgt, kThreads / 32);  // one warp per target
+      if (S && D) p2p_warp_kernel<true, true><<<gw, kThreads, 0, s>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
+      else if (S) p2p_warp_kernel<true, false><<<gw, kThreads, 0, s>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
+      else p2p_warp_kernel<false, true><<<gw, kThreads, 0, s>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
+      QBX_KCHECK("p2p", s);
+      h->launches += 1;
+    }
     stage_end(h, QBX_STAGE_P2P, s);
-    h->launches += (S || D) ? 3 : 2;
   }
   // Stages 3, 5, 8 at centres: the QBX coefficients
   if (f->n_leaves > 0 && h->n_ctr > 0) {

@@ -59,10 +59,14 @@ struct FmmPlan {
   std::vector<int> src_leaf_off, xbox_off, vbox_off;
   int q_leaf = 1, q_w = 1;              // largest Q_l among leaves / W-list boxes
   DevBuf<int> cleaf;                    // [n_centres] leaf of each sorted centre
+  DevBuf<int> tleaf;                    // [n_targets] leaf of each sorted target
+  DevBuf<int> dtgt, utgt, wtgt;         // direct targets (sorted indices): all, with
+  int n_dtgt = 0, n_utgt = 0, n_wtgt = 0;  // U-list sources, with a W list
   // M2QBXL work items: (sorted centre, W-list box) pairs grouped by centre
   int n_wpairs = 0;
   DevBuf<int> wp_ctr, wp_box, wp_off;   // [n_wpairs], [n_wpairs], [n_centres + 1]
   DevBuf<cd> wpart;                     // [n_wpairs][2p+1] partial coefficients
+  DevBuf<int> wd_off, wd_box;           // per centre: W-list boxes summed directly (CSR)
   DevBuf<cd> t_m2l;                     // [n_levels][49][4 pb_max + 1] scaled Hankel vectors
   DevBuf<cd> t_m2m;                     // [n_levels][4][4 pb_max + 1] conj(V_m(d)) child->parent
   DevBuf<cd> t_l2l;                     // [n_levels][4][4 pb_max + 1] (-1)^m V_m(d) parent->child
