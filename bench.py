@@ -261,29 +261,38 @@ def run_ours(args, w, ws, rank, local):
     comparison = {"fp64" if other == qbx.QBX_FP64 else "mixed": {
         "value": job_throughput(n_t, ws, args.steps, ms2), "ms_per_step": ms2 / args.steps}}
 
-    # speedup at equal accuracy: the fastest FP64 plan, over box orders p_fmm + p_add
-    # from 8 up to the workload's own, whose error against the full-order FP64
-    # result is no larger than the mixed path's
+    # speedup at equal accuracy: both precisions over box orders p_fmm + p_add
+    # from 8 up to the workload's own; at each tolerance, the fastest plan of each
+    # precision whose error against the workload's full-order FP64 result is
+    # within it
     eq = None
     if fmm and not args.no_equal_accuracy:
         eq_rows = []
+        ks = max(3, args.steps // 4)
         for pf, pa in [(q, 0) for q in range(8, 52, 4)] + [(w["p_fmm"], -1)]:
             lq = qbx.LayerPotential(g.as_dict(), w["p"], sides=w["sides"])
             lq.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"], mode=mode,
                      p_fmm=pf, p_add=pa, n_max=args.n_max, eps_assoc=w["eps_assoc"])
-            oq = torch.empty_like(out)
-            msq, _ = timed_steps(stepper(lq, qbx.QBX_FP64, oq), max(3, args.steps // 4), 2,
-                                 stream, flush, ws, dev, lq)
-            eq_rows.append({"p_fmm": pf, "p_add": pa, "p_box_finest": int(lq.stats()["p_box"]),
-                            "rel_err_vs_fp64": rel_l2(oq.cpu().numpy(), u64),
-                            "value": job_throughput(n_t, ws, max(3, args.steps // 4), msq)})
+            for pr, name in ((qbx.QBX_FP64, "fp64"), (qbx.QBX_MIXED, "mixed")):
+                oq = torch.empty_like(out)
+                msq, _ = timed_steps(stepper(lq, pr, oq), ks, 2, stream, flush, ws, dev, lq)
+                eq_rows.append({"precision": name, "p_fmm": pf, "p_add": pa,
+                                "p_box_finest": int(lq.stats()["p_box"]),
+                                "rel_err_vs_fp64": rel_l2(oq.cpu().numpy(), u64),
+                                "value": job_throughput(n_t, ws, ks, msq)})
             lq.close()
-        ok = [r for r in eq_rows if r["rel_err_vs_fp64"] <= err_mixed]
-        best = max(ok, key=lambda r: r["value"]) if ok else None
-        mixed_value = value if prec == qbx.QBX_MIXED else comparison["mixed"]["value"]
-        eq = {"mixed_rel_err_vs_fp64": err_mixed, "fp64_sweep": eq_rows,
-              "fp64_at_equal_accuracy": best,
-              "speedup_mixed_over_fp64": (mixed_value / best["value"]) if best else None}
+        at = {}
+        for tol in (1e-6, 1e-8, 1e-10):
+            best = {}
+            for name in ("fp64", "mixed"):
+                ok = [r for r in eq_rows if r["precision"] == name and r["rel_err_vs_fp64"] <= tol]
+                best[name] = max(ok, key=lambda r: r["value"]) if ok else None
+            at["%g" % tol] = {
+                "fp64": best["fp64"], "mixed": best["mixed"],
+                "speedup_mixed_over_fp64": (best["mixed"]["value"] / best["fp64"]["value"])
+                if best["fp64"] and best["mixed"] else None}
+        eq = {"mixed_rel_err_vs_fp64_at_workload_orders": err_mixed, "at_tolerance": at,
+              "sweep": eq_rows}
 
     # per-kernel device times (events around each kernel class on the eval stream)
     lp.set_timing(True)
@@ -300,7 +309,7 @@ def run_ours(args, w, ws, rank, local):
     roof = None
     if dom:
         achieved = flops.get(dom, 0) / (per[dom] / 1e3) / 1e12
-        fp32 = prec == qbx.QBX_MIXED and dom in ("m2l",)
+        fp32 = prec == qbx.QBX_MIXED and dom in ("m2l", "l2l")
         peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,

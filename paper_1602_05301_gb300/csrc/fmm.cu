@@ -1503,12 +1503,16 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   }
   stage_end(h, QBX_STAGE_P2M, s);
   stage_begin(h, QBX_STAGE_M2M, s);
-  for (int l = f->n_levels - 2; l >= 2; --l) {
-    const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
-    if (nb == 0) continue;
-    m2m_kernel<<<nb, kThreads, m2m_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
-    QBX_KCHECK("m2m", s);
-    h->launches += 1;
+  if (precision == QBX_MIXED) {
+    TRY(launch_m2m_f32(h, f, s));
+  } else {
+    for (int l = f->n_levels - 2; l >= 2; --l) {
+      const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
+      if (nb == 0) continue;
+      m2m_kernel<<<nb, kThreads, m2m_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+      QBX_KCHECK("m2m", s);
+      h->launches += 1;
+    }
   }
   stage_end(h, QBX_STAGE_M2M, s);
   // Stage 4: M2L
@@ -1532,12 +1536,16 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   stage_end(h, QBX_STAGE_P2L, s);
   // Stage 7: L2L
   stage_begin(h, QBX_STAGE_L2L, s);
-  for (int l = 2; l + 1 < f->n_levels; ++l) {
-    const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
-    if (nb == 0) continue;
-    l2l_kernel<<<nb, kThreads, l2l_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
-    QBX_KCHECK("l2l", s);
-    h->launches += 1;
+  if (precision == QBX_MIXED) {
+    TRY(launch_l2l_f32(h, f, s));
+  } else {
+    for (int l = 2; l + 1 < f->n_levels; ++l) {
+      const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
+      if (nb == 0) continue;
+      l2l_kernel<<<nb, kThreads, l2l_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
+      QBX_KCHECK("l2l", s);
+      h->launches += 1;
+    }
   }
   if (f->n_leaves > 0) {
     unscale_leaf_locals_kernel<<<f->n_leaves, kThreads, 0, s>>>(F, f->leaves.ptr);

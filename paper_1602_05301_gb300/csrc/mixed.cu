@@ -1,5 +1,6 @@
-// Mixed-precision kernels (QBX_MIXED): the M2L translation of Stage 4 in complex
-// FP32 with compensated (Kahan) accumulation.
+// Mixed-precision kernels (QBX_MIXED): the M2M translation of Stage 2, the M2L
+// translation of Stage 4 and the L2L translation of Stage 7 in complex FP32
+// with compensated (Kahan) accumulation.
 //
 // FP32 cannot hold the power-scaled expansions of the FP64 path (their
 // translation entries still grow like a factorial), so the FP32 operators act
@@ -7,9 +8,13 @@
 //     mu_n = a_n / sig_|n|,   lam_l = gamma_l sig_|l|,
 //     sig_j = min(1, (x/2)^j / j!),  x = k * side  (the size of J_j at a box),
 // for which every M2L entry sig_l sig_n (-1)^l W_{n+l}(D) is of order one or
-// smaller. The entries are computed in FP64 (through logarithms of the scale
-// factors) and stored as FP32 matrices, one per (level, offset class); the
-// coefficient conversions between the two normalisations are FP64.
+// smaller, and so is every L2L entry (sig'_s / sig_n) (-1)^{s-n} V_{s-n}(d)
+// (sig' of the child level) and M2M entry (sig_n / sig'_s) conj(V_{s-n}(d))
+// (sig' of the parent level): the scale ratios are binomial-sized while
+// J_{s-n}(k d) decays factorially. The entries are computed in FP64 (through logarithms
+// of the scale factors) and stored as FP32 matrices, one per (level, offset
+// class) for M2L and per (level, quadrant) for L2L; the coefficient
+// conversions between the two normalisations are FP64.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -75,23 +80,51 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
-// CTA per box with a V list; threads over output orders lo, with the
-// compensated sums (re, im, their compensations) of each order kept in shared
-// memory.
+// Compensated complex dot product sum_{n<N} M[n * ld] x[n] in FP32, returned
+// in FP64 (sums minus compensations). Two independent compensated sums (even
+// and odd n) and a four-way unrolled loop keep several matrix loads and
+// dependent additions in flight.
+__device__ __forceinline__ cd kahan_cdot(const float2* __restrict__ M, size_t ld,
+                                         const float2* __restrict__ x, int N) {
+  float sr0 = 0.f, si0 = 0.f, cr0 = 0.f, ci0 = 0.f;
+  float sr1 = 0.f, si1 = 0.f, cr1 = 0.f, ci1 = 0.f;
+  int n = 0;
+#pragma unroll 2
+  for (; n + 1 < N; n += 2) {
+    const float2 t0 = M[(size_t)n * ld], t1 = M[(size_t)(n + 1) * ld];
+    const float2 m0 = x[n], m1 = x[n + 1];
+    kahan_add(sr0, cr0, fmaf(t0.x, m0.x, -t0.y * m0.y));
+    kahan_add(si0, ci0, fmaf(t0.x, m0.y, t0.y * m0.x));
+    kahan_add(sr1, cr1, fmaf(t1.x, m1.x, -t1.y * m1.y));
+    kahan_add(si1, ci1, fmaf(t1.x, m1.y, t1.y * m1.x));
+  }
+  if (n < N) {
+    const float2 t0 = M[(size_t)n * ld];
+    const float2 m0 = x[n];
+    kahan_add(sr0, cr0, fmaf(t0.x, m0.x, -t0.y * m0.y));
+    kahan_add(si0, ci0, fmaf(t0.x, m0.y, t0.y * m0.x));
+  }
+  return mk(((double)sr0 - (double)cr0) + ((double)sr1 - (double)cr1),
+            ((double)si0 - (double)ci0) + ((double)si1 - (double)ci1));
+}
+
+// CTA per box with a V list; threads over output orders lo. Each V entry's
+// contribution is a compensated FP32 dot product; the entries' contributions
+// are added in FP64 (shared-memory accumulators).
 __global__ void __launch_bounds__(kT) m2l_f32_kernel(
     int pbmax, const int* __restrict__ boxes, const int* __restrict__ level,
     const int* __restrict__ lpb, const long long* __restrict__ tm_off,
     const long long* __restrict__ eoff, const int* __restrict__ voff, const int* __restrict__ vidx,
     const int* __restrict__ vcls, const float2* __restrict__ tm, const double* __restrict__ conv,
     const cd* __restrict__ mpole, cd* __restrict__ local) {
-  extern __shared__ float4 sacc[];               // [Q] (sum re, sum im, comp re, comp im)
+  extern __shared__ cd sacc[];                   // [Q] FP64 sums over V entries
   const int b = boxes[blockIdx.x];
   const int l = level[b];
   const int pb = lpb[l], Q = 2 * pb + 1;
   float2* mu = (float2*)(sacc + Q);              // [Q]
   const float2* Tm = tm + tm_off[l];
   const double* cv = conv + (size_t)l * (pbmax + 1);
-  for (int i = threadIdx.x; i < Q; i += kT) sacc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = threadIdx.x; i < Q; i += kT) sacc[i] = mk(0.0, 0.0);
   for (int e = voff[b]; e < voff[b + 1]; ++e) {
     const cd* mp = mpole + eoff[vidx[e]];
     for (int i = threadIdx.x; i < Q; i += kT) {
@@ -101,24 +134,127 @@ __global__ void __launch_bounds__(kT) m2l_f32_kernel(
     }
     __syncthreads();
     const float2* M = Tm + (size_t)vcls[e] * Q * Q;
-    for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += kT) {
-      float4 acc = sacc[lo + pb];
-      for (int n = 0; n < Q; ++n) {
-        const float2 t = M[(size_t)n * Q + lo + pb];
-        const float2 m = mu[n];
-        kahan_add(acc.x, acc.z, fmaf(t.x, m.x, -t.y * m.y));
-        kahan_add(acc.y, acc.w, fmaf(t.x, m.y, t.y * m.x));
-      }
-      sacc[lo + pb] = acc;
-    }
+    for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += kT)
+      sacc[lo + pb] = cadd(sacc[lo + pb], kahan_cdot(M + lo + pb, Q, mu, Q));
     __syncthreads();
   }
   cd* dst = local + eoff[b];
-  for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += kT) {
-    const float4 acc = sacc[lo + pb];
-    const double f = cv[abs(lo)];
-    dst[lo + pb].x += ((double)acc.x - (double)acc.z) * f;
-    dst[lo + pb].y += ((double)acc.y - (double)acc.w) * f;
+  for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += kT)
+    dst[lo + pb] = cadd(dst[lo + pb], cscale(sacc[lo + pb], cv[abs(lo)]));
+}
+
+// L2L matrices of parent level l (order pp) and quadrant c, child order pc:
+// Tl[c][n][s] = (sig'_s / sig_n) (-1)^{s-n} V_{s-n}(d), sig' on level l+1,
+// sig on level l, from the FP64 table of (-1)^m V_m(d) (row stride
+// 4 pbmax + 1, order m at m + 2 pbmax). Grid: (quadrant, n), threads over s.
+__global__ void l2l_f32_matrix_kernel(int l, int pp, int pc, int pbmax, const cd* __restrict__ t_l2l,
+                                      const double* __restrict__ lsig, float2* __restrict__ Tl) {
+  const int c = blockIdx.x;
+  const int n = (int)blockIdx.y - pp;
+  const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
+  const cd* v = t_l2l + ((size_t)l * 4 + c) * (4 * pbmax + 1) + 2 * pbmax;
+  const double* sp = lsig + (size_t)l * (pbmax + 1);
+  const double* sc = lsig + (size_t)(l + 1) * (pbmax + 1);
+  float2* dst = Tl + ((size_t)c * Qp + (n + pp)) * Qc;
+  for (int so = (int)threadIdx.x - pc; so <= pc; so += blockDim.x) {
+    const cd e = v[so - n];
+    const double mag = hypot(e.x, e.y);
+    float2 out = make_float2(0.f, 0.f);
+    if (mag > 0.0) {
+      const double lf = sc[abs(so)] - sp[abs(n)] + log(mag);
+      const double f = lf < -700.0 ? 0.0 : exp(lf) / mag;
+      out = make_float2((float)(e.x * f), (float)(e.y * f));
+    }
+    dst[so + pc] = out;
+  }
+}
+
+// CTA per parent box on level l: lambda_n = lh_n / conv_n (sigma-normalised,
+// FP32), then for each child lambda'_s = sum_n Tl[c][n][s] lambda_n with
+// compensated FP32 sums, and lh'_s += lambda'_s conv'_s in FP64.
+__global__ void __launch_bounds__(kT) l2l_f32_kernel(
+    int l, int pp, int pc, int pbmax, const int* __restrict__ boxes, const int* __restrict__ child,
+    const long long* __restrict__ eoff, const float2* __restrict__ Tl,
+    const double* __restrict__ conv, cd* __restrict__ local) {
+  extern __shared__ float2 lam[];  // [Qp]
+  const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
+  const int b = boxes[blockIdx.x];
+  const double* cvp = conv + (size_t)l * (pbmax + 1);
+  const double* cvc = conv + (size_t)(l + 1) * (pbmax + 1);
+  const cd* lp = local + eoff[b];
+  for (int i = threadIdx.x; i < Qp; i += kT) {
+    const double f = 1.0 / cvp[abs(i - pp)];
+    lam[i] = make_float2((float)(lp[i].x * f), (float)(lp[i].y * f));
+  }
+  __syncthreads();
+  // threads over (child, output order) pairs
+  for (int task = threadIdx.x; task < 4 * Qc; task += kT) {
+    const int c = task / Qc, so = task % Qc - pc;
+    const int d = child[4 * b + c];
+    if (d < 0) continue;
+    const cd v = kahan_cdot(Tl + (size_t)c * Qp * Qc + so + pc, Qc, lam, Qp);
+    cd* dl = local + eoff[d] + so + pc;
+    *dl = cadd(*dl, cscale(v, cvc[abs(so)]));
+  }
+}
+
+// M2M matrices of parent level l (order pp) and quadrant c, child order pc:
+// Tm2m[c][n][s] = (sig_n / sig'_s) conj(V_{s-n}(d)), sig on the child level
+// l+1, sig' on level l, from the FP64 table of conj(V_m(d)). Grid: (quadrant,
+// n), threads over s.
+__global__ void m2m_f32_matrix_kernel(int l, int pp, int pc, int pbmax, const cd* __restrict__ t_m2m,
+                                      const double* __restrict__ lsig, float2* __restrict__ Tmm) {
+  const int c = blockIdx.x;
+  const int n = (int)blockIdx.y - pc;
+  const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
+  const cd* v = t_m2m + ((size_t)l * 4 + c) * (4 * pbmax + 1) + 2 * pbmax;
+  const double* sp = lsig + (size_t)l * (pbmax + 1);
+  const double* sc = lsig + (size_t)(l + 1) * (pbmax + 1);
+  float2* dst = Tmm + ((size_t)c * Qc + (n + pc)) * Qp;
+  for (int so = (int)threadIdx.x - pp; so <= pp; so += blockDim.x) {
+    const cd e = v[so - n];
+    const double mag = hypot(e.x, e.y);
+    float2 out = make_float2(0.f, 0.f);
+    if (mag > 0.0) {
+      const double lf = sc[abs(n)] - sp[abs(so)] + log(mag);
+      const double f = lf < -700.0 ? 0.0 : exp(lf) / mag;
+      out = make_float2((float)(e.x * f), (float)(e.y * f));
+    }
+    dst[so + pp] = out;
+  }
+}
+
+// CTA per parent box on level l: mu_n = mh_n conv_n of each child (FP32),
+// mu'_s = sum_children sum_n Tm2m[c][n][s] mu_n (compensated FP32 per child,
+// children added in FP64), mh'_s = mu'_s / conv'_s.
+__global__ void __launch_bounds__(kT) m2m_f32_kernel(
+    int l, int pp, int pc, int pbmax, const int* __restrict__ boxes, const int* __restrict__ child,
+    const long long* __restrict__ eoff, const float2* __restrict__ Tmm,
+    const double* __restrict__ conv, cd* __restrict__ mpole) {
+  extern __shared__ float2 mus[];  // [4][Qc]
+  const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
+  const int b = boxes[blockIdx.x];
+  const double* cvp = conv + (size_t)l * (pbmax + 1);
+  const double* cvc = conv + (size_t)(l + 1) * (pbmax + 1);
+  for (int task = threadIdx.x; task < 4 * Qc; task += kT) {
+    const int c = task / Qc, i = task % Qc;
+    const int d = child[4 * b + c];
+    float2 v = make_float2(0.f, 0.f);
+    if (d >= 0) {
+      const cd a = mpole[eoff[d] + i];
+      const double f = cvc[abs(i - pc)];
+      v = make_float2((float)(a.x * f), (float)(a.y * f));
+    }
+    mus[task] = v;
+  }
+  __syncthreads();
+  cd* dst = mpole + eoff[b];
+  for (int so = (int)threadIdx.x - pp; so <= pp; so += kT) {
+    cd sum = mk(0.0, 0.0);
+    for (int c = 0; c < 4; ++c)
+      if (child[4 * b + c] >= 0)
+        sum = cadd(sum, kahan_cdot(Tmm + (size_t)c * Qc * Qp + so + pp, Qp, mus + c * Qc, Qc));
+    dst[so + pp] = cscale(sum, 1.0 / cvp[abs(so)]);
   }
 }
 
@@ -126,6 +262,10 @@ __global__ void __launch_bounds__(kT) m2l_f32_kernel(
 
 qbx_status configure_mixed_kernels(int smem_optin) {
   QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)m2l_f32_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+  QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)l2l_f32_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+  QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)m2m_f32_kernel,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
   return QBX_OK;
 }
@@ -160,6 +300,68 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
                                         f->tm_f32.ptr + off[l]);
     QBX_CUDA_TRY(cudaGetLastError());
   }
+  // M2M matrices for parents on levels 2 .. n_levels - 2
+  {
+    std::vector<long long> moff(f->n_levels, 0);
+    long long mtot = 0;
+    for (int l = 2; l + 1 < f->n_levels; ++l) {
+      moff[l] = mtot;
+      mtot += 4LL * (2 * f->h_pb[l] + 1) * (2 * f->h_pb[l + 1] + 1);
+    }
+    QBX_CUDA_TRY(f->tmm_f32.alloc(std::max<long long>(1, mtot)));
+    f->h_tmm_off = moff;
+    for (int l = 2; l + 1 < f->n_levels; ++l) {
+      const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
+      dim3 grid(4, 2 * pc + 1);
+      m2m_f32_matrix_kernel<<<grid, kT>>>(l, pp, pc, pbm, f->t_m2m.ptr, f->lsig.ptr,
+                                          f->tmm_f32.ptr + moff[l]);
+      QBX_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  // L2L matrices for parents on levels 2 .. n_levels - 2
+  std::vector<long long> loff(f->n_levels, 0);
+  long long ltot = 0;
+  for (int l = 2; l + 1 < f->n_levels; ++l) {
+    loff[l] = ltot;
+    ltot += 4LL * (2 * f->h_pb[l] + 1) * (2 * f->h_pb[l + 1] + 1);
+  }
+  QBX_CUDA_TRY(f->tl_f32.alloc(std::max<long long>(1, ltot)));
+  f->h_tl_off = loff;
+  for (int l = 2; l + 1 < f->n_levels; ++l) {
+    const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
+    dim3 grid(4, 2 * pp + 1);
+    l2l_f32_matrix_kernel<<<grid, kT>>>(l, pp, pc, pbm, f->t_l2l.ptr, f->lsig.ptr,
+                                        f->tl_f32.ptr + loff[l]);
+    QBX_CUDA_TRY(cudaGetLastError());
+  }
+  return QBX_OK;
+}
+
+qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
+  for (int l = f->n_levels - 2; l >= 2; --l) {
+    const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
+    if (nb == 0) continue;
+    const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
+    m2m_f32_kernel<<<nb, kT, (size_t)4 * (2 * pc + 1) * sizeof(float2), s>>>(
+        l, pp, pc, f->pb_max, f->nonleaf.ptr + f->nonleaf_off[l], f->box.child.ptr, f->eoff.ptr,
+        f->tmm_f32.ptr + f->h_tmm_off[l], f->conv.ptr, f->mpole.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+  }
+  return QBX_OK;
+}
+
+qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
+  for (int l = 2; l + 1 < f->n_levels; ++l) {
+    const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
+    if (nb == 0) continue;
+    const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
+    l2l_f32_kernel<<<nb, kT, (size_t)(2 * pp + 1) * sizeof(float2), s>>>(
+        l, pp, pc, f->pb_max, f->nonleaf.ptr + f->nonleaf_off[l], f->box.child.ptr, f->eoff.ptr,
+        f->tl_f32.ptr + f->h_tl_off[l], f->conv.ptr, f->local.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+  }
   return QBX_OK;
 }
 
@@ -168,7 +370,7 @@ qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
   int pbv = 0;  // largest order among levels with V lists (vbox runs coarse to fine)
   for (int l = 0; l < f->n_levels; ++l)
     if (f->vbox_off[l + 1] > f->vbox_off[l]) pbv = std::max(pbv, f->h_pb[l]);
-  const size_t sm = (size_t)(2 * pbv + 1) * (sizeof(float4) + sizeof(float2));
+  const size_t sm = (size_t)(2 * pbv + 1) * (sizeof(cd) + sizeof(float2));
   m2l_f32_kernel<<<f->n_vbox, kT, sm, s>>>(
       f->pb_max, f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->tm_off.ptr, f->eoff.ptr,
       f->V.off.ptr, f->V.idx.ptr, f->V_cls.ptr, f->tm_f32.ptr, f->conv.ptr, f->mpole.ptr,

@@ -10,39 +10,59 @@
 #pragma once
 #include "qbx_internal.h"
 
-// H_0 and H_1 for 0 < x < 2 from the ascending series (DLMF 10.2.2 for J,
-// DLMF 10.8.1 for Y, z = x^2/4):
-//   J0 = sum (-z)^k / (k!)^2,            J1 = (x/2) sum (-z)^k / (k! (k+1)!),
-//   Y0 = (2/pi)(ln(x/2) + gamma) J0 - (2/pi) sum_{k>=1} H_k (-z)^k / (k!)^2,
-//   Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (x/(2 pi)) sum (psi(k+1) + psi(k+2)) (-z)^k / (k! (k+1)!),
-// with H_k the harmonic numbers and psi(m) = -gamma + H_{m-1}. For z < 1 the
-// terms fall below 1e-17 by k = 13; the sums are taken forward with the term
-// ratios (compile-time constants after unrolling).
-__device__ __forceinline__ void hankel01_series(double x, cd& h0, cd& h1) {
-  const double kGamma = 0.57721566490153286061;
-  const double kTwoOverPi = 0.63661977236758134308;
-  const double mz = -0.25 * x * x;
-  double t0 = 1.0, t1 = 1.0;          // (-z)^k/(k!)^2 and (-z)^k/(k!(k+1)!)
-  double sj0 = 1.0, sj1 = 1.0;        // J series
-  double sy0 = 0.0;                   // sum H_k t0
-  double sy1 = 1.0 - 2.0 * kGamma;    // sum (psi(k+1)+psi(k+2)) t1, k = 0 term: -2g + 1
-  double hk = 0.0;                    // H_k (a compile-time constant in each unrolled step)
-#pragma unroll
-  for (int k = 1; k <= 14; ++k) {
-    hk += 1.0 / (double)k;
-    // reciprocals of the integer ratios are compile-time constants: no division
-    t0 *= mz * (1.0 / ((double)k * (double)k));
-    t1 *= mz * (1.0 / ((double)k * (double)(k + 1)));
-    sj0 += t0;
-    sj1 += t1;
-    sy0 = fma(hk, t0, sy0);
-    // psi(k+1) + psi(k+2) = -2 gamma + H_k + H_{k+1}
-    sy1 = fma(-2.0 * kGamma + 2.0 * hk + 1.0 / (double)(k + 1), t1, sy1);
+// Coefficients of the ascending series below, as compile-time constants:
+// j0 = 1/(k!)^2, j1 = 1/(k!(k+1)!), h = H_k = 1 + 1/2 + ... + 1/k,
+// y0 = H_k/(k!)^2, y1 = (psi(k+1) + psi(k+2))/(k!(k+1)!), psi(m) = -gamma + H_{m-1}.
+constexpr double kEulerGamma = 0.57721566490153286061;
+template <int K>
+struct SeriesCoef {
+  static constexpr double j0 = SeriesCoef<K - 1>::j0 / ((double)K * (double)K);
+  static constexpr double j1 = SeriesCoef<K - 1>::j1 / ((double)K * (double)(K + 1));
+  static constexpr double h = SeriesCoef<K - 1>::h + 1.0 / (double)K;
+  static constexpr double y0 = h * j0;
+  static constexpr double y1 = (-2.0 * kEulerGamma + h + (h + 1.0 / (double)(K + 1))) * j1;
+};
+template <>
+struct SeriesCoef<0> {
+  static constexpr double j0 = 1.0, j1 = 1.0, h = 0.0, y0 = 0.0;
+  static constexpr double y1 = -2.0 * kEulerGamma + 1.0;
+};
+
+// Horner steps k = K, K-1, ..., 0 for the four polynomials in u.
+template <int K>
+struct SeriesHorner {
+  __device__ __forceinline__ static void run(double u, double& pj0, double& pj1, double& py0,
+                                             double& py1) {
+    pj0 = fma(pj0, u, SeriesCoef<K>::j0);
+    pj1 = fma(pj1, u, SeriesCoef<K>::j1);
+    py0 = fma(py0, u, SeriesCoef<K>::y0);
+    py1 = fma(py1, u, SeriesCoef<K>::y1);
+    SeriesHorner<K - 1>::run(u, pj0, pj1, py0, py1);
   }
+};
+template <>
+struct SeriesHorner<-1> {
+  __device__ __forceinline__ static void run(double, double&, double&, double&, double&) {}
+};
+
+// H_0 and H_1 for 0 < x < 2 from the ascending series (DLMF 10.2.2 for J,
+// DLMF 10.8.1 for Y), in u = -x^2/4:
+//   J0 = sum u^k / (k!)^2,            J1 = (x/2) sum u^k / (k! (k+1)!),
+//   Y0 = (2/pi)(ln(x/2) + gamma) J0 - (2/pi) sum_{k>=1} H_k u^k / (k!)^2,
+//   Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (x/(2 pi)) sum (psi(k+1) + psi(k+2)) u^k / (k! (k+1)!),
+// For |u| < 1 the terms fall below 1e-17 by k = 13; each sum is a polynomial
+// in u of degree 14 evaluated by Horner's rule (one FMA per term).
+__device__ __forceinline__ void hankel01_series(double x, cd& h0, cd& h1) {
+  constexpr int kTop = 14;
+  constexpr double kTwoOverPi = 0.63661977236758134308;
+  const double u = -0.25 * x * x;
+  double pj0 = SeriesCoef<kTop>::j0, pj1 = SeriesCoef<kTop>::j1;
+  double py0 = SeriesCoef<kTop>::y0, py1 = SeriesCoef<kTop>::y1;
+  SeriesHorner<kTop - 1>::run(u, pj0, pj1, py0, py1);
   const double lx = log(0.5 * x);
-  const double J0 = sj0, J1 = 0.5 * x * sj1;
-  const double Y0 = kTwoOverPi * ((lx + kGamma) * J0 - sy0);
-  const double Y1 = -kTwoOverPi / x + kTwoOverPi * lx * J1 - (0.5 * x) * (0.5 * kTwoOverPi) * sy1;
+  const double J0 = pj0, J1 = 0.5 * x * pj1;
+  const double Y0 = kTwoOverPi * ((lx + kEulerGamma) * J0 - py0);
+  const double Y1 = -kTwoOverPi / x + kTwoOverPi * lx * J1 - (0.5 * x) * (0.5 * kTwoOverPi) * py1;
   h0 = mk(J0, Y0);
   h1 = mk(J1, Y1);
 }

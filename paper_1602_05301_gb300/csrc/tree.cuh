@@ -83,11 +83,17 @@ struct FmmPlan {
   DevBuf<float2> tm_f32;                // per level l >= 2: [49][Q_l][Q_l] M2L matrices
   DevBuf<long long> tm_off;             // [n_levels] offset of level l's matrices
   std::vector<long long> h_tm_off;
+  DevBuf<float2> tl_f32;                // per parent level l: [4][Q_l][Q_{l+1}] L2L matrices
+  std::vector<long long> h_tl_off;
+  DevBuf<float2> tmm_f32;               // per parent level l: [4][Q_{l+1}][Q_l] M2M matrices
+  std::vector<long long> h_tmm_off;
 };
 
 qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f);
 qbx_status configure_mixed_kernels(int smem_optin);
 qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
+qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
+qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 
 qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max, double kappa);
 qbx_status tree_lists(qbx_handle* h, FmmPlan* f);
