@@ -40,7 +40,15 @@ UNIT = "targets/s"
 CONFIG_NUM = 2
 WORKLOADS = {2: "%s: starfish r=1+0.3cos5t, k=10, 512 panels x 16 GL (8192 sources, 16384 "
                 "centres), D+ikS with random Fourier density |n|<=20, p=12, p_fmm=20, 316x316 "
-                "grid targets on [-2,2]^2"}
+                "grid targets on [-2,2]^2",
+             3: "%s: starfish r=1+0.3cos5t, k=50, 8192 panels x 16 GL (131072 sources, 262144 "
+                "centres), D+ikS with random Fourier density |n|<=20, p=16, p_fmm=30, 316x316 "
+                "grid targets on [-2,2]^2",
+             4: "%s: 256 random curves r=1+sum_{m<=5} a_m cos(m t+phi_m), k~U(1,40), panels "
+                "U{16..1024} x 16 GL raised to ceil(kL/5), D+ik_cS, p=12, p_fmm=20, every node "
+                "an exterior on-surface target; one graph-captured batch, plans autotuned",
+             5: "%s: 200 ellipses in [0,100]^2, k=20, 65536 panels x 16 GL (2^20 sources), "
+                "double layer, p=16, p_fmm=30, 9e5 uniform + 1e5 near-surface targets"}
 # FP64 FMA peak of a GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP32 FMA peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.070 GHz.
@@ -127,17 +135,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def flop_model(lp, stats, p, has_S, has_D, assoc, fmm):
-    """Algorithmic flops per kernel class (complex multiply-add = 8 flops; the
-    Bessel/Hankel values a kernel generates are not charged). P = 2p+1 QBX
-    terms; a box on tree level l carries Q_l = 2 pb_l + 1 terms (per-level
-    orders), and every translation is charged with the orders of its boxes."""
+# FP64 flops of the base Hankel values H0, H1 of one pair for x < 2: four
+# degree-14 polynomials by Horner's rule (the log is not charged), and of one
+# step of the upward Hankel recurrence (a real-scaled complex step, 6 flops).
+HANKEL01_FLOPS = 4 * 14 * 2
+REC_STEP_FLOPS = 6
+
+
+def flop_model(lp, stats, p, has_S, has_D, assoc, fmm, mixed=False, active_frac=1.0):
+    """Algorithmic flops per kernel class as (FP64, FP32) pairs: complex
+    multiply-add = 8 flops; special-function values as stated above. P = 2p+1
+    QBX terms; a box on tree level l carries Q_l = 2 pb_l + 1 terms (per-level
+    orders), and every translation is charged with the orders of its boxes. In
+    mixed precision M2M, M2L, L2L and the P2QBXL accumulation are FP32.
+    active_frac scales the centre stages to the centres whose coefficients are
+    formed (those some target uses)."""
     P = 2 * p + 1
     lay = (1 if has_S else 0) + (1 if has_D else 0)
+    acc = (18 * P if has_S else 0) + (10 * P if has_D else 0)
+    pairs = stats["p2qbxl_pairs"] * active_frac
+    base = pairs * (HANKEL01_FLOPS + REC_STEP_FLOPS * p)
     f = {}
-    f["p2qbxl"] = stats["p2qbxl_pairs"] * ((18 * P if has_S else 0) + (10 * P if has_D else 0))
-    f["p2p"] = stats["p2p_pairs"] * 8 * lay
-    f["qbxl2p"] = stats["n_qbx_targets"] * 16 * P
+    f["p2qbxl"] = (base, pairs * acc) if mixed else (base + pairs * acc, 0.0)
+    f["p2p"] = (stats["p2p_pairs"] * (HANKEL01_FLOPS + 8 * lay), 0.0)
+    f["qbxl2p"] = (stats["n_qbx_targets"] * 16 * P, 0.0)
     if not fmm:
         return f
     t = lp.export_tree()
@@ -161,16 +182,17 @@ def flop_model(lp, stats, p, has_S, has_D, assoc, fmm):
         own = np.repeat(np.arange(nb), cnt)
         return own, t["idx"][base[i]:base[i] + cnt.sum()].astype(np.int64)
     vb, _ = entries(1)
-    f["m2l"] = 8 * int(np.sum(Qb[vb] ** 2))
+    tr = lambda v: (0.0, float(v)) if mixed else (float(v), 0.0)  # FP32 translations in mixed
+    f["m2l"] = tr(8 * np.sum(Qb[vb] ** 2))
     parent = np.full(nb, -1, np.int64)
     for q in range(4):
         has = child[:, q] >= 0
         parent[child[has, q]] = np.nonzero(has)[0]
     mm = (lev >= 3) & (parent >= 0)
-    f["m2m"] = f["l2l"] = 8 * int(np.sum(Qb[mm] * Qb[parent[mm]]))
-    f["p2m"] = 16 * lay * int(np.sum((nsrc * Qb)[leaf & (lev >= 2)]))
+    f["m2m"] = f["l2l"] = tr(8 * np.sum(Qb[mm] * Qb[parent[mm]]))
+    f["p2m"] = (16.0 * lay * np.sum((nsrc * Qb)[leaf & (lev >= 2)]), 0.0)
     xb, xc = entries(3)
-    f["p2l"] = 16 * lay * int(np.sum(Qb[xb] * nsrc[xc]))
+    f["p2l"] = (16.0 * lay * np.sum(Qb[xb] * nsrc[xc]), 0.0)
     wb, wc = entries(2)
     wq = np.bincount(wb, weights=Qb[wc], minlength=nb)
     # M2QBXL runs for the (centre, W box) pairs whose box is far enough from the
@@ -178,10 +200,10 @@ def flop_model(lp, stats, p, has_S, has_D, assoc, fmm):
     # the mean box order over the W lists of the centres' leaves
     w_all = float(np.sum((nctr * (wq > 0) * np.diff(t["off"][2]))[leaf]))
     w_q = float(np.sum((nctr * wq)[leaf]))
-    f["m2qbxl"] = int(8 * P * stats["m2qbxl_pairs"] * (w_q / w_all if w_all else 0.0))
-    f["m2p"] = 16 * int(np.sum((ndir * wq)[leaf]))
-    f["l2qbxl"] = 8 * P * int(np.sum((nctr * Qb)[leaf]))
-    f["l2p"] = 16 * int(np.sum((ndir * Qb)[leaf]))
+    f["m2qbxl"] = (8.0 * P * stats["m2qbxl_pairs"] * active_frac * (w_q / w_all if w_all else 0.0), 0.0)
+    f["m2p"] = (16.0 * np.sum((ndir * wq)[leaf]), 0.0)
+    f["l2qbxl"] = (8.0 * P * np.sum((nctr * Qb)[leaf]) * active_frac, 0.0)
+    f["l2p"] = (16.0 * np.sum((ndir * Qb)[leaf]), 0.0)
     return f
 
 
@@ -304,21 +326,33 @@ def run_ours(args, w, ws, rank, local):
             per.setdefault(kname, []).append(ms)
     lp.set_timing(False)
     per = {k: statistics.median(v) for k, v in per.items() if max(v) > 0}
-    flops = flop_model(lp, stats, w["p"], sS is not None, sD is not None, assoc, fmm)
+    n_used = len(np.unique(assoc[assoc >= 0]))
+    active = n_used / max(1, stats["n_centres"]) if fmm else 1.0
+    flops = flop_model(lp, stats, w["p"], sS is not None, sD is not None, assoc, fmm,
+                       mixed=prec == qbx.QBX_MIXED, active_frac=active)
     dom = max(per, key=per.get) if per else None
     roof = None
     if dom:
-        achieved = flops.get(dom, 0) / (per[dom] / 1e3) / 1e12
-        fp32 = prec == qbx.QBX_MIXED and dom in ("m2l", "l2l")
-        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+        f64, f32 = flops.get(dom, (0.0, 0.0))
+        t = per[dom] / 1e3
+        # roofline time = FP64 work at the FP64 peak + FP32 work at the FP32 peak;
+        # achieved is expressed as the FP64-equivalent rate
+        roof_ms = 1e3 * (f64 / (FP64_PEAK_TFLOPS * 1e12) + f32 / (FP32_PEAK_TFLOPS * 1e12))
+        fp32_only = f64 == 0.0 and f32 > 0.0
+        peak = FP32_PEAK_TFLOPS if fp32_only else FP64_PEAK_TFLOPS
+        achieved = (f32 if fp32_only else f64 + f32 * FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS) / t / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
+                "unit": "TFLOP/s", "frac": roof_ms / per[dom],
                 "traffic": KNOWN_TRAFFIC.get((w["name"], dom, args.mode, args.precision)),
-                "flops_per_launch": flops.get(dom, 0), "ms_per_launch": per[dom],
-                "peak_basis": ("FP32" if fp32 else "FP64") +
+                "flops64_per_launch": f64, "flops32_per_launch": f32,
+                "roofline_ms": roof_ms, "ms_per_launch": per[dom],
+                "peak_basis": ("FP32" if fp32_only else "FP64") +
                               " FMA rate derived from unit counts and the 2.070 GHz max clock "
-                              "(152 SMs x %s FMA/clk x 2 flop); measured here: FP64 1.25, "
-                              "FP32 69.6 TFLOP/s" % ("128" if fp32 else "2")}
+                              "(152 SMs x 2 FP64 / 128 FP32 FMA per clock x 2 flop): 1.259 / "
+                              "80.5 TFLOP/s; measured here: FP64 1.25, FP32 69.6 TFLOP/s. "
+                              "achieved is FP64-equivalent (FP32 flops scaled by the peak "
+                              "ratio) unless the kernel is FP32 only",
+                "centres_formed": n_used if fmm else stats["n_centres"]}
 
     # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
     hS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).pin_memory() if sS is not None else None
@@ -346,7 +380,7 @@ def run_ours(args, w, ws, rank, local):
                dtype="f64" if prec == qbx.QBX_FP64 else "f32+f64",
                data="synthetic",
                rel_err_mixed_vs_fp64=err_mixed,
-               config={"workload": WORKLOADS[CONFIG_NUM] % w["name"],
+               config={"workload": WORKLOADS[args.config] % w["name"],
                        "mode": args.mode, "precision": args.precision, "n_targets": n_t,
                        "n_qbx_targets": stats["n_qbx_targets"],
                        "box_orders": [int(x) for x in lp.box_orders()] if fmm else None,
@@ -356,6 +390,78 @@ def run_ours(args, w, ws, rank, local):
                roofline=roof, per_kernel_ms=per, gpu_launches=launches,
                clocks=clk.summary(), e2e=e2e, equal_accuracy=eq, **comparison)
     lp.close()
+    return res
+
+
+def run_batch(args, w, ws, rank, local):
+    """The 256-curve batch: one LayerPotential per curve with its plan chosen by
+    qbx_autotune, all evaluated by one qbx_batch_eval (one CUDA graph)."""
+    import torch
+    from paper_1602_05301_gb300 import qbx
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = w["geom"]
+    noff = g.node_offset()
+    prec = qbx.QBX_MIXED if args.precision == "mixed" else qbx.QBX_FP64
+    t0 = time.perf_counter()
+    probs, chosen = [], []
+    for c in range(g.n_curves):
+        G = g.as_dict(c)
+        lp = qbx.LayerPotential(G, w["p"], sides=1)
+        n = G["node_xy"].shape[0]
+        _, _, ch = lp.autotune(G["node_xy"], np.arange(n), np.ones(n, np.int8), p_fmm=w["p_fmm"],
+                               precision=prec, reps=2)
+        probs.append(lp)
+        chosen.append(ch)
+    plan_s = time.perf_counter() - t0
+    b = qbx.Batch(probs, n_streams=16)
+    sS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).to(dev)
+    sD = torch.from_numpy(np.ascontiguousarray(w["sigma_D"])).to(dev)
+    out = torch.empty(b.n_targets, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    class _L:  # launches are not counted per handle inside the graph
+        @staticmethod
+        def stats():
+            return {"launches": 0}
+
+    step = lambda: b.eval(sigma_S=sS, sigma_D=sD, cS=1.0, cD=1.0, out=out, precision=prec,
+                          stream=stream.cuda_stream)
+    with ClockSampler(local) as clk:
+        total_ms, _ = timed_steps(step, args.steps, args.warmup, stream, flush, ws, dev, _L)
+    n_t = b.n_targets
+    value = job_throughput(n_t, ws, args.steps, total_ms)
+    # e2e: host densities and results (the batch stages them through its buffers)
+    hS, hD = np.ascontiguousarray(w["sigma_S"]), np.ascontiguousarray(w["sigma_D"])
+    hout = np.empty(n_t, np.complex128)
+    b.eval(sigma_S=hS, sigma_D=hD, cS=1.0, cD=1.0, out=hout, precision=prec)
+    e2e_s = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        b.eval(sigma_S=hS, sigma_D=hD, cS=1.0, cD=1.0, out=hout, precision=prec)
+        e2e_s.append(time.perf_counter() - a)
+    e2e_ms = max_over_ranks(1e3 * sum(e2e_s), ws, dev)
+    res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+               warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
+               scaling="weak", vs_baseline=None,
+               dtype="f64" if prec == qbx.QBX_FP64 else "f32+f64", data="synthetic",
+               config={"workload": WORKLOADS[4] % w["name"], "precision": args.precision,
+                       "n_curves": g.n_curves, "n_sources": int(g.n), "n_targets": n_t,
+                       "plans": {"direct": chosen.count(0),
+                                 "fmm_nmax32": chosen.count(1), "fmm_nmax64": chosen.count(2),
+                                 "fmm_nmax128": chosen.count(3)},
+                       "plan_and_autotune_s": plan_s,
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+               roofline=None, gpu_launches=None, clocks=clk.summary(),
+               e2e={"value": job_throughput(n_t, ws, args.steps, e2e_ms), "unit": UNIT,
+                    "h2d_bytes_per_step": 32 * int(g.n), "d2h_bytes_per_step": 16 * n_t})
+    b.close()
+    for lp in probs:
+        lp.close()
     return res
 
 
@@ -446,10 +552,13 @@ def main():
     ap.add_argument("--n-max", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-accuracy", action="store_true")
+    ap.add_argument("--config", type=int, default=CONFIG_NUM, choices=[2, 3, 4, 5],
+                    help="workload (2: the default line; 3, 5: large single geometries; "
+                         "4: the 256-curve batch)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     from qbx_workloads import make_config
-    w = make_config(CONFIG_NUM)
+    w = make_config(args.config)
 
     if args.impl == "reference":
         if rank == 0:
@@ -463,8 +572,8 @@ def main():
         b.build()
     if ws > 1:
         torch.distributed.barrier()
-    res = run_ours(args, w, ws, rank, local)
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    res = run_batch(args, w, ws, rank, local) if args.config == 4 else run_ours(args, w, ws, rank, local)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.config != 4:
         from paper_1602_05301_gb300 import qbx
         lp = qbx.LayerPotential(w["geom"].as_dict(), w["p"], sides=w["sides"])
         assoc = lp.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"])

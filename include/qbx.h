@@ -133,6 +133,9 @@ qbx_status qbx_tree_build(qbx_handle *h, const qbx_tree_desc *desc);
  * step 3). sigma_S / sigma_D: complex [n_src] on the source grid; either may be
  * NULL (that layer is absent). out: complex [n_targets]. alpha_out (optional):
  * complex [n_centres][2p+1], l = -p..p, the QBX coefficients of every centre.
+ * Without alpha_out, FMM mode forms the coefficients only at the centres that
+ * some target is associated with (the only ones the evaluation reads); with
+ * it, at every centre. The potential at the targets is the same either way.
  * precision: QBX_FP64 or QBX_MIXED. cuda_stream: a cudaStream_t (NULL: the
  * legacy default stream). With device buffers the call is asynchronous on the
  * stream; with any host buffer it copies through the stream and returns after

@@ -311,7 +311,7 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
   QBX_TRY(launch_strengths(h, mk(cS_re, cS_im), sS, mk(cD_re, cD_im), sD, s));
   stage_end(h, QBX_STAGE_STRENGTHS, s);
   if (h->mode == QBX_FMM) {
-    QBX_TRY(fmm_eval(h, has_S, has_D, o, precision, s));
+    QBX_TRY(fmm_eval(h, has_S, has_D, o, precision, alpha_out != nullptr, s));
   } else {
     stage_begin(h, QBX_STAGE_P2QBXL, s);
     QBX_TRY(launch_p2qbxl_direct(h, has_S, has_D, precision, s));

@@ -525,26 +525,43 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Fmm F, const int* __restr
 // CTA per leaf; one thread per target of the leaf (strided). Only targets that
 // are not associated with a QBX centre are evaluated.
 // L2P writes out[t], M2P and P2P add to it.
-// Deal the sources of box c round-robin over the lanes, continuing the
-// concatenation at index t0 (updated), calling fn(j) for this lane's sources.
-template <typename Fn>
-__device__ __forceinline__ void deal_box_sources(const Fmm& F, int c, int lane, int& t0, Fn&& fn) {
-  const int2 sr = F.rsrc[c];
-  const int cnt = sr.y - sr.x;
-  for (int jl = (lane - t0) & 31; jl < cnt; jl += 32) fn(sr.x + jl);
-  t0 += cnt;
-}
+// Sources of a list of boxes, concatenated: the boxes of leaf b's U list
+// (U.idx[uoff[b]..uoff[b+1])) followed by the boxes xidx[x0..x1) (the W-list
+// boxes summed directly for one centre; empty for targets). Lane `lane` takes
+// the sources t = lane, lane + 32, ... of the concatenation (a cursor per lane
+// walks the boxes), so a warp runs ceil(total / 32) iterations.
+struct SourceCursor {
+  const int* uidx;   // the U-list index array
+  const int2* rsrc;  // source range of every box
+  int u0, nu, x0, nx;
+  const int* xidx;
+  __device__ int box(int e) const { return e < nu ? uidx[u0 + e] : xidx[x0 + e - nu]; }
+  __device__ int total() const {
+    int t = 0;
+    for (int e = 0; e < nu + nx; ++e) {
+      const int2 r = rsrc[box(e)];
+      t += r.y - r.x;
+    }
+    return t;
+  }
+};
 
-// For each source of the U list of leaf b, in an order that deals the
-// concatenated sources round-robin over the lanes, call fn(j).
 template <typename Fn>
-__device__ __forceinline__ void for_ulist_sources(const Fmm& F, int b, int lane, Fn&& fn) {
-  int t0 = 0;  // index of the box's first source in the concatenation
-  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) deal_box_sources(F, F.uidx[e], lane, t0, fn);
+__device__ __forceinline__ void deal_sources(const SourceCursor& sc, int lane, Fn&& fn) {
+  const int tot = sc.total();
+  int e = 0, base = 0;
+  int2 r = sc.nu + sc.nx > 0 ? sc.rsrc[sc.box(0)] : make_int2(0, 0);
+  for (int t = lane; t < tot; t += 32) {
+    while (t >= base + (r.y - r.x)) {  // advance to the box holding source t
+      base += r.y - r.x;
+      r = sc.rsrc[sc.box(++e)];
+    }
+    fn(r.x + (t - base));
+  }
 }
 
 // L2P: one thread per direct target (sorted index list), from the true local
-// coefficients gamma of its leaf. Writes out (the first of the target stages).
+// coefficients gamma of its leaf; adds to out.
 __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restrict__ dtgt,
                                                        const int* __restrict__ tleaf, int n,
                                                        cd* __restrict__ out) {
@@ -590,7 +607,8 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
     }
     norm = fn + 2.0 * sum;
   }
-  out[F.tid[i]] = cscale(acc, 1.0 / norm);
+  cd* dst = out + F.tid[i];
+  *dst = cadd(*dst, cscale(acc, 1.0 / norm));
 }
 
 // M2P: one thread per direct target whose leaf has a W list; adds to out.
@@ -642,17 +660,18 @@ __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __
   if (t >= n) return;
   const int i = utgt[t];
   const int b = tleaf[i];
-  const double k = F.k;
+  const double k = F.k, ik = 1.0 / k;
   const double tx = F.txy[i].x, ty = F.txy[i].y;
   cd acc = mk(0.0, 0.0);
-  for_ulist_sources(F, b, lane, [&](int j) {
+  const SourceCursor sc{F.uidx, F.rsrc, F.uoff[b], F.uoff[b + 1] - F.uoff[b], 0, 0, nullptr};
+  deal_sources(sc, lane, [&](int j) {
     const double dx = tx - F.sxy[j].x, dy = ty - F.sxy[j].y;
-    const double rr = sqrt(dx * dx + dy * dy);
-    if (rr == 0.0) return;
-    const double x = k * rr;
+    const double r2 = dx * dx + dy * dy;
+    if (r2 == 0.0) return;
+    const double ir = rsqrt(r2), x = k * r2 * ir;
     cd h0, h1;
     if (x < 2.0) {
-      hankel01_series(x, h0, h1);
+      hankel01_series(x, ik * ir, h0, h1);
     } else {
       if (HS) h0 = mk(j0(x), y0(x));
       if (HD) h1 = mk(j1(x), y1(x));
@@ -660,7 +679,7 @@ __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __
     if (HS) cfma(acc, F.qs[j], h0);
     if (HD) {
       const double2 nv = F.snrm[j];
-      cfma(acc, F.ds[j], cscale(h1, k * (nv.x * dx + nv.y * dy) / rr));
+      cfma(acc, F.ds[j], cscale(h1, k * (nv.x * dx + nv.y * dy) * ir));
     }
   });
 #pragma unroll
@@ -675,15 +694,16 @@ __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __
 }
 
 // ---------------------------------------------------------------- centres (Stages 3, 5, 8 "New")
-// L2QBXL: alpha_s = sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p; one
+// L2QBXL: alpha_s += sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p; one
 // thread per centre, reading its leaf's true local coefficients gamma (leaf
 // locals are unscaled in place once the downward pass is complete).
-// Writes alpha (the first of the three centre stages).
 template <int PM>
 __global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __restrict__ cleaf,
-                                                          int n_ctr, cd* __restrict__ alpha) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_ctr) return;
+                                                          const int* __restrict__ clist, int n_ctr,
+                                                          cd* __restrict__ alpha) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_ctr) return;
+  const int i = clist[t];
   const int p = F.p, P = 2 * p + 1;
   const int b = cleaf[i];
   const int pb = F.lpb[F.level[b]];
@@ -744,7 +764,7 @@ __global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __re
     }
     const double in = 1.0 / norm;
     cd* dst = alpha + (size_t)F.cid[i] * P;
-    for (int so = -p; so <= p; ++so) dst[so + p] = cscale(acc[so + PM], in);
+    for (int so = -p; so <= p; ++so) dst[so + p] = cadd(dst[so + p], cscale(acc[so + PM], in));
   }
 }
 
@@ -766,15 +786,16 @@ __global__ void __launch_bounds__(kThreads) unscale_leaf_locals_kernel(Fmm F,
 // (r, th) the polar coordinates of source - centre; upward Hankel recurrence.
 template <int PM, bool HS, bool HD>
 __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, double dy, cd q,
-                                            cd A, cd B, double k, int p) {
+                                            cd A, cd B, double k, double ik, int p) {
   // A = d (k/2) nu, B = d (k/2) conj(nu): alpha_l += q W_l + A W_{l-1} - B W_{l+1}.
-  // W_m and W_{-m} are kept in sliding windows so each is formed once.
-  const double rr = sqrt(dx * dx + dy * dy);
-  if (rr == 0.0) return;
-  const double ir = 1.0 / rr, x = k * rr, ix2 = 2.0 / x;
+  // W_m and W_{-m} are kept in sliding windows so each is formed once. One
+  // reciprocal square root gives r, 1/r and 1/x (ik = 1/k): no division.
+  const double r2 = dx * dx + dy * dy;
+  if (r2 == 0.0) return;
+  const double ir = rsqrt(r2), rr = r2 * ir, x = k * rr, ix = ik * ir, ix2 = 2.0 * ix;
   const cd e1 = mk(dx * ir, dy * ir);
   cd h0, h1;
-  hankel01(x, h0, h1);
+  hankel01(x, ix, h0, h1);
   const cd w1 = cmul(h1, e1);
   const cd wm1 = cscale(cmul(h1, cconj(e1)), -1.0);
   if (HS) cfma(acc[PM], q, h0);
@@ -896,18 +917,19 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int*
     if (lo0 + j <= p) dst[lo0 + j + p] = acc[j];
 }
 
-// alpha[centre] += sum of its pairs' partial coefficients, in pair order.
-__global__ void m2qbxl_sum_kernel(int n_ctr, int P, const int* __restrict__ cpo,
+// alpha[centre] += sum of its pairs' partial coefficients, in pair order
+// (centres clist[0..n), pairs of position t at cpo[t]..cpo[t+1]).
+__global__ void m2qbxl_sum_kernel(int n, int P, const int* __restrict__ cpo,
                                   const cd* __restrict__ partial, const int* __restrict__ cid,
-                                  cd* __restrict__ alpha) {
+                                  const int* __restrict__ clist, cd* __restrict__ alpha) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= (int64_t)n_ctr * P) return;
-  const int i = (int)(g / P), l = (int)(g % P);
-  const int t0 = cpo[i], t1 = cpo[i + 1];
+  if (g >= (int64_t)n * P) return;
+  const int t = (int)(g / P), l = (int)(g % P);
+  const int t0 = cpo[t], t1 = cpo[t + 1];
   if (t1 == t0) return;
   cd sum = mk(0.0, 0.0);
-  for (int t = t0; t < t1; ++t) sum = cadd(sum, partial[(size_t)t * P + l]);
-  cd* dst = alpha + (size_t)cid[i] * P + l;
+  for (int e = t0; e < t1; ++e) sum = cadd(sum, partial[(size_t)e * P + l]);
+  cd* dst = alpha + (size_t)cid[clist[t]] * P + l;
   *dst = cadd(*dst, sum);
 }
 
@@ -934,15 +956,17 @@ __device__ __forceinline__ float2 f2(cd a) { return make_float2((float)a.x, (flo
 template <int PM, bool HS, bool HD>
 __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float2 (&C)[2 * PM + 1],
                                                   double dx, double dy, float2 q, float2 A,
-                                                  float2 B, double k, double rho, int p) {
-  const double rr = sqrt(dx * dx + dy * dy);
-  if (rr == 0.0) return;
-  const double x = k * rr;
-  const cd e1 = mk(dx / rr, dy / rr);
+                                                  float2 B, double k, double ik, double rho,
+                                                  double irho, int p) {
+  // one reciprocal square root gives r, 1/r and 1/x (ik = 1/k): no division
+  const double d2 = dx * dx + dy * dy;
+  if (d2 == 0.0) return;
+  const double irr = rsqrt(d2), rr = d2 * irr, x = k * rr, ix = ik * irr;
+  const cd e1 = mk(dx * irr, dy * irr);
   cd h0, h1;
-  hankel01(x, h0, h1);
+  hankel01(x, ix, h0, h1);
   // scaled Hankel values hs_m = H_m rho^m: hs_{m+1} = (2m rho / x) hs_m - rho^2 hs_{m-1}
-  const double r2 = rho * rho, c1 = 2.0 * rho / x, ir = 1.0 / rho;
+  const double r2 = rho * rho, c1 = 2.0 * rho * ix, ir = irho;
   cd hprev = h0, hcur = cscale(h1, rho);
   // angular factors e^{i m th} in FP32 (unit modulus; rounding grows like m eps_32)
   const float2 e1f = f2(e1);
@@ -1056,12 +1080,14 @@ template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) p2qbxl_warp_kernel(Fmm F, const int* __restrict__ cleaf,
                                                                const int* __restrict__ wdoff,
                                                                const int* __restrict__ wdbox,
+                                                               const int* __restrict__ clist,
                                                                int n_ctr, cd* __restrict__ alpha) {
-  const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // sorted centre
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // position in clist  // sorted centre
   const int lane = threadIdx.x & 31;
-  if (i >= n_ctr) return;  // whole warps leave together
+  if (w >= n_ctr) return;  // whole warps leave together
+  const int i = clist[w];  // sorted centre
   const int b = cleaf[i];
-  const double k = F.k;
+  const double k = F.k, ik = 1.0 / k;
   const int p = F.p, P = 2 * p + 1;
   const double2 c = F.cxy[i];
   cd acc[2 * PM + 1];
@@ -1076,12 +1102,12 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_kernel(Fmm F, const int*
       A = cmul(dk, nu);
       B = cmul(dk, cconj(nu));
     }
-    p2qbxl_pair<PM, HS, HD>(acc, y.x - c.x, y.y - c.y, HS ? F.qs[j] : mk(0.0, 0.0), A, B, k, p);
+    p2qbxl_pair<PM, HS, HD>(acc, y.x - c.x, y.y - c.y, HS ? F.qs[j] : mk(0.0, 0.0), A, B, k, ik, p);
   };
   // U-list boxes of the leaf, then the W-list boxes summed directly for this centre
-  int t0 = 0;
-  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) deal_box_sources(F, F.uidx[e], lane, t0, one);
-  for (int e = wdoff[i]; e < wdoff[i + 1]; ++e) deal_box_sources(F, wdbox[e], lane, t0, one);
+  const SourceCursor sc{F.uidx, F.rsrc, F.uoff[b], F.uoff[b + 1] - F.uoff[b], wdoff[i],
+                        wdoff[i + 1] - wdoff[i], wdbox};
+  deal_sources(sc, lane, one);
   warp_reduce_scatter<2 * PM + 1>(acc, lane);
   constexpr int K = (2 * PM + 1 + 31) / 32;
   cd* dst = alpha + (size_t)F.cid[i] * P;
@@ -1096,15 +1122,17 @@ template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, const int* __restrict__ cleaf,
                                                                      const int* __restrict__ wdoff,
                                                                      const int* __restrict__ wdbox,
+                                                                     const int* __restrict__ clist,
                                                                      int n_ctr, cd* __restrict__ alpha) {
-  const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);  // position in clist
   const int lane = threadIdx.x & 31;
-  if (i >= n_ctr) return;
+  if (w >= n_ctr) return;
+  const int i = clist[w];
   const int b = cleaf[i];
-  const double k = F.k;
+  const double k = F.k, ik = 1.0 / k;
   const int p = F.p, P = 2 * p + 1;
   const double2 c = F.cxy[i];
-  const double rho = k * F.crad[i];
+  const double rho = k * F.crad[i], irho = 1.0 / rho;
   float2 S[2 * PM + 1], C[2 * PM + 1];
 #pragma unroll
   for (int j = 0; j <= 2 * PM; ++j) S[j] = C[j] = make_float2(0.f, 0.f);
@@ -1118,11 +1146,11 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
       B = f2(cmul(dk, cconj(nu)));
     }
     p2qbxl_pair_mixed<PM, HS, HD>(S, C, y.x - c.x, y.y - c.y,
-                                  HS ? f2(F.qs[j]) : make_float2(0.f, 0.f), A, B, k, rho, p);
+                                  HS ? f2(F.qs[j]) : make_float2(0.f, 0.f), A, B, k, ik, rho, irho, p);
   };
-  int t0 = 0;
-  for (int e = F.uoff[b]; e < F.uoff[b + 1]; ++e) deal_box_sources(F, F.uidx[e], lane, t0, one);
-  for (int e = wdoff[i]; e < wdoff[i + 1]; ++e) deal_box_sources(F, wdbox[e], lane, t0, one);
+  const SourceCursor sc{F.uidx, F.rsrc, F.uoff[b], F.uoff[b + 1] - F.uoff[b], wdoff[i],
+                        wdoff[i + 1] - wdoff[i], wdbox};
+  deal_sources(sc, lane, one);
   // lane partial sums (compensation removed) in FP64, then the warp sum
   cd acc[2 * PM + 1];
 #pragma unroll
@@ -1131,7 +1159,6 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
   warp_reduce_scatter<2 * PM + 1>(acc, lane);
   constexpr int K = (2 * PM + 1 + 31) / 32;
   cd* dst = alpha + (size_t)F.cid[i] * P;
-  const double irho = 1.0 / rho;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int lo = K * lane + j - PM;
@@ -1229,6 +1256,11 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   QBX_CUDA_TRY(f->mpole.alloc(std::max<int64_t>(1, f->n_coef)));
   QBX_CUDA_TRY(f->local.alloc(std::max<int64_t>(1, f->n_coef)));
   TRY(configure_kernels());
+  // side stream and events for the concurrent near-field stages (created here,
+  // outside any stream capture; owned by the plan)
+  QBX_CUDA_TRY(cudaStreamCreateWithFlags(&f->near_stream, cudaStreamNonBlocking));
+  QBX_CUDA_TRY(cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming));
+  QBX_CUDA_TRY(cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming));
   // the largest per-block footprint (M2L at the largest order) bounds all others
   if (m2l_smem(f->pb_max) > (size_t)g_smem_optin) {
     set_error("box order %d needs %zu bytes of shared memory per block (device: %d)", f->pb_max,
@@ -1313,9 +1345,10 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   QBX_CUDA_TRY(f->cleaf.alloc(cl.size()));
   QBX_CUDA_TRY(cudaMemcpy(f->cleaf.ptr, cl.data(), cl.size() * sizeof(int),
                           cudaMemcpyHostToDevice));
-  // (centre, W-list box) pairs in sorted-centre order, CSR by centre: those
-  // whose box is far enough from the centre's disk for M2QBXL
-  // ((R_c + r_z) <= kW |z - m_c|), and the rest, summed directly in P2QBXL
+  // W-list boxes per centre: those far enough from the centre's disk for
+  // M2QBXL ((R_c + r_z) <= kW |z - m_c|), and the rest, summed directly in
+  // P2QBXL (wd_off / wd_box, CSR by sorted centre)
+  std::vector<std::vector<int>> wtrans(std::max<int64_t>(1, h->n_ctr));
   int64_t w_direct_src = 0;
   {
     std::vector<double2> cxy(std::max<int64_t>(1, h->n_ctr)), bctr(f->n_boxes);
@@ -1325,7 +1358,6 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
       QBX_CUDA_TRY(cudaMemcpy(crad.data(), f->c_r.ptr, h->n_ctr * sizeof(double), cudaMemcpyDeviceToHost));
     }
     QBX_CUDA_TRY(cudaMemcpy(bctr.data(), f->box.centre.ptr, f->n_boxes * sizeof(double2), cudaMemcpyDeviceToHost));
-    std::vector<int> pc, pbx, off(std::max<int64_t>(1, h->n_ctr) + 1, 0);
     std::vector<int> dbx, doff(std::max<int64_t>(1, h->n_ctr) + 1, 0);
     for (int64_t i = 0; i < h->n_ctr; ++i) {
       const int b = cl[i];
@@ -1337,11 +1369,9 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
           dbx.push_back(c);
           w_direct_src += rs[c].y - rs[c].x;
         } else {
-          pc.push_back((int)i);
-          pbx.push_back(c);
+          wtrans[i].push_back(c);
         }
       }
-      off[i + 1] = (int)pc.size();
       doff[i + 1] = (int)dbx.size();
     }
     QBX_CUDA_TRY(f->wd_box.alloc(std::max<size_t>(1, dbx.size())));
@@ -1349,16 +1379,53 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     if (!dbx.empty())
       QBX_CUDA_TRY(cudaMemcpy(f->wd_box.ptr, dbx.data(), dbx.size() * 4, cudaMemcpyHostToDevice));
     QBX_CUDA_TRY(cudaMemcpy(f->wd_off.ptr, doff.data(), doff.size() * 4, cudaMemcpyHostToDevice));
-    f->n_wpairs = (int)pc.size();
-    QBX_CUDA_TRY(f->wp_ctr.alloc(std::max<size_t>(1, pc.size())));
-    QBX_CUDA_TRY(f->wp_box.alloc(std::max<size_t>(1, pc.size())));
-    QBX_CUDA_TRY(f->wp_off.alloc(off.size()));
-    QBX_CUDA_TRY(f->wpart.alloc(std::max<size_t>(1, pc.size() * (size_t)(2 * h->p + 1))));
-    if (!pc.empty()) {
-      QBX_CUDA_TRY(cudaMemcpy(f->wp_ctr.ptr, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice));
-      QBX_CUDA_TRY(cudaMemcpy(f->wp_box.ptr, pbx.data(), pbx.size() * 4, cudaMemcpyHostToDevice));
+  }
+  // Centre sets: every centre (set 0), and the centres some target is
+  // associated with (set 1; alpha is only read there). Each set lists sorted
+  // centre indices and its M2QBXL (centre, W box) pairs, CSR by list position.
+  {
+    std::vector<int> all(std::max<int64_t>(0, h->n_ctr)), used;
+    for (int64_t i = 0; i < h->n_ctr; ++i) all[i] = (int)i;
+    if (h->n_ctr) {
+      std::vector<int> cperm(h->n_ctr), inv(h->n_ctr), ta(std::max<int64_t>(1, h->n_tgt));
+      std::vector<char> mark(h->n_ctr, 0);
+      QBX_CUDA_TRY(cudaMemcpy(cperm.data(), f->perm[PT_CTR].ptr, h->n_ctr * 4, cudaMemcpyDeviceToHost));
+      if (h->n_tgt)
+        QBX_CUDA_TRY(cudaMemcpy(ta.data(), h->assoc.ptr, h->n_tgt * 4, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < h->n_ctr; ++i) inv[cperm[i]] = (int)i;
+      for (int64_t t = 0; t < h->n_tgt; ++t)
+        if (ta[t] >= 0) mark[inv[ta[t]]] = 1;
+      for (int64_t i = 0; i < h->n_ctr; ++i)
+        if (mark[i]) used.push_back((int)i);
     }
-    QBX_CUDA_TRY(cudaMemcpy(f->wp_off.ptr, off.data(), off.size() * 4, cudaMemcpyHostToDevice));
+    size_t max_pairs = 1;
+    for (int k = 0; k < 2; ++k) {
+      const std::vector<int>& list = k == 0 ? all : used;
+      CentreSet& S = f->cset[k];
+      std::vector<int> pc, pbx, off(list.size() + 1, 0);
+      for (size_t t = 0; t < list.size(); ++t) {
+        for (int c : wtrans[list[t]]) {
+          pc.push_back(list[t]);
+          pbx.push_back(c);
+        }
+        off[t + 1] = (int)pc.size();
+      }
+      S.n = (int)list.size();
+      S.n_pairs = (int)pc.size();
+      max_pairs = std::max(max_pairs, pc.size());
+      auto up = [](DevBuf<int>& d, const std::vector<int>& v) -> qbx_status {
+        QBX_CUDA_TRY(d.alloc(std::max<size_t>(1, v.size())));
+        if (!v.empty())
+          QBX_CUDA_TRY(cudaMemcpy(d.ptr, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+        return QBX_OK;
+      };
+      TRY(up(S.clist, list));
+      TRY(up(S.wp_ctr, pc));
+      TRY(up(S.wp_box, pbx));
+      TRY(up(S.wp_off, off));
+    }
+    QBX_CUDA_TRY(f->wpart.alloc(max_pairs * (size_t)(2 * h->p + 1)));
+    f->n_wpairs = f->cset[0].n_pairs;
   }
   // leaves come in level order, so src_leaves does too
   f->src_leaf_off.assign(f->n_levels + 1, 0);
@@ -1380,7 +1447,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   h->stats[9] = f->V.nnz;
   h->stats[10] = f->W.nnz;
   h->stats[11] = f->X.nnz;
-  h->stats[12] = p2qbxl + w_direct_src;
+  h->stats[12] = p2qbxl + w_direct_src;  // over all centres
   h->stats[13] = p2p;
   h->stats[14] = f->n_wpairs;
   h->stats[15] = m2p;
@@ -1420,44 +1487,59 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   return F;
 }
 
+// The centre stages that need the tree's expansions: L2QBXL and M2QBXL (add to alpha).
 template <int PM>
-qbx_status launch_centre_kernels(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
-                                 cd* alpha, bool mixed, cudaStream_t s) {
+qbx_status launch_centre_far(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
+                             const CentreSet& C, cd* alpha, cudaStream_t s) {
+  if (C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_L2QBXL, s);
-  l2qbxl_kernel<PM><<<nblk(h->n_ctr, kThreads), kThreads, 0, s>>>(F, f->cleaf.ptr, (int)h->n_ctr, alpha);
+  l2qbxl_kernel<PM><<<nblk(C.n, kThreads), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
   QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
+  h->launches += 1;
   stage_begin(h, QBX_STAGE_M2QBXL, s);
-  if (f->n_wpairs > 0 && (S || D)) {
-    const int np = f->n_wpairs;
+  if (C.n_pairs > 0 && (S || D)) {
+    const int np = C.n_pairs;
     cd* part = f->wpart.ptr;
     const unsigned gb = nblk((int64_t)np * kM2qbxlSplit, kThreads);
-    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<gb, kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
-    else if (S) m2qbxl_pair_kernel<PM, true, false><<<gb, kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
-    else m2qbxl_pair_kernel<PM, false, true><<<gb, kThreads, 0, s>>>(F, f->wp_ctr.ptr, f->wp_box.ptr, np, part);
+    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<gb, kThreads, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+    else if (S) m2qbxl_pair_kernel<PM, true, false><<<gb, kThreads, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+    else m2qbxl_pair_kernel<PM, false, true><<<gb, kThreads, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
     QBX_KCHECK("m2qbxl", s);
     const int P = 2 * h->p + 1;
-    m2qbxl_sum_kernel<<<nblk(h->n_ctr * P, 256), 256, 0, s>>>((int)h->n_ctr, P, f->wp_off.ptr, part,
-                                                              f->perm[PT_CTR].ptr, alpha);
+    m2qbxl_sum_kernel<<<nblk((int64_t)C.n * P, 256), 256, 0, s>>>(C.n, P, C.wp_off.ptr, part,
+                                                                 f->perm[PT_CTR].ptr, C.clist.ptr,
+                                                                 alpha);
     QBX_KCHECK("m2qbxl_sum", s);
     h->launches += 2;
   }
   stage_end(h, QBX_STAGE_M2QBXL, s);
+  return QBX_OK;
+}
+
+// P2QBXL (U list and directly summed W boxes): one warp per centre, adds to alpha.
+template <int PM>
+qbx_status launch_centre_near(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
+                              const CentreSet& C, cd* alpha, bool mixed, cudaStream_t s) {
+  if (!(S || D) || C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_P2QBXL, s);
-  const int nc = (int)h->n_ctr;
+  const int nc = C.n;
   const unsigned gw = nblk(nc, kThreads / 32);  // one warp per centre
+  const int* wo = f->wd_off.ptr;
+  const int* wb = f->wd_box.ptr;
+  const int* cl = C.clist.ptr;
   if (mixed) {
-    if (S && D) p2qbxl_warp_mixed_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
-    else if (S) p2qbxl_warp_mixed_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
-    else if (D) p2qbxl_warp_mixed_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
+    if (S && D) p2qbxl_warp_mixed_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, wo, wb, cl, nc, alpha);
+    else if (S) p2qbxl_warp_mixed_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, wo, wb, cl, nc, alpha);
+    else p2qbxl_warp_mixed_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, wo, wb, cl, nc, alpha);
   } else {
-    if (S && D) p2qbxl_warp_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
-    else if (S) p2qbxl_warp_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
-    else if (D) p2qbxl_warp_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, f->wd_off.ptr, f->wd_box.ptr, nc, alpha);
+    if (S && D) p2qbxl_warp_kernel<PM, true, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, wo, wb, cl, nc, alpha);
+    else if (S) p2qbxl_warp_kernel<PM, true, false><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, wo, wb, cl, nc, alpha);
+    else p2qbxl_warp_kernel<PM, false, true><<<gw, kThreads, 0, s>>>(F, f->cleaf.ptr, wo, wb, cl, nc, alpha);
   }
   QBX_KCHECK("p2qbxl", s);
   stage_end(h, QBX_STAGE_P2QBXL, s);
-  h->launches += (S || D) ? 2 : 1;
+  h->launches += 1;
   return QBX_OK;
 }
 
@@ -1480,10 +1562,32 @@ int max_order(const std::vector<int>& pb, const std::vector<int>& off) {
 
 }  // namespace
 
-qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaStream_t s) {
+namespace {
+
+template <int PM>
+qbx_status centre_near_dispatch(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
+                                const CentreSet& C, bool mixed, cudaStream_t s) {
+  return launch_centre_near<PM>(F, f, h, S, D, C, h->alpha.ptr, mixed, s);
+}
+
+}  // namespace
+
+// Stream organisation: the near-field stages (P2QBXL at centres, P2P at
+// targets) need only the source strengths, so they run on the plan's side
+// stream while the main stream runs the upward and downward passes
+// (P2M, M2M, M2L, P2L, L2L); the main stream then waits for them and adds the
+// far-field parts (L2QBXL, M2QBXL, L2P, M2P). alpha and out are zeroed first
+// and every stage adds. With per-stage timing on, everything runs on the
+// main stream so that the stage times do not overlap.
+qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool all_centres,
+                    cudaStream_t s) {
   FmmPlan* f = h->fmm;
   if (!f) { set_error("FMM plan missing"); return QBX_ERR_STATE; }
+  // alpha is formed at every centre when the caller asks for it, else only at
+  // the centres some target is associated with (the only ones QBXL2P reads)
+  const CentreSet& C = f->cset[all_centres ? 0 : 1];
   const std::vector<int>& pb = f->h_pb;
+  const bool mixed = precision == QBX_MIXED;
   if (h->n_src > 0) {
     gather_strengths_kernel<<<nblk(h->n_src, 256), 256, 0, s>>>(
         h->n_src, f->perm[PT_SRC].ptr, h->q_str.ptr, h->d_str.ptr, f->qs.ptr, f->ds.ptr);
@@ -1491,9 +1595,37 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     h->launches += 1;
   }
   Fmm F = make_view(h, f, S, D);
+  const bool fork = !h->timing && !debug_sync() && f->near_stream != nullptr;
+  cudaStream_t s2 = fork ? f->near_stream : s;
+  if (fork) {
+    QBX_CUDA_TRY(cudaEventRecord(f->ev_fork, s));
+    QBX_CUDA_TRY(cudaStreamWaitEvent(s2, f->ev_fork, 0));
+  }
+  // ---- near field (side stream)
+  const int P = 2 * h->p + 1;
+  if (h->n_ctr > 0) QBX_CUDA_TRY(cudaMemsetAsync(h->alpha.ptr, 0, (size_t)h->n_ctr * P * sizeof(cd), s2));
+  if (h->n_tgt > 0) QBX_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)h->n_tgt * sizeof(cd), s2));
+  if (h->n_ctr > 0) {
+    if (h->p <= 4) TRY(centre_near_dispatch<4>(F, f, h, S, D, C, mixed, s2));
+    else if (h->p <= 8) TRY(centre_near_dispatch<8>(F, f, h, S, D, C, mixed, s2));
+    else if (h->p <= 12) TRY(centre_near_dispatch<12>(F, f, h, S, D, C, mixed, s2));
+    else TRY(centre_near_dispatch<16>(F, f, h, S, D, C, mixed, s2));
+  }
+  stage_begin(h, QBX_STAGE_P2P, s2);
+  if (f->n_utgt > 0 && (S || D)) {
+    const unsigned gw = nblk(f->n_utgt, kThreads / 32);  // one warp per target
+    if (S && D) p2p_warp_kernel<true, true><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
+    else if (S) p2p_warp_kernel<true, false><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
+    else p2p_warp_kernel<false, true><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
+    QBX_KCHECK("p2p", s2);
+    h->launches += 1;
+  }
+  stage_end(h, QBX_STAGE_P2P, s2);
+  if (fork) QBX_CUDA_TRY(cudaEventRecord(f->ev_join, s2));
+  // ---- upward and downward passes (main stream)
   QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
   QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
-  // Stage 2: P2M (one launch per leaf level), M2M
+  // Stage 2: P2M, M2M
   stage_begin(h, QBX_STAGE_P2M, s);
   if ((S || D) && f->n_src_leaves > 0) {
     const size_t sm = rows_launch_smem(max_order(pb, f->src_leaf_off));
@@ -1503,7 +1635,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   }
   stage_end(h, QBX_STAGE_P2M, s);
   stage_begin(h, QBX_STAGE_M2M, s);
-  if (precision == QBX_MIXED) {
+  if (mixed) {
     TRY(launch_m2m_f32(h, f, s));
   } else {
     for (int l = f->n_levels - 2; l >= 2; --l) {
@@ -1517,7 +1649,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   stage_end(h, QBX_STAGE_M2M, s);
   // Stage 4: M2L
   stage_begin(h, QBX_STAGE_M2L, s);
-  if (precision == QBX_MIXED) {
+  if (mixed) {
     TRY(launch_m2l_f32(h, f, s));
   } else if (f->n_vbox > 0) {
     m2l_kernel<<<f->n_vbox, kThreads, m2l_smem(max_order(pb, f->vbox_off)), s>>>(F, f->vbox.ptr);
@@ -1536,7 +1668,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
   stage_end(h, QBX_STAGE_P2L, s);
   // Stage 7: L2L
   stage_begin(h, QBX_STAGE_L2L, s);
-  if (precision == QBX_MIXED) {
+  if (mixed) {
     TRY(launch_l2l_f32(h, f, s));
   } else {
     for (int l = 2; l + 1 < f->n_levels; ++l) {
@@ -1553,8 +1685,8 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_L2L, s);
-  // Stages 3, 5, 8 at targets (direct targets only; QBX targets are evaluated
-  // from their centres' coefficients)
+  if (fork) QBX_CUDA_TRY(cudaStreamWaitEvent(s, f->ev_join, 0));
+  // ---- far-field parts at targets (Stages 5, 8) and centres (Stages 5, 8 "New")
   if (f->n_dtgt > 0) {
     stage_begin(h, QBX_STAGE_L2P, s);
     l2p_kernel<<<nblk(f->n_dtgt, kThreads), kThreads, 0, s>>>(F, f->dtgt.ptr, f->tleaf.ptr, f->n_dtgt, out);
@@ -1568,23 +1700,13 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, cudaS
       h->launches += 1;
     }
     stage_end(h, QBX_STAGE_M2P, s);
-    stage_begin(h, QBX_STAGE_P2P, s);
-    if (f->n_utgt > 0 && (S || D)) {
-      const unsigned gw = nblk(f->n_utgt, kThreads / 32);  // one warp per target
-      if (S && D) p2p_warp_kernel<true, true><<<gw, kThreads, 0, s>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
-      else if (S) p2p_warp_kernel<true, false><<<gw, kThreads, 0, s>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
-      else p2p_warp_kernel<false, true><<<gw, kThreads, 0, s>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
-      QBX_KCHECK("p2p", s);
-      h->launches += 1;
-    }
-    stage_end(h, QBX_STAGE_P2P, s);
   }
-  // Stages 3, 5, 8 at centres: the QBX coefficients
-  if (f->n_leaves > 0 && h->n_ctr > 0) {
-    if (h->p <= 4) TRY(launch_centre_kernels<4>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
-    else if (h->p <= 8) TRY(launch_centre_kernels<8>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
-    else if (h->p <= 12) TRY(launch_centre_kernels<12>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
-    else TRY(launch_centre_kernels<16>(F, f, h, S, D, h->alpha.ptr, precision == QBX_MIXED, s));
+  if (h->n_ctr > 0) {
+    cd* alpha = h->alpha.ptr;
+    if (h->p <= 4) TRY(launch_centre_far<4>(F, f, h, S, D, C, alpha, s));
+    else if (h->p <= 8) TRY(launch_centre_far<8>(F, f, h, S, D, C, alpha, s));
+    else if (h->p <= 12) TRY(launch_centre_far<12>(F, f, h, S, D, C, alpha, s));
+    else TRY(launch_centre_far<16>(F, f, h, S, D, C, alpha, s));
   }
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;

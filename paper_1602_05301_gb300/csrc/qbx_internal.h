@@ -115,7 +115,7 @@ qbx_status launch_place_centres(qbx_handle* h, cudaStream_t s);
 qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* on_node_dev,
                           const int8_t* on_side_dev, double eps);
 qbx_status fmm_eval(qbx_handle* h, bool has_S, bool has_D, cd* out, int precision,
-                    cudaStream_t s);
+                    bool all_centres, cudaStream_t s);
 void fmm_plan_free(FmmPlan* f);
 
 // stage timing helpers (api.cu)

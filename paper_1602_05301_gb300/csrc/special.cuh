@@ -52,7 +52,8 @@ struct SeriesHorner<-1> {
 //   Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (x/(2 pi)) sum (psi(k+1) + psi(k+2)) u^k / (k! (k+1)!),
 // For |u| < 1 the terms fall below 1e-17 by k = 13; each sum is a polynomial
 // in u of degree 14 evaluated by Horner's rule (one FMA per term).
-__device__ __forceinline__ void hankel01_series(double x, cd& h0, cd& h1) {
+// ix = 1/x is passed in (callers get it from one reciprocal square root of r^2).
+__device__ __forceinline__ void hankel01_series(double x, double ix, cd& h0, cd& h1) {
   constexpr int kTop = 14;
   constexpr double kTwoOverPi = 0.63661977236758134308;
   const double u = -0.25 * x * x;
@@ -62,9 +63,22 @@ __device__ __forceinline__ void hankel01_series(double x, cd& h0, cd& h1) {
   const double lx = log(0.5 * x);
   const double J0 = pj0, J1 = 0.5 * x * pj1;
   const double Y0 = kTwoOverPi * ((lx + kEulerGamma) * J0 - py0);
-  const double Y1 = -kTwoOverPi / x + kTwoOverPi * lx * J1 - (0.5 * x) * (0.5 * kTwoOverPi) * py1;
+  const double Y1 = -kTwoOverPi * ix + kTwoOverPi * lx * J1 - (0.5 * x) * (0.5 * kTwoOverPi) * py1;
   h0 = mk(J0, Y0);
   h1 = mk(J1, Y1);
+}
+
+__device__ __forceinline__ void hankel01_series(double x, cd& h0, cd& h1) {
+  hankel01_series(x, 1.0 / x, h0, h1);
+}
+
+__device__ __forceinline__ void hankel01(double x, double ix, cd& h0, cd& h1) {
+  if (x < 2.0) {
+    hankel01_series(x, ix, h0, h1);
+    return;
+  }
+  h0 = mk(j0(x), y0(x));
+  h1 = mk(j1(x), y1(x));
 }
 
 __device__ __forceinline__ void hankel01(double x, cd& h0, cd& h1) {

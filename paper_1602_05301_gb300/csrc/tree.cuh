@@ -21,7 +21,20 @@ struct Csr {
   int64_t nnz = 0;
 };
 
+struct CentreSet {
+  DevBuf<int> clist, wp_ctr, wp_box, wp_off;
+  int n = 0, n_pairs = 0;
+};
+
 struct FmmPlan {
+  // concurrency of the near-field stages (see fmm_eval)
+  cudaStream_t near_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  ~FmmPlan() {
+    if (near_stream) cudaStreamDestroy(near_stream);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
   // tree
   double x0 = 0, y0 = 0, side = 0;      // root square [x0, x0+side] x [y0, y0+side]
   int n_levels = 0, n_boxes = 0;
@@ -62,10 +75,12 @@ struct FmmPlan {
   DevBuf<int> tleaf;                    // [n_targets] leaf of each sorted target
   DevBuf<int> dtgt, utgt, wtgt;         // direct targets (sorted indices): all, with
   int n_dtgt = 0, n_utgt = 0, n_wtgt = 0;  // U-list sources, with a W list
-  // M2QBXL work items: (sorted centre, W-list box) pairs grouped by centre
-  int n_wpairs = 0;
-  DevBuf<int> wp_ctr, wp_box, wp_off;   // [n_wpairs], [n_wpairs], [n_centres + 1]
-  DevBuf<cd> wpart;                     // [n_wpairs][2p+1] partial coefficients
+  // Centre sets: [0] every centre, [1] the centres some target uses. Each
+  // lists sorted centre indices (clist) and its M2QBXL work items, the
+  // (sorted centre, W-list box) pairs grouped by list position (CSR wp_off).
+  CentreSet cset[2];
+  int n_wpairs = 0;                     // pairs over all centres (statistics)
+  DevBuf<cd> wpart;                     // [max pairs][2p+1] partial coefficients
   DevBuf<int> wd_off, wd_box;           // per centre: W-list boxes summed directly (CSR)
   DevBuf<cd> t_m2l;                     // [n_levels][49][4 pb_max + 1] scaled Hankel vectors
   DevBuf<cd> t_m2m;                     // [n_levels][4][4 pb_max + 1] conj(V_m(d)) child->parent

@@ -100,13 +100,14 @@ def config4(rng, n_curves=256):
         k = rng.uniform(1.0, 40.0)
         n_panels = int(rng.integers(16, 1025))
         g, dg = fourier_radial(a, phi)
-        trial = discretise_curve(g, dg, 64, 16)
-        length = trial.weight.sum()
-        need = int(math.ceil(k * length / 5.0))
-        if need > n_panels:   # panel size bounded by the wavelength (Condition 4)
-            n_panels = need
-            raised += 1
+        # panel size bounded by the wavelength (Condition 4: k * max h <= 5); the
+        # panels are equal in the parameter, so their lengths differ slightly
         geom = discretise_curve(g, dg, n_panels, 16, k=k)
+        if k * geom.panel_h.max() > 5.0:
+            raised += 1
+            while k * geom.panel_h.max() > 5.0:
+                n_panels = int(math.ceil(n_panels * k * geom.panel_h.max() / 5.0)) + 1
+                geom = discretise_curve(g, dg, n_panels, 16, k=k)
         parts.append(geom)
         dens.append(_fourier_density(geom.param_t, rng))
     geom = concat_geometries(parts)
