@@ -611,42 +611,49 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
   *dst = cadd(*dst, cscale(acc, 1.0 / norm));
 }
 
-// M2P: one thread per direct target whose leaf has a W list; adds to out.
-__global__ void __launch_bounds__(kThreads) m2p_kernel(Fmm F, const int* __restrict__ wtgt,
-                                                       const int* __restrict__ tleaf, int n,
-                                                       cd* __restrict__ out) {
+// M2P: one thread per (direct target, W-list box of its leaf) pair, in
+// target order; writes the pair's value to partial[pair]. m2p_sum_kernel adds
+// each target's pairs in order.
+__global__ void __launch_bounds__(kThreads) m2p_pair_kernel(Fmm F, const int* __restrict__ pt,
+                                                            const int* __restrict__ pbx, int n,
+                                                            cd* __restrict__ partial) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const int i = wtgt[t];
-  const int b = tleaf[i];
-  cd acc = mk(0.0, 0.0);
-  for (int e = F.woff[b]; e < F.woff[b + 1]; ++e) {
-    const int c = F.widx[e];
-    const int lc = F.level[c];
-    const int pb = F.lpb[lc];
-    const cd* a = F.mpole + F.eoff[c];
-    const double s = F.scale[lc];
-    const double2 mc = F.centre[c];
-    const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
-    const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-    const cd e1 = mk(dx / rr, dy / rr);
-    cd h0, h1;
-    hankel01(x, h0, h1);
-    cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
-    cd sum = cmul(a[pb], h0);
-    for (int m = 1; m <= pb; ++m) {
-      ee = cmul(ee, e1);
-      cfma(sum, a[pb + m], cmul(hm, ee));
-      const cd v = cmul(hm, cconj(ee));
-      cfma(sum, a[pb - m], (m & 1) ? mk(-v.x, -v.y) : v);
-      const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
-      hm1 = hm;
-      hm = hn;
-    }
-    acc = cadd(acc, sum);
+  const int i = pt[t], c = pbx[t];
+  const int lc = F.level[c];
+  const int pb = F.lpb[lc];
+  const cd* a = F.mpole + F.eoff[c];
+  const double s = F.scale[lc];
+  const double2 mc = F.centre[c];
+  const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
+  const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+  const cd e1 = mk(dx / rr, dy / rr);
+  cd h0, h1;
+  hankel01(x, h0, h1);
+  cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
+  cd sum = cmul(a[pb], h0);
+  for (int m = 1; m <= pb; ++m) {
+    ee = cmul(ee, e1);
+    cfma(sum, a[pb + m], cmul(hm, ee));
+    const cd v = cmul(hm, cconj(ee));
+    cfma(sum, a[pb - m], (m & 1) ? mk(-v.x, -v.y) : v);
+    const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
+    hm1 = hm;
+    hm = hn;
   }
-  cd* dst = out + F.tid[i];
-  *dst = cadd(*dst, acc);
+  partial[t] = sum;
+}
+
+// out[target] += sum of its M2P pairs, in pair order (targets wtgt[0..n)).
+__global__ void m2p_sum_kernel(int n, const int* __restrict__ wtgt, const int* __restrict__ off,
+                               const cd* __restrict__ partial, const int* __restrict__ tid,
+                               cd* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  cd sum = mk(0.0, 0.0);
+  for (int e = off[t]; e < off[t + 1]; ++e) sum = cadd(sum, partial[e]);
+  cd* dst = out + tid[wtgt[t]];
+  *dst = cadd(*dst, sum);
 }
 
 // P2P over the U list: one warp per direct target whose leaf's U list holds
@@ -694,11 +701,86 @@ __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __
 }
 
 // ---------------------------------------------------------------- centres (Stages 3, 5, 8 "New")
-// L2QBXL: alpha_s += sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p; one
-// thread per centre, reading its leaf's true local coefficients gamma (leaf
-// locals are unscaled in place once the downward pass is complete).
-template <int PM>
+// L2QBXL: alpha_s += sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p, from
+// the true local coefficients gamma of the centre's leaf (leaf locals are
+// unscaled in place once the downward pass is complete). One warp per centre:
+// every lane runs the (warp-uniform) backward recurrence for J_m(k|z - m_b|),
+// m <= pb + p, and accumulates its own output orders s = lane - p and
+// lane + 32 - p.
 __global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                          const int* __restrict__ clist, int n_ctr,
+                                                          cd* __restrict__ alpha) {
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n_ctr) return;
+  const int i = clist[w];
+  const int p = F.p, P = 2 * p + 1;
+  const int b = cleaf[i];
+  const int pb = F.lpb[F.level[b]];
+  const cd* g = F.local + F.eoff[b];
+  const double2 mb = F.centre[b];
+  const int M = pb + p;
+  const double dx = F.cxy[i].x - mb.x, dy = F.cxy[i].y - mb.y;
+  const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
+  const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
+  const int so0 = lane - p, so1 = lane + 32 - p;  // this lane's output orders
+  cd a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+  // one order m of V: V_m = f_m e^{im th}, V_{-m} = (-1)^m f_m e^{-im th}
+  auto add_m = [&](int mm, double fm, cd e) {
+    const double sg = (mm & 1) ? -1.0 : 1.0;
+    const cd vp = cscale(e, fm * sg);    // (-1)^m V_m
+    const cd vn = cscale(cconj(e), fm);  // (-1)^m V_{-m} = J_m e^{-im th}
+    if (so0 <= p) {
+      const int n1 = so0 - mm, n2 = so0 + mm;
+      if (n1 >= -pb && n1 <= pb) cfma(a0, g[n1 + pb], vp);
+      if (mm > 0 && n2 >= -pb && n2 <= pb) cfma(a0, g[n2 + pb], vn);
+    }
+    if (so1 <= p) {
+      const int n1 = so1 - mm, n2 = so1 + mm;
+      if (n1 >= -pb && n1 <= pb) cfma(a1, g[n1 + pb], vp);
+      if (mm > 0 && n2 >= -pb && n2 <= pb) cfma(a1, g[n2 + pb], vn);
+    }
+  };
+  double norm;
+  if (x < 1e-8) {
+    add_m(0, 1.0, mk(1.0, 0.0));
+    norm = 1.0;
+  } else {
+    cd e = mk(1.0, 0.0);
+    for (int j = 0; j < M; ++j) e = cmul(e, e1);  // e^{i M th}
+    const double inv = 2.0 / x;
+    const int N = miller_start(M, x);
+    double fn1 = 0.0, fn = 1e-200, sum = 0.0;
+    for (int n = N; n >= 1; --n) {
+      const double fm = (double)n * inv * fn - fn1;
+      if ((n & 1) == 0) sum += fn;
+      const int mm = n - 1;
+      if (mm <= M) {
+        if (mm < M) e = cmul(e, cconj(e1));
+        add_m(mm, fm, e);
+      }
+      fn1 = fn;
+      fn = fm;
+      if (fabs(fn) > kRescale) {
+        const double sc = 1.0 / kRescale;
+        fn *= sc; fn1 *= sc; sum *= sc;
+        a0 = cscale(a0, sc);
+        a1 = cscale(a1, sc);
+      }
+    }
+    norm = fn + 2.0 * sum;
+  }
+  const double in = 1.0 / norm;
+  cd* dst = alpha + (size_t)F.cid[i] * P;
+  if (so0 <= p) dst[so0 + p] = cadd(dst[so0 + p], cscale(a0, in));
+  if (so1 <= p) dst[so1 + p] = cadd(dst[so1 + p], cscale(a1, in));
+}
+
+// L2QBXL, one thread per centre computing all 2p+1 orders: less work than the
+// warp form (one recurrence per centre instead of one per lane), for centre
+// counts large enough to fill the GPU.
+template <int PM>
+__global__ void __launch_bounds__(kThreads) l2qbxl_thread_kernel(Fmm F, const int* __restrict__ cleaf,
                                                           const int* __restrict__ clist, int n_ctr,
                                                           cd* __restrict__ alpha) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -851,6 +933,9 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
 // is split over kM2qbxlSplit threads by output order; each writes its orders of
 // partial[pair][2p+1], and m2qbxl_sum_kernel adds each centre's pairs in order.
 constexpr int kM2qbxlSplit = 4;
+// Centre count from which L2QBXL runs a thread (not a warp) per centre: enough
+// threads for about eight resident warps on each of the 152 SMs.
+constexpr int kL2qbxlThreadMin = 152 * 8 * 32;
 template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int* __restrict__ pair_ctr,
                                                                const int* __restrict__ pair_box,
@@ -1041,8 +1126,7 @@ qbx_status configure_kernels() {
   int optin = 0;
   QBX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const void* k[] = {(const void*)p2m_kernel, (const void*)m2m_kernel, (const void*)m2l_kernel,
-                     (const void*)p2l_kernel, (const void*)l2l_kernel, (const void*)l2p_kernel,
-                     (const void*)m2p_kernel};
+                     (const void*)p2l_kernel, (const void*)l2l_kernel};
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   TRY_MIXED(configure_mixed_kernels(optin));
@@ -1330,13 +1414,28 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
         QBX_CUDA_TRY(cudaMemcpy(d.ptr, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
       return QBX_OK;
     };
+    // M2P work items: (target, W box) pairs in wtgt order, CSR by position
+    std::vector<int> mt, mbx, moff(wt.size() + 1, 0);
+    for (size_t t = 0; t < wt.size(); ++t) {
+      const int b = tl[wt[t]];
+      for (int e = woff[b]; e < woff[b + 1]; ++e) {
+        mt.push_back(wt[t]);
+        mbx.push_back(widx[e]);
+      }
+      moff[t + 1] = (int)mt.size();
+    }
     TRY(up(f->tleaf, tl));
     TRY(up(f->dtgt, dt));
     TRY(up(f->utgt, ut));
     TRY(up(f->wtgt, wt));
+    TRY(up(f->m2p_tgt, mt));
+    TRY(up(f->m2p_box, mbx));
+    TRY(up(f->m2p_off, moff));
+    QBX_CUDA_TRY(f->m2p_part.alloc(std::max<size_t>(1, mt.size())));
     f->n_dtgt = (int)dt.size();
     f->n_utgt = (int)ut.size();
     f->n_wtgt = (int)wt.size();
+    f->n_m2p_pairs = (int)mt.size();
   }
   // leaf of every centre (sorted order)
   std::vector<int> cl(std::max<int64_t>(1, h->n_ctr), 0);
@@ -1493,7 +1592,12 @@ qbx_status launch_centre_far(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bo
                              const CentreSet& C, cd* alpha, cudaStream_t s) {
   if (C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_L2QBXL, s);
-  l2qbxl_kernel<PM><<<nblk(C.n, kThreads), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
+  // a warp per centre while the centres are too few to fill the GPU with
+  // threads (the kernel is then latency-bound), else a thread per centre
+  if (C.n < kL2qbxlThreadMin)
+    l2qbxl_kernel<<<nblk(C.n, kThreads / 32), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
+  else
+    l2qbxl_thread_kernel<PM><<<nblk(C.n, kThreads), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
   QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
   h->launches += 1;
@@ -1694,10 +1798,14 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     stage_end(h, QBX_STAGE_L2P, s);
     h->launches += 1;
     stage_begin(h, QBX_STAGE_M2P, s);
-    if (f->n_wtgt > 0) {
-      m2p_kernel<<<nblk(f->n_wtgt, kThreads), kThreads, 0, s>>>(F, f->wtgt.ptr, f->tleaf.ptr, f->n_wtgt, out);
+    if (f->n_wtgt > 0 && f->n_m2p_pairs > 0) {
+      m2p_pair_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s>>>(
+          F, f->m2p_tgt.ptr, f->m2p_box.ptr, f->n_m2p_pairs, f->m2p_part.ptr);
       QBX_KCHECK("m2p", s);
-      h->launches += 1;
+      m2p_sum_kernel<<<nblk(f->n_wtgt, kThreads), kThreads, 0, s>>>(
+          f->n_wtgt, f->wtgt.ptr, f->m2p_off.ptr, f->m2p_part.ptr, f->perm[PT_TGT].ptr, out);
+      QBX_KCHECK("m2p_sum", s);
+      h->launches += 2;
     }
     stage_end(h, QBX_STAGE_M2P, s);
   }

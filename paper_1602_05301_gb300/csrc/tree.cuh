@@ -75,6 +75,9 @@ struct FmmPlan {
   DevBuf<int> tleaf;                    // [n_targets] leaf of each sorted target
   DevBuf<int> dtgt, utgt, wtgt;         // direct targets (sorted indices): all, with
   int n_dtgt = 0, n_utgt = 0, n_wtgt = 0;  // U-list sources, with a W list
+  DevBuf<int> m2p_tgt, m2p_box, m2p_off;   // M2P (target, W box) pairs, CSR by wtgt position
+  DevBuf<cd> m2p_part;                   // [pairs] partial values
+  int n_m2p_pairs = 0;
   // Centre sets: [0] every centre, [1] the centres some target uses. Each
   // lists sorted centre indices (clist) and its M2QBXL work items, the
   // (sorted centre, W-list box) pairs grouped by list position (CSR wp_off).
