@@ -108,39 +108,101 @@ __device__ __forceinline__ cd kahan_cdot(const float2* __restrict__ M, size_t ld
             ((double)si0 - (double)ci0) + ((double)si1 - (double)ci1));
 }
 
-// CTA per box with a V list; threads over output orders lo. Each V entry's
-// contribution is a compensated FP32 dot product; the entries' contributions
-// are added in FP64 (shared-memory accumulators).
-__global__ void __launch_bounds__(kT) m2l_f32_kernel(
+// M2L as batched complex GEMMs. The V-list pairs (target box b, source box c)
+// are grouped by (level, offset class) at plan time; all pairs of a group use
+// the same matrix Tm[cls]. A CTA takes kGemmRows pairs of one group: their
+// sigma-normalised source coefficients mu (FP32) go to shared memory ([n][row],
+// n-major), and each thread computes one output order lo for all the rows,
+// streaming matrix row n once for all of them (so the matrix is read once per
+// kGemmRows pairs instead of once per pair). Sums: plain FP32 FMAs over blocks
+// of kGemmBlock terms, blocks added with Kahan compensation. Each pair's result
+// goes to its row of Y (FP32); m2l_f32_reduce_kernel adds each target box's
+// rows in its V-list order in FP64 (deterministic).
+constexpr int kGemmRows = 16;
+constexpr int kGemmBlock = 8;
+
+__global__ void __launch_bounds__(kT) m2l_f32_gemm_kernel(
+    int pbmax, const int4* __restrict__ tiles, const int* __restrict__ lpb,
+    const long long* __restrict__ tm_off, const int* __restrict__ row_src,
+    const long long* __restrict__ eoff, const double* __restrict__ conv,
+    const cd* __restrict__ mpole, const float2* __restrict__ tm,
+    const long long* __restrict__ yoff, float2* __restrict__ Y) {
+  extern __shared__ float2 mu[];  // [Q][kGemmRows]
+  const int4 T = tiles[blockIdx.x];  // (level * 49 + class, first row, rows, level)
+  const int cls = T.x % 49, row0 = T.y, nr = T.z, l = T.w;
+  const int pb = lpb[l], Q = 2 * pb + 1;
+  const double* cv = conv + (size_t)l * (pbmax + 1);
+  for (int idx = threadIdx.x; idx < Q * kGemmRows; idx += kT) {
+    const int n = idx / kGemmRows, r = idx % kGemmRows;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nr) {
+      const cd a = mpole[eoff[row_src[row0 + r]] + n];
+      const double f = cv[abs(n - pb)];
+      v = make_float2((float)(a.x * f), (float)(a.y * f));
+    }
+    mu[idx] = v;
+  }
+  __syncthreads();
+  const float2* M = tm + tm_off[l] + (size_t)cls * Q * Q;
+  for (int lo = threadIdx.x; lo - (int)threadIdx.x < Q; lo += kT) {
+    const bool act = lo < Q;
+    float sr[kGemmRows], si[kGemmRows], cr[kGemmRows], ci[kGemmRows];
+#pragma unroll
+    for (int r = 0; r < kGemmRows; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
+    for (int n0 = 0; n0 < Q; n0 += kGemmBlock) {
+      float tr[kGemmRows], ti[kGemmRows];
+#pragma unroll
+      for (int r = 0; r < kGemmRows; ++r) tr[r] = ti[r] = 0.f;
+      // the block's matrix entries first, so their loads are in flight together
+      float2 tb[kGemmBlock];
+#pragma unroll
+      for (int j = 0; j < kGemmBlock; ++j)
+        tb[j] = (act && n0 + j < Q) ? M[(size_t)(n0 + j) * Q + lo] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kGemmBlock; ++j) {
+        if (n0 + j >= Q) break;
+        const float2 t = tb[j];
+        const float2* m = mu + (n0 + j) * kGemmRows;
+#pragma unroll
+        for (int r = 0; r < kGemmRows; ++r) {
+          tr[r] = fmaf(t.x, m[r].x, fmaf(-t.y, m[r].y, tr[r]));
+          ti[r] = fmaf(t.x, m[r].y, fmaf(t.y, m[r].x, ti[r]));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kGemmRows; ++r) {
+        kahan_add(sr[r], cr[r], tr[r]);
+        kahan_add(si[r], ci[r], ti[r]);
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < kGemmRows; ++r)
+        if (r < nr) Y[yoff[row0 + r] + lo] = make_float2(sr[r] - cr[r], si[r] - ci[r]);
+    }
+  }
+}
+
+// lh_lo(b) += conv_lo * sum over b's V entries e (in list order) of Y[row(e)][lo], in FP64.
+__global__ void __launch_bounds__(kT) m2l_f32_reduce_kernel(
     int pbmax, const int* __restrict__ boxes, const int* __restrict__ level,
-    const int* __restrict__ lpb, const long long* __restrict__ tm_off,
-    const long long* __restrict__ eoff, const int* __restrict__ voff, const int* __restrict__ vidx,
-    const int* __restrict__ vcls, const float2* __restrict__ tm, const double* __restrict__ conv,
-    const cd* __restrict__ mpole, cd* __restrict__ local) {
-  extern __shared__ cd sacc[];                   // [Q] FP64 sums over V entries
+    const int* __restrict__ lpb, const int* __restrict__ voff, const int* __restrict__ vrow,
+    const long long* __restrict__ yoff, const float2* __restrict__ Y,
+    const double* __restrict__ conv, const long long* __restrict__ eoff, cd* __restrict__ local) {
   const int b = boxes[blockIdx.x];
   const int l = level[b];
   const int pb = lpb[l], Q = 2 * pb + 1;
-  float2* mu = (float2*)(sacc + Q);              // [Q]
-  const float2* Tm = tm + tm_off[l];
   const double* cv = conv + (size_t)l * (pbmax + 1);
-  for (int i = threadIdx.x; i < Q; i += kT) sacc[i] = mk(0.0, 0.0);
-  for (int e = voff[b]; e < voff[b + 1]; ++e) {
-    const cd* mp = mpole + eoff[vidx[e]];
-    for (int i = threadIdx.x; i < Q; i += kT) {
-      const cd a = mp[i];
-      const double f = cv[abs(i - pb)];
-      mu[i] = make_float2((float)(a.x * f), (float)(a.y * f));
-    }
-    __syncthreads();
-    const float2* M = Tm + (size_t)vcls[e] * Q * Q;
-    for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += kT)
-      sacc[lo + pb] = cadd(sacc[lo + pb], kahan_cdot(M + lo + pb, Q, mu, Q));
-    __syncthreads();
-  }
   cd* dst = local + eoff[b];
-  for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += kT)
-    dst[lo + pb] = cadd(dst[lo + pb], cscale(sacc[lo + pb], cv[abs(lo)]));
+  for (int lo = threadIdx.x; lo < Q; lo += kT) {
+    cd sum = mk(0.0, 0.0);
+    for (int e = voff[b]; e < voff[b + 1]; ++e) {
+      const float2 y = Y[yoff[vrow[e]] + lo];
+      sum.x += (double)y.x;
+      sum.y += (double)y.y;
+    }
+    dst[lo] = cadd(dst[lo], cscale(sum, cv[abs(lo - pb)]));
+  }
 }
 
 // L2L matrices of parent level l (order pp) and quadrant c, child order pc:
@@ -261,7 +323,7 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
 }  // namespace
 
 qbx_status configure_mixed_kernels(int smem_optin) {
-  QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)m2l_f32_kernel,
+  QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)m2l_f32_gemm_kernel,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
   QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)l2l_f32_kernel,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
@@ -299,6 +361,61 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
     m2l_f32_matrix_kernel<<<grid, kT>>>(l, pb, pbm, f->t_m2l.ptr, f->scale.ptr, f->lsig.ptr,
                                         f->tm_f32.ptr + off[l]);
     QBX_CUDA_TRY(cudaGetLastError());
+  }
+  // M2L work: V-list pairs grouped by (level, offset class), cut into tiles
+  // of kGemmRows rows; the row of V entry e is vrow[e], its output at yoff[row]
+  {
+    const int nb = f->n_boxes;
+    const int64_t nv = f->V.nnz;
+    std::vector<int> voff(nb + 1), vidx(std::max<int64_t>(1, nv)), vcls(std::max<int64_t>(1, nv)),
+        blev(nb);
+    QBX_CUDA_TRY(cudaMemcpy(voff.data(), f->V.off.ptr, (nb + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    if (nv) {
+      QBX_CUDA_TRY(cudaMemcpy(vidx.data(), f->V.idx.ptr, nv * sizeof(int), cudaMemcpyDeviceToHost));
+      QBX_CUDA_TRY(cudaMemcpy(vcls.data(), f->V_cls.ptr, nv * sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    QBX_CUDA_TRY(cudaMemcpy(blev.data(), f->box.level.ptr, nb * sizeof(int), cudaMemcpyDeviceToHost));
+    const int ng = f->n_levels * 49;
+    std::vector<int64_t> gcount(ng + 1, 0);
+    std::vector<int> egroup(std::max<int64_t>(1, nv));
+    for (int b = 0; b < nb; ++b)
+      for (int e = voff[b]; e < voff[b + 1]; ++e) {
+        egroup[e] = blev[b] * 49 + vcls[e];
+        gcount[egroup[e] + 1] += 1;
+      }
+    for (int g = 0; g < ng; ++g) gcount[g + 1] += gcount[g];
+    std::vector<int> vrow(std::max<int64_t>(1, nv)), row_src(std::max<int64_t>(1, nv));
+    std::vector<long long> yoff(std::max<int64_t>(1, nv));
+    std::vector<int64_t> fill(gcount.begin(), gcount.end() - 1);
+    for (int b = 0; b < nb; ++b)
+      for (int e = voff[b]; e < voff[b + 1]; ++e) {
+        const int row = (int)fill[egroup[e]]++;
+        vrow[e] = row;
+        row_src[row] = vidx[e];
+      }
+    long long ytot = 0;
+    std::vector<int4> tiles;
+    for (int g = 0; g < ng; ++g) {
+      const int l = g / 49, Q = 2 * f->h_pb[l] + 1;
+      for (int64_t r = gcount[g]; r < gcount[g + 1]; ++r) {
+        yoff[r] = ytot;
+        ytot += Q;
+      }
+      for (int64_t r = gcount[g]; r < gcount[g + 1]; r += kGemmRows)
+        tiles.push_back(make_int4(g, (int)r, (int)std::min<int64_t>(kGemmRows, gcount[g + 1] - r), l));
+    }
+    // coarse levels (largest orders) first
+    f->n_m2l_tiles = (int)tiles.size();
+    QBX_CUDA_TRY(f->m2l_tiles.alloc(std::max<size_t>(1, tiles.size())));
+    QBX_CUDA_TRY(f->m2l_vrow.alloc(vrow.size()));
+    QBX_CUDA_TRY(f->m2l_rowsrc.alloc(row_src.size()));
+    QBX_CUDA_TRY(f->m2l_yoff.alloc(yoff.size()));
+    QBX_CUDA_TRY(f->m2l_y.alloc(std::max<long long>(1, ytot)));
+    if (!tiles.empty())
+      QBX_CUDA_TRY(cudaMemcpy(f->m2l_tiles.ptr, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(cudaMemcpy(f->m2l_vrow.ptr, vrow.data(), vrow.size() * sizeof(int), cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(cudaMemcpy(f->m2l_rowsrc.ptr, row_src.data(), row_src.size() * sizeof(int), cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(cudaMemcpy(f->m2l_yoff.ptr, yoff.data(), yoff.size() * sizeof(long long), cudaMemcpyHostToDevice));
   }
   // M2M matrices for parents on levels 2 .. n_levels - 2
   {
@@ -366,16 +483,19 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
 }
 
 qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
-  if (f->n_vbox == 0) return QBX_OK;
-  int pbv = 0;  // largest order among levels with V lists (vbox runs coarse to fine)
+  if (f->n_vbox == 0 || f->n_m2l_tiles == 0) return QBX_OK;
+  int pbv = 0;  // largest order among levels with V lists
   for (int l = 0; l < f->n_levels; ++l)
     if (f->vbox_off[l + 1] > f->vbox_off[l]) pbv = std::max(pbv, f->h_pb[l]);
-  const size_t sm = (size_t)(2 * pbv + 1) * (sizeof(cd) + sizeof(float2));
-  m2l_f32_kernel<<<f->n_vbox, kT, sm, s>>>(
-      f->pb_max, f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->tm_off.ptr, f->eoff.ptr,
-      f->V.off.ptr, f->V.idx.ptr, f->V_cls.ptr, f->tm_f32.ptr, f->conv.ptr, f->mpole.ptr,
-      f->local.ptr);
+  const size_t sm = (size_t)(2 * pbv + 1) * kGemmRows * sizeof(float2);
+  m2l_f32_gemm_kernel<<<f->n_m2l_tiles, kT, sm, s>>>(
+      f->pb_max, f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr,
+      f->conv.ptr, f->mpole.ptr, f->tm_f32.ptr, f->m2l_yoff.ptr, f->m2l_y.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
-  h->launches += 1;
+  m2l_f32_reduce_kernel<<<f->n_vbox, kT, 0, s>>>(
+      f->pb_max, f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->V.off.ptr, f->m2l_vrow.ptr,
+      f->m2l_yoff.ptr, f->m2l_y.ptr, f->conv.ptr, f->eoff.ptr, f->local.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  h->launches += 2;
   return QBX_OK;
 }

@@ -101,6 +101,14 @@ struct FmmPlan {
   DevBuf<float2> tm_f32;                // per level l >= 2: [49][Q_l][Q_l] M2L matrices
   DevBuf<long long> tm_off;             // [n_levels] offset of level l's matrices
   std::vector<long long> h_tm_off;
+  // M2L as batched GEMMs: tiles (group, first row, rows, level), the row of
+  // every V entry, the source box of every row, row offsets into the FP32
+  // result buffer
+  DevBuf<int4> m2l_tiles;
+  int n_m2l_tiles = 0;
+  DevBuf<int> m2l_vrow, m2l_rowsrc;
+  DevBuf<long long> m2l_yoff;
+  DevBuf<float2> m2l_y;
   DevBuf<float2> tl_f32;                // per parent level l: [4][Q_l][Q_{l+1}] L2L matrices
   std::vector<long long> h_tl_off;
   DevBuf<float2> tmm_f32;               // per parent level l: [4][Q_{l+1}][Q_l] M2M matrices
