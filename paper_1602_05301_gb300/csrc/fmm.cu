@@ -1343,8 +1343,8 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   // side stream and events for the concurrent near-field stages (created here,
   // outside any stream capture; owned by the plan)
   QBX_CUDA_TRY(cudaStreamCreateWithFlags(&f->near_stream, cudaStreamNonBlocking));
-  QBX_CUDA_TRY(cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming));
-  QBX_CUDA_TRY(cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming));
+  for (cudaEvent_t* ev : {&f->ev_fork, &f->ev_join, &f->ev_p2l, &f->ev_m2m, &f->ev_down, &f->ev_out})
+    QBX_CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   // the largest per-block footprint (M2L at the largest order) bounds all others
   if (m2l_smem(f->pb_max) > (size_t)g_smem_optin) {
     set_error("box order %d needs %zu bytes of shared memory per block (device: %d)", f->pb_max,
@@ -1586,10 +1586,10 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   return F;
 }
 
-// The centre stages that need the tree's expansions: L2QBXL and M2QBXL (add to alpha).
+// L2QBXL at the centres of set C (adds to alpha).
 template <int PM>
-qbx_status launch_centre_far(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
-                             const CentreSet& C, cd* alpha, cudaStream_t s) {
+qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSet& C, cd* alpha,
+                         cudaStream_t s) {
   if (C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_L2QBXL, s);
   // a warp per centre while the centres are too few to fill the GPU with
@@ -1601,6 +1601,14 @@ qbx_status launch_centre_far(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bo
   QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
   h->launches += 1;
+  return QBX_OK;
+}
+
+// M2QBXL at the centres of set C (adds to alpha).
+template <int PM>
+qbx_status launch_m2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
+                         const CentreSet& C, cd* alpha, cudaStream_t s) {
+  if (C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_M2QBXL, s);
   if (C.n_pairs > 0 && (S || D)) {
     const int np = C.n_pairs;
@@ -1676,13 +1684,17 @@ qbx_status centre_near_dispatch(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S,
 
 }  // namespace
 
-// Stream organisation: the near-field stages (P2QBXL at centres, P2P at
-// targets) need only the source strengths, so they run on the plan's side
-// stream while the main stream runs the upward and downward passes
-// (P2M, M2M, M2L, P2L, L2L); the main stream then waits for them and adds the
-// far-field parts (L2QBXL, M2QBXL, L2P, M2P). alpha and out are zeroed first
-// and every stage adds. With per-stage timing on, everything runs on the
-// main stream so that the stage times do not overlap.
+// Stream organisation. Two streams: the caller's (main) and the plan's side
+// stream. Every stage adds into zeroed outputs, and each output array is
+// written by one stream at a time:
+//   main: P2M, M2M | M2L (after P2L) | L2L, unscale | L2P (after M2P)
+//   side: zero alpha, out; P2L; P2QBXL; P2P | M2QBXL, M2P (after M2M) |
+//         L2QBXL (after the downward pass)
+// P2L needs only the strengths and adds into the locals before M2L does; the
+// centre coefficients alpha are written on the side stream only; out is
+// written by P2P and M2P (side) before L2P (main). The main stream waits for
+// the side stream before returning. With per-stage timing on, everything runs
+// on the main stream in the same order, so that stage times do not overlap.
 qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool all_centres,
                     cudaStream_t s) {
   FmmPlan* f = h->fmm;
@@ -1699,16 +1711,33 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     h->launches += 1;
   }
   Fmm F = make_view(h, f, S, D);
+  QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
+  QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
   const bool fork = !h->timing && !debug_sync() && f->near_stream != nullptr;
   cudaStream_t s2 = fork ? f->near_stream : s;
-  if (fork) {
-    QBX_CUDA_TRY(cudaEventRecord(f->ev_fork, s));
-    QBX_CUDA_TRY(cudaStreamWaitEvent(s2, f->ev_fork, 0));
-  }
-  // ---- near field (side stream)
+  auto signal = [&](cudaEvent_t ev, cudaStream_t from) -> qbx_status {
+    if (fork) QBX_CUDA_TRY(cudaEventRecord(ev, from));
+    return QBX_OK;
+  };
+  auto wait = [&](cudaStream_t on, cudaEvent_t ev) -> qbx_status {
+    if (fork) QBX_CUDA_TRY(cudaStreamWaitEvent(on, ev, 0));
+    return QBX_OK;
+  };
+  TRY(signal(f->ev_fork, s));
+  TRY(wait(s2, f->ev_fork));
   const int P = 2 * h->p + 1;
+  // ---- side: zero the outputs, P2L, then the near field
   if (h->n_ctr > 0) QBX_CUDA_TRY(cudaMemsetAsync(h->alpha.ptr, 0, (size_t)h->n_ctr * P * sizeof(cd), s2));
   if (h->n_tgt > 0) QBX_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)h->n_tgt * sizeof(cd), s2));
+  stage_begin(h, QBX_STAGE_P2L, s2);
+  if ((S || D) && f->n_xbox > 0) {
+    const size_t sm = rows_launch_smem(max_order(pb, f->xbox_off));
+    p2l_kernel<<<f->n_xbox, kThreads, sm, s2>>>(F, f->xbox.ptr, (unsigned)sm);
+    QBX_KCHECK("p2l", s2);
+    h->launches += 1;
+  }
+  stage_end(h, QBX_STAGE_P2L, s2);
+  TRY(signal(f->ev_p2l, s2));
   if (h->n_ctr > 0) {
     if (h->p <= 4) TRY(centre_near_dispatch<4>(F, f, h, S, D, C, mixed, s2));
     else if (h->p <= 8) TRY(centre_near_dispatch<8>(F, f, h, S, D, C, mixed, s2));
@@ -1725,11 +1754,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_P2P, s2);
-  if (fork) QBX_CUDA_TRY(cudaEventRecord(f->ev_join, s2));
-  // ---- upward and downward passes (main stream)
-  QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
-  QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
-  // Stage 2: P2M, M2M
+  // ---- main: upward pass
   stage_begin(h, QBX_STAGE_P2M, s);
   if ((S || D) && f->n_src_leaves > 0) {
     const size_t sm = rows_launch_smem(max_order(pb, f->src_leaf_off));
@@ -1751,7 +1776,30 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     }
   }
   stage_end(h, QBX_STAGE_M2M, s);
-  // Stage 4: M2L
+  TRY(signal(f->ev_m2m, s));
+  // ---- side: W-list stages (need the multipoles)
+  TRY(wait(s2, f->ev_m2m));
+  if (h->n_ctr > 0) {
+    cd* alpha = h->alpha.ptr;
+    if (h->p <= 4) TRY(launch_m2qbxl<4>(F, f, h, S, D, C, alpha, s2));
+    else if (h->p <= 8) TRY(launch_m2qbxl<8>(F, f, h, S, D, C, alpha, s2));
+    else if (h->p <= 12) TRY(launch_m2qbxl<12>(F, f, h, S, D, C, alpha, s2));
+    else TRY(launch_m2qbxl<16>(F, f, h, S, D, C, alpha, s2));
+  }
+  stage_begin(h, QBX_STAGE_M2P, s2);
+  if (f->n_wtgt > 0 && f->n_m2p_pairs > 0) {
+    m2p_pair_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s2>>>(
+        F, f->m2p_tgt.ptr, f->m2p_box.ptr, f->n_m2p_pairs, f->m2p_part.ptr);
+    QBX_KCHECK("m2p", s2);
+    m2p_sum_kernel<<<nblk(f->n_wtgt, kThreads), kThreads, 0, s2>>>(
+        f->n_wtgt, f->wtgt.ptr, f->m2p_off.ptr, f->m2p_part.ptr, f->perm[PT_TGT].ptr, out);
+    QBX_KCHECK("m2p_sum", s2);
+    h->launches += 2;
+  }
+  stage_end(h, QBX_STAGE_M2P, s2);
+  TRY(signal(f->ev_out, s2));
+  // ---- main: downward pass (M2L after P2L has added into the locals)
+  TRY(wait(s, f->ev_p2l));
   stage_begin(h, QBX_STAGE_M2L, s);
   if (mixed) {
     TRY(launch_m2l_f32(h, f, s));
@@ -1761,16 +1809,6 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_M2L, s);
-  // Stage 6: P2L
-  stage_begin(h, QBX_STAGE_P2L, s);
-  if ((S || D) && f->n_xbox > 0) {
-    const size_t sm = rows_launch_smem(max_order(pb, f->xbox_off));
-    p2l_kernel<<<f->n_xbox, kThreads, sm, s>>>(F, f->xbox.ptr, (unsigned)sm);
-    QBX_KCHECK("p2l", s);
-    h->launches += 1;
-  }
-  stage_end(h, QBX_STAGE_P2L, s);
-  // Stage 7: L2L
   stage_begin(h, QBX_STAGE_L2L, s);
   if (mixed) {
     TRY(launch_l2l_f32(h, f, s));
@@ -1789,33 +1827,26 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_L2L, s);
-  if (fork) QBX_CUDA_TRY(cudaStreamWaitEvent(s, f->ev_join, 0));
-  // ---- far-field parts at targets (Stages 5, 8) and centres (Stages 5, 8 "New")
+  TRY(signal(f->ev_down, s));
+  // ---- side: L2QBXL (alpha); main: L2P (out, after M2P)
+  TRY(wait(s2, f->ev_down));
+  if (h->n_ctr > 0) {
+    cd* alpha = h->alpha.ptr;
+    if (h->p <= 4) TRY(launch_l2qbxl<4>(F, f, h, C, alpha, s2));
+    else if (h->p <= 8) TRY(launch_l2qbxl<8>(F, f, h, C, alpha, s2));
+    else if (h->p <= 12) TRY(launch_l2qbxl<12>(F, f, h, C, alpha, s2));
+    else TRY(launch_l2qbxl<16>(F, f, h, C, alpha, s2));
+  }
+  TRY(signal(f->ev_join, s2));
+  TRY(wait(s, f->ev_out));
   if (f->n_dtgt > 0) {
     stage_begin(h, QBX_STAGE_L2P, s);
     l2p_kernel<<<nblk(f->n_dtgt, kThreads), kThreads, 0, s>>>(F, f->dtgt.ptr, f->tleaf.ptr, f->n_dtgt, out);
     QBX_KCHECK("l2p", s);
     stage_end(h, QBX_STAGE_L2P, s);
     h->launches += 1;
-    stage_begin(h, QBX_STAGE_M2P, s);
-    if (f->n_wtgt > 0 && f->n_m2p_pairs > 0) {
-      m2p_pair_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s>>>(
-          F, f->m2p_tgt.ptr, f->m2p_box.ptr, f->n_m2p_pairs, f->m2p_part.ptr);
-      QBX_KCHECK("m2p", s);
-      m2p_sum_kernel<<<nblk(f->n_wtgt, kThreads), kThreads, 0, s>>>(
-          f->n_wtgt, f->wtgt.ptr, f->m2p_off.ptr, f->m2p_part.ptr, f->perm[PT_TGT].ptr, out);
-      QBX_KCHECK("m2p_sum", s);
-      h->launches += 2;
-    }
-    stage_end(h, QBX_STAGE_M2P, s);
   }
-  if (h->n_ctr > 0) {
-    cd* alpha = h->alpha.ptr;
-    if (h->p <= 4) TRY(launch_centre_far<4>(F, f, h, S, D, C, alpha, s));
-    else if (h->p <= 8) TRY(launch_centre_far<8>(F, f, h, S, D, C, alpha, s));
-    else if (h->p <= 12) TRY(launch_centre_far<12>(F, f, h, S, D, C, alpha, s));
-    else TRY(launch_centre_far<16>(F, f, h, S, D, C, alpha, s));
-  }
+  TRY(wait(s, f->ev_join));
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;
 }

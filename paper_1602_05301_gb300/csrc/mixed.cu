@@ -121,26 +121,36 @@ __device__ __forceinline__ cd kahan_cdot(const float2* __restrict__ M, size_t ld
 constexpr int kGemmRows = 16;
 constexpr int kGemmBlock = 8;
 
+// mu32 = mh * conv (sigma-normalised multipoles in FP32), once per box that
+// is a V-list source; the GEMM tiles gather these rows.
+__global__ void __launch_bounds__(kT) mpole_to_f32_kernel(
+    int pbmax, const int* __restrict__ boxes, const int* __restrict__ level,
+    const int* __restrict__ lpb, const long long* __restrict__ eoff,
+    const double* __restrict__ conv, const cd* __restrict__ mpole, float2* __restrict__ mu32) {
+  const int b = boxes[blockIdx.x];
+  const int l = level[b];
+  const int pb = lpb[l], Q = 2 * pb + 1;
+  const double* cv = conv + (size_t)l * (pbmax + 1);
+  const cd* a = mpole + eoff[b];
+  float2* dst = mu32 + eoff[b];
+  for (int n = threadIdx.x; n < Q; n += kT) {
+    const double f = cv[abs(n - pb)];
+    dst[n] = make_float2((float)(a[n].x * f), (float)(a[n].y * f));
+  }
+}
+
 __global__ void __launch_bounds__(kT) m2l_f32_gemm_kernel(
-    int pbmax, const int4* __restrict__ tiles, const int* __restrict__ lpb,
+    const int4* __restrict__ tiles, const int* __restrict__ lpb,
     const long long* __restrict__ tm_off, const int* __restrict__ row_src,
-    const long long* __restrict__ eoff, const double* __restrict__ conv,
-    const cd* __restrict__ mpole, const float2* __restrict__ tm,
-    const long long* __restrict__ yoff, float2* __restrict__ Y) {
+    const long long* __restrict__ eoff, const float2* __restrict__ mu32,
+    const float2* __restrict__ tm, const long long* __restrict__ yoff, float2* __restrict__ Y) {
   extern __shared__ float2 mu[];  // [Q][kGemmRows]
   const int4 T = tiles[blockIdx.x];  // (level * 49 + class, first row, rows, level)
   const int cls = T.x % 49, row0 = T.y, nr = T.z, l = T.w;
   const int pb = lpb[l], Q = 2 * pb + 1;
-  const double* cv = conv + (size_t)l * (pbmax + 1);
   for (int idx = threadIdx.x; idx < Q * kGemmRows; idx += kT) {
-    const int n = idx / kGemmRows, r = idx % kGemmRows;
-    float2 v = make_float2(0.f, 0.f);
-    if (r < nr) {
-      const cd a = mpole[eoff[row_src[row0 + r]] + n];
-      const double f = cv[abs(n - pb)];
-      v = make_float2((float)(a.x * f), (float)(a.y * f));
-    }
-    mu[idx] = v;
+    const int r = idx / Q, n = idx % Q;  // coalesced reads along each source row
+    mu[n * kGemmRows + r] = r < nr ? mu32[eoff[row_src[row0 + r]] + n] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const float2* M = tm + tm_off[l] + (size_t)cls * Q * Q;
@@ -413,6 +423,17 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
     QBX_CUDA_TRY(f->m2l_y.alloc(std::max<long long>(1, ytot)));
     if (!tiles.empty())
       QBX_CUDA_TRY(cudaMemcpy(f->m2l_tiles.ptr, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    // the boxes that are V-list sources, and FP32 room for their multipoles
+    std::vector<char> is_src(nb, 0);
+    for (int64_t e = 0; e < nv; ++e) is_src[vidx[e]] = 1;
+    std::vector<int> vsrc;
+    for (int b = 0; b < nb; ++b)
+      if (is_src[b]) vsrc.push_back(b);
+    f->n_vsrc = (int)vsrc.size();
+    QBX_CUDA_TRY(f->m2l_vsrc.alloc(std::max<size_t>(1, vsrc.size())));
+    if (!vsrc.empty())
+      QBX_CUDA_TRY(cudaMemcpy(f->m2l_vsrc.ptr, vsrc.data(), vsrc.size() * sizeof(int), cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(f->mu32.alloc(std::max<int64_t>(1, f->n_coef)));
     QBX_CUDA_TRY(cudaMemcpy(f->m2l_vrow.ptr, vrow.data(), vrow.size() * sizeof(int), cudaMemcpyHostToDevice));
     QBX_CUDA_TRY(cudaMemcpy(f->m2l_rowsrc.ptr, row_src.data(), row_src.size() * sizeof(int), cudaMemcpyHostToDevice));
     QBX_CUDA_TRY(cudaMemcpy(f->m2l_yoff.ptr, yoff.data(), yoff.size() * sizeof(long long), cudaMemcpyHostToDevice));
@@ -487,10 +508,17 @@ qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
   int pbv = 0;  // largest order among levels with V lists
   for (int l = 0; l < f->n_levels; ++l)
     if (f->vbox_off[l + 1] > f->vbox_off[l]) pbv = std::max(pbv, f->h_pb[l]);
+  if (f->n_vsrc > 0) {
+    mpole_to_f32_kernel<<<f->n_vsrc, kT, 0, s>>>(f->pb_max, f->m2l_vsrc.ptr, f->box.level.ptr,
+                                                 f->lpb.ptr, f->eoff.ptr, f->conv.ptr,
+                                                 f->mpole.ptr, f->mu32.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+  }
   const size_t sm = (size_t)(2 * pbv + 1) * kGemmRows * sizeof(float2);
   m2l_f32_gemm_kernel<<<f->n_m2l_tiles, kT, sm, s>>>(
-      f->pb_max, f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr,
-      f->conv.ptr, f->mpole.ptr, f->tm_f32.ptr, f->m2l_yoff.ptr, f->m2l_y.ptr);
+      f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr, f->mu32.ptr,
+      f->tm_f32.ptr, f->m2l_yoff.ptr, f->m2l_y.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   m2l_f32_reduce_kernel<<<f->n_vbox, kT, 0, s>>>(
       f->pb_max, f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->V.off.ptr, f->m2l_vrow.ptr,

@@ -29,11 +29,12 @@ struct CentreSet {
 struct FmmPlan {
   // concurrency of the near-field stages (see fmm_eval)
   cudaStream_t near_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p2l = nullptr, ev_m2m = nullptr,
+              ev_down = nullptr, ev_out = nullptr;
   ~FmmPlan() {
     if (near_stream) cudaStreamDestroy(near_stream);
-    if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
+    for (cudaEvent_t ev : {ev_fork, ev_join, ev_p2l, ev_m2m, ev_down, ev_out})
+      if (ev) cudaEventDestroy(ev);
   }
   // tree
   double x0 = 0, y0 = 0, side = 0;      // root square [x0, x0+side] x [y0, y0+side]
@@ -109,6 +110,9 @@ struct FmmPlan {
   DevBuf<int> m2l_vrow, m2l_rowsrc;
   DevBuf<long long> m2l_yoff;
   DevBuf<float2> m2l_y;
+  DevBuf<int> m2l_vsrc;                 // boxes that are V-list sources
+  int n_vsrc = 0;
+  DevBuf<float2> mu32;                  // [n_coef] their sigma-normalised FP32 multipoles
   DevBuf<float2> tl_f32;                // per parent level l: [4][Q_l][Q_{l+1}] L2L matrices
   std::vector<long long> h_tl_off;
   DevBuf<float2> tmm_f32;               // per parent level l: [4][Q_{l+1}][Q_l] M2M matrices
