@@ -54,8 +54,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP32 FMA peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from the committed ncu summaries
-# (profiles/); None until measured for the current kernel version.
-KNOWN_TRAFFIC = {}
+# (profiles/), bytes; None until measured for the current kernel version.
+KNOWN_TRAFFIC = {
+    # profiles/m2l_f32_gemm_starfish-k10.md: dram read 26.9 MB + write 55.5 MB per launch
+    ("starfish-k10", "m2l", "fmm", "mixed"): 26.932224e6 + 55.549184e6,
+}
 
 
 # ---------------------------------------------------------------- helpers
