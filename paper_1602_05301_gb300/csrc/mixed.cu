@@ -80,34 +80,6 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
-// Compensated complex dot product sum_{n<N} M[n * ld] x[n] in FP32, returned
-// in FP64 (sums minus compensations). Two independent compensated sums (even
-// and odd n) and a four-way unrolled loop keep several matrix loads and
-// dependent additions in flight.
-__device__ __forceinline__ cd kahan_cdot(const float2* __restrict__ M, size_t ld,
-                                         const float2* __restrict__ x, int N) {
-  float sr0 = 0.f, si0 = 0.f, cr0 = 0.f, ci0 = 0.f;
-  float sr1 = 0.f, si1 = 0.f, cr1 = 0.f, ci1 = 0.f;
-  int n = 0;
-#pragma unroll 2
-  for (; n + 1 < N; n += 2) {
-    const float2 t0 = M[(size_t)n * ld], t1 = M[(size_t)(n + 1) * ld];
-    const float2 m0 = x[n], m1 = x[n + 1];
-    kahan_add(sr0, cr0, fmaf(t0.x, m0.x, -t0.y * m0.y));
-    kahan_add(si0, ci0, fmaf(t0.x, m0.y, t0.y * m0.x));
-    kahan_add(sr1, cr1, fmaf(t1.x, m1.x, -t1.y * m1.y));
-    kahan_add(si1, ci1, fmaf(t1.x, m1.y, t1.y * m1.x));
-  }
-  if (n < N) {
-    const float2 t0 = M[(size_t)n * ld];
-    const float2 m0 = x[n];
-    kahan_add(sr0, cr0, fmaf(t0.x, m0.x, -t0.y * m0.y));
-    kahan_add(si0, ci0, fmaf(t0.x, m0.y, t0.y * m0.x));
-  }
-  return mk(((double)sr0 - (double)cr0) + ((double)sr1 - (double)cr1),
-            ((double)si0 - (double)ci0) + ((double)si1 - (double)ci1));
-}
-
 // M2L as batched complex GEMMs. The V-list pairs (target box b, source box c)
 // are grouped by (level, offset class) at plan time; all pairs of a group use
 // the same matrix Tm[cls]. A CTA takes kGemmRows pairs of one group: their
@@ -120,6 +92,47 @@ __device__ __forceinline__ cd kahan_cdot(const float2* __restrict__ M, size_t ld
 // rows in its V-list order in FP64 (deterministic).
 constexpr int kGemmRows = 16;
 constexpr int kGemmBlock = 8;
+// M2M / L2L levels with fewer parents than kWideLevel use tiles of kNarrowRows
+// parents, so that the launch still spreads over the SMs.
+constexpr int kNarrowRows = 4;
+constexpr int kWideLevel = kGemmRows * 2 * 152;
+
+// One output column lo of a tile product: for every row r < R,
+// (sr, si)[r] += sum_{n < N} M[n * ld + lo] * x[n * R + r], with x in
+// shared memory. Plain FP32 FMAs over blocks of kGemmBlock terms (whose matrix
+// entries are loaded together), the blocks added with Kahan compensation
+// (cr, ci). Threads with act == false take part with zero entries.
+template <int R = kGemmRows>
+__device__ __forceinline__ void tile_gemm_column(const float2* __restrict__ M, size_t ld, int N,
+                                                 const float2* __restrict__ x, int lo, bool act,
+                                                 float (&sr)[R], float (&si)[R], float (&cr)[R],
+                                                 float (&ci)[R]) {
+  for (int n0 = 0; n0 < N; n0 += kGemmBlock) {
+    float tr[R], ti[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) tr[r] = ti[r] = 0.f;
+    float2 tb[kGemmBlock];
+#pragma unroll
+    for (int j = 0; j < kGemmBlock; ++j)
+      tb[j] = (act && n0 + j < N) ? M[(size_t)(n0 + j) * ld + lo] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kGemmBlock; ++j) {
+      if (n0 + j >= N) break;
+      const float2 t = tb[j];
+      const float2* m = x + (n0 + j) * R;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        tr[r] = fmaf(t.x, m[r].x, fmaf(-t.y, m[r].y, tr[r]));
+        ti[r] = fmaf(t.x, m[r].y, fmaf(t.y, m[r].x, ti[r]));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      kahan_add(sr[r], cr[r], tr[r]);
+      kahan_add(si[r], ci[r], ti[r]);
+    }
+  }
+}
 
 // mu32 = mh * conv (sigma-normalised multipoles in FP32), once per box that
 // is a V-list source; the GEMM tiles gather these rows.
@@ -159,32 +172,7 @@ __global__ void __launch_bounds__(kT) m2l_f32_gemm_kernel(
     float sr[kGemmRows], si[kGemmRows], cr[kGemmRows], ci[kGemmRows];
 #pragma unroll
     for (int r = 0; r < kGemmRows; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
-    for (int n0 = 0; n0 < Q; n0 += kGemmBlock) {
-      float tr[kGemmRows], ti[kGemmRows];
-#pragma unroll
-      for (int r = 0; r < kGemmRows; ++r) tr[r] = ti[r] = 0.f;
-      // the block's matrix entries first, so their loads are in flight together
-      float2 tb[kGemmBlock];
-#pragma unroll
-      for (int j = 0; j < kGemmBlock; ++j)
-        tb[j] = (act && n0 + j < Q) ? M[(size_t)(n0 + j) * Q + lo] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < kGemmBlock; ++j) {
-        if (n0 + j >= Q) break;
-        const float2 t = tb[j];
-        const float2* m = mu + (n0 + j) * kGemmRows;
-#pragma unroll
-        for (int r = 0; r < kGemmRows; ++r) {
-          tr[r] = fmaf(t.x, m[r].x, fmaf(-t.y, m[r].y, tr[r]));
-          ti[r] = fmaf(t.x, m[r].y, fmaf(t.y, m[r].x, ti[r]));
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < kGemmRows; ++r) {
-        kahan_add(sr[r], cr[r], tr[r]);
-        kahan_add(si[r], ci[r], ti[r]);
-      }
-    }
+    tile_gemm_column(M, Q, Q, mu, lo, act, sr, si, cr, ci);
     if (act) {
 #pragma unroll
       for (int r = 0; r < kGemmRows; ++r)
@@ -241,32 +229,54 @@ __global__ void l2l_f32_matrix_kernel(int l, int pp, int pc, int pbmax, const cd
   }
 }
 
-// CTA per parent box on level l: lambda_n = lh_n / conv_n (sigma-normalised,
-// FP32), then for each child lambda'_s = sum_n Tl[c][n][s] lambda_n with
-// compensated FP32 sums, and lh'_s += lambda'_s conv'_s in FP64.
+// L2L on level l as tile GEMMs: a CTA takes kGemmRows parents and one child
+// quadrant c = blockIdx.y, stages the parents' sigma-normalised locals
+// lambda_n = lh_n / conv_n (FP32) in shared memory, and computes
+// lambda'_s = sum_n Tl[c][n][s] lambda_n for all of them at once (threads over
+// s); the quadrant-c children get lh'_s += lambda'_s conv'_s in FP64.
+template <int R>
 __global__ void __launch_bounds__(kT) l2l_f32_kernel(
-    int l, int pp, int pc, int pbmax, const int* __restrict__ boxes, const int* __restrict__ child,
-    const long long* __restrict__ eoff, const float2* __restrict__ Tl,
-    const double* __restrict__ conv, cd* __restrict__ local) {
-  extern __shared__ float2 lam[];  // [Qp]
+    int l, int pp, int pc, int pbmax, const int* __restrict__ parents, int nb,
+    const int* __restrict__ child, const long long* __restrict__ eoff,
+    const float2* __restrict__ Tl, const double* __restrict__ conv, cd* __restrict__ local) {
+  extern __shared__ float2 lam[];  // [Qp][R]
   const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
-  const int b = boxes[blockIdx.x];
+  const int p0 = blockIdx.x * R, nr = min(R, nb - p0);
   const double* cvp = conv + (size_t)l * (pbmax + 1);
   const double* cvc = conv + (size_t)(l + 1) * (pbmax + 1);
-  const cd* lp = local + eoff[b];
-  for (int i = threadIdx.x; i < Qp; i += kT) {
-    const double f = 1.0 / cvp[abs(i - pp)];
-    lam[i] = make_float2((float)(lp[i].x * f), (float)(lp[i].y * f));
+  for (int idx = threadIdx.x; idx < Qp * R; idx += kT) {
+    const int r = idx / Qp, n = idx % Qp;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nr) {
+      const cd g = local[eoff[parents[p0 + r]] + n];
+      const double f = 1.0 / cvp[abs(n - pp)];
+      v = make_float2((float)(g.x * f), (float)(g.y * f));
+    }
+    lam[n * R + r] = v;
   }
   __syncthreads();
-  // threads over (child, output order) pairs
-  for (int task = threadIdx.x; task < 4 * Qc; task += kT) {
-    const int c = task / Qc, so = task % Qc - pc;
-    const int d = child[4 * b + c];
-    if (d < 0) continue;
-    const cd v = kahan_cdot(Tl + (size_t)c * Qp * Qc + so + pc, Qc, lam, Qp);
-    cd* dl = local + eoff[d] + so + pc;
-    *dl = cadd(*dl, cscale(v, cvc[abs(so)]));
+  {
+    const int c = blockIdx.y;
+    const float2* M = Tl + (size_t)c * Qp * Qc;
+    for (int so = threadIdx.x; so - (int)threadIdx.x < Qc; so += kT) {
+      const bool act = so < Qc;
+      float sr[R], si[R], cr[R], ci[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
+      tile_gemm_column<R>(M, Qc, Qp, lam, so, act, sr, si, cr, ci);
+      if (act) {
+        const double f = cvc[abs(so - pc)];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r >= nr) break;
+          const int d = child[4 * parents[p0 + r] + c];
+          if (d < 0) continue;
+          cd* dl = local + eoff[d] + so;
+          dl->x += ((double)sr[r] - (double)cr[r]) * f;
+          dl->y += ((double)si[r] - (double)ci[r]) * f;
+        }
+      }
+    }
   }
 }
 
@@ -296,37 +306,54 @@ __global__ void m2m_f32_matrix_kernel(int l, int pp, int pc, int pbmax, const cd
   }
 }
 
-// CTA per parent box on level l: mu_n = mh_n conv_n of each child (FP32),
-// mu'_s = sum_children sum_n Tm2m[c][n][s] mu_n (compensated FP32 per child,
-// children added in FP64), mh'_s = mu'_s / conv'_s.
+// M2M on level l as tile GEMMs: a CTA takes kGemmRows parents; for each
+// quadrant it stages the children's sigma-normalised multipoles
+// mu_n = mh_n conv_n (FP32) and adds sum_n Tm2m[c][n][s] mu_n to the parents'
+// compensated sums (threads over s); mh'_s = mu'_s / conv'_s in FP64.
+template <int R>
 __global__ void __launch_bounds__(kT) m2m_f32_kernel(
-    int l, int pp, int pc, int pbmax, const int* __restrict__ boxes, const int* __restrict__ child,
-    const long long* __restrict__ eoff, const float2* __restrict__ Tmm,
-    const double* __restrict__ conv, cd* __restrict__ mpole) {
-  extern __shared__ float2 mus[];  // [4][Qc]
+    int l, int pp, int pc, int pbmax, const int* __restrict__ parents, int nb,
+    const int* __restrict__ child, const long long* __restrict__ eoff,
+    const float2* __restrict__ Tmm, const double* __restrict__ conv, cd* __restrict__ mpole) {
+  extern __shared__ float2 mus[];  // [Qc][R]
   const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
-  const int b = boxes[blockIdx.x];
+  const int p0 = blockIdx.x * R, nr = min(R, nb - p0);
   const double* cvp = conv + (size_t)l * (pbmax + 1);
   const double* cvc = conv + (size_t)(l + 1) * (pbmax + 1);
-  for (int task = threadIdx.x; task < 4 * Qc; task += kT) {
-    const int c = task / Qc, i = task % Qc;
-    const int d = child[4 * b + c];
-    float2 v = make_float2(0.f, 0.f);
-    if (d >= 0) {
-      const cd a = mpole[eoff[d] + i];
-      const double f = cvc[abs(i - pc)];
-      v = make_float2((float)(a.x * f), (float)(a.y * f));
+  for (int so0 = 0; so0 < Qp; so0 += kT) {
+    const int so = so0 + threadIdx.x;
+    const bool act = so < Qp;
+    float sr[R], si[R], cr[R], ci[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
+    for (int c = 0; c < 4; ++c) {
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < Qc * R; idx += kT) {
+        const int r = idx / Qc, n = idx % Qc;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < nr) {
+          const int d = child[4 * parents[p0 + r] + c];
+          if (d >= 0) {
+            const cd a = mpole[eoff[d] + n];
+            const double f = cvc[abs(n - pc)];
+            v = make_float2((float)(a.x * f), (float)(a.y * f));
+          }
+        }
+        mus[n * R + r] = v;
+      }
+      __syncthreads();
+      tile_gemm_column<R>(Tmm + (size_t)c * Qc * Qp, Qp, Qc, mus, so, act, sr, si, cr, ci);
     }
-    mus[task] = v;
-  }
-  __syncthreads();
-  cd* dst = mpole + eoff[b];
-  for (int so = (int)threadIdx.x - pp; so <= pp; so += kT) {
-    cd sum = mk(0.0, 0.0);
-    for (int c = 0; c < 4; ++c)
-      if (child[4 * b + c] >= 0)
-        sum = cadd(sum, kahan_cdot(Tmm + (size_t)c * Qc * Qp + so + pp, Qp, mus + c * Qc, Qc));
-    dst[so + pp] = cscale(sum, 1.0 / cvp[abs(so)]);
+    if (act) {
+      const double f = 1.0 / cvp[abs(so - pp)];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (r >= nr) break;
+        cd* dst = mpole + eoff[parents[p0 + r]] + so;
+        dst->x = ((double)sr[r] - (double)cr[r]) * f;
+        dst->y = ((double)si[r] - (double)ci[r]) * f;
+      }
+    }
   }
 }
 
@@ -335,10 +362,10 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
 qbx_status configure_mixed_kernels(int smem_optin) {
   QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)m2l_f32_gemm_kernel,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
-  QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)l2l_f32_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
-  QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)m2m_f32_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+  const void* k[] = {(const void*)l2l_f32_kernel<kGemmRows>, (const void*)l2l_f32_kernel<kNarrowRows>,
+                     (const void*)m2m_f32_kernel<kGemmRows>, (const void*)m2m_f32_kernel<kNarrowRows>};
+  for (const void* fn : k)
+    QBX_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
   return QBX_OK;
 }
 
@@ -480,9 +507,14 @@ qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
     if (nb == 0) continue;
     const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
-    m2m_f32_kernel<<<nb, kT, (size_t)4 * (2 * pc + 1) * sizeof(float2), s>>>(
-        l, pp, pc, f->pb_max, f->nonleaf.ptr + f->nonleaf_off[l], f->box.child.ptr, f->eoff.ptr,
-        f->tmm_f32.ptr + f->h_tmm_off[l], f->conv.ptr, f->mpole.ptr);
+    const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
+    const float2* T = f->tmm_f32.ptr + f->h_tmm_off[l];
+    if (nb >= kWideLevel)
+      m2m_f32_kernel<kGemmRows><<<nblk(nb, kGemmRows), kT, (size_t)(2 * pc + 1) * kGemmRows * sizeof(float2), s>>>(
+          l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
+    else
+      m2m_f32_kernel<kNarrowRows><<<nblk(nb, kNarrowRows), kT, (size_t)(2 * pc + 1) * kNarrowRows * sizeof(float2), s>>>(
+          l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;
   }
@@ -494,9 +526,14 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
     if (nb == 0) continue;
     const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
-    l2l_f32_kernel<<<nb, kT, (size_t)(2 * pp + 1) * sizeof(float2), s>>>(
-        l, pp, pc, f->pb_max, f->nonleaf.ptr + f->nonleaf_off[l], f->box.child.ptr, f->eoff.ptr,
-        f->tl_f32.ptr + f->h_tl_off[l], f->conv.ptr, f->local.ptr);
+    const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
+    const float2* T = f->tl_f32.ptr + f->h_tl_off[l];
+    if (nb >= kWideLevel)
+      l2l_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), 4), kT, (size_t)(2 * pp + 1) * kGemmRows * sizeof(float2), s>>>(
+          l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
+    else
+      l2l_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), 4), kT, (size_t)(2 * pp + 1) * kNarrowRows * sizeof(float2), s>>>(
+          l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;
   }
