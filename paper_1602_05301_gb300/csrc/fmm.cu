@@ -38,7 +38,11 @@ constexpr int kThreads = 128;
 // wide, so they carry many centres (about 65 on the starfish workloads) and few
 // leaves hold any: one warp per leaf left most SMs idle (measured 2x slower).
 constexpr int kLeafThreads = 128;
-constexpr int kChunk = 16;  // sources per shared-memory chunk in P2M / P2L
+// Sources per shared-memory chunk in P2M / P2L. Their rows (one FP64 recurrence
+// per source) are built by threads 0..kChunk-1, a full warp: the SM's FP64
+// rate is shared by its warps and a warp instruction costs the same with few
+// lanes active, so partly filled warps waste it (measured).
+constexpr int kChunk = 32;
 constexpr double kRescale = 1e100;
 // Leaves holding a centre are at least this many expansion radii wide.
 constexpr double kLeafOverRadius = 4.0;
@@ -1656,9 +1660,13 @@ qbx_status launch_centre_near(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, b
 }
 
 // Shared memory of a source-row kernel (P2M, P2L) at box order pb: a full
-// chunk of rows when it fits the opt-in limit, else as many rows as fit.
+// warp's chunk of rows while that keeps the block within kRowsSmemTarget
+// (several blocks per SM), else half a warp's; never above the opt-in limit.
+constexpr size_t kRowsSmemTarget = 60 * 1024;
 size_t rows_launch_smem(int pb) {
-  return std::min(rows_smem(pb, kChunk), (size_t)g_smem_optin);
+  const size_t full = rows_smem(pb, kChunk);
+  const size_t sm = full <= kRowsSmemTarget ? full : rows_smem(pb, kChunk / 2);
+  return std::min(sm, (size_t)g_smem_optin);
 }
 
 // Largest box order among the levels l with off[l+1] > off[l] (boxes of a
