@@ -68,6 +68,7 @@ extern "C" qbx_status qbx_batch_create(int32_t n, qbx_handle* const* handles, in
     }
   qbx_batch* b = new qbx_batch();
   b->h.assign(handles, handles + n);
+  for (int i = 0; i < n; ++i) handles[i]->batched = true;
   b->soff.assign(n + 1, 0);
   b->toff.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
@@ -103,6 +104,7 @@ extern "C" qbx_status qbx_batch_create(int32_t n, qbx_handle* const* handles, in
 extern "C" void qbx_batch_destroy(qbx_batch* b) {
   if (!b) return;
   if (b->main) cudaStreamSynchronize(b->main);
+  for (qbx_handle* h : b->h) h->batched = false;
   delete b;
 }
 

@@ -1598,7 +1598,7 @@ qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSe
   stage_begin(h, QBX_STAGE_L2QBXL, s);
   // a warp per centre while the centres are too few to fill the GPU with
   // threads (the kernel is then latency-bound), else a thread per centre
-  if (C.n < kL2qbxlThreadMin)
+  if (C.n < kL2qbxlThreadMin && !h->batched)
     l2qbxl_kernel<<<nblk(C.n, kThreads / 32), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
   else
     l2qbxl_thread_kernel<PM><<<nblk(C.n, kThreads), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
@@ -1721,7 +1721,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   Fmm F = make_view(h, f, S, D);
   QBX_CUDA_TRY(cudaMemsetAsync(f->mpole.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
   QBX_CUDA_TRY(cudaMemsetAsync(f->local.ptr, 0, (size_t)f->n_coef * sizeof(cd), s));
-  const bool fork = !h->timing && !debug_sync() && f->near_stream != nullptr;
+  const bool fork = !h->timing && !debug_sync() && !h->batched && f->near_stream != nullptr;
   cudaStream_t s2 = fork ? f->near_stream : s;
   auto signal = [&](cudaEvent_t ev, cudaStream_t from) -> qbx_status {
     if (fork) QBX_CUDA_TRY(cudaEventRecord(ev, from));

@@ -509,7 +509,7 @@ qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
     const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
     const float2* T = f->tmm_f32.ptr + f->h_tmm_off[l];
-    if (nb >= kWideLevel)
+    if (nb >= kWideLevel || h->batched)
       m2m_f32_kernel<kGemmRows><<<nblk(nb, kGemmRows), kT, (size_t)(2 * pc + 1) * kGemmRows * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
     else
@@ -528,7 +528,7 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
     const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
     const float2* T = f->tl_f32.ptr + f->h_tl_off[l];
-    if (nb >= kWideLevel)
+    if (nb >= kWideLevel || h->batched)
       l2l_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), 4), kT, (size_t)(2 * pp + 1) * kGemmRows * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
     else

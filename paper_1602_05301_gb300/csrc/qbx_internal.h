@@ -79,6 +79,10 @@ struct qbx_handle {
   int64_t n_tgt = 0, n_qbx_tgt = 0, n_direct_tgt = 0;
   bool planned = false;
   int mode = QBX_DIRECT;
+  // Set while the handle belongs to a batch: many problems then run at once,
+  // so an evaluation favours throughput (one stream, thread-per-centre and
+  // wide tiles) over the latency of a single problem.
+  bool batched = false;
   DevBuf<double> tgt_xy;
   DevBuf<int32_t> assoc;                    // [n_tgt] centre or -1
   DevBuf<int32_t> qbx_tgt_list, direct_tgt_list;

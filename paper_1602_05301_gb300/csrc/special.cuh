@@ -91,11 +91,14 @@ __device__ __forceinline__ void hankel01(double x, cd& h0, cd& h1) {
 }
 
 // Start index of the backward recurrence for orders 0..pmax at argument x:
-// far enough above max(pmax, x) that the recurrence has converged to the
-// minimal solution to full double precision.
+// far enough above m = max(pmax, x) that the recurrence has converged to the
+// minimal solution to full double precision. The relative error of J_m from a
+// start N is about (x/2)^{2(N-m)} (m!/N!)^2, so for x well below m a dozen
+// orders suffice; the sqrt(40 x) term keeps the classical margin of order
+// sqrt(m) where x approaches m (the transition region).
 __device__ __forceinline__ int miller_start(int pmax, double x) {
   int m = pmax > (int)x ? pmax : (int)x;
-  int n = m + 20 + (int)(2.0 * sqrt(40.0 * (double)(m + 1)));
+  int n = m + 12 + (int)(2.0 * sqrt(40.0 * x));
   return (n + 1) & ~1;  // even
 }
 
