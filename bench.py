@@ -356,6 +356,11 @@ def run_ours(args, w, ws, rank, local):
                               "achieved is FP64-equivalent (FP32 flops scaled by the peak "
                               "ratio) unless the kernel is FP32 only",
                 "centres_formed": n_used if fmm else stats["n_centres"]}
+        # the same fraction for every timed stage (flop model over its event time)
+        roof["frac_by_stage"] = {
+            k: round(1e3 * (flops[k][0] / (FP64_PEAK_TFLOPS * 1e12) +
+                            flops[k][1] / (FP32_PEAK_TFLOPS * 1e12)) / per[k], 4)
+            for k in per if k in flops and per[k] > 0}
 
     # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
     hS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).pin_memory() if sS is not None else None

@@ -354,70 +354,9 @@ __global__ void __launch_bounds__(kThreads) m2m_kernel(Fmm F, const int* __restr
 
 // ---------------------------------------------------------------- M2L (Stage 4)
 // lh_l += (-1)^l sum_n What_{n+l} mh_n c(l,n), What_m = s^|m| W_m(m_b - m_c),
-// c(l,n) = s^{2 min(|l|,|n|)} when l and n have opposite signs, else 1.
-// sum_{n=n0}^{n1-1} w[n] a[n]. One accumulator: the FP64 pipe (two FMAs per
-// clock per SM) is the limit, not the latency of the dependent chain, so extra
-// accumulators only add instructions (measured slower).
-__device__ __forceinline__ cd cdot(const cd* w, const cd* a, int n0, int n1) {
-  cd s = mk(0.0, 0.0);
-  for (int n = n0; n < n1; ++n) cfma(s, w[n], a[n]);
-  return s;
-}
-
-__host__ __device__ inline size_t m2l_smem(int pb) {
-  return (size_t)(3 * (2 * pb + 1) + 4 * pb + 1) * sizeof(cd) + (size_t)(pb + 1) * sizeof(double);
-}
-
-__global__ void __launch_bounds__(kThreads) m2l_kernel(Fmm F, const int* __restrict__ boxes) {
-  extern __shared__ cd smem[];
-  const int b = boxes[blockIdx.x];
-  const int l = F.level[b];
-  const int pb = F.lpb[l], Q = 2 * pb + 1, T = 4 * pb + 1;
-  cd* a = smem;                       // [Q]   mh_n
-  cd* a2 = a + Q;                     // [Q]   mh_n s^{2|n|}
-  cd* w = a2 + Q;                     // [T]   What_m at m + 2 pb
-  cd* acc = w + T;                    // [Q]
-  double* p2 = (double*)(acc + Q);    // [pb+1] s^{2j}
-  const double* pwl = pw_row(F, l);
-  for (int j = threadIdx.x; j <= pb; j += kThreads) p2[j] = pwl[2 * j];
-  for (int i = threadIdx.x; i < Q; i += kThreads) acc[i] = mk(0.0, 0.0);
-  __syncthreads();
-  for (int e = F.voff[b]; e < F.voff[b + 1]; ++e) {
-    const int c = F.vidx[e];
-    const cd* tab = table(F, F.t_m2l, 49, l, F.vcls[e]);
-    const cd* mp = F.mpole + F.eoff[c];
-    for (int i = threadIdx.x; i < Q; i += kThreads) {
-      const cd v = mp[i];
-      a[i] = v;
-      a2[i] = cscale(v, p2[abs(i - pb)]);
-    }
-    for (int i = threadIdx.x; i < T; i += kThreads) w[i] = tab[i - 2 * pb];
-    __syncthreads();
-    // Split of the n range by the sign of n relative to L: same sign -> factor 1;
-    // opposite sign with |n| <= |L| -> s^{2|n|} (folded into a2); |n| > |L| -> s^{2|L|}.
-    for (int L = (int)threadIdx.x - pb; L <= pb; L += kThreads) {
-      const cd* wl = w + L + 2 * pb;   // wl[n] = What_{n+L}
-      const cd* ac = a + pb;           // ac[n] = mh_n
-      const cd* ac2 = a2 + pb;
-      cd same, near, far;
-      if (L >= 0) {
-        same = cdot(wl, ac, 0, pb + 1);
-        near = cdot(wl, ac2, -L, 0);
-        far = cdot(wl, ac, -pb, -L);
-      } else {
-        same = cdot(wl, ac, -pb, 1);
-        near = cdot(wl, ac2, 1, -L + 1);
-        far = cdot(wl, ac, -L + 1, pb + 1);
-      }
-      cd sum = cadd(cadd(same, near), cscale(far, p2[abs(L)]));
-      if (L & 1) sum = mk(-sum.x, -sum.y);
-      acc[L + pb] = cadd(acc[L + pb], sum);
-    }
-    __syncthreads();
-  }
-  cd* dst = F.local + F.eoff[b];
-  for (int i = threadIdx.x; i < Q; i += kThreads) dst[i] = cadd(dst[i], acc[i]);
-}
+// c(l,n) = s^{2 min(|l|,|n|)} when l and n have opposite signs, else 1: both
+// precisions run it as tile GEMMs over dense per-(level, offset class)
+// matrices (mixed.cu).
 
 // ---------------------------------------------------------------- P2L (Stage 6)
 // CTA per box with an X list: lh_l += s^|l| sum_j [q W_l + d (k/2)(nu W_{l-1} - conj(nu) W_{l+1})]
@@ -1129,7 +1068,7 @@ qbx_status configure_kernels() {
   if (done.count(dev)) return QBX_OK;
   int optin = 0;
   QBX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const void* k[] = {(const void*)p2m_kernel, (const void*)m2m_kernel, (const void*)m2l_kernel,
+  const void* k[] = {(const void*)p2m_kernel, (const void*)m2m_kernel,
                      (const void*)p2l_kernel, (const void*)l2l_kernel};
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -1349,10 +1288,12 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   QBX_CUDA_TRY(cudaStreamCreateWithFlags(&f->near_stream, cudaStreamNonBlocking));
   for (cudaEvent_t* ev : {&f->ev_fork, &f->ev_join, &f->ev_p2l, &f->ev_m2m, &f->ev_down, &f->ev_out})
     QBX_CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
-  // the largest per-block footprint (M2L at the largest order) bounds all others
-  if (m2l_smem(f->pb_max) > (size_t)g_smem_optin) {
+  // the largest per-block footprint (the M2M / L2L GEMMs at the largest
+  // order) bounds all others
+  const size_t smem_need = gemm_smem_bytes(f->pb_max);
+  if (smem_need > (size_t)g_smem_optin) {
     set_error("box order %d needs %zu bytes of shared memory per block (device: %d)", f->pb_max,
-              m2l_smem(f->pb_max), g_smem_optin);
+              smem_need, g_smem_optin);
     return QBX_ERR_ARG;
   }
   TRY(mixed_plan_build(h, f));
@@ -1811,10 +1752,8 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   stage_begin(h, QBX_STAGE_M2L, s);
   if (mixed) {
     TRY(launch_m2l_f32(h, f, s));
-  } else if (f->n_vbox > 0) {
-    m2l_kernel<<<f->n_vbox, kThreads, m2l_smem(max_order(pb, f->vbox_off)), s>>>(F, f->vbox.ptr);
-    QBX_KCHECK("m2l", s);
-    h->launches += 1;
+  } else {
+    TRY(launch_m2l_f64(h, f, s));
   }
   stage_end(h, QBX_STAGE_M2L, s);
   stage_begin(h, QBX_STAGE_L2L, s);

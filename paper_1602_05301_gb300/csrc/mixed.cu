@@ -152,32 +152,49 @@ __global__ void __launch_bounds__(kT) mpole_to_f32_kernel(
   }
 }
 
+// M2L work items: (tile, first row within the tile, first output order). Each
+// CTA computes kT consecutive output orders (one per thread) of its rows and
+// stages the source rows through shared memory kChunkK orders at a time, so
+// its footprint does not grow with the box order. kChunkK is a multiple of
+// kGemmBlock: the compensated blocks, and so the result bits, do not depend on
+// the staging.
+constexpr int kChunkK = 128;
+static_assert(kChunkK % kGemmBlock == 0, "staging must keep the summation blocks");
+
 __global__ void __launch_bounds__(kT) m2l_f32_gemm_kernel(
-    const int4* __restrict__ tiles, const int* __restrict__ lpb,
+    const int4* __restrict__ items, const int4* __restrict__ tiles, const int* __restrict__ lpb,
     const long long* __restrict__ tm_off, const int* __restrict__ row_src,
     const long long* __restrict__ eoff, const float2* __restrict__ mu32,
     const float2* __restrict__ tm, const long long* __restrict__ yoff, float2* __restrict__ Y) {
-  extern __shared__ float2 mu[];  // [Q][kGemmRows]
-  const int4 T = tiles[blockIdx.x];  // (level * 49 + class, first row, rows, level)
+  __shared__ float2 mu[kChunkK * kGemmRows];  // [n][row]
+  const int4 I = items[blockIdx.x];
+  const int4 T = tiles[I.x];  // (level * 49 + class, first row, rows, level)
   const int cls = T.x % 49, row0 = T.y, nr = T.z, l = T.w;
   const int pb = lpb[l], Q = 2 * pb + 1;
-  for (int idx = threadIdx.x; idx < Q * kGemmRows; idx += kT) {
-    const int r = idx / Q, n = idx % Q;  // coalesced reads along each source row
-    mu[n * kGemmRows + r] = r < nr ? mu32[eoff[row_src[row0 + r]] + n] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
+  const int lo = I.z + (int)threadIdx.x;
+  const bool act = lo < Q;
+  // warps past the last output order only help stage the sources: an FMA
+  // costs its warp the same however few lanes are active
+  const bool warp_act = I.z + (int)(threadIdx.x & ~31u) < Q;
   const float2* M = tm + tm_off[l] + (size_t)cls * Q * Q;
-  for (int lo = threadIdx.x; lo - (int)threadIdx.x < Q; lo += kT) {
-    const bool act = lo < Q;
-    float sr[kGemmRows], si[kGemmRows], cr[kGemmRows], ci[kGemmRows];
+  float sr[kGemmRows], si[kGemmRows], cr[kGemmRows], ci[kGemmRows];
 #pragma unroll
-    for (int r = 0; r < kGemmRows; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
-    tile_gemm_column(M, Q, Q, mu, lo, act, sr, si, cr, ci);
-    if (act) {
-#pragma unroll
-      for (int r = 0; r < kGemmRows; ++r)
-        if (r < nr) Y[yoff[row0 + r] + lo] = make_float2(sr[r] - cr[r], si[r] - ci[r]);
+  for (int r = 0; r < kGemmRows; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
+  for (int n0 = 0; n0 < Q; n0 += kChunkK) {
+    const int nk = min(kChunkK, Q - n0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nk * kGemmRows; idx += kT) {
+      const int r = idx / nk, n = idx % nk;  // coalesced reads along each source row
+      mu[n * kGemmRows + r] =
+          r < nr ? mu32[eoff[row_src[row0 + r]] + n0 + n] : make_float2(0.f, 0.f);
     }
+    __syncthreads();
+    if (warp_act) tile_gemm_column(M + (size_t)n0 * Q, Q, nk, mu, lo, act, sr, si, cr, ci);
+  }
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < kGemmRows; ++r)
+      if (r < nr) Y[yoff[row0 + r] + lo] = make_float2(sr[r] - cr[r], si[r] - ci[r]);
   }
 }
 
@@ -200,6 +217,100 @@ __global__ void __launch_bounds__(kT) m2l_f32_reduce_kernel(
       sum.y += (double)y.y;
     }
     dst[lo] = cadd(dst[lo], cscale(sum, cv[abs(lo - pb)]));
+  }
+}
+
+// ---------------------------------------------------------------- FP64 M2L as tile GEMMs
+// The FP64 path's M2L, lh_l += (-1)^l sum_n What_{n+l} c(l, n) mh_n with
+// What_m = s^|m| W_m(D) and c(l, n) = s^{2 min(|l|,|n|)} when l and n have
+// opposite signs (else 1), written as dense matrices per (level, offset
+// class): T64[cls][n][l] = (-1)^l What_{n+l} c(l, n) (FP64; the same tiles and
+// ordered reduction as the FP32 M2L, without normalisation or compensation).
+__global__ void m2l_f64_matrix_kernel(int l, int pb, int pbmax, const cd* __restrict__ t_m2l,
+                                      const double* __restrict__ pw, cd* __restrict__ Tm) {
+  const int cls = blockIdx.x;
+  const int n = (int)blockIdx.y - pb;
+  const int Q = 2 * pb + 1;
+  const cd* w = t_m2l + ((size_t)l * 49 + cls) * (4 * pbmax + 1) + 2 * pbmax;
+  const double* p2 = pw + (size_t)l * (2 * pbmax + 3);  // s^j
+  cd* dst = Tm + ((size_t)cls * Q + (n + pb)) * Q;
+  const int dx = cls / 7 - 3, dy = cls % 7 - 3;
+  const bool used = max(abs(dx), abs(dy)) >= 2;  // V-list offsets only
+  for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += blockDim.x) {
+    cd v = mk(0.0, 0.0);
+    if (used) {
+      v = w[n + lo];
+      if ((n < 0 && lo > 0) || (n > 0 && lo < 0)) v = cscale(v, p2[2 * min(abs(n), abs(lo))]);
+      if (lo & 1) v = mk(-v.x, -v.y);
+    }
+    dst[lo + pb] = v;
+  }
+}
+
+// FP64 work items take kF64Rows rows of a tile (the accumulators of 16 FP64
+// rows would not fit in registers), kT output orders and the same staging as
+// the FP32 items. Results go to the FP64 rows of Y64, added per target box by
+// m2l_f64_reduce_kernel in V-list order.
+constexpr int kF64Rows = 8;
+__global__ void __launch_bounds__(kT) m2l_f64_gemm_kernel(
+    const int4* __restrict__ items, const int4* __restrict__ tiles, const int* __restrict__ lpb,
+    const long long* __restrict__ tm_off, const int* __restrict__ row_src,
+    const long long* __restrict__ eoff, const cd* __restrict__ mpole,
+    const cd* __restrict__ tm, const long long* __restrict__ yoff, cd* __restrict__ Y) {
+  __shared__ cd xs[kChunkK * kF64Rows];  // [n][row]
+  const int4 I = items[blockIdx.x];
+  const int4 T = tiles[I.x];
+  const int cls = T.x % 49, row0 = T.y + I.y, nr = min(kF64Rows, T.z - I.y), l = T.w;
+  const int pb = lpb[l], Q = 2 * pb + 1;
+  const int lo = I.z + (int)threadIdx.x;
+  const bool act = lo < Q;
+  const bool warp_act = I.z + (int)(threadIdx.x & ~31u) < Q;  // as in the FP32 items
+  const cd* M = tm + tm_off[l] + (size_t)cls * Q * Q;
+  cd acc[kF64Rows];
+#pragma unroll
+  for (int r = 0; r < kF64Rows; ++r) acc[r] = mk(0.0, 0.0);
+  for (int n0 = 0; n0 < Q; n0 += kChunkK) {
+    const int nk = min(kChunkK, Q - n0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nk * kF64Rows; idx += kT) {
+      const int r = idx / nk, n = idx % nk;
+      xs[n * kF64Rows + r] = r < nr ? mpole[eoff[row_src[row0 + r]] + n0 + n] : mk(0.0, 0.0);
+    }
+    __syncthreads();
+    if (!warp_act) continue;
+    for (int j0 = 0; j0 < nk; j0 += kGemmBlock) {
+      cd tb[kGemmBlock];
+#pragma unroll
+      for (int j = 0; j < kGemmBlock; ++j)
+        tb[j] = (act && j0 + j < nk) ? M[(size_t)(n0 + j0 + j) * Q + lo] : mk(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < kGemmBlock; ++j) {
+        if (j0 + j >= nk) break;
+        const cd* x = xs + (j0 + j) * kF64Rows;
+#pragma unroll
+        for (int r = 0; r < kF64Rows; ++r) cfma(acc[r], tb[j], x[r]);
+      }
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < kF64Rows; ++r)
+      if (r < nr) Y[yoff[row0 + r] + lo] = acc[r];
+  }
+}
+
+// lh_lo(b) += sum over b's V entries e (in list order) of Y64[row(e)][lo].
+__global__ void __launch_bounds__(kT) m2l_f64_reduce_kernel(
+    const int* __restrict__ boxes, const int* __restrict__ level, const int* __restrict__ lpb,
+    const int* __restrict__ voff, const int* __restrict__ vrow, const long long* __restrict__ yoff,
+    const cd* __restrict__ Y, const long long* __restrict__ eoff, cd* __restrict__ local) {
+  const int b = boxes[blockIdx.x];
+  const int Q = 2 * lpb[level[b]] + 1;
+  cd* dst = local + eoff[b];
+  for (int lo = threadIdx.x; lo < Q; lo += kT) {
+    cd sum = mk(0.0, 0.0);
+    for (int e = voff[b]; e < voff[b + 1]; ++e) sum = cadd(sum, Y[yoff[vrow[e]] + lo]);
+    dst[lo] = cadd(dst[lo], sum);
   }
 }
 
@@ -360,8 +471,6 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
 }  // namespace
 
 qbx_status configure_mixed_kernels(int smem_optin) {
-  QBX_CUDA_TRY(cudaFuncSetAttribute((const void*)m2l_f32_gemm_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
   const void* k[] = {(const void*)l2l_f32_kernel<kGemmRows>, (const void*)l2l_f32_kernel<kNarrowRows>,
                      (const void*)m2m_f32_kernel<kGemmRows>, (const void*)m2m_f32_kernel<kNarrowRows>};
   for (const void* fn : k)
@@ -441,7 +550,24 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
       for (int64_t r = gcount[g]; r < gcount[g + 1]; r += kGemmRows)
         tiles.push_back(make_int4(g, (int)r, (int)std::min<int64_t>(kGemmRows, gcount[g + 1] - r), l));
     }
-    // coarse levels (largest orders) first
+    // coarse levels (largest orders) first; work items per tile: row groups x
+    // chunks of kT output orders
+    std::vector<int4> it32, it64;
+    for (size_t t = 0; t < tiles.size(); ++t) {
+      const int Q = 2 * f->h_pb[tiles[t].w] + 1;
+      for (int c0 = 0; c0 < Q; c0 += kT) {
+        it32.push_back(make_int4((int)t, 0, c0, 0));
+        for (int r0 = 0; r0 < tiles[t].z; r0 += kF64Rows) it64.push_back(make_int4((int)t, r0, c0, 0));
+      }
+    }
+    f->n_m2l_items32 = (int)it32.size();
+    f->n_m2l_items64 = (int)it64.size();
+    QBX_CUDA_TRY(f->m2l_items32.alloc(std::max<size_t>(1, it32.size())));
+    QBX_CUDA_TRY(f->m2l_items64.alloc(std::max<size_t>(1, it64.size())));
+    if (!it32.empty()) {
+      QBX_CUDA_TRY(cudaMemcpy(f->m2l_items32.ptr, it32.data(), it32.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->m2l_items64.ptr, it64.data(), it64.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
     f->n_m2l_tiles = (int)tiles.size();
     QBX_CUDA_TRY(f->m2l_tiles.alloc(std::max<size_t>(1, tiles.size())));
     QBX_CUDA_TRY(f->m2l_vrow.alloc(vrow.size()));
@@ -465,6 +591,16 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
     QBX_CUDA_TRY(cudaMemcpy(f->m2l_rowsrc.ptr, row_src.data(), row_src.size() * sizeof(int), cudaMemcpyHostToDevice));
     QBX_CUDA_TRY(cudaMemcpy(f->m2l_yoff.ptr, yoff.data(), yoff.size() * sizeof(long long), cudaMemcpyHostToDevice));
   }
+  // FP64 M2L matrices (same offsets as the FP32 ones) and result rows
+  QBX_CUDA_TRY(f->tm_f64.alloc(std::max<long long>(1, tot)));
+  for (int l = 2; l < f->n_levels; ++l) {
+    if (f->vbox_off[l + 1] == f->vbox_off[l]) continue;
+    const int pb = f->h_pb[l];
+    dim3 grid(49, 2 * pb + 1);
+    m2l_f64_matrix_kernel<<<grid, kT>>>(l, pb, pbm, f->t_m2l.ptr, f->pw.ptr, f->tm_f64.ptr + off[l]);
+    QBX_CUDA_TRY(cudaGetLastError());
+  }
+  QBX_CUDA_TRY(f->m2l_y64.alloc(std::max<size_t>(1, f->m2l_y.n)));
   // M2M matrices for parents on levels 2 .. n_levels - 2
   {
     std::vector<long long> moff(f->n_levels, 0);
@@ -499,6 +635,22 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
                                         f->tl_f32.ptr + loff[l]);
     QBX_CUDA_TRY(cudaGetLastError());
   }
+  return QBX_OK;
+}
+
+size_t gemm_smem_bytes(int pb) { return (size_t)(2 * pb + 1) * kGemmRows * sizeof(float2); }
+
+qbx_status launch_m2l_f64(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
+  if (f->n_vbox == 0 || f->n_m2l_tiles == 0) return QBX_OK;
+  m2l_f64_gemm_kernel<<<f->n_m2l_items64, kT, 0, s>>>(
+      f->m2l_items64.ptr, f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr, f->mpole.ptr,
+      f->tm_f64.ptr, f->m2l_yoff.ptr, f->m2l_y64.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  m2l_f64_reduce_kernel<<<f->n_vbox, kT, 0, s>>>(
+      f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->V.off.ptr, f->m2l_vrow.ptr, f->m2l_yoff.ptr,
+      f->m2l_y64.ptr, f->eoff.ptr, f->local.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  h->launches += 2;
   return QBX_OK;
 }
 
@@ -542,9 +694,6 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
 
 qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
   if (f->n_vbox == 0 || f->n_m2l_tiles == 0) return QBX_OK;
-  int pbv = 0;  // largest order among levels with V lists
-  for (int l = 0; l < f->n_levels; ++l)
-    if (f->vbox_off[l + 1] > f->vbox_off[l]) pbv = std::max(pbv, f->h_pb[l]);
   if (f->n_vsrc > 0) {
     mpole_to_f32_kernel<<<f->n_vsrc, kT, 0, s>>>(f->pb_max, f->m2l_vsrc.ptr, f->box.level.ptr,
                                                  f->lpb.ptr, f->eoff.ptr, f->conv.ptr,
@@ -552,9 +701,8 @@ qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;
   }
-  const size_t sm = (size_t)(2 * pbv + 1) * kGemmRows * sizeof(float2);
-  m2l_f32_gemm_kernel<<<f->n_m2l_tiles, kT, sm, s>>>(
-      f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr, f->mu32.ptr,
+  m2l_f32_gemm_kernel<<<f->n_m2l_items32, kT, 0, s>>>(
+      f->m2l_items32.ptr, f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr, f->mu32.ptr,
       f->tm_f32.ptr, f->m2l_yoff.ptr, f->m2l_y.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   m2l_f32_reduce_kernel<<<f->n_vbox, kT, 0, s>>>(

@@ -107,9 +107,13 @@ struct FmmPlan {
   // result buffer
   DevBuf<int4> m2l_tiles;
   int n_m2l_tiles = 0;
+  DevBuf<int4> m2l_items32, m2l_items64;  // (tile, first row, first output order)
+  int n_m2l_items32 = 0, n_m2l_items64 = 0;
   DevBuf<int> m2l_vrow, m2l_rowsrc;
   DevBuf<long long> m2l_yoff;
   DevBuf<float2> m2l_y;
+  DevBuf<cd> tm_f64;                    // FP64 M2L matrices (offsets tm_off, as the FP32 ones)
+  DevBuf<cd> m2l_y64;                   // FP64 result rows of the FP64 M2L GEMM
   DevBuf<int> m2l_vsrc;                 // boxes that are V-list sources
   int n_vsrc = 0;
   DevBuf<float2> mu32;                  // [n_coef] their sigma-normalised FP32 multipoles
@@ -124,6 +128,9 @@ qbx_status configure_mixed_kernels(int smem_optin);
 qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
+qbx_status launch_m2l_f64(qbx_handle* h, FmmPlan* f, cudaStream_t s);
+// shared memory of one M2M / L2L tile-GEMM block at box order pb
+size_t gemm_smem_bytes(int pb);
 
 qbx_status tree_build(qbx_handle* h, FmmPlan* f, int n_max, double kappa);
 qbx_status tree_lists(qbx_handle* h, FmmPlan* f);

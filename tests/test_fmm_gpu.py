@@ -186,3 +186,34 @@ def test_mixed_precision_starfish_config(qbxmod, oracle):
                                       centre_of_target=assoc[sample])
     assert rel_l2(u32[sample], u_ref) < 1e-6
     lp.close()
+
+
+def test_schedules_give_identical_fp64_results(qbxmod):
+    """The evaluation's two-stream schedule, the single-stream order used while
+    stage timing is on, and the throughput mode of a batched handle add the
+    same terms in the same order into every output: FP64 results agree bit for
+    bit (with and without the coefficients of every centre)."""
+    w = make_config(2)
+    g = w["geom"]
+    lp = qbxmod.LayerPotential(g.as_dict(), w["p"], sides=w["sides"])
+    lp.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"], mode=qbxmod.QBX_FMM,
+             p_fmm=w["p_fmm"])
+    args = dict(sigma_S=w["sigma_S"], sigma_D=w["sigma_D"], cS=w["cS"], cD=w["cD"])
+    u_fork = lp.eval(**args)
+    a_fork = np.empty((lp.n_centres, 2 * w["p"] + 1), np.complex128)
+    u_fork_all = lp.eval(alpha_out=a_fork, **args)
+    assert np.array_equal(u_fork, u_fork_all)   # used centres only vs every centre
+    lp.set_timing(True)
+    u_serial = lp.eval(**args)
+    lp.set_timing(False)
+    assert np.array_equal(u_fork, u_serial)
+    b = qbxmod.Batch([lp], n_streams=1)          # the handle is now in throughput mode
+    u_batched = lp.eval(**args)
+    a_batched = np.empty_like(a_fork)
+    lp.eval(alpha_out=a_batched, **args)
+    b.close()
+    assert np.array_equal(u_fork, u_batched)
+    assert np.array_equal(a_fork, a_batched)
+    u_after = lp.eval(**args)                     # back to the single-problem schedule
+    assert np.array_equal(u_fork, u_after)
+    lp.close()
