@@ -97,40 +97,95 @@ constexpr int kGemmBlock = 8;
 constexpr int kNarrowRows = 4;
 constexpr int kWideLevel = kGemmRows * 2 * 152;
 
+// Staged rows: x[n * stage_stride(R) + r]. Two float2 of padding per n keep
+// the row pairs 16-byte aligned and spread the staging stores over the banks.
+__host__ __device__ constexpr int stage_stride(int R) { return R + 2; }
+
+// One block of nj (1 <= nj <= kGemmBlock) terms of a tile product column:
+// (tr, ti)[r] = sum_{j < nj} tb[j] * x[j * RS + r], started from the first term.
+template <int R>
+__device__ __forceinline__ void gemm_block(const float2 (&tb)[kGemmBlock], int nj,
+                                           const float2* __restrict__ x, float (&tr)[R],
+                                           float (&ti)[R]) {
+  static_assert(R % 2 == 0, "rows are read in pairs");
+  constexpr int RS = stage_stride(R);
+#pragma unroll
+  for (int j = 0; j < kGemmBlock; ++j) {
+    if (j < nj) {
+      const float2 t = tb[j];
+      const float4* m = reinterpret_cast<const float4*>(x + j * RS);
+#pragma unroll
+      for (int r2 = 0; r2 < R / 2; ++r2) {
+        const float4 v = m[r2];  // rows 2 r2 (x, y) and 2 r2 + 1 (z, w)
+        if (j == 0) {
+          tr[2 * r2] = fmaf(t.x, v.x, -t.y * v.y);
+          ti[2 * r2] = fmaf(t.x, v.y, t.y * v.x);
+          tr[2 * r2 + 1] = fmaf(t.x, v.z, -t.y * v.w);
+          ti[2 * r2 + 1] = fmaf(t.x, v.w, t.y * v.z);
+        } else {
+          tr[2 * r2] = fmaf(t.x, v.x, fmaf(-t.y, v.y, tr[2 * r2]));
+          ti[2 * r2] = fmaf(t.x, v.y, fmaf(t.y, v.x, ti[2 * r2]));
+          tr[2 * r2 + 1] = fmaf(t.x, v.z, fmaf(-t.y, v.w, tr[2 * r2 + 1]));
+          ti[2 * r2 + 1] = fmaf(t.x, v.w, fmaf(t.y, v.z, ti[2 * r2 + 1]));
+        }
+      }
+    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void gemm_block_add(const float2 (&tb)[kGemmBlock], int nj,
+                                               const float2* __restrict__ x, float (&sr)[R],
+                                               float (&si)[R], float (&cr)[R], float (&ci)[R]) {
+  float tr[R], ti[R];
+  gemm_block<R>(tb, nj, x, tr, ti);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    kahan_add(sr[r], cr[r], tr[r]);
+    kahan_add(si[r], ci[r], ti[r]);
+  }
+}
+
 // One output column lo of a tile product: for every row r < R,
-// (sr, si)[r] += sum_{n < N} M[n * ld + lo] * x[n * R + r], with x in
-// shared memory. Plain FP32 FMAs over blocks of kGemmBlock terms (whose matrix
-// entries are loaded together), the blocks added with Kahan compensation
-// (cr, ci). Threads with act == false take part with zero entries.
+// (sr, si)[r] += sum_{n < N} M[n * ld + lo] * x[n * RS + r], with x in
+// shared memory (16-byte aligned, RS = stage_stride(R)). Plain FP32 FMAs over
+// blocks of kGemmBlock terms (whose matrix entries are loaded one block ahead,
+// into two alternating register sets), the blocks added with Kahan
+// compensation (cr, ci). Threads with act == false read column 0 and their
+// sums are not used.
 template <int R = kGemmRows>
 __device__ __forceinline__ void tile_gemm_column(const float2* __restrict__ M, size_t ld, int N,
                                                  const float2* __restrict__ x, int lo, bool act,
                                                  float (&sr)[R], float (&si)[R], float (&cr)[R],
                                                  float (&ci)[R]) {
-  for (int n0 = 0; n0 < N; n0 += kGemmBlock) {
-    float tr[R], ti[R];
+  constexpr int RS = stage_stride(R);
+  const float2* Mc = M + (act ? lo : 0);
+  const int nfull = N - N % kGemmBlock;
+  float2 ba[kGemmBlock], bb[kGemmBlock];
+  if (nfull > 0) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) tr[r] = ti[r] = 0.f;
-    float2 tb[kGemmBlock];
+    for (int j = 0; j < kGemmBlock; ++j) ba[j] = Mc[(size_t)j * ld];
+  }
+  for (int n0 = 0; n0 < nfull; n0 += 2 * kGemmBlock) {
+    const int n1 = n0 + kGemmBlock;
+    if (n1 < nfull) {
+#pragma unroll
+      for (int j = 0; j < kGemmBlock; ++j) bb[j] = Mc[(size_t)(n1 + j) * ld];
+    }
+    gemm_block_add<R>(ba, kGemmBlock, x + n0 * RS, sr, si, cr, ci);
+    if (n1 >= nfull) break;
+    if (n1 + kGemmBlock < nfull) {
+#pragma unroll
+      for (int j = 0; j < kGemmBlock; ++j) ba[j] = Mc[(size_t)(n1 + kGemmBlock + j) * ld];
+    }
+    gemm_block_add<R>(bb, kGemmBlock, x + n1 * RS, sr, si, cr, ci);
+  }
+  if (nfull < N) {  // the last, partial block
+    const int nj = N - nfull;
 #pragma unroll
     for (int j = 0; j < kGemmBlock; ++j)
-      tb[j] = (act && n0 + j < N) ? M[(size_t)(n0 + j) * ld + lo] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < kGemmBlock; ++j) {
-      if (n0 + j >= N) break;
-      const float2 t = tb[j];
-      const float2* m = x + (n0 + j) * R;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        tr[r] = fmaf(t.x, m[r].x, fmaf(-t.y, m[r].y, tr[r]));
-        ti[r] = fmaf(t.x, m[r].y, fmaf(t.y, m[r].x, ti[r]));
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      kahan_add(sr[r], cr[r], tr[r]);
-      kahan_add(si[r], ci[r], ti[r]);
-    }
+      ba[j] = j < nj ? Mc[(size_t)(nfull + j) * ld] : make_float2(0.f, 0.f);
+    gemm_block_add<R>(ba, nj, x + nfull * RS, sr, si, cr, ci);
   }
 }
 
@@ -162,31 +217,32 @@ constexpr int kChunkK = 128;
 static_assert(kChunkK % kGemmBlock == 0, "staging must keep the summation blocks");
 
 __global__ void __launch_bounds__(kT) m2l_f32_gemm_kernel(
-    const int4* __restrict__ items, const int4* __restrict__ tiles, const int* __restrict__ lpb,
-    const long long* __restrict__ tm_off, const int* __restrict__ row_src,
-    const long long* __restrict__ eoff, const float2* __restrict__ mu32,
-    const float2* __restrict__ tm, const long long* __restrict__ yoff, float2* __restrict__ Y) {
-  __shared__ float2 mu[kChunkK * kGemmRows];  // [n][row]
-  const int4 I = items[blockIdx.x];
-  const int4 T = tiles[I.x];  // (level * 49 + class, first row, rows, level)
-  const int cls = T.x % 49, row0 = T.y, nr = T.z, l = T.w;
-  const int pb = lpb[l], Q = 2 * pb + 1;
+    const int4* __restrict__ items, const int* __restrict__ lpb,
+    const long long* __restrict__ goff, const long long* __restrict__ row_off,
+    const float2* __restrict__ mu32, const float2* __restrict__ tm,
+    const long long* __restrict__ yoff, float2* __restrict__ Y) {
+  constexpr int RS = stage_stride(kGemmRows);
+  __shared__ __align__(16) float2 mu[kChunkK * RS];  // [n][row]
+  const int4 I = items[blockIdx.x];  // (first row, rows, first output order, group)
+  const int row0 = I.x, nr = I.y;
+  const int Q = 2 * lpb[I.w / 49] + 1;
   const int lo = I.z + (int)threadIdx.x;
   const bool act = lo < Q;
   // warps past the last output order only help stage the sources: an FMA
   // costs its warp the same however few lanes are active
   const bool warp_act = I.z + (int)(threadIdx.x & ~31u) < Q;
-  const float2* M = tm + tm_off[l] + (size_t)cls * Q * Q;
+  const float2* M = tm + goff[I.w];
   float sr[kGemmRows], si[kGemmRows], cr[kGemmRows], ci[kGemmRows];
 #pragma unroll
   for (int r = 0; r < kGemmRows; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
   for (int n0 = 0; n0 < Q; n0 += kChunkK) {
     const int nk = min(kChunkK, Q - n0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nk * kGemmRows; idx += kT) {
-      const int r = idx / nk, n = idx % nk;  // coalesced reads along each source row
-      mu[n * kGemmRows + r] =
-          r < nr ? mu32[eoff[row_src[row0 + r]] + n0 + n] : make_float2(0.f, 0.f);
+    for (int idx = threadIdx.x; idx < nk * (kGemmRows / 2); idx += kT) {
+      const int r = 2 * (idx / nk), n = idx % nk;  // coalesced reads along each source row
+      const float2 a = r < nr ? mu32[row_off[row0 + r] + n0 + n] : make_float2(0.f, 0.f);
+      const float2 b = r + 1 < nr ? mu32[row_off[row0 + r + 1] + n0 + n] : make_float2(0.f, 0.f);
+      *reinterpret_cast<float4*>(mu + n * RS + r) = make_float4(a.x, a.y, b.x, b.y);
     }
     __syncthreads();
     if (warp_act) tile_gemm_column(M + (size_t)n0 * Q, Q, nk, mu, lo, act, sr, si, cr, ci);
@@ -201,9 +257,9 @@ __global__ void __launch_bounds__(kT) m2l_f32_gemm_kernel(
 // lh_lo(b) += conv_lo * sum over b's V entries e (in list order) of Y[row(e)][lo], in FP64.
 __global__ void __launch_bounds__(kT) m2l_f32_reduce_kernel(
     int pbmax, const int* __restrict__ boxes, const int* __restrict__ level,
-    const int* __restrict__ lpb, const int* __restrict__ voff, const int* __restrict__ vrow,
-    const long long* __restrict__ yoff, const float2* __restrict__ Y,
-    const double* __restrict__ conv, const long long* __restrict__ eoff, cd* __restrict__ local) {
+    const int* __restrict__ lpb, const int* __restrict__ voff, const long long* __restrict__ eyoff,
+    const float2* __restrict__ Y, const double* __restrict__ conv,
+    const long long* __restrict__ eoff, cd* __restrict__ local) {
   const int b = boxes[blockIdx.x];
   const int l = level[b];
   const int pb = lpb[l], Q = 2 * pb + 1;
@@ -211,8 +267,20 @@ __global__ void __launch_bounds__(kT) m2l_f32_reduce_kernel(
   cd* dst = local + eoff[b];
   for (int lo = threadIdx.x; lo < Q; lo += kT) {
     cd sum = mk(0.0, 0.0);
-    for (int e = voff[b]; e < voff[b + 1]; ++e) {
-      const float2 y = Y[yoff[vrow[e]] + lo];
+    const int e1 = voff[b + 1];
+    int e = voff[b];
+    for (; e + 4 <= e1; e += 4) {  // four loads in flight, added in list order
+      float2 y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[u] = Y[eyoff[e + u] + lo];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sum.x += (double)y[u].x;
+        sum.y += (double)y[u].y;
+      }
+    }
+    for (; e < e1; ++e) {
+      const float2 y = Y[eyoff[e] + lo];
       sum.x += (double)y.x;
       sum.y += (double)y.y;
     }
@@ -253,19 +321,18 @@ __global__ void m2l_f64_matrix_kernel(int l, int pb, int pbmax, const cd* __rest
 // m2l_f64_reduce_kernel in V-list order.
 constexpr int kF64Rows = 8;
 __global__ void __launch_bounds__(kT) m2l_f64_gemm_kernel(
-    const int4* __restrict__ items, const int4* __restrict__ tiles, const int* __restrict__ lpb,
-    const long long* __restrict__ tm_off, const int* __restrict__ row_src,
-    const long long* __restrict__ eoff, const cd* __restrict__ mpole,
-    const cd* __restrict__ tm, const long long* __restrict__ yoff, cd* __restrict__ Y) {
-  __shared__ cd xs[kChunkK * kF64Rows];  // [n][row]
-  const int4 I = items[blockIdx.x];
-  const int4 T = tiles[I.x];
-  const int cls = T.x % 49, row0 = T.y + I.y, nr = min(kF64Rows, T.z - I.y), l = T.w;
-  const int pb = lpb[l], Q = 2 * pb + 1;
+    const int4* __restrict__ items, const int* __restrict__ lpb,
+    const long long* __restrict__ goff, const long long* __restrict__ row_off,
+    const cd* __restrict__ mpole, const cd* __restrict__ tm,
+    const long long* __restrict__ yoff, cd* __restrict__ Y) {
+  __shared__ __align__(16) cd xs[kChunkK * kF64Rows];  // [n][row]
+  const int4 I = items[blockIdx.x];  // (first row, rows <= kF64Rows, first output order, group)
+  const int row0 = I.x, nr = I.y;
+  const int Q = 2 * lpb[I.w / 49] + 1;
   const int lo = I.z + (int)threadIdx.x;
   const bool act = lo < Q;
   const bool warp_act = I.z + (int)(threadIdx.x & ~31u) < Q;  // as in the FP32 items
-  const cd* M = tm + tm_off[l] + (size_t)cls * Q * Q;
+  const cd* M = tm + goff[I.w];
   cd acc[kF64Rows];
 #pragma unroll
   for (int r = 0; r < kF64Rows; ++r) acc[r] = mk(0.0, 0.0);
@@ -274,7 +341,7 @@ __global__ void __launch_bounds__(kT) m2l_f64_gemm_kernel(
     __syncthreads();
     for (int idx = threadIdx.x; idx < nk * kF64Rows; idx += kT) {
       const int r = idx / nk, n = idx % nk;
-      xs[n * kF64Rows + r] = r < nr ? mpole[eoff[row_src[row0 + r]] + n0 + n] : mk(0.0, 0.0);
+      xs[n * kF64Rows + r] = r < nr ? mpole[row_off[row0 + r] + n0 + n] : mk(0.0, 0.0);
     }
     __syncthreads();
     if (!warp_act) continue;
@@ -302,14 +369,23 @@ __global__ void __launch_bounds__(kT) m2l_f64_gemm_kernel(
 // lh_lo(b) += sum over b's V entries e (in list order) of Y64[row(e)][lo].
 __global__ void __launch_bounds__(kT) m2l_f64_reduce_kernel(
     const int* __restrict__ boxes, const int* __restrict__ level, const int* __restrict__ lpb,
-    const int* __restrict__ voff, const int* __restrict__ vrow, const long long* __restrict__ yoff,
-    const cd* __restrict__ Y, const long long* __restrict__ eoff, cd* __restrict__ local) {
+    const int* __restrict__ voff, const long long* __restrict__ eyoff, const cd* __restrict__ Y,
+    const long long* __restrict__ eoff, cd* __restrict__ local) {
   const int b = boxes[blockIdx.x];
   const int Q = 2 * lpb[level[b]] + 1;
   cd* dst = local + eoff[b];
   for (int lo = threadIdx.x; lo < Q; lo += kT) {
     cd sum = mk(0.0, 0.0);
-    for (int e = voff[b]; e < voff[b + 1]; ++e) sum = cadd(sum, Y[yoff[vrow[e]] + lo]);
+    const int e1 = voff[b + 1];
+    int e = voff[b];
+    for (; e + 4 <= e1; e += 4) {  // four loads in flight, added in list order
+      cd y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[u] = Y[eyoff[e + u] + lo];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sum = cadd(sum, y[u]);
+    }
+    for (; e < e1; ++e) sum = cadd(sum, Y[eyoff[e] + lo]);
     dst[lo] = cadd(dst[lo], sum);
   }
 }
@@ -350,7 +426,7 @@ __global__ void __launch_bounds__(kT) l2l_f32_kernel(
     int l, int pp, int pc, int pbmax, const int* __restrict__ parents, int nb,
     const int* __restrict__ child, const long long* __restrict__ eoff,
     const float2* __restrict__ Tl, const double* __restrict__ conv, cd* __restrict__ local) {
-  extern __shared__ float2 lam[];  // [Qp][R]
+  extern __shared__ __align__(16) float2 lam[];  // [Qp][stage_stride(R)]
   const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
   const int p0 = blockIdx.x * R, nr = min(R, nb - p0);
   const double* cvp = conv + (size_t)l * (pbmax + 1);
@@ -363,7 +439,7 @@ __global__ void __launch_bounds__(kT) l2l_f32_kernel(
       const double f = 1.0 / cvp[abs(n - pp)];
       v = make_float2((float)(g.x * f), (float)(g.y * f));
     }
-    lam[n * R + r] = v;
+    lam[n * stage_stride(R) + r] = v;
   }
   __syncthreads();
   {
@@ -426,11 +502,25 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
     int l, int pp, int pc, int pbmax, const int* __restrict__ parents, int nb,
     const int* __restrict__ child, const long long* __restrict__ eoff,
     const float2* __restrict__ Tmm, const double* __restrict__ conv, cd* __restrict__ mpole) {
-  extern __shared__ float2 mus[];  // [Qc][R]
+  extern __shared__ __align__(16) float2 mus[];  // [Qc][stage_stride(R)]
+  __shared__ long long coff[4][R], poff[R];       // children's (-1: none) and parents' offsets
   const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
   const int p0 = blockIdx.x * R, nr = min(R, nb - p0);
   const double* cvp = conv + (size_t)l * (pbmax + 1);
   const double* cvc = conv + (size_t)(l + 1) * (pbmax + 1);
+  for (int idx = threadIdx.x; idx < 5 * R; idx += kT) {
+    const int r = idx % R, c = idx / R;
+    long long o = -1;
+    if (r < nr) {
+      if (c == 4) {
+        o = eoff[parents[p0 + r]];
+      } else {
+        const int d = child[4 * parents[p0 + r] + c];
+        if (d >= 0) o = eoff[d];
+      }
+    }
+    if (c == 4) poff[r] = o; else coff[c][r] = o;
+  }
   for (int so0 = 0; so0 < Qp; so0 += kT) {
     const int so = so0 + threadIdx.x;
     const bool act = so < Qp;
@@ -442,15 +532,13 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
       for (int idx = threadIdx.x; idx < Qc * R; idx += kT) {
         const int r = idx / Qc, n = idx % Qc;
         float2 v = make_float2(0.f, 0.f);
-        if (r < nr) {
-          const int d = child[4 * parents[p0 + r] + c];
-          if (d >= 0) {
-            const cd a = mpole[eoff[d] + n];
-            const double f = cvc[abs(n - pc)];
-            v = make_float2((float)(a.x * f), (float)(a.y * f));
-          }
+        const long long o = coff[c][r];
+        if (o >= 0) {
+          const cd a = mpole[o + n];
+          const double f = cvc[abs(n - pc)];
+          v = make_float2((float)(a.x * f), (float)(a.y * f));
         }
-        mus[n * R + r] = v;
+        mus[n * stage_stride(R) + r] = v;
       }
       __syncthreads();
       tile_gemm_column<R>(Tmm + (size_t)c * Qc * Qp, Qp, Qc, mus, so, act, sr, si, cr, ci);
@@ -460,7 +548,7 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (r >= nr) break;
-        cd* dst = mpole + eoff[parents[p0 + r]] + so;
+        cd* dst = mpole + poff[r] + so;
         dst->x = ((double)sr[r] - (double)cr[r]) * f;
         dst->y = ((double)si[r] - (double)ci[r]) * f;
       }
@@ -468,13 +556,24 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
   }
 }
 
+// out[i] = eoff[idx[i]]: the coefficient offset of each M2L source row
+__global__ void gather_offsets_kernel(const int* __restrict__ idx, const long long* __restrict__ eoff,
+                                      long long* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = eoff[idx[i]];
+}
+
 }  // namespace
 
 qbx_status configure_mixed_kernels(int smem_optin) {
   const void* k[] = {(const void*)l2l_f32_kernel<kGemmRows>, (const void*)l2l_f32_kernel<kNarrowRows>,
                      (const void*)m2m_f32_kernel<kGemmRows>, (const void*)m2m_f32_kernel<kNarrowRows>};
-  for (const void* fn : k)
-    QBX_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+  for (const void* fn : k) {
+    cudaFuncAttributes a;
+    QBX_CUDA_TRY(cudaFuncGetAttributes(&a, fn));  // dynamic + static must fit the opt-in size
+    QBX_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem_optin - (int)a.sharedSizeBytes));
+  }
   return QBX_OK;
 }
 
@@ -496,9 +595,6 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
     }
   }
   QBX_CUDA_TRY(f->tm_f32.alloc(std::max<long long>(1, tot)));
-  QBX_CUDA_TRY(f->tm_off.alloc(f->n_levels));
-  QBX_CUDA_TRY(cudaMemcpy(f->tm_off.ptr, off.data(), off.size() * sizeof(long long),
-                          cudaMemcpyHostToDevice));
   f->h_tm_off = off;
   for (int l = 2; l < f->n_levels; ++l) {
     if (f->vbox_off[l + 1] == f->vbox_off[l]) continue;
@@ -550,16 +646,26 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
       for (int64_t r = gcount[g]; r < gcount[g + 1]; r += kGemmRows)
         tiles.push_back(make_int4(g, (int)r, (int)std::min<int64_t>(kGemmRows, gcount[g + 1] - r), l));
     }
-    // coarse levels (largest orders) first; work items per tile: row groups x
-    // chunks of kT output orders
+    // coarse levels (largest orders) first; work items (first row, rows,
+    // first output order, group) per tile: chunks of kT output orders, and
+    // for FP64 also groups of kF64Rows rows
     std::vector<int4> it32, it64;
-    for (size_t t = 0; t < tiles.size(); ++t) {
-      const int Q = 2 * f->h_pb[tiles[t].w] + 1;
+    for (const int4& t : tiles) {
+      const int Q = 2 * f->h_pb[t.w] + 1;
       for (int c0 = 0; c0 < Q; c0 += kT) {
-        it32.push_back(make_int4((int)t, 0, c0, 0));
-        for (int r0 = 0; r0 < tiles[t].z; r0 += kF64Rows) it64.push_back(make_int4((int)t, r0, c0, 0));
+        it32.push_back(make_int4(t.y, t.z, c0, t.x));
+        for (int r0 = 0; r0 < t.z; r0 += kF64Rows)
+          it64.push_back(make_int4(t.y + r0, std::min(kF64Rows, t.z - r0), c0, t.x));
       }
     }
+    // matrix offset of each group (level l, class c): level offset + c Q_l^2
+    std::vector<long long> goff(ng, 0);
+    for (int g = 0; g < ng; ++g) {
+      const long long Q = 2 * f->h_pb[g / 49] + 1;
+      goff[g] = off[g / 49] + (long long)(g % 49) * Q * Q;
+    }
+    QBX_CUDA_TRY(f->m2l_goff.alloc(ng));
+    QBX_CUDA_TRY(cudaMemcpy(f->m2l_goff.ptr, goff.data(), ng * sizeof(long long), cudaMemcpyHostToDevice));
     f->n_m2l_items32 = (int)it32.size();
     f->n_m2l_items64 = (int)it64.size();
     QBX_CUDA_TRY(f->m2l_items32.alloc(std::max<size_t>(1, it32.size())));
@@ -568,14 +674,9 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
       QBX_CUDA_TRY(cudaMemcpy(f->m2l_items32.ptr, it32.data(), it32.size() * sizeof(int4), cudaMemcpyHostToDevice));
       QBX_CUDA_TRY(cudaMemcpy(f->m2l_items64.ptr, it64.data(), it64.size() * sizeof(int4), cudaMemcpyHostToDevice));
     }
-    f->n_m2l_tiles = (int)tiles.size();
-    QBX_CUDA_TRY(f->m2l_tiles.alloc(std::max<size_t>(1, tiles.size())));
-    QBX_CUDA_TRY(f->m2l_vrow.alloc(vrow.size()));
-    QBX_CUDA_TRY(f->m2l_rowsrc.alloc(row_src.size()));
+    QBX_CUDA_TRY(f->m2l_eyoff.alloc(vrow.size()));
     QBX_CUDA_TRY(f->m2l_yoff.alloc(yoff.size()));
     QBX_CUDA_TRY(f->m2l_y.alloc(std::max<long long>(1, ytot)));
-    if (!tiles.empty())
-      QBX_CUDA_TRY(cudaMemcpy(f->m2l_tiles.ptr, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
     // the boxes that are V-list sources, and FP32 room for their multipoles
     std::vector<char> is_src(nb, 0);
     for (int64_t e = 0; e < nv; ++e) is_src[vidx[e]] = 1;
@@ -587,8 +688,22 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
     if (!vsrc.empty())
       QBX_CUDA_TRY(cudaMemcpy(f->m2l_vsrc.ptr, vsrc.data(), vsrc.size() * sizeof(int), cudaMemcpyHostToDevice));
     QBX_CUDA_TRY(f->mu32.alloc(std::max<int64_t>(1, f->n_coef)));
-    QBX_CUDA_TRY(cudaMemcpy(f->m2l_vrow.ptr, vrow.data(), vrow.size() * sizeof(int), cudaMemcpyHostToDevice));
-    QBX_CUDA_TRY(cudaMemcpy(f->m2l_rowsrc.ptr, row_src.data(), row_src.size() * sizeof(int), cudaMemcpyHostToDevice));
+    {  // result-row offset of every V entry
+      std::vector<long long> eyoff(vrow.size(), 0);
+      for (int64_t e = 0; e < nv; ++e) eyoff[e] = yoff[vrow[e]];
+      QBX_CUDA_TRY(cudaMemcpy(f->m2l_eyoff.ptr, eyoff.data(), eyoff.size() * sizeof(long long),
+                              cudaMemcpyHostToDevice));
+    }
+    {  // coefficient offset of each row's source box
+      DevBuf<int> rs;
+      QBX_CUDA_TRY(rs.alloc(row_src.size()));
+      QBX_CUDA_TRY(cudaMemcpy(rs.ptr, row_src.data(), row_src.size() * sizeof(int), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(f->m2l_rowoff.alloc(row_src.size()));
+      gather_offsets_kernel<<<nblk((int64_t)row_src.size(), 256), 256>>>(rs.ptr, f->eoff.ptr,
+                                                                          f->m2l_rowoff.ptr, (int64_t)row_src.size());
+      QBX_CUDA_TRY(cudaGetLastError());
+      QBX_CUDA_TRY(cudaDeviceSynchronize());  // before rs is freed
+    }
     QBX_CUDA_TRY(cudaMemcpy(f->m2l_yoff.ptr, yoff.data(), yoff.size() * sizeof(long long), cudaMemcpyHostToDevice));
   }
   // FP64 M2L matrices (same offsets as the FP32 ones) and result rows
@@ -638,16 +753,19 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
   return QBX_OK;
 }
 
-size_t gemm_smem_bytes(int pb) { return (size_t)(2 * pb + 1) * kGemmRows * sizeof(float2); }
+size_t gemm_smem_bytes(int pb) {
+  return (size_t)(2 * pb + 1) * stage_stride(kGemmRows) * sizeof(float2) +
+         5 * kGemmRows * sizeof(long long);
+}
 
 qbx_status launch_m2l_f64(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
-  if (f->n_vbox == 0 || f->n_m2l_tiles == 0) return QBX_OK;
+  if (f->n_vbox == 0 || f->n_m2l_items64 == 0) return QBX_OK;
   m2l_f64_gemm_kernel<<<f->n_m2l_items64, kT, 0, s>>>(
-      f->m2l_items64.ptr, f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr, f->mpole.ptr,
+      f->m2l_items64.ptr, f->lpb.ptr, f->m2l_goff.ptr, f->m2l_rowoff.ptr, f->mpole.ptr,
       f->tm_f64.ptr, f->m2l_yoff.ptr, f->m2l_y64.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   m2l_f64_reduce_kernel<<<f->n_vbox, kT, 0, s>>>(
-      f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->V.off.ptr, f->m2l_vrow.ptr, f->m2l_yoff.ptr,
+      f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->V.off.ptr, f->m2l_eyoff.ptr,
       f->m2l_y64.ptr, f->eoff.ptr, f->local.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   h->launches += 2;
@@ -662,10 +780,10 @@ qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
     const float2* T = f->tmm_f32.ptr + f->h_tmm_off[l];
     if (nb >= kWideLevel || h->batched)
-      m2m_f32_kernel<kGemmRows><<<nblk(nb, kGemmRows), kT, (size_t)(2 * pc + 1) * kGemmRows * sizeof(float2), s>>>(
+      m2m_f32_kernel<kGemmRows><<<nblk(nb, kGemmRows), kT, (size_t)(2 * pc + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
     else
-      m2m_f32_kernel<kNarrowRows><<<nblk(nb, kNarrowRows), kT, (size_t)(2 * pc + 1) * kNarrowRows * sizeof(float2), s>>>(
+      m2m_f32_kernel<kNarrowRows><<<nblk(nb, kNarrowRows), kT, (size_t)(2 * pc + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;
@@ -681,10 +799,10 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
     const float2* T = f->tl_f32.ptr + f->h_tl_off[l];
     if (nb >= kWideLevel || h->batched)
-      l2l_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), 4), kT, (size_t)(2 * pp + 1) * kGemmRows * sizeof(float2), s>>>(
+      l2l_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), 4), kT, (size_t)(2 * pp + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
     else
-      l2l_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), 4), kT, (size_t)(2 * pp + 1) * kNarrowRows * sizeof(float2), s>>>(
+      l2l_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), 4), kT, (size_t)(2 * pp + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;
@@ -693,7 +811,7 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
 }
 
 qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
-  if (f->n_vbox == 0 || f->n_m2l_tiles == 0) return QBX_OK;
+  if (f->n_vbox == 0 || f->n_m2l_items32 == 0) return QBX_OK;
   if (f->n_vsrc > 0) {
     mpole_to_f32_kernel<<<f->n_vsrc, kT, 0, s>>>(f->pb_max, f->m2l_vsrc.ptr, f->box.level.ptr,
                                                  f->lpb.ptr, f->eoff.ptr, f->conv.ptr,
@@ -702,12 +820,12 @@ qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     h->launches += 1;
   }
   m2l_f32_gemm_kernel<<<f->n_m2l_items32, kT, 0, s>>>(
-      f->m2l_items32.ptr, f->m2l_tiles.ptr, f->lpb.ptr, f->tm_off.ptr, f->m2l_rowsrc.ptr, f->eoff.ptr, f->mu32.ptr,
+      f->m2l_items32.ptr, f->lpb.ptr, f->m2l_goff.ptr, f->m2l_rowoff.ptr, f->mu32.ptr,
       f->tm_f32.ptr, f->m2l_yoff.ptr, f->m2l_y.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   m2l_f32_reduce_kernel<<<f->n_vbox, kT, 0, s>>>(
-      f->pb_max, f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->V.off.ptr, f->m2l_vrow.ptr,
-      f->m2l_yoff.ptr, f->m2l_y.ptr, f->conv.ptr, f->eoff.ptr, f->local.ptr);
+      f->pb_max, f->vbox.ptr, f->box.level.ptr, f->lpb.ptr, f->V.off.ptr, f->m2l_eyoff.ptr,
+      f->m2l_y.ptr, f->conv.ptr, f->eoff.ptr, f->local.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   h->launches += 2;
   return QBX_OK;

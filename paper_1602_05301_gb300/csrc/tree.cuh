@@ -100,19 +100,18 @@ struct FmmPlan {
   // mixed precision (sigma-normalised FP32 M2L)
   DevBuf<double> lsig, conv;            // [n_levels][pb_max+1] log sig_j, s^j / sig_j
   DevBuf<float2> tm_f32;                // per level l >= 2: [49][Q_l][Q_l] M2L matrices
-  DevBuf<long long> tm_off;             // [n_levels] offset of level l's matrices
-  std::vector<long long> h_tm_off;
-  // M2L as batched GEMMs: tiles (group, first row, rows, level), the row of
-  // every V entry, the source box of every row, row offsets into the FP32
-  // result buffer
-  DevBuf<int4> m2l_tiles;
-  int n_m2l_tiles = 0;
-  DevBuf<int4> m2l_items32, m2l_items64;  // (tile, first row, first output order)
+  std::vector<long long> h_tm_off;      // [n_levels] offset of level l's matrices
+  // M2L as batched GEMMs: V entries grouped by (level, offset class) into
+  // rows; work items over tiles of rows, row offsets into the result
+  // buffers, and the result row of every V entry
+  DevBuf<long long> m2l_goff;           // [n_levels * 49] matrix offset per (level, class)
+  DevBuf<int4> m2l_items32, m2l_items64;  // (first row, rows, first output order, group)
   int n_m2l_items32 = 0, n_m2l_items64 = 0;
-  DevBuf<int> m2l_vrow, m2l_rowsrc;
+  DevBuf<long long> m2l_eyoff;          // result-row offset of every V entry
+  DevBuf<long long> m2l_rowoff;         // coefficient offset of each row's source box
   DevBuf<long long> m2l_yoff;
   DevBuf<float2> m2l_y;
-  DevBuf<cd> tm_f64;                    // FP64 M2L matrices (offsets tm_off, as the FP32 ones)
+  DevBuf<cd> tm_f64;                    // FP64 M2L matrices (same offsets as the FP32 ones)
   DevBuf<cd> m2l_y64;                   // FP64 result rows of the FP64 M2L GEMM
   DevBuf<int> m2l_vsrc;                 // boxes that are V-list sources
   int n_vsrc = 0;
