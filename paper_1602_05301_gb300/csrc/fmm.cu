@@ -240,10 +240,11 @@ __global__ void gather_strengths_kernel(int64_t n, const int* __restrict__ perm,
 __host__ __device__ inline size_t rows_smem(int pb, int chunk) {
   return ((size_t)(2 * pb + 1) + (size_t)chunk * (2 * pb + 6)) * sizeof(cd);
 }
-__device__ inline int rows_chunk(int pb, size_t sm_bytes) {
+__host__ __device__ inline int rows_chunk(int pb, size_t sm_bytes) {
   const size_t per = (size_t)(2 * pb + 6) * sizeof(cd);
   const size_t avail = sm_bytes - (size_t)(2 * pb + 1) * sizeof(cd);
-  return (int)min((size_t)kChunk, avail / per);
+  const size_t c = avail / per;
+  return (int)(c < (size_t)kChunk ? c : (size_t)kChunk);
 }
 
 // CTA per leaf. Threads 0..chunk-1 fill one row each with
@@ -359,74 +360,92 @@ __global__ void __launch_bounds__(kThreads) m2m_kernel(Fmm F, const int* __restr
 // matrices (mixed.cu).
 
 // ---------------------------------------------------------------- P2L (Stage 6)
-// CTA per box with an X list: lh_l += s^|l| sum_j [q W_l + d (k/2)(nu W_{l-1} - conj(nu) W_{l+1})]
-__global__ void __launch_bounds__(kThreads) p2l_kernel(Fmm F, const int* __restrict__ boxes,
-                                                       unsigned sm_bytes) {
+// lh_n += s^|n| sum_j [q_j W_n + d_j (k/2)(nu_j W_{n-1} - conj(nu_j) W_{n+1})](y_j - m_b)
+// over the sources of the boxes in b's X list. Work items: up to one row chunk
+// of an X box's sources (its X list's leaves, concatenated in list order), so
+// that a box's work spreads over several CTAs and every chunk is full. One
+// warp fills a row per source with Wh_t = s^|t| W_t, |t| <= pb + 1; then all
+// threads form the item's part of lh_n (the charge and the two dipole terms in
+// separate sums, scaled once) into partial[poff[item] + n + pb], and
+// p2l_sum_kernel adds each box's items in order.
+__global__ void __launch_bounds__(kThreads) p2l_item_kernel(Fmm F, const int4* __restrict__ items,
+                                                            const int* __restrict__ src,
+                                                            const long long* __restrict__ poff,
+                                                            cd* __restrict__ partial,
+                                                            unsigned sm_bytes) {
   extern __shared__ cd smem[];
-  const int b = boxes[blockIdx.x];
+  const int4 it = items[blockIdx.x];  // (box, first position in src, sources, -)
+  const int b = it.x, cnt = it.z;
   const int l = F.level[b];
-  const int pb = F.lpb[l], Q = 2 * pb + 1, RW = 2 * pb + 3;  // row: Wh_t, |t| <= pb+1
-  const int chunk = rows_chunk(pb, sm_bytes);
-  cd* acc = smem;                         // [Q]
-  cd* rows = acc + Q;                     // [chunk][RW]
+  const int pb = F.lpb[l], RW = 2 * pb + 3;  // row: Wh_t, |t| <= pb+1
+  const int chunk = rows_chunk(pb, sm_bytes);  // >= cnt (items are cut to fit)
+  cd* rows = smem;                        // [chunk][RW]
   cd* sq = rows + chunk * RW;             // [chunk]
   cd* sa = sq + chunk;                    // [chunk]  A = d (k/2) nu
   cd* sb = sa + chunk;                    // [chunk]  B = d (k/2) conj(nu)
   const double s = F.scale[l], is = 1.0 / s;
   const double2 m = F.centre[b];
   const double hk = 0.5 * F.k;
-  for (int i = threadIdx.x; i < Q; i += kThreads) acc[i] = mk(0.0, 0.0);
-  for (int e = F.xoff[b]; e < F.xoff[b + 1]; ++e) {
-    const int2 r = F.rsrc[F.xidx[e]];
-    for (int base = r.x; base < r.y; base += chunk) {
-      const int cnt = min(chunk, r.y - base);
-      if ((int)threadIdx.x < cnt) {
-        const int i = base + threadIdx.x;
-        const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
-        const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-        const cd e1 = mk(dx / rr, dy / rr);
-        cd h0, h1;
-        hankel01(x, h0, h1);
-        cd* row = rows + threadIdx.x * RW + (pb + 1);   // row[t], t = -(pb+1)..pb+1
-        cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
-        row[0] = h0;
-        for (int j = 1; j <= pb + 1; ++j) {
-          ee = cmul(ee, e1);
-          row[j] = cmul(hm, ee);                                  // s^j W_j
-          const cd v = cmul(hm, cconj(ee));
-          row[-j] = (j & 1) ? mk(-v.x, -v.y) : v;                 // s^j W_{-j}
-          const cd hn = csub(cscale(hm, 2.0 * j * s / x), cscale(hm1, s * s));
-          hm1 = hm;
-          hm = hn;
-        }
-        const cd dk = cscale(F.ds[i], hk);
-        const cd nu = mk(F.snrm[i].x, F.snrm[i].y);
-        sq[threadIdx.x] = F.qs[i];
-        sa[threadIdx.x] = cmul(dk, nu);
-        sb[threadIdx.x] = cmul(dk, cconj(nu));
-      }
-      __syncthreads();
-      for (int n = (int)threadIdx.x - pb; n <= pb; n += kThreads) {
-        const int an = abs(n);
-        // s^|n| W_{n-1} = Wh_{n-1} s^{|n| - |n-1|}, s^|n| W_{n+1} = Wh_{n+1} s^{|n| - |n+1|}
-        const double fm = (abs(n - 1) > an) ? is : s;
-        const double fp = (abs(n + 1) > an) ? is : s;
-        cd a = acc[n + pb];
-        for (int j = 0; j < cnt; ++j) {
-          const cd* row = rows + j * RW + (pb + 1);
-          if (F.has_S) cfma(a, sq[j], row[n]);
-          if (F.has_D) {
-            cfma(a, cscale(sa[j], fm), row[n - 1]);
-            cfma(a, cscale(sb[j], -fp), row[n + 1]);
-          }
-        }
-        acc[n + pb] = a;
-      }
-      __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    const int i = src[it.y + threadIdx.x];
+    const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
+    const double rr = sqrt(dx * dx + dy * dy), irr = 1.0 / rr;
+    const double x = F.k * rr, ix = 1.0 / x;
+    const cd e1 = mk(dx * irr, dy * irr);
+    cd h0, h1;
+    hankel01(x, ix, h0, h1);
+    const double c1 = 2.0 * s * ix, s2 = s * s;  // Wh_{j+1} = j c1 Wh_j - s2 Wh_{j-1}
+    cd* row = rows + threadIdx.x * RW + (pb + 1);   // row[t], t = -(pb+1)..pb+1
+    cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
+    row[0] = h0;
+    for (int j = 1; j <= pb + 1; ++j) {
+      ee = cmul(ee, e1);
+      const double ac = hm.x * ee.x, bd = hm.y * ee.y, ad = hm.x * ee.y, bc = hm.y * ee.x;
+      row[j] = mk(ac - bd, ad + bc);                                       // s^j W_j
+      row[-j] = (j & 1) ? mk(-(ac + bd), ad - bc) : mk(ac + bd, bc - ad);  // s^j W_{-j}
+      const cd hn = csub(cscale(hm, j * c1), cscale(hm1, s2));
+      hm1 = hm;
+      hm = hn;
     }
+    const cd dk = cscale(F.ds[i], hk);
+    const cd nu = mk(F.snrm[i].x, F.snrm[i].y);
+    sq[threadIdx.x] = F.qs[i];
+    sa[threadIdx.x] = cmul(dk, nu);
+    sb[threadIdx.x] = cmul(dk, cconj(nu));
   }
+  __syncthreads();
+  cd* dst = partial + poff[blockIdx.x] + pb;
+  for (int n = (int)threadIdx.x - pb; n <= pb; n += kThreads) {
+    const int an = abs(n);
+    // s^|n| W_{n-1} = Wh_{n-1} s^{|n| - |n-1|}, s^|n| W_{n+1} = Wh_{n+1} s^{|n| - |n+1|}
+    const double fm = (abs(n - 1) > an) ? is : s;
+    const double fp = (abs(n + 1) > an) ? is : s;
+    cd aq = mk(0.0, 0.0), aa = mk(0.0, 0.0), ab = mk(0.0, 0.0);
+    for (int j = 0; j < cnt; ++j) {
+      const cd* row = rows + j * RW + (pb + 1);
+      if (F.has_S) cfma(aq, sq[j], row[n]);
+      if (F.has_D) {
+        cfma(aa, sa[j], row[n - 1]);
+        cfma(ab, sb[j], row[n + 1]);
+      }
+    }
+    dst[n] = cadd(aq, csub(cscale(aa, fm), cscale(ab, fp)));
+  }
+}
+
+// lh(xbox[t]) += its items' partial coefficients, in item order.
+__global__ void __launch_bounds__(kThreads) p2l_sum_kernel(Fmm F, const int* __restrict__ xbox,
+                                                           const int* __restrict__ boff,
+                                                           const long long* __restrict__ poff,
+                                                           const cd* __restrict__ partial) {
+  const int t = blockIdx.x, b = xbox[t];
+  const int pb = F.lpb[F.level[b]], Q = 2 * pb + 1;
   cd* dst = F.local + F.eoff[b];
-  for (int i = threadIdx.x; i < Q; i += kThreads) dst[i] = cadd(dst[i], acc[i]);
+  for (int n = threadIdx.x; n < Q; n += kThreads) {
+    cd sum = mk(0.0, 0.0);
+    for (int it = boff[t]; it < boff[t + 1]; ++it) sum = cadd(sum, partial[poff[it] + n]);
+    dst[n] = cadd(dst[n], sum);
+  }
 }
 
 // ---------------------------------------------------------------- L2L (Stage 7)
@@ -873,9 +892,15 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
 // for the (centre, W-list box) pairs whose box is far enough from the centre's
 // disk for the multipole series to converge on it ((R_c + r_z) <= kW |z - m_c|;
 // the others are summed source by source with the U list in P2QBXL). Each pair
-// is split over kM2qbxlSplit threads by output order; each writes its orders of
-// partial[pair][2p+1], and m2qbxl_sum_kernel adds each centre's pairs in order.
-constexpr int kM2qbxlSplit = 4;
+// is split over ceil((2p+1) / kM2qbxlOrders) threads, each with kM2qbxlOrders
+// consecutive output orders; each writes its orders of partial[pair][2p+1],
+// and m2qbxl_sum_kernel adds each centre's pairs in order. Threads walk
+// m = |n + l| upwards with the Hankel recurrence; once m > p every term of
+// output l has the same power factor (s^-l for n + l = m, s^l for n + l = -m),
+// so those terms go to two plain sums scaled once at the end. One warp per
+// block spreads the pairs over all SMs (the FP64 pipe is per SM).
+constexpr int kM2qbxlOrders = 4;
+constexpr int kM2qbxlBlock = 32;
 // Centre count from which L2QBXL runs a thread (not a warp) per centre: enough
 // threads for about eight resident warps on each of the 152 SMs.
 constexpr int kL2qbxlThreadMin = 152 * 8 * 32;
@@ -883,18 +908,15 @@ template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int* __restrict__ pair_ctr,
                                                                const int* __restrict__ pair_box,
                                                                int n_pairs, cd* __restrict__ partial) {
-  constexpr int LC = (2 * PM + 1 + kM2qbxlSplit - 1) / kM2qbxlSplit;  // orders per thread
+  constexpr int LC = kM2qbxlOrders;
+  const int p = F.p, P = 2 * p + 1;
+  const int nparts = (P + LC - 1) / LC;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = g / kM2qbxlSplit, part = g % kM2qbxlSplit;
+  const int t = g / nparts, part = g % nparts;
   if (t >= n_pairs) return;
   const int i = pair_ctr[t], c = pair_box[t];
-  const int p = F.p, P = 2 * p + 1;
-  const int lo0 = -p + part * LC;  // first output order of this thread
-  if (lo0 > p) return;
+  const int lo0 = -p + part * LC;  // first output order of this thread (<= p)
   const double k = F.k;
-  cd acc[LC];
-#pragma unroll
-  for (int j = 0; j < LC; ++j) acc[j] = mk(0.0, 0.0);
   const int lc = F.level[c];
   const double s = F.scale[lc];
   const int pb = F.lpb[lc], M = pb + p;
@@ -905,44 +927,66 @@ __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int*
   const double2 mc = F.centre[c];
   const double dx = z.x - mc.x, dy = z.y - mc.y;
   const double rr = sqrt(dx * dx + dy * dy);
-  const double x = k * rr;
+  const double x = k * rr, ix = 1.0 / x;
   const cd e1 = mk(dx / rr, dy / rr);
   cd h0, h1;
-  hankel01(x, h0, h1);
+  hankel01(x, ix, h0, h1);
+  const double c1 = 2.0 * s * ix, s2 = s * s;  // Wh_{m+1} = m c1 Wh_m - s2 Wh_{m-1}
+  cd acc[LC], accp[LC], accq[LC];
+#pragma unroll
+  for (int j = 0; j < LC; ++j) acc[j] = accp[j] = accq[j] = mk(0.0, 0.0);
   cd hm1 = h0, hm = h0, ee = mk(1.0, 0.0);
   for (int mm = 0; mm <= M; ++mm) {
     if (mm == 1) { hm1 = h0; hm = cscale(h1, s); }
     if (mm >= 1) ee = cmul(ee, e1);
-    const cd wp = cmul(hm, ee);                                        // Wh_m
-    const cd wq = cscale(cmul(hm, cconj(ee)), (mm & 1) ? -1.0 : 1.0);  // Wh_{-m}
+    // Wh_m = hm ee and Wh_{-m} = (-1)^m hm conj(ee) from the same four products
+    const double ac = hm.x * ee.x, bd = hm.y * ee.y, ad = hm.x * ee.y, bc = hm.y * ee.x;
+    const cd wp = mk(ac - bd, ad + bc);
+    const double sm = (mm & 1) ? -1.0 : 1.0;
+    const cd wq = mk(sm * (ac + bd), sm * (bc - ad));
+    if (mm <= p) {  // |n| - |n + l| depends on n: per-term factors
 #pragma unroll
-    for (int j = 0; j < LC; ++j) {
-      const int lo = lo0 + j;
-      if (lo > p) break;
-      const double sg = (lo & 1) ? -1.0 : 1.0;
-      const int n1 = mm - lo;  // n + l = m
-      if (n1 >= -pb && n1 <= pb) {
-        const int ex = abs(n1) - mm;  // s^{|n| - |n+l|}, |ex| <= p
-        cfma(acc[j], cscale(a[n1 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wp);
-      }
-      if (mm > 0) {
-        const int n2 = -mm - lo;  // n + l = -m
-        if (n2 >= -pb && n2 <= pb) {
-          const int ex = abs(n2) - mm;
-          cfma(acc[j], cscale(a[n2 + pb], sg * (ex >= 0 ? pwl[ex] : ipl[-ex])), wq);
+      for (int j = 0; j < LC; ++j) {
+        const int lo = lo0 + j;
+        const int n1 = mm - lo;  // n + l = m
+        if (lo <= p && n1 >= -pb && n1 <= pb) {
+          const int ex = abs(n1) - mm;
+          cfma(acc[j], cscale(a[n1 + pb], ex >= 0 ? pwl[ex] : ipl[-ex]), wp);
         }
+        const int n2 = -mm - lo;  // n + l = -m
+        if (mm > 0 && lo <= p && n2 >= -pb && n2 <= pb) {
+          const int ex = abs(n2) - mm;
+          cfma(acc[j], cscale(a[n2 + pb], ex >= 0 ? pwl[ex] : ipl[-ex]), wq);
+        }
+      }
+    } else {  // n + l = m > 0 has n > 0, n + l = -m has n < 0: factors s^-l, s^l
+#pragma unroll
+      for (int j = 0; j < LC; ++j) {
+        const int lo = lo0 + j;
+        const int n1 = mm - lo, n2 = -mm - lo;
+        const cd av = (n1 >= -pb && n1 <= pb) ? a[n1 + pb] : mk(0.0, 0.0);
+        const cd aq = (n2 >= -pb && n2 <= pb) ? a[n2 + pb] : mk(0.0, 0.0);
+        cfma(accp[j], av, wp);
+        cfma(accq[j], aq, wq);
       }
     }
     if (mm >= 1) {
-      const cd hn = csub(cscale(hm, 2.0 * mm * s / x), cscale(hm1, s * s));
+      const cd hn = csub(cscale(hm, mm * c1), cscale(hm1, s2));
       hm1 = hm;
       hm = hn;
     }
   }
   cd* dst = partial + (size_t)t * P;
 #pragma unroll
-  for (int j = 0; j < LC; ++j)
-    if (lo0 + j <= p) dst[lo0 + j + p] = acc[j];
+  for (int j = 0; j < LC; ++j) {
+    const int lo = lo0 + j;
+    if (lo > p) break;
+    const double fp = lo <= 0 ? pwl[-lo] : ipl[lo];  // s^-l
+    const double fq = lo >= 0 ? pwl[lo] : ipl[-lo];  // s^l
+    cd v = cadd(acc[j], cadd(cscale(accp[j], fp), cscale(accq[j], fq)));
+    if (lo & 1) v = mk(-v.x, -v.y);
+    dst[lo + p] = v;
+  }
 }
 
 // alpha[centre] += sum of its pairs' partial coefficients, in pair order
@@ -1069,7 +1113,7 @@ qbx_status configure_kernels() {
   int optin = 0;
   QBX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const void* k[] = {(const void*)p2m_kernel, (const void*)m2m_kernel,
-                     (const void*)p2l_kernel, (const void*)l2l_kernel};
+                     (const void*)p2l_item_kernel, (const void*)l2l_kernel};
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   TRY_MIXED(configure_mixed_kernels(optin));
@@ -1212,6 +1256,27 @@ int p_add_default(int p) {
     qbx_status s_ = (x);                \
     if (s_ != QBX_OK) return s_;        \
   } while (0)
+
+// Shared memory of a source-row kernel (P2M, P2L) at box order pb: a full
+// warp's chunk of rows while that keeps the block within kRowsSmemTarget
+// (several blocks per SM), else half a warp's; never above the opt-in limit.
+constexpr size_t kRowsSmemTarget = 60 * 1024;
+size_t rows_launch_smem(int pb) {
+  const size_t full = rows_smem(pb, kChunk);
+  const size_t sm = full <= kRowsSmemTarget ? full : rows_smem(pb, kChunk / 2);
+  return std::min(sm, (size_t)g_smem_optin);
+}
+
+// Largest box order among the levels l with off[l+1] > off[l] (boxes of a
+// level-ordered list); the single launch over the list sizes its shared memory
+// for it. The lists are ordered coarse to fine, so the CTAs with the most work
+// (highest orders) start first.
+int max_order(const std::vector<int>& pb, const std::vector<int>& off) {
+  int m = 0;
+  for (size_t l = 0; l + 1 < off.size(); ++l)
+    if (off[l + 1] > off[l]) m = std::max(m, pb[l]);
+  return m;
+}
 
 qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* on_node_dev,
                           const int8_t* on_side_dev, double eps) {
@@ -1477,6 +1542,44 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   for (int l = 0; l < f->n_levels; ++l) f->src_leaf_off[l + 1] += f->src_leaf_off[l];
   for (int b = 0; b < f->n_boxes; ++b)
     for (int e = xoff[b]; e < xoff[b + 1]; ++e) p2l += rs[xidx[e]].y - rs[xidx[e]].x;
+  {  // P2L work items: each X box's sources, cut into pieces of one row chunk
+    std::vector<int> xb(std::max(1, f->n_xbox));
+    if (f->n_xbox)
+      QBX_CUDA_TRY(cudaMemcpy(xb.data(), f->xbox.ptr, f->n_xbox * sizeof(int), cudaMemcpyDeviceToHost));
+    const int pbx = max_order(f->h_pb, f->xbox_off);
+    f->p2l_sm = rows_launch_smem(pbx);
+    const int chunk = rows_chunk(pbx, f->p2l_sm);  // the least capacity over the X levels
+    std::vector<int> src, boff(f->n_xbox + 1, 0);
+    std::vector<int4> items;
+    std::vector<long long> poff;
+    long long ptot = 0;
+    for (int t = 0; t < f->n_xbox; ++t) {
+      const int b = xb[t];
+      const int Q = 2 * f->h_pb[blev[b]] + 1;
+      const int s0 = (int)src.size();
+      for (int e = xoff[b]; e < xoff[b + 1]; ++e)
+        for (int i = rs[xidx[e]].x; i < rs[xidx[e]].y; ++i) src.push_back(i);
+      boff[t] = (int)items.size();
+      for (int a = s0; a < (int)src.size(); a += chunk) {
+        items.push_back(make_int4(b, a, std::min(chunk, (int)src.size() - a), 0));
+        poff.push_back(ptot);
+        ptot += Q;
+      }
+    }
+    boff[f->n_xbox] = (int)items.size();
+    f->n_p2l_items = (int)items.size();
+    QBX_CUDA_TRY(f->p2l_items.alloc(std::max<size_t>(1, items.size())));
+    QBX_CUDA_TRY(f->p2l_poff.alloc(std::max<size_t>(1, poff.size())));
+    QBX_CUDA_TRY(f->p2l_src.alloc(std::max<size_t>(1, src.size())));
+    QBX_CUDA_TRY(f->p2l_boff.alloc(boff.size()));
+    QBX_CUDA_TRY(f->p2l_part.alloc(std::max<long long>(1, ptot)));
+    if (!items.empty()) {
+      QBX_CUDA_TRY(cudaMemcpy(f->p2l_items.ptr, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->p2l_poff.ptr, poff.data(), poff.size() * sizeof(long long), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->p2l_src.ptr, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    QBX_CUDA_TRY(cudaMemcpy(f->p2l_boff.ptr, boff.data(), boff.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   QBX_CUDA_TRY(f->src_leaves.alloc(std::max<size_t>(1, src_leaves.size())));
   if (!src_leaves.empty())
     QBX_CUDA_TRY(cudaMemcpy(f->src_leaves.ptr, src_leaves.data(), src_leaves.size() * 4,
@@ -1558,10 +1661,12 @@ qbx_status launch_m2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D
   if (C.n_pairs > 0 && (S || D)) {
     const int np = C.n_pairs;
     cd* part = f->wpart.ptr;
-    const unsigned gb = nblk((int64_t)np * kM2qbxlSplit, kThreads);
-    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<gb, kThreads, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
-    else if (S) m2qbxl_pair_kernel<PM, true, false><<<gb, kThreads, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
-    else m2qbxl_pair_kernel<PM, false, true><<<gb, kThreads, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+    const int nparts = (2 * h->p + 1 + kM2qbxlOrders - 1) / kM2qbxlOrders;
+    const unsigned gb = nblk((int64_t)np * nparts, kM2qbxlBlock);
+    constexpr int B = kM2qbxlBlock;
+    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+    else if (S) m2qbxl_pair_kernel<PM, true, false><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+    else m2qbxl_pair_kernel<PM, false, true><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
     QBX_KCHECK("m2qbxl", s);
     const int P = 2 * h->p + 1;
     m2qbxl_sum_kernel<<<nblk((int64_t)C.n * P, 256), 256, 0, s>>>(C.n, P, C.wp_off.ptr, part,
@@ -1600,26 +1705,6 @@ qbx_status launch_centre_near(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, b
   return QBX_OK;
 }
 
-// Shared memory of a source-row kernel (P2M, P2L) at box order pb: a full
-// warp's chunk of rows while that keeps the block within kRowsSmemTarget
-// (several blocks per SM), else half a warp's; never above the opt-in limit.
-constexpr size_t kRowsSmemTarget = 60 * 1024;
-size_t rows_launch_smem(int pb) {
-  const size_t full = rows_smem(pb, kChunk);
-  const size_t sm = full <= kRowsSmemTarget ? full : rows_smem(pb, kChunk / 2);
-  return std::min(sm, (size_t)g_smem_optin);
-}
-
-// Largest box order among the levels l with off[l+1] > off[l] (boxes of a
-// level-ordered list); the single launch over the list sizes its shared memory
-// for it. The lists are ordered coarse to fine, so the CTAs with the most work
-// (highest orders) start first.
-int max_order(const std::vector<int>& pb, const std::vector<int>& off) {
-  int m = 0;
-  for (size_t l = 0; l + 1 < off.size(); ++l)
-    if (off[l + 1] > off[l]) m = std::max(m, pb[l]);
-  return m;
-}
 
 }  // namespace
 
@@ -1680,10 +1765,13 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   if (h->n_tgt > 0) QBX_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)h->n_tgt * sizeof(cd), s2));
   stage_begin(h, QBX_STAGE_P2L, s2);
   if ((S || D) && f->n_xbox > 0) {
-    const size_t sm = rows_launch_smem(max_order(pb, f->xbox_off));
-    p2l_kernel<<<f->n_xbox, kThreads, sm, s2>>>(F, f->xbox.ptr, (unsigned)sm);
+    p2l_item_kernel<<<f->n_p2l_items, kThreads, f->p2l_sm, s2>>>(
+        F, f->p2l_items.ptr, f->p2l_src.ptr, f->p2l_poff.ptr, f->p2l_part.ptr, (unsigned)f->p2l_sm);
     QBX_KCHECK("p2l", s2);
-    h->launches += 1;
+    p2l_sum_kernel<<<f->n_xbox, kThreads, 0, s2>>>(F, f->xbox.ptr, f->p2l_boff.ptr, f->p2l_poff.ptr,
+                                                  f->p2l_part.ptr);
+    QBX_KCHECK("p2l_sum", s2);
+    h->launches += 2;
   }
   stage_end(h, QBX_STAGE_P2L, s2);
   TRY(signal(f->ev_p2l, s2));

@@ -56,6 +56,14 @@ struct FmmPlan {
   std::vector<int> nonleaf_off;         // [n_levels + 1] offsets into nonleaf
   DevBuf<int> xbox;                     // boxes with non-empty X list
   int n_xbox = 0;
+  // P2L work items (box, first position in p2l_src, sources), their partial
+  // coefficient rows (offsets p2l_poff) and each X box's first item
+  DevBuf<int4> p2l_items;
+  DevBuf<int> p2l_src, p2l_boff;
+  DevBuf<long long> p2l_poff;
+  DevBuf<cd> p2l_part;
+  int n_p2l_items = 0;
+  size_t p2l_sm = 0;
   DevBuf<int> vbox;                     // boxes with non-empty V list
   int n_vbox = 0;
   // orders and scales: box order pb_l per level (0 on levels 0 and 1, which
