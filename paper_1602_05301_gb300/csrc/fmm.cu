@@ -247,72 +247,109 @@ __host__ __device__ inline int rows_chunk(int pb, size_t sm_bytes) {
   return (int)(c < (size_t)kChunk ? c : (size_t)kChunk);
 }
 
-// CTA per leaf. Threads 0..chunk-1 fill one row each with
-// conj(V_m(y - m_b)) / s^m, m = 0..pb+1; then all threads reduce over the rows.
-__global__ void __launch_bounds__(kThreads) p2m_kernel(Fmm F, const int* __restrict__ leaves,
-                                                       unsigned sm_bytes) {
-  extern __shared__ cd smem[];
-  const int b = leaves[blockIdx.x];
-  const int l = F.level[b];
-  const int pb = F.lpb[l], Q = 2 * pb + 1, RW = 2 * pb + 3;  // row: conj(V_t)/s^|t|, |t| <= pb+1
-  const int chunk = rows_chunk(pb, sm_bytes);
-  cd* acc = smem;                         // [Q]
-  cd* rows = acc + Q;                     // [chunk][RW]
-  cd* sq = rows + chunk * RW;             // [chunk]
-  cd* sa = sq + chunk;                    // [chunk]  d (k/2) conj(nu)
-  cd* sb = sa + chunk;                    // [chunk]  d (k/2) nu
-  const int2 r = F.rsrc[b];
-  const double s = F.scale[l], is = 1.0 / s;
-  const double2 m = F.centre[b];
-  const double hk = 0.5 * F.k;
-  for (int i = threadIdx.x; i < Q; i += kThreads) acc[i] = mk(0.0, 0.0);
-  for (int base = r.x; base < r.y; base += chunk) {
-    const int cnt = min(chunk, r.y - base);
-    if ((int)threadIdx.x < cnt) {
-      const int i = base + threadIdx.x;
-      const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
-      const double rr = sqrt(dx * dx + dy * dy);
-      cd* row = rows + threadIdx.x * RW + (pb + 1);
-      // J_0..J_{pb+1} (unnormalised) into the real parts of row[0..pb+1]
-      const double norm = miller_row(F.k * rr, pb + 1, (double*)row, 2);
-      const cd em = rr > 0.0 ? mk(dx / rr, -dy / rr) : mk(1.0, 0.0);  // e^{-i th}
-      cd e = mk(1.0, 0.0);
-      double f = 1.0 / norm;
-      for (int j = 0; j <= pb + 1; ++j) {
-        const double v = row[j].x * f;                // J_j / s^j
-        const cd c = cscale(e, v);                    // conj(V_j) / s^j
-        row[j] = c;
-        if (j > 0) row[-j] = (j & 1) ? mk(-c.x, c.y) : mk(c.x, -c.y);  // (-1)^j conj(c)
-        e = cmul(e, em);
-        f *= is;
-      }
-      const cd dk = cscale(F.ds[i], hk);
-      const cd nu = mk(F.snrm[i].x, F.snrm[i].y);
-      sq[threadIdx.x] = F.qs[i];
-      sa[threadIdx.x] = cmul(dk, cconj(nu));
-      sb[threadIdx.x] = cmul(dk, nu);
-    }
-    __syncthreads();
-    for (int n = (int)threadIdx.x - pb; n <= pb; n += kThreads) {
-      const int an = abs(n);
-      // conj(V_{n-+1})/s^|n| = row[n-+1] s^{|n-+1| - |n|}
-      const double fm = (abs(n - 1) > an) ? s : is;
-      const double fp = (abs(n + 1) > an) ? s : is;
-      cd a = acc[n + pb];
-      for (int j = 0; j < cnt; ++j) {
-        const cd* row = rows + j * RW + (pb + 1);
-        if (F.has_S) cfma(a, sq[j], row[n]);
-        if (F.has_D) {
-          cfma(a, cscale(sa[j], fm), row[n - 1]);
-          cfma(a, cscale(sb[j], -fp), row[n + 1]);
-        }
-      }
-      acc[n + pb] = a;
-    }
-    __syncthreads();
+// Row of source i for the multipole of a box with centre m, order pb and
+// scale s: row[t] = conj(V_t(y_i - m)) / s^|t|, |t| <= pb + 1 (row points at
+// t = 0), and the source's charge and dipole factors in sq, sa, sb.
+__device__ __forceinline__ void p2m_fill_row(const Fmm& F, int i, double2 m, double is, int pb,
+                                             cd* row, cd& sq, cd& sa, cd& sb) {
+  const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
+  const double rr = sqrt(dx * dx + dy * dy);
+  // J_0..J_{pb+1} (unnormalised) into the real parts of row[0..pb+1]
+  const double norm = miller_row(F.k * rr, pb + 1, (double*)row, 2);
+  const cd em = rr > 0.0 ? mk(dx / rr, -dy / rr) : mk(1.0, 0.0);  // e^{-i th}
+  cd e = mk(1.0, 0.0);
+  double f = 1.0 / norm;
+  for (int j = 0; j <= pb + 1; ++j) {
+    const double v = row[j].x * f;                // J_j / s^j
+    const cd c = cscale(e, v);                    // conj(V_j) / s^j
+    row[j] = c;
+    if (j > 0) row[-j] = (j & 1) ? mk(-c.x, c.y) : mk(c.x, -c.y);  // (-1)^j conj(c)
+    e = cmul(e, em);
+    f *= is;
   }
+  const cd dk = cscale(F.ds[i], 0.5 * F.k);
+  const cd nu = mk(F.snrm[i].x, F.snrm[i].y);
+  sq = F.qs[i];
+  sa = cmul(dk, cconj(nu));
+  sb = cmul(dk, nu);
+}
+
+// Order n of a box's multipole from rows j0..j1 of the staged rows:
+// a_n = sum_j [q_j row_j[n] + s^{|n-1| - |n|} A_j row_j[n-1] - s^{|n+1| - |n|} B_j row_j[n+1]]
+// (charge and dipole terms in separate sums, each scaled once).
+__device__ __forceinline__ cd p2m_order(const Fmm& F, const cd* rows, int RW, const cd* sq,
+                                        const cd* sa, const cd* sb, int j0, int j1, int n,
+                                        double s, double is) {
+  const int an = abs(n);
+  // conj(V_{n-+1})/s^|n| = row[n-+1] s^{|n-+1| - |n|}
+  const double fm = (abs(n - 1) > an) ? s : is;
+  const double fp = (abs(n + 1) > an) ? s : is;
+  cd aq = mk(0.0, 0.0), aa = mk(0.0, 0.0), ab = mk(0.0, 0.0);
+  for (int j = j0; j < j1; ++j) {
+    const cd* row = rows + j * RW;
+    if (F.has_S) cfma(aq, sq[j], row[n]);
+    if (F.has_D) {
+      cfma(aa, sa[j], row[n - 1]);
+      cfma(ab, sb[j], row[n + 1]);
+    }
+  }
+  return cadd(aq, csub(cscale(aa, fm), cscale(ab, fp)));
+}
+
+// P2M work: every source leaf's sources are cut into segments of at most a
+// row chunk; segments of one level are packed into items of up to a chunk of
+// sources (item = (first segment, segments, first packed source, sources)),
+// so small leaves share a CTA and large ones spread over several. One warp
+// fills the item's rows with full lanes; then the threads run over
+// (segment, order) pairs and write each segment's part of its leaf's multipole
+// to partial[seg_poff[segment] + n + pb]; p2m_sum_kernel adds a leaf's
+// segments in order.
+__global__ void __launch_bounds__(kThreads) p2m_item_kernel(Fmm F, const int4* __restrict__ items,
+                                                            const int* __restrict__ seg_leaf,
+                                                            const int2* __restrict__ seg_row,
+                                                            const long long* __restrict__ seg_poff,
+                                                            const int* __restrict__ src,
+                                                            const int* __restrict__ src_leaf,
+                                                            cd* __restrict__ partial,
+                                                            unsigned sm_bytes) {
+  extern __shared__ cd smem[];
+  const int4 it = items[blockIdx.x];
+  const int l = F.level[seg_leaf[it.x]];
+  const int pb = F.lpb[l], Q = 2 * pb + 1, RW = 2 * pb + 3;
+  const int chunk = rows_chunk(pb, sm_bytes);  // >= it.w
+  cd* rows = smem;                        // [chunk][RW]
+  cd* sq = rows + chunk * RW;             // [chunk]
+  cd* sa = sq + chunk;                    // [chunk]
+  cd* sb = sa + chunk;                    // [chunk]
+  const double s = F.scale[l], is = 1.0 / s;
+  if ((int)threadIdx.x < it.w) {
+    const int j = threadIdx.x;
+    p2m_fill_row(F, src[it.z + j], F.centre[src_leaf[it.z + j]], is, pb, rows + j * RW + (pb + 1),
+                 sq[j], sa[j], sb[j]);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < it.y * Q; idx += kThreads) {
+    const int u = idx / Q, n = idx % Q - pb;
+    const int2 rr = seg_row[it.x + u];
+    partial[seg_poff[it.x + u] + n + pb] =
+        p2m_order(F, rows + (pb + 1), RW, sq, sa, sb, rr.x, rr.x + rr.y, n, s, is);
+  }
+}
+
+// mpole(leaves[t]) = sum of its segments' partial multipoles, in order
+// (segments lseg[t]..lseg[t+1]).
+__global__ void __launch_bounds__(kThreads) p2m_sum_kernel(Fmm F, const int* __restrict__ leaves,
+                                                           const int* __restrict__ lseg,
+                                                           const long long* __restrict__ seg_poff,
+                                                           const cd* __restrict__ partial) {
+  const int t = blockIdx.x, b = leaves[t];
+  const int Q = 2 * F.lpb[F.level[b]] + 1;
   cd* dst = F.mpole + F.eoff[b];
-  for (int i = threadIdx.x; i < Q; i += kThreads) dst[i] = acc[i];
+  for (int n = threadIdx.x; n < Q; n += kThreads) {
+    cd sum = mk(0.0, 0.0);
+    for (int g = lseg[t]; g < lseg[t + 1]; ++g) sum = cadd(sum, partial[seg_poff[g] + n]);
+    dst[n] = sum;
+  }
 }
 
 // ---------------------------------------------------------------- M2M (Stage 2)
@@ -1112,7 +1149,7 @@ qbx_status configure_kernels() {
   if (done.count(dev)) return QBX_OK;
   int optin = 0;
   QBX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const void* k[] = {(const void*)p2m_kernel, (const void*)m2m_kernel,
+  const void* k[] = {(const void*)p2m_item_kernel, (const void*)m2m_kernel,
                      (const void*)p2l_item_kernel, (const void*)l2l_kernel};
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -1536,6 +1573,62 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     QBX_CUDA_TRY(f->wpart.alloc(max_pairs * (size_t)(2 * h->p + 1)));
     f->n_wpairs = f->cset[0].n_pairs;
   }
+  // P2M work items over segments of the source leaves (see p2m_item_kernel)
+  {
+    int pbs = 0;  // largest order over the source leaves
+    for (int b : src_leaves) pbs = std::max(pbs, f->h_pb[blev[b]]);
+    f->p2m_sm = rows_launch_smem(pbs);
+    const int chunk = rows_chunk(pbs, f->p2m_sm);  // the least capacity over the leaf levels
+    std::vector<int> sleaf, psrc, psleaf, lseg(src_leaves.size() + 1, 0);
+    std::vector<int2> srow;
+    std::vector<long long> spoff;
+    std::vector<int4> items;
+    long long ptot = 0;
+    int cur_lev = -1;
+    for (size_t t = 0; t < src_leaves.size(); ++t) {
+      const int b = src_leaves[t];
+      const int Q = 2 * f->h_pb[blev[b]] + 1;
+      lseg[t] = (int)sleaf.size();
+      for (int i0 = rs[b].x; i0 < rs[b].y;) {
+        if (items.empty() || cur_lev != blev[b] || items.back().w == chunk) {
+          items.push_back(make_int4((int)sleaf.size(), 0, (int)psrc.size(), 0));
+          cur_lev = blev[b];
+        }
+        int4& it = items.back();
+        const int cnt = std::min(chunk - it.w, rs[b].y - i0);
+        srow.push_back(make_int2(it.w, cnt));
+        sleaf.push_back(b);
+        spoff.push_back(ptot);
+        ptot += Q;
+        for (int i = i0; i < i0 + cnt; ++i) {
+          psrc.push_back(i);
+          psleaf.push_back(b);
+        }
+        it.y += 1;
+        it.w += cnt;
+        i0 += cnt;
+      }
+    }
+    lseg[src_leaves.size()] = (int)sleaf.size();
+    f->n_p2m_items = (int)items.size();
+    QBX_CUDA_TRY(f->p2m_items.alloc(std::max<size_t>(1, items.size())));
+    QBX_CUDA_TRY(f->p2m_segleaf.alloc(std::max<size_t>(1, sleaf.size())));
+    QBX_CUDA_TRY(f->p2m_segrow.alloc(std::max<size_t>(1, srow.size())));
+    QBX_CUDA_TRY(f->p2m_segpoff.alloc(std::max<size_t>(1, spoff.size())));
+    QBX_CUDA_TRY(f->p2m_lseg.alloc(lseg.size()));
+    QBX_CUDA_TRY(f->p2m_src.alloc(std::max<size_t>(1, psrc.size())));
+    QBX_CUDA_TRY(f->p2m_srcleaf.alloc(std::max<size_t>(1, psleaf.size())));
+    QBX_CUDA_TRY(f->p2m_part.alloc(std::max<long long>(1, ptot)));
+    if (!items.empty()) {
+      QBX_CUDA_TRY(cudaMemcpy(f->p2m_items.ptr, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->p2m_segleaf.ptr, sleaf.data(), sleaf.size() * sizeof(int), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->p2m_segrow.ptr, srow.data(), srow.size() * sizeof(int2), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->p2m_segpoff.ptr, spoff.data(), spoff.size() * sizeof(long long), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->p2m_src.ptr, psrc.data(), psrc.size() * sizeof(int), cudaMemcpyHostToDevice));
+      QBX_CUDA_TRY(cudaMemcpy(f->p2m_srcleaf.ptr, psleaf.data(), psleaf.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    QBX_CUDA_TRY(cudaMemcpy(f->p2m_lseg.ptr, lseg.data(), lseg.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   // leaves come in level order, so src_leaves does too
   f->src_leaf_off.assign(f->n_levels + 1, 0);
   for (int b : src_leaves) f->src_leaf_off[blev[b] + 1] += 1;
@@ -1793,11 +1886,15 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   stage_end(h, QBX_STAGE_P2P, s2);
   // ---- main: upward pass
   stage_begin(h, QBX_STAGE_P2M, s);
-  if ((S || D) && f->n_src_leaves > 0) {
-    const size_t sm = rows_launch_smem(max_order(pb, f->src_leaf_off));
-    p2m_kernel<<<f->n_src_leaves, kThreads, sm, s>>>(F, f->src_leaves.ptr, (unsigned)sm);
+  if ((S || D) && f->n_p2m_items > 0) {
+    p2m_item_kernel<<<f->n_p2m_items, kThreads, f->p2m_sm, s>>>(
+        F, f->p2m_items.ptr, f->p2m_segleaf.ptr, f->p2m_segrow.ptr, f->p2m_segpoff.ptr,
+        f->p2m_src.ptr, f->p2m_srcleaf.ptr, f->p2m_part.ptr, (unsigned)f->p2m_sm);
     QBX_KCHECK("p2m", s);
-    h->launches += 1;
+    p2m_sum_kernel<<<f->n_src_leaves, kThreads, 0, s>>>(F, f->src_leaves.ptr, f->p2m_lseg.ptr,
+                                                       f->p2m_segpoff.ptr, f->p2m_part.ptr);
+    QBX_KCHECK("p2m_sum", s);
+    h->launches += 2;
   }
   stage_end(h, QBX_STAGE_P2M, s);
   stage_begin(h, QBX_STAGE_M2M, s);

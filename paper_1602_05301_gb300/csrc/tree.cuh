@@ -77,6 +77,17 @@ struct FmmPlan {
   DevBuf<double> pw, ipw;               // per level powers s^j, s^-j
   DevBuf<int> src_leaves;               // leaves holding sources (levels >= 2)
   int n_src_leaves = 0;
+  // P2M items over segments of the source leaves (first segment, segments,
+  // first packed source, sources); per segment its leaf, rows in its item and
+  // partial-row offset; per source leaf its first segment; per packed source
+  // its index and leaf
+  DevBuf<int4> p2m_items;
+  DevBuf<int> p2m_segleaf, p2m_lseg, p2m_src, p2m_srcleaf;
+  DevBuf<int2> p2m_segrow;
+  DevBuf<long long> p2m_segpoff;
+  DevBuf<cd> p2m_part;
+  int n_p2m_items = 0;
+  size_t p2m_sm = 0;
   // src_leaves, xbox and vbox are ordered by level; [n_levels + 1] offsets
   std::vector<int> src_leaf_off, xbox_off, vbox_off;
   int q_leaf = 1, q_w = 1;              // largest Q_l among leaves / W-list boxes
