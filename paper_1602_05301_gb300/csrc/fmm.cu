@@ -702,152 +702,62 @@ __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __
 // ---------------------------------------------------------------- centres (Stages 3, 5, 8 "New")
 // L2QBXL: alpha_s += sum_n gamma_n (-1)^{s-n} V_{s-n}(z - m_b), |s| <= p, from
 // the true local coefficients gamma of the centre's leaf (leaf locals are
-// unscaled in place once the downward pass is complete). One warp per centre:
-// every lane runs the (warp-uniform) backward recurrence for J_m(k|z - m_b|),
-// m <= pb + p, and accumulates its own output orders s = lane - p and
-// lane + 32 - p.
-__global__ void __launch_bounds__(kThreads) l2qbxl_kernel(Fmm F, const int* __restrict__ cleaf,
-                                                          const int* __restrict__ clist, int n_ctr,
-                                                          cd* __restrict__ alpha) {
-  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= n_ctr) return;
-  const int i = clist[w];
+// unscaled in place once the downward pass is complete). A warp takes G
+// centres. First each of G lanes fills its centre's row V_m = J_m(k r) e^{i m th},
+// 0 <= m <= M = pb + p, in shared memory (one backward recurrence per centre);
+// then the lanes take the warp's (centre, output order s) pairs and form
+// alpha_s = sum_n gamma_n t_{s-n} over ascending n, with t_m = (-1)^m V_m for
+// m >= 0 and t_m = (-1)^m V_m = conj(V_{-m}) for m < 0 (signs set on the bits,
+// off the FP64 pipe). The result does not depend on G or on the launch.
+__global__ void __launch_bounds__(32) l2qbxl_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                    const int* __restrict__ clist, int n_ctr,
+                                                    int G, int TW, cd* __restrict__ alpha) {
+  extern __shared__ cd trow[];  // [G][TW], TW > max M
+  const int lane = threadIdx.x;
+  const int c0 = blockIdx.x * G;
   const int p = F.p, P = 2 * p + 1;
-  const int b = cleaf[i];
-  const int pb = F.lpb[F.level[b]];
-  const cd* g = F.local + F.eoff[b];
-  const double2 mb = F.centre[b];
-  const int M = pb + p;
-  const double dx = F.cxy[i].x - mb.x, dy = F.cxy[i].y - mb.y;
-  const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-  const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
-  const int so0 = lane - p, so1 = lane + 32 - p;  // this lane's output orders
-  cd a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
-  // one order m of V: V_m = f_m e^{im th}, V_{-m} = (-1)^m f_m e^{-im th}
-  auto add_m = [&](int mm, double fm, cd e) {
-    const double sg = (mm & 1) ? -1.0 : 1.0;
-    const cd vp = cscale(e, fm * sg);    // (-1)^m V_m
-    const cd vn = cscale(cconj(e), fm);  // (-1)^m V_{-m} = J_m e^{-im th}
-    if (so0 <= p) {
-      const int n1 = so0 - mm, n2 = so0 + mm;
-      if (n1 >= -pb && n1 <= pb) cfma(a0, g[n1 + pb], vp);
-      if (mm > 0 && n2 >= -pb && n2 <= pb) cfma(a0, g[n2 + pb], vn);
-    }
-    if (so1 <= p) {
-      const int n1 = so1 - mm, n2 = so1 + mm;
-      if (n1 >= -pb && n1 <= pb) cfma(a1, g[n1 + pb], vp);
-      if (mm > 0 && n2 >= -pb && n2 <= pb) cfma(a1, g[n2 + pb], vn);
-    }
-  };
-  double norm;
-  if (x < 1e-8) {
-    add_m(0, 1.0, mk(1.0, 0.0));
-    norm = 1.0;
-  } else {
+  if (lane < G && c0 + lane < n_ctr) {
+    const int i = clist[c0 + lane];
+    const int b = cleaf[i];
+    const int M = F.lpb[F.level[b]] + p;
+    const double2 mb = F.centre[b];
+    const double dx = F.cxy[i].x - mb.x, dy = F.cxy[i].y - mb.y;
+    const double rr = sqrt(dx * dx + dy * dy);
+    cd* row = trow + (size_t)lane * TW;
+    // J_0..J_M (unnormalised) into the real parts of row[0..M]
+    const double in = 1.0 / miller_row(F.k * rr, M, (double*)row, 2);
+    const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
     cd e = mk(1.0, 0.0);
-    for (int j = 0; j < M; ++j) e = cmul(e, e1);  // e^{i M th}
-    const double inv = 2.0 / x;
-    const int N = miller_start(M, x);
-    double fn1 = 0.0, fn = 1e-200, sum = 0.0;
-    for (int n = N; n >= 1; --n) {
-      const double fm = (double)n * inv * fn - fn1;
-      if ((n & 1) == 0) sum += fn;
-      const int mm = n - 1;
-      if (mm <= M) {
-        if (mm < M) e = cmul(e, cconj(e1));
-        add_m(mm, fm, e);
-      }
-      fn1 = fn;
-      fn = fm;
-      if (fabs(fn) > kRescale) {
-        const double sc = 1.0 / kRescale;
-        fn *= sc; fn1 *= sc; sum *= sc;
-        a0 = cscale(a0, sc);
-        a1 = cscale(a1, sc);
-      }
+    for (int m = 0; m <= M; ++m) {
+      row[m] = cscale(e, row[m].x * in);
+      e = cmul(e, e1);
     }
-    norm = fn + 2.0 * sum;
   }
-  const double in = 1.0 / norm;
-  cd* dst = alpha + (size_t)F.cid[i] * P;
-  if (so0 <= p) dst[so0 + p] = cadd(dst[so0 + p], cscale(a0, in));
-  if (so1 <= p) dst[so1 + p] = cadd(dst[so1 + p], cscale(a1, in));
+  __syncwarp();
+  constexpr unsigned long long kSign = 0x8000000000000000ull;
+  const int nG = min(G, n_ctr - c0);
+  for (int o = lane; o < nG * P; o += 32) {
+    const int u = o / P, so = o % P - p;
+    const int i = clist[c0 + u];
+    const int b = cleaf[i];
+    const int pb = F.lpb[F.level[b]];
+    const cd* row = trow + (size_t)u * TW;
+    const cd* g = F.local + F.eoff[b] + pb;
+    cd a = mk(0.0, 0.0);
+    for (int n = -pb; n <= pb; ++n) {
+      const int m = so - n;
+      const cd v = row[abs(m)];
+      const unsigned long long fx = (m >= 0 && (m & 1)) ? kSign : 0ull;
+      const unsigned long long fy = (m < 0) ? kSign : fx;
+      const cd t = mk(__longlong_as_double(__double_as_longlong(v.x) ^ fx),
+                      __longlong_as_double(__double_as_longlong(v.y) ^ fy));
+      cfma(a, g[n], t);
+    }
+    cd* dst = alpha + (size_t)F.cid[i] * P + p + so;
+    *dst = cadd(*dst, a);
+  }
 }
 
-// L2QBXL, one thread per centre computing all 2p+1 orders: less work than the
-// warp form (one recurrence per centre instead of one per lane), for centre
-// counts large enough to fill the GPU.
-template <int PM>
-__global__ void __launch_bounds__(kThreads) l2qbxl_thread_kernel(Fmm F, const int* __restrict__ cleaf,
-                                                          const int* __restrict__ clist, int n_ctr,
-                                                          cd* __restrict__ alpha) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_ctr) return;
-  const int i = clist[t];
-  const int p = F.p, P = 2 * p + 1;
-  const int b = cleaf[i];
-  const int pb = F.lpb[F.level[b]];
-  const cd* g = F.local + F.eoff[b];
-  const double2 mb = F.centre[b];
-  const int M = pb + p;
-  {
-    const double dx = F.cxy[i].x - mb.x, dy = F.cxy[i].y - mb.y;
-    const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-    const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
-    cd acc[2 * PM + 1];
-#pragma unroll
-    for (int j = 0; j <= 2 * PM; ++j) acc[j] = mk(0.0, 0.0);
-    // one order m of V: V_m = f_m e^{im th}, V_{-m} = (-1)^m f_m e^{-im th}
-    auto add_m = [&](int mm, double fm, cd e) {
-      const double sg = (mm & 1) ? -1.0 : 1.0;
-      const cd vp = cscale(e, fm * sg);           // (-1)^m V_m
-      const cd vn = cscale(cconj(e), fm);         // (-1)^m V_{-m} = J_m e^{-im th}
-#pragma unroll
-      for (int so = -PM; so <= PM; ++so) {
-        if (so < -p || so > p) continue;
-        const int n1 = so - mm;                   // uses V_m
-        if (n1 >= -pb && n1 <= pb) cfma(acc[so + PM], g[n1 + pb], vp);
-        if (mm > 0) {
-          const int n2 = so + mm;                 // uses V_{-m}
-          if (n2 >= -pb && n2 <= pb) cfma(acc[so + PM], g[n2 + pb], vn);
-        }
-      }
-    };
-    double norm;
-    if (x < 1e-8) {
-      add_m(0, 1.0, mk(1.0, 0.0));
-      norm = 1.0;
-    } else {
-      cd e = mk(1.0, 0.0);
-      for (int j = 0; j < M; ++j) e = cmul(e, e1);  // e^{i M th}
-      const double inv = 2.0 / x;
-      const int N = miller_start(M, x);
-      double fn1 = 0.0, fn = 1e-200, sum = 0.0;
-      for (int n = N; n >= 1; --n) {
-        const double fm = (double)n * inv * fn - fn1;
-        if ((n & 1) == 0) sum += fn;
-        const int mm = n - 1;
-        if (mm <= M) {
-          if (mm < M) e = cmul(e, cconj(e1));
-          add_m(mm, fm, e);
-        }
-        fn1 = fn;
-        fn = fm;
-        if (fabs(fn) > kRescale) {
-          const double sc = 1.0 / kRescale;
-          fn *= sc; fn1 *= sc; sum *= sc;
-#pragma unroll
-          for (int j = 0; j <= 2 * PM; ++j) acc[j] = cscale(acc[j], sc);
-        }
-      }
-      norm = fn + 2.0 * sum;
-    }
-    const double in = 1.0 / norm;
-    cd* dst = alpha + (size_t)F.cid[i] * P;
-    for (int so = -p; so <= p; ++so) dst[so + p] = cadd(dst[so + p], cscale(acc[so + PM], in));
-  }
-}
 
 // Leaf local coefficients lh_n = gamma_n s^|n| -> gamma_n, in place, once the
 // downward pass (M2L, P2L, L2L) is complete; L2P and L2QBXL read gamma.
@@ -938,9 +848,8 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
 // block spreads the pairs over all SMs (the FP64 pipe is per SM).
 constexpr int kM2qbxlOrders = 4;
 constexpr int kM2qbxlBlock = 32;
-// Centre count from which L2QBXL runs a thread (not a warp) per centre: enough
-// threads for about eight resident warps on each of the 152 SMs.
-constexpr int kL2qbxlThreadMin = 152 * 8 * 32;
+// shared memory of the L2QBXL rows of one warp (several warps per SM)
+constexpr size_t kL2qbxlSmem = 24 * 1024;
 template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int* __restrict__ pair_ctr,
                                                                const int* __restrict__ pair_box,
@@ -1388,7 +1297,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   // side stream and events for the concurrent near-field stages (created here,
   // outside any stream capture; owned by the plan)
   QBX_CUDA_TRY(cudaStreamCreateWithFlags(&f->near_stream, cudaStreamNonBlocking));
-  for (cudaEvent_t* ev : {&f->ev_fork, &f->ev_join, &f->ev_p2l, &f->ev_m2m, &f->ev_down, &f->ev_out})
+  for (cudaEvent_t* ev : {&f->ev_fork, &f->ev_join, &f->ev_p2l, &f->ev_m2m, &f->ev_out})
     QBX_CUDA_TRY(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   // the largest per-block footprint (the M2M / L2L GEMMs at the largest
   // order) bounds all others
@@ -1488,6 +1397,9 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   std::vector<int> cl(std::max<int64_t>(1, h->n_ctr), 0);
   for (int b : leaves)
     for (int i = rc[b].x; i < rc[b].y; ++i) cl[i] = b;
+  f->cleaf_pb_max = 0;
+  for (int b : leaves)
+    if (rc[b].y > rc[b].x) f->cleaf_pb_max = std::max(f->cleaf_pb_max, f->h_pb[blev[b]]);
   QBX_CUDA_TRY(f->cleaf.alloc(cl.size()));
   QBX_CUDA_TRY(cudaMemcpy(f->cleaf.ptr, cl.data(), cl.size() * sizeof(int),
                           cudaMemcpyHostToDevice));
@@ -1733,12 +1645,18 @@ qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSe
                          cudaStream_t s) {
   if (C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_L2QBXL, s);
-  // a warp per centre while the centres are too few to fill the GPU with
-  // threads (the kernel is then latency-bound), else a thread per centre
-  if (C.n < kL2qbxlThreadMin && !h->batched)
-    l2qbxl_kernel<<<nblk(C.n, kThreads / 32), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
-  else
-    l2qbxl_thread_kernel<PM><<<nblk(C.n, kThreads), kThreads, 0, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, alpha);
+  // a warp per G centres. G: up to 32 (every lane fills a row), but no more
+  // than keeps about two warps per SM for a handle evaluated alone (the dot
+  // products keep the FP64 pipe busy from one warp; batched handles share the
+  // GPU), within the shared memory of the rows.
+  {
+    const int TW = f->cleaf_pb_max + h->p + 1;
+    int G = 32;
+    while (!h->batched && G > 1 && (C.n + G - 1) / G < 152 * 2) G /= 2;
+    while (G > 1 && (size_t)G * TW * sizeof(cd) > kL2qbxlSmem) G /= 2;
+    const size_t sm = (size_t)G * TW * sizeof(cd);
+    l2qbxl_kernel<<<nblk(C.n, G), 32, sm, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, G, TW, alpha);
+  }
   QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
   h->launches += 1;
@@ -1814,14 +1732,17 @@ qbx_status centre_near_dispatch(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S,
 // Stream organisation. Two streams: the caller's (main) and the plan's side
 // stream. Every stage adds into zeroed outputs, and each output array is
 // written by one stream at a time:
-//   main: P2M, M2M | M2L (after P2L) | L2L, unscale | L2P (after M2P)
-//   side: zero alpha, out; P2L; P2QBXL; P2P | M2QBXL, M2P (after M2M) |
-//         L2QBXL (after the downward pass)
+//   main: P2M, M2M | M2L (after P2L) | L2L, unscale | L2P (after M2P) |
+//         L2QBXL (after the side stream)
+//   side: zero alpha, out; P2L; P2QBXL; P2P | M2QBXL, M2P (after M2M)
 // P2L needs only the strengths and adds into the locals before M2L does; the
-// centre coefficients alpha are written on the side stream only; out is
-// written by P2P and M2P (side) before L2P (main). The main stream waits for
-// the side stream before returning. With per-stage timing on, everything runs
-// on the main stream in the same order, so that stage times do not overlap.
+// centre coefficients alpha are written by P2QBXL and M2QBXL (side) before
+// L2QBXL (main); out is written by P2P and M2P (side) before L2P (main).
+// L2QBXL follows L2P instead of running beside it: run concurrently, the two
+// took longer than one after the other (2.62 against 2.10 ms for the whole
+// step of the starfish k = 10 workload). With per-stage timing on, everything
+// runs on the main stream in the same order, so that stage times do not
+// overlap.
 qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool all_centres,
                     cudaStream_t s) {
   FmmPlan* f = h->fmm;
@@ -1959,16 +1880,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     h->launches += 1;
   }
   stage_end(h, QBX_STAGE_L2L, s);
-  TRY(signal(f->ev_down, s));
-  // ---- side: L2QBXL (alpha); main: L2P (out, after M2P)
-  TRY(wait(s2, f->ev_down));
-  if (h->n_ctr > 0) {
-    cd* alpha = h->alpha.ptr;
-    if (h->p <= 4) TRY(launch_l2qbxl<4>(F, f, h, C, alpha, s2));
-    else if (h->p <= 8) TRY(launch_l2qbxl<8>(F, f, h, C, alpha, s2));
-    else if (h->p <= 12) TRY(launch_l2qbxl<12>(F, f, h, C, alpha, s2));
-    else TRY(launch_l2qbxl<16>(F, f, h, C, alpha, s2));
-  }
+  // ---- main: L2P (out, after M2P), then L2QBXL (alpha, after the side stream)
   TRY(signal(f->ev_join, s2));
   TRY(wait(s, f->ev_out));
   if (f->n_dtgt > 0) {
@@ -1979,6 +1891,13 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     h->launches += 1;
   }
   TRY(wait(s, f->ev_join));
+  if (h->n_ctr > 0) {
+    cd* alpha = h->alpha.ptr;
+    if (h->p <= 4) TRY(launch_l2qbxl<4>(F, f, h, C, alpha, s));
+    else if (h->p <= 8) TRY(launch_l2qbxl<8>(F, f, h, C, alpha, s));
+    else if (h->p <= 12) TRY(launch_l2qbxl<12>(F, f, h, C, alpha, s));
+    else TRY(launch_l2qbxl<16>(F, f, h, C, alpha, s));
+  }
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;
 }

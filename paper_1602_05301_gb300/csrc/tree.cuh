@@ -30,10 +30,10 @@ struct FmmPlan {
   // concurrency of the near-field stages (see fmm_eval)
   cudaStream_t near_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p2l = nullptr, ev_m2m = nullptr,
-              ev_down = nullptr, ev_out = nullptr;
+              ev_out = nullptr;
   ~FmmPlan() {
     if (near_stream) cudaStreamDestroy(near_stream);
-    for (cudaEvent_t ev : {ev_fork, ev_join, ev_p2l, ev_m2m, ev_down, ev_out})
+    for (cudaEvent_t ev : {ev_fork, ev_join, ev_p2l, ev_m2m, ev_out})
       if (ev) cudaEventDestroy(ev);
   }
   // tree
@@ -92,6 +92,7 @@ struct FmmPlan {
   std::vector<int> src_leaf_off, xbox_off, vbox_off;
   int q_leaf = 1, q_w = 1;              // largest Q_l among leaves / W-list boxes
   DevBuf<int> cleaf;                    // [n_centres] leaf of each sorted centre
+  int cleaf_pb_max = 0;                 // largest order of a leaf holding centres
   DevBuf<int> tleaf;                    // [n_targets] leaf of each sorted target
   DevBuf<int> dtgt, utgt, wtgt;         // direct targets (sorted indices): all, with
   int n_dtgt = 0, n_utgt = 0, n_wtgt = 0;  // U-list sources, with a W list
