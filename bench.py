@@ -56,8 +56,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from the committed ncu summaries
 # (profiles/), bytes; None until measured for the current kernel version.
 KNOWN_TRAFFIC = {
-    # profiles/m2l_f32_gemm_starfish-k10.md: dram read 26.9 MB + write 55.5 MB per launch
-    ("starfish-k10", "m2l", "fmm", "mixed"): 26.932224e6 + 55.549184e6,
+    # profiles/m2l_f32_gemm_starfish-k10.md: dram read 27.5 MB + write 55.2 MB per launch
+    ("starfish-k10", "m2l", "fmm", "mixed"): 27.461376e6 + 55.244288e6,
 }
 
 
