@@ -89,7 +89,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
 // kGemmRows pairs instead of once per pair). Sums: plain FP32 FMAs over blocks
 // of kGemmBlock terms, blocks added with Kahan compensation. Each pair's result
 // goes to its row of Y (FP32); m2l_f32_reduce_kernel adds each target box's
-// rows in its V-list order in FP64 (deterministic).
+// rows in its V-list order with Kahan compensation (deterministic).
 constexpr int kGemmRows = 16;
 constexpr int kGemmBlock = 8;
 // M2M / L2L levels with fewer parents than kWideLevel use tiles of kNarrowRows
@@ -254,7 +254,9 @@ __global__ void __launch_bounds__(kT) m2l_f32_gemm_kernel(
   }
 }
 
-// lh_lo(b) += conv_lo * sum over b's V entries e (in list order) of Y[row(e)][lo], in FP64.
+// lh_lo(b) += conv_lo * sum over b's V entries e (in list order) of Y[row(e)][lo]:
+// FP32 sums with Kahan compensation (FP32 arithmetic is cheap on this GPU, a
+// conversion to FP64 per element is not), converted and scaled once in FP64.
 __global__ void __launch_bounds__(kT) m2l_f32_reduce_kernel(
     int pbmax, const int* __restrict__ boxes, const int* __restrict__ level,
     const int* __restrict__ lpb, const int* __restrict__ voff, const long long* __restrict__ eyoff,
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kT) m2l_f32_reduce_kernel(
   const double* cv = conv + (size_t)l * (pbmax + 1);
   cd* dst = local + eoff[b];
   for (int lo = threadIdx.x; lo < Q; lo += kT) {
-    cd sum = mk(0.0, 0.0);
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
     const int e1 = voff[b + 1];
     int e = voff[b];
     for (; e + 4 <= e1; e += 4) {  // four loads in flight, added in list order
@@ -275,16 +277,17 @@ __global__ void __launch_bounds__(kT) m2l_f32_reduce_kernel(
       for (int u = 0; u < 4; ++u) y[u] = Y[eyoff[e + u] + lo];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        sum.x += (double)y[u].x;
-        sum.y += (double)y[u].y;
+        kahan_add(sr, cr, y[u].x);
+        kahan_add(si, ci, y[u].y);
       }
     }
     for (; e < e1; ++e) {
       const float2 y = Y[eyoff[e] + lo];
-      sum.x += (double)y.x;
-      sum.y += (double)y.y;
+      kahan_add(sr, cr, y.x);
+      kahan_add(si, ci, y.y);
     }
-    dst[lo] = cadd(dst[lo], cscale(sum, cv[abs(lo - pb)]));
+    const double f = cv[abs(lo - pb)];
+    dst[lo] = cadd(dst[lo], mk(((double)sr - (double)cr) * f, ((double)si - (double)ci) * f));
   }
 }
 
