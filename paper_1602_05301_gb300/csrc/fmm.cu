@@ -560,7 +560,10 @@ __device__ __forceinline__ void deal_sources(const SourceCursor& sc, int lane, F
 }
 
 // L2P: one thread per direct target (sorted index list), from the true local
-// coefficients gamma of its leaf; adds to out.
+// coefficients gamma of its leaf; adds to out. The backward recurrence yields
+// f_m for descending m, so both angular sums run by Horner's rule in
+// z = e^{i th}: A = A conj(z) + f_m gamma_m (m = pb..0) and
+// B = (B + (-1)^m f_m gamma_{-m}) z (m = pb..1), psi = (A + B) / norm.
 __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restrict__ dtgt,
                                                        const int* __restrict__ tleaf, int n,
                                                        cd* __restrict__ out) {
@@ -575,9 +578,7 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
   const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
   const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
   // psi = sum_m f_m [g_m e^{-im th} + (m>0) (-1)^m g_{-m} e^{im th}] / norm
-  cd epb = mk(1.0, 0.0);
-  for (int j = 0; j < pb; ++j) epb = cmul(epb, e1);  // e^{i pb th}
-  cd acc = mk(0.0, 0.0);
+  cd acc;
   double norm;
   if (x < 1e-8) {
     acc = g[pb];  // only J_0 survives
@@ -586,24 +587,31 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
     const double inv = 2.0 / x;
     const int N = miller_start(pb, x);
     double fn1 = 0.0, fn = 1e-200, sum = 0.0;
-    cd e = epb;  // e^{i m th} for the current m (set when m <= pb)
+    cd A = mk(0.0, 0.0), B = mk(0.0, 0.0);
     for (int nn = N; nn >= 1; --nn) {
       const double fm = (double)nn * inv * fn - fn1;  // f_{nn-1}
       if ((nn & 1) == 0) sum += fn;
       const int mm = nn - 1;
       if (mm <= pb) {
-        if (mm < pb) e = cmul(e, cconj(e1));
-        cfma(acc, cscale(g[pb + mm], fm), cconj(e));
-        if (mm > 0) cfma(acc, cscale(g[pb - mm], (mm & 1) ? -fm : fm), e);
+        const cd gp = g[pb + mm];
+        A = mk(fma(A.x, e1.x, fma(A.y, e1.y, fm * gp.x)),
+               fma(A.y, e1.x, fma(-A.x, e1.y, fm * gp.y)));  // A conj(z) + f_m g_m
+        if (mm > 0) {
+          const cd gn = g[pb - mm];
+          const double fs = (mm & 1) ? -fm : fm;
+          B = cmul(mk(fma(fs, gn.x, B.x), fma(fs, gn.y, B.y)), e1);
+        }
       }
       fn1 = fn;
       fn = fm;
       if (fabs(fn) > kRescale) {
         const double sc = 1.0 / kRescale;
         fn *= sc; fn1 *= sc; sum *= sc;
-        acc = cscale(acc, sc);
+        A = cscale(A, sc);
+        B = cscale(B, sc);
       }
     }
+    acc = cadd(A, B);
     norm = fn + 2.0 * sum;
   }
   cd* dst = out + F.tid[i];
@@ -1640,7 +1648,6 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
 }
 
 // L2QBXL at the centres of set C (adds to alpha).
-template <int PM>
 qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSet& C, cd* alpha,
                          cudaStream_t s) {
   if (C.n == 0) return QBX_OK;
@@ -1893,10 +1900,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   TRY(wait(s, f->ev_join));
   if (h->n_ctr > 0) {
     cd* alpha = h->alpha.ptr;
-    if (h->p <= 4) TRY(launch_l2qbxl<4>(F, f, h, C, alpha, s));
-    else if (h->p <= 8) TRY(launch_l2qbxl<8>(F, f, h, C, alpha, s));
-    else if (h->p <= 12) TRY(launch_l2qbxl<12>(F, f, h, C, alpha, s));
-    else TRY(launch_l2qbxl<16>(F, f, h, C, alpha, s));
+    TRY(launch_l2qbxl(F, f, h, C, alpha, s));
   }
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;
