@@ -1785,7 +1785,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   if (h->n_ctr > 0) QBX_CUDA_TRY(cudaMemsetAsync(h->alpha.ptr, 0, (size_t)h->n_ctr * P * sizeof(cd), s2));
   if (h->n_tgt > 0) QBX_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)h->n_tgt * sizeof(cd), s2));
   stage_begin(h, QBX_STAGE_P2L, s2);
-  if ((S || D) && f->n_xbox > 0) {
+  if ((S || D) && f->n_p2l_items > 0) {  // X lists without sources add nothing
     p2l_item_kernel<<<f->n_p2l_items, kThreads, f->p2l_sm, s2>>>(
         F, f->p2l_items.ptr, f->p2l_src.ptr, f->p2l_poff.ptr, f->p2l_part.ptr, (unsigned)f->p2l_sm);
     QBX_KCHECK("p2l", s2);
