@@ -230,6 +230,16 @@ qbx_status qbx_fmm_level_orders(double k, double root_side, int32_t n_levels, in
                                 int32_t p_add, int32_t *pb_out);
 
 /*
+ * The p_add used when a tree descriptor asks for the default (p_add < 0):
+ * Table 2 of the paper (Sec. 8.3, "Maintaining Expansion Accuracy") gives
+ * p_add for the QBX orders p = 2, 4, 6, 8 (5, 5, 15, 20); orders in between
+ * take the value of the next tabulated order, and beyond p = 8 the table's
+ * last ratio p_add / p = 2.5 continues, rounded up (30 at p = 12, 40 at
+ * p = 16). Host computation only; returns -1 for p < 0.
+ */
+int32_t qbx_default_p_add(int32_t p);
+
+/*
  * Measured plan selection. Builds the plan of `desc` (targets, association)
  * for each candidate -- QBX_DIRECT, and QBX_FMM with n_max in {32, 64, 128}
  * -- times `reps` evaluations of each with CUDA events (random unit

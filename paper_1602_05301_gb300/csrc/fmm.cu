@@ -1195,14 +1195,6 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
   }
 }
 
-int p_add_default(int p) {
-  // Table 2 of the paper for p <= 8 (2: 5, 4: 5, 6: 15, 8: 20); 2.5 p beyond
-  if (p <= 4) return 5;
-  if (p <= 6) return 15;
-  if (p <= 8) return 20;
-  return (5 * p + 1) / 2;
-}
-
 }  // namespace
 
 #define TRY(x)                          \
@@ -1242,7 +1234,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   TRY(tree_lists(h, f));
   TRY(tree_associate(h, f, on_node_dev, on_side_dev, eps));
   TRY(gather_sorted(h, f));
-  const int p_add = d->p_add >= 0 ? d->p_add : p_add_default(h->p);
+  const int p_add = d->p_add >= 0 ? d->p_add : qbx_default_p_add(h->p);
   if (f->n_levels > kMaxLevels + 1) {
     set_error("tree has %d levels (at most %d)", f->n_levels, kMaxLevels + 1);
     return QBX_ERR_ARG;

@@ -103,6 +103,8 @@ def library() -> ctypes.CDLL:
             lib.qbx_fmm_level_orders.restype = ctypes.c_int
             lib.qbx_fmm_level_orders.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                                  ctypes.c_int32, ctypes.c_int32, _vp]
+            lib.qbx_default_p_add.restype = ctypes.c_int32
+            lib.qbx_default_p_add.argtypes = [ctypes.c_int32]
             _lib = lib
     return _lib
 
@@ -190,6 +192,11 @@ def qbx_export_tree(handle, n_src, n_ctr, n_tgt):
         pos += n
     out["lists"] = lists
     return out
+
+
+def qbx_default_p_add(p: int) -> int:
+    """p_add chosen for QBX order p when a plan is built with p_add < 0."""
+    return int(library().qbx_default_p_add(int(p)))
 
 
 def qbx_fmm_level_orders(k: float, root_side: float, n_levels: int, p_fmm: int,
