@@ -1541,10 +1541,6 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     }
     QBX_CUDA_TRY(cudaMemcpy(f->p2m_lseg.ptr, lseg.data(), lseg.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
-  // leaves come in level order, so src_leaves does too
-  f->src_leaf_off.assign(f->n_levels + 1, 0);
-  for (int b : src_leaves) f->src_leaf_off[blev[b] + 1] += 1;
-  for (int l = 0; l < f->n_levels; ++l) f->src_leaf_off[l + 1] += f->src_leaf_off[l];
   for (int b = 0; b < f->n_boxes; ++b)
     for (int e = xoff[b]; e < xoff[b + 1]; ++e) p2l += rs[xidx[e]].y - rs[xidx[e]].x;
   {  // P2L work items: each X box's sources, cut into pieces of one row chunk

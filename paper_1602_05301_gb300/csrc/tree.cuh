@@ -88,8 +88,8 @@ struct FmmPlan {
   DevBuf<cd> p2m_part;
   int n_p2m_items = 0;
   size_t p2m_sm = 0;
-  // src_leaves, xbox and vbox are ordered by level; [n_levels + 1] offsets
-  std::vector<int> src_leaf_off, xbox_off, vbox_off;
+  // xbox and vbox are ordered by level; [n_levels + 1] offsets
+  std::vector<int> xbox_off, vbox_off;
   int q_leaf = 1, q_w = 1;              // largest Q_l among leaves / W-list boxes
   DevBuf<int> cleaf;                    // [n_centres] leaf of each sorted centre
   int cleaf_pb_max = 0;                 // largest order of a leaf holding centres
