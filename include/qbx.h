@@ -270,8 +270,8 @@ qbx_status qbx_autotune(qbx_handle *h, const qbx_tree_desc *desc, int32_t precis
  * coefficients re-captures the graph. Synchronous when any pointer is host
  * memory, else asynchronous on cuda_stream. While a handle belongs to a batch
  * (until qbx_batch_destroy), its evaluations favour throughput over the
- * latency of one problem (one stream per handle, thread-per-centre kernels);
- * results are unchanged.
+ * latency of one problem (one stream per handle, wider tiles and more centres
+ * per warp); results are unchanged.
  */
 typedef struct qbx_batch qbx_batch;
 qbx_status qbx_batch_create(int32_t n, qbx_handle *const *handles, int32_t n_streams,
