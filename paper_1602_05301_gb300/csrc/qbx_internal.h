@@ -80,8 +80,8 @@ struct qbx_handle {
   bool planned = false;
   int mode = QBX_DIRECT;
   // Set while the handle belongs to a batch: many problems then run at once,
-  // so an evaluation favours throughput (one stream, thread-per-centre and
-  // wide tiles) over the latency of a single problem.
+  // so an evaluation favours throughput (one stream, 32 centres per L2QBXL
+  // warp, wide tiles) over the latency of a single problem.
   bool batched = false;
   DevBuf<double> tgt_xy;
   DevBuf<int32_t> assoc;                    // [n_tgt] centre or -1
