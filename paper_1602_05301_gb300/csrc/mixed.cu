@@ -207,8 +207,9 @@ __global__ void __launch_bounds__(kT) mpole_to_f32_kernel(
   }
 }
 
-// M2L work items: (tile, first row within the tile, first output order). Each
-// CTA computes kT consecutive output orders (one per thread) of its rows and
+// M2L work items: (first row, rows, first output order, group) over the tiles
+// of kGemmRows rows of one group. Each CTA computes kT consecutive output
+// orders (one per thread) of its rows and
 // stages the source rows through shared memory kChunkK orders at a time, so
 // its footprint does not grow with the box order. kChunkK is a multiple of
 // kGemmBlock: the compensated blocks, and so the result bits, do not depend on
