@@ -102,7 +102,7 @@ qbx_status qbx_geometry_create(const qbx_geometry_desc *desc, qbx_handle **out);
  * node of panel k is <= h_k/4 is an association failure; the rest use direct
  * quadrature.
  * mode: QBX_DIRECT (all pairs) or QBX_FMM (quadtree, Sec. 7).
- * p_fmm, p_add: box expansion orders (Sec. 8.3): p_fmm on the finest tree
+ * p_fmm, p_add: box expansion orders (Sec. 7.1): p_fmm on the finest tree
  * level, larger orders on coarser levels whose boxes span wavelengths (see
  * qbx_fmm_level_orders), each plus p_add; p_add < 0 selects Table 2 of the
  * paper (p <= 8) extended by p_add = 2.5 p beyond it.
@@ -129,7 +129,7 @@ qbx_status qbx_tree_build(qbx_handle *h, const qbx_tree_desc *desc);
 
 /*
  * Evaluates u = cS S[sigma_S] + cD D[sigma_D] at every target (Sec. 7,
- * Stages 2-8 in FMM mode, then QBX evaluation at associated targets, Sec. 2.3
+ * Stages 2-8 in FMM mode, then QBX evaluation at associated targets, Sec. 2.4
  * step 3). sigma_S / sigma_D: complex [n_src] on the source grid; either may be
  * NULL (that layer is absent). out: complex [n_targets]. alpha_out (optional):
  * complex [n_centres][2p+1], l = -p..p, the QBX coefficients of every centre.
@@ -212,7 +212,7 @@ qbx_status qbx_export_tree(const qbx_handle *h, int64_t *info, double *root, int
 qbx_status qbx_get_box_orders(const qbx_handle *h, int32_t *pb_out, int32_t n);
 
 /*
- * Box expansion orders of a quadtree level by level (Sec. 8.3, "Maintaining
+ * Box expansion orders of a quadtree level by level (Sec. 7.1, "Maintaining
  * Expansion Accuracy"). Level l has boxes of side root_side / 2^l and
  * half-side R_l; its outgoing order is the smallest p with
  *   max_{n > p} |H_n(3 k R_l)| max_{y <= sqrt2 k R_l} |J_n(y)| <= eps,
@@ -231,7 +231,7 @@ qbx_status qbx_fmm_level_orders(double k, double root_side, int32_t n_levels, in
 
 /*
  * The p_add used when a tree descriptor asks for the default (p_add < 0):
- * Table 2 of the paper (Sec. 8.3, "Maintaining Expansion Accuracy") gives
+ * Table 2 of the paper (Sec. 7.1, "Maintaining Expansion Accuracy") gives
  * p_add for the QBX orders p = 2, 4, 6, 8 (5, 5, 15, 20); orders in between
  * take the value of the next tabulated order, and beyond p = 8 the table's
  * last ratio p_add / p = 2.5 continues, rounded up (30 at p = 12, 40 at
@@ -292,23 +292,28 @@ void qbx_batch_destroy(qbx_batch *b);
  * 2^19 complex doubles (8 MiB) that the library reserves on every GPU where it
  * is loaded, held until the process exits.
  *
- * Computes, for every target t, the QBX evaluation of Eq. (phiapprox) with the
- * coefficients of centre tgt_centre[t] taken over ALL sources (the direct
- * all-pairs sum of Eq. (localexpcoeffs)) for u = cS S[sigma_S] + cD D[sigma_D]:
- * the same arithmetic as qbx_layer_potential_eval in QBX_DIRECT mode at
- * associated targets. No association is done here; an out-of-range centre
+ * What it computes: for every centre, the local-expansion coefficients
+ * l = -p..p of u = cS S[sigma_S] + cD D[sigma_D] summed directly over ALL
+ * sources (no tree, no far-field approximation); then, at every target t, the
+ * truncated Bessel (J) expansion about centre tgt_centre[t] evaluated at t.
+ * This is the same arithmetic as qbx_layer_potential_eval in QBX_DIRECT mode
+ * at associated targets. No association is done here; an out-of-range centre
  * index gives NaN at that target.
- *  - All pointers are DEVICE memory on the current device (checked): src_xy
- *    [n_src][2], src_normal_xy [n_src][2], src_weight [n_src], sigma_S /
- *    sigma_D complex [n_src] (either may be NULL, not both), ctr_xy
- *    [n_ctr][2], tgt_xy [n_tgt][2], tgt_centre int32 [n_tgt], out complex
- *    [n_tgt].
+ *  - All pointers are DEVICE memory on the current device; host memory and
+ *    memory of another GPU are rejected with QBX_ERR_ARG, the message naming
+ *    the argument: src_xy [n_src][2], src_normal_xy [n_src][2], src_weight
+ *    [n_src], sigma_S / sigma_D complex [n_src] (either may be NULL, not
+ *    both), ctr_xy [n_ctr][2], tgt_xy [n_tgt][2], tgt_centre int32 [n_tgt],
+ *    out complex [n_tgt].
  *  - Limit: 2 * n_src + n_ctr * (2p + 1) <= 2^19; larger problems return
  *    QBX_ERR_ARG with the required size in qbx_last_error(). 0 <= p <= 16.
  *  - Asynchronous on cuda_stream (NULL: legacy default stream).
  *  - The first call on a device looks up the device address of the scratch
- *    array (cudaGetSymbolAddress) and caches it; make that first call before
- *    any stream capture begins.
+ *    array (cudaGetSymbolAddress) and caches it for the life of the process;
+ *    make that first call before any stream capture begins. After
+ *    cudaDeviceReset (or anything else that destroys the device's primary
+ *    context) the cached address is stale: do not call this function again
+ *    in that process.
  *  - Every call on a device shares the one scratch array and leaves its last
  *    contents there; calls whose GPU work overlaps (different streams, no
  *    ordering between them) race on it and must be serialised by the caller.

@@ -12,7 +12,7 @@ Every function computes the plain definition of a quantity of the paper
 * ``direct_potential``       Sec. 3.2 Eq. (gauss-layerpot): smooth Gauss quadrature.
 * ``qbx_evaluate``           Sec. 2.1 Eq. (phiapprox): truncated J-expansion.
 * ``associate``              Sec. 6.1 target association, brute force over all centres.
-* ``layer_potential``        Sec. 2.3 steps 2-3 without acceleration: associate,
+* ``layer_potential``        Sec. 2.4 steps 2-3 without acceleration: associate,
                              then QBX where associated and direct quadrature elsewhere.
 """
 from __future__ import annotations
@@ -57,6 +57,9 @@ def _load():
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
             lib.oracle_bessel.argtypes = [ctypes.c_int, ctypes.c_int64, _D, _D, _D]
+            lib.oracle_set_hankel_recurrence.argtypes = [ctypes.c_int]
+            lib.oracle_hankel_recurrence.restype = ctypes.c_int
+            lib.oracle_hankel_table.argtypes = [ctypes.c_int, ctypes.c_int64, _D, _D]
             lib.oracle_centres.argtypes = [ctypes.c_int64, _D, _D, _I64, _D, ctypes.c_int, _D, _D]
             lib.oracle_qbx_coefficients.argtypes = [
                 ctypes.c_int64, _D, _D, _D, _D, _D,
@@ -98,6 +101,33 @@ def num_threads() -> int:
 
 def set_num_threads(n: int) -> None:
     _load().oracle_set_num_threads(int(n))
+
+
+def set_hankel_recurrence(on: bool) -> None:
+    """Hankel tables of the QBX coefficients: per-order library calls (False,
+    the default) or H_0, H_1 and the upward recurrence (True), the affordable
+    route at 2^20 sources per centre."""
+    _load().oracle_set_hankel_recurrence(1 if on else 0)
+
+
+class hankel_recurrence:
+    """Context manager: QBX coefficients use the Hankel recurrence inside."""
+
+    def __enter__(self):
+        self.prev = _load().oracle_hankel_recurrence()
+        set_hankel_recurrence(True)
+        return self
+
+    def __exit__(self, *a):
+        set_hankel_recurrence(bool(self.prev))
+
+
+def hankel_table(M: int, x) -> np.ndarray:
+    """H_m(x), m = 0..M, as the QBX coefficients form them: [n][M+1] complex."""
+    x = _f64(np.atleast_1d(x))
+    out = np.empty(2 * x.size * (M + 1))
+    _load().oracle_hankel_table(int(M), x.size, _p(x, _D), _p(out, _D))
+    return out.view(np.complex128).reshape(x.size, M + 1)
 
 
 def bessel_j(order: int, x) -> np.ndarray:
@@ -186,7 +216,7 @@ def associate(tgt_xy, node_xy, panel_of_node, panel_h, ctr_xy, ctr_radius, eps_a
 def layer_potential(geom, tgt_xy, p, sigma_S=None, sigma_D=None, cS=1.0, cD=1.0, sides=2,
                     eps_assoc=0.1, on_surface_node=None, on_surface_side=None,
                     centre_of_target=None):
-    """Global QBX evaluation without acceleration (Sec. 2.3, steps 2-3 done directly).
+    """Global QBX evaluation without acceleration (Sec. 2.4, steps 2-3 done directly).
 
     ``geom`` is a dict with node_xy, normal_xy, weight, panel_of_node, panel_h, k.
     If ``centre_of_target`` is given it replaces the oracle's own association

@@ -5,12 +5,14 @@
 // TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the
 // benchmark's CPU-baseline leg may load this library. It shares no code with
 // the CUDA path: every quantity below is computed from its plain definition,
-// with no tree, no translation operator and no recurrence.
+// with no tree and no translation operator.
 //
 // Special functions: every J_l / Y_l value is one call of the C++17 library
 // routines std::cyl_bessel_j / std::cyl_neumann at that order (negative orders
 // by the reflection Z_{-l} = (-1)^l Z_l). H_l = J_l + i Y_l is the Hankel
-// function of the first kind.
+// function of the first kind. For the full-size workloads the Hankel tables of
+// the QBX coefficients may instead come from H_0, H_1 and the upward
+// recurrence (oracle_set_hankel_recurrence; off by default).
 //
 // Conventions (all from Sec. 1 and Sec. 2.1 of the paper):
 //   G(x,y) = (i/4) H_0(k|x-y|)                       Eq. (helmholtz-ker)
@@ -51,10 +53,25 @@ static cplx hankel1(int l, double x) {
   return (l < 0 && (m & 1)) ? -h : h;
 }
 
-// H_m(x) for m = 0..M into h[0..M] (M + 1 library call pairs); the value at a
-// negative order follows by reflection, see hankel_from().
+// How hankel_table() fills orders m >= 2 (oracle_set_hankel_recurrence):
+//  0 (default): one library call pair per order;
+//  1: H_0 and H_1 from the library, then the upward three-term recurrence
+//     H_{m+1}(x) = (2m/x) H_m(x) - H_{m-1}(x) (DLMF 10.6.1). |H_m| grows with m,
+//     so the recurrence keeps every H_m to a few ulps of |H_m|; it is the
+//     affordable route for the full-size workloads (2^20 sources per centre),
+//     and it is checked against the per-order calls and mpmath by the pins.
+static int g_hankel_recurrence = 0;
+
+// H_m(x) for m = 0..M into h[0..M]; the value at a negative order follows by
+// reflection, see hankel_from().
 static void hankel_table(int M, double x, cplx* h) {
-  for (int m = 0; m <= M; ++m) h[m] = hankel1(m, x);
+  if (!g_hankel_recurrence) {
+    for (int m = 0; m <= M; ++m) h[m] = hankel1(m, x);
+    return;
+  }
+  h[0] = hankel1(0, x);
+  if (M >= 1) h[1] = hankel1(1, x);
+  for (int m = 1; m < M; ++m) h[m + 1] = (2.0 * m / x) * h[m] - h[m - 1];
 }
 static inline cplx hankel_from(const cplx* h, int l) {
   int m = l < 0 ? -l : l;
@@ -106,6 +123,22 @@ void oracle_set_num_threads(int n) {
 #else
   (void)n;
 #endif
+}
+
+void oracle_set_hankel_recurrence(int on) { g_hankel_recurrence = on ? 1 : 0; }
+int oracle_hankel_recurrence(void) { return g_hankel_recurrence; }
+
+// H_m(x), m = 0..M, for an array of x as hankel_table() forms them under the
+// current method: h_out [n][M+1] complex (pins only).
+void oracle_hankel_table(int M, int64_t n, const double* x, double* h_out) {
+  std::vector<cplx> h(M + 1);
+  for (int64_t i = 0; i < n; ++i) {
+    hankel_table(M, x[i], h.data());
+    for (int m = 0; m <= M; ++m) {
+      h_out[2 * (i * (M + 1) + m)] = h[m].real();
+      h_out[2 * (i * (M + 1) + m) + 1] = h[m].imag();
+    }
+  }
 }
 
 // Library values of J_l(x) and H_l(x) at one order for an array of x (pins only).

@@ -445,13 +445,16 @@ __global__ void __launch_bounds__(128) qbxl2p_each_kernel(int64_t n_tgt,
   out[t] = u;
 }
 
-bool on_device(const void* p) {
+// True if p is device (or managed) memory that belongs to device `dev`: a
+// pointer into another GPU's memory would be dereferenced through peer access
+// (or fault without it), so it is rejected like host memory.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 template <int PM>
@@ -493,22 +496,12 @@ extern "C" qbx_status qbx_direct_qbx_eval_noalloc(
     return QBX_ERR_ARG;
   }
   const int64_t P = 2 * (int64_t)p + 1;
-  const int64_t need = 2 * n_src + n_ctr * P;
-  if (need > kNoAllocScratch) {
-    set_error("qbx_direct_qbx_eval_noalloc: needs %lld complex scratch values "
-              "(2*n_src + n_ctr*(2p+1)) but the static scratch holds %lld",
-              (long long)need, (long long)kNoAllocScratch);
-    return QBX_ERR_ARG;
-  }
-  const void* dev_ptrs[] = {src_xy, src_normal_xy, src_weight, ctr_xy, tgt_xy, tgt_centre, out};
-  const int64_t sizes[] = {n_src, n_src, n_src, n_ctr, n_tgt, n_tgt, n_tgt};
-  for (int i = 0; i < 7; ++i)
-    if (sizes[i] > 0 && (!dev_ptrs[i] || !on_device(dev_ptrs[i]))) {
-      set_error("qbx_direct_qbx_eval_noalloc: argument %d must be device memory", i);
-      return QBX_ERR_ARG;
-    }
-  if ((sigma_S && !on_device(sigma_S)) || (sigma_D && !on_device(sigma_D))) {
-    set_error("qbx_direct_qbx_eval_noalloc: densities must be device memory");
+  // 2 n_src + n_ctr P <= kNoAllocScratch, checked term by term so that no
+  // product can overflow
+  if (n_src > kNoAllocScratch / 2 || n_ctr > (kNoAllocScratch - 2 * n_src) / P) {
+    set_error("qbx_direct_qbx_eval_noalloc: n_src = %lld and n_ctr = %lld at p = %d need "
+              "2*n_src + n_ctr*(2p+1) complex scratch values but the static scratch holds %lld",
+              (long long)n_src, (long long)n_ctr, p, (long long)kNoAllocScratch);
     return QBX_ERR_ARG;
   }
   int dev = 0;
@@ -517,6 +510,18 @@ extern "C" qbx_status qbx_direct_qbx_eval_noalloc(
     set_error("qbx_direct_qbx_eval_noalloc: device ordinal %d not supported", dev);
     return QBX_ERR_ARG;
   }
+  static const char* const names[] = {"src_xy", "src_normal_xy", "src_weight", "ctr_xy",
+                                      "tgt_xy", "tgt_centre", "out", "sigma_S", "sigma_D"};
+  const void* dev_ptrs[] = {src_xy, src_normal_xy, src_weight, ctr_xy, tgt_xy,
+                            tgt_centre, out, sigma_S, sigma_D};
+  const int64_t sizes[] = {n_src, n_src, n_src, n_ctr, n_tgt, n_tgt, n_tgt,
+                           sigma_S ? n_src : 0, sigma_D ? n_src : 0};
+  for (int i = 0; i < 9; ++i)
+    if (sizes[i] > 0 && (!dev_ptrs[i] || !on_device(dev_ptrs[i], dev))) {
+      set_error("qbx_direct_qbx_eval_noalloc: %s must be device memory on the current "
+                "device (%d)", names[i], dev);
+      return QBX_ERR_ARG;
+    }
   cd* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);

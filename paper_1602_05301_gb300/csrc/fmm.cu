@@ -1239,7 +1239,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     set_error("tree has %d levels (at most %d)", f->n_levels, kMaxLevels + 1);
     return QBX_ERR_ARG;
   }
-  // box order per level (Sec. 8.3): p_fmm on the finest level, more on coarse
+  // box order per level (Sec. 7.1): p_fmm on the finest level, more on coarse
   // levels whose boxes span wavelengths, plus p_add
   f->h_pb.assign(f->n_levels, 0);
   TRY(qbx_fmm_level_orders(h->k, f->side, f->n_levels, std::max(1, d->p_fmm), p_add,

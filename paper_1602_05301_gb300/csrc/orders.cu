@@ -1,4 +1,4 @@
-// Level-dependent FMM expansion orders (Sec. 8.3, "Maintaining Expansion
+// Level-dependent FMM expansion orders (Sec. 7.1, "Maintaining Expansion
 // Accuracy"). For a box of half-side R the outgoing expansion is truncated at
 // the smallest order p for which
 //     max_{rho >= 3R, rho_j <= sqrt2 R, |n| > p} |H_n(k rho) J_n(k rho_j)| <= eps,
@@ -150,7 +150,7 @@ extern "C" qbx_status qbx_fmm_level_orders(double k, double root_side, int32_t n
   return QBX_OK;
 }
 
-// Table 2 (Sec. 8.3) gives p_add for p = 2, 4, 6, 8 (5, 5, 15, 20); the orders
+// Table 2 (Sec. 7.1) gives p_add for p = 2, 4, 6, 8 (5, 5, 15, 20); the orders
 // in between take the value of the next tabulated p, and beyond p = 8 the
 // table's last ratio p_add / p = 2.5 continues (rounded up: 30 at p = 12,
 // 40 at p = 16).

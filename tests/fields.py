@@ -32,7 +32,7 @@ def circle_dlp_mode(n, k, R, xy, side):
 
 class PointSourceField:
     """u(x) = sum_m q_m H_0(k |x - x_m|), radiating, for Green's identity
-    u = D[u] - S[du/dn] outside the curve and 0 inside (Sec. 8.2 of the paper)."""
+    u = D[u] - S[du/dn] outside the curve and 0 inside (Sec. 8.1 of the paper)."""
 
     def __init__(self, k, points, charges):
         self.k = float(k)

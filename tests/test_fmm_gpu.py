@@ -59,7 +59,9 @@ def test_tree_and_lists_match_definitions(qbxmod, n_max):
 
 @pytest.mark.parametrize("layers", ["S", "D", "SD"])
 @pytest.mark.parametrize("p", [4, 12])
-def test_fmm_matches_direct(qbxmod, layers, p):
+def test_fmm_matches_direct(qbxmod, oracle, layers, p):
+    """FMM and direct plans, each layer alone and combined, against each other and
+    against the FP64 oracle (every target; coefficients at a sample of centres)."""
     g, sigma, tgt = _starfish(64, 10.0, 45)
     n = g.n
     tgt = np.concatenate([tgt, g.node_xy[::7], g.node_xy[3::11]])
@@ -85,6 +87,23 @@ def test_fmm_matches_direct(qbxmod, layers, p):
     from scipy.special import jv
     wgt = np.abs(jv(np.arange(-p, p + 1)[None, :], 10.0 * np.concatenate([r, r])[:, None]))
     assert rel_l2(al1 * wgt, al0 * wgt) < TOL64
+    # the oracle, on the shared association
+    with oracle.hankel_recurrence():
+        u_ref, _ = oracle.layer_potential(g.as_dict(), tgt, p, sS, sD, 10j, 1.0, sides=2,
+                                          centre_of_target=a1)
+        cxy, _ = oracle.centres(g.node_xy, g.normal_xy, g.panel_of_node, g.panel_h, 2)
+        cs = np.arange(0, lp_centres(g), 29)
+        al_ref = oracle.qbx_coefficients(g.node_xy, g.normal_xy, g.weight, 10.0, cxy[cs], p,
+                                         sS, sD, 10j, 1.0)
+    for u in (u0, u1):
+        assert rel_l2(u, u_ref) < TOL64
+        assert np.max(np.abs(u - u_ref)) < TOL64 * np.max(np.abs(u_ref))
+    for al in (al0, al1):
+        assert rel_l2(al[cs] * wgt[cs], al_ref * wgt[cs]) < TOL64
+
+
+def lp_centres(g):
+    return 2 * g.n
 
 
 def test_fmm_error_falls_with_box_order(qbxmod):

@@ -1,4 +1,4 @@
-"""Level-dependent box orders (Sec. 8.3, "Maintaining Expansion Accuracy"),
+"""Level-dependent box orders (Sec. 7.1, "Maintaining Expansion Accuracy"),
 computed by the library on the host, checked against the truncation bound
 evaluated independently with mpmath at 50 digits:
   B_n(R) = |H_n(3 k R)| * max_{y <= sqrt2 k R} |J_n(y)|,

@@ -38,6 +38,36 @@ def test_library_bessel_vs_mpmath(oracle):
         assert abs(oracle.bessel_j(l, [x])[0] - jj) <= 1e-13 * abs(hj)
 
 
+def test_hankel_recurrence_vs_mpmath_and_library(oracle):
+    """The optional Hankel tables of the QBX coefficients (H_0, H_1 from the library,
+    then the upward recurrence) against mpmath at 30 digits, from tiny to large
+    arguments, and the coefficients they give against the per-order library calls."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    x = np.array([1e-3, 0.05, 0.7, 3.0, 17.3, 250.0, 2900.0])
+    with oracle.hankel_recurrence():
+        h = oracle.hankel_table(18, x)
+    for i, xi in enumerate(x):
+        ref = np.array([complex(mpmath.hankel1(m, mpmath.mpf(xi))) for m in range(19)])
+        # libstdc++'s H_0, H_1 carry ~2e-13 relative error at x in the hundreds
+        assert np.max(np.abs(h[i] - ref) / np.abs(ref)) < 1e-12, xi
+    h_lib = oracle.hankel_table(18, x)          # default: one library call per order
+    assert np.max(np.abs(h - h_lib) / np.abs(h_lib)) < 1e-12
+    g = discretise_curve(*starfish(0.3, 5), 24, 16, k=10.0)
+    rng = np.random.default_rng(30)
+    sS = rng.standard_normal(g.n) + 1j * rng.standard_normal(g.n)
+    sD = rng.standard_normal(g.n) + 1j * rng.standard_normal(g.n)
+    cxy, crad = oracle.centres(g.node_xy, g.normal_xy, g.panel_of_node, g.panel_h, 2)
+    cs = cxy[::37]
+    a0 = oracle.qbx_coefficients(g.node_xy, g.normal_xy, g.weight, 10.0, cs, 12, sS, sD, 1j, 1.0)
+    with oracle.hankel_recurrence():
+        a1 = oracle.qbx_coefficients(g.node_xy, g.normal_xy, g.weight, 10.0, cs, 12, sS, sD,
+                                     1j, 1.0)
+    assert not oracle._load().oracle_hankel_recurrence()   # the context restored the default
+    wgt = np.abs(sp_jv(np.arange(-12, 13)[None, :], 10.0 * crad[::37][:, None]))
+    assert _rel(a1 * wgt, a0 * wgt) < 1e-12
+
+
 # ---------------------------------------------------------------- Graf / conventions
 def test_graf_expansion_single_source_slp(oracle):
     """alpha of one unit source, evaluated inside the disk, equals (i/4) H_0(k|x-y|)."""
