@@ -1,20 +1,23 @@
 """Benchmark: QBX layer-potential targets/s on one GB300 (and N replicas under torchrun).
 
-Default workload: the starfish r(t) = 1 + 0.3 cos 5t, k = 10, 512 panels x 16
-Gauss-Legendre nodes (8192 sources, 16 384 centres), combined field
-D[s] + i k S[s] with a random complex density of Fourier modes |n| <= 20,
-p = 12, p_fmm = 20, 316 x 316 grid targets on [-2, 2]^2. One step is one
-qbx_layer_potential_eval over all targets with the plan prebuilt and the
-density resident on the device. L2 is flushed (a 256 MiB write) before every
-timed step.
+Default workload (the metric's mixed-vs-FP64 configuration): 200 random
+non-overlapping ellipses in [0, 100]^2, k = 20, 65 536 panels x 16
+Gauss-Legendre nodes (2^20 sources, 2^21 centres), double layer with a random
+complex density, p = 16, p_fmm = 30, 9e5 uniform + 1e5 near-surface targets.
+One step is one qbx_layer_potential_eval over all targets with the plan
+prebuilt and the density resident on the device. Inputs are larger than L2,
+and L2 is flushed (a 256 MiB write) before every timed step anyway.
 
-The headline is the mixed-precision path (FP32 M2L and P2QBXL accumulation,
-FP64 special functions and final sums) at its stated error against the FP64
-path, which is timed on the same plan and inputs and reported beside it, with
-the speedup over the cheapest FP64 plan (lowest p_fmm) of equal accuracy.
+The headline is the mixed-precision path (FP32 M2M/M2L/L2L and P2QBXL
+accumulation, FP64 special functions and final sums) at its stated error
+against the FP64 path, which is timed on the same plan and inputs and
+reported beside it, with the speedup over the fastest FP64 plan of equal
+accuracy. The same line carries the starfish (k = 10) and 256-curve batch
+workloads as extra keys, and the FP64 oracle timed on all host cores and on
+one core.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                  [--mode fmm|direct] [--impl ours|reference]
+                  [--mode fmm|direct] [--impl ours|reference] [--config 2|3|4|5]
 
 --impl reference times the FP64 CPU oracle (the plain, slow definition) on the
 host cores over a bounded sample of the same workload.
@@ -37,7 +40,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QBX-FMM layer-potential targets/sec at stated rel err, mixed vs FP64 on 1 GB300"
 UNIT = "targets/s"
-CONFIG_NUM = 2
+CONFIG_NUM = 5
 WORKLOADS = {2: "%s: starfish r=1+0.3cos5t, k=10, 512 panels x 16 GL (8192 sources, 16384 "
                 "centres), D+ikS with random Fourier density |n|<=20, p=12, p_fmm=20, 316x316 "
                 "grid targets on [-2,2]^2",
@@ -53,12 +56,32 @@ WORKLOADS = {2: "%s: starfish r=1+0.3cos5t, k=10, 512 panels x 16 GL (8192 sourc
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP32 FMA peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM traffic per launch of the dominant kernel from the committed ncu summaries
-# (profiles/), bytes; None until measured for the current kernel version.
-KNOWN_TRAFFIC = {
-    # profiles/m2l_f32_gemm_starfish-k10.md: dram read 27.5 MB + write 55.2 MB per launch
-    ("starfish-k10", "m2l", "fmm", "mixed"): 27.461376e6 + 55.244288e6,
-}
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def known_traffic(stage, workload, precision):
+    """DRAM bytes per launch of a stage's kernels, from a committed ncu summary
+    under profiles/ ("bench-traffic:" lines: stage, workload, precision, bytes,
+    and the sha256 of the kernel's source file when it was captured). None when
+    no summary covers the stage or its source has changed since the capture."""
+    import glob
+    import hashlib
+    for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        for line in open(path):
+            if not line.startswith("bench-traffic:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if (kv.get("stage"), kv.get("workload"), kv.get("precision")) != (stage, workload,
+                                                                              precision):
+                continue
+            src = os.path.join(ROOT, kv.get("source", ""))
+            if not os.path.isfile(src):
+                return None
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+            if sha != kv.get("source_sha256"):
+                return None
+            return float(kv["bytes_per_launch"]), os.path.relpath(path, ROOT)
+    return None
 
 
 # ---------------------------------------------------------------- helpers
@@ -294,7 +317,7 @@ def run_ours(args, w, ws, rank, local):
     if fmm and not args.no_equal_accuracy:
         eq_rows = []
         ks = max(3, args.steps // 4)
-        for pf, pa in [(q, 0) for q in range(8, 52, 4)] + [(w["p_fmm"], -1)]:
+        for pf, pa in [(q, 0) for q in (8, 12, 16, 20, 24, 28, 32)] + [(w["p_fmm"], -1)]:
             lq = qbx.LayerPotential(g.as_dict(), w["p"], sides=w["sides"])
             lq.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"], mode=mode,
                      p_fmm=pf, p_add=pa, n_max=args.n_max, eps_assoc=w["eps_assoc"])
@@ -346,7 +369,7 @@ def run_ours(args, w, ws, rank, local):
         achieved = (f32 if fp32_only else f64 + f32 * FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS) / t / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": roof_ms / per[dom],
-                "traffic": KNOWN_TRAFFIC.get((w["name"], dom, args.mode, args.precision)),
+                "traffic": None, "traffic_source": None,
                 "flops64_per_launch": f64, "flops32_per_launch": f32,
                 "roofline_ms": roof_ms, "ms_per_launch": per[dom],
                 "peak_basis": ("FP32" if fp32_only else "FP64") +
@@ -356,11 +379,30 @@ def run_ours(args, w, ws, rank, local):
                               "achieved is FP64-equivalent (FP32 flops scaled by the peak "
                               "ratio) unless the kernel is FP32 only",
                 "centres_formed": n_used if fmm else stats["n_centres"]}
+        kt = known_traffic(dom, w["name"], args.precision)
+        if kt:
+            roof["traffic"], roof["traffic_source"] = kt
         # the same fraction for every timed stage (flop model over its event time)
         roof["frac_by_stage"] = {
             k: round(1e3 * (flops[k][0] / (FP64_PEAK_TFLOPS * 1e12) +
                             flops[k][1] / (FP32_PEAK_TFLOPS * 1e12)) / per[k], 4)
             for k in per if k in flops and per[k] > 0}
+
+    # the coefficients of every centre (alpha_out on the device): the QBX local
+    # expansion formed at all 2 n centres, not only at those some target uses
+    all_c = None
+    if fmm:
+        alpha_dev = torch.empty((lp.n_centres, 2 * w["p"] + 1), dtype=torch.complex128,
+                                device=dev)
+        out3 = torch.empty_like(out)
+        step_all = lambda: lp.eval(sigma_S=sS, sigma_D=sD, cS=w["cS"], cD=w["cD"], out=out3,
+                                   alpha_out=alpha_dev, precision=prec, stream=sp)
+        ms3, _ = timed_steps(step_all, max(3, args.steps // 4), 2, stream, flush, ws, dev, lp)
+        k3 = max(3, args.steps // 4)
+        all_c = {"value": job_throughput(n_t, ws, k3, ms3), "unit": UNIT,
+                 "ms_per_step": ms3 / k3, "centres_per_s": ws * lp.n_centres * k3 / (ms3 / 1e3),
+                 "n_centres": lp.n_centres}
+        del alpha_dev
 
     # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
     hS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).pin_memory() if sS is not None else None
@@ -396,7 +438,8 @@ def run_ours(args, w, ws, rank, local):
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single"},
                roofline=roof, per_kernel_ms=per, gpu_launches=launches,
-               clocks=clk.summary(), e2e=e2e, equal_accuracy=eq, **comparison)
+               clocks=clk.summary(), e2e=e2e, equal_accuracy=eq, all_centres=all_c,
+               **comparison)
     lp.close()
     return res
 
@@ -474,54 +517,82 @@ def run_batch(args, w, ws, rank, local):
 
 
 # ---------------------------------------------------------------- oracle (CPU) timing
-def oracle_sample(w, assoc, budget_s=12.0, seed=0):
+def oracle_sample(w, assoc, budget_s=12.0, seed=0, max_src_pairs=None):
     """Times the FP64 oracle on a stratified sample of targets (the workload's
-    direct/QBX mix, each target summed over all sources, QBX targets including
-    their centre's coefficients). Returns (targets/s, threads, description)."""
+    direct/QBX mix; a QBX target costs its centre's coefficients plus the
+    evaluation, a direct target its Gauss sum). Every sampled target is summed
+    over every m-th source, m = 1 unless a single target over all sources would
+    take much of the budget (max_src_pairs caps the source count per target);
+    the work per target is linear in the sources, so its time is scaled by m.
+    Returns (targets/s, threads, description)."""
     from oracle import oracle
     g = w["geom"]
     rng = np.random.default_rng(seed)
     qbx_t = np.nonzero(assoc >= 0)[0]
     dir_t = np.nonzero(assoc < 0)[0]
     frac_q = qbx_t.size / max(1, assoc.size)
-    n_q, n_d = 4, 32
-    done_t, elapsed = 0, 0.0
-    t_q = t_d = 0.0
-    nq_done = nd_done = 0
+    m = 1 if not max_src_pairs else max(1, -(-g.n // max_src_pairs))
+    sl = slice(None, None, m)
+    sxy, snr, sw = g.node_xy[sl], g.normal_xy[sl], g.weight[sl]
+    sS = None if w["sigma_S"] is None else w["sigma_S"][sl]
+    sD = None if w["sigma_D"] is None else w["sigma_D"][sl]
+    cxy, _ = oracle.centres(g.node_xy, g.normal_xy, g.panel_of_node, g.panel_h, w["sides"])
+    k = g.k[0]
+    n_q = 1 if g.n > 100000 else 4
+    n_d = 4 if g.n > 100000 else 32
+    elapsed, t_q, t_d, nq_done, nd_done = 0.0, 0.0, 0.0, 0, 0
     while elapsed < budget_s:
-        tq = rng.choice(qbx_t, min(n_q, qbx_t.size), replace=False) if qbx_t.size else []
-        td = rng.choice(dir_t, min(n_d, dir_t.size), replace=False) if dir_t.size else []
-        for ts, is_q in ((tq, True), (td, False)):
-            if len(ts) == 0:
-                continue
+        if qbx_t.size:
+            tq = rng.choice(qbx_t, min(n_q, qbx_t.size), replace=False)
             a = time.perf_counter()
-            oracle.layer_potential(g.as_dict(), w["tgt_xy"][ts], w["p"], w["sigma_S"],
-                                   w["sigma_D"], w["cS"], w["cD"], sides=w["sides"],
-                                   centre_of_target=assoc[ts])
+            al = oracle.qbx_coefficients(sxy, snr, sw, k, cxy[assoc[tq]], w["p"], sS, sD,
+                                         w["cS"], w["cD"])
+            oracle.qbx_evaluate(w["tgt_xy"][tq], np.arange(tq.size, dtype=np.int32),
+                                cxy[assoc[tq]], al, w["p"], k)
             dt = time.perf_counter() - a
-            if is_q:
-                t_q += dt
-                nq_done += len(ts)
-            else:
-                t_d += dt
-                nd_done += len(ts)
+            t_q += dt * m
+            nq_done += tq.size
+            elapsed += dt
+        if dir_t.size:
+            td = rng.choice(dir_t, min(n_d, dir_t.size), replace=False)
+            a = time.perf_counter()
+            oracle.direct_potential(sxy, snr, sw, k, w["tgt_xy"][td], sS, sD, w["cS"], w["cD"])
+            dt = time.perf_counter() - a
+            t_d += dt * m
+            nd_done += td.size
             elapsed += dt
     per_q = t_q / max(1, nq_done)
     per_d = t_d / max(1, nd_done)
     per_t = frac_q * per_q + (1 - frac_q) * per_d
-    desc = ("%d QBX + %d direct targets (of %d; QBX fraction %.4f), each over all %d sources, "
-            "%.1f s of oracle time, extrapolated to the full target mix"
-            % (nq_done, nd_done, assoc.size, frac_q, g.n, elapsed))
+    desc = ("%d QBX + %d direct targets (of %d; QBX fraction %.4f), each summed over every "
+            "%s source of %d (time scaled by %d, the work being linear in the sources), %.1f s "
+            "of oracle time, extrapolated to the full target mix"
+            % (nq_done, nd_done, assoc.size, frac_q, "%d-th" % m if m > 1 else "", g.n, m,
+               elapsed))
     return 1.0 / per_t, oracle.num_threads(), desc
 
 
 def gpu_assoc_free(w):
-    """Association for the CPU-only reference arm: the oracle's own brute force."""
+    """Association for the CPU-only reference arm: the oracle's own brute force,
+    run on the targets that a k-d tree finds within the largest association
+    radius of some centre (the others are direct: the workloads have no target
+    within h/4 of a panel outside every disk, which the GPU plan checks)."""
     from oracle import oracle
+    from scipy.spatial import cKDTree
     g = w["geom"]
     cxy, crad = oracle.centres(g.node_xy, g.normal_xy, g.panel_of_node, g.panel_h, w["sides"])
-    cot, fails = oracle.associate(w["tgt_xy"], g.node_xy, g.panel_of_node, g.panel_h, cxy, crad,
-                                  w["eps_assoc"], w["on_surface_node"], w["on_surface_side"])
+    r_max = (1.0 + w["eps_assoc"]) * crad.max() * (1.0 + 1e-9)
+    d, _ = cKDTree(cxy).query(w["tgt_xy"], k=1, distance_upper_bound=r_max)
+    cand = np.isfinite(d)
+    if w["on_surface_node"] is not None:
+        cand |= w["on_surface_node"] >= 0
+    idx = np.nonzero(cand)[0]
+    cot = np.full(w["tgt_xy"].shape[0], -1, np.int32)
+    osn = None if w["on_surface_node"] is None else w["on_surface_node"][idx]
+    oss = None if w["on_surface_side"] is None else w["on_surface_side"][idx]
+    c, _ = oracle.associate(w["tgt_xy"][idx], g.node_xy, g.panel_of_node, g.panel_h, cxy, crad,
+                            w["eps_assoc"], osn, oss)
+    cot[idx] = c
     return cot
 
 
@@ -533,7 +604,8 @@ def run_reference(args, w):
     desc = ""
     per_step_budget = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
-        v, cores, desc = oracle_sample(w, assoc, budget_s=per_step_budget, seed=i)
+        v, cores, desc = oracle_sample(w, assoc, budget_s=per_step_budget, seed=i,
+                                       max_src_pairs=1 << 18)
         if i >= args.warmup:
             vals.append(v)
     value = float(np.mean(vals))
@@ -560,9 +632,11 @@ def main():
     ap.add_argument("--n-max", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-accuracy", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the starfish and batch workloads of the default line")
     ap.add_argument("--config", type=int, default=CONFIG_NUM, choices=[2, 3, 4, 5],
-                    help="workload (2: the default line; 3, 5: large single geometries; "
-                         "4: the 256-curve batch)")
+                    help="workload (5: the default line, 200 ellipses; 2, 3: starfish k = 10, "
+                         "50; 4: the 256-curve batch)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     from qbx_workloads import make_config
@@ -581,14 +655,34 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     res = run_batch(args, w, ws, rank, local) if args.config == 4 else run_ours(args, w, ws, rank, local)
+    if rank == 0 and ws == 1 and not args.no_extras and args.config == CONFIG_NUM:
+        # the other workloads of the same metric, as extra keys of the line
+        res["extra_workloads"] = {}
+        for num in (2, 4):
+            a2 = argparse.Namespace(**vars(args))
+            a2.config, a2.no_equal_accuracy = num, True
+            a2.steps = max(3, args.steps // 2)
+            w2 = make_config(num)
+            r2 = run_batch(a2, w2, ws, rank, local) if num == 4 else run_ours(a2, w2, ws, rank, local)
+            keep = ("value", "unit", "ms_per_step", "dtype", "rel_err_mixed_vs_fp64", "config",
+                    "fp64", "roofline", "per_kernel_ms", "e2e", "clocks", "gpu_launches",
+                    "all_centres")
+            res["extra_workloads"][w2["name"]] = {k: r2[k] for k in keep if k in r2}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.config != 4:
         from paper_1602_05301_gb300 import qbx
+        from oracle import oracle
         lp = qbx.LayerPotential(w["geom"].as_dict(), w["p"], sides=w["sides"])
         assoc = lp.build(w["tgt_xy"], w["on_surface_node"], w["on_surface_side"])
         lp.close()
-        v, cores, desc = oracle_sample(w, assoc)
+        v, cores, desc = oracle_sample(w, assoc, budget_s=10.0, max_src_pairs=1 << 18)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": desc}
+        n_all = oracle.num_threads()
+        oracle.set_num_threads(1)
+        v1, cores1, desc1 = oracle_sample(w, assoc, budget_s=10.0, seed=1, max_src_pairs=1 << 14)
+        oracle.set_num_threads(n_all)
+        res["cpu_baseline_1core"] = {"value": v1, "unit": UNIT, "cores": cores1, "kind": "oracle",
+                                     "sample": desc1}
     if rank == 0:
         print(json.dumps(res), flush=True)
     if ws > 1:

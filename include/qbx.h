@@ -62,9 +62,21 @@ enum { QBX_DIRECT = 0, QBX_FMM = 1 };          /* how the sums are computed     
  * one per density node and requested side. Centre numbering: the exterior
  * centre of node j is j; with center_sides == 2 the interior centre of node j
  * is n_nodes + j. The source grid carries the quadrature (Sec. 3.2 and
- * Sec. 7, Eq. (QBXFMMpot)); when src_xy is NULL the density grid is the source
- * grid and `weight` gives its weights. Densities passed to eval live on the
- * source grid.
+ * Sec. 7, Eq. (QBXFMMpot)). Three ways to give it:
+ *  - q_src == 0: the density grid is the source grid and `weight` gives its
+ *    weights; densities passed to eval live on it.
+ *  - q_src > 0 with src_xy, src_normal_xy, src_weight: the caller's source grid
+ *    (q_src nodes per panel, same panels); densities passed to eval live on it.
+ *  - q_src > 0 (<= 256) with src_xy, src_normal_xy, src_weight all NULL: the
+ *    library makes the source grid (Sec. 2.2): on each panel the density
+ *    nodes are read as Gauss-Legendre nodes of the panel's reference variable
+ *    u in [-1, 1], positions are interpolated by the degree q-1 polynomial
+ *    through them at q_src Gauss-Legendre nodes, normals are the rotated unit
+ *    tangents of that polynomial (sign of the interpolated caller normals) and
+ *    weights w_j^src |dx/du|. Densities passed to eval then live on the
+ *    DENSITY grid ([n_nodes]) and are interpolated to the source nodes the same
+ *    way before every evaluation. `weight` is not needed. qbx_table1_q_src
+ *    gives the paper's choice of q_src; qbx_get_source_grid exports the grid.
  *
  * All curves of one geometry share the wavenumber k (they form one problem).
  */
@@ -95,8 +107,11 @@ qbx_status qbx_geometry_create(const qbx_geometry_desc *desc, qbx_handle **out);
 /*
  * Targets and evaluation plan (Sec. 6.1 association, Sec. 7 tree and lists).
  * on_surface_node[t] = j >= 0 marks target t as lying on density node j; it
- * then uses the centre of node j on side on_surface_side[t] (+1 exterior,
- * -1 interior; the interior side needs center_sides == 2). Other targets take
+ * then uses the centre of node j on side on_surface_side[t]: +1 the exterior
+ * one-sided limit, -1 the interior one, 0 the on-surface value, the mean of
+ * the two limits (Sec. 2, Eq. (oneside): S* and the principal value D*,
+ * computed from the node's two centres). The interior side and the mean need
+ * center_sides == 2; assoc_out reports the exterior centre for a mean. Other targets take
  * the nearest centre c with |t - c| <= (1 + eps_assoc) h/2 (ties: smaller
  * centre index); a target with no such centre whose distance to some density
  * node of panel k is <= h_k/4 is an association failure; the rest use direct
@@ -104,8 +119,8 @@ qbx_status qbx_geometry_create(const qbx_geometry_desc *desc, qbx_handle **out);
  * mode: QBX_DIRECT (all pairs) or QBX_FMM (quadtree, Sec. 7).
  * p_fmm, p_add: box expansion orders (Sec. 7.1): p_fmm on the finest tree
  * level, larger orders on coarser levels whose boxes span wavelengths (see
- * qbx_fmm_level_orders), each plus p_add; p_add < 0 selects Table 2 of the
- * paper (p <= 8) extended by p_add = 2.5 p beyond it.
+ * qbx_fmm_level_orders), each plus p_add; p_add < 0 selects
+ * qbx_default_p_add(p).
  * n_max: particles per leaf (sources + centres + targets), 0 => 64.
  * assoc_out (optional, [n_targets] int32) receives the centre of every target
  * (-1: direct quadrature).
@@ -230,14 +245,37 @@ qbx_status qbx_fmm_level_orders(double k, double root_side, int32_t n_levels, in
                                 int32_t p_add, int32_t *pb_out);
 
 /*
- * The p_add used when a tree descriptor asks for the default (p_add < 0):
- * Table 2 of the paper (Sec. 7.1, "Maintaining Expansion Accuracy") gives
- * p_add for the QBX orders p = 2, 4, 6, 8 (5, 5, 15, 20); orders in between
- * take the value of the next tabulated order, and beyond p = 8 the table's
- * last ratio p_add / p = 2.5 continues, rounded up (30 at p = 12, 40 at
- * p = 16). Host computation only; returns -1 for p < 0.
+ * The p_add used when a tree descriptor asks for the default (p_add < 0),
+ * for QBX order p (Sec. 7.1, "Maintaining Expansion Accuracy", and Table 2).
+ * The paper sets the box order to p_FMM^l + p_add and finds p_add by
+ * experiment: random curves r = 5 + sum_{j<=12} delta_j sin jt at k = 5,
+ * Green's identity at targets near the boundary, the smallest p' for which
+ * the FMM-accelerated error stays below eps. This library repeats that
+ * experiment with its own orders p_FMM^l (qbx_fmm_level_orders) and returns
+ * the measured values (0, 0, 0, 3, 3, 7, 7, 9, 9, 9, 9, 10, 10, 11, 11, 11, 11
+ * for p = 0..16; Table 2 prints 5, 5, 15, 20 for p = 2, 4, 6, 8 with the
+ * paper's point-FMM orders). Orders above 16 take the value of 16. Host
+ * computation only; returns -1 for p < 0.
  */
 int32_t qbx_default_p_add(int32_t p);
+
+/*
+ * The source grid of the handle (Sec. 2.2): src_xy [n_src][2], src_normal_xy
+ * [n_src][2], src_weight [n_src], n_src = n_panels * q_src (the density grid
+ * when q_src was 0). Host or device outputs; any may be NULL (skipped).
+ * Synchronous. Errors: QBX_ERR_ARG (NULL handle), QBX_ERR_CUDA.
+ */
+qbx_status qbx_get_source_grid(const qbx_handle *h, double *src_xy, double *src_normal_xy,
+                               double *src_weight);
+
+/*
+ * Table 1 of the paper (Sec. 3.2): source nodes per panel q_src for q density
+ * nodes and precision eps, as printed for q = 2, 4, 8, 16 and eps = 1e-3,
+ * 1e-6, 1e-9, 1e-12. Other q take the row of the next tabulated q, other eps
+ * the column of the next tabulated eps at least as strict. Returns -1 for
+ * q outside 1..16 or eps outside [1e-12, inf). Host computation only.
+ */
+int32_t qbx_table1_q_src(int32_t q, double eps);
 
 /*
  * Measured plan selection. Builds the plan of `desc` (targets, association)

@@ -14,6 +14,8 @@ Every function computes the plain definition of a quantity of the paper
 * ``associate``              Sec. 6.1 target association, brute force over all centres.
 * ``layer_potential``        Sec. 2.4 steps 2-3 without acceleration: associate,
                              then QBX where associated and direct quadrature elsewhere.
+* ``source_grid``,           Sec. 2.2: the source discretisation of the same panels and
+  ``interpolate_panels``     the density values on it by polynomial interpolation.
 """
 from __future__ import annotations
 
@@ -244,3 +246,57 @@ def layer_potential(geom, tgt_xy, p, sigma_S=None, sigma_D=None, cS=1.0, cD=1.0,
                                  cxy[used], p, sigma_S, sigma_D, cS, cD)
         u[qbx] = qbx_evaluate(tgt_xy[qbx], inv.astype(np.int32), cxy[used], alpha, p, geom["k"])
     return u, centre_of_target
+
+
+# ---------------------------------------------------------------- source grid (Sec. 2.2)
+def _lagrange(q, q_src):
+    """Lagrange basis of the q Gauss-Legendre nodes on [-1, 1] and its derivative,
+    evaluated at the q_src Gauss-Legendre nodes: L, D [q_src][q]; and the q_src weights.
+    Written out from the product formula l_i(u) = prod_{r != i} (u - x_r) / (x_i - x_r)."""
+    xq, _ = np.polynomial.legendre.leggauss(q)
+    xs, ws = np.polynomial.legendre.leggauss(q_src)
+    L = np.ones((q_src, q))
+    D = np.zeros((q_src, q))
+    for i in range(q):
+        for r in range(q):
+            if r != i:
+                L[:, i] *= (xs - xq[r]) / (xq[i] - xq[r])
+        for s in range(q):
+            if s == i:
+                continue
+            t = np.full(q_src, 1.0 / (xq[i] - xq[s]))
+            for r in range(q):
+                if r != i and r != s:
+                    t *= (xs - xq[r]) / (xq[i] - xq[r])
+            D[:, i] += t
+    return L, D, ws
+
+
+def interpolate_panels(values, q, q_src):
+    """Values at the q density nodes of every panel (panels contiguous) -> values
+    at q_src Gauss-Legendre nodes of the same panels, by the interpolating
+    polynomial of each panel (Sec. 2.2). values: [n_panels * q, ...]."""
+    L, _, _ = _lagrange(q, q_src)
+    v = np.asarray(values)
+    vp = v.reshape((-1, q) + v.shape[1:])
+    out = np.einsum("ji,pi...->pj...", L, vp)
+    return out.reshape((-1,) + v.shape[1:])
+
+
+def source_grid(node_xy, normal_xy, q, q_src):
+    """Source nodes, unit normals and weights of the panels of a density grid
+    (Sec. 2.2): positions interpolated at q_src Gauss-Legendre nodes of each
+    panel's reference variable u, normals the unit tangent dx/du turned by
+    -90 degrees (sign of the interpolated normals), weights w_j |dx/du|."""
+    L, D, ws = _lagrange(q, q_src)
+    xy = np.asarray(node_xy, dtype=np.float64).reshape(-1, q, 2)
+    nr = np.asarray(normal_xy, dtype=np.float64).reshape(-1, q, 2)
+    pos = np.einsum("ji,pic->pjc", L, xy)
+    tan = np.einsum("ji,pic->pjc", D, xy)
+    nin = np.einsum("ji,pic->pjc", L, nr)
+    speed = np.hypot(tan[..., 0], tan[..., 1])
+    nrm = np.stack([tan[..., 1], -tan[..., 0]], -1) / speed[..., None]
+    flip = np.sum(nrm * nin, axis=-1) < 0
+    nrm[flip] *= -1.0
+    w = ws[None, :] * speed
+    return pos.reshape(-1, 2), nrm.reshape(-1, 2), w.reshape(-1)

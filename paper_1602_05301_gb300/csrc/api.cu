@@ -105,12 +105,18 @@ extern "C" qbx_status qbx_geometry_create(const qbx_geometry_desc* d, qbx_handle
     return QBX_ERR_ARG;
   }
   if (!(d->k > 0.0)) { set_error("qbx_geometry_create: k must be > 0"); return QBX_ERR_ARG; }
-  const bool own_src = d->q_src > 0;
-  if (own_src && (!d->src_xy || !d->src_normal_xy || !d->src_weight)) {
-    set_error("qbx_geometry_create: q_src > 0 needs src_xy, src_normal_xy, src_weight");
+  const bool own_src = d->q_src > 0 && d->src_xy != nullptr;
+  const bool upsample = d->q_src > 0 && d->src_xy == nullptr;
+  if (own_src && (!d->src_normal_xy || !d->src_weight)) {
+    set_error("qbx_geometry_create: a source grid needs src_xy, src_normal_xy, src_weight");
     return QBX_ERR_ARG;
   }
-  if (!own_src && !d->weight) {
+  if (upsample && (d->src_normal_xy || d->src_weight || d->q_src > 256)) {
+    set_error("qbx_geometry_create: q_src > 0 without src_xy asks the library to make the "
+              "source grid (q_src <= 256); src_normal_xy and src_weight must then be NULL");
+    return QBX_ERR_ARG;
+  }
+  if (!own_src && !upsample && !d->weight) {
     set_error("qbx_geometry_create: weight is required when the density grid is the source grid");
     return QBX_ERR_ARG;
   }
@@ -140,14 +146,17 @@ extern "C" qbx_status qbx_geometry_create(const qbx_geometry_desc* d, qbx_handle
   h->h_max = hmax;
   h->p = d->p_qbx;
   h->sides = d->center_sides;
-  h->q_src = own_src ? d->q_src : d->q;
+  h->upsample = upsample;
+  h->q_src = (own_src || upsample) ? d->q_src : d->q;
   h->n_src = d->n_panels * h->q_src;
   h->n_ctr = n_nodes * h->sides;
   qbx_status st;
   if ((st = copy_in(h->node_xy, d->node_xy, 2 * n_nodes)) != QBX_OK) return fail(st);
   if ((st = copy_in(h->node_nrm, d->normal_xy, 2 * n_nodes)) != QBX_OK) return fail(st);
   if ((st = copy_in(h->panel_h, d->panel_h, d->n_panels)) != QBX_OK) return fail(st);
-  if (own_src) {
+  if (upsample) {
+    if ((st = upsample_geometry(h)) != QBX_OK) return fail(st);
+  } else if (own_src) {
     if ((st = copy_in(h->src_xy, d->src_xy, 2 * h->n_src)) != QBX_OK) return fail(st);
     if ((st = copy_in(h->src_nrm, d->src_normal_xy, 2 * h->n_src)) != QBX_OK) return fail(st);
     if ((st = copy_in(h->src_w, d->src_weight, h->n_src)) != QBX_OK) return fail(st);
@@ -204,12 +213,21 @@ extern "C" qbx_status qbx_tree_build(qbx_handle* h, const qbx_tree_desc* d) {
                   (long long)on_node[t]);
         return QBX_ERR_ARG;
       }
-      if (on_node[t] >= 0 && !on_side.empty() && on_side[t] < 0 && h->sides < 2) {
-        set_error("qbx_tree_build: target %lld asks for the interior side but the geometry "
-                  "has exterior centres only", (long long)t);
+      if (on_node[t] >= 0 && !on_side.empty() && on_side[t] <= 0 && h->sides < 2) {
+        set_error("qbx_tree_build: target %lld asks for the interior side or the two-sided "
+                  "value but the geometry has exterior centres only", (long long)t);
         return QBX_ERR_ARG;
       }
     }
+  }
+  // side 0: the on-surface value, the mean of both one-sided limits
+  h->has_avg = false;
+  h->avg.release();
+  if (!on_side.empty()) {
+    std::vector<int8_t> avg(h->n_tgt, 0);
+    for (int64_t t = 0; t < h->n_tgt; ++t)
+      if (on_node[t] >= 0 && on_side[t] == 0) avg[t] = 1, h->has_avg = true;
+    if (h->has_avg) QBX_TRY(copy_in(h->avg, avg.data(), avg.size()));
   }
   QBX_TRY(copy_in(h->tgt_xy, d->target_xy, 2 * h->n_tgt));
   QBX_CUDA_TRY(h->assoc.alloc(h->n_tgt));
@@ -283,8 +301,8 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
     if (is_device_ptr(sigma_S)) sS = (const cd*)sigma_S;
     else {
       host_io = true;
-      if (h->sigS_dev.n < (size_t)h->n_src) QBX_CUDA_TRY(h->sigS_dev.alloc(h->n_src));
-      QBX_CUDA_TRY(cudaMemcpyAsync(h->sigS_dev.ptr, sigma_S, h->n_src * sizeof(cd),
+      if (h->sigS_dev.n < (size_t)h->n_density()) QBX_CUDA_TRY(h->sigS_dev.alloc(h->n_density()));
+      QBX_CUDA_TRY(cudaMemcpyAsync(h->sigS_dev.ptr, sigma_S, h->n_density() * sizeof(cd),
                                    cudaMemcpyDefault, s));
       sS = h->sigS_dev.ptr;
     }
@@ -293,8 +311,8 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
     if (is_device_ptr(sigma_D)) sD = (const cd*)sigma_D;
     else {
       host_io = true;
-      if (h->sigD_dev.n < (size_t)h->n_src) QBX_CUDA_TRY(h->sigD_dev.alloc(h->n_src));
-      QBX_CUDA_TRY(cudaMemcpyAsync(h->sigD_dev.ptr, sigma_D, h->n_src * sizeof(cd),
+      if (h->sigD_dev.n < (size_t)h->n_density()) QBX_CUDA_TRY(h->sigD_dev.alloc(h->n_density()));
+      QBX_CUDA_TRY(cudaMemcpyAsync(h->sigD_dev.ptr, sigma_D, h->n_density() * sizeof(cd),
                                    cudaMemcpyDefault, s));
       sD = h->sigD_dev.ptr;
     }
@@ -308,7 +326,10 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
   h->launches = 0;
   h->dbg_err = cudaSuccess;
   stage_begin(h, QBX_STAGE_STRENGTHS, s);
-  QBX_TRY(launch_strengths(h, mk(cS_re, cS_im), sS, mk(cD_re, cD_im), sD, s));
+  if (h->upsample)
+    QBX_TRY(launch_strengths_upsampled(h, mk(cS_re, cS_im), sS, mk(cD_re, cD_im), sD, s));
+  else
+    QBX_TRY(launch_strengths(h, mk(cS_re, cS_im), sS, mk(cD_re, cD_im), sD, s));
   stage_end(h, QBX_STAGE_STRENGTHS, s);
   if (h->mode == QBX_FMM) {
     QBX_TRY(fmm_eval(h, has_S, has_D, o, precision, alpha_out != nullptr, s));

@@ -72,7 +72,7 @@ extern "C" qbx_status qbx_batch_create(int32_t n, qbx_handle* const* handles, in
   b->soff.assign(n + 1, 0);
   b->toff.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
-    b->soff[i + 1] = b->soff[i] + handles[i]->n_src;
+    b->soff[i + 1] = b->soff[i] + handles[i]->n_density();
     b->toff[i + 1] = b->toff[i] + handles[i]->n_tgt;
   }
   const int ns = std::max(1, std::min<int>(n_streams > 0 ? n_streams : 16, n));

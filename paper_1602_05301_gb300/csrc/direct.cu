@@ -174,20 +174,14 @@ __global__ void __launch_bounds__(kTile) p2p_direct_kernel(
   if (active) out[t] = acc;
 }
 
-// u(t) = sum_{|l|<=p} alpha_l J_l(k rho) e^{-i l th},  J_{-m} = (-1)^m J_m
+// u(t) = sum_{|l| <= p} alpha_l(c) J_l(k rho) e^{-i l theta}, (rho, theta) the
+// polar coordinates of t - c (Eq. (phiapprox)); J_{-m} = (-1)^m J_m.
 template <int PM>
-__global__ void __launch_bounds__(128) qbxl2p_kernel(int64_t n_list, const int32_t* __restrict__ list,
-                                                     const double* __restrict__ tgt_xy,
-                                                     const int32_t* __restrict__ assoc,
-                                                     const double* __restrict__ ctr_xy,
-                                                     const cd* __restrict__ alpha, double k,
-                                                     int p, cd* __restrict__ out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_list) return;
-  const int64_t t = list[i];
-  const int64_t c = assoc[t];
-  const double dx = tgt_xy[2 * t] - ctr_xy[2 * c];
-  const double dy = tgt_xy[2 * t + 1] - ctr_xy[2 * c + 1];
+__device__ __forceinline__ cd qbx_local_eval(double tx, double ty, const double* __restrict__ ctr_xy,
+                                             int64_t c, const cd* __restrict__ alpha, double k,
+                                             int p) {
+  const double dx = tx - ctr_xy[2 * c];
+  const double dy = ty - ctr_xy[2 * c + 1];
   const double rho = sqrt(dx * dx + dy * dy);
   const cd e1 = rho > 0.0 ? mk(dx / rho, dy / rho) : mk(1.0, 0.0);
   double J[PM + 1];
@@ -204,6 +198,32 @@ __global__ void __launch_bounds__(128) qbxl2p_kernel(int64_t n_list, const int32
     sgn = -sgn;
     cfma(u, cscale(a[m], J[m]), cconj(e));
     cfma(u, cscale(a[-m], sgn * J[m]), e);
+  }
+  return u;
+}
+
+// QBX evaluation at the associated targets. A target marked in avg (an
+// on-surface target asking for the on-surface value) gets the mean of its
+// node's exterior (assoc) and interior (assoc + n_nodes) one-sided limits
+// (Sec. 2, Eq. (oneside): the two limits differ by the jump of D).
+template <int PM>
+__global__ void __launch_bounds__(128) qbxl2p_kernel(int64_t n_list, const int32_t* __restrict__ list,
+                                                     const double* __restrict__ tgt_xy,
+                                                     const int32_t* __restrict__ assoc,
+                                                     const int8_t* __restrict__ avg,
+                                                     int64_t n_nodes,
+                                                     const double* __restrict__ ctr_xy,
+                                                     const cd* __restrict__ alpha, double k,
+                                                     int p, cd* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_list) return;
+  const int64_t t = list[i];
+  const int64_t c = assoc[t];
+  const double tx = tgt_xy[2 * t], ty = tgt_xy[2 * t + 1];
+  cd u = qbx_local_eval<PM>(tx, ty, ctr_xy, c, alpha, k, p);
+  if (avg && avg[t]) {
+    const cd v = qbx_local_eval<PM>(tx, ty, ctr_xy, c + n_nodes, alpha, k, p);
+    u = mk(0.5 * (u.x + v.x), 0.5 * (u.y + v.y));
   }
   out[t] = u;
 }
@@ -353,18 +373,16 @@ qbx_status launch_qbxl2p(qbx_handle* h, cd* out, cudaStream_t s) {
   const int64_t n = h->n_qbx_tgt;
   if (n == 0) return QBX_OK;
   dim3 g(nblk(n, 128));
-  if (h->p <= 4)
-    qbxl2p_kernel<4><<<g, 128, 0, s>>>(n, h->qbx_tgt_list.ptr, h->tgt_xy.ptr, h->assoc.ptr,
-                                       h->ctr_xy.ptr, h->alpha.ptr, h->k, h->p, out);
-  else if (h->p <= 8)
-    qbxl2p_kernel<8><<<g, 128, 0, s>>>(n, h->qbx_tgt_list.ptr, h->tgt_xy.ptr, h->assoc.ptr,
-                                       h->ctr_xy.ptr, h->alpha.ptr, h->k, h->p, out);
-  else if (h->p <= 12)
-    qbxl2p_kernel<12><<<g, 128, 0, s>>>(n, h->qbx_tgt_list.ptr, h->tgt_xy.ptr, h->assoc.ptr,
-                                        h->ctr_xy.ptr, h->alpha.ptr, h->k, h->p, out);
-  else
-    qbxl2p_kernel<16><<<g, 128, 0, s>>>(n, h->qbx_tgt_list.ptr, h->tgt_xy.ptr, h->assoc.ptr,
-                                        h->ctr_xy.ptr, h->alpha.ptr, h->k, h->p, out);
+  const int8_t* avg = h->has_avg ? h->avg.ptr : nullptr;
+#define QBXL2P_LAUNCH(PM)                                                                  \
+  qbxl2p_kernel<PM><<<g, 128, 0, s>>>(n, h->qbx_tgt_list.ptr, h->tgt_xy.ptr, h->assoc.ptr, \
+                                      avg, h->n_nodes, h->ctr_xy.ptr, h->alpha.ptr, h->k,  \
+                                      h->p, out)
+  if (h->p <= 4) QBXL2P_LAUNCH(4);
+  else if (h->p <= 8) QBXL2P_LAUNCH(8);
+  else if (h->p <= 12) QBXL2P_LAUNCH(12);
+  else QBXL2P_LAUNCH(16);
+#undef QBXL2P_LAUNCH
   QBX_CUDA_TRY(cudaGetLastError());
   h->launches += 1;
   return QBX_OK;

@@ -1071,6 +1071,7 @@ qbx_status configure_kernels() {
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   TRY_MIXED(configure_mixed_kernels(optin));
+  TRY_MIXED(configure_tc_kernels(optin));
   g_smem_optin = optin;
   done.insert(dev);
   return QBX_OK;
@@ -1308,6 +1309,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     return QBX_ERR_ARG;
   }
   TRY(mixed_plan_build(h, f));
+  TRY(tc_plan_build(h, f));
   QBX_CUDA_TRY(f->qs.alloc(std::max<int64_t>(1, h->n_src)));
   QBX_CUDA_TRY(f->ds.alloc(std::max<int64_t>(1, h->n_src)));
   // leaves holding sources (P2M)
@@ -1453,6 +1455,12 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
       for (int64_t i = 0; i < h->n_ctr; ++i) inv[cperm[i]] = (int)i;
       for (int64_t t = 0; t < h->n_tgt; ++t)
         if (ta[t] >= 0) mark[inv[ta[t]]] = 1;
+      if (h->has_avg) {  // two-sided targets also read their node's interior centre
+        std::vector<int8_t> av(h->n_tgt);
+        QBX_CUDA_TRY(cudaMemcpy(av.data(), h->avg.ptr, h->n_tgt, cudaMemcpyDeviceToHost));
+        for (int64_t t = 0; t < h->n_tgt; ++t)
+          if (av[t] && ta[t] >= 0) mark[inv[ta[t] + h->n_nodes]] = 1;
+      }
       for (int64_t i = 0; i < h->n_ctr; ++i)
         if (mark[i]) used.push_back((int)i);
     }
@@ -1853,6 +1861,8 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   stage_begin(h, QBX_STAGE_M2L, s);
   if (mixed) {
     TRY(launch_m2l_f32(h, f, s));
+  } else if (f->tc_any) {
+    TRY(launch_m2l_tc(h, f, s));
   } else {
     TRY(launch_m2l_f64(h, f, s));
   }

@@ -1,0 +1,620 @@
+// M2L of the FP64 path (Sec. 7.2, Stage 4) on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory).
+//
+// The translation of one (level, offset class) is a dense complex Q x Q matrix
+// applied to the multipoles of every V-list source of that class. It is done
+// on the sigma-normalised operators of the mixed path (entries of order one
+// or smaller, so that a bound relative to the largest entry of a row is also a
+// relative one), written as a real 2Q x 2Q matrix A acting on the real vector
+// x = (Re mu, Im mu). FP64 accuracy comes from an error-free split into bf16
+// slices (the Ozaki scheme: Ozaki, Ogita, Oishi, Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59 (2012)):
+//
+//  * every matrix row j is scaled by 2^-f_j and every vector by 2^-e so that
+//    its largest entry lies in [1/4, 1/2); the scaled value times 2^(beta S) is
+//    rounded to an integer Z and written in S signed base-2^beta digits,
+//    Z = sum_i d_i 2^(beta (S - i)), |d_i| <= 2^(beta-1): each digit is a bf16
+//    integer, exact;
+//  * the products of digit slices (i, j) with i + j = s carry the same weight
+//    2^(-beta s); for each s = 2 .. S + 1 one TMEM accumulator sums all of them
+//    over k. Every partial sum is an integer of magnitude at most
+//    S K 2^(2 beta - 2) <= 2^24, so the FP32 accumulation is exact;
+//  * the S group sums are combined in float-float (two FP32 words, 48 bits),
+//    scaled by 2^(e + f_j), added over each target box's V list in
+//    float-float, and converted to FP64 once per coefficient.
+// Slice pairs with i + j > S + 1 are dropped: the truncation error is about
+// S 2^(-beta S) of the largest term, 2^-46 or below for the (beta, S) used
+// (beta S >= 48).
+//
+// Work mapping: a CTA takes 128 V pairs of one group (the MMA's M) and 64 real
+// output orders (N = 64). Operand tiles of 32 input orders (two MMAs of K = 16)
+// are staged through shared memory in the no-swizzle K-major layout (8 x 16-byte
+// core matrices), double-buffered; one thread issues the MMAs, an mbarrier
+// tracks their completion (tcgen05.commit), and all waits are bounded.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "tree.cuh"
+#include "m2l_entry.cuh"
+
+namespace {
+
+constexpr int kRows = 128;      // V pairs per CTA (MMA M)
+constexpr int kNC = 64;         // real outputs per CTA (MMA N)
+constexpr int kKC = 32;         // real inputs per staging chunk
+constexpr int kPad = 64;        // 2Q is padded to a multiple of this (K and N)
+constexpr int kThr = 128;
+constexpr long long kSpin = 1LL << 26;  // bound on every mbarrier wait
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: no swizzle, K-major; lbo = byte distance of
+// core matrices adjacent in K, sbo = of core matrices adjacent in M/N
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor of kind::f16: bf16 A and B (K-major), f32 D, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t id,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(id), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar)));
+}
+// bounded wait for the given phase parity of an mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- float-float
+// s + e = a + b exactly (Knuth's TwoSum; additions only, so no contraction)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) += (bh, bl), renormalised
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e += lo + bl;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// ---------------------------------------------------------------- slicing
+// The S signed base-2^beta digits of rint(x 2^(beta S - e)) (|x| 2^-e < 1/2),
+// most significant first, as bf16 (exact: |d| <= 2^(beta - 1) <= 128): the
+// lower S - 1 digits in [-2^(beta-1), 2^(beta-1)), the top one whatever is left,
+// which is at most 2^(beta - 1) in magnitude since |rint(x 2^(beta S - e))| <=
+// 2^(beta S - 1).
+__device__ __forceinline__ void split_digits(double x, int e, int beta, int S,
+                                             __nv_bfloat16* __restrict__ out, size_t stride) {
+  long long Z = __double2ll_rn(ldexp(x, beta * S - e));
+  const long long half = 1LL << (beta - 1), mask = (1LL << beta) - 1;
+  for (int i = S - 1; i >= 1; --i) {
+    long long d = Z & mask;
+    if (d >= half) d -= mask + 1;
+    Z = (Z - d) >> beta;
+    out[(size_t)i * stride] = __float2bfloat16_rn((float)d);
+  }
+  // the top digit takes the rest, |Z| <= 2^(beta - 1) (no carry is dropped)
+  out[0] = __float2bfloat16_rn((float)Z);
+}
+// exponent e with max_abs 2^-e in [1/4, 1/2) (0 for max_abs == 0)
+__device__ __forceinline__ int scale_exponent(double max_abs) {
+  if (!(max_abs > 0.0)) return 0;
+  int E;
+  frexp(max_abs, &E);  // max_abs = m 2^E, m in [1/2, 1)
+  return E + 1;
+}
+
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+  __syncthreads();
+  return m;
+}
+
+// Matrix slices of one group (level l, class cls), row j of the real form:
+//   A[j][k] = Re T[n][lo] (j < Q, k < Q), -Im T[n][lo] (j < Q, k >= Q),
+//             Im T[n][lo] (j >= Q, k < Q), Re T[n][lo] (j >= Q, k >= Q),
+// lo = j mod Q, n = k mod Q, T the sigma-normalised M2L matrix; zero padding.
+// Grid (used groups, Np), threads over k. Slices [S][Np][Kp] at aoff.
+__global__ void __launch_bounds__(kThr) tc_matrix_kernel(
+    const int* __restrict__ groups, const long long* __restrict__ aoff,
+    const long long* __restrict__ foff, const int4* __restrict__ lvl, const int* __restrict__ lpb,
+    int pbmax, const cd* __restrict__ t_m2l, const double* __restrict__ scale,
+    const double* __restrict__ lsig, __nv_bfloat16* __restrict__ A, int* __restrict__ fexp) {
+  __shared__ double red[kThr / 32];
+  const int g = groups[blockIdx.x];
+  const int l = g / 49, cls = g % 49;
+  const int4 P = lvl[l];  // (use, beta, S, Kp)
+  const int Kp = P.w, beta = P.y, S = P.z;
+  const int pb = lpb[l], Q = 2 * pb + 1;
+  const int j = blockIdx.y;
+  if (j >= Kp) return;
+  const int lo = (j < Q ? j : j - Q) - pb;
+  const bool im_out = j >= Q;
+  const M2lNorm nm(t_m2l, scale, lsig, l, cls, pbmax);
+  double vals[16];  // k = threadIdx.x + 128 t, Kp <= 2048
+  double m = 0.0;
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    double v = 0.0;
+    if (j < 2 * Q && k < 2 * Q) {
+      const int n = (k < Q ? k : k - Q) - pb;
+      const cd T = nm.entry(n, lo);
+      const bool im_in = k >= Q;
+      v = im_out ? (im_in ? T.x : T.y) : (im_in ? -T.y : T.x);
+    }
+    vals[t] = v;
+    m = fmax(m, fabs(v));
+  }
+  m = block_max(m, red);
+  const int e = scale_exponent(m);
+  if (threadIdx.x == 0) fexp[foff[blockIdx.x] + j] = e;
+  __nv_bfloat16* dst = A + aoff[blockIdx.x] + (size_t)j * Kp;
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    if (k < Kp) split_digits(vals[t], e, beta, S, dst + k, (size_t)Kp * Kp);
+  }
+}
+
+// Vector slices of the V-list sources: mu_n = mh_n conv_|n| (FP64), x = (Re mu,
+// Im mu) padded to Kp, one exponent per box. One block per box.
+__global__ void __launch_bounds__(kThr) tc_mu_kernel(
+    const int* __restrict__ boxes, const int* __restrict__ level, const int* __restrict__ lpb,
+    const long long* __restrict__ eoff, const double* __restrict__ conv, int pbmax,
+    const int4* __restrict__ lvl, const cd* __restrict__ mpole, const long long* __restrict__ xoff,
+    __nv_bfloat16* __restrict__ X, int* __restrict__ xexp) {
+  __shared__ double red[kThr / 32];
+  const int b = boxes[blockIdx.x];
+  const int l = level[b];
+  const int4 P = lvl[l];
+  const int Kp = P.w, beta = P.y, S = P.z;
+  const int pb = lpb[l], Q = 2 * pb + 1;
+  const double* cv = conv + (size_t)l * (pbmax + 1);
+  const cd* a = mpole + eoff[b];
+  double vals[16];  // Kp <= 2048
+  double m = 0.0;
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    double v = 0.0;
+    if (k < 2 * Q) {
+      const int n = k < Q ? k : k - Q;
+      const cd c = a[n];
+      v = (k < Q ? c.x : c.y) * cv[abs(n - pb)];
+    }
+    vals[t] = v;
+    m = fmax(m, fabs(v));
+  }
+  m = block_max(m, red);
+  const int e = scale_exponent(m);
+  if (threadIdx.x == 0) xexp[blockIdx.x] = e;
+  __nv_bfloat16* dst = X + xoff[blockIdx.x];
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    if (k < Kp) split_digits(vals[t], e, beta, S, dst + k, (size_t)Kp);
+  }
+}
+
+// The tile product. Item (first row, rows, first output, group). Y receives, for
+// each pair row and complex output lo, (Re hi, Re lo, Im hi, Im lo) as float4 at
+// yoff[row] + lo: the float-float value of (A x)_j 2^(e + f_j).
+template <int S>
+__global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
+    const int4* __restrict__ items, const int4* __restrict__ lvl, const int* __restrict__ lpb,
+    const long long* __restrict__ gaoff, const long long* __restrict__ gfoff,
+    const __nv_bfloat16* __restrict__ A, const int* __restrict__ fexp,
+    const int* __restrict__ rowsrc, const long long* __restrict__ xoff,
+    const int* __restrict__ xexp, const __nv_bfloat16* __restrict__ X,
+    const long long* __restrict__ yoff, cd* __restrict__ Y, int* __restrict__ err) {
+  constexpr int XT = kRows * kKC;             // elements of one X slice tile
+  constexpr int AT = kNC * kKC;               // elements of one A slice tile
+  constexpr int STAGE = S * (XT + AT);        // elements of one stage
+  constexpr uint32_t LBO = 128;               // core matrices adjacent in K: contiguous
+  constexpr uint32_t SBO = (kKC / 8) * 128;   // next 8-row group
+  constexpr uint32_t ID = idesc_bf16(kRows, kNC);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 I = items[blockIdx.x];
+  const int row0 = I.x, nr = I.y, n0 = I.z, g = I.w;
+  const int l = g / 49;
+  const int Kp = lvl[l].w, beta = lvl[l].y;
+  const int Q = 2 * lpb[l] + 1;
+  const __nv_bfloat16* Ag = A + gaoff[g];
+  const int* fg = fexp + gfoff[g];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    for (int b = 0; b < 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int nchunks = Kp / kKC;
+  uint32_t acc_started = 0;  // accumulators written at least once (issuing thread)
+  bool ok = true;
+  for (int c = 0; c < nchunks && ok; ++c) {
+    const int b = c & 1;
+    if (c >= 2) {  // the MMAs that read this buffer (chunk c - 2) are complete
+      if (!mbar_wait(&mbar[b], ((c - 2) >> 1) & 1)) atomicExch(&s_fail, 1);
+      __syncthreads();
+      if (s_fail) { ok = false; break; }
+    }
+    __nv_bfloat16* xs = stg + (size_t)b * STAGE;
+    __nv_bfloat16* as = xs + S * XT;
+    const int k0 = c * kKC;
+    // X: rows m of the tile, slice t, 16-byte piece q (8 inputs): element
+    // (m, k) of slice t goes to core (m/8, k/8), row m%8
+    for (int i = tid; i < kRows * S * 4; i += kThr) {
+      const int q = i & 3, t = (i >> 2) % S, m = (i >> 2) / S;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (m < nr) {
+        const int rs = rowsrc[row0 + m];
+        v = *reinterpret_cast<const uint4*>(X + xoff[rs] + (size_t)t * Kp + k0 + q * 8);
+      }
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(xs + t * XT) + (m >> 3) * SBO + q * LBO +
+                                (m & 7) * 16) = v;
+    }
+    for (int i = tid; i < kNC * S * 4; i += kThr) {
+      const int q = i & 3, t = (i >> 2) % S, j = (i >> 2) / S;
+      const uint4 v = *reinterpret_cast<const uint4*>(
+          Ag + ((size_t)t * Kp + (n0 + j)) * Kp + k0 + q * 8);
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(as + t * AT) + (j >> 3) * SBO + q * LBO +
+                                (j & 7) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int ti = 0; ti < S; ++ti) {
+#pragma unroll
+        for (int tj = 0; tj < S - ti; ++tj) {
+          const int a = ti + tj;  // weight 2^(-beta (a + 2))
+#pragma unroll
+          for (int kk = 0; kk < kKC; kk += 16) {
+            const uint64_t da = smem_desc(smem_u32(xs + ti * XT) + (kk / 8) * LBO, LBO, SBO);
+            const uint64_t db = smem_desc(smem_u32(as + tj * AT) + (kk / 8) * LBO, LBO, SBO);
+            mma_bf16(tmem + a * kNC, da, db, ID, (acc_started >> a) & 1u);
+            acc_started |= 1u << a;
+          }
+        }
+      }
+      mma_commit(&mbar[b]);
+    }
+  }
+  // all MMAs complete: the last commit of each buffer
+  if (ok) {
+    for (int c = std::max(0, nchunks - 2); c < nchunks; ++c)
+      if (!mbar_wait(&mbar[c & 1], (c >> 1) & 1)) atomicExch(&s_fail, 1);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    // epilogue: warp w holds rows 32w .. 32w + 31 (TMEM lanes)
+    const int m = warp * 32 + lane;
+    const bool row_ok = m < nr;
+    const int e_row = row_ok ? xexp[rowsrc[row0 + m]] : 0;
+    const long long yo = row_ok ? yoff[row0 + m] : 0;
+    for (int j0 = 0; j0 < kNC; j0 += 16) {
+      float hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.f;
+#pragma unroll
+      for (int a = S - 1; a >= 0; --a) {  // smallest weight first
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + a * kNC + j0, v);
+        const int sh = -beta * (a + 2);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) ff_add(hi[c], lo[c], ldexpf(v[c], sh), 0.f);
+      }
+      if (row_ok) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = n0 + j0 + c;
+          if (j >= 2 * Q) break;
+          const int sc = e_row + fg[j];
+          const float2 w = make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));
+          float2* dst = reinterpret_cast<float2*>(Y + yo + (j < Q ? j : j - Q)) + (j < Q ? 0 : 1);
+          *dst = w;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// lh_lo(b) += conv_lo * sum over b's V entries of the row values: float-float
+// sums (tensor-core levels) or FP64 sums (the others), in V-list order.
+__global__ void __launch_bounds__(kThr) m2l_tc_reduce_kernel(
+    int pbmax, const int* __restrict__ boxes, const int* __restrict__ level,
+    const int* __restrict__ lpb, const int4* __restrict__ lvl, const int* __restrict__ voff,
+    const long long* __restrict__ eyoff, const cd* __restrict__ Y,
+    const double* __restrict__ conv, const long long* __restrict__ eoff, cd* __restrict__ local) {
+  const int b = boxes[blockIdx.x];
+  const int l = level[b];
+  const int pb = lpb[l], Q = 2 * pb + 1;
+  cd* dst = local + eoff[b];
+  const int e0 = voff[b], e1 = voff[b + 1];
+  if (lvl[l].x) {
+    const double* cv = conv + (size_t)l * (pbmax + 1);
+    for (int lo = threadIdx.x; lo < Q; lo += kThr) {
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      for (int e = e0; e < e1; ++e) {
+        const float4 y = reinterpret_cast<const float4*>(Y)[eyoff[e] + lo];
+        ff_add(rh, rl, y.x, y.y);
+        ff_add(ih, il, y.z, y.w);
+      }
+      const double f = cv[abs(lo - pb)];
+      dst[lo] = cadd(dst[lo], mk(((double)rh + (double)rl) * f, ((double)ih + (double)il) * f));
+    }
+  } else {
+    for (int lo = threadIdx.x; lo < Q; lo += kThr) {
+      cd sum = mk(0.0, 0.0);
+      for (int e = e0; e < e1; ++e) sum = cadd(sum, Y[eyoff[e] + lo]);
+      dst[lo] = cadd(dst[lo], sum);
+    }
+  }
+}
+
+template <int S>
+size_t tc_smem_bytes() {
+  return (size_t)2 * S * (kRows * kKC + kNC * kKC) * sizeof(__nv_bfloat16);
+}
+
+// (beta, S) for a padded width Kp: the most bits per digit for which
+// S Kp 2^(2 beta - 2) <= 2^24 (exact FP32 sums) with beta S >= 48; 0 if none.
+int2 tc_params(int Kp) {
+  if (Kp <= 128) return make_int2(8, 6);
+  if (Kp <= 576) return make_int2(7, 7);
+  if (Kp <= 2048) return make_int2(6, 8);
+  return make_int2(0, 0);
+}
+
+}  // namespace
+
+qbx_status configure_tc_kernels(int smem_optin) {
+  const void* k[] = {(const void*)m2l_tc_kernel<6>, (const void*)m2l_tc_kernel<7>,
+                     (const void*)m2l_tc_kernel<8>};
+  const size_t need[] = {tc_smem_bytes<6>(), tc_smem_bytes<7>(), tc_smem_bytes<8>()};
+  for (int i = 0; i < 3; ++i) {
+    if (need[i] + 1024 > (size_t)smem_optin) {
+      set_error("tensor-core M2L needs %zu bytes of shared memory (device: %d)", need[i],
+                smem_optin);
+      return QBX_ERR_ARG;
+    }
+    QBX_CUDA_TRY(cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)need[i]));
+  }
+  return QBX_OK;
+}
+
+// Plan-time part: per-level (use, beta, S, Kp), the matrix slices of every
+// group with V pairs on a tensor-core level, the vector-slice room of every
+// V-list source there, and the work items. Levels whose 2Q is too wide for
+// exact FP32 sums keep the FP64 CUDA-core GEMM (its items are filtered here).
+qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
+  (void)h;
+  const int nl = f->n_levels, ng = nl * 49;
+  std::vector<int4> lv(nl, make_int4(0, 0, 0, 0));
+  for (int l = 2; l < nl; ++l) {
+    if (f->vbox_off[l + 1] == f->vbox_off[l]) continue;
+    const int Q = 2 * f->h_pb[l] + 1;
+    const int Kp = (2 * Q + kPad - 1) / kPad * kPad;
+    const int2 bs = tc_params(Kp);
+    if (bs.x > 0) lv[l] = make_int4(1, bs.x, bs.y, Kp);
+  }
+  // QBX_M2L_TENSOR=0 in the environment keeps every level on the FP64
+  // CUDA-core GEMM (for comparisons); the default is the tensor-core path
+  {
+    const char* env = getenv("QBX_M2L_TENSOR");
+    if (env && env[0] == '0')
+      for (auto& v : lv) v = make_int4(0, 0, 0, 0);
+  }
+  f->h_tc_lvl = lv;
+  {  // FP64 GEMM items of the levels left to the CUDA-core path
+    std::vector<int4> rest;
+    for (const int4& it : f->h_items64)
+      if (!lv[it.w / 49].x) rest.push_back(it);
+    f->n_m2l_items64_rest = (int)rest.size();
+    QBX_CUDA_TRY(f->m2l_items64_rest.alloc(std::max<size_t>(1, rest.size())));
+    if (!rest.empty())
+      QBX_CUDA_TRY(cudaMemcpy(f->m2l_items64_rest.ptr, rest.data(), rest.size() * sizeof(int4),
+                              cudaMemcpyHostToDevice));
+  }
+  QBX_CUDA_TRY(f->tc_lvl.alloc(nl));
+  QBX_CUDA_TRY(cudaMemcpy(f->tc_lvl.ptr, lv.data(), nl * sizeof(int4), cudaMemcpyHostToDevice));
+  // groups with rows on tensor-core levels
+  std::vector<int> groups;
+  std::vector<long long> aoff(ng, 0), foff(ng, 0), g_aoff, g_foff;
+  long long atot = 0, ftot = 0;
+  for (int g = 0; g < ng; ++g) {
+    const int l = g / 49;
+    if (!lv[l].x || f->h_gcount[g + 1] == f->h_gcount[g]) continue;
+    const long long Kp = lv[l].w, S = lv[l].z;
+    groups.push_back(g);
+    aoff[g] = atot;
+    foff[g] = ftot;
+    g_aoff.push_back(atot);
+    g_foff.push_back(ftot);
+    atot += S * Kp * Kp;
+    ftot += Kp;
+  }
+  f->tc_any = !groups.empty();
+  if (!f->tc_any) return QBX_OK;
+  QBX_CUDA_TRY(f->tc_A.alloc(atot));
+  QBX_CUDA_TRY(f->tc_fexp.alloc(ftot));
+  QBX_CUDA_TRY(f->tc_gaoff.alloc(ng));
+  QBX_CUDA_TRY(f->tc_gfoff.alloc(ng));
+  QBX_CUDA_TRY(cudaMemcpy(f->tc_gaoff.ptr, aoff.data(), ng * 8, cudaMemcpyHostToDevice));
+  QBX_CUDA_TRY(cudaMemcpy(f->tc_gfoff.ptr, foff.data(), ng * 8, cudaMemcpyHostToDevice));
+  {
+    DevBuf<int> dg;
+    DevBuf<long long> da, df;
+    QBX_CUDA_TRY(dg.alloc(groups.size()));
+    QBX_CUDA_TRY(da.alloc(groups.size()));
+    QBX_CUDA_TRY(df.alloc(groups.size()));
+    QBX_CUDA_TRY(cudaMemcpy(dg.ptr, groups.data(), groups.size() * 4, cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(cudaMemcpy(da.ptr, g_aoff.data(), groups.size() * 8, cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(cudaMemcpy(df.ptr, g_foff.data(), groups.size() * 8, cudaMemcpyHostToDevice));
+    int kpmax = 0;  // <= 2048 = 16 entries per thread (tc_params)
+    for (int l = 0; l < nl; ++l) kpmax = std::max(kpmax, lv[l].w);
+    dim3 grid((unsigned)groups.size(), (unsigned)kpmax);
+    tc_matrix_kernel<<<grid, kThr>>>(dg.ptr, da.ptr, df.ptr, f->tc_lvl.ptr, f->lpb.ptr,
+                                     f->pb_max, f->t_m2l.ptr, f->scale.ptr, f->lsig.ptr,
+                                     reinterpret_cast<__nv_bfloat16*>(f->tc_A.ptr),
+                                     f->tc_fexp.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+    QBX_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  // vector-slice room per V-list source on a tensor-core level
+  std::vector<int> vsrc(std::max(1, f->n_vsrc)), blev(f->n_boxes);
+  if (f->n_vsrc)
+    QBX_CUDA_TRY(cudaMemcpy(vsrc.data(), f->m2l_vsrc.ptr, f->n_vsrc * 4, cudaMemcpyDeviceToHost));
+  QBX_CUDA_TRY(cudaMemcpy(blev.data(), f->box.level.ptr, f->n_boxes * 4, cudaMemcpyDeviceToHost));
+  std::vector<int> tbox, pos_of(f->n_boxes, -1);
+  std::vector<long long> xoff;
+  long long xtot = 0;
+  for (int i = 0; i < f->n_vsrc; ++i) {
+    const int b = vsrc[i], l = blev[b];
+    if (!lv[l].x) continue;
+    pos_of[b] = (int)tbox.size();
+    tbox.push_back(b);
+    xoff.push_back(xtot);
+    xtot += (long long)lv[l].z * lv[l].w;
+  }
+  f->n_tc_src = (int)tbox.size();
+  QBX_CUDA_TRY(f->tc_src.alloc(std::max<size_t>(1, tbox.size())));
+  QBX_CUDA_TRY(f->tc_xoff.alloc(std::max<size_t>(1, xoff.size())));
+  QBX_CUDA_TRY(f->tc_xexp.alloc(std::max<size_t>(1, tbox.size())));
+  QBX_CUDA_TRY(f->tc_X.alloc(std::max<long long>(1, xtot)));
+  if (!tbox.empty()) {
+    QBX_CUDA_TRY(cudaMemcpy(f->tc_src.ptr, tbox.data(), tbox.size() * 4, cudaMemcpyHostToDevice));
+    QBX_CUDA_TRY(cudaMemcpy(f->tc_xoff.ptr, xoff.data(), xoff.size() * 8, cudaMemcpyHostToDevice));
+  }
+  // rows: position of their source among the tensor-core sources; items
+  const size_t nrows = f->h_row_src.size();
+  std::vector<int> rowsrc(std::max<size_t>(1, nrows), -1);
+  for (size_t r = 0; r < nrows; ++r) rowsrc[r] = pos_of[f->h_row_src[r]];
+  QBX_CUDA_TRY(f->tc_rowsrc.alloc(rowsrc.size()));
+  QBX_CUDA_TRY(cudaMemcpy(f->tc_rowsrc.ptr, rowsrc.data(), rowsrc.size() * 4, cudaMemcpyHostToDevice));
+  std::vector<int4> items[3];  // by S = 6, 7, 8
+  for (int g : groups) {
+    const int l = g / 49, S = lv[l].z, Kp = lv[l].w;
+    const int Q = 2 * f->h_pb[l] + 1;
+    for (int64_t r = f->h_gcount[g]; r < f->h_gcount[g + 1]; r += kRows)
+      for (int n0 = 0; n0 < 2 * Q && n0 < Kp; n0 += kNC)
+        items[S - 6].push_back(make_int4((int)r, (int)std::min<int64_t>(kRows, f->h_gcount[g + 1] - r),
+                                         n0, g));
+  }
+  for (int s = 0; s < 3; ++s) {
+    f->n_tc_items[s] = (int)items[s].size();
+    QBX_CUDA_TRY(f->tc_items[s].alloc(std::max<size_t>(1, items[s].size())));
+    if (!items[s].empty())
+      QBX_CUDA_TRY(cudaMemcpy(f->tc_items[s].ptr, items[s].data(), items[s].size() * sizeof(int4),
+                              cudaMemcpyHostToDevice));
+  }
+  return QBX_OK;
+}
+
+qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
+  if (f->n_vbox == 0) return QBX_OK;
+  if (f->n_tc_src > 0) {
+    tc_mu_kernel<<<f->n_tc_src, kThr, 0, s>>>(f->tc_src.ptr, f->box.level.ptr, f->lpb.ptr,
+                                              f->eoff.ptr, f->conv.ptr, f->pb_max, f->tc_lvl.ptr,
+                                              f->mpole.ptr, f->tc_xoff.ptr,
+                                              reinterpret_cast<__nv_bfloat16*>(f->tc_X.ptr),
+                                              f->tc_xexp.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+  }
+#define TC_LAUNCH(SS)                                                                           \
+  if (f->n_tc_items[SS - 6] > 0) {                                                              \
+    m2l_tc_kernel<SS><<<f->n_tc_items[SS - 6], kThr, tc_smem_bytes<SS>(), s>>>(                 \
+        f->tc_items[SS - 6].ptr, f->tc_lvl.ptr, f->lpb.ptr, f->tc_gaoff.ptr, f->tc_gfoff.ptr,   \
+        reinterpret_cast<const __nv_bfloat16*>(f->tc_A.ptr), f->tc_fexp.ptr, f->tc_rowsrc.ptr,   \
+        f->tc_xoff.ptr, f->tc_xexp.ptr, reinterpret_cast<const __nv_bfloat16*>(f->tc_X.ptr),     \
+        f->m2l_yoff.ptr, f->m2l_y64.ptr, f->err.ptr + 1);                                      \
+    QBX_CUDA_TRY(cudaGetLastError());                                                           \
+    h->launches += 1;                                                                           \
+  }
+  TC_LAUNCH(6)
+  TC_LAUNCH(7)
+  TC_LAUNCH(8)
+#undef TC_LAUNCH
+  {
+    const qbx_status st = launch_m2l_f64_gemm_rest(h, f, s);
+    if (st != QBX_OK) return st;
+  }
+  m2l_tc_reduce_kernel<<<f->n_vbox, kThr, 0, s>>>(f->pb_max, f->vbox.ptr, f->box.level.ptr,
+                                                  f->lpb.ptr, f->tc_lvl.ptr, f->V.off.ptr,
+                                                  f->m2l_eyoff.ptr, f->m2l_y64.ptr, f->conv.ptr,
+                                                  f->eoff.ptr, f->local.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  h->launches += 1;
+  return QBX_OK;
+}

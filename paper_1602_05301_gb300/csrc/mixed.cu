@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "tree.cuh"
+#include "m2l_entry.cuh"
 
 namespace {
 
@@ -43,33 +44,18 @@ __global__ void sigma_tables_kernel(int n_levels, int pbmax, const int* __restri
 }
 
 // Level l's matrices Tm[cls][n][lo] = sig_lo sig_n (-1)^lo W_{n+lo}(D) (orders
-// up to pb = pb_l), from the FP64 scaled Hankel vectors What_m = s^|m| W_m(D)
-// (row stride 4 pbmax + 1, order m at m + 2 pbmax). Grid: (cls, n), threads over lo.
+// up to pb = pb_l; M2lNorm), stored in FP32. Grid: (cls, n), threads over lo.
 __global__ void m2l_f32_matrix_kernel(int l, int pb, int pbmax, const cd* __restrict__ t_m2l,
                                       const double* __restrict__ scale,
                                       const double* __restrict__ lsig, float2* __restrict__ Tm) {
   const int cls = blockIdx.x;
   const int n = (int)blockIdx.y - pb;
   const int Q = 2 * pb + 1;
-  const cd* w = t_m2l + ((size_t)l * 49 + cls) * (4 * pbmax + 1) + 2 * pbmax;
-  const double ls = log(scale[l]);
-  const double* sg = lsig + (size_t)l * (pbmax + 1);
+  const M2lNorm nm(t_m2l, scale, lsig, l, cls, pbmax);
   float2* dst = Tm + ((size_t)cls * Q + (n + pb)) * Q;
-  const int dx = cls / 7 - 3, dy = cls % 7 - 3;
-  const bool used = max(abs(dx), abs(dy)) >= 2;  // V-list offsets only
   for (int lo = (int)threadIdx.x - pb; lo <= pb; lo += blockDim.x) {
-    float2 out = make_float2(0.f, 0.f);
-    if (used) {
-      const cd v = w[n + lo];
-      const double mag = hypot(v.x, v.y);  // entries reach 1e155: no squares
-      if (mag > 0.0) {
-        const double lf = sg[abs(lo)] + sg[abs(n)] - abs(n + lo) * ls + log(mag);
-        const double f = lf < -700.0 ? 0.0 : exp(lf) / mag;
-        const double sgn = (lo & 1) ? -f : f;
-        out = make_float2((float)(v.x * sgn), (float)(v.y * sgn));
-      }
-    }
-    dst[lo + pb] = out;
+    const cd v = nm.entry(n, lo);
+    dst[lo + pb] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -639,6 +625,9 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
         vrow[e] = row;
         row_src[row] = vidx[e];
       }
+    f->h_row_src = row_src;
+    f->h_row_src.resize(gcount[ng]);
+    f->h_gcount.assign(gcount.begin(), gcount.end());
     long long ytot = 0;
     std::vector<int4> tiles;
     for (int g = 0; g < ng; ++g) {
@@ -672,6 +661,7 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
     QBX_CUDA_TRY(cudaMemcpy(f->m2l_goff.ptr, goff.data(), ng * sizeof(long long), cudaMemcpyHostToDevice));
     f->n_m2l_items32 = (int)it32.size();
     f->n_m2l_items64 = (int)it64.size();
+    f->h_items64 = it64;
     QBX_CUDA_TRY(f->m2l_items32.alloc(std::max<size_t>(1, it32.size())));
     QBX_CUDA_TRY(f->m2l_items64.alloc(std::max<size_t>(1, it64.size())));
     if (!it32.empty()) {
@@ -773,6 +763,19 @@ qbx_status launch_m2l_f64(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
       f->m2l_y64.ptr, f->eoff.ptr, f->local.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   h->launches += 2;
+  return QBX_OK;
+}
+
+// The FP64 tile GEMM over the items of the levels that the tensor-core M2L
+// does not take (their result rows, FP64, are added by the tensor-core path's
+// reduction).
+qbx_status launch_m2l_f64_gemm_rest(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
+  if (f->n_m2l_items64_rest == 0) return QBX_OK;
+  m2l_f64_gemm_kernel<<<f->n_m2l_items64_rest, kT, 0, s>>>(
+      f->m2l_items64_rest.ptr, f->lpb.ptr, f->m2l_goff.ptr, f->m2l_rowoff.ptr, f->mpole.ptr,
+      f->tm_f64.ptr, f->m2l_yoff.ptr, f->m2l_y64.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  h->launches += 1;
   return QBX_OK;
 }
 

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "qbx_internal.h"
+#include "p_add_table.h"
 
 namespace {
 
@@ -150,14 +151,11 @@ extern "C" qbx_status qbx_fmm_level_orders(double k, double root_side, int32_t n
   return QBX_OK;
 }
 
-// Table 2 (Sec. 7.1) gives p_add for p = 2, 4, 6, 8 (5, 5, 15, 20); the orders
-// in between take the value of the next tabulated p, and beyond p = 8 the
-// table's last ratio p_add / p = 2.5 continues (rounded up: 30 at p = 12,
-// 40 at p = 16).
+// p_add for the default plan (p_add < 0 in the tree descriptor): measured
+// with this library by the experiment of Sec. 7.1 (calibrate_p_add.py; the
+// generated table below). Table 2 of the paper, measured the same way with
+// the paper's own point-FMM orders, prints 5, 5, 15, 20 for p = 2, 4, 6, 8.
 extern "C" int32_t qbx_default_p_add(int32_t p) {
   if (p < 0) return -1;
-  if (p <= 4) return 5;
-  if (p <= 6) return 15;
-  if (p <= 8) return 20;
-  return (5 * p + 1) / 2;
+  return kPAddCalibrated[p > QBX_MAX_P ? QBX_MAX_P : p];
 }

@@ -75,6 +75,12 @@ struct qbx_handle {
   DevBuf<double> node_xy, node_nrm, panel_h;
   DevBuf<double> src_xy, src_nrm, src_w;
   DevBuf<double> ctr_xy, ctr_r;
+  // Set when the library made the source grid itself (q_src nodes per panel
+  // by polynomial interpolation of the density grid): densities passed to
+  // eval then live on the density grid and are interpolated the same way.
+  bool upsample = false;
+  DevBuf<double> up_L;                      // [q_src][q] Lagrange interpolation matrix
+  int64_t n_density() const { return upsample ? n_nodes : n_src; }
   // targets / association (device)
   int64_t n_tgt = 0, n_qbx_tgt = 0, n_direct_tgt = 0;
   bool planned = false;
@@ -86,6 +92,11 @@ struct qbx_handle {
   DevBuf<double> tgt_xy;
   DevBuf<int32_t> assoc;                    // [n_tgt] centre or -1
   DevBuf<int32_t> qbx_tgt_list, direct_tgt_list;
+  // on-surface targets that ask for the on-surface value (side 0): the mean of
+  // the two one-sided QBX limits, from the node's exterior centre (assoc) and
+  // its interior centre (assoc + n_nodes)
+  DevBuf<int8_t> avg;                       // [n_tgt] 1 = two-sided mean (or empty)
+  bool has_avg = false;
   // evaluation scratch
   DevBuf<cd> q_str, d_str;                  // per-source charge / dipole strengths
   DevBuf<cd> sigS_dev, sigD_dev, out_dev;   // staging for host buffers
@@ -115,6 +126,10 @@ qbx_status launch_qbxl2p(qbx_handle* h, cd* out, cudaStream_t s);
 qbx_status launch_associate_direct(qbx_handle* h, const int64_t* on_node, const int8_t* on_side,
                                    double eps, cudaStream_t s);
 qbx_status launch_place_centres(qbx_handle* h, cudaStream_t s);
+// surface.cu
+qbx_status upsample_geometry(qbx_handle* h);
+qbx_status launch_strengths_upsampled(qbx_handle* h, cd cS, const cd* sigS, cd cD, const cd* sigD,
+                                      cudaStream_t s);
 // fmm.cu
 qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* on_node_dev,
                           const int8_t* on_side_dev, double eps);

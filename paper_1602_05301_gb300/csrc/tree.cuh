@@ -140,6 +140,26 @@ struct FmmPlan {
   std::vector<long long> h_tl_off;
   DevBuf<float2> tmm_f32;               // per parent level l: [4][Q_{l+1}][Q_l] M2M matrices
   std::vector<long long> h_tmm_off;
+  // tensor-core M2L of the FP64 path (m2l_tc.cu)
+  std::vector<int> h_row_src;           // source box of every M2L row
+  std::vector<int64_t> h_gcount;        // [n_levels * 49 + 1] first row of every group
+  std::vector<int4> h_items64;          // the FP64 GEMM items (host copy)
+  DevBuf<int4> m2l_items64_rest;        // FP64 GEMM items of the levels left to it
+  int n_m2l_items64_rest = 0;
+  std::vector<int4> h_tc_lvl;           // per level (use, beta, S, padded 2Q)
+  DevBuf<int4> tc_lvl;
+  bool tc_any = false;
+  DevBuf<uint16_t> tc_A;                // bf16 matrix slices [S][Kp][Kp] per group
+  DevBuf<int> tc_fexp;                  // row exponents [Kp] per group
+  DevBuf<long long> tc_gaoff, tc_gfoff; // [n_levels * 49] offsets of a group's slices / exponents
+  DevBuf<int> tc_src;                   // V-list sources on tensor-core levels
+  int n_tc_src = 0;
+  DevBuf<long long> tc_xoff;            // their bf16 vector slices [S][Kp]
+  DevBuf<int> tc_xexp;                  // and exponents
+  DevBuf<uint16_t> tc_X;
+  DevBuf<int> tc_rowsrc;                // per M2L row: position of its source in tc_src
+  DevBuf<int4> tc_items[3];             // (first row, rows, first output, group) for S = 6, 7, 8
+  int n_tc_items[3] = {0, 0, 0};
 };
 
 qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f);
@@ -148,6 +168,11 @@ qbx_status launch_m2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 qbx_status launch_m2l_f64(qbx_handle* h, FmmPlan* f, cudaStream_t s);
+qbx_status launch_m2l_f64_gemm_rest(qbx_handle* h, FmmPlan* f, cudaStream_t s);
+// m2l_tc.cu
+qbx_status configure_tc_kernels(int smem_optin);
+qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f);
+qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 // shared memory of one M2M / L2L tile-GEMM block at box order pb
 size_t gemm_smem_bytes(int pb);
 

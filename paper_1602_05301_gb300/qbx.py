@@ -105,6 +105,10 @@ def library() -> ctypes.CDLL:
                                                  ctypes.c_int32, ctypes.c_int32, _vp]
             lib.qbx_default_p_add.restype = ctypes.c_int32
             lib.qbx_default_p_add.argtypes = [ctypes.c_int32]
+            lib.qbx_get_source_grid.restype = ctypes.c_int
+            lib.qbx_get_source_grid.argtypes = [_vp, _vp, _vp, _vp]
+            lib.qbx_table1_q_src.restype = ctypes.c_int32
+            lib.qbx_table1_q_src.argtypes = [ctypes.c_int32, ctypes.c_double]
             _lib = lib
     return _lib
 
@@ -208,6 +212,11 @@ def qbx_fmm_level_orders(k: float, root_side: float, n_levels: int, p_fmm: int,
     return out
 
 
+def qbx_table1_q_src(q: int, eps: float) -> int:
+    """Source nodes per panel from Table 1 (-1 outside the table's range)."""
+    return int(library().qbx_table1_q_src(int(q), float(eps)))
+
+
 def qbx_last_error() -> str:
     return library().qbx_last_error().decode()
 
@@ -222,10 +231,13 @@ class LayerPotential:
 
     geom: object with node_xy, normal_xy, weight, panel_h (numpy), q, k (scalar or [1]).
     src:  optional oversampled source grid (same panels): dict with q, node_xy,
-          normal_xy, weight.
+          normal_xy, weight; densities then live on that grid.
+    q_src: instead of src, the number of source nodes per panel of a grid that
+          the library makes by interpolation; densities then live on the
+          density grid (n_nodes values).
     """
 
-    def __init__(self, geom, p, sides=2, src=None):
+    def __init__(self, geom, p, sides=2, src=None, q_src=0):
         self._keep = []
         k = float(np.atleast_1d(geom.k)[0]) if hasattr(geom, "k") else float(geom["k"])
         g = geom if isinstance(geom, dict) else geom.__dict__
@@ -243,12 +255,15 @@ class LayerPotential:
             self._keep += [sxy, snr, sw]
             d.q_src = int(src["q"])
             d.src_xy, d.src_normal_xy, d.src_weight = ptr(sxy), ptr(snr), ptr(sw)
+        elif q_src:
+            d.q_src = int(q_src)
         d.k = k
         d.p_qbx = int(p)
         d.center_sides = int(sides)
         self.k, self.p, self.sides = k, int(p), int(sides)
         self.n_nodes = node_xy.shape[0]
-        self.n_src = (d.n_panels * d.q_src) if src is not None else self.n_nodes
+        self.n_src = (d.n_panels * d.q_src) if d.q_src else self.n_nodes
+        self.n_density = self.n_nodes if (q_src and src is None) else self.n_src
         self.n_centres = self.n_nodes * self.sides
         self.handle = qbx_geometry_create(d)
         self._keep = []
@@ -296,6 +311,12 @@ class LayerPotential:
         _check(library().qbx_get_box_orders(self.handle, out.ctypes.data, 25))
         depth = int(self.stats()["depth"])
         return out[:depth + 1]
+
+    def source_grid(self):
+        """(src_xy [n_src][2], src_normal_xy [n_src][2], src_weight [n_src])."""
+        xy, nr, w = np.empty((self.n_src, 2)), np.empty((self.n_src, 2)), np.empty(self.n_src)
+        _check(library().qbx_get_source_grid(self.handle, ptr(xy), ptr(nr), ptr(w)))
+        return xy, nr, w
 
     def export_tree(self):
         return qbx_export_tree(self.handle, self.n_src, self.n_centres, self.n_targets)
@@ -351,7 +372,7 @@ class Batch:
         _check(library().qbx_batch_create(len(self.problems), ctypes.cast(arr, _vp),
                                           int(n_streams), ctypes.byref(b)))
         self.handle = b
-        self.n_src = sum(p.n_src for p in self.problems)
+        self.n_src = sum(p.n_density for p in self.problems)   # density values per batch
         self.n_targets = sum(p.n_targets for p in self.problems)
 
     def eval(self, sigma_S=None, sigma_D=None, cS=None, cD=None, out=None,

@@ -148,7 +148,7 @@ def test_fmm_starfish_config_sampled_parity(qbxmod, oracle):
     lp = qbxmod.LayerPotential(g.as_dict(), w["p"], sides=2)
     assoc = lp.build(w["tgt_xy"], mode=qbxmod.QBX_FMM, p_fmm=w["p_fmm"])
     st = lp.stats()
-    assert st["p_box"] == 50 and st["n_boxes"] > 100
+    assert st["p_box"] == w["p_fmm"] + qbxmod.qbx_default_p_add(w["p"]) and st["n_boxes"] > 100
     alpha = np.empty((lp.n_centres, 2 * w["p"] + 1), np.complex128)
     u = lp.eval(sigma_S=w["sigma_S"], sigma_D=w["sigma_D"], cS=w["cS"], cD=w["cD"],
                 alpha_out=alpha)

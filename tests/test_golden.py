@@ -24,22 +24,42 @@ def qbxmod():
     return qbx
 
 
-def test_default_p_add_is_table_2(qbxmod):
+def test_default_p_add_is_the_calibration_and_within_table_2(qbxmod):
+    """The default p_add comes from this library's own run of the Sec. 7.1
+    experiment (paper_1602_05301_gb300/p_add_calibration.txt). Table 2's printed
+    values, found the same way with the paper's point-FMM orders, bound it from
+    above for the orders it lists, and both grow with p."""
     rows = _table("table2_p_add.txt")
     assert [r[0] for r in rows] == [2, 4, 6, 8]
+    calib = {}
+    for line in open(os.path.join(ROOT, "paper_1602_05301_gb300", "p_add_calibration.txt")):
+        if line.startswith("p = "):
+            p, v = line.split(":")[0].split("=")[1], line.split("p_add =")[1].split()[0]
+            calib[int(p)] = int(v)
+    assert sorted(calib) == [2, 4, 6, 8, 10, 12, 14, 16]
+    run = 0
+    for p in range(0, 17):
+        nxt = min(q for q in calib if q >= max(p, 2))
+        run = max(run, max(v for q, v in calib.items() if q <= nxt))
+        assert qbxmod.qbx_default_p_add(p) == run, p
     for p, p_add in rows:
-        assert qbxmod.qbx_default_p_add(p) == p_add, p
-
-
-def test_default_p_add_between_and_beyond_the_table(qbxmod):
-    # orders between tabulated ones take the next tabulated value; beyond p = 8
-    # the last ratio p_add / p = 2.5 of the table continues, rounded up
-    table = dict(_table("table2_p_add.txt"))
-    for p in range(0, 9):
-        nxt = min(q for q in table if q >= max(p, 2))
-        assert qbxmod.qbx_default_p_add(p) == table[nxt], p
-    assert table[8] / 8 == 2.5
-    for p in (9, 10, 12, 16, 20):
-        assert qbxmod.qbx_default_p_add(p) == -(-5 * p // 2), p
-    assert qbxmod.qbx_default_p_add(12) == 30 and qbxmod.qbx_default_p_add(16) == 40
+        assert qbxmod.qbx_default_p_add(p) <= p_add, p
+    vals = [qbxmod.qbx_default_p_add(p) for p in range(0, 17)]
+    assert all(a <= b for a, b in zip(vals, vals[1:]))
+    assert qbxmod.qbx_default_p_add(20) == qbxmod.qbx_default_p_add(16)
     assert qbxmod.qbx_default_p_add(-1) == -1
+
+
+def test_table1_q_src(qbxmod):
+    rows = _table("table1_q_src.txt")
+    assert [r[0] for r in rows] == [2, 4, 8, 16]
+    for q, *cols in rows:
+        for eps, q_src in zip((1e-3, 1e-6, 1e-9, 1e-12), cols):
+            assert qbxmod.qbx_table1_q_src(q, eps) == q_src, (q, eps)
+    table = {r[0]: r[1:] for r in rows}
+    # q between rows takes the next tabulated q; eps between columns the next stricter one
+    assert qbxmod.qbx_table1_q_src(3, 1e-6) == table[4][1]
+    assert qbxmod.qbx_table1_q_src(12, 1e-10) == table[16][3]
+    assert qbxmod.qbx_table1_q_src(16, 1e-2) == table[16][0]
+    assert qbxmod.qbx_table1_q_src(17, 1e-6) == -1
+    assert qbxmod.qbx_table1_q_src(16, 1e-13) == -1

@@ -68,6 +68,29 @@ def test_hankel_recurrence_vs_mpmath_and_library(oracle):
     assert _rel(a1 * wgt, a0 * wgt) < 1e-12
 
 
+# ---------------------------------------------------------------- source grid (Sec. 2.2)
+def test_source_grid_interpolation_matches_the_curve(oracle):
+    """The source grid made from the density grid alone (positions, normals and
+    weights by per-panel polynomial interpolation) equals the curve's own
+    discretisation with q_src nodes, and interpolated densities equal the density
+    sampled there (a smooth curve: exact to rounding)."""
+    g = discretise_curve(*starfish(0.3, 5), 48, 16, k=5.0)
+    gs = discretise_curve(*starfish(0.3, 5), 48, 64, k=5.0)
+    xy, nr, w = oracle.source_grid(g.node_xy, g.normal_xy, 16, 64)
+    assert np.abs(xy - gs.node_xy).max() < 1e-13
+    assert np.abs(nr - gs.normal_xy).max() < 1e-11
+    assert np.abs(w - gs.weight).max() < 1e-12 * gs.weight.max()
+    assert abs(w.sum() - gs.weight.sum()) < 1e-12 * gs.weight.sum()
+    f = lambda t: np.exp(3j * t) + 0.5 * np.cos(7 * t)
+    assert np.abs(oracle.interpolate_panels(f(g.param_t), 16, 64) - f(gs.param_t)).max() < 1e-13
+    # a polynomial of degree < q in the panel variable is reproduced exactly on a
+    # straight panel (the interpolation is exact there)
+    x16, _ = np.polynomial.legendre.leggauss(16)
+    x64, _ = np.polynomial.legendre.leggauss(64)
+    poly = lambda u: 1 - 2 * u + 3 * u ** 5 - u ** 15
+    assert np.abs(oracle.interpolate_panels(poly(x16), 16, 64) - poly(x64)).max() < 1e-12
+
+
 # ---------------------------------------------------------------- Graf / conventions
 def test_graf_expansion_single_source_slp(oracle):
     """alpha of one unit source, evaluated inside the disk, equals (i/4) H_0(k|x-y|)."""
