@@ -296,6 +296,15 @@ def run_ours(args, w, ws, rank, local):
                                          flush, ws, dev, lp)
     value = job_throughput(n_t, ws, args.steps, total_ms)
     stats = lp.stats()
+    if args.only_headline:   # profiling runs: the timed evaluations and nothing else
+        lp.close()
+        return dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=total_ms / args.steps,
+                    higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f64" if prec == qbx.QBX_FP64 else "f32+f64", data="synthetic",
+                    config={"workload": WORKLOADS[args.config] % w["name"],
+                            "precision": args.precision}, gpu_launches=launches,
+                    clocks=clk.summary())
     u_main = out.cpu().numpy()
 
     # the other precision on the same plan and inputs: speed and the stated error
@@ -632,6 +641,11 @@ def main():
     ap.add_argument("--n-max", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-equal-accuracy", action="store_true")
+    ap.add_argument("--size-scale", type=float, default=1.0,
+                    help="shrink the 200-ellipse workload (ellipses, panels and targets "
+                         "times this factor) for profiling captures; 1 = the full workload")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time the headline evaluations only (for profiler launch lists)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the starfish and batch workloads of the default line")
     ap.add_argument("--config", type=int, default=CONFIG_NUM, choices=[2, 3, 4, 5],
@@ -640,7 +654,16 @@ def main():
     args = ap.parse_args()
     ws, rank, local = dist_env()
     from qbx_workloads import make_config
-    w = make_config(args.config)
+    if args.size_scale != 1.0:
+        if args.config != 5 or not 0.0 < args.size_scale <= 1.0:
+            ap.error("--size-scale applies to --config 5 with a factor in (0, 1]")
+        f = args.size_scale
+        w = make_config(5, n_ellipses=max(1, int(round(200 * f))),
+                        total_panels=max(64, int(round(65536 * f))),
+                        n_uniform=int(round(900_000 * f)), n_near=int(round(100_000 * f)))
+        args.no_extras = True
+    else:
+        w = make_config(args.config)
 
     if args.impl == "reference":
         if rank == 0:
@@ -655,6 +678,8 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     res = run_batch(args, w, ws, rank, local) if args.config == 4 else run_ours(args, w, ws, rank, local)
+    if args.only_headline:
+        args.no_extras = args.no_cpu_baseline = True
     if rank == 0 and ws == 1 and not args.no_extras and args.config == CONFIG_NUM:
         # the other workloads of the same metric, as extra keys of the line
         res["extra_workloads"] = {}

@@ -94,13 +94,22 @@ typedef struct {
   double k;                      /* wavenumber, real, > 0                                  */
   int32_t p_qbx;                 /* QBX order p, 0 <= p <= QBX_MAX_P                        */
   int32_t center_sides;          /* 1: exterior centres only, 2: both sides                */
+  int32_t n_curves;              /* closed curves; 0 or 1: all panels form one curve       */
+  const int64_t *curve_panel_offset; /* [n_curves + 1] first panel of each curve, or NULL   */
+  int32_t defer_conditions;      /* 1: accept a geometry breaking Condition 4 (to refine)   */
 } qbx_geometry_desc;
 
 /*
- * Copies the geometry to the device and places the centres.
+ * Copies the geometry to the device and places the centres. The panels of a
+ * curve are consecutive and run counter-clockwise around it (outward normals);
+ * curve_panel_offset says where each curve starts, which decides which panels
+ * are adjacent (Sec. 3.2, Conditions 2 and 3). With defer_conditions == 1 a
+ * geometry that breaks Condition 4 is accepted, for qbx_refine to mend;
+ * qbx_tree_build then refuses it while the condition is still broken.
  * Errors: QBX_ERR_ARG on NULL/invalid sizes, QBX_ERR_CONDITION if
- * k * max_k h_k > 5 (Condition 4), QBX_ERR_OOM / QBX_ERR_CUDA.
- * On success *out owns the new handle (free with qbx_destroy).
+ * k * max_k h_k > 5 (Condition 4) and defer_conditions == 0,
+ * QBX_ERR_OOM / QBX_ERR_CUDA. On success *out owns the new handle (free with
+ * qbx_destroy).
  */
 qbx_status qbx_geometry_create(const qbx_geometry_desc *desc, qbx_handle **out);
 
@@ -258,6 +267,86 @@ qbx_status qbx_fmm_level_orders(double k, double root_side, int32_t n_levels, in
  * computation only; returns -1 for p < 0.
  */
 int32_t qbx_default_p_add(int32_t p);
+
+/*
+ * The four sufficient conditions of Sec. 3.3 on the handle's geometry
+ * (Sec. 3.1-3.2), checked with the panel attribution of Sec. 5:
+ *   QBX_COND1 (Condition 1, Eq. (dcgam_perpanel)): some centre of panel n lies
+ *     closer than h_n / 2 to another panel m; panel n is flagged (its disks
+ *     are too large; Sec. 5.1).
+ *   QBX_COND2 (Condition 2): adjacent panels of a curve whose lengths differ by
+ *     more than a factor 2; the longer one is flagged.
+ *   QBX_COND3 (Condition 3): a centre of panel n lies closer than h_m / 4 to a
+ *     panel m that is neither n nor adjacent to n; the source panel m is
+ *     flagged (its quadrature is too coarse there; Sec. 5.2 and its figure).
+ *   QBX_COND4 (Condition 4): k h_k > 5; panel k is flagged.
+ * Distances to a panel are to the curve through its nodes (the interpolating
+ * polynomial of degree q - 1 in the panel's reference variable). Candidate
+ * (centre, panel) pairs come from area queries in a hierarchy of panel
+ * bounding squares (Sec. 4, with a Morton-ordered bounding-volume tree in
+ * place of the paper's peer boxes).
+ * panel_flags (optional, [n_panels] int32, host or device) receives the OR of
+ * the QBX_COND* bits of each panel; counts (optional, [4] int64, host) the
+ * number of panels flagged for each condition. Synchronous.
+ * Errors: QBX_ERR_ARG, QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+enum { QBX_COND1 = 1, QBX_COND2 = 2, QBX_COND3 = 4, QBX_COND4 = 8 };
+qbx_status qbx_check_conditions(qbx_handle *h, int32_t *panel_flags, int64_t *counts);
+
+/*
+ * Refinement (Sec. 5): checks the conditions and bisects every flagged panel
+ * into two panels of equal arclength (the split point from the panel's
+ * Legendre expansion; new nodes, normals and weights from the same expansion),
+ * rechecks, and repeats until no panel is flagged or max_rounds rounds have
+ * run. The handle's geometry is replaced: centres are placed anew, any plan is
+ * dropped (build it again with qbx_tree_build), a library-made source grid is
+ * made anew. Handles with a caller-supplied source grid cannot be refined
+ * (QBX_ERR_STATE). *rounds (optional) receives the rounds run, *n_panels
+ * (optional) the new panel count. Returns QBX_ERR_CONDITION if panels are
+ * still flagged after max_rounds. Synchronous.
+ */
+qbx_status qbx_refine(qbx_handle *h, int32_t max_rounds, int32_t *rounds, int64_t *n_panels);
+
+/*
+ * The handle's density geometry, e.g. after qbx_refine: *n_panels (required)
+ * receives the panel count; the optional host or device arrays node_xy
+ * [n_panels q][2], normal_xy [n_panels q][2], weight [n_panels q], panel_h
+ * [n_panels], panel_origin [n_panels] (the panel of the geometry given to
+ * qbx_geometry_create that the panel lies on), panel_interval [n_panels][2]
+ * (the panel's part of that original panel, in its reference variable
+ * u in [-1, 1], so that a caller can sample its density there) and
+ * curve_panel_offset [n_curves + 1] are filled. Call first with NULL arrays to
+ * learn n_panels. Synchronous.
+ */
+qbx_status qbx_get_geometry(const qbx_handle *h, int64_t *n_panels, double *node_xy,
+                            double *normal_xy, double *weight, double *panel_h,
+                            int64_t *panel_origin, double *panel_interval,
+                            int64_t *curve_panel_offset);
+
+/*
+ * The exterior Dirichlet (sound-soft scattering) problem of Sec. 1 and
+ * Sec. 8.3: with u = D[sigma] + i k S[sigma] the boundary condition u = f on
+ * the curves is the second-kind equation (Eq. (extdir), Eq. (int_eq))
+ *     (1/2) sigma + D*[sigma] + i k S*[sigma] = f,
+ * whose left side is the exterior one-sided limit that Global QBX evaluates at
+ * each density node. Solves it by restarted GMRES (restart vectors, relative
+ * residual tol, at most max_iter matrix-vector products), each product one
+ * qbx_layer_potential_eval in the given mode (QBX_DIRECT or QBX_FMM with box
+ * order p_fmm plus the default p_add) and precision. The call builds its own
+ * plan (targets: every density node, exterior side), replacing any plan of
+ * the handle.
+ * rhs: f, complex [n_nodes] at the density nodes (host or device);
+ * sigma_out: complex [n_nodes] (host or device); *iters_out, *resid_out
+ * (optional): the products used and the final true relative residual
+ * ||f - A sigma|| / ||f||, which the caller compares with tol (the call
+ * returns QBX_OK also when max_iter ends it first). Synchronous on
+ * cuda_stream. Handles with a caller-supplied source grid are refused
+ * (QBX_ERR_STATE): the unknowns live on the density nodes.
+ */
+qbx_status qbx_solve_dirichlet(qbx_handle *h, const double *rhs, double *sigma_out, int32_t mode,
+                               int32_t p_fmm, int32_t precision, double tol, int32_t max_iter,
+                               int32_t restart, int32_t *iters_out, double *resid_out,
+                               void *cuda_stream);
 
 /*
  * The source grid of the handle (Sec. 2.2): src_xy [n_src][2], src_normal_xy

@@ -300,3 +300,109 @@ def source_grid(node_xy, normal_xy, q, q_src):
     nrm[flip] *= -1.0
     w = ws[None, :] * speed
     return pos.reshape(-1, 2), nrm.reshape(-1, 2), w.reshape(-1)
+
+
+# ---------------------------------------------------------------- Conditions 1-4 (Sec. 3.3)
+def panel_distances(node_xy, q, points, n_samples=257, refine_rel=0.05, thresholds=None,
+                    skip=None):
+    """Distance from every point to every panel (the curve through the panel's q
+    nodes, the interpolating polynomial in u in [-1, 1]): dense sampling, then a
+    golden-section search on the curve around the nearest sample for the pairs
+    whose sampled distance lies within refine_rel of a threshold (thresholds
+    [n_points, n_panels], or None: refine none; pairs where skip is True are
+    not refined). [n_points, n_panels]."""
+    xq, _ = np.polynomial.legendre.leggauss(q)
+    us = np.linspace(-1.0, 1.0, n_samples)
+
+    def lagrange(u):
+        L = np.ones((u.size, q))
+        for i in range(q):
+            for r in range(q):
+                if r != i:
+                    L[:, i] *= (u - xq[r]) / (xq[i] - xq[r])
+        return L
+    xy = np.asarray(node_xy, dtype=np.float64).reshape(-1, q, 2)
+    samp = np.einsum("si,pic->psc", lagrange(us), xy)              # [panels, samples, 2]
+    pts = np.asarray(points, dtype=np.float64)
+    npan = xy.shape[0]
+    dist = np.empty((pts.shape[0], npan))
+    best = np.empty((pts.shape[0], npan), np.int64)
+    chunk = max(1, int(2e7 // (npan * n_samples)))
+    for i0 in range(0, pts.shape[0], chunk):
+        d2 = ((pts[i0:i0 + chunk, None, None, :] - samp[None]) ** 2).sum(-1)
+        bi = d2.argmin(-1)
+        best[i0:i0 + chunk] = bi
+        dist[i0:i0 + chunk] = np.sqrt(np.take_along_axis(d2, bi[..., None], -1)[..., 0])
+    if thresholds is None:
+        return dist
+    near = np.abs(dist - thresholds) < refine_rel * thresholds
+    if skip is not None:
+        near &= ~skip
+    ii, mm = np.nonzero(near)
+    if ii.size == 0:
+        return dist
+    hs = 2.0 / (n_samples - 1)
+    a = np.maximum(-1.0, us[best[ii, mm]] - hs)
+    b = np.minimum(1.0, us[best[ii, mm]] + hs)
+    P = pts[ii]
+
+    def f(u):
+        x = np.einsum("ni,nic->nc", lagrange(u), xy[mm])
+        return np.hypot(*(x - P).T)
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    c, e = b - g * (b - a), a + g * (b - a)
+    fc, fe = f(c), f(e)
+    for _ in range(60):   # golden-section search, all pairs at once
+        left = fc < fe
+        b = np.where(left, e, b)
+        a = np.where(left, a, c)
+        c_new = np.where(left, b - g * (b - a), e)
+        e_new = np.where(left, c, a + g * (b - a))
+        fc_new = np.where(left, f(c_new), fe)
+        fe_new = np.where(left, fc, f(e_new))
+        c, e, fc, fe = c_new, e_new, fc_new, fe_new
+    dist[ii, mm] = np.minimum(dist[ii, mm], np.minimum(fc, fe))
+    return dist
+
+
+def conditions(geom, sides=2):
+    """Flags of Conditions 1-4 (Sec. 3.3) per panel, by brute force over every
+    (centre, panel) pair, with the panel attribution of Sec. 5: Condition 1
+    flags the panel of a centre closer than h_n/2 to another panel; Condition 2
+    the longer of two adjacent panels whose lengths differ by more than 2;
+    Condition 3 a panel m closer than h_m/4 to a centre of a panel that is
+    neither m nor adjacent to m; Condition 4 a panel with k h > 5. geom: dict
+    with node_xy, normal_xy, panel_h, q, k and panel_offset (curves). Returns
+    int32 [n_panels] of bits 1, 2, 4, 8."""
+    q = int(geom["q"])
+    h = np.asarray(geom["panel_h"], dtype=np.float64)
+    npan = h.size
+    po = np.asarray(geom.get("panel_offset", [0, npan]), dtype=np.int64)
+    curve = np.repeat(np.arange(po.size - 1), np.diff(po))
+    pon = np.repeat(np.arange(npan), q)
+    cxy, _ = centres(geom["node_xy"], geom["normal_xy"], pon, h, sides)
+    cpan = np.tile(pon, sides)
+    r1 = 0.5 * h[cpan][:, None] * np.ones((1, npan))
+    r3 = 0.25 * h[None, :] * np.ones((cpan.size, 1))
+    own = cpan[:, None] == np.arange(npan)[None, :]
+    # refine near either threshold: run twice, keep the smaller distance
+    d = np.minimum(panel_distances(geom["node_xy"], q, cxy, thresholds=r1, skip=own),
+                   panel_distances(geom["node_xy"], q, cxy, thresholds=r3, skip=own))
+    flags = np.zeros(npan, np.int32)
+    n_in = np.diff(po)[curve]
+    diff = (cpan[:, None] - np.arange(npan)[None, :]) % n_in[None, :]
+    same = curve[cpan][:, None] == curve[None, :]
+    adj = same & ((diff == 1) | (diff == n_in[None, :] - 1)) & (n_in[None, :] > 1)
+    c1 = (d < r1) & ~own
+    flags[np.unique(cpan[c1.any(1)])] |= 1
+    c3 = (d < r3) & ~own & ~adj
+    flags[np.nonzero(c3.any(0))[0]] |= 4
+    for c in range(po.size - 1):
+        ids = np.arange(po[c], po[c + 1])
+        if ids.size < 2:
+            continue
+        nxt = np.roll(ids, -1)
+        flags[ids[h[ids] > 2.0 * h[nxt]]] |= 2
+        flags[nxt[h[nxt] > 2.0 * h[ids]]] |= 2
+    flags[float(geom["k"]) * h > 5.0] |= 8
+    return flags

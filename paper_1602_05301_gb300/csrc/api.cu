@@ -132,9 +132,33 @@ extern "C" qbx_status qbx_geometry_create(const qbx_geometry_desc* d, qbx_handle
     if (!(v > 0.0)) { set_error("qbx_geometry_create: panel length <= 0"); return QBX_ERR_ARG; }
     hmax = std::max(hmax, v);
   }
-  if (d->k * hmax > 5.0) {
+  if (d->k * hmax > 5.0 && !d->defer_conditions) {
     set_error("Condition 4 violated: k * max h = %.4g > 5; refine the panels", d->k * hmax);
     return QBX_ERR_CONDITION;
+  }
+  // curves: consecutive panel ranges (one curve when none are given)
+  std::vector<long long> coff;
+  if (d->n_curves > 1 || (d->n_curves == 1 && d->curve_panel_offset)) {
+    if (!d->curve_panel_offset) {
+      set_error("qbx_geometry_create: n_curves > 1 needs curve_panel_offset");
+      return QBX_ERR_ARG;
+    }
+    std::vector<int64_t> co = to_host(d->curve_panel_offset, (size_t)d->n_curves + 1);
+    if (co[0] != 0 || co[d->n_curves] != d->n_panels) {
+      set_error("qbx_geometry_create: curve_panel_offset must run from 0 to n_panels");
+      return QBX_ERR_ARG;
+    }
+    for (int c = 0; c < d->n_curves; ++c)
+      if (co[c + 1] <= co[c]) {
+        set_error("qbx_geometry_create: curve %d has no panels", c);
+        return QBX_ERR_ARG;
+      }
+    coff.assign(co.begin(), co.end());
+  } else if (d->n_curves < 0) {
+    set_error("qbx_geometry_create: n_curves < 0");
+    return QBX_ERR_ARG;
+  } else {
+    coff = {0, (long long)d->n_panels};
   }
   qbx_handle* h = new (std::nothrow) qbx_handle();
   if (!h) { set_error("out of host memory"); return QBX_ERR_OOM; }
@@ -147,6 +171,12 @@ extern "C" qbx_status qbx_geometry_create(const qbx_geometry_desc* d, qbx_handle
   h->p = d->p_qbx;
   h->sides = d->center_sides;
   h->upsample = upsample;
+  h->own_src = own_src;
+  h->defer_conditions = d->defer_conditions != 0;
+  h->curve_off = coff;
+  h->panel_origin.resize(d->n_panels);
+  for (int64_t k = 0; k < d->n_panels; ++k) h->panel_origin[k] = k;
+  h->panel_interval.assign(d->n_panels, make_double2(-1.0, 1.0));
   h->q_src = (own_src || upsample) ? d->q_src : d->q;
   h->n_src = d->n_panels * h->q_src;
   h->n_ctr = n_nodes * h->sides;
@@ -154,6 +184,11 @@ extern "C" qbx_status qbx_geometry_create(const qbx_geometry_desc* d, qbx_handle
   if ((st = copy_in(h->node_xy, d->node_xy, 2 * n_nodes)) != QBX_OK) return fail(st);
   if ((st = copy_in(h->node_nrm, d->normal_xy, 2 * n_nodes)) != QBX_OK) return fail(st);
   if ((st = copy_in(h->panel_h, d->panel_h, d->n_panels)) != QBX_OK) return fail(st);
+  if (d->weight) {
+    if ((st = copy_in(h->node_w, d->weight, n_nodes)) != QBX_OK) return fail(st);
+  } else if ((st = density_weights(h)) != QBX_OK) {
+    return fail(st);
+  }
   if (upsample) {
     if ((st = upsample_geometry(h)) != QBX_OK) return fail(st);
   } else if (own_src) {
@@ -200,6 +235,10 @@ extern "C" qbx_status qbx_tree_build(qbx_handle* h, const qbx_tree_desc* d) {
     return QBX_ERR_ARG;
   }
   h->planned = false;
+  if (h->k * h->h_max > 5.0) {  // a geometry accepted with defer_conditions, not yet refined
+    set_error("Condition 4 violated: k * max h = %.4g > 5; call qbx_refine", h->k * h->h_max);
+    return QBX_ERR_CONDITION;
+  }
   const double eps = d->eps_assoc > 0.0 ? d->eps_assoc : 0.1;
   h->n_tgt = d->n_targets;
   std::vector<int64_t> on_node;
@@ -356,6 +395,61 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
     QBX_CUDA_TRY(cudaMemcpyAsync(alpha_out, h->alpha.ptr,
                                  h->n_ctr * (2 * h->p + 1) * sizeof(cd), cudaMemcpyDefault, s));
   if (host_io) QBX_CUDA_TRY(cudaStreamSynchronize(s));
+  return QBX_OK;
+}
+
+namespace {
+template <typename T>
+void take(DevBuf<T>& dst, DevBuf<T>& src) {
+  dst.release();
+  dst.ptr = src.ptr;
+  dst.n = src.n;
+  src.ptr = nullptr;
+  src.n = 0;
+}
+}  // namespace
+
+qbx_status replace_geometry(qbx_handle* h, int64_t n_panels, DevBuf<double>& node_xy,
+                            DevBuf<double>& node_nrm, DevBuf<double>& node_w,
+                            const std::vector<double>& panel_h) {
+  QBX_CUDA_TRY(cudaDeviceSynchronize());
+  if (h->fmm) fmm_plan_free(h->fmm);
+  h->fmm = nullptr;
+  h->planned = false;
+  h->n_panels = n_panels;
+  h->n_nodes = n_panels * h->q;
+  take(h->node_xy, node_xy);
+  take(h->node_nrm, node_nrm);
+  take(h->node_w, node_w);
+  QBX_TRY(copy_in(h->panel_h, panel_h.data(), panel_h.size()));
+  h->h_max = 0.0;
+  for (double v : panel_h) h->h_max = std::max(h->h_max, v);
+  h->n_src = n_panels * h->q_src;
+  h->n_ctr = h->n_nodes * h->sides;
+  if (h->n_ctr * (2 * h->p + 1) > ((int64_t)1 << 40) || h->n_ctr > INT32_MAX) {
+    set_error("refined geometry too large");
+    return QBX_ERR_ARG;
+  }
+  if (h->upsample) {
+    QBX_TRY(upsample_geometry(h));
+  } else {
+    QBX_TRY(copy_in(h->src_xy, h->node_xy.ptr, 2 * h->n_src));
+    QBX_TRY(copy_in(h->src_nrm, h->node_nrm.ptr, 2 * h->n_src));
+    QBX_TRY(copy_in(h->src_w, h->node_w.ptr, h->n_src));
+  }
+  cudaError_t e;
+  if ((e = h->ctr_xy.alloc(2 * h->n_ctr)) != cudaSuccess ||
+      (e = h->ctr_r.alloc(h->n_ctr)) != cudaSuccess ||
+      (e = h->q_str.alloc(h->n_src)) != cudaSuccess ||
+      (e = h->d_str.alloc(h->n_src)) != cudaSuccess ||
+      (e = h->alpha.alloc(h->n_ctr * (2 * h->p + 1))) != cudaSuccess) {
+    set_error("device allocation failed: %s", cudaGetErrorString(e));
+    return QBX_ERR_OOM;
+  }
+  QBX_TRY(launch_place_centres(h, 0));
+  QBX_CUDA_TRY(cudaDeviceSynchronize());
+  h->stats[0] = h->n_src;
+  h->stats[1] = h->n_ctr;
   return QBX_OK;
 }
 

@@ -1016,10 +1016,12 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   float2 wn_prev = w0, wn_cur = wm1;  // W^s_{-(m-1)}, W^s_{-m}
   double sgn = -1.0;                  // (-1)^m for m = 1
   const float fr = (float)rho, fi = (float)ir;
+  double c1m = 0.0;                   // c1 m, kept by addition (no conversion per order)
 #pragma unroll
   for (int m = 1; m <= PM; ++m) {
     if (m > p) break;
-    const cd hnext = csub(cscale(hcur, c1 * m), cscale(hprev, r2));
+    c1m += c1;
+    const cd hnext = mk(fma(c1m, hcur.x, -r2 * hprev.x), fma(c1m, hcur.y, -r2 * hprev.y));
     const float2 enext = fmul(ecur, e1f);
     const float2 hn32 = f2(hnext);
     const float2 wp_next = fmul(hn32, enext);                                // W^s_{m+1}
@@ -1051,6 +1053,69 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
     wn_cur = wn_next;
     sgn = -sgn;
   }
+}
+
+// ---------------------------------------------------------------- M2P in mixed precision
+// The sigma-normalised FP32 multipoles mu_n = mh_n conv_|n| of the boxes that
+// M2P reads (conv = s^j / sig_j; mu is of order one or smaller).
+__global__ void __launch_bounds__(kThreads) mpole_f32_list_kernel(
+    Fmm F, const int* __restrict__ boxes, const double* __restrict__ conv,
+    float2* __restrict__ mu) {
+  const int b = boxes[blockIdx.x];
+  const int l = F.level[b];
+  const int pb = F.lpb[l];
+  const double* cv = conv + (size_t)l * (F.pbmax + 1);
+  const cd* a = F.mpole + F.eoff[b];
+  float2* dst = mu + F.eoff[b];
+  for (int n = threadIdx.x; n <= 2 * pb; n += kThreads) {
+    const double f = cv[abs(n - pb)];
+    dst[n] = make_float2((float)(a[n].x * f), (float)(a[n].y * f));
+  }
+}
+
+// M2P with the Hankel recurrence in FP64 and the rest in FP32: the multipole
+// sum_m A_m H_m(kr) e^{imth} written as sum_m mu_m G_m e^{imth} with
+// G_m = sig_m H_m(kr) (sig of the box's level; G decays like (side / r)^m),
+//   G_{m+1} = (2m/x)(sig_{m+1}/sig_m) G_m - (sig_{m+1}/sig_{m-1}) G_{m-1}
+// (rec[l][m] = (2m sig_{m+1}/sig_m, sig_{m+1}/sig_{m-1}), rec[l][0].x = sig_1).
+// Each G_m is rounded to FP32 once; angular factors, products and the
+// compensated (Kahan) sum are FP32; H_{-m} = (-1)^m H_m.
+__global__ void __launch_bounds__(kThreads) m2p_pair_mixed_kernel(
+    Fmm F, const int* __restrict__ pt, const int* __restrict__ pbx, int n,
+    const float2* __restrict__ mu, const double2* __restrict__ rec, cd* __restrict__ partial) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = pt[t], c = pbx[t];
+  const int lc = F.level[c];
+  const int pb = F.lpb[lc];
+  const float2* a = mu + F.eoff[c] + pb;  // a[m], |m| <= pb
+  const double2* R = rec + (size_t)lc * (F.pbmax + 2);
+  const double2 mc = F.centre[c];
+  const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
+  const double d2 = dx * dx + dy * dy;
+  const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr / F.k;
+  cd h0, h1;
+  hankel01(x, ix, h0, h1);
+  cd gprev = h0, gcur = cscale(h1, R[0].x);
+  const float2 e1 = make_float2((float)(dx * irr), (float)(dy * irr));
+  float2 ee = e1;
+  float2 S = fmul(a[0], f2(h0)), C = make_float2(0.f, 0.f);
+  for (int m = 1; m <= pb; ++m) {
+    const float2 g = f2(gcur);
+    const float2 wp = fmul(g, ee);                                // G_m e^{im th}
+    float2 wn = fmul(g, make_float2(ee.x, -ee.y));                // G_m e^{-im th}
+    if (m & 1) wn = make_float2(-wn.x, -wn.y);                    // (-1)^m
+    const float2 vp = fmul(a[m], wp), vn = fmul(a[-m], wn);
+    kahan2(S, C, make_float2(vp.x + vn.x, vp.y + vn.y));
+    if (m < pb) {
+      const double c1 = R[m].x * ix, c2 = R[m].y;
+      const cd gn = mk(fma(c1, gcur.x, -c2 * gprev.x), fma(c1, gcur.y, -c2 * gprev.y));
+      gprev = gcur;
+      gcur = gn;
+      ee = fmul(ee, e1);
+    }
+  }
+  partial[t] = mk((double)S.x - (double)C.x, (double)S.y - (double)C.y);
 }
 
 // Lift the 48 KB default of dynamic shared memory to the device's opt-in
@@ -1390,6 +1455,14 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     TRY(up(f->m2p_box, mbx));
     TRY(up(f->m2p_off, moff));
     QBX_CUDA_TRY(f->m2p_part.alloc(std::max<size_t>(1, mt.size())));
+    {  // the boxes M2P reads, and FP32 room for their normalised multipoles
+      std::vector<int> wb(mbx);
+      std::sort(wb.begin(), wb.end());
+      wb.erase(std::unique(wb.begin(), wb.end()), wb.end());
+      TRY(up(f->m2p_wbox, wb));
+      f->n_m2p_wbox = (int)wb.size();
+      QBX_CUDA_TRY(f->m2p_mu.alloc(wb.empty() ? 1 : std::max<int64_t>(1, f->n_coef)));
+    }
     f->n_dtgt = (int)dt.size();
     f->n_utgt = (int)ut.size();
     f->n_wtgt = (int)wt.size();
@@ -1846,8 +1919,18 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   }
   stage_begin(h, QBX_STAGE_M2P, s2);
   if (f->n_wtgt > 0 && f->n_m2p_pairs > 0) {
-    m2p_pair_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s2>>>(
-        F, f->m2p_tgt.ptr, f->m2p_box.ptr, f->n_m2p_pairs, f->m2p_part.ptr);
+    if (mixed) {
+      mpole_f32_list_kernel<<<f->n_m2p_wbox, kThreads, 0, s2>>>(F, f->m2p_wbox.ptr, f->conv.ptr,
+                                                                f->m2p_mu.ptr);
+      QBX_KCHECK("m2p_mu", s2);
+      m2p_pair_mixed_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s2>>>(
+          F, f->m2p_tgt.ptr, f->m2p_box.ptr, f->n_m2p_pairs, f->m2p_mu.ptr, f->m2p_rec.ptr,
+          f->m2p_part.ptr);
+      h->launches += 1;
+    } else {
+      m2p_pair_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s2>>>(
+          F, f->m2p_tgt.ptr, f->m2p_box.ptr, f->n_m2p_pairs, f->m2p_part.ptr);
+    }
     QBX_KCHECK("m2p", s2);
     m2p_sum_kernel<<<nblk(f->n_wtgt, kThreads), kThreads, 0, s2>>>(
         f->n_wtgt, f->wtgt.ptr, f->m2p_off.ptr, f->m2p_part.ptr, f->perm[PT_TGT].ptr, out);

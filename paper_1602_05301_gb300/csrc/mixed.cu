@@ -43,6 +43,25 @@ __global__ void sigma_tables_kernel(int n_levels, int pbmax, const int* __restri
   }
 }
 
+// Recurrence factors of G_m = sig_m H_m on level l (mixed M2P):
+// rec[m] = (2m sig_{m+1} / sig_m, sig_{m+1} / sig_{m-1}) for 1 <= m < pb_l,
+// rec[0] = (sig_1, 0).
+__global__ void m2p_rec_kernel(int n_levels, int pbmax, const int* __restrict__ lpb,
+                               const double* __restrict__ lsig, double2* __restrict__ rec) {
+  const int l = blockIdx.x;
+  if (l >= n_levels) return;
+  const double* sg = lsig + (size_t)l * (pbmax + 1);
+  double2* r = rec + (size_t)l * (pbmax + 2);
+  const int pb = lpb[l];
+  for (int m = threadIdx.x; m <= pbmax + 1; m += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (m == 0 && pb >= 1) v.x = exp(sg[1]);
+    if (m >= 1 && m < pb)
+      v = make_double2(2.0 * m * exp(sg[m + 1] - sg[m]), exp(sg[m + 1] - sg[m - 1]));
+    r[m] = v;
+  }
+}
+
 // Level l's matrices Tm[cls][n][lo] = sig_lo sig_n (-1)^lo W_{n+lo}(D) (orders
 // up to pb = pb_l; M2lNorm), stored in FP32. Grid: (cls, n), threads over lo.
 __global__ void m2l_f32_matrix_kernel(int l, int pb, int pbmax, const cd* __restrict__ t_m2l,
@@ -573,6 +592,9 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
   QBX_CUDA_TRY(f->conv.alloc((size_t)f->n_levels * (pbm + 1)));
   sigma_tables_kernel<<<1, 64>>>(f->n_levels, pbm, f->lpb.ptr, h->k, f->side, f->scale.ptr,
                                  f->lsig.ptr, f->conv.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  QBX_CUDA_TRY(f->m2p_rec.alloc((size_t)f->n_levels * (pbm + 2)));
+  m2p_rec_kernel<<<f->n_levels, 128>>>(f->n_levels, pbm, f->lpb.ptr, f->lsig.ptr, f->m2p_rec.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   // matrices for the levels that have V lists
   std::vector<long long> off(f->n_levels, 0);

@@ -73,6 +73,12 @@ struct qbx_handle {
   double k = 0;
   double h_max = 0;                         // longest panel
   DevBuf<double> node_xy, node_nrm, panel_h;
+  DevBuf<double> node_w;                    // density-grid weights
+  bool own_src = false;                     // the caller supplied the source grid
+  bool defer_conditions = false;            // Condition 4 is checked at tree build instead
+  std::vector<long long> curve_off;         // [n_curves + 1] first panel of every curve
+  std::vector<long long> panel_origin;      // original panel of every panel (refinement)
+  std::vector<double2> panel_interval;      // its part of the original panel, in u
   DevBuf<double> src_xy, src_nrm, src_w;
   DevBuf<double> ctr_xy, ctr_r;
   // Set when the library made the source grid itself (q_src nodes per panel
@@ -127,7 +133,14 @@ qbx_status launch_associate_direct(qbx_handle* h, const int64_t* on_node, const 
                                    double eps, cudaStream_t s);
 qbx_status launch_place_centres(qbx_handle* h, cudaStream_t s);
 // surface.cu
+void gl_nodes(int n, std::vector<double>& x, std::vector<double>& w);
 qbx_status upsample_geometry(qbx_handle* h);
+// conditions.cu
+qbx_status density_weights(qbx_handle* h);
+// api.cu: replace a handle's density geometry (after refinement); drops any plan
+qbx_status replace_geometry(qbx_handle* h, int64_t n_panels, DevBuf<double>& node_xy,
+                            DevBuf<double>& node_nrm, DevBuf<double>& node_w,
+                            const std::vector<double>& panel_h);
 qbx_status launch_strengths_upsampled(qbx_handle* h, cd cS, const cd* sigS, cd cD, const cd* sigD,
                                       cudaStream_t s);
 // fmm.cu

@@ -142,6 +142,8 @@ __global__ void strengths_upsampled_kernel(int64_t n_panels, int q, int qs,
 
 }  // namespace
 
+void gl_nodes(int n, std::vector<double>& x, std::vector<double>& w) { gauss_legendre(n, x, w); }
+
 qbx_status upsample_geometry(qbx_handle* h) {
   const int q = h->q, qs = h->q_src;
   std::vector<double> xq, wq, xs, ws, L, D;

@@ -99,6 +99,10 @@ struct FmmPlan {
   DevBuf<int> m2p_tgt, m2p_box, m2p_off;   // M2P (target, W box) pairs, CSR by wtgt position
   DevBuf<cd> m2p_part;                   // [pairs] partial values
   int n_m2p_pairs = 0;
+  DevBuf<int> m2p_wbox;                  // boxes M2P reads (mixed path converts them)
+  int n_m2p_wbox = 0;
+  DevBuf<float2> m2p_mu;                 // [n_coef] their sigma-normalised FP32 multipoles
+  DevBuf<double2> m2p_rec;               // [n_levels][pbmax + 2] sigma-scaled Hankel recurrence
   // Centre sets: [0] every centre, [1] the centres some target uses. Each
   // lists sorted centre indices (clist) and its M2QBXL work items, the
   // (sorted centre, W-list box) pairs grouped by list position (CSR wp_off).

@@ -21,6 +21,7 @@ QBX_OK, QBX_ERR_ARG, QBX_ERR_OOM, QBX_ERR_CUDA, QBX_ERR_CONDITION = 0, 1, 2, 3, 
 QBX_ERR_ASSOCIATION, QBX_ERR_TIMEOUT, QBX_ERR_STATE = 5, 6, 7
 QBX_FP64, QBX_MIXED = 0, 1
 QBX_DIRECT, QBX_FMM = 0, 1
+QBX_COND1, QBX_COND2, QBX_COND3, QBX_COND4 = 1, 2, 4, 8
 QBX_MAX_P = 16
 STAGES = ["strengths", "p2m", "m2m", "p2p", "p2qbxl", "m2l", "m2p", "m2qbxl", "p2l", "l2l",
           "l2p", "l2qbxl", "qbxl2p"]
@@ -36,7 +37,8 @@ class qbx_geometry_desc(ctypes.Structure):
                 ("node_xy", _vp), ("normal_xy", _vp), ("weight", _vp), ("panel_h", _vp),
                 ("q_src", ctypes.c_int32), ("src_xy", _vp), ("src_normal_xy", _vp),
                 ("src_weight", _vp), ("k", ctypes.c_double), ("p_qbx", ctypes.c_int32),
-                ("center_sides", ctypes.c_int32)]
+                ("center_sides", ctypes.c_int32), ("n_curves", ctypes.c_int32),
+                ("curve_panel_offset", _vp), ("defer_conditions", ctypes.c_int32)]
 
 
 class qbx_tree_desc(ctypes.Structure):
@@ -109,6 +111,16 @@ def library() -> ctypes.CDLL:
             lib.qbx_get_source_grid.argtypes = [_vp, _vp, _vp, _vp]
             lib.qbx_table1_q_src.restype = ctypes.c_int32
             lib.qbx_table1_q_src.argtypes = [ctypes.c_int32, ctypes.c_double]
+            lib.qbx_check_conditions.restype = ctypes.c_int
+            lib.qbx_check_conditions.argtypes = [_vp, _vp, _vp]
+            lib.qbx_refine.restype = ctypes.c_int
+            lib.qbx_refine.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+            lib.qbx_get_geometry.restype = ctypes.c_int
+            lib.qbx_get_geometry.argtypes = [_vp] + [_vp] * 8
+            lib.qbx_solve_dirichlet.restype = ctypes.c_int
+            lib.qbx_solve_dirichlet.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                                ctypes.c_int32, _vp, _vp, _vp]
             _lib = lib
     return _lib
 
@@ -237,7 +249,7 @@ class LayerPotential:
           density grid (n_nodes values).
     """
 
-    def __init__(self, geom, p, sides=2, src=None, q_src=0):
+    def __init__(self, geom, p, sides=2, src=None, q_src=0, defer_conditions=False):
         self._keep = []
         k = float(np.atleast_1d(geom.k)[0]) if hasattr(geom, "k") else float(geom["k"])
         g = geom if isinstance(geom, dict) else geom.__dict__
@@ -260,10 +272,20 @@ class LayerPotential:
         d.k = k
         d.p_qbx = int(p)
         d.center_sides = int(sides)
+        po = g.get("panel_offset") if isinstance(g, dict) else None
+        if po is not None:
+            po = np.ascontiguousarray(po, dtype=np.int64)
+            self._keep.append(po)
+            d.n_curves = po.shape[0] - 1
+            d.curve_panel_offset = ptr(po)
+        d.defer_conditions = 1 if defer_conditions else 0
         self.k, self.p, self.sides = k, int(p), int(sides)
         self.n_nodes = node_xy.shape[0]
         self.n_src = (d.n_panels * d.q_src) if d.q_src else self.n_nodes
         self.n_density = self.n_nodes if (q_src and src is None) else self.n_src
+        self.q, self.q_src = int(g["q"]), int(d.q_src)
+        self._upsample = bool(q_src and src is None)
+        self.n_curves = int(d.n_curves) if d.n_curves > 0 else 1
         self.n_centres = self.n_nodes * self.sides
         self.handle = qbx_geometry_create(d)
         self._keep = []
@@ -311,6 +333,67 @@ class LayerPotential:
         _check(library().qbx_get_box_orders(self.handle, out.ctypes.data, 25))
         depth = int(self.stats()["depth"])
         return out[:depth + 1]
+
+    def check_conditions(self):
+        """(panel flags [n_panels] int32 of QBX_COND* bits, counts [4]) -- Sec. 3.3."""
+        n = self.geometry_size()
+        flags = np.zeros(n, np.int32)
+        counts = np.zeros(4, np.int64)
+        _check(library().qbx_check_conditions(self.handle, ptr(flags), ptr(counts)))
+        return flags, counts
+
+    def refine(self, max_rounds=20):
+        """Bisects flagged panels until Conditions 1-4 hold (qbx_refine); returns
+        (rounds, n_panels). The plan is dropped: build it again."""
+        r = np.zeros(1, np.int32)
+        npan = np.zeros(1, np.int64)
+        _check(library().qbx_refine(self.handle, int(max_rounds), ptr(r), ptr(npan)))
+        self.n_nodes = int(npan[0]) * self.q
+        self.n_src = int(npan[0]) * self.q_src if self.q_src else self.n_nodes
+        self.n_density = self.n_nodes if self._upsample else self.n_src
+        self.n_centres = self.n_nodes * self.sides
+        self.n_targets = 0
+        return int(r[0]), int(npan[0])
+
+    def solve_dirichlet(self, rhs, mode=QBX_FMM, p_fmm=20, precision=QBX_FP64, tol=1e-10,
+                        max_iter=500, restart=50, stream=None):
+        """sigma of (1/2) sigma + D* sigma + i k S* sigma = rhs (qbx_solve_dirichlet);
+        returns (sigma, iterations, relative residual). The handle's plan is
+        replaced by the solver's (targets: the nodes, exterior side)."""
+        b = np.ascontiguousarray(rhs, dtype=np.complex128) if not hasattr(rhs, "data_ptr") else rhs
+        sig = np.empty(self.n_nodes, np.complex128)
+        it = np.zeros(1, np.int32)
+        res = np.zeros(1)
+        _check(library().qbx_solve_dirichlet(self.handle, ptr(b), ptr(sig), int(mode), int(p_fmm),
+                                             int(precision), float(tol), int(max_iter),
+                                             int(restart), ptr(it), ptr(res), stream))
+        self.n_targets = self.n_nodes
+        return sig, int(it[0]), float(res[0])
+
+    def geometry_size(self):
+        n = np.zeros(1, np.int64)
+        _check(library().qbx_get_geometry(self.handle, ptr(n), None, None, None, None, None,
+                                          None, None))
+        return int(n[0])
+
+    def geometry(self):
+        """The handle's density geometry: dict with node_xy, normal_xy, weight,
+        panel_h, panel_origin, panel_interval, panel_offset (numpy)."""
+        n = self.geometry_size()
+        nn = n * self.q
+        out = dict(node_xy=np.empty((nn, 2)), normal_xy=np.empty((nn, 2)),
+                   weight=np.empty(nn), panel_h=np.empty(n),
+                   panel_origin=np.empty(n, np.int64), panel_interval=np.empty((n, 2)),
+                   panel_offset=np.empty(self.n_curves + 1, np.int64))
+        m = np.zeros(1, np.int64)
+        _check(library().qbx_get_geometry(
+            self.handle, ptr(m), ptr(out["node_xy"]), ptr(out["normal_xy"]), ptr(out["weight"]),
+            ptr(out["panel_h"]), ptr(out["panel_origin"]), ptr(out["panel_interval"]),
+            ptr(out["panel_offset"])))
+        out["q"] = self.q
+        out["k"] = self.k
+        out["panel_of_node"] = np.repeat(np.arange(n, dtype=np.int64), self.q)
+        return out
 
     def source_grid(self):
         """(src_xy [n_src][2], src_normal_xy [n_src][2], src_weight [n_src])."""

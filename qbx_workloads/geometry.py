@@ -54,12 +54,13 @@ class Geometry:
             assert self.n_curves == 1 or np.all(self.k == self.k[0])
             return dict(node_xy=self.node_xy, normal_xy=self.normal_xy, weight=self.weight,
                         panel_of_node=self.panel_of_node, panel_h=self.panel_h,
-                        k=float(self.k[0]), q=self.q)
+                        k=float(self.k[0]), q=self.q, panel_offset=self.panel_offset)
         p0, p1 = int(self.panel_offset[curve]), int(self.panel_offset[curve + 1])
         n0, n1 = p0 * self.q, p1 * self.q
         return dict(node_xy=self.node_xy[n0:n1], normal_xy=self.normal_xy[n0:n1],
                     weight=self.weight[n0:n1], panel_of_node=self.panel_of_node[n0:n1] - p0,
-                    panel_h=self.panel_h[p0:p1], k=float(self.k[curve]), q=self.q)
+                    panel_h=self.panel_h[p0:p1], k=float(self.k[curve]), q=self.q,
+                    panel_offset=np.array([0, p1 - p0], dtype=np.int64))
 
 
 def discretise_curve(gamma: Callable, dgamma: Callable, n_panels: int, q: int,
@@ -73,6 +74,28 @@ def discretise_curve(gamma: Callable, dgamma: Callable, n_panels: int, q: int,
     speed = np.hypot(d[:, 0], d[:, 1])
     normal = np.stack([d[:, 1] / speed, -d[:, 0] / speed], axis=-1)
     weight = (np.tile(w, n_panels) * 0.5 * dt) * speed
+    panel_of_node = np.repeat(np.arange(n_panels, dtype=np.int64), q)
+    panel_h = weight.reshape(n_panels, q).sum(axis=1)
+    return Geometry(node_xy=np.ascontiguousarray(xy), normal_xy=np.ascontiguousarray(normal),
+                    weight=weight, panel_of_node=panel_of_node, panel_h=panel_h, param_t=t, q=q,
+                    panel_offset=np.array([0, n_panels], dtype=np.int64),
+                    k=np.array([float(k)]))
+
+
+def discretise_breaks(gamma: Callable, dgamma: Callable, t_breaks, q: int,
+                      k: float = 1.0) -> Geometry:
+    """Like discretise_curve, with the panels between the given parameter values
+    t_breaks[0] < ... < t_breaks[n] (t_breaks[n] = t_breaks[0] + 2 pi)."""
+    x, w = gauss_legendre(q)
+    tb = np.asarray(t_breaks, dtype=np.float64)
+    dt = np.diff(tb)
+    n_panels = dt.size
+    t = (tb[:-1, None] + (x[None, :] + 1.0) * 0.5 * dt[:, None]).reshape(-1)
+    xy = np.stack(gamma(t), axis=-1)
+    d = np.stack(dgamma(t), axis=-1)
+    speed = np.hypot(d[:, 0], d[:, 1])
+    normal = np.stack([d[:, 1] / speed, -d[:, 0] / speed], axis=-1)
+    weight = (np.tile(w, n_panels) * 0.5 * np.repeat(dt, q)) * speed
     panel_of_node = np.repeat(np.arange(n_panels, dtype=np.int64), q)
     panel_h = weight.reshape(n_panels, q).sum(axis=1)
     return Geometry(node_xy=np.ascontiguousarray(xy), normal_xy=np.ascontiguousarray(normal),

@@ -343,3 +343,34 @@ def test_rotation_and_linearity(oracle):
     u = oracle.direct_potential(g.node_xy, g.normal_xy, g.weight, k, t, s1, s2)
     ut = oracle.direct_potential(g.node_xy + 10.0, g.normal_xy, g.weight, k, t + 10.0, s1, s2)
     assert _rel(ut, u) < 1e-11
+
+
+# ---------------------------------------------------------------- Conditions 1-4 (Sec. 3.3)
+def test_condition_flags_two_circles_closed_form(oracle):
+    """Two unit circles 0.05 apart: the oracle's brute-force flags equal those of
+    the closed-form distance to circular arcs (Conditions 1 and 3), for equal
+    and for very different panel sizes on the two circles."""
+    from tests.condition_geoms import expected_two_circles, two_circles
+    for n1, n2 in ((24, 24), (48, 12)):
+        g = two_circles(0.05, n1, n2)
+        got = oracle.conditions(g.as_dict(), sides=2)
+        exp = expected_two_circles(g, n1, n2, 0.05)
+        assert np.array_equal(got & 5, exp), (n1, n2, np.nonzero(got != exp))
+        assert (got & 1).any()
+    g = two_circles(0.05, 48, 12)
+    assert (oracle.conditions(g.as_dict()) & 4).any()     # coarse arcs near fine centres
+    g = two_circles(1.0, 24, 24)                           # far apart: nothing
+    assert not oracle.conditions(g.as_dict()).any()
+
+
+def test_condition_flags_two_to_one_and_wavelength(oracle):
+    from tests.condition_geoms import uneven_circle
+    g = uneven_circle(3.0)
+    f = oracle.conditions(g.as_dict())
+    assert np.nonzero(f & 2)[0].tolist() == [5]            # the long panel only
+    g = uneven_circle(1.9)
+    assert not (oracle.conditions(g.as_dict()) & 2).any()
+    g = discretise_curve(*starfish(0.3, 5), 16, 16, k=12.0)  # k h about 6 > 5
+    f = oracle.conditions(g.as_dict())
+    assert np.array_equal((f & 8) != 0, 12.0 * g.panel_h > 5.0)
+    assert (f & 8).any()
