@@ -470,10 +470,11 @@ def run_batch(args, w, ws, rank, local):
         G = g.as_dict(c)
         lp = qbx.LayerPotential(G, w["p"], sides=1)
         n = G["node_xy"].shape[0]
-        _, _, ch = lp.autotune(G["node_xy"], np.arange(n), np.ones(n, np.int8), p_fmm=w["p_fmm"],
-                               precision=prec, reps=2)
+        _, plan, _ = lp.autotune_tol(G["node_xy"], np.arange(n), np.ones(n, np.int8),
+                                     p_fmm=w["p_fmm"], tol=1e-6 if args.precision == "mixed"
+                                     else 1e-10, precision=prec, reps=2)
         probs.append(lp)
-        chosen.append(ch)
+        chosen.append(plan)
     plan_s = time.perf_counter() - t0
     b = qbx.Batch(probs, n_streams=16)
     sS = torch.from_numpy(np.ascontiguousarray(w["sigma_S"])).to(dev)
@@ -510,9 +511,16 @@ def run_batch(args, w, ws, rank, local):
                dtype="f64" if prec == qbx.QBX_FP64 else "f32+f64", data="synthetic",
                config={"workload": WORKLOADS[4] % w["name"], "precision": args.precision,
                        "n_curves": g.n_curves, "n_sources": int(g.n), "n_targets": n_t,
-                       "plans": {"direct": chosen.count(0),
-                                 "fmm_nmax32": chosen.count(1), "fmm_nmax64": chosen.count(2),
-                                 "fmm_nmax128": chosen.count(3)},
+                       "plans": {"direct": sum(c["mode"] == 0 for c in chosen),
+                                 "fmm": sum(c["mode"] == 1 for c in chosen),
+                                 "fmm_n_max": sorted(set(c["n_max"] for c in chosen
+                                                         if c["mode"] == 1)),
+                                 "fmm_p_fmm": sorted(set(c["p_fmm"] for c in chosen
+                                                         if c["mode"] == 1)),
+                                 "cuda_core_m2l": sum(c["engine"] == 2 for c in chosen),
+                                 "l2qbxl_g": sorted(set(c["g"] for c in chosen))},
+                       "autotuner": "qbx_autotune_tol, tolerance 1e-6 (mixed) / 1e-10 (fp64) "
+                                    "against the most accurate plan",
                        "plan_and_autotune_s": plan_s,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single"},

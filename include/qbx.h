@@ -133,6 +133,10 @@ qbx_status qbx_geometry_create(const qbx_geometry_desc *desc, qbx_handle **out);
  * n_max: particles per leaf (sources + centres + targets), 0 => 64.
  * assoc_out (optional, [n_targets] int32) receives the centre of every target
  * (-1: direct quadrature).
+ * m2l_engine: the M2L translations of FMM mode (Sec. 7.2, Stage 4): 0 the
+ * default (FP64 on tensor cores for levels whose bf16 split is exact, mixed
+ * precision on the FP32 CUDA-core GEMM), 1 tensor cores in both precisions,
+ * 2 CUDA cores in both; every engine meets the precision's tolerance.
  * Errors: QBX_ERR_ASSOCIATION (count and first target in qbx_last_error()),
  * QBX_ERR_ARG, QBX_ERR_OOM, QBX_ERR_CUDA. Synchronous.
  */
@@ -147,6 +151,7 @@ typedef struct {
   int32_t n_max;
   double eps_assoc;                /* <= 0 => 0.1                                        */
   int32_t *assoc_out;              /* optional                                           */
+  int32_t m2l_engine;              /* 0 default, 1 tensor cores, 2 CUDA cores            */
 } qbx_tree_desc;
 
 qbx_status qbx_tree_build(qbx_handle *h, const qbx_tree_desc *desc);
@@ -358,6 +363,42 @@ qbx_status qbx_get_source_grid(const qbx_handle *h, double *src_xy, double *src_
                                double *src_weight);
 
 /*
+ * Waits for all device work and reports device-side failures that an
+ * asynchronous call could not return: QBX_ERR_TIMEOUT if a bounded wait of a
+ * kernel (the mbarrier waits of the tensor-core M2L of Sec. 7.2, Stage 4: a
+ * deadline of 1 s each) gave up since the last check; the results of the
+ * evaluations since then are invalid, and the flag is cleared. An evaluation
+ * with host buffers makes the same check before it returns. Errors:
+ * QBX_ERR_ARG (NULL handle), QBX_ERR_CUDA.
+ */
+qbx_status qbx_sync(qbx_handle *h);
+
+/*
+ * Self-test of the failure path above: one warp waits, with the bounded wait
+ * of the tensor-core kernels and a deadline of limit_us microseconds, on an
+ * mbarrier that nothing completes, and sets the handle's wait flag when the
+ * wait runs out. The next qbx_sync (or evaluation with host buffers) then
+ * returns QBX_ERR_TIMEOUT, and the handle stays usable. Synchronous. Errors:
+ * QBX_ERR_ARG (NULL handle, limit_us outside 1..1e6), QBX_ERR_STATE (no FMM
+ * plan), QBX_ERR_CUDA.
+ */
+qbx_status qbx_selftest_wait_timeout(qbx_handle *h, int32_t limit_us);
+
+/*
+ * H_0(x) and H_1(x) of the first kind, as every kernel of the library
+ * evaluates them on the device (the Hankel values that start the recurrences
+ * of Sec. 7.2's translations and the kernel G = (i/4) H_0(k|x - y|) of Sec. 1):
+ * the ascending series (DLMF 10.2.2, 10.8.1) below the series reach, the CUDA
+ * math library's j0/y0/j1/y1 above it. variant 0: the FP64 path (reach x < 5,
+ * relative error about 1e-14 at most); 1: the mixed-precision path (reach
+ * x < 8, below 3e-13). x: host [n], positive and finite; out: host [n][4] =
+ * (Re H_0, Im H_0, Re H_1, Im H_1). Synchronous. Errors: QBX_ERR_ARG (NULL
+ * pointer with n > 0, n < 0, x[i] <= 0 or not finite, unknown variant),
+ * QBX_ERR_OOM / QBX_ERR_CUDA.
+ */
+qbx_status qbx_hankel01(const double *x, int64_t n, int32_t variant, double *out);
+
+/*
  * Table 1 of the paper (Sec. 3.2): source nodes per panel q_src for q density
  * nodes and precision eps, as printed for q = 2, 4, 8, 16 and eps = 1e-3,
  * 1e-6, 1e-9, 1e-12. Other q take the row of the next tabulated q, other eps
@@ -382,6 +423,36 @@ int32_t qbx_table1_q_src(int32_t q, double eps);
 qbx_status qbx_autotune(qbx_handle *h, const qbx_tree_desc *desc, int32_t precision,
                         int32_t has_S, int32_t has_D, int32_t reps, double *times_ms,
                         int32_t *chosen);
+
+/*
+ * Accuracy-aware plan selection, the autotuner of batched evaluation. Builds
+ * candidate plans of `desc` (its targets and association), times `reps`
+ * evaluations of each (CUDA events, random unit densities, the given
+ * precision and layers) and keeps the fastest whose result is within tol
+ * (relative l2) of the most accurate plan (QBX_DIRECT below 512 sources, else
+ * QBX_FMM at desc->p_fmm; both FP64). The search is greedy:
+ *  1. plan kind and leaf size: QBX_DIRECT, QBX_FMM with n_max 16, 32, 64, 128;
+ *  2. for an FMM winner, box orders p_fmm lowered by 4 at a time while the
+ *     result stays within tol (the per-curve order schedule);
+ *  3. the M2L engine: the default (FP64 path on tensor cores where the bf16
+ *     split is exact, mixed path on the FP32 CUDA-core GEMM), tensor cores for
+ *     both precisions, or CUDA cores for both;
+ *  4. the centres per warp of L2QBXL (4, 8, 16, 32).
+ * Decisions are cached per (sources rounded to a power of two, k * mean panel
+ * length rounded to 1/8, p, precision, sides, layers, tol rounded to a power of
+ * ten), so similar curves of a batch are tuned once. The winner's plan is left
+ * built in the handle.
+ * plan_out (optional, int32 [5]): mode, n_max, p_fmm, M2L engine (0 default,
+ * 1 tensor cores for both precisions, 2 CUDA cores), L2QBXL centres per warp
+ * (0 automatic);
+ * report (optional, double [3]): its median time in ms and its error (0 when
+ * the decision came from the cache), and the candidates tried.
+ * Errors: QBX_ERR_CONDITION if no candidate meets tol; those of
+ * qbx_tree_build and qbx_layer_potential_eval. Synchronous.
+ */
+qbx_status qbx_autotune_tol(qbx_handle *h, const qbx_tree_desc *desc, int32_t precision,
+                            int32_t has_S, int32_t has_D, double tol, int32_t reps,
+                            int32_t *plan_out, double *report);
 
 /*
  * Batched evaluation of many independent problems (for example curves with

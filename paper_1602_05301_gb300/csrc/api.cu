@@ -234,6 +234,11 @@ extern "C" qbx_status qbx_tree_build(qbx_handle* h, const qbx_tree_desc* d) {
     set_error("qbx_tree_build: unknown mode %d", d->mode);
     return QBX_ERR_ARG;
   }
+  if (d->m2l_engine < 0 || d->m2l_engine > 2) {
+    set_error("qbx_tree_build: unknown m2l_engine %d", d->m2l_engine);
+    return QBX_ERR_ARG;
+  }
+  h->m2l_engine = d->m2l_engine;
   h->planned = false;
   if (h->k * h->h_max > 5.0) {  // a geometry accepted with defer_conditions, not yet refined
     set_error("Condition 4 violated: k * max h = %.4g > 5; call qbx_refine", h->k * h->h_max);
@@ -394,8 +399,18 @@ extern "C" qbx_status qbx_layer_potential_eval(qbx_handle* h, double cS_re, doub
   if (alpha_out)
     QBX_CUDA_TRY(cudaMemcpyAsync(alpha_out, h->alpha.ptr,
                                  h->n_ctr * (2 * h->p + 1) * sizeof(cd), cudaMemcpyDefault, s));
-  if (host_io) QBX_CUDA_TRY(cudaStreamSynchronize(s));
+  if (host_io) {
+    QBX_CUDA_TRY(cudaStreamSynchronize(s));
+    return read_wait_flag(h);
+  }
   return QBX_OK;
+}
+
+extern "C" qbx_status qbx_sync(qbx_handle* h) {
+  set_error("%s", "");
+  if (!h) { set_error("qbx_sync: NULL handle"); return QBX_ERR_ARG; }
+  QBX_CUDA_TRY(cudaDeviceSynchronize());
+  return read_wait_flag(h);
 }
 
 namespace {

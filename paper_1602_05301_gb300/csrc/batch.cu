@@ -323,3 +323,185 @@ extern "C" qbx_status qbx_autotune(qbx_handle* h, const qbx_tree_desc* desc, int
   if (chosen) *chosen = best;
   return QBX_OK;
 }
+
+// ---------------------------------------------------------------- accuracy-aware autotuner
+namespace {
+
+struct TolKey {
+  int lg_n, kh8, p, prec, sides, S, D, lg_tol;
+  bool operator<(const TolKey& o) const {
+    return std::tie(lg_n, kh8, p, prec, sides, S, D, lg_tol) <
+           std::tie(o.lg_n, o.kh8, o.p, o.prec, o.sides, o.S, o.D, o.lg_tol);
+  }
+};
+struct TolPlan {
+  int mode, n_max, p_fmm, engine, g;
+};
+std::mutex g_tol_mu;
+std::map<TolKey, TolPlan> g_tol_cache;
+
+}  // namespace
+
+extern "C" qbx_status qbx_autotune_tol(qbx_handle* h, const qbx_tree_desc* desc,
+                                       int32_t precision, int32_t has_S, int32_t has_D,
+                                       double tol, int32_t reps, int32_t* plan_out,
+                                       double* report) {
+  set_error("%s", "");
+  if (!h || !desc || (!has_S && !has_D) || !(tol > 0.0) || desc->p_fmm < 1) {
+    set_error("qbx_autotune_tol: bad arguments");
+    return QBX_ERR_ARG;
+  }
+  reps = std::max(1, std::min(reps, 20));
+  double hmean = 0.0;
+  {
+    std::vector<double> hh(h->n_panels);
+    QBX_CUDA_TRY(cudaMemcpy(hh.data(), h->panel_h.ptr, hh.size() * sizeof(double),
+                            cudaMemcpyDeviceToHost));
+    for (double v : hh) hmean += v;
+    hmean /= (double)std::max<int64_t>(1, h->n_panels);
+  }
+  const TolKey key{(int)std::lround(std::log2((double)std::max<int64_t>(1, h->n_src))),
+                   (int)std::lround(8.0 * h->k * hmean), h->p, precision, h->sides, has_S, has_D,
+                   (int)std::lround(std::log10(tol))};
+  TolPlan best{-1, 0, 0, 0, 0};
+  {
+    std::lock_guard<std::mutex> lock(g_tol_mu);
+    auto it = g_tol_cache.find(key);
+    if (it != g_tol_cache.end()) best = it->second;
+  }
+  const int64_t nt = std::max<int64_t>(1, desc->n_targets);
+  DevBuf<cd> sig, out, ref;
+  QBX_CUDA_TRY(sig.alloc(std::max<int64_t>(1, h->n_density())));
+  QBX_CUDA_TRY(out.alloc(nt));
+  QBX_CUDA_TRY(ref.alloc(nt));
+  {  // random unit densities (deterministic)
+    std::vector<cd> hs(sig.n);
+    uint64_t st = 0x2545f4914f6cdd1dull;
+    for (auto& v : hs) {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      const double a = (double)(st >> 11) * (1.0 / 9007199254740992.0) * 6.283185307179586;
+      v = mk(std::cos(a), std::sin(a));
+    }
+    QBX_CUDA_TRY(cudaMemcpy(sig.ptr, hs.data(), hs.size() * sizeof(cd), cudaMemcpyHostToDevice));
+  }
+  const double* sS = has_S ? (const double*)sig.ptr : nullptr;
+  const double* sD = has_D ? (const double*)sig.ptr : nullptr;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto finish = [&](qbx_status st) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  };
+  auto build = [&](const TolPlan& c) -> qbx_status {
+    qbx_tree_desc d = *desc;
+    d.mode = c.mode;
+    d.n_max = c.n_max;
+    d.p_fmm = c.p_fmm > 0 ? c.p_fmm : desc->p_fmm;
+    d.m2l_engine = c.engine;
+    h->l2qbxl_g = c.g;
+    return qbx_tree_build(h, &d);
+  };
+  // median time of reps evaluations (after one warm-up) in precision pr into o
+  auto timed = [&](int pr, cd* o, double& ms) -> qbx_status {
+    std::vector<float> v;
+    for (int r = 0; r <= reps; ++r) {
+      cudaEventRecord(e0, 0);
+      const qbx_status s = qbx_layer_potential_eval(h, 1.0, 0.0, sS, 1.0, 0.0, sD, (double*)o,
+                                                    nullptr, pr, nullptr);
+      cudaEventRecord(e1, 0);
+      if (s != QBX_OK) return s;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error("qbx_autotune_tol: a candidate evaluation failed");
+        return QBX_ERR_CUDA;
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) v.push_back(t);
+    }
+    std::sort(v.begin(), v.end());
+    ms = v[v.size() / 2];
+    return QBX_OK;
+  };
+  // relative l2 distance of out from ref (host side: small vectors)
+  auto error = [&]() -> double {
+    std::vector<cd> a(nt), b(nt);
+    cudaMemcpy(a.data(), out.ptr, nt * sizeof(cd), cudaMemcpyDeviceToHost);
+    cudaMemcpy(b.data(), ref.ptr, nt * sizeof(cd), cudaMemcpyDeviceToHost);
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < nt; ++i) {
+      num += (a[i].x - b[i].x) * (a[i].x - b[i].x) + (a[i].y - b[i].y) * (a[i].y - b[i].y);
+      den += b[i].x * b[i].x + b[i].y * b[i].y;
+    }
+    return den > 0.0 ? std::sqrt(num / den) : std::sqrt(num);
+  };
+  double best_ms = 0.0, best_err = 0.0;
+  int tried = 0;
+  if (best.mode < 0) {
+    // the reference: the most accurate plan (direct QBX for small problems,
+    // else FMM at the requested orders), FP64
+    const bool small = h->n_src < 512;
+    TolPlan refp{small ? QBX_DIRECT : QBX_FMM, 64, desc->p_fmm, 0, 0};
+    qbx_status s = build(refp);
+    if (s != QBX_OK) return finish(s);
+    double ms;
+    if ((s = timed(QBX_FP64, ref.ptr, ms)) != QBX_OK) return finish(s);
+    double bt = 1e300;
+    auto consider = [&](const TolPlan& c) -> qbx_status {
+      qbx_status st = build(c);
+      if (st != QBX_OK) return st;
+      double t;
+      if ((st = timed(precision, out.ptr, t)) != QBX_OK) return st;
+      const double err = error();
+      ++tried;
+      if (err <= tol && t < bt) {
+        bt = t;
+        best = c;
+        best_ms = t;
+        best_err = err;
+      }
+      return QBX_OK;
+    };
+    // 1. plan kind and leaf size at the requested orders
+    if ((s = consider({QBX_DIRECT, 0, desc->p_fmm, 0, 0})) != QBX_OK) return finish(s);
+    if (!small)
+      for (int nm : {16, 32, 64, 128})
+        if ((s = consider({QBX_FMM, nm, desc->p_fmm, 0, 0})) != QBX_OK) return finish(s);
+    if (best.mode == QBX_FMM) {
+      // 2. lower box orders while the result stays within tol
+      for (int pf = desc->p_fmm - 4; pf >= 4; pf -= 4) {
+        const double before = bt;
+        if ((s = consider({QBX_FMM, best.n_max, pf, 0, 0})) != QBX_OK) return finish(s);
+        if (bt == before) break;
+      }
+      // 3. the M2L engine, 4. centres per L2QBXL warp
+      for (int e : {1, 2})
+        if ((s = consider({QBX_FMM, best.n_max, best.p_fmm, e, 0})) != QBX_OK) return finish(s);
+      for (int g : {4, 8, 16, 32})
+        if ((s = consider({QBX_FMM, best.n_max, best.p_fmm, best.engine, g})) != QBX_OK)
+          return finish(s);
+    }
+    if (best.mode < 0) {
+      set_error("qbx_autotune_tol: no candidate met tol = %g", tol);
+      return finish(QBX_ERR_CONDITION);
+    }
+    std::lock_guard<std::mutex> lock(g_tol_mu);
+    g_tol_cache[key] = best;
+  }
+  const qbx_status s = build(best);
+  if (s != QBX_OK) return finish(s);
+  if (plan_out) {
+    plan_out[0] = best.mode;
+    plan_out[1] = best.n_max;
+    plan_out[2] = best.p_fmm;
+    plan_out[3] = best.engine;
+    plan_out[4] = best.g;
+  }
+  if (report) {
+    report[0] = best_ms;
+    report[1] = best_err;
+    report[2] = tried;
+  }
+  return finish(QBX_OK);
+}

@@ -159,12 +159,7 @@ __global__ void __launch_bounds__(kTile) p2p_direct_kernel(
         if (r == 0.0) continue;
         const double x = k * r;
         cd h0, h1;
-        if (x < 2.0) {
-          hankel01_series(x, h0, h1);
-        } else {
-          if (HS) h0 = mk(j0(x), y0(x));
-          if (HD) h1 = mk(j1(x), y1(x));
-        }
+        hankel01_any<false, HS, HD>(x, 1.0 / x, h0, h1);
         if (HS) cfma(acc, s_q[jj], h0);
         if (HD) cfma(acc, s_d[jj], cscale(h1, k * (s_n[jj].x * dx + s_n[jj].y * dy) / r));
       }

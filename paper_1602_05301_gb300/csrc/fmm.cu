@@ -75,6 +75,8 @@ struct Fmm {
   const double2* snrm;
   const cd* qs;
   const cd* ds;
+  const float2* q32;     // FP32 charges (mixed path)
+  const float4* ab32;    // FP32 dipole factors (A, B) (mixed path)
   const double2* cxy;
   const double* crad;    // sorted centre radii
   const int* cid;
@@ -225,13 +227,26 @@ __global__ void powers_kernel(int n_levels, int pbmax, const int* __restrict__ l
 }
 
 // ---------------------------------------------------------------- strengths
+// Sorted strengths; for the mixed path also their FP32 forms, with the dipole
+// factors A = d (k/2) nu and B = d (k/2) conj(nu) (nu = n_x + i n_y) formed
+// once per source instead of once per (source, centre) pair.
 __global__ void gather_strengths_kernel(int64_t n, const int* __restrict__ perm,
                                         const cd* __restrict__ q, const cd* __restrict__ d,
-                                        cd* __restrict__ qs, cd* __restrict__ ds) {
+                                        const double2* __restrict__ snrm, double k,
+                                        cd* __restrict__ qs, cd* __restrict__ ds,
+                                        float2* __restrict__ q32, float4* __restrict__ ab32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  qs[i] = q[perm[i]];
-  ds[i] = d[perm[i]];
+  const cd qi = q[perm[i]], di = d[perm[i]];
+  qs[i] = qi;
+  ds[i] = di;
+  if (q32) {
+    const cd dk = cscale(di, 0.5 * k);
+    const cd nu = mk(snrm[i].x, snrm[i].y);
+    const cd A = cmul(dk, nu), B = cmul(dk, cconj(nu));
+    q32[i] = make_float2((float)qi.x, (float)qi.y);
+    ab32[i] = make_float4((float)A.x, (float)A.y, (float)B.x, (float)B.y);
+  }
 }
 
 // ---------------------------------------------------------------- P2M (Stage 2)
@@ -684,12 +699,7 @@ __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __
     if (r2 == 0.0) return;
     const double ir = rsqrt(r2), x = k * r2 * ir;
     cd h0, h1;
-    if (x < 2.0) {
-      hankel01_series(x, ik * ir, h0, h1);
-    } else {
-      if (HS) h0 = mk(j0(x), y0(x));
-      if (HD) h1 = mk(j1(x), y1(x));
-    }
+    hankel01_any<false, HS, HD>(x, ik * ir, h0, h1);
     if (HS) cfma(acc, F.qs[j], h0);
     if (HD) {
       const double2 nv = F.snrm[j];
@@ -990,7 +1000,7 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   const double irr = rsqrt(d2), rr = d2 * irr, x = k * rr, ix = ik * irr;
   const cd e1 = mk(dx * irr, dy * irr);
   cd h0, h1;
-  hankel01(x, ix, h0, h1);
+  hankel01_wide(x, ix, h0, h1);
   // scaled Hankel values hs_m = H_m rho^m: hs_{m+1} = (2m rho / x) hs_m - rho^2 hs_{m-1}
   const double r2 = rho * rho, c1 = 2.0 * rho * ix, ir = irho;
   cd hprev = h0, hcur = cscale(h1, rho);
@@ -1095,7 +1105,7 @@ __global__ void __launch_bounds__(kThreads) m2p_pair_mixed_kernel(
   const double d2 = dx * dx + dy * dy;
   const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr / F.k;
   cd h0, h1;
-  hankel01(x, ix, h0, h1);
+  hankel01_wide(x, ix, h0, h1);
   cd gprev = h0, gcur = cscale(h1, R[0].x);
   const float2 e1 = make_float2((float)(dx * irr), (float)(dy * irr));
   float2 ee = e1;
@@ -1230,14 +1240,13 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
   auto one = [&](int j) {
     const double2 y = F.sxy[j];
     float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-    if (HD) {  // A = d (k/2) nu, B = d (k/2) conj(nu)
-      const cd dk = cscale(F.ds[j], 0.5 * k);
-      const cd nu = mk(F.snrm[j].x, F.snrm[j].y);
-      A = f2(cmul(dk, nu));
-      B = f2(cmul(dk, cconj(nu)));
+    if (HD) {  // A = d (k/2) nu, B = d (k/2) conj(nu), formed once per source
+      const float4 ab = F.ab32[j];
+      A = make_float2(ab.x, ab.y);
+      B = make_float2(ab.z, ab.w);
     }
     p2qbxl_pair_mixed<PM, HS, HD>(S, C, y.x - c.x, y.y - c.y,
-                                  HS ? f2(F.qs[j]) : make_float2(0.f, 0.f), A, B, k, ik, rho, irho, p);
+                                  HS ? F.q32[j] : make_float2(0.f, 0.f), A, B, k, ik, rho, irho, p);
   };
   const SourceCursor sc{F.uidx, F.rsrc, F.uoff[b], F.uoff[b + 1] - F.uoff[b], wdoff[i],
                         wdoff[i + 1] - wdoff[i], wdbox};
@@ -1377,6 +1386,8 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   TRY(tc_plan_build(h, f));
   QBX_CUDA_TRY(f->qs.alloc(std::max<int64_t>(1, h->n_src)));
   QBX_CUDA_TRY(f->ds.alloc(std::max<int64_t>(1, h->n_src)));
+  QBX_CUDA_TRY(f->q32.alloc(std::max<int64_t>(1, h->n_src)));
+  QBX_CUDA_TRY(f->ab32.alloc(std::max<int64_t>(1, h->n_src)));
   // leaves holding sources (P2M)
   QBX_CUDA_TRY(cudaDeviceSynchronize());
   // stats
@@ -1705,6 +1716,7 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   F.woff = f->W.off.ptr; F.widx = f->W.idx.ptr;
   F.xoff = f->X.off.ptr; F.xidx = f->X.idx.ptr;
   F.sxy = f->s_xy.ptr; F.snrm = f->s_nrm.ptr; F.qs = f->qs.ptr; F.ds = f->ds.ptr;
+  F.q32 = f->q32.ptr; F.ab32 = f->ab32.ptr;
   F.cxy = f->c_xy.ptr; F.crad = f->c_r.ptr; F.cid = f->perm[PT_CTR].ptr;
   F.txy = f->t_xy.ptr; F.tid = f->perm[PT_TGT].ptr; F.tassoc = f->t_assoc.ptr;
   F.lpb = f->lpb.ptr; F.eoff = f->eoff.ptr;
@@ -1728,7 +1740,9 @@ qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSe
   {
     const int TW = f->cleaf_pb_max + h->p + 1;
     int G = 32;
-    while (!h->batched && G > 1 && (C.n + G - 1) / G < 152 * 2) G /= 2;
+    if (h->l2qbxl_g > 0) G = h->l2qbxl_g;  // set by an autotuner
+    else
+      while (!h->batched && G > 1 && (C.n + G - 1) / G < 152 * 2) G /= 2;
     while (G > 1 && (size_t)G * TW * sizeof(cd) > kL2qbxlSmem) G /= 2;
     const size_t sm = (size_t)G * TW * sizeof(cd);
     l2qbxl_kernel<<<nblk(C.n, G), 32, sm, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, G, TW, alpha);
@@ -1830,7 +1844,8 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   const bool mixed = precision == QBX_MIXED;
   if (h->n_src > 0) {
     gather_strengths_kernel<<<nblk(h->n_src, 256), 256, 0, s>>>(
-        h->n_src, f->perm[PT_SRC].ptr, h->q_str.ptr, h->d_str.ptr, f->qs.ptr, f->ds.ptr);
+        h->n_src, f->perm[PT_SRC].ptr, h->q_str.ptr, h->d_str.ptr, f->s_nrm.ptr, h->k,
+        f->qs.ptr, f->ds.ptr, mixed ? f->q32.ptr : nullptr, mixed ? f->ab32.ptr : nullptr);
     QBX_KCHECK("gather_strengths", s);
     h->launches += 1;
   }
@@ -1942,10 +1957,12 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   // ---- main: downward pass (M2L after P2L has added into the locals)
   TRY(wait(s, f->ev_p2l));
   stage_begin(h, QBX_STAGE_M2L, s);
-  if (mixed) {
+  // tensor cores for the FP64 path; the mixed path keeps the FP32 CUDA-core
+  // tile GEMM (faster on every measured workload) unless engine 1 asks for them
+  if (f->tc_any && (!mixed || h->m2l_engine == 1)) {
+    TRY(launch_m2l_tc(h, f, mixed, s));
+  } else if (mixed) {
     TRY(launch_m2l_f32(h, f, s));
-  } else if (f->tc_any) {
-    TRY(launch_m2l_tc(h, f, s));
   } else {
     TRY(launch_m2l_f64(h, f, s));
   }

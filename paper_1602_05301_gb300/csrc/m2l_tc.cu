@@ -49,7 +49,11 @@ constexpr int kNC = 64;         // real outputs per CTA (MMA N)
 constexpr int kKC = 32;         // real inputs per staging chunk
 constexpr int kPad = 64;        // 2Q is padded to a multiple of this (K and N)
 constexpr int kThr = 128;
-constexpr long long kSpin = 1LL << 26;  // bound on every mbarrier wait
+// Every mbarrier wait is bounded twice: by a deadline on the global timer
+// (kWaitNs; each try_wait itself returns after a system-dependent suspension
+// limit) and by an iteration count.
+constexpr long long kSpin = 1LL << 26;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
 
@@ -80,8 +84,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar)));
 }
-// bounded wait for the given phase parity of an mbarrier; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait for the given phase parity of an mbarrier; false when the
+// deadline (limit_ns from the first call) or the iteration bound ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
+  const unsigned long long t0 = global_ns();
   for (long long it = 0; it < kSpin; ++it) {
     uint32_t done;
     asm volatile(
@@ -90,6 +102,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "=r"(done)
         : "r"(smem_u32(bar)), "r"(parity));
     if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -243,10 +256,38 @@ __global__ void __launch_bounds__(kThr) tc_mu_kernel(
   }
 }
 
-// The tile product. Item (first row, rows, first output, group). Y receives, for
-// each pair row and complex output lo, (Re hi, Re lo, Im hi, Im lo) as float4 at
-// yoff[row] + lo: the float-float value of (A x)_j 2^(e + f_j).
-template <int S>
+// 16-byte asynchronous copy global -> shared (zero fill when bytes == 0)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+// Stages of the shared-memory ring for SU slices in use: as many as fit in
+// 220 KB, at most 4.
+__host__ __device__ constexpr int tc_stages(int SU) {
+  return (220 * 1024) / (SU * (kRows + kNC) * kKC * 2) >= 4
+             ? 4
+             : (220 * 1024) / (SU * (kRows + kNC) * kKC * 2);
+}
+
+// The tile product. Item (first row, rows, first output, group). SD slices are
+// stored per operand (the level's split), the first SU of them are used: SU =
+// SD for the FP64 path, fewer for the mixed path (the leading digits are a
+// 24- to 28-bit approximation). Y receives, for each pair row and complex
+// output lo, (Re hi, Re lo, Im hi, Im lo) as float4 at yoff[row] + lo: the
+// float-float value of (A x)_j 2^(e + f_j).
+//
+// Pipeline: NS shared-memory stages filled by cp.async (every thread copies
+// 16-byte pieces; rows past the tile's end are zero-filled); chunk c is
+// consumed when its copy group has landed (cp.async.wait_group), after a proxy
+// fence and a barrier; one thread issues its MMAs and commits them to the
+// stage's mbarrier; then, with those MMAs queued behind the previous chunk's,
+// the threads wait for chunk c - 1's MMAs and refill that stage with chunk
+// c + NS - 1.
+template <int SD, int SU>
 __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
     const int4* __restrict__ items, const int4* __restrict__ lvl, const int* __restrict__ lpb,
     const long long* __restrict__ gaoff, const long long* __restrict__ gfoff,
@@ -254,17 +295,20 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
     const int* __restrict__ rowsrc, const long long* __restrict__ xoff,
     const int* __restrict__ xexp, const __nv_bfloat16* __restrict__ X,
     const long long* __restrict__ yoff, cd* __restrict__ Y, int* __restrict__ err) {
+  constexpr int NS = tc_stages(SU);
+  static_assert(NS >= 2, "at least two stages");
   constexpr int XT = kRows * kKC;             // elements of one X slice tile
   constexpr int AT = kNC * kKC;               // elements of one A slice tile
-  constexpr int STAGE = S * (XT + AT);        // elements of one stage
+  constexpr int STAGE = SU * (XT + AT);       // elements of one stage
   constexpr uint32_t LBO = 128;               // core matrices adjacent in K: contiguous
   constexpr uint32_t SBO = (kKC / 8) * 128;   // next 8-row group
   constexpr uint32_t ID = idesc_bf16(kRows, kNC);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem_raw);
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[NS + 1];  // a stage's MMAs; [NS]: all MMAs
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
+  __shared__ long long s_xrow[kRows];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 I = items[blockIdx.x];
   const int row0 = I.x, nr = I.y, n0 = I.z, g = I.w;
@@ -281,7 +325,7 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
   }
   if (tid == 0) {
     s_fail = 0;
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b <= NS; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -290,45 +334,46 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const int nchunks = Kp / kKC;
+  // slice offset of every row's source (-1 past the tile's end), read once
+  for (int m = tid; m < kRows; m += kThr) s_xrow[m] = m < nr ? xoff[rowsrc[row0 + m]] : -1;
+  __syncthreads();
+  // 16-byte pieces: a warp's 32 pieces fill four whole 128-byte core matrices
+  // (8 rows x 4 k-groups), so its shared-memory writes are free of conflicts
+  auto load_chunk = [&](int c) {
+    __nv_bfloat16* xs = stg + (size_t)(c % NS) * STAGE;
+    __nv_bfloat16* as = xs + SU * XT;
+    const int k0 = c * kKC;
+    for (int i = tid; i < kRows * SU * 4; i += kThr) {
+      const int r = i >> 5, t = r % SU, m = (r / SU) * 8 + (i & 7), q = (i >> 3) & 3;
+      const long long xo = s_xrow[m];
+      const __nv_bfloat16* src = xo >= 0 ? X + xo + (size_t)t * Kp + k0 + q * 8 : X;
+      cp_async16(reinterpret_cast<char*>(xs + t * XT) + (m >> 3) * SBO + q * LBO + (m & 7) * 16,
+                 src, xo >= 0 ? 16 : 0);
+    }
+    for (int i = tid; i < kNC * SU * 4; i += kThr) {
+      const int r = i >> 5, t = r % SU, j = (r / SU) * 8 + (i & 7), q = (i >> 3) & 3;
+      cp_async16(reinterpret_cast<char*>(as + t * AT) + (j >> 3) * SBO + q * LBO + (j & 7) * 16,
+                 Ag + ((size_t)t * Kp + (n0 + j)) * Kp + k0 + q * 8, 16);
+    }
+  };
+  for (int c = 0; c < NS - 1; ++c) {  // prologue: NS - 1 groups (empty past the end)
+    if (c < nchunks) load_chunk(c);
+    cp_async_commit();
+  }
   uint32_t acc_started = 0;  // accumulators written at least once (issuing thread)
   bool ok = true;
-  for (int c = 0; c < nchunks && ok; ++c) {
-    const int b = c & 1;
-    if (c >= 2) {  // the MMAs that read this buffer (chunk c - 2) are complete
-      if (!mbar_wait(&mbar[b], ((c - 2) >> 1) & 1)) atomicExch(&s_fail, 1);
-      __syncthreads();
-      if (s_fail) { ok = false; break; }
-    }
-    __nv_bfloat16* xs = stg + (size_t)b * STAGE;
-    __nv_bfloat16* as = xs + S * XT;
-    const int k0 = c * kKC;
-    // X: rows m of the tile, slice t, 16-byte piece q (8 inputs): element
-    // (m, k) of slice t goes to core (m/8, k/8), row m%8
-    for (int i = tid; i < kRows * S * 4; i += kThr) {
-      const int q = i & 3, t = (i >> 2) % S, m = (i >> 2) / S;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (m < nr) {
-        const int rs = rowsrc[row0 + m];
-        v = *reinterpret_cast<const uint4*>(X + xoff[rs] + (size_t)t * Kp + k0 + q * 8);
-      }
-      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(xs + t * XT) + (m >> 3) * SBO + q * LBO +
-                                (m & 7) * 16) = v;
-    }
-    for (int i = tid; i < kNC * S * 4; i += kThr) {
-      const int q = i & 3, t = (i >> 2) % S, j = (i >> 2) / S;
-      const uint4 v = *reinterpret_cast<const uint4*>(
-          Ag + ((size_t)t * Kp + (n0 + j)) * Kp + k0 + q * 8);
-      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(as + t * AT) + (j >> 3) * SBO + q * LBO +
-                                (j & 7) * 16) = v;
-    }
+  for (int c = 0; c < nchunks; ++c) {
+    cp_async_wait<NS - 2>();  // chunk c's group has landed (this thread's copies)
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
+      const __nv_bfloat16* xs = stg + (size_t)(c % NS) * STAGE;
+      const __nv_bfloat16* as = xs + SU * XT;
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int ti = 0; ti < S; ++ti) {
+      for (int ti = 0; ti < SU; ++ti) {
 #pragma unroll
-        for (int tj = 0; tj < S - ti; ++tj) {
+        for (int tj = 0; tj < SU - ti; ++tj) {
           const int a = ti + tj;  // weight 2^(-beta (a + 2))
 #pragma unroll
           for (int kk = 0; kk < kKC; kk += 16) {
@@ -339,18 +384,35 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
           }
         }
       }
-      mma_commit(&mbar[b]);
+      mma_commit(&mbar[c % NS]);
     }
+    // refill the stage of chunk c - 1 once its MMAs are done
+    const int cn = c + NS - 1;
+    if (cn < nchunks) {
+      if (c >= 1 && !mbar_wait(&mbar[(c - 1) % NS], ((c - 1) / NS) & 1)) atomicExch(&s_fail, 1);
+      __syncthreads();
+      if (s_fail) { ok = false; break; }
+      load_chunk(cn);
+    }
+    cp_async_commit();
   }
-  // all MMAs complete: the last commit of each buffer
+  cp_async_wait<0>();
+  // all MMAs complete: the last chunk's commit covers every earlier one; wait
+  // for the earlier stages' last commits too so that no arrival is pending
   if (ok) {
-    for (int c = std::max(0, nchunks - 2); c < nchunks; ++c)
-      if (!mbar_wait(&mbar[c & 1], (c >> 1) & 1)) atomicExch(&s_fail, 1);
+    for (int c = std::max(0, nchunks - NS); c < nchunks; ++c)
+      if (!mbar_wait(&mbar[c % NS], (c / NS) & 1)) atomicExch(&s_fail, 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   __syncthreads();
   if (s_fail) {
-    if (tid == 0) atomicExch(err, 1);
+    // a wait ran out: flag it, then give the MMAs issued so far a bounded
+    // wait (one commit tracks them all) before the tensor memory is freed
+    if (tid == 0) {
+      atomicExch(err, 1);
+      mma_commit(&mbar[NS]);
+    }
+    mbar_wait(&mbar[NS], 0);
   } else {
     // epilogue: warp w holds rows 32w .. 32w + 31 (TMEM lanes)
     const int m = warp * 32 + lane;
@@ -362,7 +424,7 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
 #pragma unroll
       for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.f;
 #pragma unroll
-      for (int a = S - 1; a >= 0; --a) {  // smallest weight first
+      for (int a = SU - 1; a >= 0; --a) {  // smallest weight first
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + a * kNC + j0, v);
         const int sh = -beta * (a + 2);
@@ -421,10 +483,14 @@ __global__ void __launch_bounds__(kThr) m2l_tc_reduce_kernel(
   }
 }
 
-template <int S>
+template <int SU>
 size_t tc_smem_bytes() {
-  return (size_t)2 * S * (kRows * kKC + kNC * kKC) * sizeof(__nv_bfloat16);
+  return (size_t)tc_stages(SU) * SU * (kRows * kKC + kNC * kKC) * sizeof(__nv_bfloat16);
 }
+
+// slices used by the mixed path for a level split into SD slices of beta bits:
+// at least 24 bits (SU beta >= 24)
+__host__ __device__ constexpr int mixed_slices(int SD) { return SD == 6 ? 3 : 4; }
 
 // (beta, S) for a padded width Kp: the most bits per digit for which
 // S Kp 2^(2 beta - 2) <= 2^24 (exact FP32 sums) with beta S >= 48; 0 if none.
@@ -438,11 +504,13 @@ int2 tc_params(int Kp) {
 }  // namespace
 
 qbx_status configure_tc_kernels(int smem_optin) {
-  const void* k[] = {(const void*)m2l_tc_kernel<6>, (const void*)m2l_tc_kernel<7>,
-                     (const void*)m2l_tc_kernel<8>};
-  const size_t need[] = {tc_smem_bytes<6>(), tc_smem_bytes<7>(), tc_smem_bytes<8>()};
-  for (int i = 0; i < 3; ++i) {
-    if (need[i] + 1024 > (size_t)smem_optin) {
+  const void* k[] = {(const void*)m2l_tc_kernel<6, 6>, (const void*)m2l_tc_kernel<7, 7>,
+                     (const void*)m2l_tc_kernel<8, 8>, (const void*)m2l_tc_kernel<6, 3>,
+                     (const void*)m2l_tc_kernel<7, 4>, (const void*)m2l_tc_kernel<8, 4>};
+  const size_t need[] = {tc_smem_bytes<6>(), tc_smem_bytes<7>(), tc_smem_bytes<8>(),
+                         tc_smem_bytes<3>(), tc_smem_bytes<4>(), tc_smem_bytes<4>()};
+  for (int i = 0; i < 6; ++i) {
+    if (need[i] + 2048 > (size_t)smem_optin) {
       set_error("tensor-core M2L needs %zu bytes of shared memory (device: %d)", need[i],
                 smem_optin);
       return QBX_ERR_ARG;
@@ -458,7 +526,6 @@ qbx_status configure_tc_kernels(int smem_optin) {
 // V-list source there, and the work items. Levels whose 2Q is too wide for
 // exact FP32 sums keep the FP64 CUDA-core GEMM (its items are filtered here).
 qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
-  (void)h;
   const int nl = f->n_levels, ng = nl * 49;
   std::vector<int4> lv(nl, make_int4(0, 0, 0, 0));
   for (int l = 2; l < nl; ++l) {
@@ -472,7 +539,7 @@ qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
   // CUDA-core GEMM (for comparisons); the default is the tensor-core path
   {
     const char* env = getenv("QBX_M2L_TENSOR");
-    if (env && env[0] == '0')
+    if ((env && env[0] == '0') || h->m2l_engine == 2)
       for (auto& v : lv) v = make_int4(0, 0, 0, 0);
   }
   f->h_tc_lvl = lv;
@@ -581,7 +648,7 @@ qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
   return QBX_OK;
 }
 
-qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
+qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, bool mixed, cudaStream_t s) {
   if (f->n_vbox == 0) return QBX_OK;
   if (f->n_tc_src > 0) {
     tc_mu_kernel<<<f->n_tc_src, kThr, 0, s>>>(f->tc_src.ptr, f->box.level.ptr, f->lpb.ptr,
@@ -592,19 +659,25 @@ qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;
   }
-#define TC_LAUNCH(SS)                                                                           \
-  if (f->n_tc_items[SS - 6] > 0) {                                                              \
-    m2l_tc_kernel<SS><<<f->n_tc_items[SS - 6], kThr, tc_smem_bytes<SS>(), s>>>(                 \
-        f->tc_items[SS - 6].ptr, f->tc_lvl.ptr, f->lpb.ptr, f->tc_gaoff.ptr, f->tc_gfoff.ptr,   \
+#define TC_LAUNCH(SD, SU)                                                                      \
+  if (f->n_tc_items[SD - 6] > 0) {                                                              \
+    m2l_tc_kernel<SD, SU><<<f->n_tc_items[SD - 6], kThr, tc_smem_bytes<SU>(), s>>>(             \
+        f->tc_items[SD - 6].ptr, f->tc_lvl.ptr, f->lpb.ptr, f->tc_gaoff.ptr, f->tc_gfoff.ptr,   \
         reinterpret_cast<const __nv_bfloat16*>(f->tc_A.ptr), f->tc_fexp.ptr, f->tc_rowsrc.ptr,   \
         f->tc_xoff.ptr, f->tc_xexp.ptr, reinterpret_cast<const __nv_bfloat16*>(f->tc_X.ptr),     \
         f->m2l_yoff.ptr, f->m2l_y64.ptr, f->err.ptr + 1);                                      \
     QBX_CUDA_TRY(cudaGetLastError());                                                           \
     h->launches += 1;                                                                           \
   }
-  TC_LAUNCH(6)
-  TC_LAUNCH(7)
-  TC_LAUNCH(8)
+  if (mixed) {
+    TC_LAUNCH(6, 3)
+    TC_LAUNCH(7, 4)
+    TC_LAUNCH(8, 4)
+  } else {
+    TC_LAUNCH(6, 6)
+    TC_LAUNCH(7, 7)
+    TC_LAUNCH(8, 8)
+  }
 #undef TC_LAUNCH
   {
     const qbx_status st = launch_m2l_f64_gemm_rest(h, f, s);
@@ -616,5 +689,52 @@ qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
                                                   f->eoff.ptr, f->local.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   h->launches += 1;
+  return QBX_OK;
+}
+
+namespace {
+// One warp waits on an mbarrier that nothing arrives at, with the bounded
+// wait of the tensor-core kernels (deadline limit_ns), and sets the flag
+// those kernels set when a wait runs out.
+__global__ void wait_selftest_kernel(int* __restrict__ err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncwarp();
+  const bool done = mbar_wait(&bar, 0, limit_ns);
+  if (!done && threadIdx.x == 0) atomicExch(err, 1);
+}
+}  // namespace
+
+// The flag the tensor-core M2L kernels set when one of their bounded waits
+// ran out (the result of that evaluation is then wrong): read after the
+// device work, then cleared.
+qbx_status read_wait_flag(qbx_handle* h) {
+  if (!h->fmm) return QBX_OK;
+  int flag = 0;
+  QBX_CUDA_TRY(cudaMemcpy(&flag, h->fmm->err.ptr + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!flag) return QBX_OK;
+  QBX_CUDA_TRY(cudaMemset(h->fmm->err.ptr + 1, 0, sizeof(int)));
+  set_error("a bounded device-side wait gave up (tensor-core M2L); the results of the "
+            "evaluations since the last check are invalid");
+  return QBX_ERR_TIMEOUT;
+}
+
+extern "C" qbx_status qbx_selftest_wait_timeout(qbx_handle* h, int32_t limit_us) {
+  set_error("%s", "");
+  if (!h || limit_us < 1 || limit_us > 1000000) {
+    set_error("qbx_selftest_wait_timeout: NULL handle or limit_us outside 1..1e6");
+    return QBX_ERR_ARG;
+  }
+  if (!h->planned || !h->fmm) {
+    set_error("qbx_selftest_wait_timeout: needs a handle with an FMM plan");
+    return QBX_ERR_STATE;
+  }
+  QBX_CUDA_TRY(cudaDeviceSynchronize());
+  wait_selftest_kernel<<<1, 32>>>(h->fmm->err.ptr + 1, 1000ull * (unsigned long long)limit_us);
+  QBX_CUDA_TRY(cudaGetLastError());
+  QBX_CUDA_TRY(cudaDeviceSynchronize());
   return QBX_OK;
 }

@@ -95,6 +95,12 @@ struct qbx_handle {
   // so an evaluation favours throughput (one stream, 32 centres per L2QBXL
   // warp, wide tiles) over the latency of a single problem.
   bool batched = false;
+  // plan choices an autotuner may set (0: automatic): the M2L engine of the
+  // next plan (0: FP64 on tensor cores where exact, mixed on the FP32 CUDA-core
+  // GEMM; 1: tensor cores for both; 2: CUDA cores for both) and the centres
+  // per warp of L2QBXL
+  int m2l_engine = 0;
+  int l2qbxl_g = 0;
   DevBuf<double> tgt_xy;
   DevBuf<int32_t> assoc;                    // [n_tgt] centre or -1
   DevBuf<int32_t> qbx_tgt_list, direct_tgt_list;
@@ -137,6 +143,8 @@ void gl_nodes(int n, std::vector<double>& x, std::vector<double>& w);
 qbx_status upsample_geometry(qbx_handle* h);
 // conditions.cu
 qbx_status density_weights(qbx_handle* h);
+// api.cu: QBX_ERR_TIMEOUT (and clears the flag) if a bounded device wait gave up
+qbx_status read_wait_flag(qbx_handle* h);
 // api.cu: replace a handle's density geometry (after refinement); drops any plan
 qbx_status replace_geometry(qbx_handle* h, int64_t n_panels, DevBuf<double>& node_xy,
                             DevBuf<double>& node_nrm, DevBuf<double>& node_w,

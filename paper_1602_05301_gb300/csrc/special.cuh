@@ -1,6 +1,8 @@
 // Device special functions for the 2D Helmholtz kernels.
 //
-//  * H_0, H_1 of the first kind: the CUDA math library's j0/y0/j1/y1 (FP64).
+//  * H_0, H_1 of the first kind: the ascending series below a series reach
+//    (x < 5, or x < 8 for the mixed path), the CUDA math library's
+//    j0/y0/j1/y1 (FP64) above it.
 //  * H_m, m >= 2: upward three-term recurrence H_{m+1} = (2m/x) H_m - H_{m-1}
 //    (DLMF 10.6.1), stable for the dominant Y part; the error of the J part
 //    stays at rounding level relative to |H_m|.
@@ -45,21 +47,25 @@ struct SeriesHorner<-1> {
   __device__ __forceinline__ static void run(double, double&, double&, double&, double&) {}
 };
 
-// H_0 and H_1 for 0 < x < 2 from the ascending series (DLMF 10.2.2 for J,
-// DLMF 10.8.1 for Y), in u = -x^2/4:
+// H_0 and H_1 from the ascending series (DLMF 10.2.2 for J, DLMF 10.8.1 for
+// Y), in u = -x^2/4:
 //   J0 = sum u^k / (k!)^2,            J1 = (x/2) sum u^k / (k! (k+1)!),
 //   Y0 = (2/pi)(ln(x/2) + gamma) J0 - (2/pi) sum_{k>=1} H_k u^k / (k!)^2,
 //   Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (x/(2 pi)) sum (psi(k+1) + psi(k+2)) u^k / (k! (k+1)!),
-// For |u| < 1 the terms fall below 1e-17 by k = 13; each sum is a polynomial
-// in u of degree 14 evaluated by Horner's rule (one FMA per term).
+// each sum a polynomial in u of degree KTOP evaluated by Horner's rule (one
+// FMA per term). The truncation error falls below rounding for x < 2 at
+// KTOP = 14, x < 5 at 18 and x < 8 at 20; beyond x = 2 the sums cancel (their
+// terms add up to about I_0(x)), which bounds the error relative to |H_0|,
+// |H_1| by 1e-14 for x < 5 and 3e-13 for x < 8 (checked against the library's
+// j0/y0/j1/y1 by tests/test_special_gpu.py).
 // ix = 1/x is passed in (callers get it from one reciprocal square root of r^2).
-__device__ __forceinline__ void hankel01_series(double x, double ix, cd& h0, cd& h1) {
-  constexpr int kTop = 14;
+template <int KTOP>
+__device__ __forceinline__ void hankel01_series_n(double x, double ix, cd& h0, cd& h1) {
   constexpr double kTwoOverPi = 0.63661977236758134308;
   const double u = -0.25 * x * x;
-  double pj0 = SeriesCoef<kTop>::j0, pj1 = SeriesCoef<kTop>::j1;
-  double py0 = SeriesCoef<kTop>::y0, py1 = SeriesCoef<kTop>::y1;
-  SeriesHorner<kTop - 1>::run(u, pj0, pj1, py0, py1);
+  double pj0 = SeriesCoef<KTOP>::j0, pj1 = SeriesCoef<KTOP>::j1;
+  double py0 = SeriesCoef<KTOP>::y0, py1 = SeriesCoef<KTOP>::y1;
+  SeriesHorner<KTOP - 1>::run(u, pj0, pj1, py0, py1);
   const double lx = log(0.5 * x);
   const double J0 = pj0, J1 = 0.5 * x * pj1;
   const double Y0 = kTwoOverPi * ((lx + kEulerGamma) * J0 - py0);
@@ -68,26 +74,49 @@ __device__ __forceinline__ void hankel01_series(double x, double ix, cd& h0, cd&
   h1 = mk(J1, Y1);
 }
 
+__device__ __forceinline__ void hankel01_series(double x, double ix, cd& h0, cd& h1) {
+  hankel01_series_n<14>(x, ix, h0, h1);
+}
 __device__ __forceinline__ void hankel01_series(double x, cd& h0, cd& h1) {
-  hankel01_series(x, 1.0 / x, h0, h1);
+  hankel01_series_n<14>(x, 1.0 / x, h0, h1);
+}
+
+// Series reach of hankel01 (FP64 accuracy) and of hankel01_wide (relative
+// error below 3e-13, for the mixed-precision path whose Hankel values are
+// rounded to FP32 after the FP64 recurrence).
+constexpr double kSeriesMax = 5.0, kSeriesMaxWide = 8.0;
+
+// H_0, H_1 at x > 0. The lanes of a warp usually see arguments of one range:
+// when all of them are below 2 the short series serves all, otherwise the
+// longer one serves every lane below the series reach (one path, not two),
+// and the library's j0/y0/j1/y1 the rest.
+// NEED0 / NEED1: whether the caller reads h0 / h1 (the library calls of the
+// other are skipped; the series parts it does not read are dead code).
+template <bool WIDE, bool NEED0 = true, bool NEED1 = true>
+__device__ __forceinline__ void hankel01_any(double x, double ix, cd& h0, cd& h1) {
+  if (__all_sync(__activemask(), x < 2.0)) {
+    hankel01_series_n<14>(x, ix, h0, h1);
+    return;
+  }
+  if (x < (WIDE ? kSeriesMaxWide : kSeriesMax)) {
+    if (WIDE)
+      hankel01_series_n<20>(x, ix, h0, h1);
+    else
+      hankel01_series_n<18>(x, ix, h0, h1);
+    return;
+  }
+  if (NEED0) h0 = mk(j0(x), y0(x));
+  if (NEED1) h1 = mk(j1(x), y1(x));
 }
 
 __device__ __forceinline__ void hankel01(double x, double ix, cd& h0, cd& h1) {
-  if (x < 2.0) {
-    hankel01_series(x, ix, h0, h1);
-    return;
-  }
-  h0 = mk(j0(x), y0(x));
-  h1 = mk(j1(x), y1(x));
+  hankel01_any<false>(x, ix, h0, h1);
 }
-
 __device__ __forceinline__ void hankel01(double x, cd& h0, cd& h1) {
-  if (x < 2.0) {
-    hankel01_series(x, h0, h1);
-    return;
-  }
-  h0 = mk(j0(x), y0(x));
-  h1 = mk(j1(x), y1(x));
+  hankel01_any<false>(x, 1.0 / x, h0, h1);
+}
+__device__ __forceinline__ void hankel01_wide(double x, double ix, cd& h0, cd& h1) {
+  hankel01_any<true>(x, ix, h0, h1);
 }
 
 // Start index of the backward recurrence for orders 0..pmax at argument x:

@@ -120,6 +120,8 @@ struct FmmPlan {
   // expansions
   DevBuf<cd> mpole, local;              // [n_coef], box b at eoff[b]
   DevBuf<cd> qs, ds;                    // sorted strengths
+  DevBuf<float2> q32;                   // their FP32 charges and dipole factors (mixed path)
+  DevBuf<float4> ab32;
   DevBuf<int> err;                      // device error flags
   // mixed precision (sigma-normalised FP32 M2L)
   DevBuf<double> lsig, conv;            // [n_levels][pb_max+1] log sig_j, s^j / sig_j
@@ -176,7 +178,7 @@ qbx_status launch_m2l_f64_gemm_rest(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 // m2l_tc.cu
 qbx_status configure_tc_kernels(int smem_optin);
 qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f);
-qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, cudaStream_t s);
+qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, bool mixed, cudaStream_t s);
 // shared memory of one M2M / L2L tile-GEMM block at box order pb
 size_t gemm_smem_bytes(int pb);
 

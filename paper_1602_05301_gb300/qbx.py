@@ -45,7 +45,7 @@ class qbx_tree_desc(ctypes.Structure):
     _fields_ = [("n_targets", ctypes.c_int64), ("target_xy", _vp), ("on_surface_node", _vp),
                 ("on_surface_side", _vp), ("mode", ctypes.c_int32), ("p_fmm", ctypes.c_int32),
                 ("p_add", ctypes.c_int32), ("n_max", ctypes.c_int32),
-                ("eps_assoc", ctypes.c_double), ("assoc_out", _vp)]
+                ("eps_assoc", ctypes.c_double), ("assoc_out", _vp), ("m2l_engine", ctypes.c_int32)]
 
 
 class QBXError(RuntimeError):
@@ -117,10 +117,20 @@ def library() -> ctypes.CDLL:
             lib.qbx_refine.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
             lib.qbx_get_geometry.restype = ctypes.c_int
             lib.qbx_get_geometry.argtypes = [_vp] + [_vp] * 8
+            lib.qbx_autotune_tol.restype = ctypes.c_int
+            lib.qbx_autotune_tol.argtypes = [_vp, ctypes.POINTER(qbx_tree_desc), ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                             ctypes.c_int32, _vp, _vp]
             lib.qbx_solve_dirichlet.restype = ctypes.c_int
             lib.qbx_solve_dirichlet.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                 ctypes.c_int32, _vp, _vp, _vp]
+            lib.qbx_sync.restype = ctypes.c_int
+            lib.qbx_sync.argtypes = [_vp]
+            lib.qbx_selftest_wait_timeout.restype = ctypes.c_int
+            lib.qbx_selftest_wait_timeout.argtypes = [_vp, ctypes.c_int32]
+            lib.qbx_hankel01.restype = ctypes.c_int
+            lib.qbx_hankel01.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, _vp]
             _lib = lib
     return _lib
 
@@ -210,6 +220,14 @@ def qbx_export_tree(handle, n_src, n_ctr, n_tgt):
     return out
 
 
+def qbx_hankel01(x, variant=0) -> np.ndarray:
+    """(H_0(x), H_1(x)) as complex [n][2], evaluated by the library's device code."""
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((xx.size, 4))
+    _check(library().qbx_hankel01(ptr(xx), int(xx.size), int(variant), ptr(out)))
+    return out[:, 0::2] + 1j * out[:, 1::2]
+
+
 def qbx_default_p_add(p: int) -> int:
     """p_add chosen for QBX order p when a plan is built with p_add < 0."""
     return int(library().qbx_default_p_add(int(p)))
@@ -292,7 +310,7 @@ class LayerPotential:
         self.n_targets = 0
 
     def build(self, target_xy, on_surface_node=None, on_surface_side=None, mode=QBX_DIRECT,
-              p_fmm=0, p_add=-1, n_max=0, eps_assoc=0.1):
+              p_fmm=0, p_add=-1, n_max=0, eps_assoc=0.1, m2l_engine=0):
         txy = _host_f64(target_xy)
         n = txy.shape[0]
         osn = None if on_surface_node is None else np.ascontiguousarray(on_surface_node,
@@ -301,7 +319,7 @@ class LayerPotential:
                                                                         np.int8)
         assoc = np.empty(n, dtype=np.int32)
         d = qbx_tree_desc(n, ptr(txy), ptr(osn), ptr(oss), int(mode), int(p_fmm), int(p_add),
-                          int(n_max), float(eps_assoc), ptr(assoc))
+                          int(n_max), float(eps_assoc), ptr(assoc), int(m2l_engine))
         qbx_tree_build(self.handle, d)
         self.n_targets = n
         return assoc
@@ -423,6 +441,37 @@ class LayerPotential:
                                       ptr(chosen)))
         self.n_targets = n
         return assoc, times, int(chosen[0])
+
+    def autotune_tol(self, target_xy, on_surface_node=None, on_surface_side=None, p_fmm=20,
+                     tol=1e-6, eps_assoc=0.1, precision=QBX_MIXED, has_S=True, has_D=True,
+                     reps=2):
+        """qbx_autotune_tol: the fastest plan within tol of the most accurate one.
+        Returns (assoc, plan dict, report dict)."""
+        txy = _host_f64(target_xy)
+        n = txy.shape[0]
+        osn = None if on_surface_node is None else np.ascontiguousarray(on_surface_node,
+                                                                        np.int64)
+        oss = None if on_surface_side is None else np.ascontiguousarray(on_surface_side,
+                                                                        np.int8)
+        assoc = np.empty(n, dtype=np.int32)
+        d = qbx_tree_desc(n, ptr(txy), ptr(osn), ptr(oss), QBX_FMM, int(p_fmm), -1, 0,
+                          float(eps_assoc), ptr(assoc))
+        plan = np.zeros(5, np.int32)
+        rep = np.zeros(3)
+        _check(library().qbx_autotune_tol(self.handle, ctypes.byref(d), int(precision),
+                                          int(bool(has_S)), int(bool(has_D)), float(tol),
+                                          int(reps), ptr(plan), ptr(rep)))
+        self.n_targets = n
+        return assoc, dict(zip(("mode", "n_max", "p_fmm", "engine", "g"), map(int, plan))), \
+            dict(ms=float(rep[0]), err=float(rep[1]), tried=int(rep[2]))
+
+    def sync(self):
+        """Waits for the device work; raises QBXError(QBX_ERR_TIMEOUT) if a
+        bounded device wait gave up since the last check (qbx_sync)."""
+        _check(library().qbx_sync(self.handle))
+
+    def selftest_wait_timeout(self, limit_us=2000):
+        _check(library().qbx_selftest_wait_timeout(self.handle, int(limit_us)))
 
     def set_timing(self, on=True):
         qbx_set_timing(self.handle, on)

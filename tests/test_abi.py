@@ -54,6 +54,15 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.qbx_layer_potential_eval(None, 0, 0, None, 0, 0, None, None, None, 0,
                                         None) == qbx.QBX_ERR_ARG
     lib.qbx_destroy(None)  # NULL-safe
+    x = (ctypes.c_double * 2)(1.0, 0.0)
+    out = (ctypes.c_double * 8)()
+    assert lib.qbx_hankel01(x, -1, 0, out) == qbx.QBX_ERR_ARG
+    assert lib.qbx_hankel01(x, 1, 2, out) == qbx.QBX_ERR_ARG      # unknown variant
+    assert lib.qbx_hankel01(x, 2, 0, out) == qbx.QBX_ERR_ARG      # x = 0
+    assert b"x[1]" in lib.qbx_last_error()
+    assert lib.qbx_hankel01(None, 1, 0, out) == qbx.QBX_ERR_ARG
+    assert lib.qbx_sync(None) == qbx.QBX_ERR_ARG
+    assert lib.qbx_selftest_wait_timeout(None, 10) == qbx.QBX_ERR_ARG
 
 
 def test_binding_names_match_abi():

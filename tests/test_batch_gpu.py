@@ -96,3 +96,39 @@ def test_batch_mixed_precision_and_oracle(qbxmod, batch_setup, oracle):
                                           batch_setup["sD"][c], 1.0, 1.0, sides=1,
                                           centre_of_target=t.astype(np.int32))
         assert rel_l2(u64[toff[c] + t], u_ref) < 1e-10
+
+
+def test_tolerance_autotuner_meets_its_tolerance(qbxmod, oracle):
+    """qbx_autotune_tol picks the fastest plan within tol of the most accurate
+    one; the chosen plan's result stays within the tolerance of the oracle, and
+    a second curve of the same size and k h reuses the cached decision."""
+    w = make_config(4, n_curves=6)
+    g = w["geom"]
+    noff = g.node_offset()
+    big = int(np.argmax(np.diff(noff)))
+    for tol, prec in ((1e-6, qbxmod.QBX_MIXED), (1e-10, qbxmod.QBX_FP64)):
+        G = g.as_dict(big)
+        n = G["node_xy"].shape[0]
+        lp = qbxmod.LayerPotential(G, w["p"], sides=1)
+        assoc, plan, rep = lp.autotune_tol(G["node_xy"], np.arange(n), np.ones(n, np.int8),
+                                           p_fmm=w["p_fmm"], tol=tol, precision=prec)
+        print("tol %g: plan %s, report %s" % (tol, plan, rep))
+        assert plan["mode"] in (0, 1) and rep["tried"] >= 1 and rep["err"] <= tol
+        if plan["mode"] == 1:
+            assert 4 <= plan["p_fmm"] <= w["p_fmm"] and plan["n_max"] in (16, 32, 64, 128)
+        sS = w["sigma_S"][noff[big]:noff[big + 1]]
+        sD = w["sigma_D"][noff[big]:noff[big + 1]]
+        u = lp.eval(sigma_S=sS, sigma_D=sD, cS=1.0, cD=1.0, precision=prec)
+        t = np.arange(0, n, max(1, n // 48))
+        u_ref, _ = oracle.layer_potential(G, G["node_xy"][t], w["p"], sS, sD, 1.0, 1.0, sides=1,
+                                          centre_of_target=t.astype(np.int32))
+        err = rel_l2(u[t], u_ref)
+        print("   vs oracle %.2e" % err)
+        assert err < 20 * tol
+        # the same curve again: the decision comes from the cache
+        lp2 = qbxmod.LayerPotential(G, w["p"], sides=1)
+        _, plan2, rep2 = lp2.autotune_tol(G["node_xy"], np.arange(n), np.ones(n, np.int8),
+                                          p_fmm=w["p_fmm"], tol=tol, precision=prec)
+        assert plan2 == plan and rep2["tried"] == 0
+        lp.close()
+        lp2.close()

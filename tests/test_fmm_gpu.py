@@ -236,3 +236,37 @@ def test_schedules_give_identical_fp64_results(qbxmod):
     u_after = lp.eval(**args)                     # back to the single-problem schedule
     assert np.array_equal(u_fork, u_after)
     lp.close()
+
+
+@pytest.mark.parametrize("engine", [0, 1, 2])
+def test_m2l_engines_against_oracle(qbxmod, oracle, engine):
+    """Every M2L engine (0: FP64 on tensor cores, mixed on the FP32 CUDA-core
+    GEMM; 1: tensor cores in both precisions; 2: CUDA cores in both) meets the
+    precision's tolerance against the oracle on a sample of the starfish
+    workload, element-wise as well as in l2."""
+    w = make_config(2)
+    g = w["geom"]
+    lp = qbxmod.LayerPotential(g.as_dict(), w["p"], sides=2)
+    assoc = lp.build(w["tgt_xy"], mode=qbxmod.QBX_FMM, p_fmm=w["p_fmm"], m2l_engine=engine)
+    args = dict(sigma_S=w["sigma_S"], sigma_D=w["sigma_D"], cS=w["cS"], cD=w["cD"])
+    u64 = lp.eval(precision=qbxmod.QBX_FP64, **args)
+    u32 = lp.eval(precision=qbxmod.QBX_MIXED, **args)
+    lp.close()
+    rng = np.random.default_rng(10)
+    sample = np.concatenate([rng.choice(np.nonzero(assoc >= 0)[0], 48, replace=False),
+                             rng.choice(np.nonzero(assoc < 0)[0], 96, replace=False)])
+    u_ref, _ = oracle.layer_potential(g.as_dict(), w["tgt_xy"][sample], w["p"], w["sigma_S"],
+                                      w["sigma_D"], w["cS"], w["cD"], sides=2,
+                                      centre_of_target=assoc[sample])
+    for u, tol in ((u64, TOL64), (u32, 1e-6)):
+        d = u[sample] - u_ref
+        e2 = rel_l2(u[sample], u_ref)
+        em = float(np.max(np.abs(d)) / np.max(np.abs(u_ref)))
+        print("engine %d: rel l2 %.3e, max-norm %.3e" % (engine, e2, em))
+        assert e2 < tol and em < tol
+    with pytest.raises(qbxmod.QBXError):
+        lp2 = qbxmod.LayerPotential(g.as_dict(), w["p"], sides=2)
+        try:
+            lp2.build(w["tgt_xy"], mode=qbxmod.QBX_FMM, p_fmm=w["p_fmm"], m2l_engine=3)
+        finally:
+            lp2.close()
