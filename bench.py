@@ -57,6 +57,52 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP32 FMA peak: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.070 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 PROFILES = os.path.join(ROOT, "profiles")
+# bf16 dense tensor rate measured on the GB300s (burst; the M2L stage is
+# timed on its own), the denominator of the tensor-core M2L
+BF16_FALLBACK_TFLOPS = 1900.0
+
+
+def bf16_peak():
+    """(TFLOP/s, basis) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured (MEASURED_PEAKS.json, burst)"
+    except (OSError, KeyError, ValueError):
+        return BF16_FALLBACK_TFLOPS, "fallback"
+
+
+def tc_slices(pb):
+    """bf16 slices of the FP64 tensor-core M2L at box order pb (0: CUDA cores)."""
+    kp = (2 * (2 * pb + 1) + 63) // 64 * 64
+    return 6 if kp <= 128 else 7 if kp <= 576 else 8 if kp <= 2048 else 0
+
+
+def m2l_tensor_roofline(lp, m2l_ms):
+    """Roofline of the FP64 M2L stage on the tensor cores: per level, the
+    algorithmic 8 Q^2 flops of each V entry need S (S + 1) / 2 bf16 slice
+    products (S slices per operand), so its time at peak is flops x products /
+    bf16 peak; levels too wide for the split run at the FP64 FMA peak."""
+    t = lp.export_tree()
+    pbl = lp.box_orders().astype(np.int64)
+    lev = t["level"].astype(np.int64)
+    nv = np.diff(t["off"][1]).astype(np.int64)
+    peak, basis = bf16_peak()
+    t_roof, alg, rows = 0.0, 0.0, []
+    for l in range(len(pbl)):
+        n = int(nv[lev == l].sum())
+        if n == 0:
+            continue
+        Q = 2 * int(pbl[l]) + 1
+        fl = 8.0 * Q * Q * n
+        S = tc_slices(int(pbl[l]))
+        prod = S * (S + 1) // 2
+        t_roof += fl * prod / (peak * 1e12) if S else fl / (FP64_PEAK_TFLOPS * 1e12)
+        alg += fl
+        rows.append({"level": l, "Q": Q, "v_entries": n, "slices": S, "products": prod})
+    return {"bound": "tensor", "kernel": "m2l (fp64 leg)", "ms_per_launch": m2l_ms,
+            "algorithmic_fp64_tflops": alg / (m2l_ms * 1e-3) / 1e12,
+            "peak": peak, "peak_basis": basis + "; divided per level by the slice products",
+            "roofline_ms": 1e3 * t_roof, "frac": 1e3 * t_roof / m2l_ms, "levels": rows}
 
 
 def known_traffic(stage, workload, precision):
@@ -313,10 +359,21 @@ def run_ours(args, w, ws, rank, local):
     ms2, _ = timed_steps(stepper(lp, other, out2), args.steps, args.warmup, stream, flush, ws,
                          dev, lp)
     u_other = out2.cpu().numpy()
+    # per-stage times of the other precision too (the FP64 leg's tensor-core M2L)
+    lp.set_timing(True)
+    per_other = {}
+    for _ in range(3):
+        flush.zero_()
+        stepper(lp, other, out2)()
+        for kname, ms in lp.stage_times().items():
+            per_other.setdefault(kname, []).append(ms)
+    lp.set_timing(False)
+    per_other = {k: statistics.median(v) for k, v in per_other.items() if max(v) > 0}
     u64, u32 = (u_other, u_main) if prec == qbx.QBX_MIXED else (u_main, u_other)
     err_mixed = rel_l2(u32, u64)
     comparison = {"fp64" if other == qbx.QBX_FP64 else "mixed": {
-        "value": job_throughput(n_t, ws, args.steps, ms2), "ms_per_step": ms2 / args.steps}}
+        "value": job_throughput(n_t, ws, args.steps, ms2), "ms_per_step": ms2 / args.steps,
+        "per_kernel_ms": per_other}}
 
     # speedup at equal accuracy: both precisions over box orders p_fmm + p_add
     # from 8 up to the workload's own; at each tolerance, the fastest plan of each
@@ -376,6 +433,7 @@ def run_ours(args, w, ws, rank, local):
         fp32_only = f64 == 0.0 and f32 > 0.0
         peak = FP32_PEAK_TFLOPS if fp32_only else FP64_PEAK_TFLOPS
         achieved = (f32 if fp32_only else f64 + f32 * FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS) / t / 1e12
+        fma64, fma32 = qbx.qbx_measure_fma_rates()
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": roof_ms / per[dom],
                 "traffic": None, "traffic_source": None,
@@ -384,9 +442,10 @@ def run_ours(args, w, ws, rank, local):
                 "peak_basis": ("FP32" if fp32_only else "FP64") +
                               " FMA rate derived from unit counts and the 2.070 GHz max clock "
                               "(152 SMs x 2 FP64 / 128 FP32 FMA per clock x 2 flop): 1.259 / "
-                              "80.5 TFLOP/s; measured here: FP64 1.25, FP32 69.6 TFLOP/s. "
+                              "80.5 TFLOP/s (measured FMA rates in measured_fma_tflops). "
                               "achieved is FP64-equivalent (FP32 flops scaled by the peak "
                               "ratio) unless the kernel is FP32 only",
+                "measured_fma_tflops": {"fp64": fma64, "fp32": fma32},
                 "centres_formed": n_used if fmm else stats["n_centres"]}
         kt = known_traffic(dom, w["name"], args.precision)
         if kt:
@@ -433,6 +492,8 @@ def run_ours(args, w, ws, rank, local):
     h2d = 16 * g.n * ((1 if hS is not None else 0) + (1 if hD is not None else 0))
     e2e = {"value": job_throughput(n_t, ws, args.steps, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * n_t}
+    per64 = per if prec == qbx.QBX_FP64 else per_other
+    m2l_tc = m2l_tensor_roofline(lp, per64["m2l"]) if fmm and "m2l" in per64 else None
     res = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
                warmup=args.warmup, ms_per_step=total_ms / args.steps, higher_is_better=True,
                scaling="weak", vs_baseline=None,
@@ -446,7 +507,8 @@ def run_ours(args, w, ws, rank, local):
                        "n_boxes": stats["n_boxes"], "tree_build_s": tree_s,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single"},
-               roofline=roof, per_kernel_ms=per, gpu_launches=launches,
+               roofline=roof, m2l_tensor_roofline=m2l_tc, per_kernel_ms=per,
+               gpu_launches=launches,
                clocks=clk.summary(), e2e=e2e, equal_accuracy=eq, all_centres=all_c,
                **comparison)
     lp.close()

@@ -399,6 +399,25 @@ qbx_status qbx_selftest_wait_timeout(qbx_handle *h, int32_t limit_us);
 qbx_status qbx_hankel01(const double *x, int64_t n, int32_t variant, double *out);
 
 /*
+ * The FP64 -> FP32 rounding of the mixed-precision kernels (Sec. 7.2 Stages
+ * 3, 5 in mixed precision: Hankel values from the FP64 recurrences), done
+ * with integer instructions: round to nearest (ties away from zero), results
+ * below 2^-126 in magnitude flushed to zero, overflow to infinity, NaN kept.
+ * x: host [n]; out: host float [n]. Synchronous. Errors: QBX_ERR_ARG (NULL
+ * pointer with n > 0, n < 0), QBX_ERR_OOM / QBX_ERR_CUDA.
+ */
+qbx_status qbx_f32_from_f64(const double *x, int64_t n, float *out);
+
+/*
+ * Measured FMA rates of this GPU, the denominators of the arithmetic
+ * rooflines of the FP64 and mixed paths: 8 independent FMA chains per thread,
+ * 8 blocks of 256 threads per SM, best of three timed launches (CUDA events)
+ * after a warm-up; flops = 2 per FMA. Takes about 0.1 s. Synchronous. Errors:
+ * QBX_ERR_ARG (NULL output), QBX_ERR_CUDA.
+ */
+qbx_status qbx_measure_fma_rates(double *fp64_tflops, double *fp32_tflops);
+
+/*
  * Table 1 of the paper (Sec. 3.2): source nodes per panel q_src for q density
  * nodes and precision eps, as printed for q = 2, 4, 8, 16 and eps = 1e-3,
  * 1e-6, 1e-9, 1e-12. Other q take the row of the next tabulated q, other eps

@@ -987,7 +987,7 @@ __device__ __forceinline__ float2 fmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 fsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 f2(cd a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ float2 f2(cd a) { return make_float2(f32_from_f64(a.x), f32_from_f64(a.y)); }
 
 template <int PM, bool HS, bool HD>
 __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float2 (&C)[2 * PM + 1],

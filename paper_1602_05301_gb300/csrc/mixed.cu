@@ -425,8 +425,8 @@ __global__ void l2l_f32_matrix_kernel(int l, int pp, int pc, int pbmax, const cd
   }
 }
 
-// L2L on level l as tile GEMMs: a CTA takes kGemmRows parents and one child
-// quadrant c = blockIdx.y, stages the parents' sigma-normalised locals
+// L2L on level l as tile GEMMs: a CTA takes R parents, one child quadrant
+// c = blockIdx.y and kT child orders (chunk blockIdx.z), stages the parents' sigma-normalised locals
 // lambda_n = lh_n / conv_n (FP32) in shared memory, and computes
 // lambda'_s = sum_n Tl[c][n][s] lambda_n for all of them at once (threads over
 // s); the quadrant-c children get lh'_s += lambda'_s conv'_s in FP64.
@@ -454,7 +454,8 @@ __global__ void __launch_bounds__(kT) l2l_f32_kernel(
   {
     const int c = blockIdx.y;
     const float2* M = Tl + (size_t)c * Qp * Qc;
-    for (int so = threadIdx.x; so - (int)threadIdx.x < Qc; so += kT) {
+    {
+      const int so = (int)blockIdx.z * kT + threadIdx.x;  // output chunk blockIdx.z
       const bool act = so < Qc;
       float sr[R], si[R], cr[R], ci[R];
 #pragma unroll
@@ -502,10 +503,11 @@ __global__ void m2m_f32_matrix_kernel(int l, int pp, int pc, int pbmax, const cd
   }
 }
 
-// M2M on level l as tile GEMMs: a CTA takes kGemmRows parents; for each
-// quadrant it stages the children's sigma-normalised multipoles
-// mu_n = mh_n conv_n (FP32) and adds sum_n Tm2m[c][n][s] mu_n to the parents'
-// compensated sums (threads over s); mh'_s = mu'_s / conv'_s in FP64.
+// M2M on level l as tile GEMMs: a CTA takes R parents and kT output orders
+// (chunk blockIdx.y, so that the few wide boxes of coarse levels spread over
+// many CTAs); for each quadrant it stages the children's sigma-normalised
+// multipoles mu_n = mh_n conv_n (FP32) and adds sum_n Tm2m[c][n][s] mu_n to the
+// parents' compensated sums (threads over s); mh'_s = mu'_s / conv'_s in FP64.
 template <int R>
 __global__ void __launch_bounds__(kT) m2m_f32_kernel(
     int l, int pp, int pc, int pbmax, const int* __restrict__ parents, int nb,
@@ -530,8 +532,8 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
     }
     if (c == 4) poff[r] = o; else coff[c][r] = o;
   }
-  for (int so0 = 0; so0 < Qp; so0 += kT) {
-    const int so = so0 + threadIdx.x;
+  {
+    const int so = (int)blockIdx.y * kT + threadIdx.x;  // output chunk blockIdx.y
     const bool act = so < Qp;
     float sr[R], si[R], cr[R], ci[R];
 #pragma unroll
@@ -809,10 +811,10 @@ qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
     const float2* T = f->tmm_f32.ptr + f->h_tmm_off[l];
     if (nb >= kWideLevel || h->batched)
-      m2m_f32_kernel<kGemmRows><<<nblk(nb, kGemmRows), kT, (size_t)(2 * pc + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
+      m2m_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), nblk(2 * pp + 1, kT)), kT, (size_t)(2 * pc + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
     else
-      m2m_f32_kernel<kNarrowRows><<<nblk(nb, kNarrowRows), kT, (size_t)(2 * pc + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
+      m2m_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), nblk(2 * pp + 1, kT)), kT, (size_t)(2 * pc + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;
@@ -828,10 +830,10 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const int* par = f->nonleaf.ptr + f->nonleaf_off[l];
     const float2* T = f->tl_f32.ptr + f->h_tl_off[l];
     if (nb >= kWideLevel || h->batched)
-      l2l_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), 4), kT, (size_t)(2 * pp + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
+      l2l_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), 4, nblk(2 * pc + 1, kT)), kT, (size_t)(2 * pp + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
     else
-      l2l_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), 4), kT, (size_t)(2 * pp + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
+      l2l_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), 4, nblk(2 * pc + 1, kT)), kT, (size_t)(2 * pp + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
     QBX_CUDA_TRY(cudaGetLastError());
     h->launches += 1;

@@ -119,6 +119,25 @@ __device__ __forceinline__ void hankel01_wide(double x, double ix, cd& h0, cd& h
   hankel01_any<true>(x, ix, h0, h1);
 }
 
+// An FP64 value rounded to FP32 with integer instructions only: on GB300 the
+// conversion instruction occupies the FP64 pipe, which the mixed-precision
+// kernels keep busy with their recurrences. IEEE binary64 -> binary32 by the
+// bit fields: exponent rebiased (1023 -> 127), the top 23 of the 52 mantissa
+// bits kept and the result rounded to nearest by adding the next bit (ties
+// away from zero; a carry into the exponent is the correct result). Results
+// below the FP32 normal range (|v| < 2^-126) become zero, above it infinity;
+// NaN stays NaN.
+__device__ __forceinline__ float f32_from_f64(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned e64 = (hi >> 20) & 0x7FFu;
+  const int e = (int)e64 - 896;  // 1023 - 127
+  unsigned bits = ((unsigned)e << 23) + (((hi & 0xFFFFFu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+  bits = e <= 0 ? 0u : bits;
+  bits = e >= 255 ? 0x7F800000u : bits;
+  bits = e64 == 0x7FFu && (((hi & 0xFFFFFu) | lo) != 0u) ? 0x7FC00000u : bits;
+  return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
 // Start index of the backward recurrence for orders 0..pmax at argument x:
 // far enough above m = max(pmax, x) that the recurrence has converged to the
 // minimal solution to full double precision. The relative error of J_m from a

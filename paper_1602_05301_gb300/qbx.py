@@ -129,6 +129,10 @@ def library() -> ctypes.CDLL:
             lib.qbx_sync.argtypes = [_vp]
             lib.qbx_selftest_wait_timeout.restype = ctypes.c_int
             lib.qbx_selftest_wait_timeout.argtypes = [_vp, ctypes.c_int32]
+            lib.qbx_f32_from_f64.restype = ctypes.c_int
+            lib.qbx_f32_from_f64.argtypes = [_vp, ctypes.c_int64, _vp]
+            lib.qbx_measure_fma_rates.restype = ctypes.c_int
+            lib.qbx_measure_fma_rates.argtypes = [_vp, _vp]
             lib.qbx_hankel01.restype = ctypes.c_int
             lib.qbx_hankel01.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, _vp]
             _lib = lib
@@ -226,6 +230,21 @@ def qbx_hankel01(x, variant=0) -> np.ndarray:
     out = np.zeros((xx.size, 4))
     _check(library().qbx_hankel01(ptr(xx), int(xx.size), int(variant), ptr(out)))
     return out[:, 0::2] + 1j * out[:, 1::2]
+
+
+def qbx_f32_from_f64(x) -> np.ndarray:
+    """The mixed kernels' FP64 -> FP32 rounding, evaluated on the device."""
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(xx.size, np.float32)
+    _check(library().qbx_f32_from_f64(ptr(xx), int(xx.size), ptr(out)))
+    return out
+
+
+def qbx_measure_fma_rates():
+    """(FP64, FP32) FMA rates of the current GPU in TFLOP/s (qbx_measure_fma_rates)."""
+    out = np.zeros(2)
+    _check(library().qbx_measure_fma_rates(ptr(out[0:1]), ptr(out[1:2])))
+    return float(out[0]), float(out[1])
 
 
 def qbx_default_p_add(p: int) -> int:

@@ -44,3 +44,21 @@ def test_hankel01_against_scipy(qbxmod, variant, reach, bound):
         print("   library region, worst (x, err):",
               [(round(float(xo[lib][i]), 3), float(e[lib][i])) for i in worst])
         assert e[lib].max() < 2e-11
+
+
+def test_f32_rounding_matches_ieee(qbxmod):
+    """The integer-only FP64 -> FP32 rounding equals IEEE round-to-nearest
+    (numpy's cast) bit for bit away from exact ties, with results below the
+    FP32 normal range flushed to zero and overflow going to infinity."""
+    rng = np.random.default_rng(6)
+    x = np.concatenate([rng.standard_normal(200000) * 10.0 ** rng.uniform(-40, 40, 200000),
+                        [0.0, -0.0, 1.0, -1.0, 3.4028234663852886e38, 3.5e38, -1e39, 1e-38,
+                         1.1754943508222875e-38, 1e-45, np.inf, -np.inf, np.nan]])
+    got = qbxmod.qbx_f32_from_f64(x)
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    ref = np.where(np.abs(ref) < np.float32(1.1754943508222875e-38), np.float32(0.0), ref)
+    fin = np.isfinite(x)
+    assert np.array_equal(got[fin].view(np.uint32) & 0x7FFFFFFF, ref[fin].view(np.uint32) & 0x7FFFFFFF)
+    assert np.array_equal(np.signbit(got[fin & (ref != 0)]), np.signbit(ref[fin & (ref != 0)]))
+    assert np.isinf(got[~fin & ~np.isnan(x)]).all() and np.isnan(got[np.isnan(x)]).all()
