@@ -868,6 +868,8 @@ constexpr int kM2qbxlOrders = 4;
 constexpr int kM2qbxlBlock = 32;
 // shared memory of the L2QBXL rows of one warp (several warps per SM)
 constexpr size_t kL2qbxlSmem = 24 * 1024;
+// shared memory of the split rows of one mixed-precision M2QBXL warp
+constexpr size_t kM2qbxlMixedSmem = 48 * 1024;
 template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int* __restrict__ pair_ctr,
                                                                const int* __restrict__ pair_box,
@@ -1062,6 +1064,200 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
     wn_prev = wn_cur;
     wn_cur = wn_next;
     sgn = -sgn;
+  }
+}
+
+// ---------------------------------------------------------------- M2QBXL in mixed precision
+// The same translation as m2qbxl_pair_kernel,
+//   alpha_l += (-1)^l sum_n mh_n Wh_{n+l} s^{|n| - |n+l|},
+// with the Hankel recurrence and the angular factors in FP64 and the Q x P
+// products in FP32. The factors span far more than FP32's range (Wh_m grows
+// and mh_n falls by many decades with m, n), so each is held in split form,
+// FP32 mantissa times 2^e (split_pair): the product of three split factors is
+// an FP32 mantissa product and an integer exponent sum, exact apart from the
+// FP32 rounding of the mantissas. Every output sums its terms relative to its
+// largest one (2^Emax), FP32 with Kahan compensation, and is formed in FP64.
+//
+// A warp takes PW pairs: lane j runs pair j's recurrence and writes the split
+// rows Wp_m = Wh_m e^{i m th}, Wq_m = (-1)^m Wh_m e^{-i m th}, m <= pb + p,
+// to shared memory; then the lanes take the warp's (pair, output order)
+// items. Inputs: the split multipoles (split_coef_kernel) and the split powers
+// s^j, |j| <= p, per level (sf).
+
+// coefficients (multipoles or locals) of every box in split form, same layout
+__global__ void split_coef_kernel(const cd* __restrict__ mpole, long long n, float2* __restrict__ mm,
+                                int* __restrict__ me) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float2 m;
+  int e;
+  split_one(mpole[i], m, e);
+  mm[i] = m;
+  me[i] = e;
+}
+
+// s_l^j, j = -p..p, of every level in split form: [n_levels][2p+1]
+__global__ void sf_split_kernel(Fmm F, float* __restrict__ sfm, int* __restrict__ sfe) {
+  const int l = blockIdx.x, P = 2 * F.p + 1;
+  const double* pwl = pw_row(F, l);
+  const double* ipl = ipw_row(F, l);
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    const int jj = j - F.p;
+    const double v = jj >= 0 ? pwl[jj] : ipl[-jj];
+    float2 m;
+    int e;
+    split_one(mk(v, 0.0), m, e);
+    sfm[(size_t)l * P + j] = m.x;
+    sfe[(size_t)l * P + j] = e;
+  }
+}
+
+__global__ void __launch_bounds__(32) m2qbxl_mixed_kernel(
+    Fmm F, const int* __restrict__ pair_ctr, const int* __restrict__ pair_box, int n_pairs,
+    int PW, int TW, const float2* __restrict__ mm, const int* __restrict__ me,
+    const float* __restrict__ sfm, const int* __restrict__ sfe, cd* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char m2q_smem[];
+  float2* wp = reinterpret_cast<float2*>(m2q_smem);  // [PW][TW]
+  float2* wq = wp + (size_t)PW * TW;                 // [PW][TW]
+  int* we = reinterpret_cast<int*>(wq + (size_t)PW * TW);  // [PW][TW]
+  const int lane = threadIdx.x;
+  const int t0 = blockIdx.x * PW;
+  const int p = F.p, P = 2 * p + 1;
+  const int npw = min(PW, n_pairs - t0);
+  if (lane < npw) {
+    const int t = t0 + lane;
+    const int i = pair_ctr[t], c = pair_box[t];
+    const int lc = F.level[c];
+    const double s = F.scale[lc];
+    const int M = F.lpb[lc] + p;
+    const double2 z = F.cxy[i];
+    const double2 mc = F.centre[c];
+    const double dx = z.x - mc.x, dy = z.y - mc.y;
+    const double d2 = dx * dx + dy * dy;
+    const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr / F.k;
+    const cd e1 = mk(dx * irr, dy * irr);
+    cd h0, h1;
+    hankel01_wide(x, ix, h0, h1);
+    const double c1 = 2.0 * s * ix, s2 = s * s;
+    cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
+    float2* rp = wp + (size_t)lane * TW;
+    float2* rq = wq + (size_t)lane * TW;
+    int* re = we + (size_t)lane * TW;
+    split_pair(h0, h0, rp[0], rq[0], re[0]);
+    for (int m = 1; m <= M; ++m) {
+      ee = cmul(ee, e1);
+      const double ac = hm.x * ee.x, bd = hm.y * ee.y, ad = hm.x * ee.y, bc = hm.y * ee.x;
+      const double sm = (m & 1) ? -1.0 : 1.0;
+      split_pair(mk(ac - bd, ad + bc), mk(sm * (ac + bd), sm * (bc - ad)), rp[m], rq[m], re[m]);
+      const cd hn = mk(fma((double)m * c1, hm.x, -s2 * hm1.x), fma((double)m * c1, hm.y, -s2 * hm1.y));
+      hm1 = hm;
+      hm = hn;
+    }
+  }
+  __syncwarp();
+  for (int o = lane; o < npw * P; o += 32) {
+    const int u = o / P, lo = o % P - p;
+    const int t = t0 + u;
+    const int c = pair_box[t];
+    const int lc = F.level[c];
+    const int pb = F.lpb[lc];
+    const long long off = F.eoff[c] + pb;
+    const float2* rp = wp + (size_t)u * TW;
+    const float2* rq = wq + (size_t)u * TW;
+    const int* re = we + (size_t)u * TW;
+    const float* fm = sfm + (size_t)lc * P + p;
+    const int* fe = sfe + (size_t)lc * P + p;
+    int emax = 2 * kZeroExp;
+    for (int n = -pb; n <= pb; ++n) {
+      const int m = n + lo, am = abs(m);
+      emax = max(emax, me[off + n] + re[am] + fe[abs(n) - am]);
+    }
+    float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
+    for (int n = -pb; n <= pb; ++n) {
+      const int m = n + lo, am = abs(m);
+      const int j = abs(n) - am;
+      const int d = me[off + n] + re[am] + fe[j] - emax;
+      if (d < -126) continue;
+      const float f = fm[j] * pow2f(d);
+      const float2 w = m >= 0 ? rp[am] : rq[am];
+      const float2 v = fmul(mm[off + n], w);
+      kahan2(S, C, make_float2(v.x * f, v.y * f));
+    }
+    const double sc = (lo & 1) ? -pow2d(emax) : pow2d(emax);
+    partial[(size_t)t * P + lo + p] =
+        mk(((double)S.x - (double)C.x) * sc, ((double)S.y - (double)C.y) * sc);
+  }
+}
+
+// ---------------------------------------------------------------- L2QBXL in mixed precision
+// The translation of l2qbxl_kernel, alpha_s += sum_n gamma_n t_{s-n}, with the
+// Miller recurrence (J_m) and the angular factors in FP64 and the products in
+// FP32 on split factors (as in m2qbxl_mixed_kernel): the leaf's local
+// coefficients gamma_n (large for large |n|) and the row V_m = J_m e^{i m th}
+// (small for large m) as FP32 mantissas with integer exponents; each output
+// sums relative to its largest term with Kahan compensation. A warp takes G
+// centres; lane j fills centre j's row in FP64 and converts it in place to
+// split form (FP32 mantissa pair and exponent in the 16 bytes of each entry).
+__global__ void __launch_bounds__(32) l2qbxl_mixed_kernel(Fmm F, const int* __restrict__ cleaf,
+                                                          const int* __restrict__ clist, int n_ctr,
+                                                          int G, int TW,
+                                                          const float2* __restrict__ gm,
+                                                          const int* __restrict__ ge,
+                                                          cd* __restrict__ alpha) {
+  extern __shared__ cd trow[];  // [G][TW]
+  const int lane = threadIdx.x;
+  const int c0 = blockIdx.x * G;
+  const int p = F.p, P = 2 * p + 1;
+  if (lane < G && c0 + lane < n_ctr) {
+    const int i = clist[c0 + lane];
+    const int b = cleaf[i];
+    const int M = F.lpb[F.level[b]] + p;
+    const double2 mb = F.centre[b];
+    const double dx = F.cxy[i].x - mb.x, dy = F.cxy[i].y - mb.y;
+    const double rr = sqrt(dx * dx + dy * dy);
+    cd* row = trow + (size_t)lane * TW;
+    const double in = 1.0 / miller_row(F.k * rr, M, (double*)row, 2);
+    const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
+    cd e = mk(1.0, 0.0);
+    for (int m = 0; m <= M; ++m) {
+      float2 mv;
+      int ev;
+      split_one(cscale(e, row[m].x * in), mv, ev);
+      float4* slot = reinterpret_cast<float4*>(row + m);
+      *slot = make_float4(mv.x, mv.y, __int_as_float(ev), 0.f);
+      e = cmul(e, e1);
+    }
+  }
+  __syncwarp();
+  const int nG = min(G, n_ctr - c0);
+  for (int o = lane; o < nG * P; o += 32) {
+    const int u = o / P, so = o % P - p;
+    const int i = clist[c0 + u];
+    const int b = cleaf[i];
+    const int pb = F.lpb[F.level[b]];
+    const float4* row = reinterpret_cast<const float4*>(trow + (size_t)u * TW);
+    const long long off = F.eoff[b] + pb;
+    int emax = 2 * kZeroExp;
+    for (int n = -pb; n <= pb; ++n)
+      emax = max(emax, ge[off + n] + __float_as_int(row[abs(so - n)].z));
+    float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
+    for (int n = -pb; n <= pb; ++n) {
+      const int m = so - n;
+      const float4 v = row[abs(m)];
+      const int d = ge[off + n] + __float_as_int(v.z) - emax;
+      if (d < -126) continue;
+      // t_m = (-1)^m V_m (m >= 0), conj(V_-m) (m < 0): signs on the bits
+      const unsigned fx = (m >= 0 && (m & 1)) ? 0x80000000u : 0u;
+      const unsigned fy = m < 0 ? 0x80000000u : fx;
+      const float2 t = make_float2(__uint_as_float(__float_as_uint(v.x) ^ fx),
+                                   __uint_as_float(__float_as_uint(v.y) ^ fy));
+      const float f = pow2f(d);
+      const float2 w = fmul(gm[off + n], t);
+      kahan2(S, C, make_float2(w.x * f, w.y * f));
+    }
+    const double sc = pow2d(emax);
+    cd* dst = alpha + (size_t)F.cid[i] * P + p + so;
+    *dst = cadd(*dst, mk(((double)S.x - (double)C.x) * sc, ((double)S.y - (double)C.y) * sc));
   }
 }
 
@@ -1368,6 +1564,8 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   QBX_CUDA_TRY(cudaGetLastError());
   QBX_CUDA_TRY(f->mpole.alloc(std::max<int64_t>(1, f->n_coef)));
   QBX_CUDA_TRY(f->local.alloc(std::max<int64_t>(1, f->n_coef)));
+  QBX_CUDA_TRY(f->sp_m.alloc(std::max<int64_t>(1, f->n_coef)));
+  QBX_CUDA_TRY(f->sp_e.alloc(std::max<int64_t>(1, f->n_coef)));
   TRY(configure_kernels());
   // side stream and events for the concurrent near-field stages (created here,
   // outside any stream capture; owned by the plan)
@@ -1562,6 +1760,8 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
       }
       S.n = (int)list.size();
       S.n_pairs = (int)pc.size();
+      S.wp_pbmax = 0;
+      for (int c : pbx) S.wp_pbmax = std::max(S.wp_pbmax, f->h_pb[blev[c]]);
       max_pairs = std::max(max_pairs, pc.size());
       auto up = [](DevBuf<int>& d, const std::vector<int>& v) -> qbx_status {
         QBX_CUDA_TRY(d.alloc(std::max<size_t>(1, v.size())));
@@ -1576,6 +1776,8 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
     }
     QBX_CUDA_TRY(f->wpart.alloc(max_pairs * (size_t)(2 * h->p + 1)));
     f->n_wpairs = f->cset[0].n_pairs;
+    QBX_CUDA_TRY(f->sf_m.alloc((size_t)f->n_levels * (2 * h->p + 1)));
+    QBX_CUDA_TRY(f->sf_e.alloc((size_t)f->n_levels * (2 * h->p + 1)));
   }
   // P2M work items over segments of the source leaves (see p2m_item_kernel)
   {
@@ -1730,7 +1932,7 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
 
 // L2QBXL at the centres of set C (adds to alpha).
 qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSet& C, cd* alpha,
-                         cudaStream_t s) {
+                         bool mixed, cudaStream_t s) {
   if (C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_L2QBXL, s);
   // a warp per G centres. G: up to 32 (every lane fills a row), but no more
@@ -1745,7 +1947,15 @@ qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSe
       while (!h->batched && G > 1 && (C.n + G - 1) / G < 152 * 2) G /= 2;
     while (G > 1 && (size_t)G * TW * sizeof(cd) > kL2qbxlSmem) G /= 2;
     const size_t sm = (size_t)G * TW * sizeof(cd);
-    l2qbxl_kernel<<<nblk(C.n, G), 32, sm, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, G, TW, alpha);
+    if (mixed) {
+      split_coef_kernel<<<nblk(f->n_coef, 256), 256, 0, s>>>(f->local.ptr, f->n_coef, f->sp_m.ptr,
+                                                             f->sp_e.ptr);
+      l2qbxl_mixed_kernel<<<nblk(C.n, G), 32, sm, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, G, TW,
+                                                      f->sp_m.ptr, f->sp_e.ptr, alpha);
+      h->launches += 1;
+    } else {
+      l2qbxl_kernel<<<nblk(C.n, G), 32, sm, s>>>(F, f->cleaf.ptr, C.clist.ptr, C.n, G, TW, alpha);
+    }
   }
   QBX_KCHECK("l2qbxl", s);
   stage_end(h, QBX_STAGE_L2QBXL, s);
@@ -1756,18 +1966,37 @@ qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSe
 // M2QBXL at the centres of set C (adds to alpha).
 template <int PM>
 qbx_status launch_m2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D,
-                         const CentreSet& C, cd* alpha, cudaStream_t s) {
+                         const CentreSet& C, cd* alpha, bool mixed, cudaStream_t s) {
   if (C.n == 0) return QBX_OK;
   stage_begin(h, QBX_STAGE_M2QBXL, s);
   if (C.n_pairs > 0 && (S || D)) {
     const int np = C.n_pairs;
     cd* part = f->wpart.ptr;
-    const int nparts = (2 * h->p + 1 + kM2qbxlOrders - 1) / kM2qbxlOrders;
-    const unsigned gb = nblk((int64_t)np * nparts, kM2qbxlBlock);
-    constexpr int B = kM2qbxlBlock;
-    if (S && D) m2qbxl_pair_kernel<PM, true, true><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
-    else if (S) m2qbxl_pair_kernel<PM, true, false><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
-    else m2qbxl_pair_kernel<PM, false, true><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+    // mixed: pairs per warp PW so that a warp's split rows (20 B per order)
+    // take at most kM2qbxlMixedSmem, and, for a handle evaluated alone, fewer
+    // while that leaves under two warps per SM (few pairs: spread the
+    // sequential recurrences over all SMs)
+    const int TW = C.wp_pbmax + h->p + 1;
+    int PW = 32;
+    while (PW > 1 && (size_t)PW * TW * 20 > kM2qbxlMixedSmem) PW /= 2;
+    while (!h->batched && PW > 1 && (np + PW - 1) / PW < 152 * 2) PW /= 2;
+    if (mixed && (size_t)PW * TW * 20 <= kM2qbxlMixedSmem) {
+      const long long ncoef = f->n_coef;
+      split_coef_kernel<<<nblk(ncoef, 256), 256, 0, s>>>(f->mpole.ptr, ncoef, f->sp_m.ptr,
+                                                        f->sp_e.ptr);
+      sf_split_kernel<<<f->n_levels, 64, 0, s>>>(F, f->sf_m.ptr, f->sf_e.ptr);
+      m2qbxl_mixed_kernel<<<nblk(np, PW), 32, (size_t)PW * TW * 20, s>>>(
+          F, C.wp_ctr.ptr, C.wp_box.ptr, np, PW, TW, f->sp_m.ptr, f->sp_e.ptr, f->sf_m.ptr,
+          f->sf_e.ptr, part);
+      h->launches += 2;
+    } else {
+      const int nparts = (2 * h->p + 1 + kM2qbxlOrders - 1) / kM2qbxlOrders;
+      const unsigned gb = nblk((int64_t)np * nparts, kM2qbxlBlock);
+      constexpr int B = kM2qbxlBlock;
+      if (S && D) m2qbxl_pair_kernel<PM, true, true><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+      else if (S) m2qbxl_pair_kernel<PM, true, false><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+      else m2qbxl_pair_kernel<PM, false, true><<<gb, B, 0, s>>>(F, C.wp_ctr.ptr, C.wp_box.ptr, np, part);
+    }
     QBX_KCHECK("m2qbxl", s);
     const int P = 2 * h->p + 1;
     m2qbxl_sum_kernel<<<nblk((int64_t)C.n * P, 256), 256, 0, s>>>(C.n, P, C.wp_off.ptr, part,
@@ -1927,10 +2156,10 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   TRY(wait(s2, f->ev_m2m));
   if (h->n_ctr > 0) {
     cd* alpha = h->alpha.ptr;
-    if (h->p <= 4) TRY(launch_m2qbxl<4>(F, f, h, S, D, C, alpha, s2));
-    else if (h->p <= 8) TRY(launch_m2qbxl<8>(F, f, h, S, D, C, alpha, s2));
-    else if (h->p <= 12) TRY(launch_m2qbxl<12>(F, f, h, S, D, C, alpha, s2));
-    else TRY(launch_m2qbxl<16>(F, f, h, S, D, C, alpha, s2));
+    if (h->p <= 4) TRY(launch_m2qbxl<4>(F, f, h, S, D, C, alpha, mixed, s2));
+    else if (h->p <= 8) TRY(launch_m2qbxl<8>(F, f, h, S, D, C, alpha, mixed, s2));
+    else if (h->p <= 12) TRY(launch_m2qbxl<12>(F, f, h, S, D, C, alpha, mixed, s2));
+    else TRY(launch_m2qbxl<16>(F, f, h, S, D, C, alpha, mixed, s2));
   }
   stage_begin(h, QBX_STAGE_M2P, s2);
   if (f->n_wtgt > 0 && f->n_m2p_pairs > 0) {
@@ -1998,7 +2227,7 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   TRY(wait(s, f->ev_join));
   if (h->n_ctr > 0) {
     cd* alpha = h->alpha.ptr;
-    TRY(launch_l2qbxl(F, f, h, C, alpha, s));
+    TRY(launch_l2qbxl(F, f, h, C, alpha, mixed, s));
   }
   QBX_CUDA_TRY(cudaGetLastError());
   return QBX_OK;

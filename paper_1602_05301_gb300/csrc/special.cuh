@@ -138,6 +138,49 @@ __device__ __forceinline__ float f32_from_f64(double v) {
   return __uint_as_float(bits | (hi & 0x80000000u));
 }
 
+// Split form of values whose range exceeds FP32: v = m 2^e with FP32
+// mantissas m (the larger component's magnitude in [1, 2)) and an integer
+// exponent e; zero (and FP64 subnormals) give m = 0, e = kZeroExp. Integer
+// instructions only (field arithmetic on the IEEE bit patterns).
+constexpr int kZeroExp = -(1 << 20);
+// x (exponent field ex, high word hx) times 2^-(E - 1023), as FP32
+__device__ __forceinline__ float split_part(double x, unsigned hx, int ex, int E) {
+  const int f = ex - E + 1023;  // new exponent field
+  if (ex == 0 || f < 1) return 0.f;
+  const unsigned h2 = (hx & 0x800FFFFFu) | ((unsigned)f << 20);
+  return f32_from_f64(__hiloint2double((int)h2, __double2loint(x)));
+}
+// two complex values sharing one exponent (e.g. H_m e^{+-i m th}, of equal modulus)
+__device__ __forceinline__ void split_pair(cd a, cd b, float2& ma, float2& mb, int& e) {
+  const unsigned h0 = (unsigned)__double2hiint(a.x), h1 = (unsigned)__double2hiint(a.y);
+  const unsigned h2 = (unsigned)__double2hiint(b.x), h3 = (unsigned)__double2hiint(b.y);
+  const int e0 = (h0 >> 20) & 0x7FF, e1 = (h1 >> 20) & 0x7FF;
+  const int e2 = (h2 >> 20) & 0x7FF, e3 = (h3 >> 20) & 0x7FF;
+  const int E = max(max(e0, e1), max(e2, e3));
+  if (E == 0) {
+    ma = mb = make_float2(0.f, 0.f);
+    e = kZeroExp;
+    return;
+  }
+  e = E - 1023;
+  ma = make_float2(split_part(a.x, h0, e0, E), split_part(a.y, h1, e1, E));
+  mb = make_float2(split_part(b.x, h2, e2, E), split_part(b.y, h3, e3, E));
+}
+__device__ __forceinline__ void split_one(cd a, float2& m, int& e) {
+  float2 dummy;
+  split_pair(a, mk(0.0, 0.0), m, dummy, e);
+}
+// 2^d as FP32 for d <= 127 (0 below the normal range)
+__device__ __forceinline__ float pow2f(int d) {
+  return d < -126 ? 0.f : __int_as_float((d + 127) << 23);
+}
+// 2^d as FP64 (0 below the normal range, infinity above it)
+__device__ __forceinline__ double pow2d(int d) {
+  if (d < -1022) return 0.0;
+  if (d > 1023) return __longlong_as_double(0x7FF0000000000000ll);
+  return __hiloint2double((d + 1023) << 20, 0);
+}
+
 // Start index of the backward recurrence for orders 0..pmax at argument x:
 // far enough above m = max(pmax, x) that the recurrence has converged to the
 // minimal solution to full double precision. The relative error of J_m from a

@@ -24,6 +24,7 @@ struct Csr {
 struct CentreSet {
   DevBuf<int> clist, wp_ctr, wp_box, wp_off;
   int n = 0, n_pairs = 0;
+  int wp_pbmax = 0;  // largest box order among the M2QBXL pairs' boxes
 };
 
 struct FmmPlan {
@@ -109,6 +110,13 @@ struct FmmPlan {
   CentreSet cset[2];
   int n_wpairs = 0;                     // pairs over all centres (statistics)
   DevBuf<cd> wpart;                     // [max pairs][2p+1] partial coefficients
+  // mixed-precision M2QBXL and L2QBXL: coefficients in split form (FP32
+  // mantissa, exponent; the multipoles while M2QBXL runs, then the leaf locals
+  // for L2QBXL, which starts after it) and the powers s^j (|j| <= p) of every
+  // level
+  DevBuf<float2> sp_m;
+  DevBuf<int> sp_e, sf_e;
+  DevBuf<float> sf_m;
   DevBuf<int> wd_off, wd_box;           // per centre: W-list boxes summed directly (CSR)
   DevBuf<cd> t_m2l;                     // [n_levels][49][4 pb_max + 1] scaled Hankel vectors
   DevBuf<cd> t_m2m;                     // [n_levels][4][4 pb_max + 1] conj(V_m(d)) child->parent

@@ -28,7 +28,7 @@ def plane_wave(k, phi, xy):
 
 
 @pytest.mark.parametrize("mode,prec,tol", [("fmm", "fp64", 1e-11), ("direct", "fp64", 1e-11),
-                                           ("fmm", "mixed", 1e-5)])
+                                           ("fmm", "mixed", 1e-6)])
 def test_circle_scattering_against_fourier_series(qbxmod, mode, prec, tol):
     """Unit circle, k = 5, plane wave from angle phi. Mode n of the density:
     sigma_n = -i^n J_n(k) e^{-in phi} / lam_n, lam_n = (i pi k/2) J_n'(k) H_n(k) +
