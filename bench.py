@@ -105,13 +105,51 @@ def m2l_tensor_roofline(lp, m2l_ms):
             "roofline_ms": 1e3 * t_roof, "frac": 1e3 * t_roof / m2l_ms, "levels": rows}
 
 
+def function_text(src, name):
+    """Source text of the first definition of function `name` in src: from
+    the line that declares it to its matching closing brace."""
+    i = 0
+    while True:
+        i = src.find(name + "(", i)
+        if i < 0:
+            return None
+        j = src.find("{", i)
+        k = src.find(";", i)
+        if j >= 0 and (k < 0 or j < k):   # a definition, not a call or declaration
+            break
+        i += len(name)
+    depth, e = 0, j
+    while e < len(src):
+        depth += {"{": 1, "}": -1}.get(src[e], 0)
+        e += 1
+        if depth == 0:
+            break
+    return src[src.rfind("\n", 0, i) + 1:e]
+
+
+def kernel_sha256(spec):
+    """sha256 over the definitions named by spec, "file:fn+fn;file:fn" (files
+    relative to the repository root), so that an ncu summary stays valid for
+    edits elsewhere in those files and goes stale when the kernel changes."""
+    import hashlib
+    h = hashlib.sha256()
+    for part in spec.split(";"):
+        path, fns = part.split(":")
+        text = open(os.path.join(ROOT, path)).read()
+        for fn in fns.split("+"):
+            body = function_text(text, fn)
+            if body is None:
+                return None
+            h.update(body.encode())
+    return h.hexdigest()
+
+
 def known_traffic(stage, workload, precision):
     """DRAM bytes per launch of a stage's kernels, from a committed ncu summary
     under profiles/ ("bench-traffic:" lines: stage, workload, precision, bytes,
-    and the sha256 of the kernel's source file when it was captured). None when
-    no summary covers the stage or its source has changed since the capture."""
+    and the sha256 of the kernel's source functions when it was captured). None
+    when no summary covers the stage or its kernel has changed since."""
     import glob
-    import hashlib
     for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
         for line in open(path):
             if not line.startswith("bench-traffic:"):
@@ -120,11 +158,11 @@ def known_traffic(stage, workload, precision):
             if (kv.get("stage"), kv.get("workload"), kv.get("precision")) != (stage, workload,
                                                                               precision):
                 continue
-            src = os.path.join(ROOT, kv.get("source", ""))
-            if not os.path.isfile(src):
+            try:
+                sha = kernel_sha256(kv.get("functions", ""))
+            except (OSError, ValueError):
                 return None
-            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-            if sha != kv.get("source_sha256"):
+            if sha is None or sha != kv.get("functions_sha256"):
                 return None
             return float(kv["bytes_per_launch"]), os.path.relpath(path, ROOT)
     return None

@@ -1582,6 +1582,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   }
   TRY(mixed_plan_build(h, f));
   TRY(tc_plan_build(h, f));
+  TRY(tc_mml_plan_build(h, f));
   QBX_CUDA_TRY(f->qs.alloc(std::max<int64_t>(1, h->n_src)));
   QBX_CUDA_TRY(f->ds.alloc(std::max<int64_t>(1, h->n_src)));
   QBX_CUDA_TRY(f->q32.alloc(std::max<int64_t>(1, h->n_src)));
@@ -2145,6 +2146,12 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     for (int l = f->n_levels - 2; l >= 2; --l) {
       const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
       if (nb == 0) continue;
+      bool done = false;  // tensor cores where the level's split is exact
+      TRY(launch_mml_tc(h, f, 0, l, &done, s));
+      if (done) {
+        QBX_KCHECK("m2m_tc", s);
+        continue;
+      }
       m2m_kernel<<<nb, kThreads, m2m_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
       QBX_KCHECK("m2m", s);
       h->launches += 1;
@@ -2203,6 +2210,12 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
     for (int l = 2; l + 1 < f->n_levels; ++l) {
       const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
       if (nb == 0) continue;
+      bool done = false;  // tensor cores where the level's split is exact
+      TRY(launch_mml_tc(h, f, 1, l, &done, s));
+      if (done) {
+        QBX_KCHECK("l2l_tc", s);
+        continue;
+      }
       l2l_kernel<<<nb, kThreads, l2l_smem(pb[l], pb[l + 1]), s>>>(F, f->nonleaf.ptr + f->nonleaf_off[l]);
       QBX_KCHECK("l2l", s);
       h->launches += 1;

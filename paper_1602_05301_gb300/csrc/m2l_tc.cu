@@ -256,6 +256,133 @@ __global__ void __launch_bounds__(kThr) tc_mu_kernel(
   }
 }
 
+// Matrix slices of the four quadrant groups of one parent level l of M2M
+// (kind 0: child orders in, parent orders out) or L2L (kind 1: parent orders
+// in, child orders out), from the FP64 tables of conj(V_m) (M2M) and
+// (-1)^m V_m (L2L) of the quadrant's shift, sigma-normalised:
+//   M2M  T[so][n] = (sig_{l+1,|n|} / sig_{l,|so|}) conj(V_{so-n}),
+//   L2L  T[so][n] = (sig_{l+1,|so|} / sig_{l,|n|}) (-1)^{so-n} V_{so-n},
+// in the real form of tc_matrix_kernel. Grid (4, Np), threads over k < K.
+// Slices [quadrant][S][Np][K], row exponents [quadrant][Np].
+__global__ void __launch_bounds__(kThr) tc_mml_matrix_kernel(
+    int kind, int l, int pp, int pc, int pbmax, const cd* __restrict__ tab,
+    const double* __restrict__ lsig, int K, int Np, int beta, int S, __nv_bfloat16* __restrict__ A,
+    int* __restrict__ fexp) {
+  __shared__ double red[kThr / 32];
+  const int c = blockIdx.x, j = blockIdx.y;
+  const int pin = kind == 0 ? pc : pp, pout = kind == 0 ? pp : pc;
+  const int Qin = 2 * pin + 1, Qout = 2 * pout + 1;
+  const cd* v = tab + ((size_t)l * 4 + c) * (4 * pbmax + 1) + 2 * pbmax;
+  const double* sp = lsig + (size_t)l * (pbmax + 1);        // parent level
+  const double* sc = lsig + (size_t)(l + 1) * (pbmax + 1);  // child level
+  const int so = (j < Qout ? j : j - Qout) - pout;
+  const bool im_out = j >= Qout;
+  double vals[16];  // k = threadIdx.x + 128 t, K <= 2048
+  double m = 0.0;
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    double val = 0.0;
+    if (j < 2 * Qout && k < 2 * Qin) {
+      const int n = (k < Qin ? k : k - Qin) - pin;
+      const cd e = v[so - n];
+      const double mag = hypot(e.x, e.y);
+      cd T = mk(0.0, 0.0);
+      if (mag > 0.0) {
+        const double lf = (kind == 0 ? sc[abs(n)] - sp[abs(so)] : sc[abs(so)] - sp[abs(n)]) + log(mag);
+        const double f = lf < -700.0 ? 0.0 : exp(lf) / mag;
+        T = mk(e.x * f, e.y * f);
+      }
+      const bool im_in = k >= Qin;
+      val = im_out ? (im_in ? T.x : T.y) : (im_in ? -T.y : T.x);
+    }
+    vals[t] = val;
+    m = fmax(m, fabs(val));
+  }
+  m = block_max(m, red);
+  const int e = scale_exponent(m);
+  if (threadIdx.x == 0) fexp[(size_t)c * Np + j] = e;
+  __nv_bfloat16* dst = A + (size_t)c * S * Np * K + (size_t)j * K;
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    if (k < K) split_digits(vals[t], e, beta, S, dst + k, (size_t)Np * K);
+  }
+}
+
+// Vector slices of the source boxes of one M2M / L2L level: M2M the children's
+// multipoles mu_n = mh_n conv_|n| (level l+1), L2L the parents' locals
+// lambda_n = lh_n / conv_|n| (level l); x = (Re, Im) padded to K, one exponent
+// per box, slices [S][K] at xoff[i]. One block per source box.
+__global__ void __launch_bounds__(kThr) tc_mml_vec_kernel(
+    int kind, const int* __restrict__ boxes, const cd* __restrict__ coef, int lsrc, int pb, int K,
+    int beta, int S, const double* __restrict__ conv, int pbmax, const long long* __restrict__ eoff,
+    const long long* __restrict__ xoff, __nv_bfloat16* __restrict__ X, int* __restrict__ xexp) {
+  __shared__ double red[kThr / 32];
+  const int b = boxes[blockIdx.x];
+  const int Q = 2 * pb + 1;
+  const double* cv = conv + (size_t)lsrc * (pbmax + 1);
+  const cd* a = coef + eoff[b];
+  double vals[16];  // K <= 2048
+  double m = 0.0;
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    double v = 0.0;
+    if (k < 2 * Q) {
+      const int n = k < Q ? k : k - Q;
+      const double f = kind == 0 ? cv[abs(n - pb)] : 1.0 / cv[abs(n - pb)];
+      v = (k < Q ? a[n].x : a[n].y) * f;
+    }
+    vals[t] = v;
+    m = fmax(m, fabs(v));
+  }
+  m = block_max(m, red);
+  const int e = scale_exponent(m);
+  if (threadIdx.x == 0) xexp[blockIdx.x] = e;
+  __nv_bfloat16* dst = X + xoff[blockIdx.x];
+  for (int t = 0; t < 16; ++t) {
+    const int k = threadIdx.x + kThr * t;
+    if (k < K) split_digits(vals[t], e, beta, S, dst + k, (size_t)K);
+  }
+}
+
+// M2M: mh_p[so] = (sum over the parent's child rows, quadrant order, float-float)
+// / conv_l[|so|]. prow[i][c]: the row of parent i's quadrant-c child (-1: none).
+__global__ void __launch_bounds__(kThr) tc_m2m_reduce_kernel(
+    const int* __restrict__ parents, const int* __restrict__ prow, int pp, int l, int pbmax,
+    const double* __restrict__ conv, const cd* __restrict__ Y, const long long* __restrict__ eoff,
+    cd* __restrict__ mpole) {
+  const int i = blockIdx.x;
+  const int Q = 2 * pp + 1;
+  const double* cv = conv + (size_t)l * (pbmax + 1);
+  cd* dst = mpole + eoff[parents[i]];
+  for (int lo = threadIdx.x; lo < Q; lo += kThr) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int c = 0; c < 4; ++c) {
+      const int r = prow[4 * i + c];
+      if (r < 0) continue;
+      const float4 y = reinterpret_cast<const float4*>(Y)[(size_t)r * Q + lo];
+      ff_add(rh, rl, y.x, y.y);
+      ff_add(ih, il, y.z, y.w);
+    }
+    const double f = 1.0 / cv[abs(lo - pp)];
+    dst[lo] = mk(((double)rh + (double)rl) * f, ((double)ih + (double)il) * f);
+  }
+}
+
+// L2L: lh_child[so] += row value * conv_{l+1}[|so|]. One block per row (child).
+__global__ void __launch_bounds__(kThr) tc_l2l_apply_kernel(
+    const int* __restrict__ rowdst, int pc, int lc, int pbmax, const double* __restrict__ conv,
+    const cd* __restrict__ Y, const long long* __restrict__ eoff, cd* __restrict__ local) {
+  const int r = blockIdx.x;
+  const int Q = 2 * pc + 1;
+  const double* cv = conv + (size_t)lc * (pbmax + 1);
+  cd* dst = local + eoff[rowdst[r]];
+  for (int lo = threadIdx.x; lo < Q; lo += kThr) {
+    const float4 y = reinterpret_cast<const float4*>(Y)[(size_t)r * Q + lo];
+    const double f = cv[abs(lo - pc)];
+    dst[lo] = cadd(dst[lo], mk(((double)y.x + (double)y.y) * f, ((double)y.z + (double)y.w) * f));
+  }
+}
+
 // 16-byte asynchronous copy global -> shared (zero fill when bytes == 0)
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
@@ -273,7 +400,11 @@ __host__ __device__ constexpr int tc_stages(int SU) {
              : (220 * 1024) / (SU * (kRows + kNC) * kKC * 2);
 }
 
-// The tile product. Item (first row, rows, first output, group). SD slices are
+// The tile product. A group is one operator: a (level, offset class) of M2L
+// or a (level, quadrant) of M2M / L2L, with gp[group] = (K, Q, beta, Np): the
+// padded input width (slice stride of X, row stride of A), Q complex outputs
+// (2Q real rows of A, padded to Np), the digit bits. Item (first row, rows,
+// first output, group). SD slices are
 // stored per operand (the level's split), the first SU of them are used: SU =
 // SD for the FP64 path, fewer for the mixed path (the leading digits are a
 // 24- to 28-bit approximation). Y receives, for each pair row and complex
@@ -289,7 +420,7 @@ __host__ __device__ constexpr int tc_stages(int SU) {
 // c + NS - 1.
 template <int SD, int SU>
 __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
-    const int4* __restrict__ items, const int4* __restrict__ lvl, const int* __restrict__ lpb,
+    const int4* __restrict__ items, const int4* __restrict__ gp,
     const long long* __restrict__ gaoff, const long long* __restrict__ gfoff,
     const __nv_bfloat16* __restrict__ A, const int* __restrict__ fexp,
     const int* __restrict__ rowsrc, const long long* __restrict__ xoff,
@@ -312,9 +443,10 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 I = items[blockIdx.x];
   const int row0 = I.x, nr = I.y, n0 = I.z, g = I.w;
-  const int l = g / 49;
-  const int Kp = lvl[l].w, beta = lvl[l].y;
-  const int Q = 2 * lpb[l] + 1;
+  // group: K (padded input width; slice stride of X and of an A row), Q
+  // complex outputs, digit bits, Np (padded output rows of A)
+  const int4 G = gp[g];
+  const int Kp = G.x, Q = G.y, beta = G.z, Np = G.w;
   const __nv_bfloat16* Ag = A + gaoff[g];
   const int* fg = fexp + gfoff[g];
   if (warp == 0) {
@@ -353,7 +485,7 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
     for (int i = tid; i < kNC * SU * 4; i += kThr) {
       const int r = i >> 5, t = r % SU, j = (r / SU) * 8 + (i & 7), q = (i >> 3) & 3;
       cp_async16(reinterpret_cast<char*>(as + t * AT) + (j >> 3) * SBO + q * LBO + (j & 7) * 16,
-                 Ag + ((size_t)t * Kp + (n0 + j)) * Kp + k0 + q * 8, 16);
+                 Ag + ((size_t)t * Np + (n0 + j)) * Kp + k0 + q * 8, 16);
     }
   };
   for (int c = 0; c < NS - 1; ++c) {  // prologue: NS - 1 groups (empty past the end)
@@ -555,6 +687,15 @@ qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
   }
   QBX_CUDA_TRY(f->tc_lvl.alloc(nl));
   QBX_CUDA_TRY(cudaMemcpy(f->tc_lvl.ptr, lv.data(), nl * sizeof(int4), cudaMemcpyHostToDevice));
+  {  // per-group parameters of the tile product: (K, Q, beta, Np) of the level
+    std::vector<int4> gp(ng);
+    for (int g = 0; g < ng; ++g) {
+      const int l = g / 49;
+      gp[g] = make_int4(lv[l].w, 2 * f->h_pb[l] + 1, lv[l].y, lv[l].w);
+    }
+    QBX_CUDA_TRY(f->tc_gp.alloc(ng));
+    QBX_CUDA_TRY(cudaMemcpy(f->tc_gp.ptr, gp.data(), ng * sizeof(int4), cudaMemcpyHostToDevice));
+  }
   // groups with rows on tensor-core levels
   std::vector<int> groups;
   std::vector<long long> aoff(ng, 0), foff(ng, 0), g_aoff, g_foff;
@@ -648,6 +789,170 @@ qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
   return QBX_OK;
 }
 
+#define TRY_TC(x)               \
+  do {                          \
+    const qbx_status s_ = (x);  \
+    if (s_ != QBX_OK) return s_; \
+  } while (0)
+
+namespace {
+template <typename T>
+qbx_status upload(DevBuf<T>& d, const std::vector<T>& v) {
+  QBX_CUDA_TRY(d.alloc(std::max<size_t>(1, v.size())));
+  if (!v.empty())
+    QBX_CUDA_TRY(cudaMemcpy(d.ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return QBX_OK;
+}
+}  // namespace
+
+// Plan of the FP64 M2M and L2L on the tensor cores: for every parent level l
+// whose contraction width K (2 Q of the child level for M2M, of level l for
+// L2L, padded to 64) admits an exact split, the matrix slices of the four
+// quadrant operators, the rows (one per child: quadrant-major, parents in
+// level order), the source boxes and the work items. Levels without one keep
+// the CUDA-core kernels; so do all levels with m2l_engine == 2 or
+// QBX_M2L_TENSOR=0.
+qbx_status tc_mml_plan_build(qbx_handle* h, FmmPlan* f) {
+  const int nl = f->n_levels;
+  f->tc_m2m.clear();
+  f->tc_l2l.clear();
+  f->tc_m2m.resize(nl);
+  f->tc_l2l.resize(nl);
+  {
+    const char* env = getenv("QBX_M2L_TENSOR");
+    if ((env && env[0] == '0') || h->m2l_engine == 2) return QBX_OK;
+  }
+  std::vector<int> child((size_t)4 * f->n_boxes), nonleaf(std::max(1, f->nonleaf_off[nl]));
+  QBX_CUDA_TRY(cudaMemcpy(child.data(), f->box.child.ptr, child.size() * sizeof(int),
+                          cudaMemcpyDeviceToHost));
+  if (f->nonleaf_off[nl] > 0)
+    QBX_CUDA_TRY(cudaMemcpy(nonleaf.data(), f->nonleaf.ptr, f->nonleaf_off[nl] * sizeof(int),
+                            cudaMemcpyDeviceToHost));
+  size_t ymax = 1;
+  for (int kind = 0; kind < 2; ++kind) {
+    for (int l = 2; l + 1 < nl; ++l) {
+      // the level's parents, in the order of the device list (the reduce
+      // kernel walks that list)
+      const std::vector<int> par(nonleaf.begin() + f->nonleaf_off[l],
+                                 nonleaf.begin() + f->nonleaf_off[l + 1]);
+      if (par.empty()) continue;
+      TcLevelOp& op = kind == 0 ? f->tc_m2m[l] : f->tc_l2l[l];
+      const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
+      const int qin = kind == 0 ? 2 * pc + 1 : 2 * pp + 1;
+      const int qout = kind == 0 ? 2 * pp + 1 : 2 * pc + 1;
+      const int K = (2 * qin + kPad - 1) / kPad * kPad;
+      const int Np = (2 * qout + kPad - 1) / kPad * kPad;
+      const int2 bs = tc_params(K);
+      if (bs.x == 0) continue;
+      op.use = true;
+      op.beta = bs.x;
+      op.S = bs.y;
+      op.K = K;
+      op.Np = Np;
+      op.Q = qout;
+      op.n_par = (int)par.size();
+      // rows: quadrant-major, parents in level order; sources
+      std::vector<int> rowsrc, rowdst, prow((size_t)4 * par.size(), -1), src;
+      std::vector<int64_t> gcount(5, 0);
+      for (int c = 0; c < 4; ++c) {
+        gcount[c] = (int64_t)rowdst.size();
+        for (size_t i = 0; i < par.size(); ++i) {
+          const int d = child[4 * (size_t)par[i] + c];
+          if (d < 0) continue;
+          prow[4 * i + c] = (int)rowdst.size();
+          if (kind == 0) {  // M2M: the row's source is the child
+            rowsrc.push_back((int)src.size());
+            src.push_back(d);
+            rowdst.push_back(par[i]);
+          } else {          // L2L: the parent (one source per parent)
+            rowsrc.push_back((int)i);
+            rowdst.push_back(d);
+          }
+        }
+      }
+      gcount[4] = (int64_t)rowdst.size();
+      if (kind == 1) src = par;
+      op.n_rows = (int)rowdst.size();
+      op.n_src = (int)src.size();
+      ymax = std::max(ymax, (size_t)op.n_rows * qout);
+      std::vector<int4> gp(4, make_int4(K, qout, bs.x, Np));
+      std::vector<long long> gaoff(4), gfoff(4), xoff(src.size()), yoff(rowdst.size());
+      for (int c = 0; c < 4; ++c) {
+        gaoff[c] = (long long)c * bs.y * Np * K;
+        gfoff[c] = (long long)c * Np;
+      }
+      for (size_t i = 0; i < src.size(); ++i) xoff[i] = (long long)i * bs.y * K;
+      for (size_t r = 0; r < rowdst.size(); ++r) yoff[r] = (long long)r * qout;
+      std::vector<int4> items;
+      for (int c = 0; c < 4; ++c)
+        for (int64_t r = gcount[c]; r < gcount[c + 1]; r += kRows)
+          for (int n0 = 0; n0 < 2 * qout; n0 += kNC)
+            items.push_back(make_int4((int)r, (int)std::min<int64_t>(kRows, gcount[c + 1] - r), n0, c));
+      op.n_items = (int)items.size();
+      TRY_TC(upload(op.gp, gp));
+      TRY_TC(upload(op.items, items));
+      TRY_TC(upload(op.gaoff, gaoff));
+      TRY_TC(upload(op.gfoff, gfoff));
+      TRY_TC(upload(op.xoff, xoff));
+      TRY_TC(upload(op.yoff, yoff));
+      TRY_TC(upload(op.src, src));
+      TRY_TC(upload(op.rowsrc, rowsrc));
+      TRY_TC(upload(op.rowdst, rowdst));
+      TRY_TC(upload(op.prow, prow));
+      QBX_CUDA_TRY(op.A.alloc((size_t)4 * bs.y * Np * K));
+      QBX_CUDA_TRY(op.fexp.alloc((size_t)4 * Np));
+      QBX_CUDA_TRY(op.X.alloc(std::max<size_t>(1, src.size() * (size_t)bs.y * K)));
+      QBX_CUDA_TRY(op.xexp.alloc(std::max<size_t>(1, src.size())));
+      tc_mml_matrix_kernel<<<dim3(4, Np), kThr>>>(
+          kind, l, pp, pc, f->pb_max, kind == 0 ? f->t_m2m.ptr : f->t_l2l.ptr, f->lsig.ptr, K, Np,
+          bs.x, bs.y, reinterpret_cast<__nv_bfloat16*>(op.A.ptr), op.fexp.ptr);
+      QBX_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  QBX_CUDA_TRY(f->tc_mml_y.alloc(ymax));
+  QBX_CUDA_TRY(cudaDeviceSynchronize());
+  return QBX_OK;
+}
+
+qbx_status launch_mml_tc(qbx_handle* h, FmmPlan* f, int kind, int l, bool* done, cudaStream_t s) {
+  *done = false;
+  if (l >= (int)f->tc_m2m.size()) return QBX_OK;
+  TcLevelOp& op = kind == 0 ? f->tc_m2m[l] : f->tc_l2l[l];
+  if (!op.use) return QBX_OK;
+  const int pp = f->h_pb[l], pc = f->h_pb[l + 1];
+  if (op.n_src > 0) {
+    tc_mml_vec_kernel<<<op.n_src, kThr, 0, s>>>(
+        kind, op.src.ptr, kind == 0 ? f->mpole.ptr : f->local.ptr, kind == 0 ? l + 1 : l,
+        kind == 0 ? pc : pp, op.K, op.beta, op.S, f->conv.ptr, f->pb_max, f->eoff.ptr,
+        op.xoff.ptr, reinterpret_cast<__nv_bfloat16*>(op.X.ptr), op.xexp.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+  }
+#define TC_MML(S_)                                                                              \
+  m2l_tc_kernel<S_, S_><<<op.n_items, kThr, tc_smem_bytes<S_>(), s>>>(                           \
+      op.items.ptr, op.gp.ptr, op.gaoff.ptr, op.gfoff.ptr,                                      \
+      reinterpret_cast<const __nv_bfloat16*>(op.A.ptr), op.fexp.ptr, op.rowsrc.ptr, op.xoff.ptr, \
+      op.xexp.ptr, reinterpret_cast<const __nv_bfloat16*>(op.X.ptr), op.yoff.ptr,               \
+      f->tc_mml_y.ptr, f->err.ptr + 1)
+  if (op.n_items > 0) {
+    if (op.S == 6) TC_MML(6);
+    else if (op.S == 7) TC_MML(7);
+    else TC_MML(8);
+    QBX_CUDA_TRY(cudaGetLastError());
+  }
+#undef TC_MML
+  if (kind == 0)
+    tc_m2m_reduce_kernel<<<op.n_par, kThr, 0, s>>>(f->nonleaf.ptr + f->nonleaf_off[l], op.prow.ptr,
+                                                   pp, l, f->pb_max, f->conv.ptr, f->tc_mml_y.ptr,
+                                                   f->eoff.ptr, f->mpole.ptr);
+  else if (op.n_rows > 0)
+    tc_l2l_apply_kernel<<<op.n_rows, kThr, 0, s>>>(op.rowdst.ptr, pc, l + 1, f->pb_max, f->conv.ptr,
+                                                   f->tc_mml_y.ptr, f->eoff.ptr, f->local.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  h->launches += 3;
+  *done = true;
+  return QBX_OK;
+}
+
 qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, bool mixed, cudaStream_t s) {
   if (f->n_vbox == 0) return QBX_OK;
   if (f->n_tc_src > 0) {
@@ -662,7 +967,7 @@ qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, bool mixed, cudaStream_t s) 
 #define TC_LAUNCH(SD, SU)                                                                      \
   if (f->n_tc_items[SD - 6] > 0) {                                                              \
     m2l_tc_kernel<SD, SU><<<f->n_tc_items[SD - 6], kThr, tc_smem_bytes<SU>(), s>>>(             \
-        f->tc_items[SD - 6].ptr, f->tc_lvl.ptr, f->lpb.ptr, f->tc_gaoff.ptr, f->tc_gfoff.ptr,   \
+        f->tc_items[SD - 6].ptr, f->tc_gp.ptr, f->tc_gaoff.ptr, f->tc_gfoff.ptr,               \
         reinterpret_cast<const __nv_bfloat16*>(f->tc_A.ptr), f->tc_fexp.ptr, f->tc_rowsrc.ptr,   \
         f->tc_xoff.ptr, f->tc_xexp.ptr, reinterpret_cast<const __nv_bfloat16*>(f->tc_X.ptr),     \
         f->m2l_yoff.ptr, f->m2l_y64.ptr, f->err.ptr + 1);                                      \

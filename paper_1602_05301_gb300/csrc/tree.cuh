@@ -27,6 +27,19 @@ struct CentreSet {
   int wp_pbmax = 0;  // largest box order among the M2QBXL pairs' boxes
 };
 
+// One parent level of the FP64 M2M or L2L on the tensor cores: four groups
+// (the child quadrants), the bf16 matrix slices of their sigma-normalised
+// operators, the source vectors' slices, and the rows (one per child).
+struct TcLevelOp {
+  bool use = false;
+  int S = 0, beta = 0, K = 0, Np = 0, Q = 0;  // slices, digit bits, input width, output rows, outputs
+  int n_rows = 0, n_src = 0, n_items = 0, n_par = 0;
+  DevBuf<int4> gp, items;
+  DevBuf<long long> gaoff, gfoff, xoff, yoff;
+  DevBuf<uint16_t> A, X;
+  DevBuf<int> fexp, xexp, src, rowsrc, rowdst, prow;
+};
+
 struct FmmPlan {
   // concurrency of the near-field stages (see fmm_eval)
   cudaStream_t near_stream = nullptr;
@@ -52,7 +65,6 @@ struct FmmPlan {
   DevBuf<int> V_cls;                    // offset class of every V entry (0..48)
   DevBuf<int> leaves;                   // leaf box ids
   int n_leaves = 0;
-  std::vector<std::vector<int>> h_nonleaf_by_level;  // parents per level (host copy of ids)
   DevBuf<int> nonleaf;                  // all non-leaf boxes ordered by level
   std::vector<int> nonleaf_off;         // [n_levels + 1] offsets into nonleaf
   DevBuf<int> xbox;                     // boxes with non-empty X list
@@ -162,6 +174,9 @@ struct FmmPlan {
   int n_m2l_items64_rest = 0;
   std::vector<int4> h_tc_lvl;           // per level (use, beta, S, padded 2Q)
   DevBuf<int4> tc_lvl;
+  DevBuf<int4> tc_gp;                   // per group (K, Q, beta, Np) of the tile product
+  std::vector<TcLevelOp> tc_m2m, tc_l2l;  // per parent level (FP64 path)
+  DevBuf<cd> tc_mml_y;                  // their result rows (one level at a time)
   bool tc_any = false;
   DevBuf<uint16_t> tc_A;                // bf16 matrix slices [S][Kp][Kp] per group
   DevBuf<int> tc_fexp;                  // row exponents [Kp] per group
@@ -186,6 +201,10 @@ qbx_status launch_m2l_f64_gemm_rest(qbx_handle* h, FmmPlan* f, cudaStream_t s);
 // m2l_tc.cu
 qbx_status configure_tc_kernels(int smem_optin);
 qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f);
+qbx_status tc_mml_plan_build(qbx_handle* h, FmmPlan* f);
+// FP64 M2M (kind 0) or L2L (kind 1) of parent level l on the tensor cores;
+// *done = false when the level stays on the CUDA-core kernel
+qbx_status launch_mml_tc(qbx_handle* h, FmmPlan* f, int kind, int l, bool* done, cudaStream_t s);
 qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, bool mixed, cudaStream_t s);
 // shared memory of one M2M / L2L tile-GEMM block at box order pb
 size_t gemm_smem_bytes(int pb);
