@@ -144,6 +144,29 @@ def kernel_sha256(spec):
     return h.hexdigest()
 
 
+def known_pipe(stage, workload, precision):
+    """FP64-pipe utilisation of a stage's kernel (fraction of the FP64
+    instruction rate) from a committed ncu summary ("bench-pipe:" lines, keyed
+    like the traffic lines); None when absent or stale."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
+        for line in open(path):
+            if not line.startswith("bench-pipe:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if (kv.get("stage"), kv.get("workload"), kv.get("precision")) != (stage, workload,
+                                                                              precision):
+                continue
+            try:
+                sha = kernel_sha256(kv.get("functions", ""))
+            except (OSError, ValueError):
+                return None
+            if sha is None or sha != kv.get("functions_sha256"):
+                return None
+            return float(kv["fp64_pipe"]), os.path.relpath(path, ROOT)
+    return None
+
+
 def known_traffic(stage, workload, precision):
     """DRAM bytes per launch of a stage's kernels, from a committed ncu summary
     under profiles/ ("bench-traffic:" lines: stage, workload, precision, bytes,
@@ -488,6 +511,12 @@ def run_ours(args, w, ws, rank, local):
         kt = known_traffic(dom, w["name"], args.precision)
         if kt:
             roof["traffic"], roof["traffic_source"] = kt
+        # the flop model is a lower bound (logarithms, square roots and FP32
+        # conversions are charged nothing); ncu's FP64-pipe utilisation of the
+        # same kernel is the measured bound
+        kp = known_pipe(dom, w["name"], args.precision)
+        if kp:
+            roof["fp64_pipe_utilisation_ncu"], roof["fp64_pipe_source"] = kp
         # the same fraction for every timed stage (flop model over its event time)
         roof["frac_by_stage"] = {
             k: round(1e3 * (flops[k][0] / (FP64_PEAK_TFLOPS * 1e12) +
