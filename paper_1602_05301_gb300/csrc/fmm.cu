@@ -596,8 +596,19 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
   cd acc;
   double norm;
   if (x < 1e-8) {
-    acc = g[pb];  // only J_0 survives
+    // J_m(x) = (x/2)^m / m! to relative O(x^2); the terms vanish after a few
+    // orders (a target a rounding distance from the leaf centre still needs
+    // the m = 1 term: it is O(x) of the result, not O(x^2))
+    acc = mk(0.0, 0.0);
     norm = 1.0;
+    double t = 1.0;
+    cd e = mk(1.0, 0.0);  // e^{i m th}
+    for (int mm = 0; mm <= pb && t != 0.0; ++mm) {
+      acc = cadd(acc, cscale(cmul(g[pb + mm], cconj(e)), t));
+      if (mm > 0) acc = cadd(acc, cscale(cmul(g[pb - mm], e), (mm & 1) ? -t : t));
+      t *= 0.5 * x / (double)(mm + 1);
+      e = cmul(e, e1);
+    }
   } else {
     const double inv = 2.0 / x;
     const int N = miller_start(pb, x);
