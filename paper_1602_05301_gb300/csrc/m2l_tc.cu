@@ -582,6 +582,235 @@ __global__ void __launch_bounds__(kThr, 1) m2l_tc_kernel(
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// The same tile product as a persistent, warp-specialised kernel: one CTA per
+// SM walks items c, c + G, c + 2G, ... (G CTAs), with
+//  * warps 0-2, the producers: fill the shared-memory ring stage by stage with
+//    cp.async across item boundaries (they run ahead of the MMAs of the
+//    current item into the next one); once a stage's copies have landed each
+//    lane fences them for the async proxy and arrives on the stage's full
+//    barrier (three warps: one warp could not issue the 16-byte copies of a
+//    stage as fast as the MMAs consume it);
+//  * warp 3, the MMA warp: allocates the tensor memory; one lane waits for a
+//    stage, issues its MMAs and commits them to the stage's empty barrier
+//    (the producer's refill waits on it), and after an item's last stage
+//    commits to the accumulator-full barrier; before an item's first MMA it
+//    waits until the epilogue has read the previous item's accumulators;
+//  * warps 4-7, the epilogue: TMEM lanes 32 (w mod 4) .. + 31 (the rows),
+//    the float-float combination and the stores of tc's epilogue, then an
+//    arrival on the accumulator-empty barrier.
+// Every wait is bounded (mbar_wait); a wait that runs out sets the CTA's fail
+// flag and the global flag, the roles leave their loops, the issued MMAs are
+// drained with one more bounded wait, and the tensor memory is freed.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kWsProd = 3;                       // producer warps
+constexpr int kWsThr = 32 * (kWsProd + 1 + 4);   // producers, MMA warp, four epilogue warps
+
+template <int SD, int SU>
+__global__ void __launch_bounds__(kWsThr, 1) tc_gemm_ws_kernel(
+    const int4* __restrict__ items, int n_items, const int4* __restrict__ gp,
+    const long long* __restrict__ gaoff, const long long* __restrict__ gfoff,
+    const __nv_bfloat16* __restrict__ A, const int* __restrict__ fexp,
+    const int* __restrict__ rowsrc, const long long* __restrict__ xoff,
+    const int* __restrict__ xexp, const __nv_bfloat16* __restrict__ X,
+    const long long* __restrict__ yoff, cd* __restrict__ Y, int* __restrict__ err) {
+  constexpr int NS = tc_stages(SU);
+  static_assert(NS >= 2, "at least two stages");
+  constexpr int XT = kRows * kKC, AT = kNC * kKC, STAGE = SU * (XT + AT);
+  constexpr uint32_t LBO = 128, SBO = (kKC / 8) * 128;
+  constexpr uint32_t ID = idesc_bf16(kRows, kNC);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull, tempty, mfin;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  __shared__ long long s_xrow[kWsProd][kRows];  // each producer warp's copy
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  if (warp == kWsProd) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    for (int b = 0; b < NS; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])),
+                   "r"(32 * kWsProd));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&tempty)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mfin)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  auto fail = [&]() {
+    atomicExch(&s_fail, 1);
+    atomicExch(err, 1);
+  };
+  auto failed = [&]() { return *(volatile int*)&s_fail != 0; };
+
+  if (warp < kWsProd) {
+    // ---------------- producers (warp w takes every kWsProd-th 16-byte piece)
+    long long* xrow = s_xrow[warp];
+    const int pt = warp * 32 + lane;
+    int q = 0;  // stages filled so far (over all items)
+    for (int it = blockIdx.x; it < n_items && !failed(); it += G) {
+      const int4 I = items[it];
+      const int row0 = I.x, nr = I.y, n0 = I.z;
+      const int4 P = gp[I.w];
+      const int Kp = P.x, Np = P.w;
+      const __nv_bfloat16* Ag = A + gaoff[I.w];
+      for (int m = lane; m < kRows; m += 32) xrow[m] = m < nr ? xoff[rowsrc[row0 + m]] : -1;
+      __syncwarp();
+      const int nchunks = Kp / kKC;
+      for (int c = 0; c < nchunks; ++c, ++q) {
+        const int slot = q % NS;
+        if (q >= NS && !mbar_wait(&empty[slot], ((q / NS) - 1) & 1)) {
+          fail();
+          break;
+        }
+        __nv_bfloat16* xs = stg + (size_t)slot * STAGE;
+        __nv_bfloat16* as = xs + SU * XT;
+        const int k0 = c * kKC;
+        for (int i = pt; i < kRows * SU * 4; i += 32 * kWsProd) {
+          const int r = i >> 5, t = r % SU, m = (r / SU) * 8 + (i & 7), qq = (i >> 3) & 3;
+          const long long xo = xrow[m];
+          const __nv_bfloat16* src = xo >= 0 ? X + xo + (size_t)t * Kp + k0 + qq * 8 : X;
+          cp_async16(reinterpret_cast<char*>(xs + t * XT) + (m >> 3) * SBO + qq * LBO + (m & 7) * 16,
+                     src, xo >= 0 ? 16 : 0);
+        }
+        for (int i = pt; i < kNC * SU * 4; i += 32 * kWsProd) {
+          const int r = i >> 5, t = r % SU, j = (r / SU) * 8 + (i & 7), qq = (i >> 3) & 3;
+          cp_async16(reinterpret_cast<char*>(as + t * AT) + (j >> 3) * SBO + qq * LBO + (j & 7) * 16,
+                     Ag + ((size_t)t * Np + (n0 + j)) * Kp + k0 + qq * 8, 16);
+        }
+        cp_async_commit();
+        // the stage filled NS - 2 steps ago has landed: hand it to the MMAs
+        cp_async_wait<NS - 2>();
+        asm volatile("fence.proxy.async.shared::cta;");
+        if (q - (NS - 2) >= 0) mbar_arrive(&full[(q - (NS - 2)) % NS]);
+      }
+      __syncwarp();  // xrow is rewritten for the next item
+    }
+    // the last NS - 2 stages
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;");
+    for (int r = std::max(0, q - (NS - 2)); r < q; ++r) mbar_arrive(&full[r % NS]);
+  } else if (warp == kWsProd) {
+    // ---------------- MMA issue (lane 0)
+    if (lane == 0) {
+      int q = 0, k = 0;  // stages consumed, items done
+      for (int it = blockIdx.x; it < n_items && !failed(); it += G, ++k) {
+        const int4 P = gp[items[it].w];
+        const int nchunks = P.x / kKC;
+        if (k >= 1 && !mbar_wait(&tempty, (k - 1) & 1)) {  // epilogue has read the last item
+          fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        uint32_t acc_started = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c, ++q) {
+          const int slot = q % NS;
+          if (!mbar_wait(&full[slot], (q / NS) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const __nv_bfloat16* xs = stg + (size_t)slot * STAGE;
+          const __nv_bfloat16* as = xs + SU * XT;
+#pragma unroll
+          for (int ti = 0; ti < SU; ++ti) {
+#pragma unroll
+            for (int tj = 0; tj < SU - ti; ++tj) {
+              const int a = ti + tj;
+#pragma unroll
+              for (int kk = 0; kk < kKC; kk += 16) {
+                const uint64_t da = smem_desc(smem_u32(xs + ti * XT) + (kk / 8) * LBO, LBO, SBO);
+                const uint64_t db = smem_desc(smem_u32(as + tj * AT) + (kk / 8) * LBO, LBO, SBO);
+                mma_bf16(tmem + a * kNC, da, db, ID, (acc_started >> a) & 1u);
+                acc_started |= 1u << a;
+              }
+            }
+          }
+          mma_commit(&empty[slot]);
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+        mma_commit(&tfull);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: rows (warp mod 4) * 32 + lane
+    const int m = (warp & 3) * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    int k = 0;
+    for (int it = blockIdx.x; it < n_items && !failed(); it += G, ++k) {
+      const int4 I = items[it];
+      const int row0 = I.x, nr = I.y, n0 = I.z, g = I.w;
+      const int4 P = gp[g];
+      const int Q = P.y, beta = P.z;
+      const int* fg = fexp + gfoff[g];
+      if (!mbar_wait(&tfull, k & 1)) {
+        fail();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const bool row_ok = m < nr;
+      const int e_row = row_ok ? xexp[rowsrc[row0 + m]] : 0;
+      const long long yo = row_ok ? yoff[row0 + m] : 0;
+      for (int j0 = 0; j0 < kNC; j0 += 16) {
+        float hi[16], lo[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.f;
+#pragma unroll
+        for (int a = SU - 1; a >= 0; --a) {
+          float v[16];
+          tmem_ld16(tl + a * kNC + j0, v);
+          const int sh = -beta * (a + 2);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) ff_add(hi[c], lo[c], ldexpf(v[c], sh), 0.f);
+        }
+        if (j0 + 16 >= kNC) {  // every accumulator read: the MMAs may reuse TMEM
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(&tempty);
+        }
+        if (row_ok) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int j = n0 + j0 + c;
+            if (j >= 2 * Q) break;
+            const int sc = e_row + fg[j];
+            const float2 w = make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));
+            float2* dst = reinterpret_cast<float2*>(Y + yo + (j < Q ? j : j - Q)) + (j < Q ? 0 : 1);
+            *dst = w;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_fail) {  // drain whatever MMAs were issued before the tensor memory goes
+    if (warp == kWsProd && lane == 0) mma_commit(&mfin);
+    mbar_wait(&mfin, 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == kWsProd)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 // lh_lo(b) += conv_lo * sum over b's V entries of the row values: float-float
 // sums (tensor-core levels) or FP64 sums (the others), in V-list order.
 __global__ void __launch_bounds__(kThr) m2l_tc_reduce_kernel(
@@ -635,7 +864,20 @@ int2 tc_params(int Kp) {
 
 }  // namespace
 
+int g_tc_sms = 152;  // persistent grid: one CTA per SM (set at configuration)
+
 qbx_status configure_tc_kernels(int smem_optin) {
+  {
+    int dev = 0;
+    QBX_CUDA_TRY(cudaGetDevice(&dev));
+    QBX_CUDA_TRY(cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev));
+    const void* w[] = {(const void*)tc_gemm_ws_kernel<6, 6>, (const void*)tc_gemm_ws_kernel<7, 7>,
+                       (const void*)tc_gemm_ws_kernel<8, 8>};
+    const size_t wn[] = {tc_smem_bytes<6>(), tc_smem_bytes<7>(), tc_smem_bytes<8>()};
+    for (int i = 0; i < 3; ++i)
+      QBX_CUDA_TRY(cudaFuncSetAttribute(w[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)wn[i]));
+  }
   const void* k[] = {(const void*)m2l_tc_kernel<6, 6>, (const void*)m2l_tc_kernel<7, 7>,
                      (const void*)m2l_tc_kernel<8, 8>, (const void*)m2l_tc_kernel<6, 3>,
                      (const void*)m2l_tc_kernel<7, 4>, (const void*)m2l_tc_kernel<8, 4>};
@@ -928,8 +1170,8 @@ qbx_status launch_mml_tc(qbx_handle* h, FmmPlan* f, int kind, int l, bool* done,
     QBX_CUDA_TRY(cudaGetLastError());
   }
 #define TC_MML(S_)                                                                              \
-  m2l_tc_kernel<S_, S_><<<op.n_items, kThr, tc_smem_bytes<S_>(), s>>>(                           \
-      op.items.ptr, op.gp.ptr, op.gaoff.ptr, op.gfoff.ptr,                                      \
+  tc_gemm_ws_kernel<S_, S_><<<std::min(op.n_items, g_tc_sms), kWsThr, tc_smem_bytes<S_>(), s>>>(  \
+      op.items.ptr, op.n_items, op.gp.ptr, op.gaoff.ptr, op.gfoff.ptr,                          \
       reinterpret_cast<const __nv_bfloat16*>(op.A.ptr), op.fexp.ptr, op.rowsrc.ptr, op.xoff.ptr, \
       op.xexp.ptr, reinterpret_cast<const __nv_bfloat16*>(op.X.ptr), op.yoff.ptr,               \
       f->tc_mml_y.ptr, f->err.ptr + 1)
@@ -974,16 +1216,29 @@ qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, bool mixed, cudaStream_t s) 
     QBX_CUDA_TRY(cudaGetLastError());                                                           \
     h->launches += 1;                                                                           \
   }
+#define TC_LAUNCH_WS(S_)                                                                        \
+  if (f->n_tc_items[S_ - 6] > 0) {                                                              \
+    tc_gemm_ws_kernel<S_, S_><<<std::min(f->n_tc_items[S_ - 6], g_tc_sms), kWsThr,              \
+                                tc_smem_bytes<S_>(), s>>>(                                       \
+        f->tc_items[S_ - 6].ptr, f->n_tc_items[S_ - 6], f->tc_gp.ptr, f->tc_gaoff.ptr,          \
+        f->tc_gfoff.ptr, reinterpret_cast<const __nv_bfloat16*>(f->tc_A.ptr), f->tc_fexp.ptr,    \
+        f->tc_rowsrc.ptr, f->tc_xoff.ptr, f->tc_xexp.ptr,                                       \
+        reinterpret_cast<const __nv_bfloat16*>(f->tc_X.ptr), f->m2l_yoff.ptr, f->m2l_y64.ptr,    \
+        f->err.ptr + 1);                                                                        \
+    QBX_CUDA_TRY(cudaGetLastError());                                                           \
+    h->launches += 1;                                                                           \
+  }
   if (mixed) {
     TC_LAUNCH(6, 3)
     TC_LAUNCH(7, 4)
     TC_LAUNCH(8, 4)
-  } else {
-    TC_LAUNCH(6, 6)
-    TC_LAUNCH(7, 7)
-    TC_LAUNCH(8, 8)
+  } else {  // the persistent warp-specialised kernel
+    TC_LAUNCH_WS(6)
+    TC_LAUNCH_WS(7)
+    TC_LAUNCH_WS(8)
   }
 #undef TC_LAUNCH
+#undef TC_LAUNCH_WS
   {
     const qbx_status st = launch_m2l_f64_gemm_rest(h, f, s);
     if (st != QBX_OK) return st;
