@@ -145,8 +145,12 @@ def test_batch256_against_oracle(qbxmod, batch256, oracle):
             got64.append(u64[noff[c] + t])
             got32.append(u32[noff[c] + t])
             ref.append(u_ref)
+            # per curve, the FMM's own truncation at the batch's p_fmm = 20: up to
+            # 1.4e-10 (curve 43, k = 30.9, leaves of n_max <= 64; 9.6e-12 at
+            # p_fmm = 25, 1.1e-12 at 30), so the per-curve bound is 1e-9 and the
+            # 1e-10 bound applies to the 16 curves together
             check("batch-256 curve %d (n=%d, k=%.1f) fp64 vs oracle" % (c, n, g.k[c]),
-                  got64[-1], u_ref, TOL64)
+                  got64[-1], u_ref, 1e-9)
     check("batch-256, 16 curves, fp64 vs oracle", np.concatenate(got64), np.concatenate(ref),
           TOL64)
     check("batch-256, 16 curves, mixed vs oracle", np.concatenate(got32), np.concatenate(ref),
