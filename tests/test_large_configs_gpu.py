@@ -37,10 +37,10 @@ def rel_max(a, b):
     return float(np.max(np.abs(np.ravel(a - b))) / np.max(np.abs(np.ravel(b))))
 
 
-def check(name, got, ref, tol):
+def check(name, got, ref, tol, tol_max=None):
     e2, em = rel_l2(got, ref), rel_max(got, ref)
     print("%s: rel l2 %.3e, max-norm %.3e" % (name, e2, em))
-    assert e2 < tol and em < tol, (name, e2, em)
+    assert e2 < tol and em < (tol if tol_max is None else tol_max), (name, e2, em)
 
 
 @pytest.fixture(scope="module")
@@ -146,12 +146,12 @@ def test_batch256_against_oracle(qbxmod, batch256, oracle):
             got32.append(u32[noff[c] + t])
             ref.append(u_ref)
             # per curve, the FMM's own truncation at the batch's p_fmm = 20: up to
-            # 1.4e-10 (curve 43, k = 30.9, leaves of n_max <= 64; 9.6e-12 at
-            # p_fmm = 25, 1.1e-12 at 30), so the per-curve bound is 1e-9 and the
-            # 1e-10 bound applies to the 16 curves together
+            # 1.4e-10 in l2 and 4.7e-10 element-wise (curve 43, k = 30.9, leaves of
+            # n_max <= 64; 9.6e-12 at p_fmm = 25, 1.1e-12 at 30), so the bound is
+            # 1e-9 per curve and element-wise, 1e-10 in l2 over the 16 curves
             check("batch-256 curve %d (n=%d, k=%.1f) fp64 vs oracle" % (c, n, g.k[c]),
                   got64[-1], u_ref, 1e-9)
     check("batch-256, 16 curves, fp64 vs oracle", np.concatenate(got64), np.concatenate(ref),
-          TOL64)
+          TOL64, tol_max=1e-9)
     check("batch-256, 16 curves, mixed vs oracle", np.concatenate(got32), np.concatenate(ref),
           TOL32)
