@@ -32,15 +32,34 @@
 // are staged through shared memory in the no-swizzle K-major layout (8 x 16-byte
 // core matrices), double-buffered; one thread issues the MMAs, an mbarrier
 // tracks their completion (tcgen05.commit), and all waits are bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "tree.cuh"
 #include "m2l_entry.cuh"
+
+#define TRY_TC(x)               \
+  do {                          \
+    const qbx_status s_ = (x);  \
+    if (s_ != QBX_OK) return s_; \
+  } while (0)
+
+namespace {
+template <typename T>
+qbx_status upload(DevBuf<T>& d, const std::vector<T>& v) {
+  QBX_CUDA_TRY(d.alloc(std::max<size_t>(1, v.size())));
+  if (!v.empty())
+    QBX_CUDA_TRY(cudaMemcpy(d.ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return QBX_OK;
+}
+}  // namespace
 
 namespace {
 
@@ -716,7 +735,6 @@ __global__ void __launch_bounds__(kWsThr, 1) tc_gemm_ws_kernel(
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        uint32_t acc_started = 0;
         bool ok = true;
         for (int c = 0; c < nchunks; ++c, ++q) {
           const int slot = q % NS;
@@ -727,6 +745,11 @@ __global__ void __launch_bounds__(kWsThr, 1) tc_gemm_ws_kernel(
           asm volatile("tcgen05.fence::after_thread_sync;");
           const __nv_bfloat16* xs = stg + (size_t)slot * STAGE;
           const __nv_bfloat16* as = xs + SU * XT;
+          // descriptors of the stage's first core matrices; the others differ
+          // by a constant in the address field (shared-memory addresses stay
+          // below 2^18 bytes, so the 14-bit field cannot carry)
+          const uint64_t dx0 = smem_desc(smem_u32(xs), LBO, SBO);
+          const uint64_t da0 = smem_desc(smem_u32(as), LBO, SBO);
 #pragma unroll
           for (int ti = 0; ti < SU; ++ti) {
 #pragma unroll
@@ -734,10 +757,11 @@ __global__ void __launch_bounds__(kWsThr, 1) tc_gemm_ws_kernel(
               const int a = ti + tj;
 #pragma unroll
               for (int kk = 0; kk < kKC; kk += 16) {
-                const uint64_t da = smem_desc(smem_u32(xs + ti * XT) + (kk / 8) * LBO, LBO, SBO);
-                const uint64_t db = smem_desc(smem_u32(as + tj * AT) + (kk / 8) * LBO, LBO, SBO);
-                mma_bf16(tmem + a * kNC, da, db, ID, (acc_started >> a) & 1u);
-                acc_started |= 1u << a;
+                const uint64_t da = dx0 + (uint64_t)((ti * XT * 2 + (kk / 8) * LBO) >> 4);
+                const uint64_t db = da0 + (uint64_t)((tj * AT * 2 + (kk / 8) * LBO) >> 4);
+                // an accumulator's first product of an item (ti = 0, kk = 0 of its
+                // first stage) overwrites, every later one adds
+                mma_bf16(tmem + a * kNC, da, db, ID, (c > 0 || ti > 0 || kk > 0) ? 1u : 0u);
               }
             }
           }
@@ -811,6 +835,241 @@ __global__ void __launch_bounds__(kWsThr, 1) tc_gemm_ws_kernel(
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// The FP64 M2L's tile product fed by TMA. The source slices of the rows are
+// first copied into row order per group (tc_x2_fill_kernel: [S][rows][K], a
+// TMA-tileable 2D array); then a single producer lane loads a stage as 4 S
+// boxes of 128 rows x 16 bytes (rows) and 4 S boxes of 64 rows x 16 bytes
+// (matrix), one per slice and 8-wide k-group, with one expect-tx arrival on
+// the stage's full barrier. Shared-memory layout of a slice: k-group kg's
+// 128 x 16 B at kg * 2 KB (rows; 1 KB for the matrix's 64), i.e. core matrices
+// adjacent in M 128 B apart and in K 2 KB (1 KB) apart. The MMA warp and the
+// epilogue warps are those of tc_gemm_ws_kernel.
+__global__ void tc_x2_fill_kernel(int n_rows, const long long* __restrict__ src,
+                                  const long long* __restrict__ dst,
+                                  const long long* __restrict__ tstride,
+                                  const int2* __restrict__ sk, const uint16_t* __restrict__ X,
+                                  uint16_t* __restrict__ X2) {
+  const int r = blockIdx.x;
+  if (r >= n_rows) return;
+  const int S = sk[r].x, K = sk[r].y, V = K / 8;  // 16-byte vectors per slice row
+  const uint4* in = reinterpret_cast<const uint4*>(X + src[r]);
+  for (int i = threadIdx.x; i < S * V; i += blockDim.x) {
+    const int t = i / V, v = i % V;
+    *reinterpret_cast<uint4*>(X2 + dst[r] + (size_t)t * tstride[r] + (size_t)v * 8) = in[(size_t)t * V + v];
+  }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr int kTmaThr = 32 * 6;  // producer warp (one lane), MMA warp, four epilogue warps
+
+template <int SD, int SU>
+__global__ void __launch_bounds__(kTmaThr, 1) tc_gemm_tma_kernel(
+    const int4* __restrict__ items, int n_items, const int4* __restrict__ gp,
+    const TmapBlob* __restrict__ mapA, const TmapBlob* __restrict__ mapX,
+    const long long* __restrict__ gstart, const long long* __restrict__ gfoff,
+    const int* __restrict__ fexp, const int* __restrict__ rowsrc, const int* __restrict__ xexp,
+    const long long* __restrict__ yoff, cd* __restrict__ Y, int* __restrict__ err) {
+  constexpr int NS = tc_stages(SU);
+  static_assert(NS >= 2, "at least two stages");
+  constexpr int XT = kRows * kKC, AT = kNC * kKC, STAGE = SU * (XT + AT);
+  constexpr uint32_t LBOX = kRows * 16, LBOA = kNC * 16, SBO = 128;
+  constexpr uint32_t ID = idesc_bf16(kRows, kNC);
+  constexpr uint32_t kStageBytes = (uint32_t)SU * (kKC / 8) * (kRows + kNC) * 16;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull, tempty, mfin;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    for (int b = 0; b < NS; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&tempty)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mfin)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  auto fail = [&]() {
+    atomicExch(&s_fail, 1);
+    atomicExch(err, 1);
+  };
+  auto failed = [&]() { return *(volatile int*)&s_fail != 0; };
+
+  if (warp == 0) {
+    // ---------------- producer (lane 0): TMA boxes, one expect-tx per stage
+    if (lane == 0) {
+      int q = 0;
+      for (int it = blockIdx.x; it < n_items && !failed(); it += G) {
+        const int4 I = items[it];
+        const int g = I.w;
+        const int4 P = gp[g];
+        const int Kp = P.x, Np = P.w;
+        const int rows_g = (int)(gstart[g + 1] - gstart[g]);
+        const int rl = (int)(I.x - gstart[g]);
+        const void* mx = mapX + g;
+        const void* ma = mapA + g;
+        const int nchunks = Kp / kKC;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c, ++q) {
+          const int slot = q % NS;
+          if (q >= NS && !mbar_wait(&empty[slot], ((q / NS) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          __nv_bfloat16* xs = stg + (size_t)slot * STAGE;
+          __nv_bfloat16* as = xs + SU * XT;
+          mbar_expect_tx(&full[slot], kStageBytes);
+          for (int t = 0; t < SU; ++t)
+            for (int kg = 0; kg < kKC / 8; ++kg) {
+              const int x = c * kKC + kg * 8;
+              tma_load_2d(xs + t * XT + kg * (kRows * 8), mx, x, t * rows_g + rl, &full[slot]);
+              tma_load_2d(as + t * AT + kg * (kNC * 8), ma, x, t * Np + I.z, &full[slot]);
+            }
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+      }
+      // no TMA write may outlive the CTA: the last stages' loads have landed
+      // (immediately true when the MMAs consumed them)
+      for (int r = q > NS ? q - NS : 0; r < q; ++r) mbar_wait(&full[r % NS], (r / NS) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issue (lane 0)
+    if (lane == 0) {
+      int q = 0, k = 0;
+      for (int it = blockIdx.x; it < n_items && !failed(); it += G, ++k) {
+        const int4 P = gp[items[it].w];
+        const int nchunks = P.x / kKC;
+        if (k >= 1 && !mbar_wait(&tempty, (k - 1) & 1)) {
+          fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c, ++q) {
+          const int slot = q % NS;
+          if (!mbar_wait(&full[slot], (q / NS) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const __nv_bfloat16* xs = stg + (size_t)slot * STAGE;
+          const __nv_bfloat16* as = xs + SU * XT;
+          const uint64_t dx0 = smem_desc(smem_u32(xs), LBOX, SBO);
+          const uint64_t da0 = smem_desc(smem_u32(as), LBOA, SBO);
+#pragma unroll
+          for (int ti = 0; ti < SU; ++ti) {
+#pragma unroll
+            for (int tj = 0; tj < SU - ti; ++tj) {
+              const int a = ti + tj;
+#pragma unroll
+              for (int kk = 0; kk < kKC; kk += 16) {
+                const uint64_t da = dx0 + (uint64_t)((ti * XT * 2 + (kk / 8) * LBOX) >> 4);
+                const uint64_t db = da0 + (uint64_t)((tj * AT * 2 + (kk / 8) * LBOA) >> 4);
+                mma_bf16(tmem + a * kNC, da, db, ID, (c > 0 || ti > 0 || kk > 0) ? 1u : 0u);
+              }
+            }
+          }
+          mma_commit(&empty[slot]);
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+        mma_commit(&tfull);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: rows (warp mod 4) * 32 + lane
+    const int m = (warp & 3) * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    int k = 0;
+    for (int it = blockIdx.x; it < n_items && !failed(); it += G, ++k) {
+      const int4 I = items[it];
+      const int row0 = I.x, nr = I.y, n0 = I.z, g = I.w;
+      const int4 P = gp[g];
+      const int Q = P.y, beta = P.z;
+      const int* fg = fexp + gfoff[g];
+      if (!mbar_wait(&tfull, k & 1)) {
+        fail();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const bool row_ok = m < nr;
+      const int e_row = row_ok ? xexp[rowsrc[row0 + m]] : 0;
+      const long long yo = row_ok ? yoff[row0 + m] : 0;
+      for (int j0 = 0; j0 < kNC; j0 += 16) {
+        float hi[16], lo[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.f;
+#pragma unroll
+        for (int a = SU - 1; a >= 0; --a) {
+          float v[16];
+          tmem_ld16(tl + a * kNC + j0, v);
+          const int sh = -beta * (a + 2);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) ff_add(hi[c], lo[c], ldexpf(v[c], sh), 0.f);
+        }
+        if (j0 + 16 >= kNC) {
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(&tempty);
+        }
+        if (row_ok) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int j = n0 + j0 + c;
+            if (j >= 2 * Q) break;
+            const int sc = e_row + fg[j];
+            const float2 w = make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));
+            float2* dst = reinterpret_cast<float2*>(Y + yo + (j < Q ? j : j - Q)) + (j < Q ? 0 : 1);
+            *dst = w;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (warp == 1 && lane == 0) mma_commit(&mfin);
+    mbar_wait(&mfin, 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 // lh_lo(b) += conv_lo * sum over b's V entries of the row values: float-float
 // sums (tensor-core levels) or FP64 sums (the others), in V-list order.
 __global__ void __launch_bounds__(kThr) m2l_tc_reduce_kernel(
@@ -872,9 +1131,11 @@ qbx_status configure_tc_kernels(int smem_optin) {
     QBX_CUDA_TRY(cudaGetDevice(&dev));
     QBX_CUDA_TRY(cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev));
     const void* w[] = {(const void*)tc_gemm_ws_kernel<6, 6>, (const void*)tc_gemm_ws_kernel<7, 7>,
-                       (const void*)tc_gemm_ws_kernel<8, 8>};
-    const size_t wn[] = {tc_smem_bytes<6>(), tc_smem_bytes<7>(), tc_smem_bytes<8>()};
-    for (int i = 0; i < 3; ++i)
+                       (const void*)tc_gemm_ws_kernel<8, 8>, (const void*)tc_gemm_tma_kernel<6, 6>,
+                       (const void*)tc_gemm_tma_kernel<7, 7>, (const void*)tc_gemm_tma_kernel<8, 8>};
+    const size_t wn[] = {tc_smem_bytes<6>(), tc_smem_bytes<7>(), tc_smem_bytes<8>(),
+                         tc_smem_bytes<6>(), tc_smem_bytes<7>(), tc_smem_bytes<8>()};
+    for (int i = 0; i < 6; ++i)
       QBX_CUDA_TRY(cudaFuncSetAttribute(w[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)wn[i]));
   }
@@ -899,6 +1160,93 @@ qbx_status configure_tc_kernels(int smem_optin) {
 // group with V pairs on a tensor-core level, the vector-slice room of every
 // V-list source there, and the work items. Levels whose 2Q is too wide for
 // exact FP32 sums keep the FP64 CUDA-core GEMM (its items are filtered here).
+namespace {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to
+// the driver library); null when the driver does not provide it
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+// 2D bf16 tensor [outer][inner] at base, boxes of 8 (16 bytes) x box_rows
+bool encode_map(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* base, uint64_t inner,
+                uint64_t outer, uint32_t box_rows, TmapBlob* out) {
+  static_assert(sizeof(CUtensorMap) == sizeof(TmapBlob), "tensor map size");
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {8, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+// TMA layout of the FP64 M2L: every tensor-core group's rows get their source
+// slices in row order ([S][rows][K] at x2off), and each group a tensor map of
+// that copy and one of its matrix slices ([S][K][K]). QBX_TC_TMA=0 in the
+// environment keeps the cp.async kernel (for comparisons).
+qbx_status tc_tma_plan_build(qbx_handle* h, FmmPlan* f, const std::vector<int>& groups,
+                             const std::vector<int4>& lv, const std::vector<long long>& aoff,
+                             const std::vector<int>& rowsrc, const std::vector<long long>& xoff) {
+  (void)h;
+  f->tc_tma = false;
+  const char* env = getenv("QBX_TC_TMA");
+  if (env && env[0] == '0') return QBX_OK;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || groups.empty()) return QBX_OK;
+  const int ng = f->n_levels * 49;
+  std::vector<long long> gstart(ng + 1, 0), x2off(ng, 0);
+  for (int g = 0; g <= ng; ++g) gstart[g] = f->h_gcount[g];
+  std::vector<long long> src, dst, ts;
+  std::vector<int2> sk;
+  long long tot = 0;
+  for (int g : groups) {
+    const int l = g / 49, S = lv[l].z, K = lv[l].w;
+    const long long rows = gstart[g + 1] - gstart[g];
+    x2off[g] = tot;
+    for (long long r = gstart[g]; r < gstart[g + 1]; ++r) {
+      src.push_back(xoff[rowsrc[r]]);
+      dst.push_back(tot + (r - gstart[g]) * K);
+      ts.push_back(rows * K);
+      sk.push_back(make_int2(S, K));
+    }
+    tot += (long long)S * rows * K;
+  }
+  QBX_CUDA_TRY(f->tc_X2.alloc(std::max<long long>(1, tot)));
+  std::vector<TmapBlob> ma(ng), mx(ng);
+  std::memset(ma.data(), 0, ng * sizeof(TmapBlob));
+  std::memset(mx.data(), 0, ng * sizeof(TmapBlob));
+  for (int g : groups) {
+    const int l = g / 49, S = lv[l].z, K = lv[l].w;
+    const long long rows = gstart[g + 1] - gstart[g];
+    if (!encode_map(enc, reinterpret_cast<const uint16_t*>(f->tc_A.ptr) + aoff[g], K,
+                    (uint64_t)S * K, kNC, &ma[g]) ||
+        !encode_map(enc, f->tc_X2.ptr + x2off[g], K, (uint64_t)S * rows, kRows, &mx[g]))
+      return QBX_OK;  // no TMA maps: the cp.async kernel serves
+  }
+  f->n_tc_rows = (int)src.size();
+  TRY_TC(upload(f->tc_x2src, src));
+  TRY_TC(upload(f->tc_x2dst, dst));
+  TRY_TC(upload(f->tc_x2ts, ts));
+  TRY_TC(upload(f->tc_x2sk, sk));
+  TRY_TC(upload(f->tc_gstart, gstart));
+  TRY_TC(upload(f->tc_mapA, ma));
+  TRY_TC(upload(f->tc_mapX, mx));
+  f->tc_tma = true;
+  return QBX_OK;
+}
+
 qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
   const int nl = f->n_levels, ng = nl * 49;
   std::vector<int4> lv(nl, make_int4(0, 0, 0, 0));
@@ -1028,24 +1376,10 @@ qbx_status tc_plan_build(qbx_handle* h, FmmPlan* f) {
       QBX_CUDA_TRY(cudaMemcpy(f->tc_items[s].ptr, items[s].data(), items[s].size() * sizeof(int4),
                               cudaMemcpyHostToDevice));
   }
-  return QBX_OK;
+  return tc_tma_plan_build(h, f, groups, lv, aoff, rowsrc, xoff);
 }
 
-#define TRY_TC(x)               \
-  do {                          \
-    const qbx_status s_ = (x);  \
-    if (s_ != QBX_OK) return s_; \
-  } while (0)
 
-namespace {
-template <typename T>
-qbx_status upload(DevBuf<T>& d, const std::vector<T>& v) {
-  QBX_CUDA_TRY(d.alloc(std::max<size_t>(1, v.size())));
-  if (!v.empty())
-    QBX_CUDA_TRY(cudaMemcpy(d.ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return QBX_OK;
-}
-}  // namespace
 
 // Plan of the FP64 M2M and L2L on the tensor cores: for every parent level l
 // whose contraction width K (2 Q of the child level for M2M, of level l for
@@ -1232,7 +1566,27 @@ qbx_status launch_m2l_tc(qbx_handle* h, FmmPlan* f, bool mixed, cudaStream_t s) 
     TC_LAUNCH(6, 3)
     TC_LAUNCH(7, 4)
     TC_LAUNCH(8, 4)
-  } else {  // the persistent warp-specialised kernel
+  } else if (f->tc_tma) {  // TMA-fed: the rows' slices in row order first
+    tc_x2_fill_kernel<<<f->n_tc_rows, 128, 0, s>>>(f->n_tc_rows, f->tc_x2src.ptr, f->tc_x2dst.ptr,
+                                                  f->tc_x2ts.ptr, f->tc_x2sk.ptr, f->tc_X.ptr,
+                                                  f->tc_X2.ptr);
+    QBX_CUDA_TRY(cudaGetLastError());
+    h->launches += 1;
+#define TC_LAUNCH_TMA(S_)                                                                       \
+    if (f->n_tc_items[S_ - 6] > 0) {                                                            \
+      tc_gemm_tma_kernel<S_, S_><<<std::min(f->n_tc_items[S_ - 6], g_tc_sms), kTmaThr,          \
+                                  tc_smem_bytes<S_>(), s>>>(                                     \
+          f->tc_items[S_ - 6].ptr, f->n_tc_items[S_ - 6], f->tc_gp.ptr, f->tc_mapA.ptr,         \
+          f->tc_mapX.ptr, f->tc_gstart.ptr, f->tc_gfoff.ptr, f->tc_fexp.ptr, f->tc_rowsrc.ptr,  \
+          f->tc_xexp.ptr, f->m2l_yoff.ptr, f->m2l_y64.ptr, f->err.ptr + 1);                      \
+      QBX_CUDA_TRY(cudaGetLastError());                                                         \
+      h->launches += 1;                                                                         \
+    }
+    TC_LAUNCH_TMA(6)
+    TC_LAUNCH_TMA(7)
+    TC_LAUNCH_TMA(8)
+#undef TC_LAUNCH_TMA
+  } else {  // the persistent warp-specialised kernel on cp.async
     TC_LAUNCH_WS(6)
     TC_LAUNCH_WS(7)
     TC_LAUNCH_WS(8)

@@ -27,6 +27,11 @@ struct CentreSet {
   int wp_pbmax = 0;  // largest box order among the M2QBXL pairs' boxes
 };
 
+// An opaque TMA tensor map (CUtensorMap: 128 bytes, 64-byte aligned)
+struct alignas(64) TmapBlob {
+  unsigned char b[128];
+};
+
 // One parent level of the FP64 M2M or L2L on the tensor cores: four groups
 // (the child quadrants), the bf16 matrix slices of their sigma-normalised
 // operators, the source vectors' slices, and the rows (one per child).
@@ -176,6 +181,15 @@ struct FmmPlan {
   DevBuf<int4> tc_lvl;
   DevBuf<int4> tc_gp;                   // per group (K, Q, beta, Np) of the tile product
   std::vector<TcLevelOp> tc_m2m, tc_l2l;  // per parent level (FP64 path)
+  // FP64 M2L through TMA: the rows' source slices copied into row order per
+  // group ([S][rows][K] at x2off), and the tensor maps of those copies and of
+  // the matrix slices, per group
+  bool tc_tma = false;
+  int n_tc_rows = 0;
+  DevBuf<uint16_t> tc_X2;
+  DevBuf<long long> tc_x2src, tc_x2dst, tc_x2ts, tc_gstart;
+  DevBuf<int2> tc_x2sk;
+  DevBuf<TmapBlob> tc_mapA, tc_mapX;
   DevBuf<cd> tc_mml_y;                  // their result rows (one level at a time)
   bool tc_any = false;
   DevBuf<uint16_t> tc_A;                // bf16 matrix slices [S][Kp][Kp] per group
