@@ -139,6 +139,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without the wait: several loads in flight, one
+// tcgen05.wait::ld, then reg_fence16 on each destination so that nothing
+// reads the registers before the wait
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
+__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+// 2^e as an FP32 for -126 <= e <= 127 (0 outside: callers fall back to ldexpf)
+__device__ __forceinline__ float exp2i(int e) {
+  return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : 0.f;
+}
+
 // ---------------------------------------------------------------- float-float
 // s + e = a + b exactly (Knuth's TwoSum; additions only, so no contraction)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -795,16 +819,21 @@ __global__ void __launch_bounds__(kWsThr, 1) tc_gemm_ws_kernel(
       const int e_row = row_ok ? xexp[rowsrc[row0 + m]] : 0;
       const long long yo = row_ok ? yoff[row0 + m] : 0;
       for (int j0 = 0; j0 < kNC; j0 += 16) {
+        // the SU accumulators of these 16 columns: all loads in flight, one wait
+        uint32_t r[SU][16];
+#pragma unroll
+        for (int a = 0; a < SU; ++a) tmem_ld16_async(tl + a * kNC + j0, r[a]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int a = 0; a < SU; ++a) reg_fence16(r[a]);
         float hi[16], lo[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.f;
 #pragma unroll
         for (int a = SU - 1; a >= 0; --a) {
-          float v[16];
-          tmem_ld16(tl + a * kNC + j0, v);
-          const int sh = -beta * (a + 2);
+          const float sa = exp2i(-beta * (a + 2));  // exact: -beta (a + 2) >= -80
 #pragma unroll
-          for (int c = 0; c < 16; ++c) ff_add(hi[c], lo[c], ldexpf(v[c], sh), 0.f);
+          for (int c = 0; c < 16; ++c) ff_add(hi[c], lo[c], __uint_as_float(r[a][c]) * sa, 0.f);
         }
         if (j0 + 16 >= kNC) {  // every accumulator read: the MMAs may reuse TMEM
           asm volatile("tcgen05.fence::before_thread_sync;");
@@ -816,7 +845,9 @@ __global__ void __launch_bounds__(kWsThr, 1) tc_gemm_ws_kernel(
             const int j = n0 + j0 + c;
             if (j >= 2 * Q) break;
             const int sc = e_row + fg[j];
-            const float2 w = make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));
+            const float f = exp2i(sc);
+            const float2 w = f != 0.f ? make_float2(hi[c] * f, lo[c] * f)
+                                      : make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));
             float2* dst = reinterpret_cast<float2*>(Y + yo + (j < Q ? j : j - Q)) + (j < Q ? 0 : 1);
             *dst = w;
           }
@@ -1030,16 +1061,21 @@ __global__ void __launch_bounds__(kTmaThr, 1) tc_gemm_tma_kernel(
       const int e_row = row_ok ? xexp[rowsrc[row0 + m]] : 0;
       const long long yo = row_ok ? yoff[row0 + m] : 0;
       for (int j0 = 0; j0 < kNC; j0 += 16) {
+        // the SU accumulators of these 16 columns: all loads in flight, one wait
+        uint32_t r[SU][16];
+#pragma unroll
+        for (int a = 0; a < SU; ++a) tmem_ld16_async(tl + a * kNC + j0, r[a]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int a = 0; a < SU; ++a) reg_fence16(r[a]);
         float hi[16], lo[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.f;
 #pragma unroll
         for (int a = SU - 1; a >= 0; --a) {
-          float v[16];
-          tmem_ld16(tl + a * kNC + j0, v);
-          const int sh = -beta * (a + 2);
+          const float sa = exp2i(-beta * (a + 2));  // exact: -beta (a + 2) >= -80
 #pragma unroll
-          for (int c = 0; c < 16; ++c) ff_add(hi[c], lo[c], ldexpf(v[c], sh), 0.f);
+          for (int c = 0; c < 16; ++c) ff_add(hi[c], lo[c], __uint_as_float(r[a][c]) * sa, 0.f);
         }
         if (j0 + 16 >= kNC) {
           asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1051,7 +1087,9 @@ __global__ void __launch_bounds__(kTmaThr, 1) tc_gemm_tma_kernel(
             const int j = n0 + j0 + c;
             if (j >= 2 * Q) break;
             const int sc = e_row + fg[j];
-            const float2 w = make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));
+            const float f = exp2i(sc);
+            const float2 w = f != 0.f ? make_float2(hi[c] * f, lo[c] * f)
+                                      : make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));
             float2* dst = reinterpret_cast<float2*>(Y + yo + (j < Q ? j : j - Q)) + (j < Q ? 0 : 1);
             *dst = w;
           }
