@@ -110,8 +110,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 // bounded wait for the given phase parity of an mbarrier; false when the
 // deadline (limit_ns from the first call) or the iteration bound ran out
+// sleep_ns > 0: a waiter off the critical path (a whole warp waiting for the
+// next accumulators, a producer ahead of the MMAs) sleeps between tries and
+// leaves its scheduler's issue slots to the warps that work
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          unsigned long long limit_ns = kWaitNs) {
+                                          unsigned long long limit_ns = kWaitNs,
+                                          unsigned sleep_ns = 0) {
   const unsigned long long t0 = global_ns();
   for (long long it = 0; it < kSpin; ++it) {
     uint32_t done;
@@ -122,6 +126,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
         : "r"(smem_u32(bar)), "r"(parity));
     if (done) return true;
     if (global_ns() - t0 > limit_ns) return false;
+    if (sleep_ns) __nanosleep(sleep_ns);
   }
   return false;
 }
@@ -970,7 +975,7 @@ __global__ void __launch_bounds__(kTmaThr, 1) tc_gemm_tma_kernel(
         bool ok = true;
         for (int c = 0; c < nchunks; ++c, ++q) {
           const int slot = q % NS;
-          if (q >= NS && !mbar_wait(&empty[slot], ((q / NS) - 1) & 1)) {
+          if (q >= NS && !mbar_wait(&empty[slot], ((q / NS) - 1) & 1, kWaitNs, 32)) {
             ok = false;
             break;
           }
@@ -1052,7 +1057,7 @@ __global__ void __launch_bounds__(kTmaThr, 1) tc_gemm_tma_kernel(
       const int4 P = gp[g];
       const int Q = P.y, beta = P.z;
       const int* fg = fexp + gfoff[g];
-      if (!mbar_wait(&tfull, k & 1)) {
+      if (!mbar_wait(&tfull, k & 1, kWaitNs, 64)) {
         fail();
         break;
       }
