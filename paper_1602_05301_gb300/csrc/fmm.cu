@@ -983,10 +983,11 @@ __global__ void m2qbxl_sum_kernel(int n, int P, const int* __restrict__ cpo,
 }
 
 // ---------------------------------------------------------------- mixed precision P2QBXL
-// H_0, H_1, the Hankel recurrence and the angular factors stay FP64; the terms
-// rho^|l| W_l (rho = k r_c, which keeps them of moderate size) are rounded to
-// FP32, multiplied by the FP32 strengths and added with Kahan compensation into
-// ah_l = alpha_l rho^|l|; alpha_l = ah_l rho^-|l| is formed in FP64 at the end.
+// H_0, H_1 and the Hankel recurrence stay FP64; the terms sigma^|l| W_l
+// (sigma = 2^s near rho = k r_c, which keeps them of moderate size) are
+// rounded to FP32, multiplied by the FP32 strengths and added with Kahan
+// compensation into ah_l = alpha_l sigma^|l|; alpha_l = ah_l sigma^-|l| is
+// formed in FP64 at the end.
 __device__ __forceinline__ void kahan2(float2& s, float2& c, float2 v) {
   float y = v.x - c.x, t = s.x + y;
   c.x = (t - s.x) - y;
@@ -1005,8 +1006,8 @@ __device__ __forceinline__ float2 f2(cd a) { return make_float2(f32_from_f64(a.x
 template <int PM, bool HS, bool HD>
 __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float2 (&C)[2 * PM + 1],
                                                   double dx, double dy, float2 q, float2 A,
-                                                  float2 B, double k, double ik, double rho,
-                                                  double irho, int p) {
+                                                  float2 B, double k, double ik, int s, float fr,
+                                                  float fi, int p) {
   // one reciprocal square root gives r, 1/r and 1/x (ik = 1/k): no division
   const double d2 = dx * dx + dy * dy;
   if (d2 == 0.0) return;
@@ -1014,22 +1015,27 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   const cd e1 = mk(dx * irr, dy * irr);
   cd h0, h1;
   hankel01_wide(x, ix, h0, h1);
-  // scaled Hankel values hs_m = H_m rho^m: hs_{m+1} = (2m rho / x) hs_m - rho^2 hs_{m-1}
-  const double r2 = rho * rho, c1 = 2.0 * rho * ix, ir = irho;
-  cd hprev = h0, hcur = cscale(h1, rho);
+  // The FP64 recurrence runs on H_m itself, H_{m+1} = (2m/x) H_m - H_{m-1}
+  // (two FMAs per order); the terms are sigma^|l| W_l with sigma = 2^s close
+  // to rho = k r_c (fr = sigma, fi = 1/sigma), so H_m sigma^m is formed by an
+  // exponent offset while H_m is rounded to FP32, which keeps the terms of
+  // moderate size.
+  const double c2 = 2.0 * ix;
+  cd hprev = h0, hcur = h1;
   // angular factors e^{i m th} in FP32 (unit modulus; rounding grows like m eps_32)
   const float2 e1f = f2(e1);
   float2 ecur = e1f;
-  // W^s_m = rho^|m| W_m for m = -1, 0, 1
-  float2 wm1 = f2(cscale(cmul(hcur, cconj(e1)), -1.0));  // W^s_{-1}
+  // W^s_m = sigma^|m| W_m for m = -1, 0, 1
+  const cd t1 = cmul(hcur, cconj(e1));
+  float2 wm1 = make_float2(-f32_from_f64_sh(t1.x, s), -f32_from_f64_sh(t1.y, s));  // W^s_{-1}
   float2 w0 = f2(h0);
-  float2 w1 = f2(cmul(hcur, e1));
-  // l = 0: q W_0 + A W_{-1} - B W_1, with rho^0 W_{-1} = W^s_{-1} / rho, W_1 = W^s_1 / rho
+  const cd t2 = cmul(hcur, e1);
+  float2 w1 = make_float2(f32_from_f64_sh(t2.x, s), f32_from_f64_sh(t2.y, s));
+  // l = 0: q W_0 + A W_{-1} - B W_1, with W_{-1} = W^s_{-1} / sigma, W_1 = W^s_1 / sigma
   {
     float2 v = make_float2(0.f, 0.f);
     if (HS) v = fmul(q, w0);
     if (HD) {
-      const float fi = (float)ir;
       const float2 t = fsub(fmul(A, wm1), fmul(B, w1));
       v = make_float2(v.x + fi * t.x, v.y + fi * t.y);
     }
@@ -1037,21 +1043,20 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   }
   float2 wp_prev = w0, wp_cur = w1;   // W^s_{m-1}, W^s_m (positive side)
   float2 wn_prev = w0, wn_cur = wm1;  // W^s_{-(m-1)}, W^s_{-m}
-  double sgn = -1.0;                  // (-1)^m for m = 1
-  const float fr = (float)rho, fi = (float)ir;
-  double c1m = 0.0;                   // c1 m, kept by addition (no conversion per order)
+  double cm = 0.0;                    // 2m/x, kept by addition
 #pragma unroll
   for (int m = 1; m <= PM; ++m) {
     if (m > p) break;
-    c1m += c1;
-    const cd hnext = mk(fma(c1m, hcur.x, -r2 * hprev.x), fma(c1m, hcur.y, -r2 * hprev.y));
+    cm += c2;
+    const cd hnext = mk(fma(cm, hcur.x, -hprev.x), fma(cm, hcur.y, -hprev.y));
     const float2 enext = fmul(ecur, e1f);
-    const float2 hn32 = f2(hnext);
+    const int sh = (m + 1) * s;
+    const float2 hn32 = make_float2(f32_from_f64_sh(hnext.x, sh), f32_from_f64_sh(hnext.y, sh));
     const float2 wp_next = fmul(hn32, enext);                                // W^s_{m+1}
     const float2 wq = fmul(hn32, make_float2(enext.x, -enext.y));
-    const float fs = (float)(-sgn);
-    const float2 wn_next = make_float2(fs * wq.x, fs * wq.y);                // W^s_{-(m+1)}
-    // rho^m W_{m-1} = rho W^s_{m-1},  rho^m W_{m+1} = W^s_{m+1} / rho (same for -m)
+    // W^s_{-(m+1)} = (-1)^{m+1} conj-angle term
+    const float2 wn_next = (m & 1) ? wq : make_float2(-wq.x, -wq.y);
+    // sigma^m W_{m-1} = sigma W^s_{m-1},  sigma^m W_{m+1} = W^s_{m+1} / sigma (same for -m)
     float2 vp = make_float2(0.f, 0.f), vn = make_float2(0.f, 0.f);
     if (HS) {
       vp = fmul(q, wp_cur);
@@ -1074,7 +1079,6 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
     wp_cur = wp_next;
     wn_prev = wn_cur;
     wn_cur = wn_next;
-    sgn = -sgn;
   }
 }
 
@@ -1440,7 +1444,10 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
   const double k = F.k, ik = 1.0 / k;
   const int p = F.p, P = 2 * p + 1;
   const double2 c = F.cxy[i];
-  const double rho = k * F.crad[i], irho = 1.0 / rho;
+  // sigma = 2^s within a factor sqrt 2 of rho = k r_c: the power that scales
+  // the lane sums (ah_l = alpha_l sigma^|l|)
+  const int s = ilogb(k * F.crad[i] * 1.4142135623730951);
+  const float fr = pow2f(s), fi = pow2f(-s);
   float2 S[2 * PM + 1], C[2 * PM + 1];
 #pragma unroll
   for (int j = 0; j <= 2 * PM; ++j) S[j] = C[j] = make_float2(0.f, 0.f);
@@ -1453,7 +1460,8 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
       B = make_float2(ab.z, ab.w);
     }
     p2qbxl_pair_mixed<PM, HS, HD>(S, C, y.x - c.x, y.y - c.y,
-                                  HS ? F.q32[j] : make_float2(0.f, 0.f), A, B, k, ik, rho, irho, p);
+                                  HS ? F.q32[j] : make_float2(0.f, 0.f), A, B, k, ik, s, fr, fi,
+                                  p);
   };
   const SourceCursor sc{F.uidx, F.rsrc, F.uoff[b], F.uoff[b + 1] - F.uoff[b], wdoff[i],
                         wdoff[i + 1] - wdoff[i], wdbox};
@@ -1470,8 +1478,7 @@ __global__ void __launch_bounds__(kThreads) p2qbxl_warp_mixed_kernel(Fmm F, cons
   for (int j = 0; j < K; ++j) {
     const int lo = K * lane + j - PM;
     if (lo >= -p && lo <= p) {
-      double ip = 1.0;  // rho^-|lo|: ah_l = alpha_l rho^|l|
-      for (int t = 0; t < abs(lo); ++t) ip *= irho;
+      const double ip = pow2d(-s * abs(lo));  // sigma^-|lo|: ah_l = alpha_l sigma^|l|
       dst[lo + p] = cadd(dst[lo + p], cscale(acc[j], ip));
     }
   }

@@ -138,6 +138,19 @@ __device__ __forceinline__ float f32_from_f64(double v) {
   return __uint_as_float(bits | (hi & 0x80000000u));
 }
 
+// f32_from_f64(v * 2^sh) without the multiplication: the exponent field is
+// offset before the rounding (zero stays zero)
+__device__ __forceinline__ float f32_from_f64_sh(double v, int sh) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned e64 = (hi >> 20) & 0x7FFu;
+  const int e = (int)e64 - 896 + sh;
+  unsigned bits = ((unsigned)e << 23) + (((hi & 0xFFFFFu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+  bits = (e <= 0 || e64 == 0u) ? 0u : bits;
+  bits = e >= 255 ? 0x7F800000u : bits;
+  bits = e64 == 0x7FFu ? ((((hi & 0xFFFFFu) | lo) != 0u) ? 0x7FC00000u : 0x7F800000u) : bits;
+  return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
 // Split form of values whose range exceeds FP32: v = m 2^e with FP32
 // mantissas m (the larger component's magnitude in [1, 2)) and an integer
 // exponent e; zero (and FP64 subnormals) give m = 0, e = kZeroExp. Integer
