@@ -1277,63 +1277,99 @@ __global__ void __launch_bounds__(32) l2qbxl_mixed_kernel(Fmm F, const int* __re
 }
 
 // ---------------------------------------------------------------- M2P in mixed precision
-// The sigma-normalised FP32 multipoles mu_n = mh_n conv_|n| of the boxes that
-// M2P reads (conv = s^j / sig_j; mu is of order one or smaller).
+// The FP32 multipoles that M2P reads. On levels where the unscaled Hankel
+// recurrence stays in range (scaled[l] == 0): mu'_n = a_n 2^-t_|n|, a_n = mh_n
+// s^|n| the true coefficient and t_m = round(log2 sig_m), so that mu' is of
+// order one; otherwise the sigma-normalised mu_n = mh_n conv_|n| (conv = s^j /
+// sig_j).
 __global__ void __launch_bounds__(kThreads) mpole_f32_list_kernel(
     Fmm F, const int* __restrict__ boxes, const double* __restrict__ conv,
-    float2* __restrict__ mu) {
+    const int* __restrict__ tpow, const int* __restrict__ scaled, float2* __restrict__ mu) {
   const int b = boxes[blockIdx.x];
   const int l = F.level[b];
   const int pb = F.lpb[l];
   const double* cv = conv + (size_t)l * (F.pbmax + 1);
+  const double* pwl = pw_row(F, l);
+  const int* tl = tpow + (size_t)l * (F.pbmax + 2);
+  const bool sc = scaled[l] != 0;
   const cd* a = F.mpole + F.eoff[b];
   float2* dst = mu + F.eoff[b];
   for (int n = threadIdx.x; n <= 2 * pb; n += kThreads) {
-    const double f = cv[abs(n - pb)];
+    const int m = abs(n - pb);
+    const double f = sc ? cv[m] : pwl[m] * pow2d(-tl[m]);
     dst[n] = make_float2((float)(a[n].x * f), (float)(a[n].y * f));
   }
 }
 
 // M2P with the Hankel recurrence in FP64 and the rest in FP32: the multipole
-// sum_m A_m H_m(kr) e^{imth} written as sum_m mu_m G_m e^{imth} with
-// G_m = sig_m H_m(kr) (sig of the box's level; G decays like (side / r)^m),
-//   G_{m+1} = (2m/x)(sig_{m+1}/sig_m) G_m - (sig_{m+1}/sig_{m-1}) G_{m-1}
-// (rec[l][m] = (2m sig_{m+1}/sig_m, sig_{m+1}/sig_{m-1}), rec[l][0].x = sig_1).
-// Each G_m is rounded to FP32 once; angular factors, products and the
-// compensated (Kahan) sum are FP32; H_{-m} = (-1)^m H_m.
+// sum_m a_m H_m(kr) e^{imth}, each term formed as an FP32 product of order-one
+// factors:
+//  * unscaled levels: H_{m+1} = (2m/x) H_m - H_{m-1} (two FMAs per order), H_m
+//    rounded to FP32 with the exponent offset t_m (H_m 2^t_m, t_m = round(log2
+//    sig_m)) against mu'_m = a_m 2^-t_m;
+//  * levels where H_pb could leave the FP64 range: G_m = sig_m H_m by
+//      G_{m+1} = (2m/x)(sig_{m+1}/sig_m) G_m - (sig_{m+1}/sig_{m-1}) G_{m-1}
+//    (rec[l][m] = (2m sig_{m+1}/sig_m, sig_{m+1}/sig_{m-1}), rec[l][0].x =
+//    sig_1) against mu_m = a_m / sig_m.
+// Angular factors, products and the compensated (Kahan) sum are FP32;
+// H_{-m} = (-1)^m H_m.
 __global__ void __launch_bounds__(kThreads) m2p_pair_mixed_kernel(
     Fmm F, const int* __restrict__ pt, const int* __restrict__ pbx, int n,
-    const float2* __restrict__ mu, const double2* __restrict__ rec, cd* __restrict__ partial) {
+    const float2* __restrict__ mu, const double2* __restrict__ rec, const int* __restrict__ tpow,
+    const int* __restrict__ scaled, cd* __restrict__ partial) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = pt[t], c = pbx[t];
   const int lc = F.level[c];
   const int pb = F.lpb[lc];
   const float2* a = mu + F.eoff[c] + pb;  // a[m], |m| <= pb
-  const double2* R = rec + (size_t)lc * (F.pbmax + 2);
   const double2 mc = F.centre[c];
   const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
   const double d2 = dx * dx + dy * dy;
   const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr / F.k;
   cd h0, h1;
   hankel01_wide(x, ix, h0, h1);
-  cd gprev = h0, gcur = cscale(h1, R[0].x);
-  const float2 e1 = make_float2((float)(dx * irr), (float)(dy * irr));
+  const float2 e1 = make_float2(f32_from_f64(dx * irr), f32_from_f64(dy * irr));
   float2 ee = e1;
   float2 S = fmul(a[0], f2(h0)), C = make_float2(0.f, 0.f);
-  for (int m = 1; m <= pb; ++m) {
-    const float2 g = f2(gcur);
-    const float2 wp = fmul(g, ee);                                // G_m e^{im th}
-    float2 wn = fmul(g, make_float2(ee.x, -ee.y));                // G_m e^{-im th}
-    if (m & 1) wn = make_float2(-wn.x, -wn.y);                    // (-1)^m
-    const float2 vp = fmul(a[m], wp), vn = fmul(a[-m], wn);
-    kahan2(S, C, make_float2(vp.x + vn.x, vp.y + vn.y));
-    if (m < pb) {
-      const double c1 = R[m].x * ix, c2 = R[m].y;
-      const cd gn = mk(fma(c1, gcur.x, -c2 * gprev.x), fma(c1, gcur.y, -c2 * gprev.y));
-      gprev = gcur;
-      gcur = gn;
-      ee = fmul(ee, e1);
+  if (!scaled[lc]) {
+    const int* tl = tpow + (size_t)lc * (F.pbmax + 2);
+    const double c2 = 2.0 * ix;
+    double cm = 0.0;  // 2m/x
+    cd hprev = h0, hcur = h1;
+    for (int m = 1; m <= pb; ++m) {
+      const int sh = tl[m];
+      const float2 g = make_float2(f32_from_f64_sh(hcur.x, sh), f32_from_f64_sh(hcur.y, sh));
+      const float2 wp = fmul(g, ee);                                // H_m 2^t e^{im th}
+      float2 wn = fmul(g, make_float2(ee.x, -ee.y));                // H_m 2^t e^{-im th}
+      if (m & 1) wn = make_float2(-wn.x, -wn.y);                    // (-1)^m
+      const float2 vp = fmul(a[m], wp), vn = fmul(a[-m], wn);
+      kahan2(S, C, make_float2(vp.x + vn.x, vp.y + vn.y));
+      if (m < pb) {
+        cm += c2;
+        const cd hn = mk(fma(cm, hcur.x, -hprev.x), fma(cm, hcur.y, -hprev.y));
+        hprev = hcur;
+        hcur = hn;
+        ee = fmul(ee, e1);
+      }
+    }
+  } else {
+    const double2* R = rec + (size_t)lc * (F.pbmax + 2);
+    cd gprev = h0, gcur = cscale(h1, R[0].x);
+    for (int m = 1; m <= pb; ++m) {
+      const float2 g = f2(gcur);
+      const float2 wp = fmul(g, ee);                                // G_m e^{im th}
+      float2 wn = fmul(g, make_float2(ee.x, -ee.y));                // G_m e^{-im th}
+      if (m & 1) wn = make_float2(-wn.x, -wn.y);                    // (-1)^m
+      const float2 vp = fmul(a[m], wp), vn = fmul(a[-m], wn);
+      kahan2(S, C, make_float2(vp.x + vn.x, vp.y + vn.y));
+      if (m < pb) {
+        const double c1 = R[m].x * ix, c2 = R[m].y;
+        const cd gn = mk(fma(c1, gcur.x, -c2 * gprev.x), fma(c1, gcur.y, -c2 * gprev.y));
+        gprev = gcur;
+        gcur = gn;
+        ee = fmul(ee, e1);
+      }
     }
   }
   partial[t] = mk((double)S.x - (double)C.x, (double)S.y - (double)C.y);
@@ -2189,12 +2225,12 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   stage_begin(h, QBX_STAGE_M2P, s2);
   if (f->n_wtgt > 0 && f->n_m2p_pairs > 0) {
     if (mixed) {
-      mpole_f32_list_kernel<<<f->n_m2p_wbox, kThreads, 0, s2>>>(F, f->m2p_wbox.ptr, f->conv.ptr,
-                                                                f->m2p_mu.ptr);
+      mpole_f32_list_kernel<<<f->n_m2p_wbox, kThreads, 0, s2>>>(
+          F, f->m2p_wbox.ptr, f->conv.ptr, f->m2p_t.ptr, f->m2p_scaled.ptr, f->m2p_mu.ptr);
       QBX_KCHECK("m2p_mu", s2);
       m2p_pair_mixed_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s2>>>(
           F, f->m2p_tgt.ptr, f->m2p_box.ptr, f->n_m2p_pairs, f->m2p_mu.ptr, f->m2p_rec.ptr,
-          f->m2p_part.ptr);
+          f->m2p_t.ptr, f->m2p_scaled.ptr, f->m2p_part.ptr);
       h->launches += 1;
     } else {
       m2p_pair_kernel<<<nblk(f->n_m2p_pairs, kThreads), kThreads, 0, s2>>>(

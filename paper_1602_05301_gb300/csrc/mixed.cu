@@ -62,6 +62,17 @@ __global__ void m2p_rec_kernel(int n_levels, int pbmax, const int* __restrict__ 
   }
 }
 
+// t[l][m] = round(log2 sig_m) of level l: the power of two that M2P moves from
+// the multipole to the Hankel value (exponent offsets, no arithmetic)
+__global__ void m2p_t_kernel(int n_levels, int pbmax, const int* __restrict__ lpb,
+                             const double* __restrict__ lsig, int* __restrict__ t) {
+  const int l = blockIdx.x;
+  if (l >= n_levels) return;
+  const double* sg = lsig + (size_t)l * (pbmax + 1);
+  for (int m = threadIdx.x; m <= pbmax + 1; m += blockDim.x)
+    t[(size_t)l * (pbmax + 2) + m] = m <= lpb[l] ? (int)lrint(sg[m] * 1.4426950408889634) : 0;
+}
+
 // Level l's matrices Tm[cls][n][lo] = sig_lo sig_n (-1)^lo W_{n+lo}(D) (orders
 // up to pb = pb_l; M2lNorm), stored in FP32. Grid: (cls, n), threads over lo.
 __global__ void m2l_f32_matrix_kernel(int l, int pb, int pbmax, const cd* __restrict__ t_m2l,
@@ -598,6 +609,23 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
   QBX_CUDA_TRY(f->m2p_rec.alloc((size_t)f->n_levels * (pbm + 2)));
   m2p_rec_kernel<<<f->n_levels, 128>>>(f->n_levels, pbm, f->lpb.ptr, f->lsig.ptr, f->m2p_rec.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
+  QBX_CUDA_TRY(f->m2p_t.alloc((size_t)f->n_levels * (pbm + 2)));
+  m2p_t_kernel<<<f->n_levels, 128>>>(f->n_levels, pbm, f->lpb.ptr, f->lsig.ptr, f->m2p_t.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  {  // levels where H_pb(x) could leave the FP64 range: x = k |t - m_c| >= 1.5 k
+     // side for a W-list box (taken as 0.5 k side), |H_m(x)| <~ (m-1)! (2/x)^m
+    std::vector<int> scaled(f->n_levels, 0);
+    for (int l = 0; l < f->n_levels; ++l) {
+      const int pb = f->h_pb[l];
+      if (pb < 1) continue;
+      const double x_lo = 0.5 * h->k * f->side / (double)(1LL << std::min(l, 62));
+      const double ln_h = std::lgamma((double)pb) + pb * std::log(2.0 / x_lo);
+      scaled[l] = ln_h > 650.0 ? 1 : 0;
+    }
+    QBX_CUDA_TRY(f->m2p_scaled.alloc(f->n_levels));
+    QBX_CUDA_TRY(cudaMemcpy(f->m2p_scaled.ptr, scaled.data(), f->n_levels * sizeof(int),
+                            cudaMemcpyHostToDevice));
+  }
   // matrices for the levels that have V lists
   std::vector<long long> off(f->n_levels, 0);
   long long tot = 0;
