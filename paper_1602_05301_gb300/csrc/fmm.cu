@@ -94,6 +94,9 @@ struct Fmm {
   const cd* t_l2l;       // [n_levels][4][4 pbmax + 1]
   cd* mpole;
   cd* local;
+  const double* conv;    // [n_levels][pbmax + 1] s^j / sig_j (mixed path)
+  const double* lsig;    // [n_levels][pbmax + 1] log sig_j
+  const double2* sigr;   // [n_levels][pbmax + 2] (sig_{j-1} / sig_j, sig_{j+1} / sig_j)
   double k, side;
   int pbmax, p, n_levels, has_S, has_D;
 };
@@ -1375,6 +1378,103 @@ __global__ void __launch_bounds__(kThreads) m2p_pair_mixed_kernel(
   partial[t] = mk((double)S.x - (double)C.x, (double)S.y - (double)C.y);
 }
 
+// ---------------------------------------------------------------- P2M in mixed precision
+// The item structure of p2m_item_kernel with the sums in FP32: the rows
+// R_t = conj(V_t) / sig_|t| (the FP64 Miller recurrence and angular factors,
+// each entry rounded to FP32 once; stored in the first half of each 16-byte
+// row slot) and, over the item's sources with Kahan compensation,
+//   mu_n = sum_j [q_j R_n + A_j R_{n-1} sig_|n-1| / sig_|n| - B_j R_{n+1} sig_|n+1| / sig_|n|],
+// A = d (k/2) conj(nu), B = d (k/2) nu; mu_n = a_n / sig_|n|, of order one.
+// p2m_sum_mixed_kernel adds a leaf's segments in FP64 and forms mh_n = mu_n /
+// conv_|n| (conv = s^j / sig_j).
+__device__ __forceinline__ void p2m_fill_row_mixed(const Fmm& F, int i, double2 m, double is,
+                                                   int l, int pb, cd* row, cd& sq, cd& sa,
+                                                   cd& sb) {
+  const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
+  const double rr = sqrt(dx * dx + dy * dy);
+  const double norm = miller_row(F.k * rr, pb + 1, (double*)row, 2);
+  const double* cv = F.conv + (size_t)l * (F.pbmax + 1);
+  const cd em = rr > 0.0 ? mk(dx / rr, -dy / rr) : mk(1.0, 0.0);  // e^{-i th}
+  cd e = mk(1.0, 0.0);
+  double f = 1.0 / norm;  // 1 / (norm s^j)
+  for (int j = 0; j <= pb + 1; ++j) {
+    // f conv_j = 1 / (norm sig_j); order pb + 1 enters only as sig_pb-normalised
+    // (its factor sig_|pb+1| / sig_|pb| is taken as 1 below)
+    const double sc = j <= pb ? cv[j] : cv[pb] / is;
+    const double v = row[j].x * f * sc;
+    const cd c = cscale(e, v);                    // R_j
+    reinterpret_cast<float2*>(row + j)[0] = f2(c);
+    if (j > 0) reinterpret_cast<float2*>(row - j)[0] = (j & 1) ? f2(mk(-c.x, c.y)) : f2(mk(c.x, -c.y));
+    e = cmul(e, em);
+    f *= is;
+  }
+  const float4 ab = F.ab32[i];
+  reinterpret_cast<float2*>(&sq)[0] = F.q32[i];
+  reinterpret_cast<float2*>(&sa)[0] = make_float2(ab.z, ab.w);  // d (k/2) conj(nu)
+  reinterpret_cast<float2*>(&sb)[0] = make_float2(ab.x, ab.y);  // d (k/2) nu
+}
+
+__global__ void __launch_bounds__(kThreads) p2m_item_mixed_kernel(
+    Fmm F, const int4* __restrict__ items, const int* __restrict__ seg_leaf,
+    const int2* __restrict__ seg_row, const long long* __restrict__ seg_poff,
+    const int* __restrict__ src, const int* __restrict__ src_leaf, cd* __restrict__ partial,
+    unsigned sm_bytes) {
+  extern __shared__ cd smem[];
+  const int4 it = items[blockIdx.x];
+  const int l = F.level[seg_leaf[it.x]];
+  const int pb = F.lpb[l], Q = 2 * pb + 1, RW = 2 * pb + 3;
+  const int chunk = rows_chunk(pb, sm_bytes);  // >= it.w
+  cd* rows = smem;                        // [chunk][RW]
+  cd* sq = rows + chunk * RW;             // [chunk]
+  cd* sa = sq + chunk;                    // [chunk]
+  cd* sb = sa + chunk;                    // [chunk]
+  const double is = 1.0 / F.scale[l];
+  if ((int)threadIdx.x < it.w) {
+    const int j = threadIdx.x;
+    p2m_fill_row_mixed(F, src[it.z + j], F.centre[src_leaf[it.z + j]], is, l, pb,
+                       rows + j * RW + (pb + 1), sq[j], sa[j], sb[j]);
+  }
+  __syncthreads();
+  const double2* sr = F.sigr + (size_t)l * (F.pbmax + 2);
+  for (int idx = threadIdx.x; idx < it.y * Q; idx += kThreads) {
+    const int u = idx / Q, n = idx % Q - pb;
+    const int2 rg = seg_row[it.x + u];
+    float2 Sq = make_float2(0.f, 0.f), Cq = Sq, Sa = Sq, Ca = Sq, Sb = Sq, Cb = Sq;
+    for (int j = rg.x; j < rg.x + rg.y; ++j) {
+      const float2* r = reinterpret_cast<const float2*>(rows + j * RW + (pb + 1));
+      if (F.has_S) kahan2(Sq, Cq, fmul(reinterpret_cast<const float2*>(sq + j)[0], r[2 * n]));
+      if (F.has_D) {
+        kahan2(Sa, Ca, fmul(reinterpret_cast<const float2*>(sa + j)[0], r[2 * (n - 1)]));
+        kahan2(Sb, Cb, fmul(reinterpret_cast<const float2*>(sb + j)[0], r[2 * (n + 1)]));
+      }
+    }
+    // sig_|n-1| / sig_|n| and sig_|n+1| / sig_|n| (1 beyond order pb)
+    const int an = abs(n);
+    const double2 rt = sr[an];  // (sig_{an-1} / sig_an, sig_{an+1} / sig_an)
+    const double fm = n > 0 ? rt.x : rt.y, fp = n < 0 ? rt.x : rt.y;
+    const double re = ((double)Sq.x - (double)Cq.x) + fm * ((double)Sa.x - (double)Ca.x) -
+                      fp * ((double)Sb.x - (double)Cb.x);
+    const double im = ((double)Sq.y - (double)Cq.y) + fm * ((double)Sa.y - (double)Ca.y) -
+                      fp * ((double)Sb.y - (double)Cb.y);
+    partial[seg_poff[it.x + u] + n + pb] = mk(re, im);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) p2m_sum_mixed_kernel(
+    Fmm F, const int* __restrict__ leaves, const int* __restrict__ lseg,
+    const long long* __restrict__ seg_poff, const cd* __restrict__ partial) {
+  const int t = blockIdx.x, b = leaves[t];
+  const int l = F.level[b];
+  const int pb = F.lpb[l], Q = 2 * pb + 1;
+  const double* cv = F.conv + (size_t)l * (F.pbmax + 1);
+  cd* dst = F.mpole + F.eoff[b];
+  for (int n = threadIdx.x; n < Q; n += kThreads) {
+    cd sum = mk(0.0, 0.0);
+    for (int g = lseg[t]; g < lseg[t + 1]; ++g) sum = cadd(sum, partial[seg_poff[g] + n]);
+    dst[n] = cscale(sum, 1.0 / cv[abs(n - pb)]);
+  }
+}
+
 // Lift the 48 KB default of dynamic shared memory to the device's opt-in
 // maximum for every kernel that uses it (once per device); the size given at
 // each launch still decides the occupancy.
@@ -1388,7 +1488,8 @@ qbx_status configure_kernels() {
   if (done.count(dev)) return QBX_OK;
   int optin = 0;
   QBX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const void* k[] = {(const void*)p2m_item_kernel, (const void*)m2m_kernel,
+  const void* k[] = {(const void*)p2m_item_kernel, (const void*)p2m_item_mixed_kernel,
+                     (const void*)m2m_kernel,
                      (const void*)p2l_item_kernel, (const void*)l2l_kernel};
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -1980,6 +2081,7 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   F.scale = f->scale.ptr; F.pw = f->pw.ptr; F.ipw = f->ipw.ptr;
   F.t_m2l = f->t_m2l.ptr; F.t_m2m = f->t_m2m.ptr; F.t_l2l = f->t_l2l.ptr;
   F.mpole = f->mpole.ptr; F.local = f->local.ptr;
+  F.conv = f->conv.ptr; F.lsig = f->lsig.ptr; F.sigr = f->sigr.ptr;
   F.k = h->k; F.side = f->side; F.pbmax = f->pb_max; F.p = h->p; F.n_levels = f->n_levels;
   F.has_S = S ? 1 : 0; F.has_D = D ? 1 : 0;
   return F;
@@ -2183,12 +2285,21 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   // ---- main: upward pass
   stage_begin(h, QBX_STAGE_P2M, s);
   if ((S || D) && f->n_p2m_items > 0) {
-    p2m_item_kernel<<<f->n_p2m_items, kThreads, f->p2m_sm, s>>>(
-        F, f->p2m_items.ptr, f->p2m_segleaf.ptr, f->p2m_segrow.ptr, f->p2m_segpoff.ptr,
-        f->p2m_src.ptr, f->p2m_srcleaf.ptr, f->p2m_part.ptr, (unsigned)f->p2m_sm);
-    QBX_KCHECK("p2m", s);
-    p2m_sum_kernel<<<f->n_src_leaves, kThreads, 0, s>>>(F, f->src_leaves.ptr, f->p2m_lseg.ptr,
-                                                       f->p2m_segpoff.ptr, f->p2m_part.ptr);
+    if (mixed) {
+      p2m_item_mixed_kernel<<<f->n_p2m_items, kThreads, f->p2m_sm, s>>>(
+          F, f->p2m_items.ptr, f->p2m_segleaf.ptr, f->p2m_segrow.ptr, f->p2m_segpoff.ptr,
+          f->p2m_src.ptr, f->p2m_srcleaf.ptr, f->p2m_part.ptr, (unsigned)f->p2m_sm);
+      QBX_KCHECK("p2m", s);
+      p2m_sum_mixed_kernel<<<f->n_src_leaves, kThreads, 0, s>>>(
+          F, f->src_leaves.ptr, f->p2m_lseg.ptr, f->p2m_segpoff.ptr, f->p2m_part.ptr);
+    } else {
+      p2m_item_kernel<<<f->n_p2m_items, kThreads, f->p2m_sm, s>>>(
+          F, f->p2m_items.ptr, f->p2m_segleaf.ptr, f->p2m_segrow.ptr, f->p2m_segpoff.ptr,
+          f->p2m_src.ptr, f->p2m_srcleaf.ptr, f->p2m_part.ptr, (unsigned)f->p2m_sm);
+      QBX_KCHECK("p2m", s);
+      p2m_sum_kernel<<<f->n_src_leaves, kThreads, 0, s>>>(F, f->src_leaves.ptr, f->p2m_lseg.ptr,
+                                                         f->p2m_segpoff.ptr, f->p2m_part.ptr);
+    }
     QBX_KCHECK("p2m_sum", s);
     h->launches += 2;
   }

@@ -73,6 +73,25 @@ __global__ void m2p_t_kernel(int n_levels, int pbmax, const int* __restrict__ lp
     t[(size_t)l * (pbmax + 2) + m] = m <= lpb[l] ? (int)lrint(sg[m] * 1.4426950408889634) : 0;
 }
 
+// r[l][m] = (sig_{m-1} / sig_m, sig_{m+1} / sig_m) of level l, 1 where the
+// neighbour order is outside 0..pb (the mixed P2M's dipole terms)
+__global__ void sig_ratio_kernel(int n_levels, int pbmax, const int* __restrict__ lpb,
+                                 const double* __restrict__ lsig, double2* __restrict__ r) {
+  const int l = blockIdx.x;
+  if (l >= n_levels) return;
+  const double* sg = lsig + (size_t)l * (pbmax + 1);
+  const int pb = lpb[l];
+  for (int m = threadIdx.x; m <= pbmax + 1; m += blockDim.x) {
+    double2 v = make_double2(1.0, 1.0);
+    if (m <= pb) {
+      if (m >= 1) v.x = exp(sg[m - 1] - sg[m]);
+      else v.x = exp(sg[1 <= pb ? 1 : 0] - sg[0]);  // |0 - 1| = 1
+      if (m + 1 <= pb) v.y = exp(sg[m + 1] - sg[m]);
+    }
+    r[(size_t)l * (pbmax + 2) + m] = v;
+  }
+}
+
 // Level l's matrices Tm[cls][n][lo] = sig_lo sig_n (-1)^lo W_{n+lo}(D) (orders
 // up to pb = pb_l; M2lNorm), stored in FP32. Grid: (cls, n), threads over lo.
 __global__ void m2l_f32_matrix_kernel(int l, int pb, int pbmax, const cd* __restrict__ t_m2l,
@@ -608,6 +627,9 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
   QBX_CUDA_TRY(cudaGetLastError());
   QBX_CUDA_TRY(f->m2p_rec.alloc((size_t)f->n_levels * (pbm + 2)));
   m2p_rec_kernel<<<f->n_levels, 128>>>(f->n_levels, pbm, f->lpb.ptr, f->lsig.ptr, f->m2p_rec.ptr);
+  QBX_CUDA_TRY(cudaGetLastError());
+  QBX_CUDA_TRY(f->sigr.alloc((size_t)f->n_levels * (pbm + 2)));
+  sig_ratio_kernel<<<f->n_levels, 128>>>(f->n_levels, pbm, f->lpb.ptr, f->lsig.ptr, f->sigr.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   QBX_CUDA_TRY(f->m2p_t.alloc((size_t)f->n_levels * (pbm + 2)));
   m2p_t_kernel<<<f->n_levels, 128>>>(f->n_levels, pbm, f->lpb.ptr, f->lsig.ptr, f->m2p_t.ptr);

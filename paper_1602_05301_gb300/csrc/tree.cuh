@@ -122,6 +122,7 @@ struct FmmPlan {
   DevBuf<float2> m2p_mu;                 // [n_coef] their sigma-normalised FP32 multipoles
   DevBuf<double2> m2p_rec;               // [n_levels][pbmax + 2] sigma-scaled Hankel recurrence
   DevBuf<int> m2p_t;                     // [n_levels][pbmax + 2] round(log2 sig_m)
+  DevBuf<double2> sigr;                  // [n_levels][pbmax + 2] (sig_{m-1}/sig_m, sig_{m+1}/sig_m)
   DevBuf<int> m2p_scaled;                // [n_levels] 1: the unscaled recurrence could overflow
   // Centre sets: [0] every centre, [1] the centres some target uses. Each
   // lists sorted centre indices (clist) and its M2QBXL work items, the
