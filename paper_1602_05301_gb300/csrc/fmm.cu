@@ -94,6 +94,7 @@ struct Fmm {
   const cd* t_l2l;       // [n_levels][4][4 pbmax + 1]
   cd* mpole;
   cd* local;
+  cd* lpq;               // [n_coef] leaf cos/sin coefficients of L2P (see unscale_leaf_locals_kernel)
   const double* conv;    // [n_levels][pbmax + 1] s^j / sig_j (mixed path)
   const double* lsig;    // [n_levels][pbmax + 1] log sig_j
   const double2* sigr;   // [n_levels][pbmax + 2] (sig_{j-1} / sig_j, sig_{j+1} / sig_j)
@@ -577,11 +578,11 @@ __device__ __forceinline__ void deal_sources(const SourceCursor& sc, int lane, F
   }
 }
 
-// L2P: one thread per direct target (sorted index list), from the true local
-// coefficients gamma of its leaf; adds to out. The backward recurrence yields
-// f_m for descending m, so both angular sums run by Horner's rule in
-// z = e^{i th}: A = A conj(z) + f_m gamma_m (m = pb..0) and
-// B = (B + (-1)^m f_m gamma_{-m}) z (m = pb..1), psi = (A + B) / norm.
+// L2P: one thread per direct target (sorted index list), from the local
+// coefficients of its leaf in cosine/sine form (P_m, Q_m); adds to out. The
+// backward recurrence yields f_m for descending m, and Clenshaw's recurrences
+// for the cosine and sine sums run in the same loop (two FMAs per real
+// component and order, no complex products).
 __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restrict__ dtgt,
                                                        const int* __restrict__ tleaf, int n,
                                                        cd* __restrict__ out) {
@@ -613,34 +614,55 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
       e = cmul(e, e1);
     }
   } else {
+    // Miller's backward recurrence for f_m ~ J_m(x) (unnormalised), fused with
+    // Clenshaw's recurrences for sum_m f_m P_m cos(m th) (u: b_{m+1}, b_{m+2})
+    // and sum_m f_m Q_m sin(m th) (v), both run from m = pb down:
+    //   b_m = f_m c_m + 2 cos(th) b_{m+1} - b_{m+2},
+    //   sum c_m cos(m th) = b_0 - cos(th) b_1,  sum_{m>=1} c_m sin(m th) = sin(th) b_1.
+    const cd* pq = F.lpq + F.eoff[b];
+    const double c = e1.x, c2 = 2.0 * c;
     const double inv = 2.0 / x;
     const int N = miller_start(pb, x);
-    double fn1 = 0.0, fn = 1e-200, sum = 0.0;
-    cd A = mk(0.0, 0.0), B = mk(0.0, 0.0);
-    for (int nn = N; nn >= 1; --nn) {
-      const double fm = (double)nn * inv * fn - fn1;  // f_{nn-1}
-      if ((nn & 1) == 0) sum += fn;
-      const int mm = nn - 1;
-      if (mm <= pb) {
-        const cd gp = g[pb + mm];
-        A = mk(fma(A.x, e1.x, fma(A.y, e1.y, fm * gp.x)),
-               fma(A.y, e1.x, fma(-A.x, e1.y, fm * gp.y)));  // A conj(z) + f_m g_m
-        if (mm > 0) {
-          const cd gn = g[pb - mm];
-          const double fs = (mm & 1) ? -fm : fm;
-          B = cmul(mk(fma(fs, gn.x, B.x), fma(fs, gn.y, B.y)), e1);
-        }
-      }
+    double fn1 = 0.0, fn = 0x1p-600, sum = 0.0, dn = (double)N;
+    // f_{n-1} = (2n/x) f_n - f_{n+1}; the sum of the even orders normalises
+    // (J_0 + 2 sum J_{2k} = 1); a power of two rescales everything kept when
+    // f grows past 2^332 (an integer test on the exponent field)
+    auto step = [&]() {
+      const double fm = fma(dn * inv, fn, -fn1);
       fn1 = fn;
       fn = fm;
-      if (fabs(fn) > kRescale) {
-        const double sc = 1.0 / kRescale;
-        fn *= sc; fn1 *= sc; sum *= sc;
-        A = cscale(A, sc);
-        B = cscale(B, sc);
+      dn -= 1.0;
+    };
+    int nn = N;
+    for (; nn >= pb + 2; --nn) {  // orders above pb: the recurrence alone
+      if ((nn & 1) == 0) sum += fn;
+      step();
+      if ((__double2hiint(fn) & 0x7FFFFFFF) >= (1355 << 20)) {
+        fn *= 0x1p-332; fn1 *= 0x1p-332; sum *= 0x1p-332;
       }
     }
-    acc = cadd(A, B);
+    cd u1 = mk(0.0, 0.0), u2 = u1, v1 = u1, v2 = u1;
+    for (; nn >= 1; --nn) {
+      if ((nn & 1) == 0) sum += fn;
+      step();
+      const int mm = nn - 1;  // fn = f_mm
+      const cd P = pq[mm];
+      const cd u0 = mk(fma(fn, P.x, fma(c2, u1.x, -u2.x)), fma(fn, P.y, fma(c2, u1.y, -u2.y)));
+      u2 = u1;
+      u1 = u0;
+      if (mm >= 1) {
+        const cd Qm = pq[pb + mm];
+        const cd v0 = mk(fma(fn, Qm.x, fma(c2, v1.x, -v2.x)), fma(fn, Qm.y, fma(c2, v1.y, -v2.y)));
+        v2 = v1;
+        v1 = v0;
+      }
+      if ((__double2hiint(fn) & 0x7FFFFFFF) >= (1355 << 20)) {
+        const double sc = 0x1p-332;
+        fn *= sc; fn1 *= sc; sum *= sc;
+        u1 = cscale(u1, sc); u2 = cscale(u2, sc); v1 = cscale(v1, sc); v2 = cscale(v2, sc);
+      }
+    }
+    acc = mk(fma(-c, u2.x, u1.x) + e1.y * v1.x, fma(-c, u2.y, u1.y) + e1.y * v1.y);
     norm = fn + 2.0 * sum;
   }
   cd* dst = out + F.tid[i];
@@ -792,15 +814,35 @@ __global__ void __launch_bounds__(32) l2qbxl_kernel(Fmm F, const int* __restrict
 
 
 // Leaf local coefficients lh_n = gamma_n s^|n| -> gamma_n, in place, once the
-// downward pass (M2L, P2L, L2L) is complete; L2P and L2QBXL read gamma.
+// downward pass (M2L, P2L, L2L) is complete; L2P and L2QBXL read gamma. The
+// same pass writes the leaf's L2P coefficients in cosine/sine form: with
+// s_m = (-1)^m, the term of order m of the local expansion at (r, th) is
+//   J_m(k r) [gamma_m e^{-i m th} + s_m gamma_{-m} e^{i m th}]
+//     = J_m(k r) [P_m cos(m th) + Q_m sin(m th)],
+//   P_m = gamma_m + s_m gamma_{-m},  Q_m = i (s_m gamma_{-m} - gamma_m),  P_0 = gamma_0,
+// stored as lpq[eoff + m] = P_m (m = 0..pb), lpq[eoff + pb + m] = Q_m (m = 1..pb).
 __global__ void __launch_bounds__(kThreads) unscale_leaf_locals_kernel(Fmm F,
                                                                        const int* __restrict__ leaves) {
   const int b = leaves[blockIdx.x];
   const int l = F.level[b];
-  const int pb = F.lpb[l], Q = 2 * pb + 1;
+  const int pb = F.lpb[l];
   const double* ipp = ipw_row(F, l);
   cd* lp = F.local + F.eoff[b];
-  for (int i = threadIdx.x; i < Q; i += kThreads) lp[i] = cscale(lp[i], ipp[abs(i - pb)]);
+  cd* pq = F.lpq + F.eoff[b];
+  for (int m = threadIdx.x; m <= pb; m += kThreads) {
+    const cd gp = cscale(lp[pb + m], ipp[m]);
+    lp[pb + m] = gp;
+    if (m == 0) {
+      pq[0] = gp;
+      continue;
+    }
+    const cd gn = cscale(lp[pb - m], ipp[m]);
+    lp[pb - m] = gn;
+    const cd sg = (m & 1) ? mk(-gn.x, -gn.y) : gn;
+    pq[m] = cadd(gp, sg);
+    const cd d = csub(sg, gp);
+    pq[pb + m] = mk(-d.y, d.x);
+  }
 }
 
 
@@ -1719,6 +1761,7 @@ qbx_status fmm_plan_build(qbx_handle* h, const qbx_tree_desc* d, const int64_t* 
   QBX_CUDA_TRY(cudaGetLastError());
   QBX_CUDA_TRY(f->mpole.alloc(std::max<int64_t>(1, f->n_coef)));
   QBX_CUDA_TRY(f->local.alloc(std::max<int64_t>(1, f->n_coef)));
+  QBX_CUDA_TRY(f->lpq.alloc(std::max<int64_t>(1, f->n_coef)));
   QBX_CUDA_TRY(f->sp_m.alloc(std::max<int64_t>(1, f->n_coef)));
   QBX_CUDA_TRY(f->sp_e.alloc(std::max<int64_t>(1, f->n_coef)));
   TRY(configure_kernels());
@@ -2080,7 +2123,7 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   F.lpb = f->lpb.ptr; F.eoff = f->eoff.ptr;
   F.scale = f->scale.ptr; F.pw = f->pw.ptr; F.ipw = f->ipw.ptr;
   F.t_m2l = f->t_m2l.ptr; F.t_m2m = f->t_m2m.ptr; F.t_l2l = f->t_l2l.ptr;
-  F.mpole = f->mpole.ptr; F.local = f->local.ptr;
+  F.mpole = f->mpole.ptr; F.local = f->local.ptr; F.lpq = f->lpq.ptr;
   F.conv = f->conv.ptr; F.lsig = f->lsig.ptr; F.sigr = f->sigr.ptr;
   F.k = h->k; F.side = f->side; F.pbmax = f->pb_max; F.p = h->p; F.n_levels = f->n_levels;
   F.has_S = S ? 1 : 0; F.has_D = D ? 1 : 0;

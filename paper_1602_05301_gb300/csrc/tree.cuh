@@ -147,6 +147,7 @@ struct FmmPlan {
   DevBuf<int> t_assoc;                  // association of sorted targets (centre id or -1)
   // expansions
   DevBuf<cd> mpole, local;              // [n_coef], box b at eoff[b]
+  DevBuf<cd> lpq;                       // [n_coef], leaf L2P coefficients in cos/sin form
   DevBuf<cd> qs, ds;                    // sorted strengths
   DevBuf<float2> q32;                   // their FP32 charges and dipole factors (mixed path)
   DevBuf<float4> ab32;
