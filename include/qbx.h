@@ -388,10 +388,12 @@ qbx_status qbx_selftest_wait_timeout(qbx_handle *h, int32_t limit_us);
  * H_0(x) and H_1(x) of the first kind, as every kernel of the library
  * evaluates them on the device (the Hankel values that start the recurrences
  * of Sec. 7.2's translations and the kernel G = (i/4) H_0(k|x - y|) of Sec. 1):
- * the ascending series (DLMF 10.2.2, 10.8.1) below the series reach, the CUDA
- * math library's j0/y0/j1/y1 above it. variant 0: the FP64 path (reach x < 5,
- * relative error about 1e-14 at most); 1: the mixed-precision path (reach
- * x < 8, below 3e-13). x: host [n], positive and finite; out: host [n][4] =
+ * below x = 8 piecewise polynomials (the ascending series, DLMF 10.2.2 and
+ * 10.8.1, economised on x < 2; Chebyshev fits on sixteen intervals of
+ * [2, 8)), the CUDA math library's j0/y0/j1/y1 above. variant 0: the FP64
+ * path (degree 10, relative error below 1e-15 of |H_0|, |H_1|); 1: the
+ * mixed-precision path (degree 8, below 1e-13). x: host [n], positive and
+ * finite; out: host [n][4] =
  * (Re H_0, Im H_0, Re H_1, Im H_1). Synchronous. Errors: QBX_ERR_ARG (NULL
  * pointer with n > 0, n < 0, x[i] <= 0 or not finite, unknown variant),
  * QBX_ERR_OOM / QBX_ERR_CUDA.

@@ -98,7 +98,7 @@ struct Fmm {
   const double* conv;    // [n_levels][pbmax + 1] s^j / sig_j (mixed path)
   const double* lsig;    // [n_levels][pbmax + 1] log sig_j
   const double2* sigr;   // [n_levels][pbmax + 2] (sig_{j-1} / sig_j, sig_{j+1} / sig_j)
-  double k, side;
+  double k, ik, side;    // wavenumber, 1 / k, root box side
   int pbmax, p, n_levels, has_S, has_D;
 };
 
@@ -1055,9 +1055,8 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
                                                   float fi, int p) {
   // one reciprocal square root gives r, 1/r and 1/x (ik = 1/k): no division
   const double d2 = dx * dx + dy * dy;
-  if (d2 == 0.0) return;
+  if ((__double2hiint(d2) | __double2loint(d2)) == 0) return;  // d2 == 0 (integer test)
   const double irr = rsqrt(d2), rr = d2 * irr, x = k * rr, ix = ik * irr;
-  const cd e1 = mk(dx * irr, dy * irr);
   cd h0, h1;
   hankel01_wide(x, ix, h0, h1);
   // The FP64 recurrence runs on H_m itself, H_{m+1} = (2m/x) H_m - H_{m-1}
@@ -1067,15 +1066,18 @@ __device__ __forceinline__ void p2qbxl_pair_mixed(float2 (&S)[2 * PM + 1], float
   // moderate size.
   const double c2 = 2.0 * ix;
   cd hprev = h0, hcur = h1;
-  // angular factors e^{i m th} in FP32 (unit modulus; rounding grows like m eps_32)
-  const float2 e1f = f2(e1);
+  // angular factors e^{i m th} in FP32 (unit modulus; rounding grows like m eps_32),
+  // from the FP32 roundings of dx, dy and 1/r
+  const float irf = f32_from_f64(irr);
+  const float2 e1f = make_float2(f32_from_f64(dx) * irf, f32_from_f64(dy) * irf);
   float2 ecur = e1f;
-  // W^s_m = sigma^|m| W_m for m = -1, 0, 1
-  const cd t1 = cmul(hcur, cconj(e1));
-  float2 wm1 = make_float2(-f32_from_f64_sh(t1.x, s), -f32_from_f64_sh(t1.y, s));  // W^s_{-1}
+  // W^s_m = sigma^|m| W_m for m = -1, 0, 1, the products in FP32 as for every
+  // other order
+  const float2 h1s = make_float2(f32_from_f64_sh(h1.x, s), f32_from_f64_sh(h1.y, s));
+  const float2 t1 = fmul(h1s, make_float2(e1f.x, -e1f.y));
+  float2 wm1 = make_float2(-t1.x, -t1.y);  // W^s_{-1}
   float2 w0 = f2(h0);
-  const cd t2 = cmul(hcur, e1);
-  float2 w1 = make_float2(f32_from_f64_sh(t2.x, s), f32_from_f64_sh(t2.y, s));
+  float2 w1 = fmul(h1s, e1f);
   // l = 0: q W_0 + A W_{-1} - B W_1, with W_{-1} = W^s_{-1} / sigma, W_1 = W^s_1 / sigma
   {
     float2 v = make_float2(0.f, 0.f);
@@ -1194,7 +1196,7 @@ __global__ void __launch_bounds__(32) m2qbxl_mixed_kernel(
     const double2 mc = F.centre[c];
     const double dx = z.x - mc.x, dy = z.y - mc.y;
     const double d2 = dx * dx + dy * dy;
-    const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr / F.k;
+    const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr * F.ik;
     const cd e1 = mk(dx * irr, dy * irr);
     cd h0, h1;
     hankel01_wide(x, ix, h0, h1);
@@ -1371,10 +1373,11 @@ __global__ void __launch_bounds__(kThreads) m2p_pair_mixed_kernel(
   const double2 mc = F.centre[c];
   const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
   const double d2 = dx * dx + dy * dy;
-  const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr / F.k;
+  const double irr = rsqrt(d2), rr = d2 * irr, x = F.k * rr, ix = irr * F.ik;
   cd h0, h1;
   hankel01_wide(x, ix, h0, h1);
-  const float2 e1 = make_float2(f32_from_f64(dx * irr), f32_from_f64(dy * irr));
+  const float irf = f32_from_f64(irr);
+  const float2 e1 = make_float2(f32_from_f64(dx) * irf, f32_from_f64(dy) * irf);
   float2 ee = e1;
   float2 S = fmul(a[0], f2(h0)), C = make_float2(0.f, 0.f);
   if (!scaled[lc]) {
@@ -2125,7 +2128,7 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   F.t_m2l = f->t_m2l.ptr; F.t_m2m = f->t_m2m.ptr; F.t_l2l = f->t_l2l.ptr;
   F.mpole = f->mpole.ptr; F.local = f->local.ptr; F.lpq = f->lpq.ptr;
   F.conv = f->conv.ptr; F.lsig = f->lsig.ptr; F.sigr = f->sigr.ptr;
-  F.k = h->k; F.side = f->side; F.pbmax = f->pb_max; F.p = h->p; F.n_levels = f->n_levels;
+  F.k = h->k; F.ik = 1.0 / h->k; F.side = f->side; F.pbmax = f->pb_max; F.p = h->p; F.n_levels = f->n_levels;
   F.has_S = S ? 1 : 0; F.has_D = D ? 1 : 0;
   return F;
 }

@@ -1,7 +1,6 @@
 // qbx_hankel01: the device evaluation of H_0 and H_1 of the first kind that
-// every kernel of the library uses (ascending series, DLMF 10.2.2 and 10.8.1,
-// below the series reach; the CUDA math library above), exposed so that it
-// can be checked on its own.
+// every kernel of the library uses (piecewise polynomials below x = 8, the
+// CUDA math library above), exposed so that it can be checked on its own.
 #include <cmath>
 
 #include "special.cuh"

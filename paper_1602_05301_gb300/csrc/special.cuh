@@ -1,8 +1,8 @@
 // Device special functions for the 2D Helmholtz kernels.
 //
-//  * H_0, H_1 of the first kind: the ascending series below a series reach
-//    (x < 5, or x < 8 for the mixed path), the CUDA math library's
-//    j0/y0/j1/y1 (FP64) above it.
+//  * H_0, H_1 of the first kind: piecewise polynomials below x = 8 (the
+//    economised ascending series below 2, Chebyshev fits on sixteen
+//    intervals of [2, 8)), the CUDA math library's j0/y0/j1/y1 (FP64) above.
 //  * H_m, m >= 2: upward three-term recurrence H_{m+1} = (2m/x) H_m - H_{m-1}
 //    (DLMF 10.6.1), stable for the dominant Y part; the error of the J part
 //    stays at rounding level relative to |H_m|.
@@ -12,97 +12,128 @@
 #pragma once
 #include "qbx_internal.h"
 
-// Coefficients of the ascending series below, as compile-time constants:
-// j0 = 1/(k!)^2, j1 = 1/(k!(k+1)!), h = H_k = 1 + 1/2 + ... + 1/k,
-// y0 = H_k/(k!)^2, y1 = (psi(k+1) + psi(k+2))/(k!(k+1)!), psi(m) = -gamma + H_{m-1}.
+// Polynomial pieces of H_0 and H_1 below x = 8 (generated tables, see
+// gen_hankel_table.py): sixteen intervals of [2, 8), eight per octave, with
+// degree-D Chebyshev fits of J_0, Y_0, J_1, Y_1 in t in [-1, 1], and the
+// ascending series (DLMF 10.2.2, 10.8.1) economised to degree D on
+// u = -x^2/4 in [-1, 0] for x < 2. D = 10 for the FP64 path (truncation below
+// 1e-16 of |H_0|, |H_1|), 8 for the mixed path (below 1e-13).
+#include "hankel_table.h"
 constexpr double kEulerGamma = 0.57721566490153286061;
-template <int K>
-struct SeriesCoef {
-  static constexpr double j0 = SeriesCoef<K - 1>::j0 / ((double)K * (double)K);
-  static constexpr double j1 = SeriesCoef<K - 1>::j1 / ((double)K * (double)(K + 1));
-  static constexpr double h = SeriesCoef<K - 1>::h + 1.0 / (double)K;
-  static constexpr double y0 = h * j0;
-  static constexpr double y1 = (-2.0 * kEulerGamma + h + (h + 1.0 / (double)(K + 1))) * j1;
+constexpr double kTwoOverPi = 0.63661977236758134308;
+
+template <bool WIDE>
+struct HankTab;
+template <>
+struct HankTab<false> {
+  static constexpr int D = kHankDeg64;
+  __device__ static const double2* tab() { return kHankTab64; }
+  __device__ static double ser(int d, int f) { return kHankSer64[d][f]; }
 };
 template <>
-struct SeriesCoef<0> {
-  static constexpr double j0 = 1.0, j1 = 1.0, h = 0.0, y0 = 0.0;
-  static constexpr double y1 = -2.0 * kEulerGamma + 1.0;
+struct HankTab<true> {
+  static constexpr int D = kHankDegMx;
+  __device__ static const double2* tab() { return kHankTabMx; }
+  __device__ static double ser(int d, int f) { return kHankSerMx[d][f]; }
 };
 
-// Horner steps k = K, K-1, ..., 0 for the four polynomials in u.
-template <int K>
-struct SeriesHorner {
-  __device__ __forceinline__ static void run(double u, double& pj0, double& pj1, double& py0,
-                                             double& py1) {
-    pj0 = fma(pj0, u, SeriesCoef<K>::j0);
-    pj1 = fma(pj1, u, SeriesCoef<K>::j1);
-    py0 = fma(py0, u, SeriesCoef<K>::y0);
-    py1 = fma(py1, u, SeriesCoef<K>::y1);
-    SeriesHorner<K - 1>::run(u, pj0, pj1, py0, py1);
-  }
-};
-template <>
-struct SeriesHorner<-1> {
-  __device__ __forceinline__ static void run(double, double&, double&, double&, double&) {}
-};
-
-// H_0 and H_1 from the ascending series (DLMF 10.2.2 for J, DLMF 10.8.1 for
-// Y), in u = -x^2/4:
-//   J0 = sum u^k / (k!)^2,            J1 = (x/2) sum u^k / (k! (k+1)!),
-//   Y0 = (2/pi)(ln(x/2) + gamma) J0 - (2/pi) sum_{k>=1} H_k u^k / (k!)^2,
-//   Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (x/(2 pi)) sum (psi(k+1) + psi(k+2)) u^k / (k! (k+1)!),
-// each sum a polynomial in u of degree KTOP evaluated by Horner's rule (one
-// FMA per term). The truncation error falls below rounding for x < 2 at
-// KTOP = 14, x < 5 at 18 and x < 8 at 20; beyond x = 2 the sums cancel (their
-// terms add up to about I_0(x)), which bounds the error relative to |H_0|,
-// |H_1| by 1e-14 for x < 5 and 3e-13 for x < 8 (checked against the library's
-// j0/y0/j1/y1 by tests/test_special_gpu.py).
-// ix = 1/x is passed in (callers get it from one reciprocal square root of r^2).
-template <int KTOP>
-__device__ __forceinline__ void hankel01_series_n(double x, double ix, cd& h0, cd& h1) {
-  constexpr double kTwoOverPi = 0.63661977236758134308;
-  const double u = -0.25 * x * x;
-  double pj0 = SeriesCoef<KTOP>::j0, pj1 = SeriesCoef<KTOP>::j1;
-  double py0 = SeriesCoef<KTOP>::y0, py1 = SeriesCoef<KTOP>::y1;
-  SeriesHorner<KTOP - 1>::run(u, pj0, pj1, py0, py1);
+// The logarithmic terms of the ascending series: from the four series sums
+// J0, P1 = J1 / (x/2), R0, R1 in u = -x^2/4,
+//   Y0 = (2/pi)((ln(x/2) + gamma) J0 - R0),
+//   Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (x/(2 pi)) R1.
+template <bool NEED0, bool NEED1>
+__device__ __forceinline__ void hankel01_from_series(double x, double ix, double j0s, double r0s,
+                                                     double p1s, double r1s, cd& h0, cd& h1) {
   const double lx = log(0.5 * x);
-  const double J0 = pj0, J1 = 0.5 * x * pj1;
-  const double Y0 = kTwoOverPi * ((lx + kEulerGamma) * J0 - py0);
-  const double Y1 = -kTwoOverPi * ix + kTwoOverPi * lx * J1 - (0.5 * x) * (0.5 * kTwoOverPi) * py1;
-  h0 = mk(J0, Y0);
-  h1 = mk(J1, Y1);
+  if (NEED0) h0 = mk(j0s, kTwoOverPi * ((lx + kEulerGamma) * j0s - r0s));
+  if (NEED1) {
+    const double J1 = 0.5 * x * p1s;
+    h1 = mk(J1, -kTwoOverPi * ix + kTwoOverPi * lx * J1 - (0.5 * x) * (0.5 * kTwoOverPi) * r1s);
+  }
 }
 
-__device__ __forceinline__ void hankel01_series(double x, double ix, cd& h0, cd& h1) {
-  hankel01_series_n<14>(x, ix, h0, h1);
-}
-__device__ __forceinline__ void hankel01_series(double x, cd& h0, cd& h1) {
-  hankel01_series_n<14>(x, 1.0 / x, h0, h1);
+// H_0, H_1 at 0 < x < 8 from the tables: each lane evaluates its own row (its
+// interval, or the series row below 2) by Horner's rule, two FMAs per degree
+// for each function read; lanes on the series row add the logarithmic terms.
+template <bool WIDE, bool NEED0, bool NEED1>
+__device__ __forceinline__ void hankel01_table(double x, double ix, cd& h0, cd& h1) {
+  using T = HankTab<WIDE>;
+  const bool small = x < 2.0;
+  // interval row from the bit fields of x in [2, 8): 8 (E - 1) + top three
+  // mantissa bits; t = 16 x / 2^E - 17 - 2 j
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const int ej = (int)((hi >> 17) & 0x3FFFu) - (1024 << 3);
+  const int row = small ? kHankSeriesRow : ej;
+  // (16 / 2^E and -(17 + 2 j) built from their bit fields: no conversion
+  // instruction; u = x (-x/4) on the series row)
+  const double a = small ? -0.25 * x
+                         : __hiloint2double((int)((2050u - ((hi >> 20) & 0x7FFu)) << 20), 0);
+  const double b = small ? 0.0
+                         : __hiloint2double((int)(0x80000000u | (1027u << 20) |
+                                                  ((unsigned)(1 + 2 * (ej & 7)) << 16)),
+                                            0);
+  const double v = fma(x, a, b);
+  const double2* tb = T::tab() + row;
+  double2 c0 = make_double2(0.0, 0.0), c1 = c0;
+  if (NEED0) c0 = tb[(2 * T::D) * kHankRows];
+  if (NEED1) c1 = tb[(2 * T::D + 1) * kHankRows];
+#pragma unroll
+  for (int d = T::D - 1; d >= 0; --d) {
+    if (NEED0) {
+      const double2 k0 = tb[(2 * d) * kHankRows];
+      c0 = make_double2(fma(c0.x, v, k0.x), fma(c0.y, v, k0.y));
+    }
+    if (NEED1) {
+      const double2 k1 = tb[(2 * d + 1) * kHankRows];
+      c1 = make_double2(fma(c1.x, v, k1.x), fma(c1.y, v, k1.y));
+    }
+  }
+  if (small) {
+    hankel01_from_series<NEED0, NEED1>(x, ix, c0.x, c0.y, c1.x, c1.y, h0, h1);
+  } else {
+    if (NEED0) h0 = mk(c0.x, c0.y);
+    if (NEED1) h1 = mk(c1.x, c1.y);
+  }
 }
 
-// Series reach of hankel01 (FP64 accuracy) and of hankel01_wide (relative
-// error below 3e-13, for the mixed-precision path whose Hankel values are
-// rounded to FP32 after the FP64 recurrence).
-constexpr double kSeriesMax = 5.0, kSeriesMaxWide = 8.0;
+// H_0, H_1 from the series row alone (every lane of the warp below x = 2): the
+// coefficients are warp-uniform constants.
+template <bool WIDE, bool NEED0, bool NEED1>
+__device__ __forceinline__ void hankel01_series_row(double x, double ix, cd& h0, cd& h1) {
+  using T = HankTab<WIDE>;
+  const double u = -0.25 * x * x;
+  double j0s = T::ser(T::D, 0), r0s = T::ser(T::D, 1), p1s = T::ser(T::D, 2), r1s = T::ser(T::D, 3);
+#pragma unroll
+  for (int d = T::D - 1; d >= 0; --d) {
+    if (NEED0) {
+      j0s = fma(j0s, u, T::ser(d, 0));
+      r0s = fma(r0s, u, T::ser(d, 1));
+    }
+    if (NEED1) {
+      p1s = fma(p1s, u, T::ser(d, 2));
+      r1s = fma(r1s, u, T::ser(d, 3));
+    }
+  }
+  hankel01_from_series<NEED0, NEED1>(x, ix, j0s, r0s, p1s, r1s, h0, h1);
+}
 
-// H_0, H_1 at x > 0. The lanes of a warp usually see arguments of one range:
-// when all of them are below 2 the short series serves all, otherwise the
-// longer one serves every lane below the series reach (one path, not two),
-// and the library's j0/y0/j1/y1 the rest.
-// NEED0 / NEED1: whether the caller reads h0 / h1 (the library calls of the
-// other are skipped; the series parts it does not read are dead code).
+// Reach of the tables; the CUDA math library's j0/y0/j1/y1 serve x >= 8.
+constexpr double kTableMax = 8.0;
+
+// H_0, H_1 at x > 0. When every lane of the warp is below 2 the series row
+// serves all with uniform coefficients; otherwise each lane below 8 reads its
+// own table row, and the library serves the rest.
+// WIDE: the mixed path's lower-degree tables (relative error below 2e-13).
+// NEED0 / NEED1: whether the caller reads h0 / h1 (the other's polynomials
+// and library calls are skipped).
 template <bool WIDE, bool NEED0 = true, bool NEED1 = true>
 __device__ __forceinline__ void hankel01_any(double x, double ix, cd& h0, cd& h1) {
   if (__all_sync(__activemask(), x < 2.0)) {
-    hankel01_series_n<14>(x, ix, h0, h1);
+    hankel01_series_row<WIDE, NEED0, NEED1>(x, ix, h0, h1);
     return;
   }
-  if (x < (WIDE ? kSeriesMaxWide : kSeriesMax)) {
-    if (WIDE)
-      hankel01_series_n<20>(x, ix, h0, h1);
-    else
-      hankel01_series_n<18>(x, ix, h0, h1);
+  if (x < kTableMax) {
+    hankel01_table<WIDE, NEED0, NEED1>(x, ix, h0, h1);
     return;
   }
   if (NEED0) h0 = mk(j0(x), y0(x));
