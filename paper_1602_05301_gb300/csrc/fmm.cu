@@ -43,7 +43,6 @@ constexpr int kLeafThreads = 128;
 // rate is shared by its warps and a warp instruction costs the same with few
 // lanes active, so partly filled warps waste it (measured).
 constexpr int kChunk = 32;
-constexpr double kRescale = 1e100;
 // Leaves holding a centre are at least this many expansion radii wide.
 constexpr double kLeafOverRadius = 4.0;
 // A W-list box c is translated to a centre z (M2QBXL) only if
@@ -97,6 +96,7 @@ struct Fmm {
   cd* lpq;               // [n_coef] leaf cos/sin coefficients of L2P (see unscale_leaf_locals_kernel)
   const double* conv;    // [n_levels][pbmax + 1] s^j / sig_j (mixed path)
   const double* lsig;    // [n_levels][pbmax + 1] log sig_j
+  const double* isig;    // [n_levels][pbmax + 2] 1 / sig_min(j, pb) (mixed P2M)
   const double2* sigr;   // [n_levels][pbmax + 2] (sig_{j-1} / sig_j, sig_{j+1} / sig_j)
   double k, ik, side;    // wavenumber, 1 / k, root box side
   int pbmax, p, n_levels, has_S, has_D;
@@ -121,17 +121,19 @@ __device__ double miller_row(double x, int M, double* row, int stride) {
     return 1.0;
   }
   const double inv = 2.0 / x;
-  const int N = miller_start(M, x);
-  double fn1 = 0.0, fn = 1e-200, sum = 0.0;
-  for (int i = 0; i <= M; ++i) row[i * stride] = 0.0;
+  const int N = miller_start(M, x);  // > M + 1: every row entry is written
+  double fn1 = 0.0, fn = 0x1p-600, sum = 0.0, dn = (double)N;
   for (int n = N; n >= 1; --n) {
-    const double fm = (double)n * inv * fn - fn1;
+    const double fm = fma(dn * inv, fn, -fn1);  // f_{n-1} = (2n/x) f_n - f_{n+1}
+    dn -= 1.0;
     if ((n & 1) == 0) sum += fn;
     if (n - 1 <= M) row[(n - 1) * stride] = fm;
     fn1 = fn;
     fn = fm;
-    if (fabs(fn) > kRescale) {
-      const double sc = 1.0 / kRescale;
+    // rescale by 2^-332 (exact) once |f| reaches 2^332: an integer test on the
+    // exponent field
+    if ((__double2hiint(fn) & 0x7FFFFFFF) >= (1355 << 20)) {
+      const double sc = 0x1p-332;
       fn *= sc;
       fn1 *= sc;
       sum *= sc;
@@ -1425,33 +1427,47 @@ __global__ void __launch_bounds__(kThreads) m2p_pair_mixed_kernel(
 
 // ---------------------------------------------------------------- P2M in mixed precision
 // The item structure of p2m_item_kernel with the sums in FP32: the rows
-// R_t = conj(V_t) / sig_|t| (the FP64 Miller recurrence and angular factors,
-// each entry rounded to FP32 once; stored in the first half of each 16-byte
-// row slot) and, over the item's sources with Kahan compensation,
+// R_t = conj(V_t) / sig_|t| (the FP64 Miller recurrence, FP32 from the
+// normalisation on; stored in the first half of each 16-byte row slot) and,
+// over the item's sources with Kahan compensation,
 //   mu_n = sum_j [q_j R_n + A_j R_{n-1} sig_|n-1| / sig_|n| - B_j R_{n+1} sig_|n+1| / sig_|n|],
 // A = d (k/2) conj(nu), B = d (k/2) nu; mu_n = a_n / sig_|n|, of order one.
 // p2m_sum_mixed_kernel adds a leaf's segments in FP64 and forms mh_n = mu_n /
 // conv_|n| (conv = s^j / sig_j).
-__device__ __forceinline__ void p2m_fill_row_mixed(const Fmm& F, int i, double2 m, double is,
-                                                   int l, int pb, cd* row, cd& sq, cd& sa,
-                                                   cd& sb) {
+__device__ __forceinline__ void p2m_fill_row_mixed(const Fmm& F, int i, double2 m, int l, int pb,
+                                                   cd* row, cd& sq, cd& sa, cd& sb) {
   const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
-  const double rr = sqrt(dx * dx + dy * dy);
-  const double norm = miller_row(F.k * rr, pb + 1, (double*)row, 2);
-  const double* cv = F.conv + (size_t)l * (F.pbmax + 1);
-  const cd em = rr > 0.0 ? mk(dx / rr, -dy / rr) : mk(1.0, 0.0);  // e^{-i th}
-  cd e = mk(1.0, 0.0);
-  double f = 1.0 / norm;  // 1 / (norm s^j)
+  const double d2 = dx * dx + dy * dy;
+  const bool at_centre = (__double2hiint(d2) | __double2loint(d2)) == 0;
+  const double ir = at_centre ? 0.0 : rsqrt(d2);
+  const double norm = miller_row(F.k * (d2 * ir), pb + 1, (double*)row, 2);
+  // R_j = J_j / sig_j e^{-i j th} = row_j / (norm sig_j) e^{-i j th}: row_j / sig_j
+  // in FP64 (one product), the factor 2^-e of norm = mn 2^e as an exponent offset
+  // in the FP32 rounding, 1 / mn and the angular factor in FP32
+  const double* isg = F.isig + (size_t)l * (F.pbmax + 2);
+  const int en = (int)((__double2hiint(norm) >> 20) & 0x7FF) - 1023;
+  const float imn = 1.0f / f32_from_f64_sh(norm, -en);
+  // e^{-i j th}: FP64 anchors every eighth order (e^{-8 i th} by three
+  // squarings), FP32 products in between
+  const cd em = at_centre ? mk(1.0, 0.0) : mk(dx * ir, -dy * ir);
+  cd e8 = cmul(em, em);
+  e8 = cmul(e8, e8);
+  e8 = cmul(e8, e8);
+  const float2 emf = f2(em);
+  cd E = mk(1.0, 0.0);
+  float2 ef = make_float2(1.f, 0.f);
   for (int j = 0; j <= pb + 1; ++j) {
-    // f conv_j = 1 / (norm sig_j); order pb + 1 enters only as sig_pb-normalised
-    // (its factor sig_|pb+1| / sig_|pb| is taken as 1 below)
-    const double sc = j <= pb ? cv[j] : cv[pb] / is;
-    const double v = row[j].x * f * sc;
-    const cd c = cscale(e, v);                    // R_j
-    reinterpret_cast<float2*>(row + j)[0] = f2(c);
-    if (j > 0) reinterpret_cast<float2*>(row - j)[0] = (j & 1) ? f2(mk(-c.x, c.y)) : f2(mk(c.x, -c.y));
-    e = cmul(e, em);
-    f *= is;
+    if ((j & 7) == 0) {
+      ef = f2(E);
+      E = cmul(E, e8);
+    } else {
+      ef = fmul(ef, emf);
+    }
+    const float v = f32_from_f64_sh(row[j].x * isg[j], -en) * imn;
+    const float2 c = make_float2(ef.x * v, ef.y * v);  // R_j
+    reinterpret_cast<float2*>(row + j)[0] = c;
+    if (j > 0) reinterpret_cast<float2*>(row - j)[0] = (j & 1) ? make_float2(-c.x, c.y)
+                                                                : make_float2(c.x, -c.y);
   }
   const float4 ab = F.ab32[i];
   reinterpret_cast<float2*>(&sq)[0] = F.q32[i];
@@ -1473,10 +1489,9 @@ __global__ void __launch_bounds__(kThreads) p2m_item_mixed_kernel(
   cd* sq = rows + chunk * RW;             // [chunk]
   cd* sa = sq + chunk;                    // [chunk]
   cd* sb = sa + chunk;                    // [chunk]
-  const double is = 1.0 / F.scale[l];
   if ((int)threadIdx.x < it.w) {
     const int j = threadIdx.x;
-    p2m_fill_row_mixed(F, src[it.z + j], F.centre[src_leaf[it.z + j]], is, l, pb,
+    p2m_fill_row_mixed(F, src[it.z + j], F.centre[src_leaf[it.z + j]], l, pb,
                        rows + j * RW + (pb + 1), sq[j], sa[j], sb[j]);
   }
   __syncthreads();
@@ -2127,7 +2142,7 @@ Fmm make_view(qbx_handle* h, FmmPlan* f, bool S, bool D) {
   F.scale = f->scale.ptr; F.pw = f->pw.ptr; F.ipw = f->ipw.ptr;
   F.t_m2l = f->t_m2l.ptr; F.t_m2m = f->t_m2m.ptr; F.t_l2l = f->t_l2l.ptr;
   F.mpole = f->mpole.ptr; F.local = f->local.ptr; F.lpq = f->lpq.ptr;
-  F.conv = f->conv.ptr; F.lsig = f->lsig.ptr; F.sigr = f->sigr.ptr;
+  F.conv = f->conv.ptr; F.lsig = f->lsig.ptr; F.isig = f->isig.ptr; F.sigr = f->sigr.ptr;
   F.k = h->k; F.ik = 1.0 / h->k; F.side = f->side; F.pbmax = f->pb_max; F.p = h->p; F.n_levels = f->n_levels;
   F.has_S = S ? 1 : 0; F.has_D = D ? 1 : 0;
   return F;

@@ -28,19 +28,24 @@ constexpr int kT = 128;
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
 
-// per level: lsig[j] = log sig_j, conv[j] = s^j / sig_j  (j = 0..pb_l; stride pbmax + 1)
+// per level: lsig[j] = log sig_j, conv[j] = s^j / sig_j  (j = 0..pb_l; stride
+// pbmax + 1), isig[j] = 1 / sig_min(j, pb_l) (j = 0..pb_l + 1; stride pbmax + 2)
 __global__ void sigma_tables_kernel(int n_levels, int pbmax, const int* __restrict__ lpb,
                                     double k, double side, const double* __restrict__ scale,
-                                    double* __restrict__ lsig, double* __restrict__ conv) {
+                                    double* __restrict__ lsig, double* __restrict__ conv,
+                                    double* __restrict__ isig) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_levels) return;
   const double x = k * side / (double)(1 << l);
   const double ls = log(scale[l]);
+  double v = 0.0;
   for (int j = 0; j <= lpb[l]; ++j) {
-    const double v = fmin(0.0, j * log(0.5 * x) - lgamma((double)j + 1.0));
+    v = fmin(0.0, j * log(0.5 * x) - lgamma((double)j + 1.0));
     lsig[(size_t)l * (pbmax + 1) + j] = v;
     conv[(size_t)l * (pbmax + 1) + j] = exp(j * ls - v);
+    isig[(size_t)l * (pbmax + 2) + j] = exp(-v);
   }
+  isig[(size_t)l * (pbmax + 2) + lpb[l] + 1] = exp(-v);
 }
 
 // Recurrence factors of G_m = sig_m H_m on level l (mixed M2P):
@@ -622,8 +627,9 @@ qbx_status mixed_plan_build(qbx_handle* h, FmmPlan* f) {
   const int pbm = f->pb_max;
   QBX_CUDA_TRY(f->lsig.alloc((size_t)f->n_levels * (pbm + 1)));
   QBX_CUDA_TRY(f->conv.alloc((size_t)f->n_levels * (pbm + 1)));
+  QBX_CUDA_TRY(f->isig.alloc((size_t)f->n_levels * (pbm + 2)));
   sigma_tables_kernel<<<1, 64>>>(f->n_levels, pbm, f->lpb.ptr, h->k, f->side, f->scale.ptr,
-                                 f->lsig.ptr, f->conv.ptr);
+                                 f->lsig.ptr, f->conv.ptr, f->isig.ptr);
   QBX_CUDA_TRY(cudaGetLastError());
   QBX_CUDA_TRY(f->m2p_rec.alloc((size_t)f->n_levels * (pbm + 2)));
   m2p_rec_kernel<<<f->n_levels, 128>>>(f->n_levels, pbm, f->lpb.ptr, f->lsig.ptr, f->m2p_rec.ptr);

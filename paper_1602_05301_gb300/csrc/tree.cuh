@@ -154,6 +154,7 @@ struct FmmPlan {
   DevBuf<int> err;                      // device error flags
   // mixed precision (sigma-normalised FP32 M2L)
   DevBuf<double> lsig, conv;            // [n_levels][pb_max+1] log sig_j, s^j / sig_j
+  DevBuf<double> isig;                  // [n_levels][pb_max+2] 1 / sig_min(j, pb) (mixed P2M)
   DevBuf<float2> tm_f32;                // per level l >= 2: [49][Q_l][Q_l] M2L matrices
   std::vector<long long> h_tm_off;      // [n_levels] offset of level l's matrices
   // M2L as batched GEMMs: V entries grouped by (level, offset class) into
