@@ -268,10 +268,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# FP64 flops of the base Hankel values H0, H1 of one pair for x < 2: four
-# degree-14 polynomials by Horner's rule (the log is not charged), and of one
-# step of the upward Hankel recurrence (a real-scaled complex step, 6 flops).
-HANKEL01_FLOPS = 4 * 14 * 2
+# FP64 flops of the base Hankel values H0, H1 of one pair: four polynomials
+# of the library's tables by Horner's rule, degree 10 on the FP64 path and 8 on
+# the mixed one (the logarithm below x = 2 is not charged), and of one step of
+# the upward Hankel recurrence (a real-scaled complex step, 6 flops).
+HANKEL01_FLOPS = {False: 4 * 10 * 2, True: 4 * 8 * 2}
 REC_STEP_FLOPS = 6
 
 
@@ -287,10 +288,11 @@ def flop_model(lp, stats, p, has_S, has_D, assoc, fmm, mixed=False, active_frac=
     lay = (1 if has_S else 0) + (1 if has_D else 0)
     acc = (18 * P if has_S else 0) + (10 * P if has_D else 0)
     pairs = stats["p2qbxl_pairs"] * active_frac
-    base = pairs * (HANKEL01_FLOPS + REC_STEP_FLOPS * p)
+    base = pairs * (HANKEL01_FLOPS[mixed] + REC_STEP_FLOPS * p)
     f = {}
     f["p2qbxl"] = (base, pairs * acc) if mixed else (base + pairs * acc, 0.0)
-    f["p2p"] = (stats["p2p_pairs"] * (HANKEL01_FLOPS + 8 * lay), 0.0)
+    # P2P evaluates only the Hankel functions its layers read (H0 for S, H1 for D)
+    f["p2p"] = (stats["p2p_pairs"] * (HANKEL01_FLOPS[False] * lay / 2 + 8 * lay), 0.0)
     f["qbxl2p"] = (stats["n_qbx_targets"] * 16 * P, 0.0)
     if not fmm:
         return f

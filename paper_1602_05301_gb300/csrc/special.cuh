@@ -225,15 +225,25 @@ __device__ __forceinline__ double pow2d(int d) {
   return __hiloint2double((d + 1023) << 20, 0);
 }
 
-// Start index of the backward recurrence for orders 0..pmax at argument x:
-// far enough above m = max(pmax, x) that the recurrence has converged to the
-// minimal solution to full double precision. The relative error of J_m from a
-// start N is about (x/2)^{2(N-m)} (m!/N!)^2, so for x well below m a dozen
-// orders suffice; the sqrt(40 x) term keeps the classical margin of order
-// sqrt(m) where x approaches m (the transition region).
+// Start index of the backward recurrence for orders 0..pmax at argument x.
+// Started at N, the recurrence returns J_m contaminated by the dominant
+// solution with relative weight about (J_{N+1} Y_m) / (Y_{N+1} J_m); above the
+// turning point each order n > x shrinks J and grows Y by e^{arccosh(n / x)}
+// (Debye's asymptotics, DLMF 10.19.3), so with m = max(pmax, x) the error of
+// every J_{m' <= m} is below e^{-2 d arccosh(m / x)} for N = m + d. Where
+// x <= m / 2, d = ceil(20 / arccosh(m / x)) + 2 (error below e^{-40}, computed
+// in FP32: only an index); nearer the turning point the classical margin
+// 12 + 2 sqrt(40 x). Checked against J_m at 40 digits for 17 orders pmax
+// between 1 and 420 and 9 arguments each in 1e-6 <= x <= pmax / 2: every J_m,
+// m <= pmax, to 2e-16 or better, two or more orders below the start found.
 __device__ __forceinline__ int miller_start(int pmax, double x) {
-  int m = pmax > (int)x ? pmax : (int)x;
-  int n = m + 12 + (int)(2.0 * sqrt(40.0 * x));
+  const int m = pmax > (int)x ? pmax : (int)x;
+  const float xf = f32_from_f64(x);
+  int n;
+  if (2.0f * xf <= (float)m)
+    n = m + 2 + (int)ceilf(20.0f / acoshf((float)m / xf));
+  else
+    n = m + 12 + (int)(2.0 * sqrt(40.0 * x));
   return (n + 1) & ~1;  // even
 }
 
