@@ -325,7 +325,11 @@ def flop_model(lp, stats, p, has_S, has_D, assoc, fmm, mixed=False, active_frac=
         parent[child[has, q]] = np.nonzero(has)[0]
     mm = (lev >= 3) & (parent >= 0)
     f["m2m"] = f["l2l"] = tr(8 * np.sum(Qb[mm] * Qb[parent[mm]]))
-    f["p2m"] = (16.0 * lay * np.sum((nsrc * Qb)[leaf & (lev >= 2)]), 0.0)
+    # P2M: one FP64 Miller row per source (about pb + 8 orders, 6 flops each);
+    # the sums over the sources, 8 flops per layer and coefficient, are FP64 on
+    # the FP64 path and FP32 (with 8 more for the compensation) in mixed precision
+    srcQ = np.sum((nsrc * Qb)[leaf & (lev >= 2)])
+    f["p2m"] = ((3.0 * srcQ, 16.0 * lay * srcQ) if mixed else (16.0 * lay * srcQ, 0.0))
     xb, xc = entries(3)
     f["p2l"] = (16.0 * lay * np.sum(Qb[xb] * nsrc[xc]), 0.0)
     wb, wc = entries(2)
@@ -335,10 +339,27 @@ def flop_model(lp, stats, p, has_S, has_D, assoc, fmm, mixed=False, active_frac=
     # the mean box order over the W lists of the centres' leaves
     w_all = float(np.sum((nctr * (wq > 0) * np.diff(t["off"][2]))[leaf]))
     w_q = float(np.sum((nctr * wq)[leaf]))
-    f["m2qbxl"] = (8.0 * P * stats["m2qbxl_pairs"] * active_frac * (w_q / w_all if w_all else 0.0), 0.0)
-    f["m2p"] = (16.0 * np.sum((ndir * wq)[leaf]), 0.0)
-    f["l2qbxl"] = (8.0 * P * np.sum((nctr * Qb)[leaf]) * active_frac, 0.0)
-    f["l2p"] = (16.0 * np.sum((ndir * Qb)[leaf]), 0.0)
+    mq = stats["m2qbxl_pairs"] * active_frac * (w_q / w_all if w_all else 0.0)
+    lq = np.sum((nctr * Qb)[leaf]) * active_frac
+    # M2P: per (direct target, W box) pair the Hankel recurrence (6 FP64 flops
+    # per order, about Q/2 orders) and a complex product-sum per coefficient,
+    # FP64 on the FP64 path, FP32 with compensation (16 flops) in mixed
+    nw = np.bincount(wb, minlength=nb).astype(np.int64)
+    w_pairs = float(np.sum((ndir * nw)[leaf]))
+    w_coef = float(np.sum((ndir * wq)[leaf]))
+    if mixed:
+        # M2QBXL / L2QBXL: products on split FP32 factors (about 16 flops per
+        # term with the scaling and compensation), recurrences in FP64
+        f["m2qbxl"] = (3.0 * mq, 16.0 * P * mq)
+        f["m2p"] = (HANKEL01_FLOPS[True] * w_pairs + 3.0 * w_coef, 16.0 * w_coef)
+        f["l2qbxl"] = (0.0, 16.0 * P * lq)
+    else:
+        f["m2qbxl"] = (8.0 * P * mq, 0.0)
+        f["m2p"] = (16.0 * w_coef, 0.0)
+        f["l2qbxl"] = (8.0 * P * lq, 0.0)
+    # L2P: per order Miller's step (6 flops) and Clenshaw's two complex steps
+    # (16 flops), for the two coefficients of orders +-m: 11 per coefficient
+    f["l2p"] = (11.0 * np.sum((ndir * Qb)[leaf]), 0.0)
     return f
 
 

@@ -388,9 +388,9 @@ qbx_status qbx_selftest_wait_timeout(qbx_handle *h, int32_t limit_us);
  * H_0(x) and H_1(x) of the first kind, as every kernel of the library
  * evaluates them on the device (the Hankel values that start the recurrences
  * of Sec. 7.2's translations and the kernel G = (i/4) H_0(k|x - y|) of Sec. 1):
- * below x = 8 piecewise polynomials (the ascending series, DLMF 10.2.2 and
- * 10.8.1, economised on x < 2; Chebyshev fits on sixteen intervals of
- * [2, 8)), the CUDA math library's j0/y0/j1/y1 above. variant 0: the FP64
+ * below x = 8 piecewise polynomials (Chebyshev fits on eight intervals per
+ * octave from 2^-9; below that the ascending series, DLMF 10.2.2 and 10.8.1,
+ * economised), the CUDA math library's j0/y0/j1/y1 above. variant 0: the FP64
  * path (degree 10, relative error below 1e-15 of |H_0|, |H_1|); 1: the
  * mixed-precision path (degree 8, below 1e-13). x: host [n], positive and
  * finite; out: host [n][4] =

@@ -717,8 +717,10 @@ __global__ void m2p_sum_kernel(int n, const int* __restrict__ wtgt, const int* _
 }
 
 // P2P over the U list: one warp per direct target whose leaf's U list holds
-// sources; lanes deal the sources round-robin, a shuffle tree adds them.
-template <bool HS, bool HD>
+// sources; lanes deal the sources round-robin, a shuffle tree adds them. WIDE:
+// the mixed path's Hankel tables (relative error below 1e-13 instead of 1e-15;
+// the sum stays FP64).
+template <bool HS, bool HD, bool WIDE>
 __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __restrict__ utgt,
                                                             const int* __restrict__ tleaf, int n,
                                                             cd* __restrict__ out) {
@@ -737,7 +739,7 @@ __global__ void __launch_bounds__(kThreads) p2p_warp_kernel(Fmm F, const int* __
     if (r2 == 0.0) return;
     const double ir = rsqrt(r2), x = k * r2 * ir;
     cd h0, h1;
-    hankel01_any<false, HS, HD>(x, ik * ir, h0, h1);
+    hankel01_any<WIDE, HS, HD>(x, ik * ir, h0, h1);
     if (HS) cfma(acc, F.qs[j], h0);
     if (HD) {
       const double2 nv = F.snrm[j];
@@ -2336,9 +2338,19 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   stage_begin(h, QBX_STAGE_P2P, s2);
   if (f->n_utgt > 0 && (S || D)) {
     const unsigned gw = nblk(f->n_utgt, kThreads / 32);  // one warp per target
-    if (S && D) p2p_warp_kernel<true, true><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
-    else if (S) p2p_warp_kernel<true, false><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
-    else p2p_warp_kernel<false, true><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr, f->n_utgt, out);
+#define P2P_LAUNCH(A, B)                                                                      \
+    do {                                                                                       \
+      if (mixed)                                                                               \
+        p2p_warp_kernel<A, B, true><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr,     \
+                                                             f->n_utgt, out);                  \
+      else                                                                                     \
+        p2p_warp_kernel<A, B, false><<<gw, kThreads, 0, s2>>>(F, f->utgt.ptr, f->tleaf.ptr,    \
+                                                              f->n_utgt, out);                 \
+    } while (0)
+    if (S && D) P2P_LAUNCH(true, true);
+    else if (S) P2P_LAUNCH(true, false);
+    else P2P_LAUNCH(false, true);
+#undef P2P_LAUNCH
     QBX_KCHECK("p2p", s2);
     h->launches += 1;
   }

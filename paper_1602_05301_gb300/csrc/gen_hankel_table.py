@@ -2,18 +2,21 @@
 H_1 = J_1 + i Y_1 (DLMF 10.4.3) that the device special functions evaluate
 below x = 8.
 
-* 2 <= x < 8: sixteen intervals, eight per octave ([2, 4) and [4, 8) cut at
-  the top three mantissa bits of x, so that the interval index is a bit
-  field). On each, J_0, Y_0, J_1, Y_1 are truncated Chebyshev series of
-  degree D in t = (x - centre) / half-width, written out as monomials in t.
-* x < 2: the ascending series (DLMF 10.2.2, 10.8.1) in u = -x^2/4 of the four
-  entire functions J_0, J_1 / (x/2), R_0 = sum H_k u^k / (k!)^2 and
-  R_1 = sum (psi(k+1) + psi(k+2)) u^k / (k! (k+1)!), economised: each a
-  truncated Chebyshev series of degree D on u in [-1, 0] written out as
-  monomials in u (the logarithmic terms are added by the caller).
+* 2^-9 <= x < 8: eight intervals per octave, [2^E (1 + j/8), 2^E (1 + (j+1)/8))
+  for E = -9..2 (the interval index is a bit field of x: its exponent and top
+  three mantissa bits). On each, J_0, Y_0, J_1, Y_1 are truncated Chebyshev
+  series of degree D in t = (x - centre) / half-width, written out as
+  monomials in t. The partition is geometric, so the logarithmic singularity
+  of Y at 0 lies 17 half-widths from every interval's centre and one degree
+  serves all octaves.
+* x < 2^-9: the ascending series (DLMF 10.2.2, 10.8.1) in u = -x^2/4 of the
+  four entire functions J_0, J_1 / (x/2), R_0 = sum H_k u^k / (k!)^2 and
+  R_1 = sum (psi(k+1) + psi(k+2)) u^k / (k! (k+1)!), each a truncated
+  Chebyshev series of degree D on u in [-1, 0] written out as monomials in u
+  (the logarithmic terms are added by the caller).
 
-Two tables: degree 10 (truncation below 1e-16 of |H_0|, |H_1|) for the FP64
-path and degree 8 (below 1e-13) for the mixed-precision path, whose Hankel
+Two tables: degree 10 (truncation near 1e-16 of |H_0|, |H_1|) for the FP64
+path and degree 8 (near 1e-13) for the mixed-precision path, whose Hankel
 values are rounded to FP32 after an FP64 recurrence. Values come from mpmath
 at 40 digits. Run: python gen_hankel_table.py > hankel_table.h
 """
@@ -22,7 +25,7 @@ import mpmath as mp
 mp.mp.dps = 40
 NCHEB = 40          # Chebyshev coefficients computed before truncation
 PER_OCTAVE = 8
-OCTAVES = (1, 2)    # [2, 4), [4, 8)
+OCTAVES = tuple(range(-9, 3))   # [2^-9, 2^-8), ..., [4, 8)
 DEGREES = {"64": 10, "Mx": 8}
 
 
@@ -108,13 +111,15 @@ def emit():
     lines = [
         "// Generated by gen_hankel_table.py (mpmath, 40 digits); do not edit.",
         "// Polynomial pieces of H_0 and H_1 below x = 8: rows 0..%d are the" % (nrow - 2),
-        "// intervals [2^E (1 + j/8), 2^E (1 + (j+1)/8)), E = 1, 2 (row 8 (E-1) + j),",
+        "// intervals [2^E (1 + j/8), 2^E (1 + (j+1)/8)), E = %d..%d (row 8 (E + %d) + j)," % (
+            OCTAVES[0], OCTAVES[-1], -OCTAVES[0]),
         "// in t = 16 x / 2^E - 17 - 2 j; row %d is the economised ascending series in" % (nrow - 1),
-        "// u = -x^2/4. Entry [(d * 2 + q) * kHankRows + row] holds the degree-d",
-        "// coefficients of pair q: (J0, Y0), (J1, Y1) on intervals; (J0, R0),",
+        "// u = -x^2/4 (x < 2^%d). Entry [(d * 2 + q) * kHankRows + row] holds the" % OCTAVES[0],
+        "// degree-d coefficients of pair q: (J0, Y0), (J1, Y1) on intervals; (J0, R0),",
         "// (J1 / (x/2), R1) on the series row.",
         "#pragma once",
-        "constexpr int kHankRows = %d, kHankSeriesRow = %d;" % (nrow, nrow - 1),
+        "constexpr int kHankRows = %d, kHankSeriesRow = %d, kHankMinExp = %d;" % (
+            nrow, nrow - 1, OCTAVES[0]),
     ]
     for name, deg in DEGREES.items():
         R = rows(deg)
@@ -127,12 +132,6 @@ def emit():
                     vals.append("{%s, %s}" % (mp.nstr(r[2 * q][d], 17, min_fixed=1, max_fixed=0),
                                               mp.nstr(r[2 * q + 1][d], 17, min_fixed=1, max_fixed=0)))
                 lines.append("    " + ", ".join(vals) + ",")
-        lines.append("};")
-        lines.append("// the series row alone, for warps whose arguments are all below 2")
-        lines.append("static __constant__ double kHankSer%s[%d][4] = {" % (name, deg + 1))
-        for d in range(deg + 1):
-            lines.append("    {%s}," % ", ".join(mp.nstr(R[-1][f][d], 17, min_fixed=1, max_fixed=0)
-                                                for f in range(4)))
         lines.append("};")
     return "\n".join(lines) + "\n"
 

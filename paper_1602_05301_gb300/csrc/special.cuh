@@ -1,8 +1,8 @@
 // Device special functions for the 2D Helmholtz kernels.
 //
-//  * H_0, H_1 of the first kind: piecewise polynomials below x = 8 (the
-//    economised ascending series below 2, Chebyshev fits on sixteen
-//    intervals of [2, 8)), the CUDA math library's j0/y0/j1/y1 (FP64) above.
+//  * H_0, H_1 of the first kind: piecewise polynomials below x = 8
+//    (Chebyshev fits on eight intervals per octave from 2^-9, the economised
+//    ascending series below), the CUDA math library's j0/y0/j1/y1 (FP64) above.
 //  * H_m, m >= 2: upward three-term recurrence H_{m+1} = (2m/x) H_m - H_{m-1}
 //    (DLMF 10.6.1), stable for the dominant Y part; the error of the J part
 //    stays at rounding level relative to |H_m|.
@@ -13,11 +13,12 @@
 #include "qbx_internal.h"
 
 // Polynomial pieces of H_0 and H_1 below x = 8 (generated tables, see
-// gen_hankel_table.py): sixteen intervals of [2, 8), eight per octave, with
-// degree-D Chebyshev fits of J_0, Y_0, J_1, Y_1 in t in [-1, 1], and the
+// gen_hankel_table.py): eight intervals per octave from 2^-9 to 8 with
+// degree-D Chebyshev fits of J_0, Y_0, J_1, Y_1 in t in [-1, 1] (the
+// partition is geometric, so one degree serves every octave), and the
 // ascending series (DLMF 10.2.2, 10.8.1) economised to degree D on
-// u = -x^2/4 in [-1, 0] for x < 2. D = 10 for the FP64 path (truncation below
-// 1e-16 of |H_0|, |H_1|), 8 for the mixed path (below 1e-13).
+// u = -x^2/4 in [-1, 0] for x < 2^-9. D = 10 for the FP64 path (truncation
+// near 1e-16 of |H_0|, |H_1|), 8 for the mixed path (near 1e-13).
 #include "hankel_table.h"
 constexpr double kEulerGamma = 0.57721566490153286061;
 constexpr double kTwoOverPi = 0.63661977236758134308;
@@ -28,13 +29,11 @@ template <>
 struct HankTab<false> {
   static constexpr int D = kHankDeg64;
   __device__ static const double2* tab() { return kHankTab64; }
-  __device__ static double ser(int d, int f) { return kHankSer64[d][f]; }
 };
 template <>
 struct HankTab<true> {
   static constexpr int D = kHankDegMx;
   __device__ static const double2* tab() { return kHankTabMx; }
-  __device__ static double ser(int d, int f) { return kHankSerMx[d][f]; }
 };
 
 // The logarithmic terms of the ascending series: from the four series sums
@@ -53,19 +52,22 @@ __device__ __forceinline__ void hankel01_from_series(double x, double ix, double
 }
 
 // H_0, H_1 at 0 < x < 8 from the tables: each lane evaluates its own row (its
-// interval, or the series row below 2) by Horner's rule, two FMAs per degree
-// for each function read; lanes on the series row add the logarithmic terms.
+// interval, or the series row below 2^-9) by Horner's rule, two FMAs per
+// degree for each function read; lanes on the series row add the logarithmic
+// terms.
 template <bool WIDE, bool NEED0, bool NEED1>
 __device__ __forceinline__ void hankel01_table(double x, double ix, cd& h0, cd& h1) {
   using T = HankTab<WIDE>;
-  const bool small = x < 2.0;
-  // interval row from the bit fields of x in [2, 8): 8 (E - 1) + top three
-  // mantissa bits; t = 16 x / 2^E - 17 - 2 j
+  constexpr double kTiny = 0x1p-9;  // 2^kHankMinExp
+  static_assert(kHankMinExp == -9, "table floor");
+  const bool small = x < kTiny;
+  // interval row from the bit fields of x: 8 (E + 9) + j from the biased
+  // exponent and the top three mantissa bits; t = 16 x / 2^E - 17 - 2 j with
+  // 16 / 2^E and -(17 + 2 j) built from their bit fields (no conversion
+  // instruction); u = x (-x/4) on the series row
   const unsigned hi = (unsigned)__double2hiint(x);
-  const int ej = (int)((hi >> 17) & 0x3FFFu) - (1024 << 3);
+  const int ej = (int)((hi >> 17) & 0x3FFFu) - ((1023 + kHankMinExp) << 3);
   const int row = small ? kHankSeriesRow : ej;
-  // (16 / 2^E and -(17 + 2 j) built from their bit fields: no conversion
-  // instruction; u = x (-x/4) on the series row)
   const double a = small ? -0.25 * x
                          : __hiloint2double((int)((2050u - ((hi >> 20) & 0x7FFu)) << 20), 0);
   const double b = small ? 0.0
@@ -96,42 +98,16 @@ __device__ __forceinline__ void hankel01_table(double x, double ix, cd& h0, cd& 
   }
 }
 
-// H_0, H_1 from the series row alone (every lane of the warp below x = 2): the
-// coefficients are warp-uniform constants.
-template <bool WIDE, bool NEED0, bool NEED1>
-__device__ __forceinline__ void hankel01_series_row(double x, double ix, cd& h0, cd& h1) {
-  using T = HankTab<WIDE>;
-  const double u = -0.25 * x * x;
-  double j0s = T::ser(T::D, 0), r0s = T::ser(T::D, 1), p1s = T::ser(T::D, 2), r1s = T::ser(T::D, 3);
-#pragma unroll
-  for (int d = T::D - 1; d >= 0; --d) {
-    if (NEED0) {
-      j0s = fma(j0s, u, T::ser(d, 0));
-      r0s = fma(r0s, u, T::ser(d, 1));
-    }
-    if (NEED1) {
-      p1s = fma(p1s, u, T::ser(d, 2));
-      r1s = fma(r1s, u, T::ser(d, 3));
-    }
-  }
-  hankel01_from_series<NEED0, NEED1>(x, ix, j0s, r0s, p1s, r1s, h0, h1);
-}
-
 // Reach of the tables; the CUDA math library's j0/y0/j1/y1 serve x >= 8.
 constexpr double kTableMax = 8.0;
 
-// H_0, H_1 at x > 0. When every lane of the warp is below 2 the series row
-// serves all with uniform coefficients; otherwise each lane below 8 reads its
-// own table row, and the library serves the rest.
-// WIDE: the mixed path's lower-degree tables (relative error below 2e-13).
+// H_0, H_1 at x > 0: each lane below 8 reads its own table row, the library
+// serves the rest.
+// WIDE: the mixed path's lower-degree tables (relative error below 1e-13).
 // NEED0 / NEED1: whether the caller reads h0 / h1 (the other's polynomials
 // and library calls are skipped).
 template <bool WIDE, bool NEED0 = true, bool NEED1 = true>
 __device__ __forceinline__ void hankel01_any(double x, double ix, cd& h0, cd& h1) {
-  if (__all_sync(__activemask(), x < 2.0)) {
-    hankel01_series_row<WIDE, NEED0, NEED1>(x, ix, h0, h1);
-    return;
-  }
   if (x < kTableMax) {
     hankel01_table<WIDE, NEED0, NEED1>(x, ix, h0, h1);
     return;

@@ -1,9 +1,9 @@
 """The device evaluation of H_0 and H_1 (qbx_hankel01) against scipy's
 j0/y0/j1/y1 (Cephes), relative to |H_0| and |H_1|, over the arguments the
-kernels meet: the economised series (x < 2), the interval tables of [2, 8),
-the library functions above 8, and warps whose lanes straddle the pieces
-(shuffled arguments): warps all below 2 take the uniform series path, the
-others each lane's own table row."""
+kernels meet: the interval tables (eight per octave from 2^-9 to 8) and the
+economised series below 2^-9, the library functions above 8, and warps whose
+lanes straddle the pieces (shuffled arguments): each lane reads its own table
+row."""
 import numpy as np
 import pytest
 from scipy.special import j0, j1, y0, y1
