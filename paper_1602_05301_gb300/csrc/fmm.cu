@@ -596,8 +596,10 @@ __global__ void __launch_bounds__(kThreads) l2p_kernel(Fmm F, const int* __restr
   const cd* g = F.local + F.eoff[b];
   const double2 m = F.centre[b];
   const double dx = F.txy[i].x - m.x, dy = F.txy[i].y - m.y;
-  const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-  const cd e1 = rr > 0.0 ? mk(dx / rr, dy / rr) : mk(1.0, 0.0);
+  const double d2 = dx * dx + dy * dy;
+  const bool at_centre = (__double2hiint(d2) | __double2loint(d2)) == 0;
+  const double ir = at_centre ? 0.0 : rsqrt(d2), x = F.k * (d2 * ir);
+  const cd e1 = at_centre ? mk(1.0, 0.0) : mk(dx * ir, dy * ir);
   // psi = sum_m f_m [g_m e^{-im th} + (m>0) (-1)^m g_{-m} e^{im th}] / norm
   cd acc;
   double norm;
@@ -686,18 +688,27 @@ __global__ void __launch_bounds__(kThreads) m2p_pair_kernel(Fmm F, const int* __
   const double s = F.scale[lc];
   const double2 mc = F.centre[c];
   const double dx = F.txy[i].x - mc.x, dy = F.txy[i].y - mc.y;
-  const double rr = sqrt(dx * dx + dy * dy), x = F.k * rr;
-  const cd e1 = mk(dx / rr, dy / rr);
+  // one reciprocal square root gives r, 1/r and 1/x: no division
+  const double d2 = dx * dx + dy * dy;
+  const double ir = rsqrt(d2), x = F.k * (d2 * ir), ix = ir * F.ik;
+  const cd e1 = mk(dx * ir, dy * ir);
   cd h0, h1;
-  hankel01(x, h0, h1);
+  hankel01(x, ix, h0, h1);
+  // Wh_m = s^m H_m: Wh_{m+1} = m c1 Wh_m - s^2 Wh_{m-1}, c1 = 2 s / x
+  const double c1 = 2.0 * s * ix, s2 = s * s;
   cd hm1 = h0, hm = cscale(h1, s), ee = mk(1.0, 0.0);
   cd sum = cmul(a[pb], h0);
+  double dm = 0.0;
   for (int m = 1; m <= pb; ++m) {
     ee = cmul(ee, e1);
-    cfma(sum, a[pb + m], cmul(hm, ee));
-    const cd v = cmul(hm, cconj(ee));
+    // Wh_m e^{i m th} and Wh_m e^{-i m th} from the same four products
+    const double rr_ = hm.x * ee.x, ii_ = hm.y * ee.y, ri_ = hm.x * ee.y, ir_ = hm.y * ee.x;
+    cfma(sum, a[pb + m], mk(rr_ - ii_, ri_ + ir_));
+    const cd v = mk(rr_ + ii_, ir_ - ri_);
     cfma(sum, a[pb - m], (m & 1) ? mk(-v.x, -v.y) : v);
-    const cd hn = csub(cscale(hm, 2.0 * m * s / x), cscale(hm1, s * s));
+    dm += 1.0;
+    const double cm = dm * c1;
+    const cd hn = mk(fma(cm, hm.x, -s2 * hm1.x), fma(cm, hm.y, -s2 * hm1.y));
     hm1 = hm;
     hm = hn;
   }
@@ -876,7 +887,20 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
   cd wp_prev = h0, wp_cur = w1;   // W_{m-1}, W_m
   cd wn_prev = h0, wn_cur = wm1;  // W_{-(m-1)}, W_{-m}
   const cd mB = mk(-B.x, -B.y);
-  double sgn = -1.0;              // (-1)^m
+  // H_{m+1} = (2m/x) H_m - H_{m-1} (two FMAs per component; 2m/x = dm ix2 with
+  // dm counted exactly); W_{m+1} = H_{m+1} e^{i(m+1)th} and
+  // W_{-(m+1)} = (-1)^{m+1} H_{m+1} e^{-i(m+1)th} from the same four products
+  double dm = 0.0;
+  auto step = [&](int m, cd& hnext, cd& enext, cd& wp, cd& wn) {
+    dm += 1.0;
+    const double cm = dm * ix2;
+    hnext = mk(fma(cm, hcur.x, -hprev.x), fma(cm, hcur.y, -hprev.y));
+    enext = cmul(ecur, e1);
+    const double rr_ = hnext.x * enext.x, ii_ = hnext.y * enext.y;
+    const double ri_ = hnext.x * enext.y, ir_ = hnext.y * enext.x;
+    wp = mk(rr_ - ii_, ri_ + ir_);
+    wn = (m & 1) ? mk(rr_ + ii_, ir_ - ri_) : mk(-(rr_ + ii_), ri_ - ir_);
+  };
 #pragma unroll
   for (int m = 1; m <= PM; ++m) {
     if (m > p) break;
@@ -885,10 +909,8 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
       cfma(acc[PM - m], q, wn_cur);
     }
     if (HD) {
-      const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
-      const cd enext = cmul(ecur, e1);
-      const cd wp_next = cmul(hnext, enext);
-      const cd wn_next = cscale(cmul(hnext, cconj(enext)), -sgn);
+      cd hnext, enext, wp_next, wn_next;
+      step(m, hnext, enext, wp_next, wn_next);
       cfma(acc[PM + m], A, wp_prev);
       cfma(acc[PM + m], mB, wp_next);
       cfma(acc[PM - m], A, wn_next);
@@ -901,15 +923,12 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
       wn_prev = wn_cur;
       wn_cur = wn_next;
     } else if (m < p) {
-      const cd hnext = csub(cscale(hcur, (double)m * ix2), hprev);
-      const cd enext = cmul(ecur, e1);
+      cd hnext, enext;
+      step(m, hnext, enext, wp_cur, wn_cur);
       hprev = hcur;
       hcur = hnext;
       ecur = enext;
-      wp_cur = cmul(hnext, enext);
-      wn_cur = cscale(cmul(hnext, cconj(enext)), -sgn);
     }
-    sgn = -sgn;
   }
 }
 
