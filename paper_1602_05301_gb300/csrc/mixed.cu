@@ -602,6 +602,150 @@ __global__ void __launch_bounds__(kT) m2m_f32_kernel(
   }
 }
 
+// Coarse levels (few parents, high orders) as split-K tile GEMMs: the two
+// kernels above give each thread one output column and the whole K range, so
+// a level of a few dozen boxes runs a few CTAs with K-long dependent chains.
+// Here a CTA of kT threads takes R parents and 32 output orders (chunk
+// blockIdx.y or blockIdx.z); warp w sums its quarter of K (M2M: child quadrant
+// w; L2L: the w-th quarter of the parent's orders) for the 32 orders, and the
+// four partial sums are added in FP64 in warp order (deterministic).
+constexpr int kSplitCols = 32, kSplitWarps = kT / 32;
+
+template <int R>
+__device__ __forceinline__ void split_reduce(float (&sr)[R], float (&si)[R], float (&cr)[R],
+                                             float (&ci)[R], float2* red, int warp, int lane,
+                                             double (&outr)[R], double (&outi)[R]) {
+  // red: [kSplitWarps][R][32]
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    red[(warp * R + r) * 32 + lane] = make_float2(sr[r] - cr[r], si[r] - ci[r]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kSplitWarps; ++w) {
+      const float2 v = red[(w * R + r) * 32 + lane];
+      a += (double)v.x;
+      b += (double)v.y;
+    }
+    outr[r] = a;
+    outi[r] = b;
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kT) m2m_f32_split_kernel(
+    int l, int pp, int pc, int pbmax, const int* __restrict__ parents, int nb,
+    const int* __restrict__ child, const long long* __restrict__ eoff,
+    const float2* __restrict__ Tmm, const double* __restrict__ conv, cd* __restrict__ mpole) {
+  extern __shared__ __align__(16) float2 mus4[];  // [4][Qc][stage_stride(R)], then red
+  __shared__ long long coff[4][R], poff[R];
+  const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
+  const int RS = stage_stride(R);
+  const int p0 = blockIdx.x * R, nr = min(R, nb - p0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* cvp = conv + (size_t)l * (pbmax + 1);
+  const double* cvc = conv + (size_t)(l + 1) * (pbmax + 1);
+  for (int idx = threadIdx.x; idx < 5 * R; idx += kT) {
+    const int r = idx % R, c = idx / R;
+    long long o = -1;
+    if (r < nr) {
+      if (c == 4) {
+        o = eoff[parents[p0 + r]];
+      } else {
+        const int d = child[4 * parents[p0 + r] + c];
+        if (d >= 0) o = eoff[d];
+      }
+    }
+    if (c == 4) poff[r] = o; else coff[c][r] = o;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 4 * Qc * R; idx += kT) {
+    const int c = idx / (Qc * R), rem = idx % (Qc * R), r = rem / Qc, n = rem % Qc;
+    float2 v = make_float2(0.f, 0.f);
+    const long long o = coff[c][r];
+    if (o >= 0) {
+      const cd a = mpole[o + n];
+      const double f = cvc[abs(n - pc)];
+      v = make_float2((float)(a.x * f), (float)(a.y * f));
+    }
+    mus4[((size_t)c * Qc + n) * RS + r] = v;
+  }
+  __syncthreads();
+  const int so = (int)blockIdx.y * kSplitCols + lane;
+  const bool act = so < Qp;
+  float sr[R], si[R], cr[R], ci[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
+  tile_gemm_column<R>(Tmm + (size_t)warp * Qc * Qp, Qp, Qc, mus4 + (size_t)warp * Qc * RS, so,
+                      act, sr, si, cr, ci);
+  __syncthreads();  // the staged rows are dead: the reduction reuses the space
+  double outr[R], outi[R];
+  split_reduce<R>(sr, si, cr, ci, mus4, warp, lane, outr, outi);
+  if (warp == 0 && act) {
+    const double f = 1.0 / cvp[abs(so - pp)];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r >= nr) break;
+      cd* dst = mpole + poff[r] + so;
+      dst->x = outr[r] * f;
+      dst->y = outi[r] * f;
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kT) l2l_f32_split_kernel(
+    int l, int pp, int pc, int pbmax, const int* __restrict__ parents, int nb,
+    const int* __restrict__ child, const long long* __restrict__ eoff,
+    const float2* __restrict__ Tl, const double* __restrict__ conv, cd* __restrict__ local) {
+  extern __shared__ __align__(16) float2 lam2[];  // [Qp][stage_stride(R)], then red
+  const int Qp = 2 * pp + 1, Qc = 2 * pc + 1;
+  const int RS = stage_stride(R);
+  const int p0 = blockIdx.x * R, nr = min(R, nb - p0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* cvp = conv + (size_t)l * (pbmax + 1);
+  const double* cvc = conv + (size_t)(l + 1) * (pbmax + 1);
+  for (int idx = threadIdx.x; idx < Qp * R; idx += kT) {
+    const int r = idx / Qp, n = idx % Qp;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nr) {
+      const cd g = local[eoff[parents[p0 + r]] + n];
+      const double f = 1.0 / cvp[abs(n - pp)];
+      v = make_float2((float)(g.x * f), (float)(g.y * f));
+    }
+    lam2[n * RS + r] = v;
+  }
+  __syncthreads();
+  const int c = blockIdx.y;
+  const int so = (int)blockIdx.z * kSplitCols + lane;
+  const bool act = so < Qc;
+  // warp w: parent orders [n0, n1)
+  const int per = (Qp + kSplitWarps - 1) / kSplitWarps;
+  const int n0 = min(Qp, warp * per), n1 = min(Qp, n0 + per);
+  float sr[R], si[R], cr[R], ci[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) sr[r] = si[r] = cr[r] = ci[r] = 0.f;
+  if (n1 > n0)
+    tile_gemm_column<R>(Tl + (size_t)c * Qp * Qc + (size_t)n0 * Qc, Qc, n1 - n0, lam2 + n0 * RS,
+                        so, act, sr, si, cr, ci);
+  __syncthreads();
+  double outr[R], outi[R];
+  split_reduce<R>(sr, si, cr, ci, lam2, warp, lane, outr, outi);
+  if (warp == 0 && act) {
+    const double f = cvc[abs(so - pc)];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r >= nr) break;
+      const int d = child[4 * parents[p0 + r] + c];
+      if (d < 0) continue;
+      cd* dl = local + eoff[d] + so;
+      dl->x += outr[r] * f;
+      dl->y += outi[r] * f;
+    }
+  }
+}
+
 // out[i] = eoff[idx[i]]: the coefficient offset of each M2L source row
 __global__ void gather_offsets_kernel(const int* __restrict__ idx, const long long* __restrict__ eoff,
                                       long long* __restrict__ out, int64_t n) {
@@ -611,9 +755,14 @@ __global__ void gather_offsets_kernel(const int* __restrict__ idx, const long lo
 
 }  // namespace
 
+static int g_mixed_smem_optin = 48 * 1024;  // the device's opt-in limit once configured
+
 qbx_status configure_mixed_kernels(int smem_optin) {
+  g_mixed_smem_optin = smem_optin;
   const void* k[] = {(const void*)l2l_f32_kernel<kGemmRows>, (const void*)l2l_f32_kernel<kNarrowRows>,
-                     (const void*)m2m_f32_kernel<kGemmRows>, (const void*)m2m_f32_kernel<kNarrowRows>};
+                     (const void*)m2m_f32_kernel<kGemmRows>, (const void*)m2m_f32_kernel<kNarrowRows>,
+                     (const void*)m2m_f32_split_kernel<kNarrowRows>,
+                     (const void*)l2l_f32_split_kernel<kNarrowRows>};
   for (const void* fn : k) {
     cudaFuncAttributes a;
     QBX_CUDA_TRY(cudaFuncGetAttributes(&a, fn));  // dynamic + static must fit the opt-in size
@@ -859,6 +1008,19 @@ qbx_status launch_m2l_f64_gemm_rest(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
   return QBX_OK;
 }
 
+// Dynamic shared memory of a split-K M2M / L2L CTA staging `rows` coefficient
+// rows of kNarrowRows boxes (the reduction reuses the space); split_fits: within
+// the opt-in limit with room for the kernels' static shared memory.
+static size_t split_smem(int rows) {
+  const size_t stage = (size_t)rows * stage_stride(kNarrowRows) * sizeof(float2);
+  const size_t red = (size_t)kSplitWarps * kNarrowRows * 32 * sizeof(float2);
+  return std::max(stage, red);
+}
+static bool split_fits(int rows) { return split_smem(rows) + 1024 <= (size_t)g_mixed_smem_optin; }
+// The split kernels serve levels whose one-column-per-thread grid would have
+// fewer than four CTAs per SM (GB300: 152 SMs); wider levels keep the others.
+constexpr long long kSplitBelow = 4 * 152;
+
 qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
   for (int l = f->n_levels - 2; l >= 2; --l) {
     const int nb = f->nonleaf_off[l + 1] - f->nonleaf_off[l];
@@ -868,6 +1030,10 @@ qbx_status launch_m2m_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const float2* T = f->tmm_f32.ptr + f->h_tmm_off[l];
     if (nb >= kWideLevel || h->batched)
       m2m_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), nblk(2 * pp + 1, kT)), kT, (size_t)(2 * pc + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
+          l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
+    else if ((long long)nblk(nb, kNarrowRows) * nblk(2 * pp + 1, kT) < kSplitBelow &&
+             split_fits(4 * (2 * pc + 1)))
+      m2m_f32_split_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), nblk(2 * pp + 1, kSplitCols)), kT, split_smem(4 * (2 * pc + 1)), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->mpole.ptr);
     else
       m2m_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), nblk(2 * pp + 1, kT)), kT, (size_t)(2 * pc + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
@@ -887,6 +1053,10 @@ qbx_status launch_l2l_f32(qbx_handle* h, FmmPlan* f, cudaStream_t s) {
     const float2* T = f->tl_f32.ptr + f->h_tl_off[l];
     if (nb >= kWideLevel || h->batched)
       l2l_f32_kernel<kGemmRows><<<dim3(nblk(nb, kGemmRows), 4, nblk(2 * pc + 1, kT)), kT, (size_t)(2 * pp + 1) * stage_stride(kGemmRows) * sizeof(float2), s>>>(
+          l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
+    else if ((long long)nblk(nb, kNarrowRows) * 4 * nblk(2 * pc + 1, kT) < kSplitBelow &&
+             split_fits(2 * pp + 1))
+      l2l_f32_split_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), 4, nblk(2 * pc + 1, kSplitCols)), kT, split_smem(2 * pp + 1), s>>>(
           l, pp, pc, f->pb_max, par, nb, f->box.child.ptr, f->eoff.ptr, T, f->conv.ptr, f->local.ptr);
     else
       l2l_f32_kernel<kNarrowRows><<<dim3(nblk(nb, kNarrowRows), 4, nblk(2 * pc + 1, kT)), kT, (size_t)(2 * pp + 1) * stage_stride(kNarrowRows) * sizeof(float2), s>>>(
