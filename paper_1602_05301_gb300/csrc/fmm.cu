@@ -1252,16 +1252,21 @@ __global__ void __launch_bounds__(32) m2qbxl_mixed_kernel(
     const int* re = we + (size_t)u * TW;
     const float* fm = sfm + (size_t)lc * P + p;
     const int* fe = sfe + (size_t)lc * P + p;
+    // one pass: the sums are kept relative to the largest exponent seen so
+    // far and rescaled (by a power of two) when a larger one appears
     int emax = 2 * kZeroExp;
-    for (int n = -pb; n <= pb; ++n) {
-      const int m = n + lo, am = abs(m);
-      emax = max(emax, me[off + n] + re[am] + fe[abs(n) - am]);
-    }
     float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
     for (int n = -pb; n <= pb; ++n) {
       const int m = n + lo, am = abs(m);
       const int j = abs(n) - am;
-      const int d = me[off + n] + re[am] + fe[j] - emax;
+      const int e = me[off + n] + re[am] + fe[j];
+      if (e > emax) {
+        const float r = pow2f(emax - e);
+        S = make_float2(S.x * r, S.y * r);
+        C = make_float2(C.x * r, C.y * r);
+        emax = e;
+      }
+      const int d = e - emax;
       if (d < -126) continue;
       const float f = fm[j] * pow2f(d);
       const float2 w = m >= 0 ? rp[am] : rq[am];
@@ -1322,14 +1327,21 @@ __global__ void __launch_bounds__(32) l2qbxl_mixed_kernel(Fmm F, const int* __re
     const int pb = F.lpb[F.level[b]];
     const float4* row = reinterpret_cast<const float4*>(trow + (size_t)u * TW);
     const long long off = F.eoff[b] + pb;
+    // one pass: the sums are kept relative to the largest exponent seen so
+    // far and rescaled (by a power of two) when a larger one appears
     int emax = 2 * kZeroExp;
-    for (int n = -pb; n <= pb; ++n)
-      emax = max(emax, ge[off + n] + __float_as_int(row[abs(so - n)].z));
     float2 S = make_float2(0.f, 0.f), C = make_float2(0.f, 0.f);
     for (int n = -pb; n <= pb; ++n) {
       const int m = so - n;
       const float4 v = row[abs(m)];
-      const int d = ge[off + n] + __float_as_int(v.z) - emax;
+      const int e = ge[off + n] + __float_as_int(v.z);
+      if (e > emax) {
+        const float r = pow2f(emax - e);
+        S = make_float2(S.x * r, S.y * r);
+        C = make_float2(C.x * r, C.y * r);
+        emax = e;
+      }
+      const int d = e - emax;
       if (d < -126) continue;
       // t_m = (-1)^m V_m (m >= 0), conj(V_-m) (m < 0): signs on the bits
       const unsigned fx = (m >= 0 && (m & 1)) ? 0x80000000u : 0u;
