@@ -1568,6 +1568,101 @@ __global__ void __launch_bounds__(kThreads) p2m_sum_mixed_kernel(
   }
 }
 
+// P2L in mixed precision: the item structure of p2l_item_kernel with FP32
+// rows and sums. Row j of a source holds G_j e^{i j th} (j >= 0) and
+// (-1)^j G_j e^{-i j th} (j < 0), G_j = sig_j H_j(k r) by the FP64 recurrence
+// G_{j+1} = rec[j].x (1/x) G_j - rec[j].y G_{j-1} (sig of the box's level,
+// sig_{pb+1} taken as sig_pb); X-list sources lie at least 1.5 box sides from
+// the centre, so G_j is of order one or smaller. The angular factors are FP32
+// between FP64 anchors every eighth order. Per output order n the charge and
+// the two dipole sums are FP32 with Kahan compensation over the item's
+// sources; lambda_n = sig_n gamma_n = Sq + (sig_n / sig_|n-1|) Sa -
+// (sig_n / sig_|n+1|) Sb and lh_n = lambda_n conv_|n| are formed in FP64.
+__global__ void __launch_bounds__(kThreads) p2l_item_mixed_kernel(
+    Fmm F, const int4* __restrict__ items, const int* __restrict__ src,
+    const long long* __restrict__ poff, cd* __restrict__ partial, unsigned sm_bytes,
+    const double2* __restrict__ rec) {
+  extern __shared__ cd smem[];
+  const int4 it = items[blockIdx.x];  // (box, first position in src, sources, -)
+  const int b = it.x, cnt = it.z;
+  const int l = F.level[b];
+  const int pb = F.lpb[l], RW = 2 * pb + 3;  // row: |t| <= pb+1
+  const int chunk = rows_chunk(pb, sm_bytes);
+  cd* rows = smem;                        // [chunk][RW], FP32 entries in the first half of each slot
+  cd* sq = rows + chunk * RW;             // [chunk]
+  cd* sa = sq + chunk;                    // [chunk]  A = d (k/2) nu
+  cd* sb = sa + chunk;                    // [chunk]  B = d (k/2) conj(nu)
+  const double2 m = F.centre[b];
+  if ((int)threadIdx.x < cnt) {
+    const int i = src[it.y + threadIdx.x];
+    const double dx = F.sxy[i].x - m.x, dy = F.sxy[i].y - m.y;
+    const double d2 = dx * dx + dy * dy;
+    const double ir = rsqrt(d2), x = F.k * (d2 * ir), ix = ir * F.ik;
+    cd h0, h1;
+    hankel01_wide(x, ix, h0, h1);
+    const double2* R = rec + (size_t)l * (F.pbmax + 2);
+    const cd e1 = mk(dx * ir, dy * ir);
+    cd e8 = cmul(e1, e1);
+    e8 = cmul(e8, e8);
+    e8 = cmul(e8, e8);
+    const float2 e1f = f2(e1);
+    float2* row = reinterpret_cast<float2*>(rows + threadIdx.x * RW + (pb + 1));
+    cd gprev = h0, gcur = cscale(h1, R[0].x);  // G_0, G_1
+    cd E = mk(1.0, 0.0);
+    float2 ef = make_float2(1.f, 0.f);
+    row[0] = f2(h0);
+    for (int j = 1; j <= pb + 1; ++j) {
+      if ((j & 7) == 0) {  // e^{i j th}: an FP64 anchor every eighth order
+        E = cmul(E, e8);
+        ef = f2(E);
+      } else {
+        ef = fmul(ef, e1f);
+      }
+      const float2 g = f2(gcur);
+      const float2 wp = fmul(g, ef);
+      const float2 wq = fmul(g, make_float2(ef.x, -ef.y));
+      row[2 * j] = wp;
+      row[-2 * j] = (j & 1) ? make_float2(-wq.x, -wq.y) : wq;
+      if (j <= pb) {
+        const double c1 = R[j].x * ix, c2 = R[j].y;
+        const cd gn = mk(fma(c1, gcur.x, -c2 * gprev.x), fma(c1, gcur.y, -c2 * gprev.y));
+        gprev = gcur;
+        gcur = gn;
+      }
+    }
+    const float4 ab = F.ab32[i];
+    reinterpret_cast<float2*>(sq + threadIdx.x)[0] = F.q32[i];
+    reinterpret_cast<float2*>(sa + threadIdx.x)[0] = make_float2(ab.x, ab.y);  // d (k/2) nu
+    reinterpret_cast<float2*>(sb + threadIdx.x)[0] = make_float2(ab.z, ab.w);  // d (k/2) conj(nu)
+  }
+  __syncthreads();
+  const double2* sr = F.sigr + (size_t)l * (F.pbmax + 2);
+  const double* cv = F.conv + (size_t)l * (F.pbmax + 1);
+  cd* dst = partial + poff[blockIdx.x] + pb;
+  for (int n = (int)threadIdx.x - pb; n <= pb; n += kThreads) {
+    float2 Sq = make_float2(0.f, 0.f), Cq = Sq, Sa = Sq, Ca = Sq, Sb = Sq, Cb = Sq;
+    for (int j = 0; j < cnt; ++j) {
+      const float2* r = reinterpret_cast<const float2*>(rows + j * RW + (pb + 1));
+      if (F.has_S) kahan2(Sq, Cq, fmul(reinterpret_cast<const float2*>(sq + j)[0], r[2 * n]));
+      if (F.has_D) {
+        kahan2(Sa, Ca, fmul(reinterpret_cast<const float2*>(sa + j)[0], r[2 * (n - 1)]));
+        kahan2(Sb, Cb, fmul(reinterpret_cast<const float2*>(sb + j)[0], r[2 * (n + 1)]));
+      }
+    }
+    // sig_|n| / sig_|n-1| and sig_|n| / sig_|n+1| from the ratio table (which
+    // holds sig_|n-1| / sig_|n| and sig_|n+1| / sig_|n|, 1 beyond order pb)
+    const int an = abs(n);
+    const double2 rt = sr[an];
+    const double fm = 1.0 / (n > 0 ? rt.x : rt.y), fp = 1.0 / (n < 0 ? rt.x : rt.y);
+    const double c = cv[an];
+    const double re = ((double)Sq.x - (double)Cq.x) + fm * ((double)Sa.x - (double)Ca.x) -
+                      fp * ((double)Sb.x - (double)Cb.x);
+    const double im = ((double)Sq.y - (double)Cq.y) + fm * ((double)Sa.y - (double)Ca.y) -
+                      fp * ((double)Sb.y - (double)Cb.y);
+    dst[n] = mk(re * c, im * c);
+  }
+}
+
 // Lift the 48 KB default of dynamic shared memory to the device's opt-in
 // maximum for every kernel that uses it (once per device); the size given at
 // each launch still decides the occupancy.
@@ -1583,7 +1678,8 @@ qbx_status configure_kernels() {
   QBX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const void* k[] = {(const void*)p2m_item_kernel, (const void*)p2m_item_mixed_kernel,
                      (const void*)m2m_kernel,
-                     (const void*)p2l_item_kernel, (const void*)l2l_kernel};
+                     (const void*)p2l_item_kernel, (const void*)p2l_item_mixed_kernel,
+                     (const void*)l2l_kernel};
   for (const void* f : k)
     QBX_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   TRY_MIXED(configure_mixed_kernels(optin));
@@ -2350,8 +2446,13 @@ qbx_status fmm_eval(qbx_handle* h, bool S, bool D, cd* out, int precision, bool 
   if (h->n_tgt > 0) QBX_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)h->n_tgt * sizeof(cd), s2));
   stage_begin(h, QBX_STAGE_P2L, s2);
   if ((S || D) && f->n_p2l_items > 0) {  // X lists without sources add nothing
-    p2l_item_kernel<<<f->n_p2l_items, kThreads, f->p2l_sm, s2>>>(
-        F, f->p2l_items.ptr, f->p2l_src.ptr, f->p2l_poff.ptr, f->p2l_part.ptr, (unsigned)f->p2l_sm);
+    if (mixed)
+      p2l_item_mixed_kernel<<<f->n_p2l_items, kThreads, f->p2l_sm, s2>>>(
+          F, f->p2l_items.ptr, f->p2l_src.ptr, f->p2l_poff.ptr, f->p2l_part.ptr,
+          (unsigned)f->p2l_sm, f->m2p_rec.ptr);
+    else
+      p2l_item_kernel<<<f->n_p2l_items, kThreads, f->p2l_sm, s2>>>(
+          F, f->p2l_items.ptr, f->p2l_src.ptr, f->p2l_poff.ptr, f->p2l_part.ptr, (unsigned)f->p2l_sm);
     QBX_KCHECK("p2l", s2);
     p2l_sum_kernel<<<f->n_xbox, kThreads, 0, s2>>>(F, f->xbox.ptr, f->p2l_boff.ptr, f->p2l_poff.ptr,
                                                   f->p2l_part.ptr);

@@ -48,9 +48,9 @@ __global__ void sigma_tables_kernel(int n_levels, int pbmax, const int* __restri
   isig[(size_t)l * (pbmax + 2) + lpb[l] + 1] = exp(-v);
 }
 
-// Recurrence factors of G_m = sig_m H_m on level l (mixed M2P):
+// Recurrence factors of G_m = sig_m H_m on level l (mixed M2P and P2L):
 // rec[m] = (2m sig_{m+1} / sig_m, sig_{m+1} / sig_{m-1}) for 1 <= m < pb_l,
-// rec[0] = (sig_1, 0).
+// rec[0] = (sig_1, 0), and rec[pb_l] with sig_{pb+1} taken as sig_pb.
 __global__ void m2p_rec_kernel(int n_levels, int pbmax, const int* __restrict__ lpb,
                                const double* __restrict__ lsig, double2* __restrict__ rec) {
   const int l = blockIdx.x;
@@ -63,6 +63,8 @@ __global__ void m2p_rec_kernel(int n_levels, int pbmax, const int* __restrict__ 
     if (m == 0 && pb >= 1) v.x = exp(sg[1]);
     if (m >= 1 && m < pb)
       v = make_double2(2.0 * m * exp(sg[m + 1] - sg[m]), exp(sg[m + 1] - sg[m - 1]));
+    // one order beyond pb, normalised by sig_pb (mixed P2L's dipole terms)
+    if (m == pb && pb >= 1) v = make_double2(2.0 * m, exp(sg[m] - sg[m - 1]));
     r[m] = v;
   }
 }
