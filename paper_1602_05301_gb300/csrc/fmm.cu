@@ -945,10 +945,17 @@ __device__ __forceinline__ void p2qbxl_pair(cd (&acc)[2 * PM + 1], double dx, do
 // block spreads the pairs over all SMs (the FP64 pipe is per SM).
 constexpr int kM2qbxlOrders = 4;
 constexpr int kM2qbxlBlock = 32;
-// shared memory of the L2QBXL rows of one warp (several warps per SM)
-constexpr size_t kL2qbxlSmem = 24 * 1024;
-// shared memory of the split rows of one mixed-precision M2QBXL warp
+// shared memory of the L2QBXL rows of one warp. FP64: 16 centres per warp at
+// order 16 on 41-order leaves (the dot products keep the FP64 pipe busy);
+// mixed: small enough for a dozen or more warps per SM, which hide the latency
+// of the split coefficients' loads (8 centres per warp: L2QBXL 1.29 -> 1.02
+// ms on ellipses-200; 4 was slower again)
+constexpr size_t kL2qbxlSmem = 24 * 1024, kL2qbxlMixedSmem = 12 * 1024;
+// shared memory of the split rows of one mixed-precision M2QBXL warp, and the
+// pairs per warp: at most 8, so that a dozen or more warps share an SM (8 on
+// ellipses-200: M2QBXL 1.08 -> 0.69 ms against 32)
 constexpr size_t kM2qbxlMixedSmem = 48 * 1024;
+constexpr int kM2qbxlMixedPairs = 8;
 template <int PM, bool HS, bool HD>
 __global__ void __launch_bounds__(kThreads) m2qbxl_pair_kernel(Fmm F, const int* __restrict__ pair_ctr,
                                                                const int* __restrict__ pair_box,
@@ -2292,7 +2299,8 @@ qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSe
     if (h->l2qbxl_g > 0) G = h->l2qbxl_g;  // set by an autotuner
     else
       while (!h->batched && G > 1 && (C.n + G - 1) / G < 152 * 2) G /= 2;
-    while (G > 1 && (size_t)G * TW * sizeof(cd) > kL2qbxlSmem) G /= 2;
+    const size_t lim = mixed ? kL2qbxlMixedSmem : kL2qbxlSmem;
+    while (G > 1 && (size_t)G * TW * sizeof(cd) > lim) G /= 2;
     const size_t sm = (size_t)G * TW * sizeof(cd);
     if (mixed) {
       split_coef_kernel<<<nblk(f->n_coef, 256), 256, 0, s>>>(f->local.ptr, f->n_coef, f->sp_m.ptr,
@@ -2319,12 +2327,12 @@ qbx_status launch_m2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D
   if (C.n_pairs > 0 && (S || D)) {
     const int np = C.n_pairs;
     cd* part = f->wpart.ptr;
-    // mixed: pairs per warp PW so that a warp's split rows (20 B per order)
-    // take at most kM2qbxlMixedSmem, and, for a handle evaluated alone, fewer
-    // while that leaves under two warps per SM (few pairs: spread the
-    // sequential recurrences over all SMs)
+    // mixed: pairs per warp PW (at most kM2qbxlMixedPairs) so that a warp's
+    // split rows (20 B per order) take at most kM2qbxlMixedSmem, and, for a
+    // handle evaluated alone, fewer while that leaves under two warps per SM
+    // (few pairs: spread the sequential recurrences over all SMs)
     const int TW = C.wp_pbmax + h->p + 1;
-    int PW = 32;
+    int PW = kM2qbxlMixedPairs;
     while (PW > 1 && (size_t)PW * TW * 20 > kM2qbxlMixedSmem) PW /= 2;
     while (!h->batched && PW > 1 && (np + PW - 1) / PW < 152 * 2) PW /= 2;
     if (mixed && (size_t)PW * TW * 20 <= kM2qbxlMixedSmem) {
