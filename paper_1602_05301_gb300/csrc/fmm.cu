@@ -2299,7 +2299,9 @@ qbx_status launch_l2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, const CentreSe
     if (h->l2qbxl_g > 0) G = h->l2qbxl_g;  // set by an autotuner
     else
       while (!h->batched && G > 1 && (C.n + G - 1) / G < 152 * 2) G /= 2;
-    const size_t lim = mixed ? kL2qbxlMixedSmem : kL2qbxlSmem;
+    // (batched handles share the SMs with other curves' stages and keep the
+    // larger rows)
+    const size_t lim = (mixed && !h->batched) ? kL2qbxlMixedSmem : kL2qbxlSmem;
     while (G > 1 && (size_t)G * TW * sizeof(cd) > lim) G /= 2;
     const size_t sm = (size_t)G * TW * sizeof(cd);
     if (mixed) {
@@ -2327,12 +2329,14 @@ qbx_status launch_m2qbxl(const Fmm& F, FmmPlan* f, qbx_handle* h, bool S, bool D
   if (C.n_pairs > 0 && (S || D)) {
     const int np = C.n_pairs;
     cd* part = f->wpart.ptr;
-    // mixed: pairs per warp PW (at most kM2qbxlMixedPairs) so that a warp's
-    // split rows (20 B per order) take at most kM2qbxlMixedSmem, and, for a
-    // handle evaluated alone, fewer while that leaves under two warps per SM
-    // (few pairs: spread the sequential recurrences over all SMs)
+    // mixed: pairs per warp PW (at most kM2qbxlMixedPairs for a handle
+    // evaluated alone, 32 for batched handles, which share the SMs with other
+    // curves' stages) so that a warp's split rows (20 B per order) take at most
+    // kM2qbxlMixedSmem, and, for a handle evaluated alone, fewer while that
+    // leaves under two warps per SM (few pairs: spread the sequential
+    // recurrences over all SMs)
     const int TW = C.wp_pbmax + h->p + 1;
-    int PW = kM2qbxlMixedPairs;
+    int PW = h->batched ? 32 : kM2qbxlMixedPairs;
     while (PW > 1 && (size_t)PW * TW * 20 > kM2qbxlMixedSmem) PW /= 2;
     while (!h->batched && PW > 1 && (np + PW - 1) / PW < 152 * 2) PW /= 2;
     if (mixed && (size_t)PW * TW * 20 <= kM2qbxlMixedSmem) {
